@@ -1,0 +1,789 @@
+/*
+ * abc_oracle.c -- plain, slow, sequential CPU oracle for P-ABC-SMC with
+ * Beta-distributed step sizes (arXiv 2106.15508).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  The
+ * product path (paper_2106_15508_gb300) never calls it and shares no code,
+ * header, table or constant with it.
+ *
+ * Every function cites the passage of the paper it follows.  The paper fixes
+ * the method but not its floating-point detail; the operation order below is
+ * the project's numerics specification (fp32 for per-particle arithmetic,
+ * explicit fmaf where the spec says fma, no contraction otherwise), written
+ * from the mathematics:
+ *   - Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ *     easy as 1, 2, 3", SC'11.
+ *   - log/exp/expm1: Cody & Waite argument reduction (x = k ln2 + r) with the
+ *     Taylor series of exp and the atanh series of log, coefficients the
+ *     fp32 values nearest to 1/k! and 1/(2k+1).
+ *   - log1p: Goldberg's identity log1p(x) = x log(u)/(u-1), u = 1+x.
+ *   - cos(2 pi w): reduction in turns by symmetry, Taylor series of sin/cos.
+ *   - Binomial: BINV inversion (Kachitvichyanukul & Schmeiser 1988) when the
+ *     mean is below 10, else a rounded normal approximation.
+ *   - Beta(a, b) for integer b: product of B(a+m, 1) variates.
+ *
+ * Parity status of every function is stated in the tests that pin it; the
+ * end-to-end SAIRD posterior has no ground truth ("parity unpinned" beyond
+ * oracle agreement, the invariants and recovery of the true parameters).
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared [-fopenmp]
+ * (-ffp-contract=off is mandatory: it forbids the compiler from fusing a*b+c).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_API __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (SC'11): 10 rounds of two 32x32->64 multiplies, key bumped   */
+/* by the Weyl constants between rounds.                                      */
+/* ------------------------------------------------------------------------ */
+OR_API void or_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+    uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+    uint32_t y1 = (uint32_t)p1;
+    uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+    uint32_t y3 = (uint32_t)p0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static void philox_ctr(const uint32_t key[2], uint32_t c0, uint32_t c1, uint32_t c2,
+                       uint32_t c3, uint32_t out[4]) {
+  uint32_t c[4] = {c0, c1, c2, c3};
+  or_philox(c, key, out);
+}
+
+/* Stream tags: the fourth counter word. */
+enum { TAG_PRIOR = 0, TAG_ANCESTOR = 1, TAG_BETA = 2, TAG_WALK = 3, TAG_SIM = 4,
+       TAG_OBS = 7, TAG_OBS_THETA = 8 };
+
+/* u32 -> (0,1): the top 23 bits plus one half, times 2^-23.  Every step is
+ * exact in fp32 and the result lies in [2^-24, 1 - 2^-24] (with 24 bits the
+ * largest value would round up to 1). */
+OR_API float or_uniform(uint32_t x) {
+  return ((float)(x >> 9) + 0.5f) * 0x1p-23f;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Transcendentals (fp32).                                                    */
+/* ------------------------------------------------------------------------ */
+static const float LN2_HI = 0x1.62e4p-1f;      /* 0.693145751953125, 15 significant bits */
+static const float LN2_LO = 0x1.7f7d1cp-20f;   /* fp32 nearest to ln2 - LN2_HI */
+static const float LOG2E  = 0x1.715476p+0f;    /* fp32 nearest to 1/ln2 */
+static const float TWO_PI = 0x1.921fb6p+2f;    /* fp32 nearest to 2 pi */
+static const float SQRT2F = 0x1.6a09e6p+0f;    /* fp32 nearest to sqrt 2 */
+/* fp32 nearest to 1/k!, k = 0..13 */
+static const float INV_FACT[14] = {
+  1.0f, 1.0f, 0.5f, 0x1.555556p-3f, 0x1.555556p-5f, 0x1.111112p-7f, 0x1.6c16c2p-10f,
+  0x1.a01a02p-13f, 0x1.a01a02p-16f, 0x1.71de3ap-19f, 0x1.27e4fcp-22f, 0x1.ae6456p-26f,
+  0x1.1eed8ep-29f, 0x1.612462p-33f};
+/* fp32 nearest to 1/(2k+1), k = 1..5 */
+static const float INV_ODD[6] = {1.0f, 0x1.555556p-2f, 0x1.99999ap-3f, 0x1.24924ap-3f,
+                                 0x1.c71c72p-4f, 0x1.745d18p-4f};
+
+static inline uint32_t f2u(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+static inline float u2f(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
+
+/* Exposes the constants so that a test can pin them to their definitions. */
+OR_API int or_constants(float* out, int n) {
+  float all[5 + 14 + 5] = {LN2_HI, LN2_LO, LOG2E, TWO_PI, SQRT2F};
+  for (int k = 0; k < 14; ++k) all[5 + k] = INV_FACT[k];
+  for (int k = 1; k <= 5; ++k) all[18 + k] = INV_ODD[k];
+  int m = n < 24 ? n : 24;
+  for (int i = 0; i < m; ++i) out[i] = all[i];
+  return 24;
+}
+
+/* natural log: x = m 2^e, m in [sqrt(1/2), sqrt 2), log m = 2 atanh(f),
+ * f = (m-1)/(m+1), series up to f^11; result e*LN2_HI + (e*LN2_LO + log m). */
+OR_API float or_logf(float x) {
+  if (x != x || x < 0.0f) return NAN;
+  if (x == 0.0f) return -INFINITY;
+  if (x == INFINITY) return INFINITY;
+  int e = 0;
+  if (x < 0x1p-126f) { x = x * 0x1p24f; e = -24; }
+  uint32_t b = f2u(x);
+  e += (int)(b >> 23) - 127;
+  float m = u2f((b & 0x007FFFFFu) | 0x3F800000u);
+  if (m > SQRT2F) { m = m * 0.5f; e = e + 1; }
+  float f = (m - 1.0f) / (m + 1.0f);
+  float f2 = f * f;
+  float p = INV_ODD[5];
+  p = fmaf(p, f2, INV_ODD[4]);
+  p = fmaf(p, f2, INV_ODD[3]);
+  p = fmaf(p, f2, INV_ODD[2]);
+  p = fmaf(p, f2, INV_ODD[1]);
+  float t = f2 * p;
+  float r = f + f;
+  float lm = fmaf(r, t, r);
+  float fe = (float)e;
+  float hi = fe * LN2_HI;
+  float lo = fmaf(fe, LN2_LO, lm);
+  return hi + lo;
+}
+
+/* 2^k as fp32 for k in [-126, 127] */
+static inline float pow2i(int k) { return u2f((uint32_t)(k + 127) << 23); }
+
+/* multiply by 2^k with at most one rounding (into the subnormal range) */
+static float scale2(float p, int k) {
+  if (k > 127) return (p * 0x1p127f) * pow2i(k - 127);
+  if (k < -126) return (p * pow2i(k + 64)) * 0x1p-64f;
+  return p * pow2i(k);
+}
+
+/* exp: k = floor(x log2e + 1/2), r = (x - k LN2_HI) - k LN2_LO, Taylor to r^8. */
+OR_API float or_expf(float x) {
+  if (x != x) return x;
+  if (x > 88.72283935546875f) return INFINITY;
+  if (x < -103.972084045410156f) return 0.0f;
+  float kf = floorf(x * LOG2E + 0.5f);
+  int k = (int)kf;
+  float r = x - kf * LN2_HI;
+  r = r - kf * LN2_LO;
+  float p = INV_FACT[8];
+  for (int i = 7; i >= 0; --i) p = fmaf(p, r, INV_FACT[i]);
+  return scale2(p, k);
+}
+
+/* Taylor series of expm1 on |r| <= ln2/2 up to r^9: r + r^2 (1/2 + r/6 + ...) */
+static float expm1_series(float r) {
+  float q = INV_FACT[9];
+  for (int i = 8; i >= 2; --i) q = fmaf(q, r, INV_FACT[i]);
+  float t = r * r;
+  return fmaf(t, q, r);
+}
+
+OR_API float or_expm1f(float x) {
+  if (x != x) return x;
+  if (x > 88.72283935546875f) return INFINITY;
+  if (x < -17.5f) return -1.0f;
+  if (fabsf(x) <= 0.3465735912322998f) return expm1_series(x);
+  float kf = floorf(x * LOG2E + 0.5f);
+  int k = (int)kf;
+  float r = x - kf * LN2_HI;
+  r = r - kf * LN2_LO;
+  float em = expm1_series(r);
+  if (k > 127) return INFINITY;
+  float two = pow2i(k);
+  return fmaf(two, em, two - 1.0f);
+}
+
+/* log1p(x), x > -1: Goldberg's identity. */
+OR_API float or_log1pf(float x) {
+  float u = 1.0f + x;
+  if (u == 1.0f) return x;
+  return (or_logf(u) / (u - 1.0f)) * x;
+}
+
+/* cos(2 pi w) for w in [0, 1]. */
+OR_API float or_cos2pi(float w) {
+  float v = w;
+  if (v > 0.5f) v = 1.0f - v;             /* cos(2pi(1-v)) = cos(2pi v), exact */
+  float sign = 1.0f;
+  if (v > 0.25f) { v = 0.5f - v; sign = -1.0f; }  /* cos(pi - y) = -cos y, exact */
+  float c;
+  if (v <= 0.125f) {
+    float x = v * TWO_PI;
+    float x2 = x * x;
+    /* cos x = sum (-1)^k x^2k/(2k)!, k = 0..6 */
+    float p = INV_FACT[12];
+    p = fmaf(p, x2, -INV_FACT[10]);
+    p = fmaf(p, x2, INV_FACT[8]);
+    p = fmaf(p, x2, -INV_FACT[6]);
+    p = fmaf(p, x2, INV_FACT[4]);
+    p = fmaf(p, x2, -INV_FACT[2]);
+    c = fmaf(p, x2, 1.0f);
+  } else {
+    float x = (0.25f - v) * TWO_PI;          /* cos(pi/2 - y) = sin y */
+    float x2 = x * x;
+    /* sin x = x + x x2 Q(x2), Q = sum_{k=1..6} (-1)^k x2^(k-1)/(2k+1)! */
+    float q = INV_FACT[13];
+    q = fmaf(q, x2, -INV_FACT[11]);
+    q = fmaf(q, x2, INV_FACT[9]);
+    q = fmaf(q, x2, -INV_FACT[7]);
+    q = fmaf(q, x2, INV_FACT[5]);
+    q = fmaf(q, x2, -INV_FACT[3]);
+    c = fmaf(x * x2, q, x);
+  }
+  return sign * c;
+}
+
+/* Box-Muller, cosine branch only. */
+OR_API float or_normal(float w1, float w2) {
+  float l = or_logf(w1);
+  float t = -2.0f * l;
+  float r = sqrtf(t);
+  return r * or_cos2pi(w2);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Binomial(n, p) from two uniforms (spec: binomial daily transitions; */
+/* the paper's tau-leap flows, Sec. 2.2, as exact-count competing risks).    */
+/* ------------------------------------------------------------------------ */
+OR_API int32_t or_binomial(int32_t n, float p, float w1, float w2) {
+  if (n <= 0 || !(p > 0.0f)) return 0;
+  if (p >= 1.0f) return n;
+  int flip = p > 0.5f;
+  float q = flip ? (1.0f - p) : p;
+  float nf = (float)n;
+  float mu = nf * q;
+  int32_t k;
+  if (mu < 10.0f) {
+    /* BINV: walk the pmf from 0, f(x) = f(x-1) (a/x - s) */
+    float s = q / (1.0f - q);
+    float a = (nf + 1.0f) * s;
+    float r = or_expf(nf * or_log1pf(-q));
+    float u = w1;
+    int32_t cap = n < 110 ? n : 110;
+    int32_t x = 0;
+    for (;;) {
+      if (u <= r) break;
+      if (x == cap) break;
+      u = u - r;
+      x = x + 1;
+      r = r * (a / (float)x - s);
+    }
+    k = x;
+  } else {
+    float sd = sqrtf(mu * (1.0f - q));
+    float z = or_normal(w1, w2);
+    float y = floorf((mu + sd * z) + 0.5f);
+    if (y < 0.0f) y = 0.0f;
+    if (y > nf) y = nf;
+    k = (int32_t)y;
+    if (k > n) k = n;
+  }
+  return flip ? n - k : k;
+}
+
+/* Paper's flow draw (Sec. 2.2): floor(Normal(h, sd sqrt h)), clamped to [0, cap]. */
+static int32_t paper_flow(float h, int32_t cap, float w1, float w2) {
+  if (cap <= 0 || !(h > 0.0f)) return 0;
+  float z = or_normal(w1, w2);
+  float y = floorf(h + sqrtf(h) * z);
+  if (y < 0.0f) y = 0.0f;
+  if (y > (float)cap) y = (float)cap;
+  int32_t k = (int32_t)y;
+  return k > cap ? cap : k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Model description                                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t model;        /* 0 = stochastic SAIRD (Sec. 2.2), 1 = Gaussian toy      */
+  int32_t sampler;      /* 0 = binomial transitions, 1 = paper floor-normal      */
+  int32_t T;            /* days                                                  */
+  int32_t pad0;
+  int64_t P;            /* population                                            */
+  int32_t A0, R0, D0;   /* observed day-0 state                                  */
+  int32_t pad1;
+  float theta_lo[8];    /* prior U(theta_lo, theta_hi) (Eq. 2)                   */
+  float theta_hi[8];
+  const int32_t* obs;   /* [3][T+1] rows A, R, D; column t = day t               */
+  float x_obs[8];       /* toy model observation                                 */
+  uint32_t key[2];      /* Philox key = (seed_lo, seed_hi ^ run)                  */
+} or_model;
+
+/* theta_d = lo_d + u_d (hi_d - lo_d), the paper's reparameterisation (Sec. 3.1) */
+static void theta_from_u(const or_model* m, const float u[8], float th[8]) {
+  for (int d = 0; d < 8; ++d) {
+    float w = m->theta_hi[d] - m->theta_lo[d];
+    th[d] = m->theta_lo[d] + u[d] * w;
+  }
+}
+
+/* Correctly rounded double of an unsigned 128-bit integer (gcc's conversion). */
+static double u128_to_double(unsigned __int128 v) { return (double)v; }
+
+/*
+ * One stochastic SAIRD trajectory (Sec. 2.2, Eq. 3-5) and its Euclidean
+ * distance to the observed A, R, D series over days 1..T (Sec. 2.3).
+ * theta = [alpha0, alpha, n, beta, gamma, delta, eta, kappa] (Eq. 1).
+ * Philox counters: (c0, c1, 4 day + block, tag), blocks 0..2 per day.
+ * traj (nullable): [T+1][6][stride] compartments S, I, A, R, D, Ru.
+ */
+static double simulate_saird(const or_model* m, const float th[8], uint32_t c0, uint32_t c1,
+                             uint32_t tag, int32_t* traj, int64_t stride, int64_t col,
+                             int32_t* out_ard) {
+  float alpha0 = th[0], alpha = th[1], n = th[2], beta = th[3], gamma = th[4],
+        delta = th[5], eta = th[6], kappa = th[7];
+  /* initial state: Ru = 0, I0 = kappa A0, S = P - (A0 + R0 + D0 + I0) */
+  int64_t A = m->A0, R = m->R0, D = m->D0;
+  int64_t I = (int64_t)floorf(kappa * (float)m->A0);
+  int64_t S = m->P - (A + R + D + I);
+  if (S < 0) { I = m->P - (A + R + D); if (I < 0) I = 0; S = 0; }
+  int64_t Ru = 0;
+  float Pf = (float)m->P;
+  /* per-particle constants of the competing risks out of I and A */
+  float lamI = gamma + beta * eta;            /* I -> A at gamma, I -> Ru at beta eta */
+  float lamA = beta + delta;                  /* A -> R at beta, A -> D at delta */
+  float pI = -or_expm1f(-lamI);
+  float pA = -or_expm1f(-lamA);
+  float fI = lamI > 0.0f ? gamma / lamI : 0.0f;
+  float fA = lamA > 0.0f ? beta / lamA : 0.0f;
+  unsigned __int128 acc = 0;
+  if (traj) {
+    int32_t* t0 = traj + col;
+    t0[0 * stride] = (int32_t)S; t0[1 * stride] = (int32_t)I; t0[2 * stride] = (int32_t)A;
+    t0[3 * stride] = (int32_t)R; t0[4 * stride] = (int32_t)D; t0[5 * stride] = (int32_t)Ru;
+  }
+  for (int32_t day = 0; day < m->T; ++day) {
+    uint32_t w[12];
+    philox_ctr(m->key, c0, c1, (uint32_t)day * 4u + 0u, tag, w + 0);
+    philox_ctr(m->key, c0, c1, (uint32_t)day * 4u + 1u, tag, w + 4);
+    philox_ctr(m->key, c0, c1, (uint32_t)day * 4u + 2u, tag, w + 8);
+    float v[10];
+    for (int i = 0; i < 10; ++i) v[i] = or_uniform(w[i]);
+    /* g = alpha0 + alpha / (1 + (A+R+D)^n)  (Eq. 4), x^n = exp(n log x) */
+    int64_t x = A + R + D;
+    float xn;
+    if (x == 0) xn = n > 0.0f ? 0.0f : 1.0f;
+    else xn = or_expf(n * or_logf((float)x));
+    float g = alpha0 + alpha / (1.0f + xn);
+    int64_t k1, k2, k3, k4, k5;
+    if (m->sampler == 0) {
+      /* hazard g S I / P (Eq. 5) as the per-susceptible daily probability */
+      float t = g * (float)I;
+      t = t / Pf;
+      float pSI = -or_expm1f(-t);
+      k1 = or_binomial((int32_t)S, pSI, v[0], v[1]);
+      int64_t LI = or_binomial((int32_t)I, pI, v[2], v[3]);
+      k2 = or_binomial((int32_t)LI, fI, v[4], v[5]);
+      k5 = LI - k2;
+      int64_t LA = or_binomial((int32_t)A, pA, v[6], v[7]);
+      k3 = or_binomial((int32_t)LA, fA, v[8], v[9]);
+      k4 = LA - k3;
+    } else {
+      /* the paper's floor(Normal(h, sqrt h)) in h order (Sec. 2.2) */
+      float h1 = (g * (float)S) * ((float)I / Pf);
+      float h2 = gamma * (float)I;
+      float h3 = beta * (float)A;
+      float h4 = delta * (float)A;
+      float h5 = (beta * eta) * (float)I;
+      k1 = paper_flow(h1, (int32_t)S, v[0], v[1]);
+      k2 = paper_flow(h2, (int32_t)I, v[2], v[3]);
+      k3 = paper_flow(h3, (int32_t)A, v[4], v[5]);
+      k4 = paper_flow(h4, (int32_t)(A - k3), v[6], v[7]);
+      k5 = paper_flow(h5, (int32_t)(I - k2), v[8], v[9]);
+    }
+    S -= k1;
+    I += k1 - k2 - k5;
+    A += k2 - k3 - k4;
+    R += k3;
+    D += k4;
+    Ru += k5;
+    if (traj) {
+      int32_t* tt = traj + (int64_t)(day + 1) * 6 * stride + col;
+      tt[0 * stride] = (int32_t)S; tt[1 * stride] = (int32_t)I; tt[2 * stride] = (int32_t)A;
+      tt[3 * stride] = (int32_t)R; tt[4 * stride] = (int32_t)D; tt[5 * stride] = (int32_t)Ru;
+    }
+    if (out_ard) {
+      out_ard[0 * (m->T + 1) + day + 1] = (int32_t)A;
+      out_ard[1 * (m->T + 1) + day + 1] = (int32_t)R;
+      out_ard[2 * (m->T + 1) + day + 1] = (int32_t)D;
+    }
+    if (m->obs) {
+      const int32_t* o = m->obs;
+      int64_t dA = A - o[0 * (m->T + 1) + day + 1];
+      int64_t dR = R - o[1 * (m->T + 1) + day + 1];
+      int64_t dD = D - o[2 * (m->T + 1) + day + 1];
+      acc += (unsigned __int128)(uint64_t)(dA * dA);
+      acc += (unsigned __int128)(uint64_t)(dR * dR);
+      acc += (unsigned __int128)(uint64_t)(dD * dD);
+    }
+  }
+  return sqrt(u128_to_double(acc));
+}
+
+/* Gaussian toy: x = theta + z, z ~ N(0, I8); distance ||x - x_obs|| (test model). */
+static double simulate_toy(const or_model* m, const float th[8], uint32_t c0, uint32_t c1,
+                           uint32_t tag) {
+  double acc = 0.0;
+  for (int b = 0; b < 4; ++b) {
+    uint32_t w[4];
+    philox_ctr(m->key, c0, c1, (uint32_t)b, tag, w);
+    for (int h = 0; h < 2; ++h) {
+      int d = 2 * b + h;
+      float z = or_normal(or_uniform(w[2 * h]), or_uniform(w[2 * h + 1]));
+      float x = th[d] + z;
+      double e = (double)x - (double)m->x_obs[d];
+      acc = acc + e * e;
+    }
+  }
+  return sqrt(acc);
+}
+
+/*
+ * Simulate n particles given in unit coordinates u ([8][n] SoA).  c0 of
+ * particle i is c0_idx[i] (or i when c0_idx is NULL); skip[i] != 0 gives +inf.
+ */
+OR_API void or_simulate(const or_model* m, const float* u, int64_t n, const uint32_t* c0_idx,
+                        uint32_t c1, uint32_t tag, const uint8_t* skip, double* dist,
+                        int32_t* traj, int nthreads) {
+  (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    if (skip && skip[i]) { dist[i] = INFINITY; continue; }
+    float ui[8], th[8];
+    for (int d = 0; d < 8; ++d) ui[d] = u[(int64_t)d * n + i];
+    theta_from_u(m, ui, th);
+    uint32_t c0 = c0_idx ? c0_idx[i] : (uint32_t)i;
+    if (m->model == 1) dist[i] = simulate_toy(m, th, c0, c1, tag);
+    else dist[i] = simulate_saird(m, th, c0, c1, tag, traj, n, i, NULL);
+  }
+}
+
+/*
+ * Synthetic observations (stand-in for the JHU series, Sec. 2.2): theta* from
+ * the growing-epidemic sub-box [lo, hi] with the OBS_THETA stream, simulated
+ * with the OBS stream; redrawn (attempt = c1) until A_T > A0, at most 64 times.
+ */
+OR_API int32_t or_synth_obs(or_model* m, const float lo[8], const float hi[8], int32_t* obs,
+                            float* theta_star) {
+  const int32_t* keep = m->obs;
+  m->obs = NULL;
+  int32_t attempt = 0;
+  for (attempt = 0; attempt < 64; ++attempt) {
+    uint32_t w[8];
+    philox_ctr(m->key, 0u, (uint32_t)attempt, 0u, TAG_OBS_THETA, w);
+    philox_ctr(m->key, 0u, (uint32_t)attempt, 1u, TAG_OBS_THETA, w + 4);
+    float th[8];
+    for (int d = 0; d < 8; ++d) {
+      float v = or_uniform(w[d]);
+      float span = hi[d] - lo[d];
+      th[d] = lo[d] + v * span;
+    }
+    obs[0 * (m->T + 1)] = m->A0;
+    obs[1 * (m->T + 1)] = m->R0;
+    obs[2 * (m->T + 1)] = m->D0;
+    simulate_saird(m, th, 0u, (uint32_t)attempt, TAG_OBS, NULL, 0, 0, obs);
+    memcpy(theta_star, th, sizeof th);
+    if (obs[0 * (m->T + 1) + m->T] > m->A0) break;
+  }
+  m->obs = keep;
+  return attempt < 64 ? attempt + 1 : -64;
+}
+
+/* ------------------------------------------------------------------------ */
+/* ABC-SMC steps (Sec. 2.3-2.4, 3.2)                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Stage 0 (Sec. 2.4): u ~ U(0,1)^8 with the PRIOR stream, blocks 0 and 1. */
+OR_API void or_prior(const or_model* m, int64_t n, float* u) {
+  for (int64_t j = 0; j < n; ++j) {
+    uint32_t w[8];
+    philox_ctr(m->key, (uint32_t)j, 0u, 0u, TAG_PRIOR, w);
+    philox_ctr(m->key, (uint32_t)j, 0u, 1u, TAG_PRIOR, w + 4);
+    for (int d = 0; d < 8; ++d) u[(int64_t)d * n + j] = or_uniform(w[d]);
+  }
+}
+
+static int cmp_double(const void* a, const void* b) {
+  double x = *(const double*)a, y = *(const double*)b;
+  return (x > y) - (x < y);
+}
+
+/* Percentile (Eq. 8): the k-th smallest distance (1-based, lower order statistic). */
+OR_API double or_kth(const double* d, int64_t n, int64_t k) {
+  double* c = (double*)malloc(sizeof(double) * (size_t)n);
+  memcpy(c, d, sizeof(double) * (size_t)n);
+  qsort(c, (size_t)n, sizeof(double), cmp_double);
+  double v = c[k - 1];
+  free(c);
+  return v;
+}
+
+/* k = ceil(alpha N), clamped to [1, N] */
+OR_API int64_t or_rank(double alpha, int64_t n) {
+  int64_t k = (int64_t)ceil(alpha * (double)n);
+  if (k < 1) k = 1;
+  if (k > n) k = n;
+  return k;
+}
+
+/*
+ * Stage prior and its weights (Eq. 9-10): survivors are d_j <= eps.
+ * mode 0 (paper): r_j = eps - d_j; mode 1 (importance): r_j = W_j.
+ * q_j = floor(r_j / max r * (2^32 - 1)); prefix = inclusive sum of q (u64).
+ * When max r is zero every survivor gets q_j = 1.  Returns the total.
+ */
+OR_API uint64_t or_resample_prefix(const double* d, const double* W, int64_t n, double eps,
+                                   int mode, uint32_t* q, uint64_t* prefix) {
+  double rmax = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    double r = 0.0;
+    if (d[j] <= eps) r = mode == 0 ? eps - d[j] : W[j];
+    if (r > rmax) rmax = r;
+  }
+  uint64_t tot = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    uint32_t qj;
+    if (rmax > 0.0 && rmax <= 1.79e308) {
+      double r = 0.0;
+      if (d[j] <= eps) r = mode == 0 ? eps - d[j] : W[j];
+      qj = (uint32_t)floor(r / rmax * 4294967295.0);
+    } else {
+      qj = d[j] <= eps ? 1u : 0u;
+    }
+    q[j] = qj;
+    tot += qj;
+    prefix[j] = tot;
+  }
+  return tot;
+}
+
+/* Categorical draw (Eq. 11): first k with prefix[k] > x, x = floor(U total / 2^64). */
+static int64_t draw_ancestor(const uint64_t* prefix, int64_t n, uint64_t total, uint32_t w0,
+                             uint32_t w1) {
+  uint64_t U = ((uint64_t)w1 << 32) | (uint64_t)w0;
+  uint64_t x = (uint64_t)(((unsigned __int128)U * (unsigned __int128)total) >> 64);
+  /* binary search for the first k with prefix[k] > x */
+  int64_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (prefix[mid] > x) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+/* s ~ Beta(a, b), integer b: exp(sum_{m<b} log(U_m) / (a + m)) (BETA stream). */
+OR_API float or_beta(const uint32_t key[2], float a, int32_t b, uint32_t c0, uint32_t c1,
+                     uint32_t attempt) {
+  float acc = 0.0f;
+  uint32_t w[4] = {0, 0, 0, 0};
+  for (int32_t mm = 0; mm < b; ++mm) {
+    if ((mm & 3) == 0)
+      philox_ctr(key, c0, c1, (attempt << 8) | (uint32_t)(mm >> 2), TAG_BETA, w);
+    float U = or_uniform(w[mm & 3]);
+    acc = acc + or_logf(U) / (a + (float)mm);
+  }
+  return or_expf(acc);
+}
+
+/*
+ * BDSS perturbation (Eq. 16-17) with the categorical ancestor draw (Eq. 11)
+ * and a prior-support check: for slot j of batch c1 = (t << 16) | batch,
+ * attempt a = 0..max_redraw-1 draws (ancestor, s, z) afresh until
+ * u' = u_anc + sqrt(s) z lies in [0,1]^8.  On exhaustion flag = 1.
+ */
+OR_API void or_propose(const or_model* m, const float* u, int64_t n, const uint64_t* prefix,
+                       uint64_t total, float beta_a, int32_t beta_b, int64_t slots,
+                       const uint32_t* c0_idx, uint32_t c1, int32_t max_redraw, float* u_out,
+                       float* s_out, int32_t* anc_out, int32_t* attempts_out, uint8_t* flag_out,
+                       int nthreads) {
+  (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int64_t i = 0; i < slots; ++i) {
+    uint32_t j = c0_idx ? c0_idx[i] : (uint32_t)i;
+    float up[8] = {0};
+    float s = 0.0f;
+    int64_t anc = 0;
+    int ok = 0;
+    int32_t a;
+    for (a = 0; a < max_redraw; ++a) {
+      uint32_t w[4];
+      philox_ctr(m->key, j, c1, (uint32_t)a, TAG_ANCESTOR, w);
+      anc = draw_ancestor(prefix, n, total, w[0], w[1]);
+      s = or_beta(m->key, beta_a, beta_b, j, c1, (uint32_t)a);
+      float sd = sqrtf(s);
+      ok = 1;
+      for (int blk = 0; blk < 4; ++blk) {
+        uint32_t z4[4];
+        philox_ctr(m->key, j, c1, ((uint32_t)a << 8) | (uint32_t)blk, TAG_WALK, z4);
+        for (int h = 0; h < 2; ++h) {
+          int d = 2 * blk + h;
+          float z = or_normal(or_uniform(z4[2 * h]), or_uniform(z4[2 * h + 1]));
+          float step = sd * z;
+          up[d] = u[(int64_t)d * n + anc] + step;
+          if (!(up[d] >= 0.0f && up[d] <= 1.0f)) ok = 0;
+        }
+      }
+      if (ok) break;
+    }
+    for (int d = 0; d < 8; ++d) u_out[(int64_t)d * slots + i] = up[d];
+    s_out[i] = s;
+    anc_out[i] = (int32_t)anc;
+    attempts_out[i] = ok ? a + 1 : max_redraw;
+    flag_out[i] = ok ? 0 : 1;
+  }
+}
+
+/*
+ * Importance weight (auxiliary-variable form, spec extension; not in
+ * the paper): log W_j = log pi(u'_j) - log sum_k rhat_k N(u'_j; u_k, s_j I8),
+ * rhat_k = q_k / total, pi uniform on the unit cube.  fp64 throughout.
+ */
+OR_API void or_weights(const float* up, const float* s, int64_t rows, const float* u,
+                       const uint32_t* q, int64_t n, uint64_t total, double* logW,
+                       int nthreads) {
+  (void)nthreads;
+  double ltot = log((double)total);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int64_t j = 0; j < rows; ++j) {
+    double sj = (double)s[j];
+    if (!(sj > 0.0)) { logW[j] = -INFINITY; continue; }
+    double* e = (double*)malloc(sizeof(double) * (size_t)n);
+    double mx = -INFINITY;
+    for (int64_t k = 0; k < n; ++k) {
+      if (q[k] == 0) { e[k] = -INFINITY; continue; }
+      double D = 0.0;
+      for (int d = 0; d < 8; ++d) {
+        double diff = (double)up[(int64_t)d * rows + j] - (double)u[(int64_t)d * n + k];
+        D += diff * diff;
+      }
+      e[k] = (log((double)q[k]) - ltot) - D / (2.0 * sj);
+      if (e[k] > mx) mx = e[k];
+    }
+    double sum = 0.0;
+    for (int64_t k = 0; k < n; ++k)
+      if (e[k] > -INFINITY) sum += exp(e[k] - mx);
+    double lse = mx + log(sum);
+    logW[j] = 4.0 * log(2.0 * M_PI * sj) - lse;
+    free(e);
+  }
+}
+
+/* W_j = exp(logW_j - max) / sum; ESS = 1 / sum W_j^2 (fp64). */
+OR_API double or_normalize(const double* logW, int64_t n, double* W) {
+  double mx = -INFINITY;
+  for (int64_t j = 0; j < n; ++j) if (logW[j] > mx) mx = logW[j];
+  if (!(mx > -INFINITY) || mx != mx) {
+    for (int64_t j = 0; j < n; ++j) W[j] = 1.0 / (double)n;
+    return (double)n;
+  }
+  double sum = 0.0;
+  for (int64_t j = 0; j < n; ++j) { W[j] = exp(logW[j] - mx); sum += W[j]; }
+  double s2 = 0.0;
+  for (int64_t j = 0; j < n; ++j) { W[j] = W[j] / sum; s2 += W[j] * W[j]; }
+  return 1.0 / s2;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One SMC generation (Sec. 2.4 and 3.2).                                     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t N;            /* population (samples kept per stage)             */
+  int32_t M;            /* proposals per batch ("parallel simulations")    */
+  int32_t pad;
+  double alpha;         /* survival ratio (Eq. 8), 0.5 in the paper         */
+  int32_t beta_mode;    /* 0: Beta(eps_t/eps_1, 2t) (Eq. 16); 1: fixed      */
+  float beta_a;
+  int32_t beta_b;
+  int32_t weight_mode;  /* 0: eps - d (Eq. 10); 1: importance weights       */
+  int32_t max_batches;
+  int32_t max_redraw;
+  int32_t nthreads;
+} or_smc;
+
+typedef struct {
+  double eps;           /* eps_t used by this generation                    */
+  double eps1;          /* eps_1                                            */
+  double ess;
+  float beta_a;
+  int32_t beta_b;
+  int64_t batches, sims, exhausted, accepted_total;
+  uint64_t total;       /* resampling total                                  */
+  int32_t status;       /* 0 ok, 1 batch budget exhausted                   */
+} or_gen_stats;
+
+/* Generation 0 (Sec. 2.4): plain ABC from the prior with eps_0 = +inf. */
+OR_API void or_generation0(const or_model* m, const or_smc* c, float* u, double* d, double* W) {
+  or_prior(m, c->N, u);
+  or_simulate(m, u, c->N, NULL, 0u, TAG_SIM, NULL, d, NULL, c->nthreads);
+  for (int64_t j = 0; j < c->N; ++j) W[j] = 1.0 / (double)c->N;
+}
+
+/*
+ * Generation t >= 1: eps_t from the previous population (Eq. 8), the stage
+ * prior and weights (Eq. 9-10), then batches of M proposals (Eq. 11, 16, 17),
+ * simulation and acceptance d' <= eps_t, appended in (batch, slot) order
+ * until N are filled; then the new weights.
+ */
+OR_API int32_t or_generation(const or_model* m, const or_smc* c, int32_t t, double eps1_in,
+                             const float* u, const double* d, const double* W, float* u_new,
+                             double* d_new, double* W_new, float* s_new, int32_t* anc_new,
+                             double* logW_new, or_gen_stats* st) {
+  int64_t N = c->N, M = c->M;
+  memset(st, 0, sizeof *st);
+  double eps = or_kth(d, N, or_rank(c->alpha, N));
+  double eps1 = t == 1 ? eps : eps1_in;
+  st->eps = eps;
+  st->eps1 = eps1;
+  float ba;
+  int32_t bb;
+  if (c->beta_mode == 0) {
+    ba = eps1 > 0.0 ? (float)(eps / eps1) : 1.0f;
+    bb = 2 * t;
+  } else {
+    ba = c->beta_a;
+    bb = c->beta_b;
+  }
+  st->beta_a = ba;
+  st->beta_b = bb;
+  uint32_t* q = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
+  uint64_t* prefix = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)N);
+  uint64_t total = or_resample_prefix(d, W, N, eps, c->weight_mode, q, prefix);
+  st->total = total;
+  float* up = (float*)malloc(sizeof(float) * 8 * (size_t)M);
+  float* sp = (float*)malloc(sizeof(float) * (size_t)M);
+  int32_t* ap = (int32_t*)malloc(sizeof(int32_t) * (size_t)M);
+  int32_t* att = (int32_t*)malloc(sizeof(int32_t) * (size_t)M);
+  uint8_t* fl = (uint8_t*)malloc((size_t)M);
+  double* dp = (double*)malloc(sizeof(double) * (size_t)M);
+  int64_t filled = 0;
+  int32_t b;
+  for (b = 0; b < c->max_batches && filled < N; ++b) {
+    uint32_t c1 = ((uint32_t)t << 16) | (uint32_t)b;
+    or_propose(m, u, N, prefix, total, ba, bb, M, NULL, c1, c->max_redraw, up, sp, ap, att, fl,
+               c->nthreads);
+    or_simulate(m, up, M, NULL, c1, TAG_SIM, fl, dp, NULL, c->nthreads);
+    st->sims += M;
+    for (int64_t j = 0; j < M; ++j) {
+      if (fl[j]) st->exhausted += 1;
+      int acc = !fl[j] && dp[j] <= eps;
+      if (!acc) continue;
+      st->accepted_total += 1;
+      if (filled < N) {
+        for (int dd = 0; dd < 8; ++dd) u_new[(int64_t)dd * N + filled] = up[(int64_t)dd * M + j];
+        d_new[filled] = dp[j];
+        s_new[filled] = sp[j];
+        anc_new[filled] = ap[j];
+        filled += 1;
+      }
+    }
+  }
+  st->batches = b;
+  if (filled < N) {
+    st->status = 1;
+  } else if (c->weight_mode == 1) {
+    or_weights(u_new, s_new, N, u, q, N, total, logW_new, c->nthreads);
+    st->ess = or_normalize(logW_new, N, W_new);
+  } else {
+    for (int64_t j = 0; j < N; ++j) { W_new[j] = 1.0 / (double)N; logW_new[j] = 0.0; }
+    st->ess = (double)N;
+  }
+  free(q); free(prefix); free(up); free(sp); free(ap); free(att); free(fl); free(dp);
+  return st->status;
+}
