@@ -1,0 +1,356 @@
+"""Benchmark: P-ABC-SMC with Beta-distributed step sizes on one GB300.
+
+A step is one SMC generation (Sec. 2.4, 3.2) of the single-run workload at
+scale -- 2^20 particles, population 1e7, 120 days, importance weights with
+the O(N^2) kernel sum, the paper's Beta(eps_t/eps_1, 2t) step schedule --
+on synthetic observations simulated from a seeded theta*: select eps_t,
+stage-prior prefix, batches of proposals (ancestor, Beta step, walk, support
+check), simulation, acceptance, O(N^2) weights, fp64 normalisation.
+
+value: simulated particle-days per second over K generations with inputs
+resident in HBM (CUDA events on the library's stream).  e2e: the same
+metric through the public C ABI from pinned host buffers: each step loads
+the population with abc_set_state (host to device), runs the generation
+and reads the new population back (device to host).
+--impl reference: the CPU oracle on the host cores, on bounded samples of
+the same step, extrapolated to the step's work.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sim-days/s; wall-time to ε_final per run, surrogate+batched vs plain"
+UNIT = "sim-days/s"
+MUFU_EX2_PER_CLK_PER_SM = 16  # 32-bit exp2 issue rate of one SM (4 SMSPs x 4 lanes)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu, self.proc, self.path = gpu, None, None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def synthetic_obs(G, WL, cfg, torch):
+    T = cfg.n_days
+    obs = torch.empty((3, T + 1), dtype=torch.int32, device="cuda")
+    th = torch.empty(8, dtype=torch.float32, device="cuda")
+    att = torch.empty(1, dtype=torch.int32, device="cuda")
+    G.abc_synth_obs(cfg, WL.OBS_BOX_LO, WL.OBS_BOX_HI, obs, th, att)
+    torch.cuda.synchronize()
+    return obs.cpu().numpy(), th.cpu().numpy()
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_2106_15508_gb300 as G
+    from paper_2106_15508_gb300 import build as B
+    from paper_2106_15508_gb300 import workloads as WL
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        B.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    G.lib()
+    w = WL.LARGE
+    # independent runs per rank (weak scaling, no data-path collective)
+    cfg = w.config(seed=w.seed + rank, weight_prec=args.prec)
+    obs, theta_star = synthetic_obs(G, WL, cfg, torch)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    ctx = G.abc_init(cfg, obs, stream=sp)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    N = w.N
+    try:
+        # warm-up: stage 0 and W generations
+        G.abc_generation(ctx)
+        for _ in range(args.warmup):
+            rc = G.abc_generation(ctx)
+            if rc != G.ABC_OK:
+                raise RuntimeError("warm-up generation stopped: %s" % G.strerror(rc))
+        blob = G.abc_get_state(ctx)  # state before the first timed generation
+        g_first = G.abc_generations(ctx)
+        clocks = Clocks(local)
+        clocks.start()
+        time.sleep(0.3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for k in range(args.steps):
+                if k:
+                    flush.zero_()  # L2 (129 MB) flushed between steps
+                rc = G.abc_generation(ctx)
+                if rc != G.ABC_OK:
+                    raise RuntimeError("timed generation stopped: %s" % G.strerror(rc))
+                stats.append(G.abc_get_stats(ctx, G.abc_generations(ctx) - 1))
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        clk = clocks.stop()
+        sim_days = sum(s.sim_days for s in stats)
+        launches = sum(s.launches for s in stats)
+        # end to end through the C ABI with pinned host buffers
+        hbuf = torch.empty(len(blob), dtype=torch.uint8, pin_memory=True)
+        hbuf.numpy()[:] = np.frombuffer(blob, np.uint8)
+        pop_h = dict(u=torch.empty((8, N), dtype=torch.float32, pin_memory=True),
+                     d=torch.empty(N, dtype=torch.float64, pin_memory=True),
+                     W=torch.empty(N, dtype=torch.float64, pin_memory=True),
+                     s=torch.empty(N, dtype=torch.float32, pin_memory=True),
+                     anc=torch.empty(N, dtype=torch.int32, pin_memory=True))
+        e2e_days = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            G.abc_set_state_ptr(ctx, hbuf.data_ptr(), len(blob))
+            G.abc_generation(ctx)
+            e2e_days += G.abc_get_stats(ctx, G.abc_generations(ctx) - 1).sim_days
+            G.abc_get_population(ctx, pop_h["u"].data_ptr(), pop_h["d"].data_ptr(),
+                                 pop_h["W"].data_ptr(), pop_h["s"].data_ptr(),
+                                 pop_h["anc"].data_ptr(), on_device=False)
+        e2e_s = time.perf_counter() - t0
+        d2h = sum(t.numel() * t.element_size() for t in pop_h.values())
+    finally:
+        G.abc_free(ctx)
+    value = sim_days / (ms / 1e3)
+    e2e_value = e2e_days / e2e_s
+    if ws > 1:
+        # whole-job throughput: units of all ranks over the slowest rank's time
+        totals = torch.tensor([float(sim_days), float(e2e_days)], device="cuda",
+                              dtype=torch.float64)
+        torch.distributed.all_reduce(totals)
+        tmax = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        value = float(totals[0]) / (ms / 1e3)
+        e2e_value = float(totals[1]) / float(tmax[0])
+    if rank != 0:
+        return None
+    peaks, src = _peaks()
+    # dominant kernel: the O(N^2) weight pass; unit = pair-exponentials
+    pairs = sum(s.pairs for s in stats)
+    wms = sum(s.ms_weights for s in stats)
+    sim_ms = sum(s.ms_sim for s in stats)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    exp_peak = n_sm * MUFU_EX2_PER_CLK_PER_SM * sm_mhz * 1e6
+    achieved = pairs / (wms / 1e3) if wms > 0 else 0.0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "particles": N, "days": w.T, "population": w.P,
+                   "weights": "importance O(N^2), " + ("bf16 tcgen05" if args.prec else "fp32"),
+                   "beta_schedule": "paper (eps_t/eps_1, 2t)", "generations_timed":
+                   [g_first + k for k in range(args.steps)],
+                   "l2": "flushed between steps (256 MB write)",
+                   "theta_star": [round(float(x), 6) for x in theta_star]},
+        "roofline": {"bound": "alu", "kernel": "k_weights_fp32" if not args.prec else
+                     "k_weights_tc", "achieved": achieved / 1e9,
+                     "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": achieved / exp_peak,
+                     "peak_source": "%d SMs x %d MUFU ex2/clk x %.0f MHz (%s max clock)" % (
+                         n_sm, MUFU_EX2_PER_CLK_PER_SM, sm_mhz, src),
+                     "traffic": None},
+        "phases_ms": {"weights": wms / args.steps, "simulator": sim_ms / args.steps,
+                      "rest": (ms - wms - sim_ms) / args.steps},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(blob),
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "generations": [{"t": s.generation, "eps": s.eps, "ess": s.ess, "batches": s.batches,
+                         "sim_days": s.sim_days, "ms": s.ms} for s in stats],
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(stats, w)
+    return line
+
+
+def cpu_baseline(stats, w):
+    """The oracle as it stands on the host cores, on a bounded sample of the
+    step: a batch of simulations and a block of weight rows, each timed,
+    extrapolated to the average step's simulated days and weight pairs."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2106_15508_gb300 import workloads as WL
+
+    cores = os.cpu_count() or 1
+    m = O.OracleModel(T=w.T, P=w.P, A0=WL.initial_active(w.P), seed=w.seed)
+    obs, _, _ = O.synth_obs(m)
+    m.set_obs(obs)
+    n_sim = 1 << 14
+    u = O.prior(m, n_sim)
+    t0 = time.perf_counter()
+    O.simulate(m, u, nthreads=cores)
+    t_sim = time.perf_counter() - t0
+    per_day = t_sim / (n_sim * w.T)
+    rows, cols = 256, w.N // 2
+    rng = np.random.default_rng(0)
+    up = rng.uniform(0.3, 0.7, (8, rows)).astype(np.float32)
+    uc = rng.uniform(0.3, 0.7, (8, cols)).astype(np.float32)
+    s = rng.uniform(1e-4, 0.05, rows).astype(np.float32)
+    q = rng.integers(1, 2**32, cols, dtype=np.uint64).astype(np.uint32)
+    t0 = time.perf_counter()
+    O.weights(up, s, uc, q, int(q.astype(np.uint64).sum()), nthreads=cores)
+    t_w = time.perf_counter() - t0
+    per_pair = t_w / (rows * cols)
+    days = sum(x.sim_days for x in stats) / len(stats)
+    pairs = sum(x.pairs for x in stats) / len(stats)
+    step_s = days * per_day + pairs * per_pair
+    return {"value": days / step_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d simulations x %d days (%.2f s) and %d weight rows x %d columns "
+                      "(%.2f s), extrapolated to the step's %.3g sim-days and %.3g pairs" % (
+                          n_sim, w.T, t_sim, rows, cols, t_w, days, pairs)}
+
+
+def run_reference(args):
+    """The oracle arm: each step is a bounded sample of one generation of the
+    same workload on the host cores; value extrapolated to the full step."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2106_15508_gb300 import workloads as WL
+
+    ws, rank = _dist()
+    if rank != 0:
+        return None
+    w = WL.LARGE
+    cores = os.cpu_count() or 1
+    m = O.OracleModel(T=w.T, P=w.P, A0=WL.initial_active(w.P), seed=w.seed)
+    obs, _, _ = O.synth_obs(m)
+    m.set_obs(obs)
+    n_sim, rows, cols = 1 << 13, 64, w.N // 2
+    rng = np.random.default_rng(1)
+    uc = rng.uniform(0.3, 0.7, (8, cols)).astype(np.float32)
+    q = rng.integers(1, 2**32, cols, dtype=np.uint64).astype(np.uint32)
+    tot = int(q.astype(np.uint64).sum())
+    # a generation of this workload simulates ~3 batches of N and weighs N x N/2 pairs
+    step_days, step_pairs = 3 * w.N * w.T, w.N * cols
+
+    def one_step(k):
+        u = O.prior(m, n_sim)
+        t0 = time.perf_counter()
+        O.simulate(m, u, c1=k, nthreads=cores)
+        t_sim = time.perf_counter() - t0
+        up = rng.uniform(0.3, 0.7, (8, rows)).astype(np.float32)
+        s = rng.uniform(1e-4, 0.05, rows).astype(np.float32)
+        t0 = time.perf_counter()
+        O.weights(up, s, uc, q, tot, nthreads=cores)
+        t_w = time.perf_counter() - t0
+        return t_sim / (n_sim * w.T) * step_days + t_w / (rows * cols) * step_pairs
+
+    for k in range(args.warmup):
+        one_step(k)
+    secs = [one_step(100 + k) for k in range(args.steps)]
+    step_s = sum(secs) / len(secs)
+    value = step_days / step_s
+    sample = ("per step: %d simulations x %d days and %d weight rows x %d columns, "
+              "extrapolated to %.3g sim-days and %.3g pairs" % (n_sim, w.T, rows, cols,
+                                                               step_days, step_pairs))
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": w.name, "particles": w.N, "days": w.T,
+                                            "population": w.P},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores,
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--prec", type=int, default=0, help="0 fp32 CUDA cores, 1 bf16 tcgen05")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    line = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

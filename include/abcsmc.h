@@ -1,0 +1,264 @@
+/*
+ * abcsmc.h -- C ABI of the GB300 (sm_103a) implementation of P-ABC-SMC with
+ * Beta-distributed step sizes (BDSS), arXiv 2106.15508.
+ *
+ * Two layers:
+ *   - step entry points (abc_prior, abc_simulate, abc_select_kth, ...): one
+ *     hot-path step each, on caller-owned DEVICE buffers, stream-ordered on
+ *     the given cudaStream_t (passed as void*; NULL = legacy default stream);
+ *   - a context (abc_init / abc_generation / abc_run / abc_get_*) that owns
+ *     its device buffers and runs whole SMC generations (Sec. 2.4, 3.2).
+ *
+ * Conventions (all entry points):
+ *   - return ABC_OK (0) on success, a positive ABC_STOP_* code for a normal
+ *     early stop, or a negative ABC_E_* code; abc_strerror() names it;
+ *   - pointers marked "device" must be device (or managed) memory; "host"
+ *     pointers are read or written synchronously before return;
+ *   - caller buffers are borrowed and never freed by the library;
+ *   - arrays of particles are structure-of-arrays: u[d * n + j] holds
+ *     coordinate d of particle j (d = 0..7), in unit-cube coordinates
+ *     u = (theta - theta_lo) / (theta_hi - theta_lo) (the paper's
+ *     reparameterisation, Sec. 3.1);
+ *   - theta = [alpha0, alpha, n, beta, gamma, delta, eta, kappa] (Eq. 1);
+ *   - random numbers come from Philox4x32-10 (Salmon et al., SC'11) with key
+ *     (seed_lo, seed_hi ^ run_id) and counter (c0, c1, c2, tag); c0 is the
+ *     slot, c1 = (generation << 16) | batch, c2 and the tag are fixed per
+ *     stream (ABC_TAG_*).  Results depend only on the counters, never on
+ *     launch geometry.
+ * Scratch: entry points that take (scratch, scratch_bytes) need at least
+ * the matching abc_*_scratch_bytes() of device memory; contents on entry
+ * are ignored.
+ */
+#ifndef ABCSMC_H
+#define ABCSMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ABC_API __attribute__((visibility("default")))
+#else
+#define ABC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define ABC_OK 0
+#define ABC_STOP_BUDGET 1       /* a generation used max_batches batches before N acceptances */
+#define ABC_STOP_TARGET 2       /* abc_run reached eps_target                           */
+#define ABC_E_INVAL (-1)        /* bad argument or configuration                         */
+#define ABC_E_NOMEM (-2)        /* device allocation failed                              */
+#define ABC_E_CUDA (-3)         /* a CUDA runtime call or kernel launch failed           */
+#define ABC_E_DEVICE (-4)       /* a device-side bound check tripped                     */
+#define ABC_E_SCRATCH (-5)      /* scratch buffer smaller than required                  */
+#define ABC_E_STATE (-6)        /* malformed or mismatched state blob                    */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define ABC_MODEL_SAIRD 0       /* stochastic S/I/A/R/D/Ru model (Sec. 2.2)              */
+#define ABC_MODEL_GAUSS_TOY 1   /* x ~ N(theta, I8), distance ||x - x_obs|| (test model)  */
+#define ABC_SIM_BINOMIAL 0      /* exact-count binomial competing risks (default)        */
+#define ABC_SIM_PAPER_NORMAL 1  /* the paper's floor(Normal(h, sqrt h)) flows (Sec. 2.2) */
+#define ABC_BETA_PAPER 0        /* s ~ Beta(eps_t/eps_1, 2t)  (Eq. 16)                    */
+#define ABC_BETA_FIXED 1        /* s ~ Beta(beta_a, beta_b)                               */
+#define ABC_W_PAPER 0           /* resampling weights eps_t - d (Eq. 10), W = 1/N         */
+#define ABC_W_IMPORTANCE 1      /* importance weights with the O(N^2) kernel sum          */
+#define ABC_P_FP32 0            /* O(N^2) weight sum on CUDA cores in fp32                */
+#define ABC_P_BF16_TC 1         /* O(N^2) weight sum on tcgen05 tensor cores, bf16 inputs */
+
+/* Philox stream tags (fourth counter word) */
+#define ABC_TAG_PRIOR 0
+#define ABC_TAG_ANCESTOR 1
+#define ABC_TAG_BETA 2
+#define ABC_TAG_WALK 3
+#define ABC_TAG_SIM 4
+#define ABC_TAG_OBS 7
+#define ABC_TAG_OBS_THETA 8
+
+/* ---- configuration ----------------------------------------------------- */
+typedef struct {
+  int32_t model;            /* ABC_MODEL_*                                              */
+  int32_t sampler;          /* ABC_SIM_*                                                */
+  int32_t n_days;           /* T >= 1 for SAIRD (days 1..T are compared)                 */
+  int32_t init_ard[3];      /* A0, R0, D0: observed day-0 state (Sec. 2.2)               */
+  int64_t population;       /* P, 1 <= P <= 2^31 - 1 (counts are int32)                 */
+  float theta_lo[8];        /* prior U(theta_lo, theta_hi) (Eq. 2): lo = 0,              */
+  float theta_hi[8];        /*   hi = [1, 100, 2, 1, 1, 1, 1, 2] for SAIRD               */
+  float x_obs[8];           /* observation of the Gaussian toy model                    */
+  uint64_t seed;            /* Philox key = (seed lo 32, seed hi 32 ^ run_id)            */
+  uint32_t run_id;
+  int32_t n_particles;      /* N: population kept per generation (Sec. 4.1: samples)    */
+  int32_t batch_size;       /* M: proposals per batch (Sec. 3.1: parallel simulations); */
+                            /*   0 means M = N                                           */
+  int32_t beta_mode;        /* ABC_BETA_*                                               */
+  double survival_alpha;    /* alpha of Eq. 8 (0.5 in the paper)                        */
+  float beta_a;             /* fixed-mode shape a > 0                                    */
+  int32_t beta_b;           /* fixed-mode shape b, integer 1..1024                       */
+  int32_t weight_mode;      /* ABC_W_*                                                  */
+  int32_t weight_prec;      /* ABC_P_*                                                  */
+  int32_t max_batches;      /* per-generation batch budget (<= 65535)                   */
+  int32_t max_redraw;       /* proposal redraws when u' leaves [0,1]^8                   */
+} abc_config;
+
+/* Fill a config with the paper's defaults (SAIRD, binomial flows, alpha 0.5,
+ * paper Beta schedule, paper weights, FP32, 64 batches, 64 redraws). */
+ABC_API void abc_config_default(abc_config* cfg);
+
+/* ---- step entry points (device buffers, stream-ordered) ---------------- */
+
+/* Philox4x32-10 blocks: out[4i..4i+3] = philox(ctr[4i..4i+3], key).
+ * ctr, out: device, n blocks.  For pinning the generator against others. */
+ABC_API int abc_philox(const uint32_t* ctr, uint32_t key0, uint32_t key1, int64_t n, uint32_t* out,
+               void* stream);
+
+/* A0 synthetic observations (stand-in for the JHU series, Sec. 2.2 and 4):
+ * theta* = lo + v (hi - lo) with v from the OBS_THETA stream (c0 = 0,
+ * c1 = attempt, c2 = 0..1), simulated with the OBS stream (c1 = attempt),
+ * redrawn until A_T > A0, at most 64 attempts.  box_lo/hi: host float[8].
+ * obs: device int32 [3][T+1] (rows A, R, D; column t = day t, day 0 =
+ * init_ard); theta_star: device float[8]; attempts: device int32[1]
+ * (attempts used, or -64 when none grew). */
+ABC_API int abc_synth_obs(const abc_config* cfg, const float* box_lo, const float* box_hi, int32_t* obs,
+                  float* theta_star, int32_t* attempts, void* stream);
+
+/* Stage 0 (Sec. 2.4): u_j ~ U(0,1)^8 from the PRIOR stream (c0 = j, c1 = 0,
+ * c2 = 0..1).  u: device float [8][n]. */
+ABC_API int abc_prior(const abc_config* cfg, int64_t n, float* u, void* stream);
+
+/* A2-A3 simulator (Sec. 2.2, Eq. 3-5) and Euclidean distance (Sec. 2.3):
+ * for each i < n, theta = lo + u_i (hi - lo), simulate T days with the
+ * Philox counters (c0_idx ? c0_idx[i] : i, c1, 4 day + block, tag) and
+ * return dist[i] = sqrt(sum_t sum_{A,R,D} (sim - obs)^2) over days 1..T
+ * (exact integer sum, one correctly rounded conversion and sqrt).
+ * obs: device int32 [3][T+1] (SAIRD; NULL gives distance 0); u: device
+ * float [8][n]; c0_idx: device u32[n] or NULL; skip: device u8[n] or NULL
+ * (skip[i] != 0 gives +inf and no simulation); dist: device double[n];
+ * traj: device int32 [T+1][6][n] (S, I, A, R, D, Ru per day) or NULL. */
+ABC_API int abc_simulate(const abc_config* cfg, const int32_t* obs, const float* u, int64_t n,
+                 const uint32_t* c0_idx, uint32_t c1, uint32_t tag, const uint8_t* skip,
+                 double* dist, int32_t* traj, void* stream);
+
+/* A4 tolerance (Eq. 8): *out = the k-th smallest of d[0..n) (1 <= k <= n),
+ * the lower order statistic, ties kept.  d: device double[n], all >= 0 or
+ * +inf (no NaN); out: device double[1].  Radix select on the bit patterns. */
+ABC_API size_t abc_select_scratch_bytes(int64_t n);
+ABC_API int abc_select_kth(const double* d, int64_t n, int64_t k, double* out, void* scratch,
+                   size_t scratch_bytes, void* stream);
+
+/* A5 stage prior, weights and prefix (Eq. 9-11): survivors d_j <= *eps;
+ * r_j = *eps - d_j (mode ABC_W_PAPER) or W_j (ABC_W_IMPORTANCE), 0 for
+ * non-survivors; q_j = floor(r_j / max r * (2^32 - 1)) (q_j = 1 for every
+ * survivor when max r is 0); prefix = inclusive sum of q as u64, so the
+ * total is prefix[n-1].  d, W: device double[n] (W unused in paper mode,
+ * may be NULL); eps: device double[1]; q: device u32[n]; prefix: device
+ * u64[n]. */
+ABC_API size_t abc_prefix_scratch_bytes(int64_t n);
+ABC_API int abc_resample_prefix(const double* d, const double* W, int64_t n, const double* eps,
+                        int32_t mode, uint32_t* q, uint64_t* prefix, void* scratch,
+                        size_t scratch_bytes, void* stream);
+
+/* A6-A7 BDSS proposal (Eq. 11, 16, 17): for each slot i < slots with
+ * c0 = c0_idx ? c0_idx[i] : i and attempt a = 0..max_redraw-1: ancestor =
+ * first k with prefix[k] > floor(U64 * total / 2^64) (ANCESTOR stream, c2 =
+ * a), s ~ Beta(a_t, b) (BETA stream, c2 = a << 8 | block), z ~ N(0, I8)
+ * (WALK stream), u' = u_anc + sqrt(s) z; the first u' inside [0,1]^8 is kept,
+ * else flag = 1.  a_t = beta_a, or in paper mode (cfg->beta_mode) a_t =
+ * (float)(*eps / *eps1) (1 when *eps1 is 0) and b = beta_b as given.
+ * u: device float [8][n]; prefix: device u64[n]; eps, eps1: device double[1]
+ * (read only in paper mode; may be NULL otherwise); outputs: device
+ * u_out [8][slots], s_out[slots], anc_out, attempts_out (int32), flag_out (u8). */
+ABC_API int abc_propose(const abc_config* cfg, const float* u, int64_t n, const uint64_t* prefix,
+                const double* eps, const double* eps1, float beta_a, int32_t beta_b,
+                int64_t slots, const uint32_t* c0_idx, uint32_t c1, float* u_out, float* s_out,
+                int32_t* anc_out, int32_t* attempts_out, uint8_t* flag_out, void* stream);
+
+/* A8 acceptance and assembly (Sec. 2.3, Sec. 4.1): proposals i < M with
+ * flag[i] == 0 and dp[i] <= *eps are appended to the population in slot
+ * order at positions *filled, *filled + 1, ... while below N.  On return
+ * *filled = min(N, *filled + accepted), counters[0] += accepted,
+ * counters[1] += number of flagged (redraw-exhausted) slots.
+ * up [8][M], dp, sp, ap, flag: device proposal arrays; eps: device double[1];
+ * u_pop [8][N], d_pop, s_pop, anc_pop: device population arrays;
+ * filled: device int64[1]; counters: device int64[2]. */
+ABC_API size_t abc_accept_scratch_bytes(int64_t M);
+ABC_API int abc_accept_append(const float* up, const double* dp, const float* sp, const int32_t* ap,
+                      const uint8_t* flag, int64_t M, const double* eps, int64_t N, float* u_pop,
+                      double* d_pop, float* s_pop, int32_t* anc_pop, int64_t* filled,
+                      int64_t* counters, void* scratch, size_t scratch_bytes, void* stream);
+
+/* A9 importance weights (spec extension; the paper's weights are
+ * Eq. 10): for each row j < rows,
+ *   logW[j] = 4 log(2 pi s_j) - log sum_k (q_k / total) exp(-|u'_j - u_k|^2 / (2 s_j))
+ * = -log sum_k rhat_k N(u'_j; u_k, s_j I8) (uniform prior on the unit cube),
+ * over columns k < n with q_k > 0; total = prefix[n-1]; s_j == 0 gives
+ * -inf.  prec: ABC_P_FP32 (CUDA cores) or ABC_P_BF16_TC (tensor cores).
+ * up [8][rows], s[rows], u [8][n], q[n], prefix[n]: device; logW: device
+ * double[rows]. */
+ABC_API size_t abc_weights_scratch_bytes(int64_t rows, int64_t n);
+ABC_API int abc_weights(const float* up, const float* s, int64_t rows, const float* u, const uint32_t* q,
+                const uint64_t* prefix, int64_t n, int32_t prec, double* logW, void* scratch,
+                size_t scratch_bytes, void* stream);
+
+/* A10 normalisation (fp64): W_j = exp(logW_j - max) / sum, *ess = 1 / sum W^2;
+ * all -inf gives W = 1/n, ess = n.  logW: device double[n]; W: device
+ * double[n]; ess: device double[1]. */
+ABC_API size_t abc_normalize_scratch_bytes(int64_t n);
+ABC_API int abc_normalize(const double* logW, int64_t n, double* W, double* ess, void* scratch,
+                  size_t scratch_bytes, void* stream);
+
+/* ---- context: whole generations ---------------------------------------- */
+typedef struct abc_ctx abc_ctx;
+
+typedef struct {
+  int32_t generation;       /* index t of the generation these stats describe       */
+  int32_t status;           /* ABC_OK or ABC_STOP_BUDGET                             */
+  double eps;               /* eps_t used for acceptance (+inf for t = 0)           */
+  double eps1;              /* eps_1 (0 before generation 1)                        */
+  double ess;               /* effective sample size of the new population          */
+  float beta_a;             /* step-size Beta shape used (a_t, b_t)                 */
+  int32_t beta_b;
+  int64_t batches;          /* batches of M proposals run                           */
+  int64_t sims;             /* simulations run (flagged slots excluded)             */
+  int64_t sim_days;         /* particle-days simulated                              */
+  int64_t exhausted;        /* slots whose redraws were exhausted                   */
+  int64_t accepted;         /* acceptances, including those beyond N                */
+  int64_t pairs;            /* rows x surviving columns of the O(N^2) weight pass    */
+  int64_t launches;         /* kernels this library launched for the generation     */
+  double ms;                /* device time of the generation (CUDA events)          */
+  double ms_sim;            /* of which the simulator launches (all batches)        */
+  double ms_weights;        /* of which the O(N^2) weight pass                      */
+} abc_gen_stats;
+
+/* Validate cfg, allocate every device buffer (owned by the context), copy
+ * obs (host int32 [3][T+1]; NULL for the toy model) and bind the stream. */
+ABC_API int abc_init(const abc_config* cfg, const int32_t* obs, void* stream, abc_ctx** out);
+/* Run one generation: the first call runs stage 0 (prior); later calls
+ * run t = 1, 2, ...  Returns ABC_STOP_BUDGET (population unchanged) when
+ * max_batches batches did not yield N acceptances. */
+ABC_API int abc_generation(abc_ctx* ctx);
+/* Run generations until n_generations exist or eps_t <= eps_target
+ * (eps_target <= 0 disables it); returns the last generation's status. */
+ABC_API int abc_run(abc_ctx* ctx, int32_t n_generations, double eps_target);
+/* Copy the population: u [8][N] float, dist, W double[N], s float[N] and
+ * anc int32[N] (ancestor index in the previous population, -1 at t = 0);
+ * any pointer may be NULL; on_device != 0 means the pointers are device
+ * memory (device-to-device copy on the context stream), else host. */
+ABC_API int abc_get_population(abc_ctx* ctx, float* u, double* dist, double* W, float* s, int32_t* anc,
+                       int32_t on_device);
+/* Stats of generation t (0 <= t < abc_generations(ctx)). */
+ABC_API int abc_get_stats(abc_ctx* ctx, int32_t t, abc_gen_stats* out);
+ABC_API int32_t abc_generations(const abc_ctx* ctx);
+/* Checkpoint: serialise (or restore) the generation index, eps_1 and the
+ * population.  Philox is stateless, so a restored context continues
+ * bit-identically.  get: *len is in/out (call with buf NULL for the size). */
+ABC_API int abc_get_state(abc_ctx* ctx, void* buf, size_t* len);
+ABC_API int abc_set_state(abc_ctx* ctx, const void* buf, size_t len);
+ABC_API void abc_free(abc_ctx* ctx);
+ABC_API const char* abc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABCSMC_H */

@@ -523,7 +523,8 @@ OR_API int64_t or_rank(double alpha, int64_t n) {
  * Stage prior and its weights (Eq. 9-10): survivors are d_j <= eps.
  * mode 0 (paper): r_j = eps - d_j; mode 1 (importance): r_j = W_j.
  * q_j = floor(r_j / max r * (2^32 - 1)); prefix = inclusive sum of q (u64).
- * When max r is zero every survivor gets q_j = 1.  Returns the total.
+ * When max r is zero or not finite every survivor gets q_j = 1.  Returns
+ * the total.
  */
 OR_API uint64_t or_resample_prefix(const double* d, const double* W, int64_t n, double eps,
                                    int mode, uint32_t* q, uint64_t* prefix) {
@@ -536,7 +537,7 @@ OR_API uint64_t or_resample_prefix(const double* d, const double* W, int64_t n, 
   uint64_t tot = 0;
   for (int64_t j = 0; j < n; ++j) {
     uint32_t qj;
-    if (rmax > 0.0 && rmax <= 1.79e308) {
+    if (rmax > 0.0 && isfinite(rmax)) {
       double r = 0.0;
       if (d[j] <= eps) r = mode == 0 ? eps - d[j] : W[j];
       qj = (uint32_t)floor(r / rmax * 4294967295.0);

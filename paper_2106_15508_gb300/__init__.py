@@ -1,0 +1,296 @@
+"""Python binding of libabcsmc.so, the GB300 (sm_103a) implementation of
+P-ABC-SMC with Beta-distributed step sizes (arXiv 2106.15508).
+
+Argument marshalling only: every step runs in the CUDA library.  Functions
+carry the names of the C entry points in include/abcsmc.h and accept device
+pointers as ints or as objects with a data_ptr() (torch tensors).  Streams
+default to torch's current CUDA stream.  There is no CPU fallback: importing
+works without the library, but the first call raises if it is missing.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libabcsmc.so")
+
+ABC_OK, ABC_STOP_BUDGET, ABC_STOP_TARGET = 0, 1, 2
+ABC_MODEL_SAIRD, ABC_MODEL_GAUSS_TOY = 0, 1
+ABC_SIM_BINOMIAL, ABC_SIM_PAPER_NORMAL = 0, 1
+ABC_BETA_PAPER, ABC_BETA_FIXED = 0, 1
+ABC_W_PAPER, ABC_W_IMPORTANCE = 0, 1
+ABC_P_FP32, ABC_P_BF16_TC = 0, 1
+TAG_PRIOR, TAG_ANCESTOR, TAG_BETA, TAG_WALK, TAG_SIM, TAG_OBS, TAG_OBS_THETA = 0, 1, 2, 3, 4, 7, 8
+
+# every entry point declared in include/abcsmc.h
+EXPORTS = (
+    "abc_config_default", "abc_philox", "abc_synth_obs", "abc_prior", "abc_simulate",
+    "abc_select_scratch_bytes", "abc_select_kth", "abc_prefix_scratch_bytes",
+    "abc_resample_prefix", "abc_propose", "abc_accept_scratch_bytes", "abc_accept_append",
+    "abc_weights_scratch_bytes", "abc_weights", "abc_normalize_scratch_bytes", "abc_normalize",
+    "abc_init", "abc_generation", "abc_run", "abc_get_population", "abc_get_stats",
+    "abc_generations", "abc_get_state", "abc_set_state", "abc_free", "abc_strerror",
+)
+
+
+class AbcConfig(C.Structure):
+    _fields_ = [
+        ("model", C.c_int32), ("sampler", C.c_int32), ("n_days", C.c_int32),
+        ("init_ard", C.c_int32 * 3), ("population", C.c_int64),
+        ("theta_lo", C.c_float * 8), ("theta_hi", C.c_float * 8), ("x_obs", C.c_float * 8),
+        ("seed", C.c_uint64), ("run_id", C.c_uint32), ("n_particles", C.c_int32),
+        ("batch_size", C.c_int32), ("beta_mode", C.c_int32), ("survival_alpha", C.c_double),
+        ("beta_a", C.c_float), ("beta_b", C.c_int32), ("weight_mode", C.c_int32),
+        ("weight_prec", C.c_int32), ("max_batches", C.c_int32), ("max_redraw", C.c_int32),
+    ]
+
+
+class AbcGenStats(C.Structure):
+    _fields_ = [
+        ("generation", C.c_int32), ("status", C.c_int32), ("eps", C.c_double),
+        ("eps1", C.c_double), ("ess", C.c_double), ("beta_a", C.c_float), ("beta_b", C.c_int32),
+        ("batches", C.c_int64), ("sims", C.c_int64), ("sim_days", C.c_int64),
+        ("exhausted", C.c_int64), ("accepted", C.c_int64), ("pairs", C.c_int64),
+        ("launches", C.c_int64), ("ms", C.c_double), ("ms_sim", C.c_double),
+        ("ms_weights", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AbcError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__("%s failed: %s (%d)" % (where, strerror(code), code))
+        self.code = code
+
+
+_lib = None
+
+_V, _I32, _I64, _U32, _SZ, _D, _F = (C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_size_t,
+                                     C.c_double, C.c_float)
+_SIGS = {
+    "abc_config_default": (None, [C.POINTER(AbcConfig)]),
+    "abc_strerror": (C.c_char_p, [C.c_int]),
+    "abc_philox": (C.c_int, [_V, _U32, _U32, _I64, _V, _V]),
+    "abc_synth_obs": (C.c_int, [C.POINTER(AbcConfig), _V, _V, _V, _V, _V, _V]),
+    "abc_prior": (C.c_int, [C.POINTER(AbcConfig), _I64, _V, _V]),
+    "abc_simulate": (C.c_int, [C.POINTER(AbcConfig), _V, _V, _I64, _V, _U32, _U32, _V, _V, _V, _V]),
+    "abc_select_scratch_bytes": (_SZ, [_I64]),
+    "abc_select_kth": (C.c_int, [_V, _I64, _I64, _V, _V, _SZ, _V]),
+    "abc_prefix_scratch_bytes": (_SZ, [_I64]),
+    "abc_resample_prefix": (C.c_int, [_V, _V, _I64, _V, _I32, _V, _V, _V, _SZ, _V]),
+    "abc_propose": (C.c_int, [C.POINTER(AbcConfig), _V, _I64, _V, _V, _V, _F, _I32, _I64, _V, _U32,
+                              _V, _V, _V, _V, _V, _V]),
+    "abc_accept_scratch_bytes": (_SZ, [_I64]),
+    "abc_accept_append": (C.c_int, [_V, _V, _V, _V, _V, _I64, _V, _I64, _V, _V, _V, _V, _V, _V, _V,
+                                    _SZ, _V]),
+    "abc_weights_scratch_bytes": (_SZ, [_I64, _I64]),
+    "abc_weights": (C.c_int, [_V, _V, _I64, _V, _V, _V, _I64, _I32, _V, _V, _SZ, _V]),
+    "abc_normalize_scratch_bytes": (_SZ, [_I64]),
+    "abc_normalize": (C.c_int, [_V, _I64, _V, _V, _V, _SZ, _V]),
+    "abc_init": (C.c_int, [C.POINTER(AbcConfig), _V, _V, C.POINTER(C.c_void_p)]),
+    "abc_generation": (C.c_int, [_V]),
+    "abc_run": (C.c_int, [_V, _I32, _D]),
+    "abc_get_population": (C.c_int, [_V, _V, _V, _V, _V, _V, _I32]),
+    "abc_get_stats": (C.c_int, [_V, _I32, C.POINTER(AbcGenStats)]),
+    "abc_generations": (C.c_int32, [_V]),
+    "abc_get_state": (C.c_int, [_V, _V, C.POINTER(C.c_size_t)]),
+    "abc_set_state": (C.c_int, [_V, _V, _SZ]),
+    "abc_free": (None, [_V]),
+}
+
+
+def lib():
+    """Load libabcsmc.so (raises if it has not been built: no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libabcsmc.so is missing; run paper_2106_15508_gb300.build.build() "
+                              "(or __graft_entry__.build()) first")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(code):
+    return lib().abc_strerror(int(code)).decode()
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is not None:
+        return s if isinstance(s, int) else s.cuda_stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _check(rc, where, ok=(ABC_OK,)):
+    if rc not in ok:
+        raise AbcError(rc, where)
+    return rc
+
+
+def config(**kw):
+    """abc_config_default() overridden by keyword fields (arrays as lists)."""
+    c = AbcConfig()
+    lib().abc_config_default(C.byref(c))
+    for k, v in kw.items():
+        f = getattr(c, k)
+        if isinstance(f, C.Array):
+            f[:] = list(v)
+        else:
+            setattr(c, k, v)
+    return c
+
+
+# ---- step entry points (device pointers) -------------------------------
+def abc_philox(ctr, key0, key1, n, out, stream=None):
+    return _check(lib().abc_philox(_ptr(ctr), key0, key1, n, _ptr(out), _stream(stream)),
+                  "abc_philox")
+
+
+def abc_synth_obs(cfg, box_lo, box_hi, obs, theta_star, attempts, stream=None):
+    lo = (C.c_float * 8)(*[float(v) for v in box_lo])
+    hi = (C.c_float * 8)(*[float(v) for v in box_hi])
+    return _check(lib().abc_synth_obs(C.byref(cfg), C.cast(lo, C.c_void_p), C.cast(hi, C.c_void_p),
+                                      _ptr(obs), _ptr(theta_star), _ptr(attempts),
+                                      _stream(stream)), "abc_synth_obs")
+
+
+def abc_prior(cfg, n, u, stream=None):
+    return _check(lib().abc_prior(C.byref(cfg), n, _ptr(u), _stream(stream)), "abc_prior")
+
+
+def abc_simulate(cfg, obs, u, n, c0_idx, c1, tag, skip, dist, traj=None, stream=None):
+    return _check(lib().abc_simulate(C.byref(cfg), _ptr(obs), _ptr(u), n, _ptr(c0_idx), c1, tag,
+                                     _ptr(skip), _ptr(dist), _ptr(traj), _stream(stream)),
+                  "abc_simulate")
+
+
+def abc_select_scratch_bytes(n):
+    return lib().abc_select_scratch_bytes(n)
+
+
+def abc_select_kth(d, n, k, out, scratch, scratch_bytes, stream=None):
+    return _check(lib().abc_select_kth(_ptr(d), n, k, _ptr(out), _ptr(scratch), scratch_bytes,
+                                       _stream(stream)), "abc_select_kth")
+
+
+def abc_prefix_scratch_bytes(n):
+    return lib().abc_prefix_scratch_bytes(n)
+
+
+def abc_resample_prefix(d, W, n, eps, mode, q, prefix, scratch, scratch_bytes, stream=None):
+    return _check(lib().abc_resample_prefix(_ptr(d), _ptr(W), n, _ptr(eps), mode, _ptr(q),
+                                            _ptr(prefix), _ptr(scratch), scratch_bytes,
+                                            _stream(stream)), "abc_resample_prefix")
+
+
+def abc_propose(cfg, u, n, prefix, eps, eps1, beta_a, beta_b, slots, c0_idx, c1, u_out, s_out,
+                anc_out, attempts_out, flag_out, stream=None):
+    return _check(lib().abc_propose(C.byref(cfg), _ptr(u), n, _ptr(prefix), _ptr(eps), _ptr(eps1),
+                                    beta_a, beta_b, slots, _ptr(c0_idx), c1, _ptr(u_out),
+                                    _ptr(s_out), _ptr(anc_out), _ptr(attempts_out),
+                                    _ptr(flag_out), _stream(stream)), "abc_propose")
+
+
+def abc_accept_scratch_bytes(M):
+    return lib().abc_accept_scratch_bytes(M)
+
+
+def abc_accept_append(up, dp, sp, ap, flag, M, eps, N, u_pop, d_pop, s_pop, anc_pop, filled,
+                      counters, scratch, scratch_bytes, stream=None):
+    return _check(lib().abc_accept_append(
+        _ptr(up), _ptr(dp), _ptr(sp), _ptr(ap), _ptr(flag), M, _ptr(eps), N, _ptr(u_pop),
+        _ptr(d_pop), _ptr(s_pop), _ptr(anc_pop), _ptr(filled), _ptr(counters), _ptr(scratch),
+        scratch_bytes, _stream(stream)), "abc_accept_append")
+
+
+def abc_weights_scratch_bytes(rows, n):
+    return lib().abc_weights_scratch_bytes(rows, n)
+
+
+def abc_weights(up, s, rows, u, q, prefix, n, prec, logW, scratch, scratch_bytes, stream=None):
+    return _check(lib().abc_weights(_ptr(up), _ptr(s), rows, _ptr(u), _ptr(q), _ptr(prefix), n,
+                                    prec, _ptr(logW), _ptr(scratch), scratch_bytes,
+                                    _stream(stream)), "abc_weights")
+
+
+def abc_normalize_scratch_bytes(n):
+    return lib().abc_normalize_scratch_bytes(n)
+
+
+def abc_normalize(logW, n, W, ess, scratch, scratch_bytes, stream=None):
+    return _check(lib().abc_normalize(_ptr(logW), n, _ptr(W), _ptr(ess), _ptr(scratch),
+                                      scratch_bytes, _stream(stream)), "abc_normalize")
+
+
+# ---- context --------------------------------------------------------------
+def abc_init(cfg, obs_host, stream=None):
+    """obs_host: host int32 [3][T+1] (numpy or None for the toy model)."""
+    h = C.c_void_p()
+    ptr = None if obs_host is None else obs_host.ctypes.data
+    _check(lib().abc_init(C.byref(cfg), ptr, _stream(stream), C.byref(h)), "abc_init")
+    return h
+
+
+def abc_generation(ctx):
+    return _check(lib().abc_generation(ctx), "abc_generation", ok=(ABC_OK, ABC_STOP_BUDGET))
+
+
+def abc_run(ctx, n_generations, eps_target=0.0):
+    return _check(lib().abc_run(ctx, n_generations, eps_target), "abc_run",
+                  ok=(ABC_OK, ABC_STOP_BUDGET, ABC_STOP_TARGET))
+
+
+def abc_get_population(ctx, u=None, dist=None, W=None, s=None, anc=None, on_device=False):
+    def p(x):
+        if x is None:
+            return None
+        return x.ctypes.data if hasattr(x, "ctypes") else _ptr(x)
+    return _check(lib().abc_get_population(ctx, p(u), p(dist), p(W), p(s), p(anc),
+                                           1 if on_device else 0), "abc_get_population")
+
+
+def abc_get_stats(ctx, t):
+    st = AbcGenStats()
+    _check(lib().abc_get_stats(ctx, t, C.byref(st)), "abc_get_stats")
+    return st
+
+
+def abc_generations(ctx):
+    return lib().abc_generations(ctx)
+
+
+def abc_get_state(ctx):
+    n = C.c_size_t(0)
+    _check(lib().abc_get_state(ctx, None, C.byref(n)), "abc_get_state")
+    buf = C.create_string_buffer(n.value)
+    _check(lib().abc_get_state(ctx, C.cast(buf, C.c_void_p), C.byref(n)), "abc_get_state")
+    return buf.raw[: n.value]
+
+
+def abc_set_state(ctx, blob: bytes):
+    buf = C.create_string_buffer(blob, len(blob))
+    return _check(lib().abc_set_state(ctx, C.cast(buf, C.c_void_p), len(blob)), "abc_set_state")
+
+
+def abc_set_state_ptr(ctx, host_ptr: int, nbytes: int):
+    """abc_set_state from a host buffer given by address (e.g. pinned memory)."""
+    return _check(lib().abc_set_state(ctx, host_ptr, nbytes), "abc_set_state")
+
+
+def abc_free(ctx):
+    if ctx:
+        lib().abc_free(ctx)

@@ -1,0 +1,104 @@
+// common.cuh -- internal types and helpers shared by the kernels and the
+// C ABI layer (never exposed in the public header).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/abcsmc.h"
+
+namespace abc {
+
+// Model parameters as the kernels see them (by value, ~140 bytes).
+struct SimParams {
+  int32_t model, sampler, T, pad;
+  int32_t A0, R0, D0, pad2;
+  int64_t P;
+  float lo[8], hi[8], x_obs[8];
+  uint32_t k0, k1;  // Philox key
+};
+
+inline SimParams make_params(const abc_config& c) {
+  SimParams p{};
+  p.model = c.model;
+  p.sampler = c.sampler;
+  p.T = c.n_days;
+  p.A0 = c.init_ard[0];
+  p.R0 = c.init_ard[1];
+  p.D0 = c.init_ard[2];
+  p.P = c.population;
+  for (int d = 0; d < 8; ++d) {
+    p.lo[d] = c.theta_lo[d];
+    p.hi[d] = c.theta_hi[d];
+    p.x_obs[d] = c.x_obs[d];
+  }
+  p.k0 = static_cast<uint32_t>(c.seed & 0xFFFFFFFFull);
+  p.k1 = static_cast<uint32_t>(c.seed >> 32) ^ c.run_id;
+  return p;
+}
+
+#define ABC_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t abc_err_ = (expr);                          \
+    if (abc_err_ != cudaSuccess) return ABC_E_CUDA;         \
+  } while (0)
+
+// Every kernel launch is followed by ABC_LAUNCH_CHECK(), which also counts
+// the launch (reported per generation).
+int64_t count_launch();
+#define ABC_LAUNCH_CHECK()      \
+  do {                          \
+    ::abc::count_launch();      \
+    ABC_CUDA_TRY(cudaGetLastError()); \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// round up to 256 bytes so that sub-buffers of one scratch area stay aligned
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ---- block-level scans and reductions (blockDim.x a multiple of 32) ------
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+// inclusive scan over the block; smem needs blockDim.x / 32 elements
+template <typename T>
+__device__ __forceinline__ T block_incl_scan(T v, T* smem) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  v = warp_incl_scan(v);
+  if (lane == 31) smem[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < nw ? smem[lane] : T(0);
+    w = warp_incl_scan(w);
+    if (lane < nw) smem[lane] = w;
+  }
+  __syncthreads();
+  T off = warp > 0 ? smem[warp - 1] : T(0);
+  __syncthreads();
+  return v + off;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* smem) {
+  T inc = block_incl_scan(v, smem);
+  __shared__ T last;
+  if (threadIdx.x == blockDim.x - 1) last = inc;
+  __syncthreads();
+  T r = last;
+  __syncthreads();
+  return r;
+}
+
+}  // namespace abc

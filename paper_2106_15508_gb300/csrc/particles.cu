@@ -1,0 +1,539 @@
+// particles.cu -- the HBM-bound particle passes of one SMC generation:
+//   A4 tolerance: radix select of the k-th smallest distance (Eq. 8)
+//   A5 stage-prior weights, u32 quantisation and u64 inclusive prefix
+//      (Eq. 9-11) with a reduce-then-scan over 1024-element tiles
+//   A6-A7 BDSS proposal: categorical ancestor, Beta step, Gaussian walk and
+//      support redraw (Eq. 11, 16, 17)
+//   A8 acceptance and in-order append (Sec. 2.3, Sec. 4.1)
+//   survivor compaction for the weight pass, A10 fp64 normalisation / ESS
+// Every reduction runs in a fixed order (block partials, then one block),
+// so results never depend on scheduling.
+#include <algorithm>
+
+#include "common.cuh"
+#include "numerics.cuh"
+
+namespace abc {
+
+constexpr int kTile = 1024;    // elements per scan tile
+constexpr int kTileThr = 256;  // threads per tile (4 elements each)
+
+// --------------------------------------------------------------- A4 select -
+struct SelState {
+  unsigned long long prefix, mask;
+  long long k;
+};
+
+__global__ void k_sel_init(SelState* st, unsigned* hist, long long k) {
+  if (threadIdx.x == 0) *st = SelState{0ull, 0ull, k};
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0u;
+}
+
+__global__ void k_sel_hist(const double* __restrict__ d, int64_t n, const SelState* st,
+                           int shift, unsigned* hist) {
+  __shared__ unsigned sh[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) sh[i] = 0u;
+  __syncthreads();
+  const unsigned long long prefix = st->prefix, mask = st->mask;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const unsigned long long key = static_cast<unsigned long long>(__double_as_longlong(d[i]));
+    if ((key & mask) == prefix) atomicAdd(&sh[(key >> shift) & 255ull], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+__global__ void k_sel_pick(SelState* st, unsigned* hist, int shift, double* out) {
+  if (threadIdx.x == 0) {
+    long long k = st->k;
+    int b = 0;
+    long long below = 0;
+    for (b = 0; b < 255; ++b) {
+      if (below + hist[b] >= k) break;
+      below += hist[b];
+    }
+    st->k = k - below;
+    st->prefix |= static_cast<unsigned long long>(b) << shift;
+    st->mask |= 255ull << shift;
+    if (shift == 0) *out = __longlong_as_double(static_cast<long long>(st->prefix));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0u;
+}
+
+size_t select_scratch_bytes(int64_t) { return align256(sizeof(SelState)) + align256(256 * 4); }
+
+int launch_select(const double* d, int64_t n, int64_t k, double* out, void* scratch,
+                  size_t bytes, cudaStream_t st) {
+  if (n <= 0 || k < 1 || k > n) return ABC_E_INVAL;
+  if (bytes < select_scratch_bytes(n)) return ABC_E_SCRATCH;
+  char* base = static_cast<char*>(scratch);
+  SelState* s = reinterpret_cast<SelState*>(base);
+  unsigned* hist = reinterpret_cast<unsigned*>(base + align256(sizeof(SelState)));
+  k_sel_init<<<1, 256, 0, st>>>(s, hist, static_cast<long long>(k));
+  ABC_LAUNCH_CHECK();
+  const unsigned grid = static_cast<unsigned>(std::min<int64_t>(ceil_div(n, 1024), 152 * 8));
+  for (int pass = 0; pass < 8; ++pass) {
+    const int shift = 56 - 8 * pass;
+    k_sel_hist<<<grid, 256, 0, st>>>(d, n, s, shift, hist);
+    ABC_LAUNCH_CHECK();
+    k_sel_pick<<<1, 256, 0, st>>>(s, hist, shift, out);
+    ABC_LAUNCH_CHECK();
+  }
+  return ABC_OK;
+}
+
+// ------------------------------------------------- A5 weights and prefix ---
+__device__ __forceinline__ double stage_weight(double d, double w, double eps, int mode) {
+  if (!(d <= eps)) return 0.0;
+  return mode == ABC_W_PAPER ? __dsub_rn(eps, d) : w;
+}
+
+__global__ void k_rmax(const double* __restrict__ d, const double* __restrict__ W, int64_t n,
+                       const double* eps_p, int mode, unsigned long long* rmax_bits) {
+  const double eps = *eps_p;
+  double m = 0.0;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    m = fmax(m, stage_weight(d[i], W ? W[i] : 0.0, eps, mode));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  // r >= 0, so the IEEE bit pattern orders like the value
+  if ((threadIdx.x & 31) == 0)
+    atomicMax(rmax_bits, static_cast<unsigned long long>(__double_as_longlong(m)));
+}
+
+__global__ void k_quantize(const double* __restrict__ d, const double* __restrict__ W, int64_t n,
+                           const double* eps_p, int mode, const unsigned long long* rmax_bits,
+                           uint32_t* __restrict__ q, unsigned long long* tile_sum) {
+  __shared__ unsigned long long sm[32];
+  const double eps = *eps_p;
+  const double rmax = __longlong_as_double(static_cast<long long>(*rmax_bits));
+  const bool proper = rmax > 0.0 && isfinite(rmax);
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
+  unsigned long long s = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int64_t i = base + e * kTileThr + threadIdx.x;
+    if (i < n) {
+      uint32_t qi;
+      if (proper) {
+        const double r = stage_weight(d[i], W ? W[i] : 0.0, eps, mode);
+        qi = static_cast<uint32_t>(floor(__dmul_rn(__ddiv_rn(r, rmax), 4294967295.0)));
+      } else {
+        qi = d[i] <= eps ? 1u : 0u;
+      }
+      q[i] = qi;
+      s += qi;
+    }
+  }
+  s = block_sum<unsigned long long>(s, sm);
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = s;
+}
+
+// exclusive scan of per-tile totals by one block, in chunks of blockDim.x
+template <typename T>
+__global__ void k_scan_tiles(const T* __restrict__ in, int64_t ntiles, T* __restrict__ out,
+                             T* total) {
+  __shared__ T sm[32];
+  T carry = 0;
+  for (int64_t b = 0; b < ntiles; b += blockDim.x) {
+    const int64_t i = b + threadIdx.x;
+    const T v = i < ntiles ? in[i] : T(0);
+    const T inc = block_incl_scan<T>(v, sm);
+    if (i < ntiles) out[i] = carry + inc - v;
+    __shared__ T last;
+    if (threadIdx.x == blockDim.x - 1) last = inc;
+    __syncthreads();
+    carry += last;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void k_prefix_tiles(const uint32_t* __restrict__ q, int64_t n,
+                               const unsigned long long* __restrict__ tile_off,
+                               uint64_t* __restrict__ prefix) {
+  __shared__ unsigned long long sm[32];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile + 4 * threadIdx.x;
+  unsigned long long v[4];
+  unsigned long long s = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    v[e] = base + e < n ? q[base + e] : 0ull;
+    s += v[e];
+  }
+  const unsigned long long inc = block_incl_scan<unsigned long long>(s, sm);
+  unsigned long long run = tile_off[blockIdx.x] + inc - s;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    run += v[e];
+    if (base + e < n) prefix[base + e] = run;
+  }
+}
+
+size_t prefix_scratch_bytes(int64_t n) {
+  const int64_t nt = ceil_div(std::max<int64_t>(n, 1), kTile);
+  return align256(8) + 2 * align256(8 * nt) + align256(8);
+}
+
+int launch_resample_prefix(const double* d, const double* W, int64_t n, const double* eps,
+                           int mode, uint32_t* q, uint64_t* prefix, void* scratch, size_t bytes,
+                           cudaStream_t st) {
+  if (n <= 0) return ABC_E_INVAL;
+  if (mode == ABC_W_IMPORTANCE && !W) return ABC_E_INVAL;
+  if (bytes < prefix_scratch_bytes(n)) return ABC_E_SCRATCH;
+  const int64_t nt = ceil_div(n, kTile);
+  char* b = static_cast<char*>(scratch);
+  auto* rmax = reinterpret_cast<unsigned long long*>(b);
+  auto* tsum = reinterpret_cast<unsigned long long*>(b + align256(8));
+  auto* toff = reinterpret_cast<unsigned long long*>(b + align256(8) + align256(8 * nt));
+  ABC_CUDA_TRY(cudaMemsetAsync(rmax, 0, 8, st));
+  const unsigned g = static_cast<unsigned>(std::min<int64_t>(ceil_div(n, 256), 152 * 8));
+  k_rmax<<<g, 256, 0, st>>>(d, mode == ABC_W_PAPER ? nullptr : W, n, eps, mode, rmax);
+  ABC_LAUNCH_CHECK();
+  k_quantize<<<static_cast<unsigned>(nt), kTileThr, 0, st>>>(
+      d, mode == ABC_W_PAPER ? nullptr : W, n, eps, mode, rmax, q, tsum);
+  ABC_LAUNCH_CHECK();
+  k_scan_tiles<unsigned long long><<<1, 1024, 0, st>>>(tsum, nt, toff, nullptr);
+  ABC_LAUNCH_CHECK();
+  k_prefix_tiles<<<static_cast<unsigned>(nt), kTileThr, 0, st>>>(q, n, toff, prefix);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+// -------------------------------------------------------- A6-A7 propose ---
+__global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
+                          const uint64_t* __restrict__ prefix, int paper_beta,
+                          const double* eps_p, const double* eps1_p, float beta_a, int beta_b,
+                          int64_t slots, const uint32_t* __restrict__ c0_idx, uint32_t c1,
+                          int max_redraw, float* __restrict__ u_out, float* __restrict__ s_out,
+                          int32_t* __restrict__ anc_out, int32_t* __restrict__ att_out,
+                          uint8_t* __restrict__ flag_out) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= slots) return;
+  const uint32_t j = c0_idx ? c0_idx[i] : static_cast<uint32_t>(i);
+  const unsigned long long total = prefix[n - 1];
+  float a_t = beta_a;
+  if (paper_beta) {
+    // Eq. 16: a_t = eps_t / eps_1 (1 when eps_1 is zero)
+    const double e1 = *eps1_p;
+    a_t = e1 > 0.0 ? __double2float_rn(__ddiv_rn(*eps_p, e1)) : 1.0f;
+  }
+  float up[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float s = 0.0f;
+  int64_t anc = 0;
+  bool ok = false;
+  int a;
+  for (a = 0; a < max_redraw; ++a) {
+    // Eq. 11: categorical ancestor by inverting the u64 prefix
+    const u32x4 wa = philox4x32_10(j, c1, static_cast<uint32_t>(a), ABC_TAG_ANCESTOR, p.k0, p.k1);
+    const unsigned long long U = (static_cast<unsigned long long>(wa.y) << 32) | wa.x;
+    const unsigned long long x = __umul64hi(U, total);
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int64_t mid = lo + ((hi - lo) >> 1);
+      if (prefix[mid] > x) hi = mid;
+      else lo = mid + 1;
+    }
+    anc = lo;
+    // Eq. 16: s ~ Beta(a_t, b) as exp(sum_m log(U_m) / (a_t + m))
+    float acc = 0.0f;
+    u32x4 wb{0u, 0u, 0u, 0u};
+    for (int m = 0; m < beta_b; ++m) {
+      if ((m & 3) == 0)
+        wb = philox4x32_10(j, c1, (static_cast<uint32_t>(a) << 8) | static_cast<uint32_t>(m >> 2),
+                           ABC_TAG_BETA, p.k0, p.k1);
+      const uint32_t wm = (m & 3) == 0 ? wb.x : (m & 3) == 1 ? wb.y : (m & 3) == 2 ? wb.z : wb.w;
+      acc = __fadd_rn(acc, __fdiv_rn(dev_log(unif(wm)), __fadd_rn(a_t, __int2float_rn(m))));
+    }
+    s = dev_exp(acc);
+    const float sd = __fsqrt_rn(s);
+    // Eq. 17: u' = u_anc + sqrt(s) z; the support check covers all 8 coordinates
+    ok = true;
+#pragma unroll
+    for (int blk = 0; blk < 4; ++blk) {
+      const u32x4 wz = philox4x32_10(j, c1, (static_cast<uint32_t>(a) << 8) | blk, ABC_TAG_WALK,
+                                     p.k0, p.k1);
+      const float z0 = dev_normal(unif(wz.x), unif(wz.y));
+      const float z1 = dev_normal(unif(wz.z), unif(wz.w));
+      const float v0 = __fadd_rn(u[static_cast<int64_t>(2 * blk) * n + anc], __fmul_rn(sd, z0));
+      const float v1 = __fadd_rn(u[static_cast<int64_t>(2 * blk + 1) * n + anc], __fmul_rn(sd, z1));
+      up[2 * blk] = v0;
+      up[2 * blk + 1] = v1;
+      ok = ok && v0 >= 0.0f && v0 <= 1.0f && v1 >= 0.0f && v1 <= 1.0f;
+    }
+    if (ok) break;
+  }
+#pragma unroll
+  for (int d = 0; d < 8; ++d) u_out[static_cast<int64_t>(d) * slots + i] = up[d];
+  s_out[i] = s;
+  anc_out[i] = static_cast<int32_t>(anc);
+  att_out[i] = ok ? a + 1 : max_redraw;
+  flag_out[i] = ok ? 0 : 1;
+}
+
+int launch_propose(const SimParams& p, const float* u, int64_t n, const uint64_t* prefix,
+                   int paper_beta, const double* eps, const double* eps1, float beta_a,
+                   int beta_b, int64_t slots, const uint32_t* c0_idx, uint32_t c1, int max_redraw,
+                   float* u_out, float* s_out, int32_t* anc_out, int32_t* att_out,
+                   uint8_t* flag_out, cudaStream_t st) {
+  if (n <= 0 || slots < 0 || beta_b < 1 || beta_b > 1024 || max_redraw < 1) return ABC_E_INVAL;
+  if (paper_beta && (!eps || !eps1)) return ABC_E_INVAL;
+  if (slots == 0) return ABC_OK;
+  k_propose<<<static_cast<unsigned>(ceil_div(slots, 128)), 128, 0, st>>>(
+      p, u, n, prefix, paper_beta, eps, eps1, beta_a, beta_b, slots, c0_idx, c1, max_redraw,
+      u_out, s_out, anc_out, att_out, flag_out);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+// ----------------------------------------------------------- A8 accept ---
+__global__ void k_acc_count(const double* __restrict__ dp, const uint8_t* __restrict__ flag,
+                            int64_t M, const double* eps_p, int* __restrict__ tile_cnt,
+                            long long* counters) {
+  __shared__ int sm[32];
+  __shared__ int smf[32];
+  const double eps = *eps_p;
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile + 4 * threadIdx.x;
+  int c = 0, f = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int64_t i = base + e;
+    if (i < M) {
+      const bool fl = flag[i] != 0;
+      f += fl;
+      c += (!fl && dp[i] <= eps);
+    }
+  }
+  c = block_sum<int>(c, sm);
+  f = block_sum<int>(f, smf);
+  if (threadIdx.x == 0) {
+    tile_cnt[blockIdx.x] = c;
+    if (f) atomicAdd(reinterpret_cast<unsigned long long*>(&counters[1]),
+                     static_cast<unsigned long long>(f));
+  }
+}
+
+__global__ void k_acc_finish(const int* tile_total, long long* filled, long long* base_out,
+                             long long* counters, int64_t N) {
+  const long long tot = *tile_total;
+  const long long f0 = *filled;
+  *base_out = f0;
+  counters[0] += tot;
+  *filled = f0 + tot < N ? f0 + tot : N;
+}
+
+__global__ void k_acc_scatter(const float* __restrict__ up, const double* __restrict__ dp,
+                              const float* __restrict__ sp, const int32_t* __restrict__ ap,
+                              const uint8_t* __restrict__ flag, int64_t M, const double* eps_p,
+                              const int* __restrict__ tile_off, const long long* base_p,
+                              int64_t N, float* __restrict__ u_pop, double* __restrict__ d_pop,
+                              float* __restrict__ s_pop, int32_t* __restrict__ anc_pop) {
+  __shared__ int sm[32];
+  const double eps = *eps_p;
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile + 4 * threadIdx.x;
+  bool acc[4];
+  int c = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int64_t i = base + e;
+    acc[e] = i < M && flag[i] == 0 && dp[i] <= eps;
+    c += acc[e];
+  }
+  const int inc = block_incl_scan<int>(c, sm);
+  long long pos = *base_p + tile_off[blockIdx.x] + inc - c;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (!acc[e]) continue;
+    const int64_t i = base + e;
+    if (pos < N) {
+#pragma unroll
+      for (int d = 0; d < 8; ++d) u_pop[static_cast<int64_t>(d) * N + pos] = up[static_cast<int64_t>(d) * M + i];
+      d_pop[pos] = dp[i];
+      s_pop[pos] = sp[i];
+      anc_pop[pos] = ap[i];
+    }
+    ++pos;
+  }
+}
+
+size_t accept_scratch_bytes(int64_t M) {
+  const int64_t nt = ceil_div(std::max<int64_t>(M, 1), kTile);
+  return 2 * align256(4 * nt) + align256(8) + align256(8);
+}
+
+int launch_accept(const float* up, const double* dp, const float* sp, const int32_t* ap,
+                  const uint8_t* flag, int64_t M, const double* eps, int64_t N, float* u_pop,
+                  double* d_pop, float* s_pop, int32_t* anc_pop, int64_t* filled,
+                  int64_t* counters, void* scratch, size_t bytes, cudaStream_t st) {
+  if (M < 0 || N <= 0) return ABC_E_INVAL;
+  if (M == 0) return ABC_OK;
+  if (bytes < accept_scratch_bytes(M)) return ABC_E_SCRATCH;
+  const int64_t nt = ceil_div(M, kTile);
+  char* b = static_cast<char*>(scratch);
+  int* cnt = reinterpret_cast<int*>(b);
+  int* off = reinterpret_cast<int*>(b + align256(4 * nt));
+  int* tot = reinterpret_cast<int*>(b + 2 * align256(4 * nt));
+  long long* basep = reinterpret_cast<long long*>(b + 2 * align256(4 * nt) + align256(8));
+  long long* cnts = reinterpret_cast<long long*>(counters);
+  k_acc_count<<<static_cast<unsigned>(nt), kTileThr, 0, st>>>(dp, flag, M, eps, cnt, cnts);
+  ABC_LAUNCH_CHECK();
+  k_scan_tiles<int><<<1, 1024, 0, st>>>(cnt, nt, off, tot);
+  ABC_LAUNCH_CHECK();
+  k_acc_finish<<<1, 1, 0, st>>>(tot, reinterpret_cast<long long*>(filled), basep, cnts, N);
+  ABC_LAUNCH_CHECK();
+  k_acc_scatter<<<static_cast<unsigned>(nt), kTileThr, 0, st>>>(up, dp, sp, ap, flag, M, eps, off,
+                                                                basep, N, u_pop, d_pop, s_pop,
+                                                                anc_pop);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+// --------------------------------------- survivor columns for the weights -
+// Columns with q_k > 0, in index order: cu [8][nc] and c_k = log2(q_k) - 32.
+__global__ void k_surv_count(const uint32_t* __restrict__ q, int64_t n, int* __restrict__ cnt) {
+  __shared__ int sm[32];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile + 4 * threadIdx.x;
+  int c = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) c += (base + e < n && q[base + e] > 0u);
+  c = block_sum<int>(c, sm);
+  if (threadIdx.x == 0) cnt[blockIdx.x] = c;
+}
+
+__global__ void k_surv_scatter(const float* __restrict__ u, const uint32_t* __restrict__ q,
+                               int64_t n, const int* __restrict__ off, float* __restrict__ cu,
+                               float* __restrict__ cc, int64_t ncap) {
+  __shared__ int sm[32];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile + 4 * threadIdx.x;
+  int c = 0;
+  bool keep[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    keep[e] = base + e < n && q[base + e] > 0u;
+    c += keep[e];
+  }
+  const int inc = block_incl_scan<int>(c, sm);
+  int64_t pos = static_cast<int64_t>(off[blockIdx.x]) + inc - c;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (!keep[e]) continue;
+    const int64_t i = base + e;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) cu[static_cast<int64_t>(d) * ncap + pos] = u[static_cast<int64_t>(d) * n + i];
+    cc[pos] = static_cast<float>(log2(static_cast<double>(q[i])) - 32.0);
+    ++pos;
+  }
+}
+
+size_t survivors_scratch_bytes(int64_t n) {
+  const int64_t nt = ceil_div(std::max<int64_t>(n, 1), kTile);
+  return 2 * align256(4 * nt) + align256(4);
+}
+
+// compacts into cu [8][n] / cc[n] (capacity n); *nc_dev receives the count
+int launch_survivors(const float* u, const uint32_t* q, int64_t n, float* cu, float* cc,
+                     int* nc_dev, void* scratch, cudaStream_t st) {
+  const int64_t nt = ceil_div(n, kTile);
+  char* b = static_cast<char*>(scratch);
+  int* cnt = reinterpret_cast<int*>(b);
+  int* off = reinterpret_cast<int*>(b + align256(4 * nt));
+  k_surv_count<<<static_cast<unsigned>(nt), kTileThr, 0, st>>>(q, n, cnt);
+  ABC_LAUNCH_CHECK();
+  k_scan_tiles<int><<<1, 1024, 0, st>>>(cnt, nt, off, nc_dev);
+  ABC_LAUNCH_CHECK();
+  k_surv_scatter<<<static_cast<unsigned>(nt), kTileThr, 0, st>>>(u, q, n, off, cu, cc, n);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+// ------------------------------------------------------ A10 normalise ----
+constexpr int kNormBlocks = 512;
+
+__global__ void k_nz_max(const double* __restrict__ lw, int64_t n, double* part) {
+  __shared__ double sm[32];
+  double m = -__longlong_as_double(0x7ff0000000000000ll);
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    m = fmax(m, lw[i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (blockDim.x >> 5); ++w) m = fmax(m, sm[w]);
+    part[blockIdx.x] = m;
+  }
+}
+
+// mode 0: exp(lw - M) summed; mode 1: (exp(lw - M) / S)^2 summed, W written
+__global__ void k_nz_sum(const double* __restrict__ lw, int64_t n, const double* stat, int mode,
+                         double* __restrict__ W, double* part) {
+  __shared__ double sm[32];
+  const double M = stat[0];
+  const bool uniform = !(M > -__longlong_as_double(0x7ff0000000000000ll));
+  const double S = stat[1];
+  double acc = 0.0;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double w = uniform ? 1.0 : exp(lw[i] - M);
+    if (mode == 1) {
+      w = uniform ? 1.0 / static_cast<double>(n) : w / S;
+      W[i] = w;
+      w = w * w;
+    }
+    acc += w;
+  }
+  acc = block_sum<double>(acc, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// one block folds the partials: op 0 max -> stat[0], 1 sum -> stat[1], 2 ess
+__global__ void k_nz_fold(const double* part, int np, int op, double* stat, double* ess) {
+  if (threadIdx.x != 0) return;
+  double r = op == 0 ? -__longlong_as_double(0x7ff0000000000000ll) : 0.0;
+  for (int i = 0; i < np; ++i) r = op == 0 ? fmax(r, part[i]) : r + part[i];
+  if (op == 0) stat[0] = r;
+  else if (op == 1) stat[1] = r;
+  else *ess = 1.0 / r;
+}
+
+size_t normalize_scratch_bytes(int64_t) { return align256(8 * kNormBlocks) + align256(16); }
+
+int launch_normalize(const double* lw, int64_t n, double* W, double* ess, void* scratch,
+                     size_t bytes, cudaStream_t st) {
+  if (n <= 0) return ABC_E_INVAL;
+  if (bytes < normalize_scratch_bytes(n)) return ABC_E_SCRATCH;
+  char* b = static_cast<char*>(scratch);
+  double* part = reinterpret_cast<double*>(b);
+  double* stat = reinterpret_cast<double*>(b + align256(8 * kNormBlocks));
+  const int g = static_cast<int>(std::min<int64_t>(kNormBlocks, ceil_div(n, 256)));
+  k_nz_max<<<g, 256, 0, st>>>(lw, n, part);
+  ABC_LAUNCH_CHECK();
+  k_nz_fold<<<1, 32, 0, st>>>(part, g, 0, stat, ess);
+  ABC_LAUNCH_CHECK();
+  k_nz_sum<<<g, 256, 0, st>>>(lw, n, stat, 0, W, part);
+  ABC_LAUNCH_CHECK();
+  k_nz_fold<<<1, 32, 0, st>>>(part, g, 1, stat, ess);
+  ABC_LAUNCH_CHECK();
+  k_nz_sum<<<g, 256, 0, st>>>(lw, n, stat, 1, W, part);
+  ABC_LAUNCH_CHECK();
+  k_nz_fold<<<1, 32, 0, st>>>(part, g, 2, stat, ess);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+__global__ void k_fill_f64(double* p, int64_t n, double v) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+int launch_fill(double* p, int64_t n, double v, cudaStream_t st) {
+  if (n <= 0) return ABC_OK;
+  k_fill_f64<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, st>>>(p, n, v);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+}  // namespace abc

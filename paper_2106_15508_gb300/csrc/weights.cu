@@ -1,0 +1,151 @@
+// weights.cu -- A9 importance weights, FP32 CUDA-core path.
+//
+//   log W_j = 4 ln(2 pi s_j) - ln sum_k (q_k / total) exp(-|u'_j - u_k|^2 / (2 s_j))
+//
+// over the surviving columns (q_k > 0), compacted beforehand into cu [8][nc]
+// and c_k = log2(q_k) - 32 (in [-32, 0), so the dominant terms carry small
+// absolute rounding error).  Work is in base 2: e_jk = c_k - D_jk log2(e) /
+// (2 s_j), an online row maximum m and a running sum of 2^(e - m).
+// Accuracy: D_jk from direct differences (no |a|^2 + |b|^2 - 2ab
+// cancellation); each 128-column tile is summed locally and folded into the
+// row total with Kahan compensation.  Columns are split into chunks over
+// grid.y; a combine kernel merges the (m, S) partials in fp64.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace abc {
+
+constexpr int kWThreads = 128;  // threads per CTA
+constexpr int kWRows = 4;       // rows per thread
+constexpr int kWTile = 128;     // columns per shared-memory tile
+
+__global__ void __launch_bounds__(kWThreads)
+k_weights_fp32(const float* __restrict__ up, const float* __restrict__ s, int64_t rows,
+               const float* __restrict__ cu, const float* __restrict__ cc,
+               const int* __restrict__ nc_p, int64_t ncap, int64_t chunk_cols,
+               float2* __restrict__ part) {
+  __shared__ float su[8][kWTile];
+  __shared__ float sc[kWTile];
+  const int64_t nc = *nc_p;
+  const int64_t c_begin = static_cast<int64_t>(blockIdx.y) * chunk_cols;
+  const int64_t c_end = nc < c_begin + chunk_cols ? nc : c_begin + chunk_cols;
+  const int64_t row0 = static_cast<int64_t>(blockIdx.x) * (kWThreads * kWRows) + threadIdx.x;
+  float x[kWRows][8], ninv[kWRows], m[kWRows], S[kWRows], cS[kWRows], t[kWRows];
+#pragma unroll
+  for (int r = 0; r < kWRows; ++r) {
+    const int64_t j = row0 + r * kWThreads;
+    const bool live = j < rows;
+    const float sj = live ? s[j] : 1.0f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) x[r][d] = live ? up[static_cast<int64_t>(d) * rows + j] : 0.0f;
+    // -log2(e) / (2 s_j); rows with s_j == 0 are finished by the combine kernel
+    ninv[r] = sj > 0.0f ? -1.4426950408889634f / (2.0f * sj) : 0.0f;
+    m[r] = -INFINITY;
+    S[r] = 0.0f;
+    cS[r] = 0.0f;
+    t[r] = 0.0f;
+  }
+  for (int64_t c0 = c_begin; c0 < c_end; c0 += kWTile) {
+    const int cnt = static_cast<int>(c_end - c0 < kWTile ? c_end - c0 : kWTile);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kWTile; i += kWThreads) {
+      const bool in = i < cnt;
+#pragma unroll
+      for (int d = 0; d < 8; ++d) su[d][i] = in ? cu[static_cast<int64_t>(d) * ncap + c0 + i] : 0.0f;
+      sc[i] = in ? cc[c0 + i] : -INFINITY;
+    }
+    __syncthreads();
+    for (int k = 0; k < cnt; ++k) {
+      float uk[8];
+#pragma unroll
+      for (int d = 0; d < 8; ++d) uk[d] = su[d][k];
+      const float ck = sc[k];
+#pragma unroll
+      for (int r = 0; r < kWRows; ++r) {
+        float D = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+          const float df = x[r][d] - uk[d];
+          D = __fmaf_rn(df, df, D);
+        }
+        const float e = __fmaf_rn(D, ninv[r], ck);
+        if (e > m[r]) {
+          const float f = exp2f(m[r] - e);
+          S[r] *= f;
+          cS[r] *= f;
+          t[r] *= f;
+          m[r] = e;
+        }
+        t[r] += exp2f(e - m[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kWRows; ++r) {
+      const float y = t[r] - cS[r];
+      const float tt = S[r] + y;
+      cS[r] = (tt - S[r]) - y;
+      S[r] = tt;
+      t[r] = 0.0f;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kWRows; ++r) {
+    const int64_t j = row0 + r * kWThreads;
+    if (j < rows) part[static_cast<int64_t>(blockIdx.y) * rows + j] = make_float2(m[r], S[r]);
+  }
+}
+
+__global__ void k_weights_combine(const float2* __restrict__ part, int nchunks,
+                                  const float* __restrict__ s, int64_t rows,
+                                  const uint64_t* __restrict__ total_p, double* __restrict__ logW) {
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= rows) return;
+  const double sj = static_cast<double>(s[j]);
+  if (!(sj > 0.0)) {
+    logW[j] = -INFINITY;
+    return;
+  }
+  double M = -INFINITY;
+  for (int c = 0; c < nchunks; ++c) M = fmax(M, static_cast<double>(part[static_cast<int64_t>(c) * rows + j].x));
+  double S = 0.0;
+  for (int c = 0; c < nchunks; ++c) {
+    const float2 p = part[static_cast<int64_t>(c) * rows + j];
+    if (p.y > 0.0f) S += static_cast<double>(p.y) * exp2(static_cast<double>(p.x) - M);
+  }
+  // ln sum_k rhat_k exp(.) = ln2 (M + log2 S + 32 - log2 total)
+  const double lse = 0.6931471805599453 * (M + log2(S) + 32.0 - log2(static_cast<double>(*total_p)));
+  logW[j] = 4.0 * log(6.283185307179586 * sj) - lse;
+}
+
+static int weight_chunks(int64_t rows, int64_t ncap) {
+  const int64_t gx = ceil_div(std::max<int64_t>(rows, 1), kWThreads * kWRows);
+  const int64_t want = std::max<int64_t>(1, 2432 / gx);  // about 16 CTAs per SM in total
+  const int64_t maxc = std::max<int64_t>(1, ceil_div(ncap, kWTile));
+  return static_cast<int>(std::min<int64_t>(want, maxc));
+}
+
+size_t weights_fp32_scratch_bytes(int64_t rows, int64_t ncap) {
+  return align256(sizeof(float2) * static_cast<size_t>(weight_chunks(rows, ncap)) * rows);
+}
+
+// cu/cc/nc_dev: compacted survivor columns (capacity ncap); total_p: device u64
+int launch_weights_fp32(const float* up, const float* s, int64_t rows, const float* cu,
+                        const float* cc, const int* nc_dev, int64_t ncap,
+                        const uint64_t* total_p, double* logW, void* scratch, size_t bytes,
+                        cudaStream_t st) {
+  if (rows <= 0) return ABC_OK;
+  if (bytes < weights_fp32_scratch_bytes(rows, ncap)) return ABC_E_SCRATCH;
+  const int nch = weight_chunks(rows, ncap);
+  const int64_t chunk_cols = ceil_div(ceil_div(ncap, nch), kWTile) * kWTile;
+  float2* part = static_cast<float2*>(scratch);
+  dim3 grid(static_cast<unsigned>(ceil_div(rows, kWThreads * kWRows)), static_cast<unsigned>(nch));
+  k_weights_fp32<<<grid, kWThreads, 0, st>>>(up, s, rows, cu, cc, nc_dev, ncap, chunk_cols, part);
+  ABC_LAUNCH_CHECK();
+  k_weights_combine<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(part, nch, s, rows,
+                                                                                total_p, logW);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+}  // namespace abc
