@@ -196,10 +196,24 @@ ABC_API int abc_accept_append(const float* up, const double* dp, const float* sp
  * -inf.  prec: ABC_P_FP32 (CUDA cores) or ABC_P_BF16_TC (tensor cores).
  * up [8][rows], s[rows], u [8][n], q[n], prefix[n]: device; logW: device
  * double[rows]. */
+/* ABC_P_BF16_TC: the exponent of each pair is an inner product of row and
+ * column feature vectors, evaluated by tcgen05.mma with every feature split
+ * into three bf16 parts (24 significant bits) and fp32 accumulation in tensor
+ * memory; the per-row log-sum-exp runs in fp32 with an fp64 combine.  The
+ * call synchronises the stream to read the kernel's error word (a wait that
+ * timed out gives ABC_E_DEVICE). */
 ABC_API size_t abc_weights_scratch_bytes(int64_t rows, int64_t n);
 ABC_API int abc_weights(const float* up, const float* s, int64_t rows, const float* u, const uint32_t* q,
                 const uint64_t* prefix, int64_t n, int32_t prec, double* logW, void* scratch,
                 size_t scratch_bytes, void* stream);
+
+/* Diagnostic of the tensor-core path: one 128 x 256 x 64 bf16 product
+ * D[i][n] = sum_k A[i][k] B[n][k] (fp32) with the operand layout and
+ * descriptors the weight kernel uses.  A, B: device bf16 tiles packed as
+ * 8 x 8 core matrices, element (r, k) at index ((r/8)*8 + k/8)*64 + (r%8)*8
+ * + k%8 (A: 128 rows, 16 KB; B: 256 rows, 32 KB); D: device float [128][256].
+ * Synchronises the stream; ABC_E_DEVICE if a wait timed out. */
+ABC_API int abc_tc_probe(const void* A, const void* B, float* D, void* stream);
 
 /* A10 normalisation (fp64): W_j = exp(logW_j - max) / sum, *ess = 1 / sum W^2;
  * all -inf gives W = 1/n, ess = n.  logW: device double[n]; W: device

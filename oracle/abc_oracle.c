@@ -633,6 +633,9 @@ OR_API void or_propose(const or_model* m, const float* u, int64_t n, const uint6
  * Importance weight (auxiliary-variable form, spec extension; not in
  * the paper): log W_j = log pi(u'_j) - log sum_k rhat_k N(u'_j; u_k, s_j I8),
  * rhat_k = q_k / total, pi uniform on the unit cube.  fp64 throughout.
+ * The kernel variance is floored at 1e-30f: a row with a smaller step has
+ * relative weight below (1e-30)^4 against any row with s >= 1e-6, and the
+ * floor keeps 1/(2s) finite in fp32 on the device.
  */
 OR_API void or_weights(const float* up, const float* s, int64_t rows, const float* u,
                        const uint32_t* q, int64_t n, uint64_t total, double* logW,
@@ -643,8 +646,7 @@ OR_API void or_weights(const float* up, const float* s, int64_t rows, const floa
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : 1)
 #endif
   for (int64_t j = 0; j < rows; ++j) {
-    double sj = (double)s[j];
-    if (!(sj > 0.0)) { logW[j] = -INFINITY; continue; }
+    double sj = (double)fmaxf(s[j], 1e-30f);
     double* e = (double*)malloc(sizeof(double) * (size_t)n);
     double mx = -INFINITY;
     for (int64_t k = 0; k < n; ++k) {
@@ -666,7 +668,8 @@ OR_API void or_weights(const float* up, const float* s, int64_t rows, const floa
   }
 }
 
-/* W_j = exp(logW_j - max) / sum; ESS = 1 / sum W_j^2 (fp64). */
+/* W_j = exp(logW_j - max) / sum; ESS = 1 / sum W_j^2 (fp64).  A NaN log
+ * weight (no valid input produces one) counts as weight 0. */
 OR_API double or_normalize(const double* logW, int64_t n, double* W) {
   double mx = -INFINITY;
   for (int64_t j = 0; j < n; ++j) if (logW[j] > mx) mx = logW[j];
@@ -675,7 +678,10 @@ OR_API double or_normalize(const double* logW, int64_t n, double* W) {
     return (double)n;
   }
   double sum = 0.0;
-  for (int64_t j = 0; j < n; ++j) { W[j] = exp(logW[j] - mx); sum += W[j]; }
+  for (int64_t j = 0; j < n; ++j) {
+    W[j] = logW[j] == logW[j] ? exp(logW[j] - mx) : 0.0;
+    sum += W[j];
+  }
   double s2 = 0.0;
   for (int64_t j = 0; j < n; ++j) { W[j] = W[j] / sum; s2 += W[j] * W[j]; }
   return 1.0 / s2;

@@ -26,7 +26,8 @@ EXPORTS = (
     "abc_config_default", "abc_philox", "abc_synth_obs", "abc_prior", "abc_simulate",
     "abc_select_scratch_bytes", "abc_select_kth", "abc_prefix_scratch_bytes",
     "abc_resample_prefix", "abc_propose", "abc_accept_scratch_bytes", "abc_accept_append",
-    "abc_weights_scratch_bytes", "abc_weights", "abc_normalize_scratch_bytes", "abc_normalize",
+    "abc_weights_scratch_bytes", "abc_weights", "abc_tc_probe", "abc_normalize_scratch_bytes",
+    "abc_normalize",
     "abc_init", "abc_generation", "abc_run", "abc_get_population", "abc_get_stats",
     "abc_generations", "abc_get_state", "abc_set_state", "abc_free", "abc_strerror",
 )
@@ -86,6 +87,7 @@ _SIGS = {
                                     _SZ, _V]),
     "abc_weights_scratch_bytes": (_SZ, [_I64, _I64]),
     "abc_weights": (C.c_int, [_V, _V, _I64, _V, _V, _V, _I64, _I32, _V, _V, _SZ, _V]),
+    "abc_tc_probe": (C.c_int, [_V, _V, _V, _V]),
     "abc_normalize_scratch_bytes": (_SZ, [_I64]),
     "abc_normalize": (C.c_int, [_V, _I64, _V, _V, _V, _SZ, _V]),
     "abc_init": (C.c_int, [C.POINTER(AbcConfig), _V, _V, C.POINTER(C.c_void_p)]),
@@ -225,6 +227,10 @@ def abc_weights(up, s, rows, u, q, prefix, n, prec, logW, scratch, scratch_bytes
     return _check(lib().abc_weights(_ptr(up), _ptr(s), rows, _ptr(u), _ptr(q), _ptr(prefix), n,
                                     prec, _ptr(logW), _ptr(scratch), scratch_bytes,
                                     _stream(stream)), "abc_weights")
+
+
+def abc_tc_probe(A, B, D, stream=None):
+    return _check(lib().abc_tc_probe(_ptr(A), _ptr(B), _ptr(D), _stream(stream)), "abc_tc_probe")
 
 
 def abc_normalize_scratch_bytes(n):

@@ -35,6 +35,11 @@ size_t weights_fp32_scratch_bytes(int64_t, int64_t);
 int launch_weights_fp32(const float*, const float*, int64_t, const float*, const float*,
                         const int*, int64_t, const uint64_t*, double*, void*, size_t,
                         cudaStream_t);
+size_t weights_tc_scratch_bytes(int64_t, int64_t);
+int launch_weights_tc(const float*, const float*, int64_t, const float*, const float*, const int*,
+                      int64_t, const uint64_t*, double*, void*, size_t, unsigned**,
+                      cudaStream_t);
+int launch_tc_probe(const void*, const void*, float*, unsigned*, cudaStream_t);
 size_t normalize_scratch_bytes(int64_t);
 int launch_normalize(const double*, int64_t, double*, double*, void*, size_t, cudaStream_t);
 int launch_fill(double*, int64_t, double, cudaStream_t);
@@ -223,8 +228,16 @@ static size_t weights_layout(int64_t rows, int64_t n, size_t* off_cc, size_t* of
   *off_comp = o;
   o += align256(survivors_scratch_bytes(n));
   *off_w = o;
-  o += align256(weights_fp32_scratch_bytes(rows, n));
+  o += align256(std::max(weights_fp32_scratch_bytes(rows, n), weights_tc_scratch_bytes(rows, n)));
   return o;
+}
+
+// reads a device error word after the stream drains; nonzero -> ABC_E_DEVICE
+static int check_device_error(const unsigned* err, cudaStream_t st) {
+  unsigned h = 0;
+  ABC_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, st));
+  ABC_CUDA_TRY(cudaStreamSynchronize(st));
+  return h ? ABC_E_DEVICE : ABC_OK;
 }
 
 ABC_API size_t abc_weights_scratch_bytes(int64_t rows, int64_t n) {
@@ -237,7 +250,7 @@ ABC_API int abc_weights(const float* up, const float* s, int64_t rows, const flo
                         double* logW, void* scratch, size_t scratch_bytes, void* stream) {
   if (rows < 0 || n < 1 || rows > kMaxIndex || n > kMaxIndex) return ABC_E_INVAL;
   if (!up || !s || !u || !q || !prefix || !logW || !scratch) return ABC_E_INVAL;
-  if (prec != ABC_P_FP32) return ABC_E_INVAL;
+  if (prec != ABC_P_FP32 && prec != ABC_P_BF16_TC) return ABC_E_INVAL;
   size_t occ, onc, ocomp, ow;
   const size_t need = weights_layout(rows, n, &occ, &onc, &ocomp, &ow);
   if (scratch_bytes < need) return ABC_E_SCRATCH;
@@ -248,8 +261,26 @@ ABC_API int abc_weights(const float* up, const float* s, int64_t rows, const flo
   int* nc = reinterpret_cast<int*>(b + onc);
   int rc = launch_survivors(u, q, n, cu, cc, nc, b + ocomp, st);
   if (rc) return rc;
-  return launch_weights_fp32(up, s, rows, cu, cc, nc, n, prefix + (n - 1), logW, b + ow,
-                             scratch_bytes - ow, st);
+  if (prec == ABC_P_FP32)
+    return launch_weights_fp32(up, s, rows, cu, cc, nc, n, prefix + (n - 1), logW, b + ow,
+                               scratch_bytes - ow, st);
+  unsigned* err = nullptr;
+  rc = launch_weights_tc(up, s, rows, cu, cc, nc, n, prefix + (n - 1), logW, b + ow,
+                         scratch_bytes - ow, &err, st);
+  if (rc) return rc;
+  return check_device_error(err, st);
+}
+
+ABC_API int abc_tc_probe(const void* A, const void* B, float* D, void* stream) {
+  if (!A || !B || !D) return ABC_E_INVAL;
+  cudaStream_t st = as_stream(stream);
+  unsigned* err = nullptr;
+  ABC_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&err), sizeof(unsigned), st));
+  int rc = launch_tc_probe(A, B, D, err, st);
+  if (rc == ABC_OK) rc = check_device_error(err, st);
+  cudaFreeAsync(err, st);
+  cudaStreamSynchronize(st);
+  return rc;
 }
 
 ABC_API size_t abc_normalize_scratch_bytes(int64_t n) { return normalize_scratch_bytes(n); }
@@ -355,7 +386,8 @@ int ctx_alloc(abc_ctx* c) {
                         accept_scratch_bytes(c->M), survivors_scratch_bytes(c->N),
                         normalize_scratch_bytes(c->N)});
   if (c->cfg.weight_mode == ABC_W_IMPORTANCE)
-    sb = std::max(sb, weights_fp32_scratch_bytes(c->N, c->N));
+    sb = std::max(sb, c->cfg.weight_prec == ABC_P_BF16_TC ? weights_tc_scratch_bytes(c->N, c->N)
+                                                          : weights_fp32_scratch_bytes(c->N, c->N));
   c->scratch_bytes = sb;
   char* sc = nullptr;
   if ((rc = c->alloc(&sc, sb)) != ABC_OK) return rc;
@@ -451,6 +483,8 @@ int generation_t(abc_ctx* c) {
   g.ms_sim = ms_sim;
   int h_nc = 0;
   bool weighted = false;
+  unsigned* tc_err = nullptr;
+  unsigned h_err = 0;
   if (filled < c->N) {
     g.status = ABC_STOP_BUDGET;
   } else {
@@ -459,10 +493,17 @@ int generation_t(abc_ctx* c) {
       rc = launch_survivors(c->u[cur], c->q, c->N, c->cu, c->cc, c->nc, c->scratch, st);
       if (rc) return rc;
       ABC_CUDA_TRY(cudaEventRecord(c->ew0, st));
-      rc = launch_weights_fp32(c->u[nxt], c->s[nxt], c->N, c->cu, c->cc, c->nc, c->N,
-                               c->prefix + (c->N - 1), c->logW, c->scratch, c->scratch_bytes, st);
+      if (c->cfg.weight_prec == ABC_P_BF16_TC)
+        rc = launch_weights_tc(c->u[nxt], c->s[nxt], c->N, c->cu, c->cc, c->nc, c->N,
+                               c->prefix + (c->N - 1), c->logW, c->scratch, c->scratch_bytes,
+                               &tc_err, st);
+      else
+        rc = launch_weights_fp32(c->u[nxt], c->s[nxt], c->N, c->cu, c->cc, c->nc, c->N,
+                                 c->prefix + (c->N - 1), c->logW, c->scratch, c->scratch_bytes,
+                                 st);
       if (rc) return rc;
       ABC_CUDA_TRY(cudaEventRecord(c->ew1, st));
+      if (tc_err) ABC_CUDA_TRY(cudaMemcpyAsync(&h_err, tc_err, sizeof h_err, cudaMemcpyDeviceToHost, st));
       ABC_CUDA_TRY(cudaMemcpyAsync(&h_nc, c->nc, sizeof(int), cudaMemcpyDeviceToHost, st));
       weighted = true;
       rc = launch_normalize(c->logW, c->N, c->W[nxt], ess, c->scratch, c->scratch_bytes, st);
@@ -475,6 +516,7 @@ int generation_t(abc_ctx* c) {
   double h_scal[3];
   ABC_CUDA_TRY(cudaMemcpyAsync(h_scal, c->scal, sizeof h_scal, cudaMemcpyDeviceToHost, st));
   ABC_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h_err) return ABC_E_DEVICE;
   if (weighted) {
     float ms = 0.f;
     ABC_CUDA_TRY(cudaEventElapsedTime(&ms, c->ew0, c->ew1));

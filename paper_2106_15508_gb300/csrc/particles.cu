@@ -477,7 +477,8 @@ __global__ void k_nz_sum(const double* __restrict__ lw, int64_t n, const double*
   double acc = 0.0;
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    double w = uniform ? 1.0 : exp(lw[i] - M);
+    const double li = lw[i];
+    double w = uniform ? 1.0 : (li == li ? exp(li - M) : 0.0);
     if (mode == 1) {
       w = uniform ? 1.0 / static_cast<double>(n) : w / S;
       W[i] = w;
@@ -490,13 +491,15 @@ __global__ void k_nz_sum(const double* __restrict__ lw, int64_t n, const double*
 }
 
 // one block folds the partials: op 0 max -> stat[0], 1 sum -> stat[1], 2 ess
-__global__ void k_nz_fold(const double* part, int np, int op, double* stat, double* ess) {
+__global__ void k_nz_fold(const double* part, int np, int op, double* stat, double* ess,
+                          int64_t n) {
   if (threadIdx.x != 0) return;
   double r = op == 0 ? -__longlong_as_double(0x7ff0000000000000ll) : 0.0;
   for (int i = 0; i < np; ++i) r = op == 0 ? fmax(r, part[i]) : r + part[i];
   if (op == 0) stat[0] = r;
   else if (op == 1) stat[1] = r;
-  else *ess = 1.0 / r;
+  else *ess = stat[0] > -__longlong_as_double(0x7ff0000000000000ll) ? 1.0 / r
+                                                                      : static_cast<double>(n);
 }
 
 size_t normalize_scratch_bytes(int64_t) { return align256(8 * kNormBlocks) + align256(16); }
@@ -511,15 +514,15 @@ int launch_normalize(const double* lw, int64_t n, double* W, double* ess, void* 
   const int g = static_cast<int>(std::min<int64_t>(kNormBlocks, ceil_div(n, 256)));
   k_nz_max<<<g, 256, 0, st>>>(lw, n, part);
   ABC_LAUNCH_CHECK();
-  k_nz_fold<<<1, 32, 0, st>>>(part, g, 0, stat, ess);
+  k_nz_fold<<<1, 32, 0, st>>>(part, g, 0, stat, ess, n);
   ABC_LAUNCH_CHECK();
   k_nz_sum<<<g, 256, 0, st>>>(lw, n, stat, 0, W, part);
   ABC_LAUNCH_CHECK();
-  k_nz_fold<<<1, 32, 0, st>>>(part, g, 1, stat, ess);
+  k_nz_fold<<<1, 32, 0, st>>>(part, g, 1, stat, ess, n);
   ABC_LAUNCH_CHECK();
   k_nz_sum<<<g, 256, 0, st>>>(lw, n, stat, 1, W, part);
   ABC_LAUNCH_CHECK();
-  k_nz_fold<<<1, 32, 0, st>>>(part, g, 2, stat, ess);
+  k_nz_fold<<<1, 32, 0, st>>>(part, g, 2, stat, ess, n);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

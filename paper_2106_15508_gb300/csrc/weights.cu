@@ -9,7 +9,9 @@
 // Accuracy: D_jk from direct differences (no |a|^2 + |b|^2 - 2ab
 // cancellation); each 128-column tile is summed locally and folded into the
 // row total with Kahan compensation.  Columns are split into chunks over
-// grid.y; a combine kernel merges the (m, S) partials in fp64.
+// grid.y; a combine kernel merges the (m, S) partials in fp64.  The kernel
+// variance is floored at 1e-30 (1/(2s) must stay finite in fp32; such rows
+// carry negligible weight).
 #include <algorithm>
 
 #include "common.cuh"
@@ -19,6 +21,7 @@ namespace abc {
 constexpr int kWThreads = 128;  // threads per CTA
 constexpr int kWRows = 4;       // rows per thread
 constexpr int kWTile = 128;     // columns per shared-memory tile
+constexpr float kSMin = 1e-30f; // floor of the kernel variance s_j
 
 __global__ void __launch_bounds__(kWThreads)
 k_weights_fp32(const float* __restrict__ up, const float* __restrict__ s, int64_t rows,
@@ -36,11 +39,11 @@ k_weights_fp32(const float* __restrict__ up, const float* __restrict__ s, int64_
   for (int r = 0; r < kWRows; ++r) {
     const int64_t j = row0 + r * kWThreads;
     const bool live = j < rows;
-    const float sj = live ? s[j] : 1.0f;
+    // kernel variance floored at 1e-30 so that 1/(2 s) stays finite
+    const float sj = live ? fmaxf(s[j], kSMin) : 1.0f;
 #pragma unroll
     for (int d = 0; d < 8; ++d) x[r][d] = live ? up[static_cast<int64_t>(d) * rows + j] : 0.0f;
-    // -log2(e) / (2 s_j); rows with s_j == 0 are finished by the combine kernel
-    ninv[r] = sj > 0.0f ? -1.4426950408889634f / (2.0f * sj) : 0.0f;
+    ninv[r] = -1.4426950408889634f / (2.0f * sj);  // -log2(e) / (2 s_j)
     m[r] = -INFINITY;
     S[r] = 0.0f;
     cS[r] = 0.0f;
@@ -63,12 +66,15 @@ k_weights_fp32(const float* __restrict__ up, const float* __restrict__ s, int64_
       const float ck = sc[k];
 #pragma unroll
       for (int r = 0; r < kWRows; ++r) {
-        float D = 0.0f;
+        // pairwise sum of the 8 squared differences (3 rounding levels)
+        float q[4];
 #pragma unroll
-        for (int d = 0; d < 8; ++d) {
-          const float df = x[r][d] - uk[d];
-          D = __fmaf_rn(df, df, D);
+        for (int h = 0; h < 4; ++h) {
+          const float a = x[r][2 * h] - uk[2 * h];
+          const float b = x[r][2 * h + 1] - uk[2 * h + 1];
+          q[h] = __fmaf_rn(a, a, b * b);
         }
+        const float D = (q[0] + q[1]) + (q[2] + q[3]);
         const float e = __fmaf_rn(D, ninv[r], ck);
         if (e > m[r]) {
           const float f = exp2f(m[r] - e);
@@ -101,11 +107,7 @@ __global__ void k_weights_combine(const float2* __restrict__ part, int nchunks,
                                   const uint64_t* __restrict__ total_p, double* __restrict__ logW) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= rows) return;
-  const double sj = static_cast<double>(s[j]);
-  if (!(sj > 0.0)) {
-    logW[j] = -INFINITY;
-    return;
-  }
+  const double sj = static_cast<double>(fmaxf(s[j], kSMin));
   double M = -INFINITY;
   for (int c = 0; c < nchunks; ++c) M = fmax(M, static_cast<double>(part[static_cast<int64_t>(c) * rows + j].x));
   double S = 0.0;

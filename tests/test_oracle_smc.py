@@ -155,7 +155,10 @@ def test_weights_mixture_against_scipy():
                 .logpdf(up[:, j].astype(np.float64)) for k in np.where(keep)[0]]
         want = -logsumexp(np.array(comp) + np.log(q[keep].astype(np.float64) / tot))
         assert abs(lw[j] - want) <= 1e-9 * max(1, abs(want)), (j, lw[j], want)
-    assert O.weights(up[:, :1], np.zeros(1, np.float32), u, q, tot)[0] == -math.inf
+    # the kernel variance is floored at 1e-30: s = 0 and s = 1e-30 agree
+    w0 = O.weights(up[:, :3], np.zeros(3, np.float32), u, q, tot)
+    w1 = O.weights(up[:, :3], np.full(3, 1e-30, np.float32), u, q, tot)
+    assert np.array_equal(w0, w1) and np.all(np.isfinite(w0))
 
 
 def test_normalize_and_ess():
@@ -171,6 +174,8 @@ def test_normalize_and_ess():
     assert abs(ess - 1 / np.sum(p**2)) < 1e-9 * ess
     W, ess = O.normalize(np.full(4, -np.inf))
     assert np.allclose(W, 0.25) and ess == 4
+    W, ess = O.normalize(np.array([0.0, np.nan, 0.0]))  # NaN counts as weight 0
+    assert np.allclose(W, [0.5, 0.0, 0.5]) and abs(ess - 2) < 1e-12
 
 
 def _small_saird(seed=1, T=30, P=100000):
