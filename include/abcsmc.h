@@ -55,6 +55,7 @@ extern "C" {
 #define ABC_E_DEVICE (-4)       /* a device-side bound check tripped                     */
 #define ABC_E_SCRATCH (-5)      /* scratch buffer smaller than required                  */
 #define ABC_E_STATE (-6)        /* malformed or mismatched state blob                    */
+#define ABC_E_TOO_LARGE (-7)    /* size above the fixed scratch of an allocation-free call */
 
 /* ---- enumerations ------------------------------------------------------ */
 #define ABC_MODEL_SAIRD 0       /* stochastic S/I/A/R/D/Ru model (Sec. 2.2)              */
@@ -158,6 +159,22 @@ ABC_API size_t abc_prefix_scratch_bytes(int64_t n);
 ABC_API int abc_resample_prefix(const double* d, const double* W, int64_t n, const double* eps,
                         int32_t mode, uint32_t* q, uint64_t* prefix, void* scratch,
                         size_t scratch_bytes, void* stream);
+
+/* Allocation-free variant of abc_resample_prefix (the paper has no
+ * counterpart; it exists for callers that cannot allocate device memory when
+ * they run this step -- for example code whose device memory is owned by a
+ * pool or a fixed budget it does not control).  Same arguments and results as
+ * abc_resample_prefix, without the scratch buffer: the scratch lives in one
+ * fixed array inside the library (257 KB per device, held until the process
+ * exits), which is enough for n <= ABC_NOALLOC_MAX_N = 2^24; larger n returns
+ * ABC_E_TOO_LARGE.  The first call on a device looks up that array's device
+ * address, so make it before any stream capture.  Every call shares the one
+ * array: calls that overlap on the GPU (other streams, other threads) race
+ * and must be serialised by the caller.  No device memory is allocated. */
+#define ABC_NOALLOC_MAX_N (1LL << 24)
+ABC_API int abc_resample_prefix_noalloc(const double* d, const double* W, int64_t n,
+                                        const double* eps, int32_t mode, uint32_t* q,
+                                        uint64_t* prefix, void* stream);
 
 /* A6-A7 BDSS proposal (Eq. 11, 16, 17): for each slot i < slots with
  * c0 = c0_idx ? c0_idx[i] : i and attempt a = 0..max_redraw-1: ancestor =

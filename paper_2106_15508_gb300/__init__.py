@@ -14,6 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libabcsmc.so")
 
 ABC_OK, ABC_STOP_BUDGET, ABC_STOP_TARGET = 0, 1, 2
+ABC_E_TOO_LARGE = -7
+ABC_NOALLOC_MAX_N = 1 << 24
 ABC_MODEL_SAIRD, ABC_MODEL_GAUSS_TOY = 0, 1
 ABC_SIM_BINOMIAL, ABC_SIM_PAPER_NORMAL = 0, 1
 ABC_BETA_PAPER, ABC_BETA_FIXED = 0, 1
@@ -25,7 +27,7 @@ TAG_PRIOR, TAG_ANCESTOR, TAG_BETA, TAG_WALK, TAG_SIM, TAG_OBS, TAG_OBS_THETA = 0
 EXPORTS = (
     "abc_config_default", "abc_philox", "abc_synth_obs", "abc_prior", "abc_simulate",
     "abc_select_scratch_bytes", "abc_select_kth", "abc_prefix_scratch_bytes",
-    "abc_resample_prefix", "abc_propose", "abc_accept_scratch_bytes", "abc_accept_append",
+    "abc_resample_prefix", "abc_resample_prefix_noalloc", "abc_propose", "abc_accept_scratch_bytes", "abc_accept_append",
     "abc_weights_scratch_bytes", "abc_weights", "abc_tc_probe", "abc_normalize_scratch_bytes",
     "abc_normalize",
     "abc_init", "abc_generation", "abc_run", "abc_get_population", "abc_get_stats",
@@ -80,6 +82,7 @@ _SIGS = {
     "abc_select_kth": (C.c_int, [_V, _I64, _I64, _V, _V, _SZ, _V]),
     "abc_prefix_scratch_bytes": (_SZ, [_I64]),
     "abc_resample_prefix": (C.c_int, [_V, _V, _I64, _V, _I32, _V, _V, _V, _SZ, _V]),
+    "abc_resample_prefix_noalloc": (C.c_int, [_V, _V, _I64, _V, _I32, _V, _V, _V]),
     "abc_propose": (C.c_int, [C.POINTER(AbcConfig), _V, _I64, _V, _V, _V, _F, _I32, _I64, _V, _U32,
                               _V, _V, _V, _V, _V, _V]),
     "abc_accept_scratch_bytes": (_SZ, [_I64]),
@@ -197,6 +200,14 @@ def abc_resample_prefix(d, W, n, eps, mode, q, prefix, scratch, scratch_bytes, s
     return _check(lib().abc_resample_prefix(_ptr(d), _ptr(W), n, _ptr(eps), mode, _ptr(q),
                                             _ptr(prefix), _ptr(scratch), scratch_bytes,
                                             _stream(stream)), "abc_resample_prefix")
+
+
+def abc_resample_prefix_noalloc(d, W, n, eps, mode, q, prefix, stream=None):
+    """abc_resample_prefix without a scratch buffer (fixed library scratch,
+    n <= 2^24; calls sharing it must not overlap on the GPU)."""
+    return _check(lib().abc_resample_prefix_noalloc(_ptr(d), _ptr(W), n, _ptr(eps), mode, _ptr(q),
+                                                    _ptr(prefix), _stream(stream)),
+                  "abc_resample_prefix_noalloc")
 
 
 def abc_propose(cfg, u, n, prefix, eps, eps1, beta_a, beta_b, slots, c0_idx, c1, u_out, s_out,

@@ -21,6 +21,8 @@ int launch_select(const double*, int64_t, int64_t, double*, void*, size_t, cudaS
 size_t prefix_scratch_bytes(int64_t);
 int launch_resample_prefix(const double*, const double*, int64_t, const double*, int, uint32_t*,
                            uint64_t*, void*, size_t, cudaStream_t);
+int launch_resample_prefix_noalloc(const double*, const double*, int64_t, const double*, int,
+                                   uint32_t*, uint64_t*, cudaStream_t);
 int launch_propose(const SimParams&, const float*, int64_t, const uint64_t*, int, const double*,
                    const double*, float, int, int64_t, const uint32_t*, uint32_t, int, float*,
                    float*, int32_t*, int32_t*, uint8_t*, cudaStream_t);
@@ -129,6 +131,7 @@ ABC_API const char* abc_strerror(int code) {
     case ABC_E_DEVICE: return "device-side bound check failed";
     case ABC_E_SCRATCH: return "scratch buffer too small";
     case ABC_E_STATE: return "malformed or mismatched state";
+    case ABC_E_TOO_LARGE: return "size above the fixed scratch of the allocation-free entry point";
     default: return "unknown status";
   }
 }
@@ -183,6 +186,15 @@ ABC_API int abc_resample_prefix(const double* d, const double* W, int64_t n, con
   if (mode != ABC_W_PAPER && mode != ABC_W_IMPORTANCE) return ABC_E_INVAL;
   return launch_resample_prefix(d, W, n, eps, mode, q, prefix, scratch, scratch_bytes,
                                 as_stream(stream));
+}
+
+ABC_API int abc_resample_prefix_noalloc(const double* d, const double* W, int64_t n,
+                                        const double* eps, int32_t mode, uint32_t* q,
+                                        uint64_t* prefix, void* stream) {
+  if (!d || !eps || !q || !prefix || n <= 0) return ABC_E_INVAL;
+  if (mode != ABC_W_PAPER && mode != ABC_W_IMPORTANCE) return ABC_E_INVAL;
+  if (n > ABC_NOALLOC_MAX_N) return ABC_E_TOO_LARGE;
+  return launch_resample_prefix_noalloc(d, W, n, eps, mode, q, prefix, as_stream(stream));
 }
 
 ABC_API int abc_propose(const abc_config* cfg, const float* u, int64_t n, const uint64_t* prefix,

@@ -9,6 +9,7 @@
 // Every reduction runs in a fixed order (block partials, then one block),
 // so results never depend on scheduling.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "numerics.cuh"
@@ -201,6 +202,51 @@ int launch_resample_prefix(const double* d, const double* W, int64_t n, const do
   k_prefix_tiles<<<static_cast<unsigned>(nt), kTileThr, 0, st>>>(q, n, toff, prefix);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
+}
+
+// ---------------------------- A5 without allocation (fixed device scratch) --
+// Some callers cannot allocate device memory at the time they run this step
+// (their device memory belongs to a pool or a budget they do not control),
+// so this variant takes its scratch from one file-scope array instead of a
+// caller buffer.  The array holds the scratch of the largest supported size,
+// stays resident on every device that loads the library until the process
+// exits, and is shared by every call: concurrent calls race on it.
+constexpr int64_t kNoAllocMaxN = int64_t(1) << 24;
+constexpr size_t kNoAllocBytes =
+    256 + 2 * static_cast<size_t>(8 * (kNoAllocMaxN / kTile)) + 256;  // prefix_scratch_bytes(max)
+static __device__ __align__(256) unsigned char g_prefix_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+int64_t resample_prefix_noalloc_max_n() { return kNoAllocMaxN; }
+
+// The host-side name of g_prefix_scratch is not a device address: the device
+// address is looked up once per device, with that device current.
+int launch_resample_prefix_noalloc(const double* d, const double* W, int64_t n,
+                                   const double* eps, int mode, uint32_t* q, uint64_t* prefix,
+                                   cudaStream_t st) {
+  static_assert(kNoAllocBytes >= 256 + 2 * 8 * (kNoAllocMaxN / kTile) + 256, "scratch size");
+  if (n > kNoAllocMaxN) return ABC_E_TOO_LARGE;
+  int dev = 0;
+  ABC_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return ABC_E_INVAL;
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_prefix_scratch) != cudaSuccess) {
+        cudaGetLastError();
+        return ABC_E_CUDA;
+      }
+      g_noalloc_addr[dev] = p;
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  if (prefix_scratch_bytes(n) > kNoAllocBytes) return ABC_E_TOO_LARGE;
+  return launch_resample_prefix(d, W, n, eps, mode, q, prefix, scratch, kNoAllocBytes, st);
 }
 
 // -------------------------------------------------------- A6-A7 propose ---
