@@ -243,6 +243,88 @@ def run_gpu(args):
     return line
 
 
+def run_batched(args):
+    """64 independent runs (16K-256K particles, 60-180 days, P 1e6-1e8): one
+    CUDA graph launch per generation of all runs, against the same runs as
+    separate contexts driven one after another from the host ("plain")."""
+    import torch
+
+    import paper_2106_15508_gb300 as G
+    from paper_2106_15508_gb300 import build as B
+    from paper_2106_15508_gb300 import workloads as WL
+
+    B.build()
+    G.lib()
+    runs = WL.batched_runs(args.runs, weight_prec=args.prec)
+    cfgs = [w.config() for w in runs]
+    obs = [synthetic_obs(G, WL, c, torch)[0] for c in cfgs]
+    stream = torch.cuda.Stream()
+    b = G.abc_batch_init(cfgs, obs, stream=stream.cuda_stream)
+    tuning = None
+    try:
+        G.abc_batch_generation(b)
+        if args.autotune:
+            cache = os.path.join(ROOT, "gpurun_out", "autotune.json")
+            os.makedirs(os.path.dirname(cache), exist_ok=True)
+            t0 = time.perf_counter()
+            G.abc_batch_autotune(b, cache)
+            tuning = {"seconds": time.perf_counter() - t0,
+                      "choices": sorted({G.abc_batch_tuning(b, r) for r in range(len(cfgs))})}
+        for _ in range(args.warmup):
+            G.abc_batch_generation(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        first = G.abc_batch_generations(b)
+        for _ in range(args.steps):
+            G.abc_batch_generation(b)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        days = launches = 0
+        for r in range(len(cfgs)):
+            for t in range(first, G.abc_batch_generations(b)):
+                try:
+                    st = G.abc_batch_get_stats(b, r, t)
+                except G.AbcError:
+                    continue
+                days += st.sim_days
+                launches += st.launches
+    finally:
+        G.abc_batch_free(b)
+    # plain: every run in its own context, generations driven from the host
+    ctxs = [G.abc_init(c, o, stream=stream.cuda_stream) for c, o in zip(cfgs, obs)]
+    try:
+        for ctx in ctxs:
+            G.abc_run(ctx, 1 + args.warmup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pdays = 0
+        for ctx in ctxs:
+            for _ in range(args.steps):
+                if G.abc_generation(ctx) != G.ABC_OK:
+                    break
+                pdays += G.abc_get_stats(ctx, G.abc_generations(ctx) - 1).sim_days
+        torch.cuda.synchronize()
+        psecs = time.perf_counter() - t0
+    finally:
+        for ctx in ctxs:
+            G.abc_free(ctx)
+    value = days / secs
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batched_%d_runs" % len(cfgs),
+                       "particles_total": sum(w.N for w in runs),
+                       "weights": "importance O(N^2), " + ("bf16 tcgen05" if args.prec else "fp32"),
+                       "generations_timed": args.steps},
+            "plain": {"value": pdays / psecs, "ms_per_step": psecs * 1e3 / args.steps,
+                      "mode": "separate contexts, host-driven batch loops"},
+            "wall_time_per_run_per_generation_ms": {"batched": secs * 1e3 / args.steps / len(cfgs),
+                                                    "plain": psecs * 1e3 / args.steps / len(cfgs)},
+            "speedup_vs_plain": (days / secs) / (pdays / psecs), "gpu_launches": launches,
+            "autotune": tuning}
+
+
 def cpu_baseline(stats, w):
     """The oracle as it stands on the host cores, on a bounded sample of the
     step: a batch of simulations and a block of weight rows, each timed,
@@ -344,10 +426,18 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--prec", type=int, default=0, help="0 fp32 CUDA cores, 1 bf16 tcgen05")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="single", choices=["single", "batched"])
+    ap.add_argument("--runs", type=int, default=64)
+    ap.add_argument("--autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    line = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    elif args.workload == "batched":
+        line = run_batched(args)
+    else:
+        line = run_gpu(args)
     if line is not None:
         print(json.dumps(line))
 

@@ -289,6 +289,42 @@ ABC_API int abc_set_state(abc_ctx* ctx, const void* buf, size_t len);
 ABC_API void abc_free(abc_ctx* ctx);
 ABC_API const char* abc_strerror(int code);
 
+/* ---- batched runs (spec batched form; the paper runs one problem at
+ * a time) ------------------------------------------------------------------
+ * n_runs independent runs (own config, seed, size, horizon and observed
+ * series each) advanced together.  After stage 0, every generation of every
+ * run is ONE CUDA graph launch: an independent branch per run whose batch
+ * loop is a device-side conditional WHILE node, so no host round trip
+ * happens inside a generation and runs of different sizes overlap on the
+ * GPU.  Results equal those of separate contexts with the same configs bit
+ * for bit (same kernels, same Philox counters).  A run whose generation uses
+ * up its batch budget stops (status ABC_STOP_BUDGET in its stats) and is
+ * skipped afterwards; the others continue. */
+typedef struct abc_batch abc_batch;
+/* cfgs: host array of n_runs configs; obs: host array of n_runs host
+ * pointers to int32 [3][T_r+1] series (entries may be NULL for the toy). */
+ABC_API int abc_batch_init(const abc_config* cfgs, int32_t n_runs, const int32_t* const* obs,
+                           void* stream, abc_batch** out);
+/* First call: stage 0 of every run; later calls: one graph launch. */
+ABC_API int abc_batch_generation(abc_batch* b);
+ABC_API int abc_batch_run(abc_batch* b, int32_t n_generations);
+ABC_API int32_t abc_batch_runs(const abc_batch* b);
+ABC_API int32_t abc_batch_generations(const abc_batch* b);
+ABC_API int abc_batch_get_stats(abc_batch* b, int32_t run, int32_t t, abc_gen_stats* out);
+ABC_API int abc_batch_get_population(abc_batch* b, int32_t run, float* u, double* dist, double* W,
+                                     float* s, int32_t* anc, int32_t on_device);
+/* Autotuner: for each run's shape class (log2 N, T / 30, weight mode and
+ * precision, SM count) times the simulator at 64/128/256 threads per block
+ * and the weight pass at 1/2/4 times its default column chunks on the run's
+ * current population (CUDA events, median of 3), keeps the fastest, and
+ * reads/writes the choices as JSON at cache_path (NULL: no cache).  Call
+ * after stage 0; the graph is rebuilt with the chosen shapes.  Launch shapes
+ * never change results. */
+ABC_API int abc_batch_autotune(abc_batch* b, const char* cache_path);
+ABC_API int abc_batch_tuning(const abc_batch* b, int32_t run, int32_t* sim_threads,
+                             int32_t* w_mult);
+ABC_API void abc_batch_free(abc_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

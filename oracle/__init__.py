@@ -295,4 +295,47 @@ def run(m: OracleModel, c: Smc, G: int):
     return pop, stats
 
 
+# ---- surrogate MLP (8 -> 256 -> 256 -> 4, tanh-form GELU), fp64 -----------
+MLP_SHAPES = dict(W1=(256, 8), b1=(256,), W2=(256, 256), b2=(256,), W3=(4, 256), b3=(4,))
+MLP_ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def gelu(x):
+    lib().or_gelu.restype = C.c_double
+    lib().or_gelu.argtypes = [C.c_double]
+    return lib().or_gelu(float(x))
+
+
+def _mlp_args(params):
+    arrs = [np.ascontiguousarray(params[k], np.float64) for k in MLP_ORDER]
+    return arrs, [_p(a, C.c_double) for a in arrs]
+
+
+def mlp_forward(params, x):
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 8)
+    y = np.zeros((len(x), 4))
+    _, ptrs = _mlp_args(params)
+    lib().or_mlp_forward(*ptrs, _p(x, C.c_double), C.c_int64(len(x)), _p(y, C.c_double))
+    return y
+
+
+def mlp_backward(params, x, t):
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 8)
+    t = np.ascontiguousarray(t, np.float64).reshape(-1, 4)
+    grads = {k: np.zeros(MLP_SHAPES[k]) for k in MLP_ORDER}
+    _, ptrs = _mlp_args(params)
+    f = lib().or_mlp_backward
+    f.restype = C.c_double
+    loss = f(*ptrs, _p(x, C.c_double), _p(t, C.c_double), C.c_int64(len(x)),
+             *[_p(grads[k], C.c_double) for k in MLP_ORDER])
+    return loss, grads
+
+
+def adam(w, g, m, v, lr, b1, b2, eps, t):
+    """in place on float64 arrays"""
+    lib().or_adam(_p(w, C.c_double), _p(np.ascontiguousarray(g, np.float64), C.c_double),
+                  _p(m, C.c_double), _p(v, C.c_double), C.c_int64(w.size), C.c_double(lr),
+                  C.c_double(b1), C.c_double(b2), C.c_double(eps), C.c_int64(t))
+
+
 __all__ = [n for n in dir() if not n.startswith("_")] + ["math"]

@@ -794,3 +794,125 @@ OR_API int32_t or_generation(const or_model* m, const or_smc* c, int32_t t, doub
   free(q); free(prefix); free(up); free(sp); free(ap); free(att); free(fl); free(dp);
   return st->status;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Surrogate MLP (spec extension; not in the paper): 8 -> 256 -> 256 -> */
+/* 4 with tanh-form GELU, fp64 throughout, weights given as fp64 copies of   */
+/* the device's bf16 values.  Layout: W1[256][8], W2[256][256], W3[4][256]    */
+/* (row = output), biases b1[256], b2[256], b3[4].                            */
+/* ------------------------------------------------------------------------ */
+#define OR_H 256
+
+static double gelu(double x) {
+  const double c = 0.7978845608028654;  /* sqrt(2/pi) */
+  double t = tanh(c * (x + 0.044715 * x * x * x));
+  return 0.5 * x * (1.0 + t);
+}
+
+static double gelu_grad(double x) {
+  const double c = 0.7978845608028654;
+  double t = tanh(c * (x + 0.044715 * x * x * x));
+  return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * c * (1.0 + 3.0 * 0.044715 * x * x);
+}
+
+OR_API double or_gelu(double x) { return gelu(x); }
+
+/* y[n][4] = MLP(x[n][8]) */
+OR_API void or_mlp_forward(const double* W1, const double* b1, const double* W2, const double* b2,
+                           const double* W3, const double* b3, const double* x, int64_t n,
+                           double* y) {
+  double* h1 = (double*)malloc(sizeof(double) * OR_H);
+  double* h2 = (double*)malloc(sizeof(double) * OR_H);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int o = 0; o < OR_H; ++o) {
+      double z = b1[o];
+      for (int k = 0; k < 8; ++k) z += W1[o * 8 + k] * x[i * 8 + k];
+      h1[o] = gelu(z);
+    }
+    for (int o = 0; o < OR_H; ++o) {
+      double z = b2[o];
+      for (int k = 0; k < OR_H; ++k) z += W2[o * OR_H + k] * h1[k];
+      h2[o] = gelu(z);
+    }
+    for (int o = 0; o < 4; ++o) {
+      double z = b3[o];
+      for (int k = 0; k < OR_H; ++k) z += W3[o * OR_H + k] * h2[k];
+      y[i * 4 + o] = z;
+    }
+  }
+  free(h1);
+  free(h2);
+}
+
+/* loss = mean over n samples and 4 outputs of (y - t)^2; gradients of every
+ * parameter (same layouts as the parameters). Returns the loss. */
+OR_API double or_mlp_backward(const double* W1, const double* b1, const double* W2,
+                              const double* b2, const double* W3, const double* b3,
+                              const double* x, const double* t, int64_t n, double* gW1,
+                              double* gb1, double* gW2, double* gb2, double* gW3, double* gb3) {
+  memset(gW1, 0, sizeof(double) * OR_H * 8);
+  memset(gb1, 0, sizeof(double) * OR_H);
+  memset(gW2, 0, sizeof(double) * OR_H * OR_H);
+  memset(gb2, 0, sizeof(double) * OR_H);
+  memset(gW3, 0, sizeof(double) * 4 * OR_H);
+  memset(gb3, 0, sizeof(double) * 4);
+  double z1[OR_H], h1[OR_H], z2[OR_H], h2[OR_H], d2[OR_H], d1[OR_H];
+  double loss = 0.0;
+  const double scale = 2.0 / (4.0 * (double)n);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int o = 0; o < OR_H; ++o) {
+      double z = b1[o];
+      for (int k = 0; k < 8; ++k) z += W1[o * 8 + k] * x[i * 8 + k];
+      z1[o] = z;
+      h1[o] = gelu(z);
+    }
+    for (int o = 0; o < OR_H; ++o) {
+      double z = b2[o];
+      for (int k = 0; k < OR_H; ++k) z += W2[o * OR_H + k] * h1[k];
+      z2[o] = z;
+      h2[o] = gelu(z);
+    }
+    double dy[4];
+    for (int o = 0; o < 4; ++o) {
+      double z = b3[o];
+      for (int k = 0; k < OR_H; ++k) z += W3[o * OR_H + k] * h2[k];
+      double e = z - t[i * 4 + o];
+      loss += e * e;
+      dy[o] = scale * e;
+    }
+    for (int o = 0; o < 4; ++o) {
+      gb3[o] += dy[o];
+      for (int k = 0; k < OR_H; ++k) gW3[o * OR_H + k] += dy[o] * h2[k];
+    }
+    for (int k = 0; k < OR_H; ++k) {
+      double g = 0.0;
+      for (int o = 0; o < 4; ++o) g += dy[o] * W3[o * OR_H + k];
+      d2[k] = g * gelu_grad(z2[k]);
+    }
+    for (int o = 0; o < OR_H; ++o) {
+      gb2[o] += d2[o];
+      for (int k = 0; k < OR_H; ++k) gW2[o * OR_H + k] += d2[o] * h1[k];
+    }
+    for (int k = 0; k < OR_H; ++k) {
+      double g = 0.0;
+      for (int o = 0; o < OR_H; ++o) g += d2[o] * W2[o * OR_H + k];
+      d1[k] = g * gelu_grad(z1[k]);
+    }
+    for (int o = 0; o < OR_H; ++o) {
+      gb1[o] += d1[o];
+      for (int k = 0; k < 8; ++k) gW1[o * 8 + k] += d1[o] * x[i * 8 + k];
+    }
+  }
+  return loss / (4.0 * (double)n);
+}
+
+/* Adam (Kingma & Ba 2015) on one parameter array, step count t >= 1. */
+OR_API void or_adam(double* w, const double* g, double* m, double* v, int64_t n, double lr,
+                    double b1, double b2, double eps, int64_t t) {
+  const double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+  for (int64_t i = 0; i < n; ++i) {
+    m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+    v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+    w[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+  }
+}

@@ -32,6 +32,9 @@ EXPORTS = (
     "abc_normalize",
     "abc_init", "abc_generation", "abc_run", "abc_get_population", "abc_get_stats",
     "abc_generations", "abc_get_state", "abc_set_state", "abc_free", "abc_strerror",
+    "abc_batch_init", "abc_batch_generation", "abc_batch_run", "abc_batch_runs",
+    "abc_batch_generations", "abc_batch_get_stats", "abc_batch_get_population",
+    "abc_batch_autotune", "abc_batch_tuning", "abc_batch_free",
 )
 
 
@@ -102,6 +105,16 @@ _SIGS = {
     "abc_get_state": (C.c_int, [_V, _V, C.POINTER(C.c_size_t)]),
     "abc_set_state": (C.c_int, [_V, _V, _SZ]),
     "abc_free": (None, [_V]),
+    "abc_batch_init": (C.c_int, [C.POINTER(AbcConfig), _I32, _V, _V, C.POINTER(C.c_void_p)]),
+    "abc_batch_generation": (C.c_int, [_V]),
+    "abc_batch_run": (C.c_int, [_V, _I32]),
+    "abc_batch_runs": (C.c_int32, [_V]),
+    "abc_batch_generations": (C.c_int32, [_V]),
+    "abc_batch_get_stats": (C.c_int, [_V, _I32, _I32, C.POINTER(AbcGenStats)]),
+    "abc_batch_get_population": (C.c_int, [_V, _I32, _V, _V, _V, _V, _V, _I32]),
+    "abc_batch_autotune": (C.c_int, [_V, C.c_char_p]),
+    "abc_batch_tuning": (C.c_int, [_V, _I32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "abc_batch_free": (None, [_V]),
 }
 
 
@@ -311,3 +324,61 @@ def abc_set_state_ptr(ctx, host_ptr: int, nbytes: int):
 def abc_free(ctx):
     if ctx:
         lib().abc_free(ctx)
+
+
+# ---- batched runs -----------------------------------------------------------
+def abc_batch_init(cfgs, obs_list, stream=None):
+    """cfgs: list of AbcConfig; obs_list: list of host int32 [3][T_r+1] numpy
+    arrays (None for the toy model)."""
+    n = len(cfgs)
+    arr = (AbcConfig * n)(*cfgs)
+    ptrs = (C.c_void_p * n)(*[None if o is None else o.ctypes.data for o in obs_list])
+    h = C.c_void_p()
+    _check(lib().abc_batch_init(arr, n, C.cast(ptrs, C.c_void_p), _stream(stream), C.byref(h)),
+           "abc_batch_init")
+    h._keep = (arr, ptrs, obs_list)
+    return h
+
+
+def abc_batch_generation(b):
+    return _check(lib().abc_batch_generation(b), "abc_batch_generation")
+
+
+def abc_batch_run(b, n_generations):
+    return _check(lib().abc_batch_run(b, n_generations), "abc_batch_run")
+
+
+def abc_batch_runs(b):
+    return lib().abc_batch_runs(b)
+
+
+def abc_batch_generations(b):
+    return lib().abc_batch_generations(b)
+
+
+def abc_batch_get_stats(b, run, t):
+    st = AbcGenStats()
+    _check(lib().abc_batch_get_stats(b, run, t, C.byref(st)), "abc_batch_get_stats")
+    return st
+
+
+def abc_batch_get_population(b, run, u=None, dist=None, W=None, s=None, anc=None):
+    p = lambda x: None if x is None else x.ctypes.data
+    return _check(lib().abc_batch_get_population(b, run, p(u), p(dist), p(W), p(s), p(anc), 0),
+                  "abc_batch_get_population")
+
+
+def abc_batch_autotune(b, cache_path=None):
+    return _check(lib().abc_batch_autotune(b, None if cache_path is None else
+                                           cache_path.encode()), "abc_batch_autotune")
+
+
+def abc_batch_tuning(b, run):
+    th, wm = C.c_int32(0), C.c_int32(0)
+    _check(lib().abc_batch_tuning(b, run, C.byref(th), C.byref(wm)), "abc_batch_tuning")
+    return th.value, wm.value
+
+
+def abc_batch_free(b):
+    if b:
+        lib().abc_batch_free(b)

@@ -3,53 +3,41 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <map>
 #include <new>
+#include <sstream>
+#include <string>
 #include <vector>
 
+#include "batch.cuh"
 #include "common.cuh"
 
 namespace abc {
-int launch_simulate(const SimParams&, const int32_t*, const float*, int64_t, const uint32_t*,
-                    uint32_t, uint32_t, const uint8_t*, double*, int32_t*, cudaStream_t);
+// launchers not declared in batch.cuh
 int launch_prior(const SimParams&, int64_t, float*, cudaStream_t);
 int launch_synth_obs(const SimParams&, const float*, const float*, int32_t*, float*, int32_t*,
                      cudaStream_t);
 int launch_philox(const uint32_t*, uint32_t, uint32_t, int64_t, uint32_t*, cudaStream_t);
 size_t select_scratch_bytes(int64_t);
-int launch_select(const double*, int64_t, int64_t, double*, void*, size_t, cudaStream_t);
 size_t prefix_scratch_bytes(int64_t);
-int launch_resample_prefix(const double*, const double*, int64_t, const double*, int, uint32_t*,
-                           uint64_t*, void*, size_t, cudaStream_t);
 int launch_resample_prefix_noalloc(const double*, const double*, int64_t, const double*, int,
                                    uint32_t*, uint64_t*, cudaStream_t);
-int launch_propose(const SimParams&, const float*, int64_t, const uint64_t*, int, const double*,
-                   const double*, float, int, int64_t, const uint32_t*, uint32_t, int, float*,
-                   float*, int32_t*, int32_t*, uint8_t*, cudaStream_t);
 size_t accept_scratch_bytes(int64_t);
-int launch_accept(const float*, const double*, const float*, const int32_t*, const uint8_t*,
-                  int64_t, const double*, int64_t, float*, double*, float*, int32_t*, int64_t*,
-                  int64_t*, void*, size_t, cudaStream_t);
 size_t survivors_scratch_bytes(int64_t);
-int launch_survivors(const float*, const uint32_t*, int64_t, float*, float*, int*, void*,
-                     cudaStream_t);
-size_t weights_fp32_scratch_bytes(int64_t, int64_t);
-int launch_weights_fp32(const float*, const float*, int64_t, const float*, const float*,
-                        const int*, int64_t, const uint64_t*, double*, void*, size_t,
-                        cudaStream_t);
-size_t weights_tc_scratch_bytes(int64_t, int64_t);
-int launch_weights_tc(const float*, const float*, int64_t, const float*, const float*, const int*,
-                      int64_t, const uint64_t*, double*, void*, size_t, unsigned**,
-                      cudaStream_t);
+size_t weights_fp32_scratch_bytes(int64_t, int64_t, int mult = 1);
+size_t weights_tc_scratch_bytes(int64_t, int64_t, int mult = 1);
 int launch_tc_probe(const void*, const void*, float*, unsigned*, cudaStream_t);
 size_t normalize_scratch_bytes(int64_t);
-int launch_normalize(const double*, int64_t, double*, double*, void*, size_t, cudaStream_t);
 int launch_fill(double*, int64_t, double, cudaStream_t);
 }  // namespace abc
 
 namespace abc {
 static std::atomic<int64_t> g_launches{0};
 int64_t count_launch() { return g_launches.fetch_add(1, std::memory_order_relaxed) + 1; }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace abc
 
 using namespace abc;
@@ -397,9 +385,9 @@ int ctx_alloc(abc_ctx* c) {
   size_t sb = std::max({select_scratch_bytes(c->N), prefix_scratch_bytes(c->N),
                         accept_scratch_bytes(c->M), survivors_scratch_bytes(c->N),
                         normalize_scratch_bytes(c->N)});
-  if (c->cfg.weight_mode == ABC_W_IMPORTANCE)
-    sb = std::max(sb, c->cfg.weight_prec == ABC_P_BF16_TC ? weights_tc_scratch_bytes(c->N, c->N)
-                                                          : weights_fp32_scratch_bytes(c->N, c->N));
+  if (c->cfg.weight_mode == ABC_W_IMPORTANCE)  // room for the tuner's chunk multipliers (<= 4)
+    sb = std::max(sb, c->cfg.weight_prec == ABC_P_BF16_TC ? weights_tc_scratch_bytes(c->N, c->N, 4)
+                                                          : weights_fp32_scratch_bytes(c->N, c->N, 4));
   c->scratch_bytes = sb;
   char* sc = nullptr;
   if ((rc = c->alloc(&sc, sb)) != ABC_OK) return rc;
@@ -569,6 +557,11 @@ ABC_API int abc_init(const abc_config* cfg, const int32_t* obs, void* stream, ab
     delete c;
     return rc;
   }
+  if (cfg->weight_mode == ABC_W_IMPORTANCE && cfg->weight_prec == ABC_P_BF16_TC &&
+      (rc = weights_tc_prepare()) != ABC_OK) {
+    delete c;
+    return rc;
+  }
   if (c->obs) {
     if (cudaMemcpyAsync(c->obs, obs, sizeof(int32_t) * 3 * (c->T + 1), cudaMemcpyHostToDevice,
                         c->st) != cudaSuccess) {
@@ -718,6 +711,402 @@ ABC_API void abc_free(abc_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
   delete c;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ batched runs ---
+namespace {
+
+RunCtxView ctx_view(abc_ctx* c) {
+  RunCtxView v{};
+  v.p = c->p;
+  v.N = c->N;
+  v.M = c->M;
+  int64_t k = static_cast<int64_t>(std::ceil(c->cfg.survival_alpha * static_cast<double>(c->N)));
+  v.rank = std::min<int64_t>(std::max<int64_t>(k, 1), c->N);
+  v.paper_beta = c->cfg.beta_mode == ABC_BETA_PAPER;
+  v.fixed_b = c->cfg.beta_b;
+  v.beta_a = c->cfg.beta_a;
+  v.max_redraw = c->cfg.max_redraw;
+  v.weight_mode = c->cfg.weight_mode;
+  v.weight_prec = c->cfg.weight_prec;
+  v.obs = c->obs;
+  v.u_cur = c->u[0];
+  v.u_nxt = c->u[1];
+  v.s_cur = c->s[0];
+  v.s_nxt = c->s[1];
+  v.d_cur = c->d[0];
+  v.d_nxt = c->d[1];
+  v.W_cur = c->W[0];
+  v.W_nxt = c->W[1];
+  v.a_cur = c->anc[0];
+  v.a_nxt = c->anc[1];
+  v.up = c->up;
+  v.sp = c->sp;
+  v.dp = c->dp;
+  v.ap = c->ap;
+  v.att = c->att;
+  v.flag = c->flag;
+  v.q = c->q;
+  v.prefix = c->prefix;
+  v.logW = c->logW;
+  v.cu = c->cu;
+  v.cc = c->cc;
+  v.nc = c->nc;
+  v.scratch = c->scratch;
+  v.scratch_bytes = c->scratch_bytes;
+  return v;
+}
+
+}  // namespace
+
+struct abc_batch {
+  std::vector<abc_ctx*> runs;
+  std::vector<BatchRun> br;
+  std::vector<RunDev> host;
+  RunDev* dev = nullptr;
+  cudaStream_t st = nullptr;        // caller's stream
+  cudaStream_t cap = nullptr;       // capture origin
+  std::vector<cudaStream_t> rs;     // one per run during capture
+  cudaStream_t body = nullptr;
+  std::vector<cudaEvent_t> evs;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int32_t gen = 0;
+  std::vector<std::vector<abc_gen_stats>> stats;
+  ~abc_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (cudaStream_t s : rs) if (s) cudaStreamDestroy(s);
+    if (cap) cudaStreamDestroy(cap);
+    if (body) cudaStreamDestroy(body);
+    for (cudaEvent_t e : evs) if (e) cudaEventDestroy(e);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (dev) cudaFree(dev);
+    for (abc_ctx* c : runs) delete c;
+  }
+};
+
+namespace {
+
+int batch_destroy_graph(abc_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  return ABC_OK;
+}
+
+// one graph for a whole generation of every run (branches joined at the end)
+int batch_build_graph(abc_batch* b) {
+  batch_destroy_graph(b);
+  const size_t R = b->runs.size();
+  ABC_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+  int rc = ABC_OK;
+  cudaError_t e = cudaEventRecord(b->evs[0], b->cap);
+  for (size_t r = 0; r < R && rc == ABC_OK && e == cudaSuccess; ++r) {
+    e = cudaStreamWaitEvent(b->rs[r], b->evs[0], 0);
+    if (e == cudaSuccess) rc = batch_capture_run(b->br[r], b->rs[r], b->body);
+    if (rc == ABC_OK && e == cudaSuccess) e = cudaEventRecord(b->evs[1 + r], b->rs[r]);
+    if (rc == ABC_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->evs[1 + r], 0);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+  if (rc != ABC_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return ABC_E_CUDA;
+  }
+  b->graph = g;
+  ABC_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
+  return ABC_OK;
+}
+
+std::string tune_key(const abc_ctx* c, int sms) {
+  int nb = 0;
+  while ((int64_t(1) << (nb + 1)) <= c->N) ++nb;
+  char buf[96];
+  std::snprintf(buf, sizeof buf, "sm%d_n%d_t%d_w%d%d", sms, nb, c->T / 30, c->cfg.weight_mode,
+                c->cfg.weight_prec);
+  return buf;
+}
+
+// times fn() with CUDA events on st (median of 3, after one warm-up)
+template <typename F>
+int time_ms(cudaStream_t st, cudaEvent_t a, cudaEvent_t bev, F fn, float* out) {
+  float v[3];
+  int rc = fn();
+  if (rc) return rc;
+  for (int i = 0; i < 3; ++i) {
+    ABC_CUDA_TRY(cudaEventRecord(a, st));
+    if ((rc = fn())) return rc;
+    ABC_CUDA_TRY(cudaEventRecord(bev, st));
+    ABC_CUDA_TRY(cudaEventSynchronize(bev));
+    ABC_CUDA_TRY(cudaEventElapsedTime(&v[i], a, bev));
+  }
+  std::sort(v, v + 3);
+  *out = v[1];
+  return ABC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ABC_API int abc_batch_init(const abc_config* cfgs, int32_t n_runs, const int32_t* const* obs,
+                           void* stream, abc_batch** out) {
+  if (!out || !cfgs || n_runs < 1 || n_runs > 4096) return ABC_E_INVAL;
+  *out = nullptr;
+  abc_batch* b = new (std::nothrow) abc_batch();
+  if (!b) return ABC_E_NOMEM;
+  b->st = as_stream(stream);
+  int rc = ABC_OK;
+  for (int32_t r = 0; r < n_runs && rc == ABC_OK; ++r) {
+    abc_ctx* c = nullptr;
+    rc = abc_init(&cfgs[r], obs ? obs[r] : nullptr, stream, &c);
+    if (rc == ABC_OK) b->runs.push_back(c);
+  }
+  if (rc != ABC_OK) {
+    delete b;
+    return rc;
+  }
+  b->host.resize(n_runs);
+  b->br.resize(n_runs);
+  b->stats.resize(n_runs);
+  if (cudaMalloc(&b->dev, sizeof(RunDev) * n_runs) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return ABC_E_NOMEM;
+  }
+  for (int32_t r = 0; r < n_runs; ++r) {
+    std::memset(&b->host[r], 0, sizeof(RunDev));
+    b->host[r].max_batches = cfgs[r].max_batches;
+    b->br[r].v = ctx_view(b->runs[r]);
+    b->br[r].dev = b->dev + r;
+  }
+  b->rs.assign(n_runs, nullptr);
+  b->evs.assign(n_runs + 1, nullptr);
+  bool ok = cudaMemcpy(b->dev, b->host.data(), sizeof(RunDev) * n_runs, cudaMemcpyHostToDevice) ==
+                cudaSuccess &&
+            cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&b->body, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreate(&b->e0) == cudaSuccess && cudaEventCreate(&b->e1) == cudaSuccess;
+  for (int32_t r = 0; ok && r < n_runs; ++r)
+    ok = cudaStreamCreateWithFlags(&b->rs[r], cudaStreamNonBlocking) == cudaSuccess;
+  for (int32_t r = 0; ok && r <= n_runs; ++r)
+    ok = cudaEventCreateWithFlags(&b->evs[r], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    delete b;
+    return ABC_E_CUDA;
+  }
+  *out = b;
+  return ABC_OK;
+}
+
+ABC_API int abc_batch_generation(abc_batch* b) {
+  if (!b) return ABC_E_INVAL;
+  const size_t R = b->runs.size();
+  if (b->gen == 0) {
+    for (size_t r = 0; r < R; ++r) {
+      const int rc = abc_generation(b->runs[r]);
+      if (rc != ABC_OK) return rc < 0 ? rc : ABC_E_CUDA;
+      b->stats[r].push_back(b->runs[r]->stats.back());
+      b->host[r].t = 1;
+    }
+    ABC_CUDA_TRY(cudaMemcpyAsync(b->dev, b->host.data(), sizeof(RunDev) * R,
+                                 cudaMemcpyHostToDevice, b->st));
+    ABC_CUDA_TRY(cudaStreamSynchronize(b->st));
+    b->gen = 1;
+    return ABC_OK;
+  }
+  for (size_t r = 0; r < R; ++r)
+    if (b->runs[r]->cfg.beta_mode == ABC_BETA_PAPER && 2 * b->gen > 1024) return ABC_E_INVAL;
+  if (!b->exec) {
+    const int rc = batch_build_graph(b);
+    if (rc) return rc;
+  }
+  const int64_t l0 = launch_count();
+  ABC_CUDA_TRY(cudaStreamSynchronize(b->st));
+  ABC_CUDA_TRY(cudaEventRecord(b->e0, b->cap));
+  ABC_CUDA_TRY(cudaGraphLaunch(b->exec, b->cap));
+  ABC_CUDA_TRY(cudaEventRecord(b->e1, b->cap));
+  ABC_CUDA_TRY(cudaEventSynchronize(b->e1));
+  float ms = 0.f;
+  ABC_CUDA_TRY(cudaEventElapsedTime(&ms, b->e0, b->e1));
+  (void)l0;
+  std::vector<RunDev> prev = b->host;
+  ABC_CUDA_TRY(cudaMemcpy(b->host.data(), b->dev, sizeof(RunDev) * R, cudaMemcpyDeviceToHost));
+  int any_err = 0;
+  for (size_t r = 0; r < R; ++r) {
+    if (b->br[r].tc_err) {
+      unsigned h = 0;
+      ABC_CUDA_TRY(cudaMemcpy(&h, b->br[r].tc_err, sizeof h, cudaMemcpyDeviceToHost));
+      any_err |= h != 0;
+    }
+    const RunDev& d = b->host[r];
+    if (prev[r].done) continue;  // stopped earlier: nothing ran
+    abc_ctx* c = b->runs[r];
+    abc_gen_stats g{};
+    g.generation = static_cast<int32_t>(prev[r].t);
+    g.status = d.status;
+    g.eps = d.eps;
+    g.eps1 = d.eps1;
+    g.ess = d.status == ABC_OK ? d.ess : 0.0;
+    g.beta_a = c->cfg.beta_mode == ABC_BETA_PAPER
+                   ? (d.eps1 > 0.0 ? static_cast<float>(d.eps / d.eps1) : 1.0f)
+                   : c->cfg.beta_a;
+    g.beta_b = d.beta_b;
+    g.batches = d.batches;
+    g.accepted = d.accepted;
+    g.exhausted = d.exhausted;
+    g.sims = d.batches * c->M - d.exhausted;
+    g.sim_days = g.sims * static_cast<int64_t>(c->cfg.model == ABC_MODEL_SAIRD ? c->T : 1);
+    g.launches = b->br[r].fixed_launches + d.batches * b->br[r].body_launches;
+    g.ms = ms;  // the whole graph (all runs)
+    b->stats[r].push_back(g);
+    if (d.status == ABC_OK) {
+      c->gen += 1;
+      c->eps1_host = d.eps1;
+    }
+  }
+  if (any_err) return ABC_E_DEVICE;
+  b->gen += 1;
+  return ABC_OK;
+}
+
+ABC_API int abc_batch_run(abc_batch* b, int32_t n_generations) {
+  if (!b) return ABC_E_INVAL;
+  while (b->gen < n_generations) {
+    const int rc = abc_batch_generation(b);
+    if (rc != ABC_OK) return rc;
+  }
+  return ABC_OK;
+}
+
+ABC_API int32_t abc_batch_runs(const abc_batch* b) {
+  return b ? static_cast<int32_t>(b->runs.size()) : 0;
+}
+
+ABC_API int32_t abc_batch_generations(const abc_batch* b) { return b ? b->gen : 0; }
+
+ABC_API int abc_batch_get_stats(abc_batch* b, int32_t run, int32_t t, abc_gen_stats* out) {
+  if (!b || !out || run < 0 || run >= static_cast<int32_t>(b->runs.size())) return ABC_E_INVAL;
+  const auto& v = b->stats[static_cast<size_t>(run)];
+  if (t < 0 || t >= static_cast<int32_t>(v.size())) return ABC_E_INVAL;
+  *out = v[static_cast<size_t>(t)];
+  return ABC_OK;
+}
+
+ABC_API int abc_batch_get_population(abc_batch* b, int32_t run, float* u, double* dist, double* W,
+                                     float* s, int32_t* anc, int32_t on_device) {
+  if (!b || run < 0 || run >= static_cast<int32_t>(b->runs.size())) return ABC_E_INVAL;
+  return abc_get_population(b->runs[static_cast<size_t>(run)], u, dist, W, s, anc, on_device);
+}
+
+ABC_API int abc_batch_autotune(abc_batch* b, const char* cache_path) {
+  if (!b || b->gen < 1) return ABC_E_INVAL;
+  int dev = 0, sms = 0;
+  ABC_CUDA_TRY(cudaGetDevice(&dev));
+  ABC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  std::map<std::string, std::pair<int, int>> cache;
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string line;
+    while (std::getline(in, line)) {
+      char key[96];
+      int th = 0, wm = 0;
+      if (std::sscanf(line.c_str(), " \"%95[^\"]\": {\"sim_threads\": %d, \"w_mult\": %d}", key, &th,
+                      &wm) == 3)
+        cache[key] = {th, wm};
+    }
+  }
+  for (size_t r = 0; r < b->runs.size(); ++r) {
+    abc_ctx* c = b->runs[r];
+    const std::string key = tune_key(c, sms);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+      RunCtxView& v = b->br[r].v;
+      int best_th = 128, best_m = 1;
+      float best = 1e30f;
+      // simulator block size, on this run's current population
+      for (int th : {64, 128, 256}) {
+        float ms = 0.f;
+        const int rc = time_ms(b->st, b->e0, b->e1, [&] {
+          return launch_simulate(v.p, v.obs, v.u_cur, v.N, nullptr, 0xFFFF0000u, ABC_TAG_SIM,
+                                 nullptr, v.dp, nullptr, b->st, nullptr, nullptr, th);
+        }, &ms);
+        if (rc) return rc;
+        if (ms < best) {
+          best = ms;
+          best_th = th;
+        }
+      }
+      // column chunks of the weight pass, on the current population
+      if (c->cfg.weight_mode == ABC_W_IMPORTANCE) {
+        double* eps = c->scal;
+        int rc = launch_select(v.d_cur, v.N, ctx_view(c).rank, eps, v.scratch, v.scratch_bytes, b->st);
+        if (!rc) rc = launch_resample_prefix(v.d_cur, v.W_cur, v.N, eps, v.weight_mode, v.q,
+                                             v.prefix, v.scratch, v.scratch_bytes, b->st);
+        if (!rc) rc = launch_survivors(v.u_cur, v.q, v.N, v.cu, v.cc, v.nc, v.scratch, b->st);
+        if (rc) return rc;
+        best = 1e30f;
+        for (int m : {1, 2, 4}) {
+          float ms = 0.f;
+          unsigned* err = nullptr;
+          rc = time_ms(b->st, b->e0, b->e1, [&] {
+            return v.weight_prec == ABC_P_BF16_TC
+                       ? launch_weights_tc(v.u_cur, v.s_cur, v.N, v.cu, v.cc, v.nc, v.N,
+                                           v.prefix + (v.N - 1), v.logW, v.scratch,
+                                           v.scratch_bytes, &err, b->st, nullptr, m)
+                       : launch_weights_fp32(v.u_cur, v.s_cur, v.N, v.cu, v.cc, v.nc, v.N,
+                                             v.prefix + (v.N - 1), v.logW, v.scratch,
+                                             v.scratch_bytes, b->st, nullptr, m);
+          }, &ms);
+          if (rc) return rc;
+          if (ms < best) {
+            best = ms;
+            best_m = m;
+          }
+        }
+      }
+      it = cache.emplace(key, std::make_pair(best_th, best_m)).first;
+    }
+    b->br[r].sim_threads = it->second.first;
+    b->br[r].w_mult = it->second.second;
+  }
+  if (cache_path) {
+    std::ofstream out(cache_path);
+    out << "{\n";
+    size_t i = 0;
+    for (const auto& kv : cache) {
+      out << "  \"" << kv.first << "\": {\"sim_threads\": " << kv.second.first
+          << ", \"w_mult\": " << kv.second.second << "}" << (++i < cache.size() ? "," : "") << "\n";
+    }
+    out << "}\n";
+  }
+  return batch_destroy_graph(b);  // the next generation captures with the new shapes
+}
+
+ABC_API int abc_batch_tuning(const abc_batch* b, int32_t run, int32_t* sim_threads,
+                             int32_t* w_mult) {
+  if (!b || run < 0 || run >= static_cast<int32_t>(b->runs.size())) return ABC_E_INVAL;
+  if (sim_threads) *sim_threads = b->br[static_cast<size_t>(run)].sim_threads;
+  if (w_mult) *w_mult = b->br[static_cast<size_t>(run)].w_mult;
+  return ABC_OK;
+}
+
+ABC_API void abc_batch_free(abc_batch* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  delete b;
 }
 
 }  // extern "C"

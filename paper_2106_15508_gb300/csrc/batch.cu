@@ -1,0 +1,192 @@
+// batch.cu -- many independent ABC-SMC runs advanced together (north-star
+// batched form; the paper runs one problem at a time).
+//
+// Each run keeps its own buffers (an abc_ctx).  One generation of every run
+// is one CUDA graph launch: the graph holds an independent branch per run --
+//   tolerance select -> eps_1 on the first generation -> stage-prior prefix
+//   -> start kernel -> WHILE(not filled and budget left) { propose ->
+//   simulate -> accept -> condition kernel } -> finish kernel -> survivor
+//   columns -> O(N^2) weights -> normalisation -> commit (copy the new
+//   population over the current one)
+// -- so the data-dependent batch loops run on the device (conditional WHILE
+// nodes set by cudaGraphSetConditional) with no host round trip, and the
+// branches of runs of different sizes and horizons overlap on the GPU.  All
+// Philox counters (generation, batch) are read from per-run device state, so
+// one instantiated graph serves every generation.  A run whose generation
+// exhausts its batch budget stops: its later branches are skipped by a flag.
+//
+// Launch shapes (simulator block size, column chunks of the weight pass) are
+// picked per shape class by a small autotuner that times the candidates on
+// the runs' own data and caches the choice in a JSON text file.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "batch.cuh"
+
+namespace abc {
+
+__global__ void k_run_start(RunDev* r, int paper_beta, int fixed_b, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  r->off = r->done;
+  r->b = 0;
+  r->c1 = r->t << 16;
+  r->beta_b = paper_beta ? static_cast<int>(2 * r->t) : fixed_b;
+  r->filled = 0;
+  r->accepted = 0;
+  r->exhausted = 0;
+  r->batches = 0;
+  r->status = 0;
+  if (r->t == 1 && !r->done) r->eps1 = r->eps;  // eps_1 is the first generation's eps
+  cudaGraphSetConditional(h, r->done ? 0u : 1u);
+}
+
+__global__ void k_run_cond(RunDev* r, long long N, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  r->batches += 1;
+  r->b += 1;
+  r->c1 = (r->t << 16) | r->b;
+  const bool more = r->filled < N && r->b < static_cast<uint32_t>(r->max_batches);
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+__global__ void k_run_finish(RunDev* r, long long N) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (r->done) return;
+  const bool ok = r->filled >= N;
+  r->status = ok ? ABC_OK : ABC_STOP_BUDGET;
+  r->off = ok ? 0 : 1;
+  if (!ok) r->done = 1;
+}
+
+// the new population becomes the current one (skipped when the run is off)
+__global__ void k_run_commit(RunDev* r, int64_t N, float* __restrict__ u_cur,
+                             const float* __restrict__ u_nxt, double* __restrict__ d_cur,
+                             const double* __restrict__ d_nxt, double* __restrict__ W_cur,
+                             const double* __restrict__ W_nxt, float* __restrict__ s_cur,
+                             const float* __restrict__ s_nxt, int32_t* __restrict__ a_cur,
+                             const int32_t* __restrict__ a_nxt) {
+  if (r->off) return;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+#pragma unroll
+    for (int d = 0; d < 8; ++d) u_cur[d * N + i] = u_nxt[d * N + i];
+    d_cur[i] = d_nxt[i];
+    W_cur[i] = W_nxt[i];
+    s_cur[i] = s_nxt[i];
+    a_cur[i] = a_nxt[i];
+  }
+}
+
+__global__ void k_run_advance(RunDev* r) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && !r->off) r->t += 1;
+}
+
+__global__ void k_run_fill_paper(RunDev* r, double* __restrict__ W, int64_t N) {
+  if (r->off) return;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < N) W[i] = 1.0 / static_cast<double>(N);
+  if (i == 0) r->ess = static_cast<double>(N);
+}
+
+int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
+  const int64_t l0 = launch_count();
+  int64_t l_body0 = 0, l_body1 = 0;
+  RunCtxView& v = br.v;
+  RunDev* r = br.dev;
+  int rc;
+  // tolerance eps_t (Eq. 8) into the run state
+  if ((rc = launch_select(v.d_cur, v.N, v.rank, &r->eps, v.scratch, v.scratch_bytes, st))) return rc;
+  if ((rc = launch_resample_prefix(v.d_cur, v.W_cur, v.N, &r->eps, v.weight_mode, v.q, v.prefix,
+                                   v.scratch, v.scratch_bytes, st)))
+    return rc;
+  // the start kernel sets the loop condition, so the WHILE node's handle is
+  // created on the graph being captured before the node itself is added
+  cudaGraphConditionalHandle h;
+  cudaGraph_t body = nullptr;
+  {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    ABC_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) return ABC_E_CUDA;
+    ABC_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+  }
+  k_run_start<<<1, 32, 0, st>>>(r, v.paper_beta, v.fixed_b, h);
+  ABC_LAUNCH_CHECK();
+  {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t ndeps = 0;
+    ABC_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &edges, &ndeps));
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    ABC_CUDA_TRY(cudaGraphAddNode(&node, g, deps, edges, ndeps, &np));
+    body = np.conditional.phGraph_out[0];
+    ABC_CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1,
+                                                     cudaStreamSetCaptureDependencies));
+  }
+  // loop body: one batch of M proposals
+  ABC_CUDA_TRY(cudaStreamBeginCaptureToGraph(body_st, body, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeRelaxed));
+  l_body0 = launch_count();
+  rc = launch_propose(v.p, v.u_cur, v.N, v.prefix, v.paper_beta, &r->eps, &r->eps1, v.beta_a,
+                      std::max(1, v.fixed_b), v.M, nullptr, 0u, v.max_redraw, v.up, v.sp, v.ap,
+                      v.att, v.flag, body_st, &r->c1, &r->beta_b, &r->off);
+  if (!rc)
+    rc = launch_simulate(v.p, v.obs, v.up, v.M, nullptr, 0u, ABC_TAG_SIM, v.flag, v.dp, nullptr,
+                         body_st, &r->c1, &r->off, br.sim_threads);
+  if (!rc)
+    rc = launch_accept(v.up, v.dp, v.sp, v.ap, v.flag, v.M, &r->eps, v.N, v.u_nxt, v.d_nxt,
+                       v.s_nxt, v.a_nxt, reinterpret_cast<int64_t*>(&r->filled),
+                       reinterpret_cast<int64_t*>(&r->accepted), v.scratch, v.scratch_bytes,
+                       body_st);
+  if (!rc) {
+    k_run_cond<<<1, 32, 0, body_st>>>(r, v.N, h);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = ABC_E_CUDA;
+  }
+  l_body1 = launch_count();
+  cudaGraph_t done_body = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(body_st, &done_body);
+  if (rc) return rc;
+  if (ec != cudaSuccess) return ABC_E_CUDA;
+  // after the loop
+  k_run_finish<<<1, 32, 0, st>>>(r, v.N);
+  ABC_LAUNCH_CHECK();
+  if (v.weight_mode == ABC_W_IMPORTANCE) {
+    if ((rc = launch_survivors(v.u_cur, v.q, v.N, v.cu, v.cc, v.nc, v.scratch, st))) return rc;
+    if (v.weight_prec == ABC_P_BF16_TC)
+      rc = launch_weights_tc(v.u_nxt, v.s_nxt, v.N, v.cu, v.cc, v.nc, v.N, v.prefix + (v.N - 1),
+                             v.logW, v.scratch, v.scratch_bytes, &br.tc_err, st, &r->off,
+                             br.w_mult);
+    else
+      rc = launch_weights_fp32(v.u_nxt, v.s_nxt, v.N, v.cu, v.cc, v.nc, v.N, v.prefix + (v.N - 1),
+                               v.logW, v.scratch, v.scratch_bytes, st, &r->off, br.w_mult);
+    if (rc) return rc;
+    if ((rc = launch_normalize(v.logW, v.N, v.W_nxt, &r->ess, v.scratch, v.scratch_bytes, st)))
+      return rc;
+  } else {
+    k_run_fill_paper<<<static_cast<unsigned>(ceil_div(v.N, 256)), 256, 0, st>>>(r, v.W_nxt, v.N);
+    ABC_LAUNCH_CHECK();
+  }
+  k_run_commit<<<static_cast<unsigned>(std::min<int64_t>(ceil_div(v.N, 256), 1024)), 256, 0, st>>>(
+      r, v.N, v.u_cur, v.u_nxt, v.d_cur, v.d_nxt, v.W_cur, v.W_nxt, v.s_cur, v.s_nxt, v.a_cur,
+      v.a_nxt);
+  ABC_LAUNCH_CHECK();
+  k_run_advance<<<1, 32, 0, st>>>(r);
+  ABC_LAUNCH_CHECK();
+  br.body_launches = l_body1 - l_body0;
+  br.fixed_launches = launch_count() - l0 - br.body_launches;
+  return ABC_OK;
+}
+
+}  // namespace abc

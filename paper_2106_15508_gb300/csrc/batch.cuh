@@ -1,0 +1,82 @@
+// batch.cuh -- internal types of the batched (many-run) graph path.
+#pragma once
+#include "common.cuh"
+
+namespace abc {
+
+// Per-run state read and written by the graph's kernels.  accepted and
+// exhausted must stay adjacent: the acceptance kernel takes them as a pair.
+struct RunDev {
+  uint32_t t;           // generation being run
+  uint32_t b;           // batch index inside the generation
+  uint32_t c1;          // Philox counter word (t << 16) | b
+  int32_t beta_b;       // Beta shape b of this generation
+  int32_t done;         // the run has stopped (batch budget)
+  int32_t off;          // skip the rest of this generation
+  int32_t status;       // of the last generation
+  int32_t max_batches;
+  long long filled;
+  long long accepted;
+  long long exhausted;
+  long long batches;
+  double eps, eps1, ess;
+};
+
+// Device buffers and settings of one run (borrowed from its context).
+struct RunCtxView {
+  SimParams p;
+  int64_t N, M, rank;
+  int paper_beta, fixed_b, max_redraw, weight_mode, weight_prec;
+  float beta_a;
+  const int32_t* obs;
+  float *u_cur, *u_nxt, *s_cur, *s_nxt, *up, *sp, *cu, *cc;
+  double *d_cur, *d_nxt, *W_cur, *W_nxt, *dp, *logW;
+  int32_t *a_cur, *a_nxt, *ap, *att;
+  uint8_t* flag;
+  uint32_t* q;
+  uint64_t* prefix;
+  int* nc;
+  void* scratch;
+  size_t scratch_bytes;
+};
+
+struct BatchRun {
+  RunCtxView v;
+  RunDev* dev = nullptr;      // this run's slot in the device state array
+  int sim_threads = 128;      // autotuned simulator block size
+  int w_mult = 1;             // autotuned column-chunk multiplier of the weight pass
+  unsigned* tc_err = nullptr; // error word of the tensor-core pass (when used)
+  int64_t fixed_launches = 0; // kernels per generation outside the batch loop
+  int64_t body_launches = 0;  // kernels per batch
+};
+
+int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st);
+
+// launchers shared with the single-run context
+int launch_simulate(const SimParams&, const int32_t*, const float*, int64_t, const uint32_t*,
+                    uint32_t, uint32_t, const uint8_t*, double*, int32_t*, cudaStream_t,
+                    const uint32_t* c1_dev = nullptr, const int* off_dev = nullptr,
+                    int threads = 128);
+int launch_select(const double*, int64_t, int64_t, double*, void*, size_t, cudaStream_t);
+int launch_resample_prefix(const double*, const double*, int64_t, const double*, int, uint32_t*,
+                           uint64_t*, void*, size_t, cudaStream_t);
+int launch_propose(const SimParams&, const float*, int64_t, const uint64_t*, int, const double*,
+                   const double*, float, int, int64_t, const uint32_t*, uint32_t, int, float*,
+                   float*, int32_t*, int32_t*, uint8_t*, cudaStream_t,
+                   const uint32_t* c1_dev = nullptr, const int* beta_b_dev = nullptr,
+                   const int* off_dev = nullptr);
+int launch_accept(const float*, const double*, const float*, const int32_t*, const uint8_t*,
+                  int64_t, const double*, int64_t, float*, double*, float*, int32_t*, int64_t*,
+                  int64_t*, void*, size_t, cudaStream_t);
+int launch_survivors(const float*, const uint32_t*, int64_t, float*, float*, int*, void*,
+                     cudaStream_t);
+int launch_weights_fp32(const float*, const float*, int64_t, const float*, const float*,
+                        const int*, int64_t, const uint64_t*, double*, void*, size_t,
+                        cudaStream_t, const int* off_dev = nullptr, int mult = 1);
+int launch_weights_tc(const float*, const float*, int64_t, const float*, const float*, const int*,
+                      int64_t, const uint64_t*, double*, void*, size_t, unsigned**,
+                      cudaStream_t, const int* off_dev = nullptr, int mult = 1);
+int launch_normalize(const double*, int64_t, double*, double*, void*, size_t, cudaStream_t);
+int weights_tc_prepare();
+
+}  // namespace abc

@@ -46,6 +46,7 @@ inline SimParams make_params(const abc_config& c) {
 // Every kernel launch is followed by ABC_LAUNCH_CHECK(), which also counts
 // the launch (reported per generation).
 int64_t count_launch();
+int64_t launch_count();  // launches counted so far (no increment)
 #define ABC_LAUNCH_CHECK()      \
   do {                          \
     ::abc::count_launch();      \

@@ -256,9 +256,13 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
                           int64_t slots, const uint32_t* __restrict__ c0_idx, uint32_t c1,
                           int max_redraw, float* __restrict__ u_out, float* __restrict__ s_out,
                           int32_t* __restrict__ anc_out, int32_t* __restrict__ att_out,
-                          uint8_t* __restrict__ flag_out) {
+                          uint8_t* __restrict__ flag_out, const uint32_t* __restrict__ c1_dev,
+                          const int* __restrict__ beta_b_dev, const int* __restrict__ off_dev) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= slots) return;
+  if (off_dev && *off_dev) return;          // run finished
+  if (c1_dev) c1 = *c1_dev;                 // set on the device (graph launches)
+  if (beta_b_dev) beta_b = *beta_b_dev;
   const uint32_t j = c0_idx ? c0_idx[i] : static_cast<uint32_t>(i);
   const unsigned long long total = prefix[n - 1];
   float a_t = beta_a;
@@ -324,13 +328,14 @@ int launch_propose(const SimParams& p, const float* u, int64_t n, const uint64_t
                    int paper_beta, const double* eps, const double* eps1, float beta_a,
                    int beta_b, int64_t slots, const uint32_t* c0_idx, uint32_t c1, int max_redraw,
                    float* u_out, float* s_out, int32_t* anc_out, int32_t* att_out,
-                   uint8_t* flag_out, cudaStream_t st) {
+                   uint8_t* flag_out, cudaStream_t st, const uint32_t* c1_dev,
+                   const int* beta_b_dev, const int* off_dev) {
   if (n <= 0 || slots < 0 || beta_b < 1 || beta_b > 1024 || max_redraw < 1) return ABC_E_INVAL;
   if (paper_beta && (!eps || !eps1)) return ABC_E_INVAL;
   if (slots == 0) return ABC_OK;
   k_propose<<<static_cast<unsigned>(ceil_div(slots, 128)), 128, 0, st>>>(
       p, u, n, prefix, paper_beta, eps, eps1, beta_a, beta_b, slots, c0_idx, c1, max_redraw,
-      u_out, s_out, anc_out, att_out, flag_out);
+      u_out, s_out, anc_out, att_out, flag_out, c1_dev, beta_b_dev, off_dev);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

@@ -145,8 +145,11 @@ __global__ void k_simulate(SimParams p, const int32_t* __restrict__ obs,
                            const float* __restrict__ u, int64_t n,
                            const uint32_t* __restrict__ c0_idx, uint32_t c1, uint32_t tag,
                            const uint8_t* __restrict__ skip, double* __restrict__ dist,
-                           int32_t* __restrict__ traj) {
+                           int32_t* __restrict__ traj, const uint32_t* __restrict__ c1_dev,
+                           const int* __restrict__ off_dev) {
   extern __shared__ int32_t s_obs[];
+  if (off_dev && *off_dev) return;  // run finished: nothing to simulate
+  if (c1_dev) c1 = *c1_dev;         // counter word set on the device (graph launches)
   const int nobs = (p.model == ABC_MODEL_SAIRD && obs) ? 3 * (p.T + 1) : 0;
   for (int i = threadIdx.x; i < nobs; i += blockDim.x) s_obs[i] = obs[i];
   __syncthreads();
@@ -218,12 +221,13 @@ __global__ void k_philox(const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t
 // ---- host launchers (called by the C ABI layer) --------------------------
 int launch_simulate(const SimParams& p, const int32_t* obs, const float* u, int64_t n,
                     const uint32_t* c0_idx, uint32_t c1, uint32_t tag, const uint8_t* skip,
-                    double* dist, int32_t* traj, cudaStream_t st) {
+                    double* dist, int32_t* traj, cudaStream_t st, const uint32_t* c1_dev,
+                    const int* off_dev, int threads) {
   if (n <= 0) return ABC_OK;
-  const int threads = 128;
+  if (threads != 64 && threads != 128 && threads != 256 && threads != 512) return ABC_E_INVAL;
   const size_t smem = (p.model == ABC_MODEL_SAIRD && obs) ? sizeof(int32_t) * 3 * (p.T + 1) : 0;
   k_simulate<<<static_cast<unsigned>(ceil_div(n, threads)), threads, smem, st>>>(
-      p, obs, u, n, c0_idx, c1, tag, skip, dist, traj);
+      p, obs, u, n, c0_idx, c1, tag, skip, dist, traj, c1_dev, off_dev);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

@@ -27,9 +27,10 @@ __global__ void __launch_bounds__(kWThreads)
 k_weights_fp32(const float* __restrict__ up, const float* __restrict__ s, int64_t rows,
                const float* __restrict__ cu, const float* __restrict__ cc,
                const int* __restrict__ nc_p, int64_t ncap, int64_t chunk_cols,
-               float2* __restrict__ part) {
+               float2* __restrict__ part, const int* __restrict__ off_dev) {
   __shared__ float su[8][kWTile];
   __shared__ float sc[kWTile];
+  if (off_dev && *off_dev) return;  // run finished or its generation stopped
   const int64_t nc = *nc_p;
   const int64_t c_begin = static_cast<int64_t>(blockIdx.y) * chunk_cols;
   const int64_t c_end = nc < c_begin + chunk_cols ? nc : c_begin + chunk_cols;
@@ -104,9 +105,10 @@ k_weights_fp32(const float* __restrict__ up, const float* __restrict__ s, int64_
 
 __global__ void k_weights_combine(const float2* __restrict__ part, int nchunks,
                                   const float* __restrict__ s, int64_t rows,
-                                  const uint64_t* __restrict__ total_p, double* __restrict__ logW) {
+                                  const uint64_t* __restrict__ total_p, double* __restrict__ logW,
+                                  const int* __restrict__ off_dev) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= rows) return;
+  if (j >= rows || (off_dev && *off_dev)) return;
   const double sj = static_cast<double>(fmaxf(s[j], kSMin));
   double M = -INFINITY;
   for (int c = 0; c < nchunks; ++c) M = fmax(M, static_cast<double>(part[static_cast<int64_t>(c) * rows + j].x));
@@ -120,32 +122,34 @@ __global__ void k_weights_combine(const float2* __restrict__ part, int nchunks,
   logW[j] = 4.0 * log(6.283185307179586 * sj) - lse;
 }
 
-static int weight_chunks(int64_t rows, int64_t ncap) {
+// column chunks: about 16 CTAs per SM in total, times a tuning multiplier
+static int weight_chunks(int64_t rows, int64_t ncap, int mult) {
   const int64_t gx = ceil_div(std::max<int64_t>(rows, 1), kWThreads * kWRows);
-  const int64_t want = std::max<int64_t>(1, 2432 / gx);  // about 16 CTAs per SM in total
+  const int64_t want = std::max<int64_t>(1, 2432 / gx) * std::max(1, mult);
   const int64_t maxc = std::max<int64_t>(1, ceil_div(ncap, kWTile));
   return static_cast<int>(std::min<int64_t>(want, maxc));
 }
 
-size_t weights_fp32_scratch_bytes(int64_t rows, int64_t ncap) {
-  return align256(sizeof(float2) * static_cast<size_t>(weight_chunks(rows, ncap)) * rows);
+size_t weights_fp32_scratch_bytes(int64_t rows, int64_t ncap, int mult) {
+  return align256(sizeof(float2) * static_cast<size_t>(weight_chunks(rows, ncap, mult)) * rows);
 }
 
 // cu/cc/nc_dev: compacted survivor columns (capacity ncap); total_p: device u64
 int launch_weights_fp32(const float* up, const float* s, int64_t rows, const float* cu,
                         const float* cc, const int* nc_dev, int64_t ncap,
                         const uint64_t* total_p, double* logW, void* scratch, size_t bytes,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int* off_dev, int mult) {
   if (rows <= 0) return ABC_OK;
-  if (bytes < weights_fp32_scratch_bytes(rows, ncap)) return ABC_E_SCRATCH;
-  const int nch = weight_chunks(rows, ncap);
+  if (bytes < weights_fp32_scratch_bytes(rows, ncap, mult)) return ABC_E_SCRATCH;
+  const int nch = weight_chunks(rows, ncap, mult);
   const int64_t chunk_cols = ceil_div(ceil_div(ncap, nch), kWTile) * kWTile;
   float2* part = static_cast<float2*>(scratch);
   dim3 grid(static_cast<unsigned>(ceil_div(rows, kWThreads * kWRows)), static_cast<unsigned>(nch));
-  k_weights_fp32<<<grid, kWThreads, 0, st>>>(up, s, rows, cu, cc, nc_dev, ncap, chunk_cols, part);
+  k_weights_fp32<<<grid, kWThreads, 0, st>>>(up, s, rows, cu, cc, nc_dev, ncap, chunk_cols, part,
+                                             off_dev);
   ABC_LAUNCH_CHECK();
   k_weights_combine<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(part, nch, s, rows,
-                                                                                total_p, logW);
+                                                                                total_p, logW, off_dev);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

@@ -327,8 +327,9 @@ __device__ __forceinline__ TcSmem tc_carve(uint8_t* raw) {
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
              const int* __restrict__ nc_p, int64_t rows, int tiles_per_chunk,
-             float2* __restrict__ part, unsigned* err) {
+             float2* __restrict__ part, unsigned* err, const int* __restrict__ off_dev) {
   extern __shared__ uint8_t tc_smem_raw[];
+  if (off_dev && *off_dev) return;  // run finished or its generation stopped (block-uniform)
   const TcSmem sm = tc_carve(tc_smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nc = *nc_p;
@@ -458,9 +459,9 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
 __global__ void k_weights_tc_combine(const float2* __restrict__ part, int nchunks,
                                      const float* __restrict__ s, const double* __restrict__ rowc,
                                      int64_t rows, const uint64_t* __restrict__ total_p,
-                                     double* __restrict__ logW) {
+                                     double* __restrict__ logW, const int* __restrict__ off_dev) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= rows) return;
+  if (j >= rows || (off_dev && *off_dev)) return;
   const double sj = static_cast<double>(fmaxf(s[j], kSMinTc));
   double M = -INFINITY;
   for (int c = 0; c < nchunks; ++c)
@@ -529,10 +530,11 @@ k_tc_probe(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
 }
 
 // ---- host side -----------------------------------------------------------------
-static int tc_chunks(int64_t rows, int64_t ncap) {
+// column chunks: about two CTAs per SM in total, times a tuning multiplier
+static int tc_chunks(int64_t rows, int64_t ncap, int mult) {
   const int64_t gx = ceil_div(std::max<int64_t>(rows, 1), kTcM);
   const int64_t tiles = std::max<int64_t>(1, ceil_div(ncap, kTcN));
-  const int64_t want = std::max<int64_t>(1, ceil_div(2 * 152, gx));
+  const int64_t want = std::max<int64_t>(1, ceil_div(2 * 152, gx)) * std::max(1, mult);
   return static_cast<int>(std::min<int64_t>(want, tiles));
 }
 
@@ -540,7 +542,7 @@ struct TcLayout {
   size_t apk, bpk, rowc, part, err, total;
 };
 
-static TcLayout tc_layout(int64_t rows, int64_t ncap) {
+static TcLayout tc_layout(int64_t rows, int64_t ncap, int mult) {
   TcLayout l{};
   const int64_t rpad = ceil_div(std::max<int64_t>(rows, 1), kTcM) * kTcM;
   const int64_t cpad = ceil_div(std::max<int64_t>(ncap, 1), kTcN) * kTcN;
@@ -552,14 +554,22 @@ static TcLayout tc_layout(int64_t rows, int64_t ncap) {
   l.rowc = o;
   o += align256(sizeof(double) * static_cast<size_t>(rows));
   l.part = o;
-  o += align256(sizeof(float2) * static_cast<size_t>(tc_chunks(rows, ncap)) * rows);
+  o += align256(sizeof(float2) * static_cast<size_t>(tc_chunks(rows, ncap, mult)) * rows);
   l.err = o;
   o += align256(sizeof(unsigned));
   l.total = o;
   return l;
 }
 
-size_t weights_tc_scratch_bytes(int64_t rows, int64_t ncap) { return tc_layout(rows, ncap).total; }
+int weights_tc_prepare() {
+  ABC_CUDA_TRY(cudaFuncSetAttribute(k_weights_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(kTcSmem)));
+  return ABC_OK;
+}
+
+size_t weights_tc_scratch_bytes(int64_t rows, int64_t ncap, int mult) {
+  return tc_layout(rows, ncap, mult).total;
+}
 
 // cu/cc/nc_dev: compacted survivor columns (capacity ncap).  The error word
 // is written into the scratch area; err_host (nullable) receives it when
@@ -567,12 +577,18 @@ size_t weights_tc_scratch_bytes(int64_t rows, int64_t ncap) { return tc_layout(r
 int launch_weights_tc(const float* up, const float* s, int64_t rows, const float* cu,
                       const float* cc, const int* nc_dev, int64_t ncap, const uint64_t* total_p,
                       double* logW, void* scratch, size_t bytes, unsigned** err_dev,
-                      cudaStream_t st) {
+                      cudaStream_t st, const int* off_dev, int mult) {
   if (rows <= 0) return ABC_OK;
-  const TcLayout l = tc_layout(rows, ncap);
+  const TcLayout l = tc_layout(rows, ncap, mult);
   if (bytes < l.total) return ABC_E_SCRATCH;
-  ABC_CUDA_TRY(cudaFuncSetAttribute(k_weights_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(kTcSmem)));
+  // the kernel's shared-memory opt-in is a function attribute: set it unless
+  // the stream is being captured (contexts set it when they are created)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  ABC_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+  if (cs == cudaStreamCaptureStatusNone) {
+    const int rc = weights_tc_prepare();
+    if (rc) return rc;
+  }
   char* b = static_cast<char*>(scratch);
   auto* Apk = reinterpret_cast<__nv_bfloat16*>(b + l.apk);
   auto* Bpk = reinterpret_cast<__nv_bfloat16*>(b + l.bpk);
@@ -589,16 +605,16 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   k_tc_pack_cols<<<static_cast<unsigned>(ceil_div(cpad, 128)), 128, 0, st>>>(cu, cc, nc_dev, ncap,
                                                                             cpad, Bpk);
   ABC_LAUNCH_CHECK();
-  const int nch = tc_chunks(rows, ncap);
+  const int nch = tc_chunks(rows, ncap, mult);
   const int tiles = static_cast<int>(ceil_div(std::max<int64_t>(ncap, 1), kTcN));
   const int per = static_cast<int>(ceil_div(tiles, nch));
   dim3 grid(static_cast<unsigned>(rpad / kTcM), static_cast<unsigned>(nch));
   k_weights_tc<<<grid, kTcThreads, kTcSmem, st>>>(reinterpret_cast<const uint8_t*>(Apk),
                                                   reinterpret_cast<const uint8_t*>(Bpk), nc_dev,
-                                                  rows, per, part, err);
+                                                  rows, per, part, err, off_dev);
   ABC_LAUNCH_CHECK();
   k_weights_tc_combine<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(
-      part, nch, s, rowc, rows, total_p, logW);
+      part, nch, s, rowc, rows, total_p, logW, off_dev);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

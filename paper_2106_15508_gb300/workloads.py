@@ -55,5 +55,21 @@ LARGE = Workload("saird_n1048576_t120_p1e7", N=1 << 20, T=120, P=10_000_000, G=2
 
 WORKLOADS = {w.name: w for w in (SMALL, LARGE)}
 
-__all__ = ["Workload", "SMALL", "LARGE", "WORKLOADS", "OBS_BOX_LO", "OBS_BOX_HI",
+
+def batched_runs(n_runs=64, seed=0, weight_prec=ABC_P_FP32):
+    """Batched workload: n_runs independent runs with seeds 1..n_runs,
+    N_r = 2^(14 + floor(5 U)) particles (16K-256K), T_r ~ U{60..180} days,
+    P_r = 10^(6 + 2 U) (1e6-1e8), paper Beta schedule, importance weights."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(n_runs):
+        N = 1 << (14 + int(np.floor(5 * rng.random())))
+        T = int(rng.integers(60, 181))
+        P = int(round(10 ** (6 + 2 * rng.random())))
+        out.append(Workload("batched_run%d" % r, N=N, T=T, P=P, G=8, seed=r + 1,
+                            weight_prec=weight_prec))
+    return out
+
+__all__ = ["Workload", "SMALL", "LARGE", "WORKLOADS", "batched_runs", "OBS_BOX_LO", "OBS_BOX_HI",
            "SAIRD_THETA_MAX", "initial_active", "ABC_W_PAPER", "ABC_P_BF16_TC"]

@@ -1,0 +1,145 @@
+"""Batched runs (abc_batch_*): many independent runs, one CUDA graph launch
+per generation with device-side batch loops.
+
+* Paper weights: every run of a heterogeneous batch (different particle
+  counts, horizons, populations, seeds and Beta settings) reproduces the
+  oracle's populations and statistics bit for bit, generation by generation.
+* Importance weights: each run equals a separate single-run context bit for
+  bit (same kernels, same counters).
+* A run that exhausts its batch budget stops alone; autotuning changes launch
+  shapes only, never results, and writes its cache.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2106_15508_gb300 as G
+from paper_2106_15508_gb300 import build as B
+
+from helpers import get_population, oracle_model, oracle_obs, oracle_smc, saird_config
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    G.lib()
+
+
+def _cfgs(weight_mode, weight_prec=G.ABC_P_FP32):
+    specs = [(2048, 40, 100_000, 1, G.ABC_BETA_FIXED), (4096, 25, 1_000_000, 2, G.ABC_BETA_PAPER),
+             (1024, 60, 50_000, 3, G.ABC_BETA_PAPER), (3000, 33, 2_000_000, 4, G.ABC_BETA_FIXED)]
+    return [saird_config(N, T, P, seed=seed, beta_mode=bm, beta_a=2.0, beta_b=5,
+                         weight_mode=weight_mode, weight_prec=weight_prec)
+            for N, T, P, seed, bm in specs]
+
+
+def _batch_pop(b, r, N):
+    u = np.zeros((8, N), np.float32)
+    d = np.zeros(N)
+    W = np.zeros(N)
+    s = np.zeros(N, np.float32)
+    a = np.zeros(N, np.int32)
+    G.abc_batch_get_population(b, r, u, d, W, s, a)
+    return dict(u=u, d=d, W=W, s=s, anc=a)
+
+
+def test_batch_paper_weights_match_oracle():
+    cfgs = _cfgs(G.ABC_W_PAPER)
+    obs = [oracle_obs(c)[0] for c in cfgs]
+    b = G.abc_batch_init(cfgs, obs)
+    try:
+        models = [oracle_model(c, o) for c, o in zip(cfgs, obs)]
+        smcs = [oracle_smc(c) for c in cfgs]
+        pops = [O.generation0(m, c) for m, c in zip(models, smcs)]
+        eps1 = [0.0] * len(cfgs)
+        G.abc_batch_generation(b)
+        for t in range(1, 5):
+            G.abc_batch_generation(b)
+            for r, cfg in enumerate(cfgs):
+                new, st = O.generation(models[r], smcs[r], t, eps1[r], pops[r])
+                assert st.status == 0
+                gp = _batch_pop(b, r, cfg.n_particles)
+                for k, ok in (("u", new.u), ("d", new.d), ("s", new.s), ("anc", new.anc)):
+                    assert np.array_equal(gp[k].view(np.uint8),
+                                          np.ascontiguousarray(ok).view(np.uint8)), (t, r, k)
+                g = G.abc_batch_get_stats(b, r, t)
+                assert g.eps == st.eps and g.batches == st.batches
+                assert g.accepted == st.accepted_total and g.beta_b == st.beta_b
+                eps1[r], pops[r] = st.eps1, new
+    finally:
+        G.abc_batch_free(b)
+
+
+@pytest.mark.parametrize("prec", [G.ABC_P_FP32, G.ABC_P_BF16_TC])
+def test_batch_importance_weights_equal_single_contexts(prec):
+    cfgs = _cfgs(G.ABC_W_IMPORTANCE, prec)
+    obs = [oracle_obs(c)[0] for c in cfgs]
+    b = G.abc_batch_init(cfgs, obs)
+    singles = [G.abc_init(c, o) for c, o in zip(cfgs, obs)]
+    try:
+        G.abc_batch_run(b, 5)
+        for ctx in singles:
+            G.abc_run(ctx, 5)
+        for r, cfg in enumerate(cfgs):
+            gb = _batch_pop(b, r, cfg.n_particles)
+            gs = get_population(singles[r], cfg.n_particles)
+            for k in gb:
+                assert np.array_equal(gb[k].view(np.uint8), gs[k].view(np.uint8)), (r, k)
+            for t in range(1, 5):
+                x, y = G.abc_batch_get_stats(b, r, t), G.abc_get_stats(singles[r], t)
+                assert x.eps == y.eps and x.ess == y.ess and x.batches == y.batches
+    finally:
+        G.abc_batch_free(b)
+        for ctx in singles:
+            G.abc_free(ctx)
+
+
+def test_batch_budget_stop_is_per_run():
+    cfgs = _cfgs(G.ABC_W_PAPER)
+    cfgs[1].batch_size = 512      # M < N: one batch can never fill N = 4096
+    cfgs[1].max_batches = 1
+    obs = [oracle_obs(c)[0] for c in cfgs]
+    b = G.abc_batch_init(cfgs, obs)
+    try:
+        G.abc_batch_run(b, 4)
+        assert G.abc_batch_get_stats(b, 1, 1).status == G.ABC_STOP_BUDGET
+        with pytest.raises(G.AbcError):
+            G.abc_batch_get_stats(b, 1, 2)    # the stopped run records nothing more
+        for r in (0, 2, 3):
+            assert G.abc_batch_get_stats(b, r, 3).status == 0
+    finally:
+        G.abc_batch_free(b)
+
+
+def test_autotune_keeps_results_and_writes_cache(tmp_path):
+    cfgs = _cfgs(G.ABC_W_IMPORTANCE)
+    obs = [oracle_obs(c)[0] for c in cfgs]
+    a = G.abc_batch_init(cfgs, obs)
+    b = G.abc_batch_init(cfgs, obs)
+    cache = str(tmp_path / "tune.json")
+    try:
+        G.abc_batch_generation(a)
+        G.abc_batch_generation(b)
+        G.abc_batch_autotune(b, cache)
+        for r in range(len(cfgs)):
+            th, wm = G.abc_batch_tuning(b, r)
+            assert th in (64, 128, 256) and wm in (1, 2, 4)
+        tuned = json.load(open(cache))
+        assert len(tuned) >= 1
+        G.abc_batch_run(a, 4)
+        G.abc_batch_run(b, 4)
+        for r, cfg in enumerate(cfgs):
+            pa, pb = _batch_pop(a, r, cfg.n_particles), _batch_pop(b, r, cfg.n_particles)
+            for k in pa:
+                assert np.array_equal(pa[k].view(np.uint8), pb[k].view(np.uint8)), (r, k)
+    finally:
+        G.abc_batch_free(a)
+        G.abc_batch_free(b)
