@@ -124,6 +124,9 @@ def run_gpu(args):
         torch.distributed.barrier()
     G.lib()
     w = WL.LARGE
+    if args.particles:  # a smaller case of the same workload (profiling)
+        import dataclasses
+        w = dataclasses.replace(w, N=args.particles, name="saird_n%d_t120_p1e7" % args.particles)
     # independent runs per rank (weak scaling, no data-path collective)
     cfg = w.config(seed=w.seed + rank, weight_prec=args.prec)
     obs, theta_star = synthetic_obs(G, WL, cfg, torch)
@@ -218,7 +221,8 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "particles": N, "days": w.T, "population": w.P,
-                   "weights": "importance O(N^2), " + ("bf16 tcgen05" if args.prec else "fp32"),
+                   "weights": "importance O(N^2), " + ("bf16 tcgen05 (rows with log W error bound <= 0.0166) + fp32"
+                                                      if args.prec else "fp32"),
                    "beta_schedule": "paper (eps_t/eps_1, 2t)", "generations_timed":
                    [g_first + k for k in range(args.steps)],
                    "l2": "flushed between steps (256 MB write)",
@@ -424,9 +428,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--prec", type=int, default=0, help="0 fp32 CUDA cores, 1 bf16 tcgen05")
+    ap.add_argument("--prec", type=int, default=1,
+                    help="1: tcgen05 (bf16 x3 split, fp32 accumulation; FP32 path below s=1e-3); "
+                         "0: FP32 CUDA cores only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="single", choices=["single", "batched"])
+    ap.add_argument("--particles", type=int, default=0,
+                    help="override the particle count (smaller cases for profiling)")
     ap.add_argument("--runs", type=int, default=64)
     ap.add_argument("--autotune", action="store_true")
     args = ap.parse_args()

@@ -75,6 +75,8 @@ extern "C" {
 #define ABC_TAG_BETA 2
 #define ABC_TAG_WALK 3
 #define ABC_TAG_SIM 4
+#define ABC_TAG_SCREEN 5
+#define ABC_TAG_AUDIT 6
 #define ABC_TAG_OBS 7
 #define ABC_TAG_OBS_THETA 8
 
@@ -101,6 +103,25 @@ typedef struct {
   int32_t weight_prec;      /* ABC_P_*                                                  */
   int32_t max_batches;      /* per-generation batch budget (<= 65535)                   */
   int32_t max_redraw;       /* proposal redraws when u' leaves [0,1]^8                   */
+  /* Surrogate pre-screen (spec extension; the paper simulates every
+   * proposal): an MLP u -> [log1p d, log1p A_T, log1p R_T, log1p D_T],
+   * 8 -> 256 -> 256 -> 4 with GELU, bf16 weights and fp32 accumulation,
+   * trained after every generation on the (u, summary) pairs simulated so
+   * far, screens proposals by delayed acceptance: a proposal is simulated
+   * with probability rho = clamp(sigmoid((log1p eps_t - y0) / tau), rho_min,
+   * 1) and its importance weight divided by rho; screened-out proposals are
+   * simulated anyway with probability audit_frac to estimate the
+   * false-rejection rate (never accepted).  Single-run contexts only. */
+  int32_t surrogate;        /* 0 off, 1 on                                              */
+  int32_t surrogate_start;  /* first generation that screens (>= 1)                      */
+  int32_t surrogate_steps;  /* Adam steps after each generation                          */
+  int32_t surrogate_batch;  /* minibatch size (<= 65536)                                 */
+  float surrogate_lr;       /* Adam learning rate                                       */
+  float surrogate_tau;      /* screen temperature in log1p-distance units               */
+  float surrogate_rho_min;  /* floor of the pass probability (0 < rho_min <= 1)          */
+  float audit_frac;         /* audit probability of a screened-out proposal             */
+  int32_t surrogate_ring;   /* training pairs kept; 0 = min(2^21, 16 N)                 */
+  int32_t pad_end;
 } abc_config;
 
 /* Fill a config with the paper's defaults (SAIRD, binomial flows, alpha 0.5,
@@ -239,6 +260,27 @@ ABC_API size_t abc_normalize_scratch_bytes(int64_t n);
 ABC_API int abc_normalize(const double* logW, int64_t n, double* W, double* ess, void* scratch,
                   size_t scratch_bytes, void* stream);
 
+/* A11 delayed-acceptance screen (spec extension; the paper simulates
+ * every proposal; two-stage acceptance after Christen & Fox 2005).  For
+ * slot i < M with flag[i] == 0 the surrogate's prediction of log1p d is
+ * y0 = ystat[0] + ystat[4] * Y[4 i] (fp32 product, then sum) and
+ *   rho[i] = min(max(1 / (1 + exp(-(log1p((float) *eps) - y0) / tau)), rho_min), 1)
+ * in fp32 with the library's own exp and log1p (a NaN prediction gives
+ * rho_min).  sflag[i] = 0 (simulate; may be accepted) when
+ * U(i, c1, 0, ABC_TAG_SCREEN) < rho[i]; else 2 (simulate for the audit of
+ * the false-rejection rate; never accepted) when
+ * U(i, c1, 0, ABC_TAG_AUDIT) < audit_frac; else 3 (screened out).
+ * flag[i] != 0 (redraw-exhausted) gives sflag 1 and rho 1.  tau = cfg
+ * surrogate_tau, rho_min = cfg surrogate_rho_min, audit_frac = cfg
+ * audit_frac, the Philox key from cfg seed and run_id; U(.) is the first
+ * word of the block, mapped as everywhere.  Y: device float [M][4];
+ * ystat: device float[8] (means, then standard deviations); flag: device
+ * u8[M] or NULL (all 0); eps: device double[1]; rho: device float[M];
+ * sflag: device u8[M].  ABC_E_INVAL for bad sizes or parameters. */
+ABC_API int abc_screen(const abc_config* cfg, const float* Y, const float* ystat,
+                       const uint8_t* flag, int64_t M, const double* eps, uint32_t c1, float* rho,
+                       uint8_t* sflag, void* stream);
+
 /* ---- context: whole generations ---------------------------------------- */
 typedef struct abc_ctx abc_ctx;
 
@@ -260,6 +302,12 @@ typedef struct {
   double ms;                /* device time of the generation (CUDA events)          */
   double ms_sim;            /* of which the simulator launches (all batches)        */
   double ms_weights;        /* of which the O(N^2) weight pass                      */
+  int64_t screened;         /* proposals the surrogate did not pass                 */
+  int64_t audited;          /* of which simulated for the audit                     */
+  int64_t audit_accepted;   /* audited proposals with d <= eps (false rejections)   */
+  double train_loss;        /* surrogate minibatch loss after the generation        */
+  double ms_screen;         /* device time of the screening inference               */
+  double ms_train;          /* device time of the surrogate training                */
 } abc_gen_stats;
 
 /* Validate cfg, allocate every device buffer (owned by the context), copy
@@ -288,6 +336,35 @@ ABC_API int abc_get_state(abc_ctx* ctx, void* buf, size_t* len);
 ABC_API int abc_set_state(abc_ctx* ctx, const void* buf, size_t len);
 ABC_API void abc_free(abc_ctx* ctx);
 ABC_API const char* abc_strerror(int code);
+
+/* ---- surrogate MLP (spec extension; the paper has no surrogate) ----
+ * 8 -> 256 -> 256 -> 4 with tanh-form GELU; parameters in one fp32 array
+ * (row = output): W1[256][8], b1[256], W2[256][256], b2[256], W3[4][256],
+ * b3[4] (69124 values); every product uses their bf16 rounding with fp32
+ * accumulation.  These entry points expose the kernels the context uses. */
+typedef struct abc_mlp abc_mlp;
+ABC_API int32_t abc_mlp_param_count(void);
+/* Weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from Philox (key = seed), zero
+ * biases, zero Adam moments. */
+ABC_API int abc_mlp_create(uint64_t seed, abc_mlp** out);
+ABC_API int abc_mlp_set_params(abc_mlp* m, const float* host_params);
+/* host_params: fp32 master values; host_bf16 (nullable): the bf16 copy's bits */
+ABC_API int abc_mlp_get_params(abc_mlp* m, float* host_params, uint16_t* host_bf16);
+ABC_API size_t abc_mlp_scratch_bytes(int32_t batch, int64_t n);
+/* Gradient of the mean squared error over B samples and 4 outputs (CUDA
+ * cores): X device [B][8], T device [B][4]; grad device [69124]; sse device
+ * float[1] receives the sum of squared errors. */
+ABC_API int abc_mlp_grad(abc_mlp* m, const float* X, const float* T, int32_t B, float* grad,
+                         float* sse, void* scratch, size_t scratch_bytes, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step >= 1) on the fp32
+ * parameters; refreshes the bf16 copy. */
+ABC_API int abc_mlp_adam(abc_mlp* m, const float* grad, int64_t step, float lr, void* stream);
+/* Inference on tensor cores: Y device [n][4] for u device [8][n] (layer 1 on
+ * CUDA cores, hidden layer rounded to bf16, layer 2 on tcgen05 with GELU and
+ * layer 3 fused).  Synchronises the stream. */
+ABC_API int abc_mlp_forward(abc_mlp* m, const float* u, int64_t n, float* Y, void* scratch,
+                            size_t scratch_bytes, void* stream);
+ABC_API void abc_mlp_free(abc_mlp* m);
 
 /* ---- batched runs (spec batched form; the paper runs one problem at
  * a time) ------------------------------------------------------------------

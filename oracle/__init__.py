@@ -14,7 +14,8 @@ from .build import build_oracle
 
 _lib = None
 
-TAG_PRIOR, TAG_ANCESTOR, TAG_BETA, TAG_WALK, TAG_SIM, TAG_OBS, TAG_OBS_THETA = 0, 1, 2, 3, 4, 7, 8
+TAG_PRIOR, TAG_ANCESTOR, TAG_BETA, TAG_WALK, TAG_SIM, TAG_SCREEN, TAG_AUDIT = 0, 1, 2, 3, 4, 5, 6
+TAG_OBS, TAG_OBS_THETA = 7, 8
 
 SAIRD_THETA_MAX = np.array([1, 100, 2, 1, 1, 1, 1, 2], np.float32)  # Eq. 2
 OBS_BOX_LO = np.array([0.2, 10, 0.5, 0.02, 0.05, 0.005, 0.2, 0.5], np.float32)
@@ -329,6 +330,21 @@ def mlp_backward(params, x, t):
     loss = f(*ptrs, _p(x, C.c_double), _p(t, C.c_double), C.c_int64(len(x)),
              *[_p(grads[k], C.c_double) for k in MLP_ORDER])
     return loss, grads
+
+
+def screen(m: OracleModel, Y, ystat, flag, eps, c1, tau, rho_min, audit_frac):
+    """Delayed-acceptance screen: returns (rho float32[M], sflag uint8[M])."""
+    Y = np.ascontiguousarray(Y, np.float32).reshape(-1, 4)
+    M = len(Y)
+    ystat = np.ascontiguousarray(ystat, np.float32)
+    fl = None if flag is None else np.ascontiguousarray(flag, np.uint8)
+    rho = np.zeros(M, np.float32)
+    sflag = np.zeros(M, np.uint8)
+    lib().or_screen(m.ref(), _p(Y, C.c_float), _p(ystat, C.c_float), _p(fl, C.c_uint8),
+                    C.c_int64(M), C.c_double(eps), C.c_uint32(c1), C.c_float(tau),
+                    C.c_float(rho_min), C.c_float(audit_frac), _p(rho, C.c_float),
+                    _p(sflag, C.c_uint8))
+    return rho, sflag
 
 
 def adam(w, g, m, v, lr, b1, b2, eps, t):

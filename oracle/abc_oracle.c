@@ -69,7 +69,7 @@ static void philox_ctr(const uint32_t key[2], uint32_t c0, uint32_t c1, uint32_t
 
 /* Stream tags: the fourth counter word. */
 enum { TAG_PRIOR = 0, TAG_ANCESTOR = 1, TAG_BETA = 2, TAG_WALK = 3, TAG_SIM = 4,
-       TAG_OBS = 7, TAG_OBS_THETA = 8 };
+       TAG_SCREEN = 5, TAG_AUDIT = 6, TAG_OBS = 7, TAG_OBS_THETA = 8 };
 
 /* u32 -> (0,1): the top 23 bits plus one half, times 2^-23.  Every step is
  * exact in fp32 and the result lies in [2^-24, 1 - 2^-24] (with 24 bits the
@@ -904,6 +904,47 @@ OR_API double or_mlp_backward(const double* W1, const double* b1, const double* 
     }
   }
   return loss / (4.0 * (double)n);
+}
+
+/*
+ * Delayed-acceptance screen (spec extension; not in the paper; the
+ * two-stage acceptance of Christen & Fox 2005 with a surrogate first stage).
+ * A proposal u' whose surrogate prediction of log1p d is y0 is simulated
+ * with probability rho = min(max(sigmoid((log1p eps - y0) / tau), rho_min), 1);
+ * an accepted one then has density q(u') rho(u') 1[d <= eps], so its
+ * importance weight carries the factor 1/rho.  Screened-out proposals are
+ * simulated anyway with probability audit_frac (never accepted) to measure
+ * how often the screen rejects a proposal that d <= eps would keep.
+ * Y[i][0] is the standardised prediction: y0 = ystat[0] + ystat[4] Y[i][0].
+ * fp32 in this order with the oracle's own exp and log1p; the uniforms are
+ * the first words of Philox blocks (i, c1, 0, SCREEN) and (i, c1, 0, AUDIT).
+ * sflag: 0 simulate, 1 redraw-exhausted (flag != 0; rho 1), 2 audit only,
+ * 3 screened out.
+ */
+OR_API void or_screen(const or_model* m, const float* Y, const float* ystat, const uint8_t* flag,
+                      int64_t M, double eps, uint32_t c1, float tau, float rho_min,
+                      float audit_frac, float* rho, uint8_t* sflag) {
+  const float le = or_log1pf((float)eps);
+  for (int64_t i = 0; i < M; ++i) {
+    if (flag && flag[i]) {
+      sflag[i] = 1;
+      rho[i] = 1.0f;
+      continue;
+    }
+    const float y0 = ystat[0] + ystat[4] * Y[i * 4];
+    const float z = (le - y0) / tau;
+    float r = 1.0f / (1.0f + or_expf(-z));
+    r = fminf(fmaxf(r, rho_min), 1.0f);
+    rho[i] = r;
+    uint32_t w[4];
+    philox_ctr(m->key, (uint32_t)i, c1, 0u, TAG_SCREEN, w);
+    if (or_uniform(w[0]) < r) {
+      sflag[i] = 0;
+      continue;
+    }
+    philox_ctr(m->key, (uint32_t)i, c1, 0u, TAG_AUDIT, w);
+    sflag[i] = or_uniform(w[0]) < audit_frac ? 2 : 3;
+  }
 }
 
 /* Adam (Kingma & Ba 2015) on one parameter array, step count t >= 1. */

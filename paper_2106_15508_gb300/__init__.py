@@ -21,7 +21,8 @@ ABC_SIM_BINOMIAL, ABC_SIM_PAPER_NORMAL = 0, 1
 ABC_BETA_PAPER, ABC_BETA_FIXED = 0, 1
 ABC_W_PAPER, ABC_W_IMPORTANCE = 0, 1
 ABC_P_FP32, ABC_P_BF16_TC = 0, 1
-TAG_PRIOR, TAG_ANCESTOR, TAG_BETA, TAG_WALK, TAG_SIM, TAG_OBS, TAG_OBS_THETA = 0, 1, 2, 3, 4, 7, 8
+TAG_PRIOR, TAG_ANCESTOR, TAG_BETA, TAG_WALK, TAG_SIM, TAG_SCREEN, TAG_AUDIT = 0, 1, 2, 3, 4, 5, 6
+TAG_OBS, TAG_OBS_THETA = 7, 8
 
 # every entry point declared in include/abcsmc.h
 EXPORTS = (
@@ -35,6 +36,8 @@ EXPORTS = (
     "abc_batch_init", "abc_batch_generation", "abc_batch_run", "abc_batch_runs",
     "abc_batch_generations", "abc_batch_get_stats", "abc_batch_get_population",
     "abc_batch_autotune", "abc_batch_tuning", "abc_batch_free",
+    "abc_screen", "abc_mlp_param_count", "abc_mlp_create", "abc_mlp_set_params", "abc_mlp_get_params",
+    "abc_mlp_scratch_bytes", "abc_mlp_grad", "abc_mlp_adam", "abc_mlp_forward", "abc_mlp_free",
 )
 
 
@@ -47,6 +50,10 @@ class AbcConfig(C.Structure):
         ("batch_size", C.c_int32), ("beta_mode", C.c_int32), ("survival_alpha", C.c_double),
         ("beta_a", C.c_float), ("beta_b", C.c_int32), ("weight_mode", C.c_int32),
         ("weight_prec", C.c_int32), ("max_batches", C.c_int32), ("max_redraw", C.c_int32),
+        ("surrogate", C.c_int32), ("surrogate_start", C.c_int32), ("surrogate_steps", C.c_int32),
+        ("surrogate_batch", C.c_int32), ("surrogate_lr", C.c_float), ("surrogate_tau", C.c_float),
+        ("surrogate_rho_min", C.c_float), ("audit_frac", C.c_float), ("surrogate_ring", C.c_int32),
+        ("pad_end", C.c_int32),
     ]
 
 
@@ -57,7 +64,9 @@ class AbcGenStats(C.Structure):
         ("batches", C.c_int64), ("sims", C.c_int64), ("sim_days", C.c_int64),
         ("exhausted", C.c_int64), ("accepted", C.c_int64), ("pairs", C.c_int64),
         ("launches", C.c_int64), ("ms", C.c_double), ("ms_sim", C.c_double),
-        ("ms_weights", C.c_double),
+        ("ms_weights", C.c_double), ("screened", C.c_int64), ("audited", C.c_int64),
+        ("audit_accepted", C.c_int64), ("train_loss", C.c_double), ("ms_screen", C.c_double),
+        ("ms_train", C.c_double),
     ]
 
     def as_dict(self):
@@ -115,6 +124,16 @@ _SIGS = {
     "abc_batch_autotune": (C.c_int, [_V, C.c_char_p]),
     "abc_batch_tuning": (C.c_int, [_V, _I32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "abc_batch_free": (None, [_V]),
+    "abc_screen": (C.c_int, [_V, _V, _V, _V, _I64, _V, C.c_uint32, _V, _V, _V]),
+    "abc_mlp_param_count": (C.c_int32, []),
+    "abc_mlp_create": (C.c_int, [C.c_uint64, C.POINTER(C.c_void_p)]),
+    "abc_mlp_set_params": (C.c_int, [_V, _V]),
+    "abc_mlp_get_params": (C.c_int, [_V, _V, _V]),
+    "abc_mlp_scratch_bytes": (_SZ, [_I32, _I64]),
+    "abc_mlp_grad": (C.c_int, [_V, _V, _V, _I32, _V, _V, _V, _SZ, _V]),
+    "abc_mlp_adam": (C.c_int, [_V, _V, _I64, _F, _V]),
+    "abc_mlp_forward": (C.c_int, [_V, _V, _I64, _V, _V, _SZ, _V]),
+    "abc_mlp_free": (None, [_V]),
 }
 
 
@@ -382,3 +401,52 @@ def abc_batch_tuning(b, run):
 def abc_batch_free(b):
     if b:
         lib().abc_batch_free(b)
+
+
+# ---- surrogate MLP ------------------------------------------------------------
+MLP_SHAPES = dict(W1=(256, 8), b1=(256,), W2=(256, 256), b2=(256,), W3=(4, 256), b3=(4,))
+MLP_ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def abc_screen(cfg, Y, ystat, flag, M, eps, c1, rho, sflag, stream=None):
+    return _check(lib().abc_screen(C.byref(cfg), _ptr(Y), _ptr(ystat), _ptr(flag), M, _ptr(eps), c1,
+                                   _ptr(rho), _ptr(sflag), _stream(stream)), "abc_screen")
+
+
+def abc_mlp_create(seed=1):
+    h = C.c_void_p()
+    _check(lib().abc_mlp_create(seed, C.byref(h)), "abc_mlp_create")
+    return h
+
+
+def abc_mlp_set_params(m, params):
+    """params: host float32 array of abc_mlp_param_count() values"""
+    return _check(lib().abc_mlp_set_params(m, params.ctypes.data), "abc_mlp_set_params")
+
+
+def abc_mlp_get_params(m, params=None, bf16=None):
+    p = lambda x: None if x is None else x.ctypes.data
+    return _check(lib().abc_mlp_get_params(m, p(params), p(bf16)), "abc_mlp_get_params")
+
+
+def abc_mlp_scratch_bytes(batch, n):
+    return lib().abc_mlp_scratch_bytes(batch, n)
+
+
+def abc_mlp_grad(m, X, T, B, grad, sse, scratch, scratch_bytes, stream=None):
+    return _check(lib().abc_mlp_grad(m, _ptr(X), _ptr(T), B, _ptr(grad), _ptr(sse), _ptr(scratch),
+                                     scratch_bytes, _stream(stream)), "abc_mlp_grad")
+
+
+def abc_mlp_adam(m, grad, step, lr, stream=None):
+    return _check(lib().abc_mlp_adam(m, _ptr(grad), step, lr, _stream(stream)), "abc_mlp_adam")
+
+
+def abc_mlp_forward(m, u, n, Y, scratch, scratch_bytes, stream=None):
+    return _check(lib().abc_mlp_forward(m, _ptr(u), n, _ptr(Y), _ptr(scratch), scratch_bytes,
+                                        _stream(stream)), "abc_mlp_forward")
+
+
+def abc_mlp_free(m):
+    if m:
+        lib().abc_mlp_free(m)

@@ -19,7 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libabcsmc.so")
-SOURCES = ["api.cu", "simulate.cu", "particles.cu", "weights.cu", "weights_tc.cu", "batch.cu"]
+SOURCES = ["api.cu", "simulate.cu", "particles.cu", "weights.cu", "weights_tc.cu", "batch.cu",
+           "surrogate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cuda_bf16.h>
 #include <cstdio>
 #include <cstring>
 #include <fstream>
@@ -14,6 +15,7 @@
 
 #include "batch.cuh"
 #include "common.cuh"
+#include "surrogate.cuh"
 
 namespace abc {
 // launchers not declared in batch.cuh
@@ -78,6 +80,14 @@ int check_smc(const abc_config* c) {
   if (c->weight_prec != ABC_P_FP32 && c->weight_prec != ABC_P_BF16_TC) return ABC_E_INVAL;
   if (c->max_batches < 1 || c->max_batches > 65535) return ABC_E_INVAL;
   if (c->max_redraw < 1 || c->max_redraw > (1 << 23)) return ABC_E_INVAL;
+  if (c->surrogate) {
+    if (c->surrogate != 1 || c->surrogate_start < 1 || c->surrogate_steps < 0 ||
+        c->surrogate_batch < 32 || c->surrogate_batch > 65536 || !(c->surrogate_lr > 0.0f) ||
+        !(c->surrogate_tau > 0.0f) || !(c->surrogate_rho_min > 0.0f) ||
+        !(c->surrogate_rho_min <= 1.0f) || !(c->audit_frac >= 0.0f && c->audit_frac <= 1.0f) ||
+        c->surrogate_ring < 0)
+      return ABC_E_INVAL;
+  }
   return ABC_OK;
 }
 
@@ -106,6 +116,15 @@ ABC_API void abc_config_default(abc_config* c) {
   c->weight_prec = ABC_P_FP32;
   c->max_batches = 64;
   c->max_redraw = 64;
+  c->surrogate = 0;
+  c->surrogate_start = 3;
+  c->surrogate_steps = 64;
+  c->surrogate_batch = 8192;
+  c->surrogate_lr = 1e-3f;
+  c->surrogate_tau = 0.5f;
+  c->surrogate_rho_min = 0.05f;
+  c->audit_frac = 0.01f;
+  c->surrogate_ring = 0;
 }
 
 ABC_API const char* abc_strerror(int code) {
@@ -291,6 +310,21 @@ ABC_API int abc_normalize(const double* logW, int64_t n, double* W, double* ess,
   return launch_normalize(logW, n, W, ess, scratch, scratch_bytes, as_stream(stream));
 }
 
+ABC_API int abc_screen(const abc_config* cfg, const float* Y, const float* ystat,
+                       const uint8_t* flag, int64_t M, const double* eps, uint32_t c1, float* rho,
+                       uint8_t* sflag, void* stream) {
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (M < 0 || M > kMaxIndex) return ABC_E_INVAL;
+  if (!(cfg->surrogate_tau > 0.0f) || !(cfg->surrogate_rho_min > 0.0f) ||
+      !(cfg->surrogate_rho_min <= 1.0f) || !(cfg->audit_frac >= 0.0f && cfg->audit_frac <= 1.0f))
+    return ABC_E_INVAL;
+  if (M > 0 && (!Y || !ystat || !eps || !rho || !sflag)) return ABC_E_INVAL;
+  const SimParams p = make_params(*cfg);
+  return screen(Y, ystat, flag, M, eps, p.k0, p.k1, c1, cfg->surrogate_tau, cfg->surrogate_rho_min,
+                cfg->audit_frac, rho, sflag, as_stream(stream), nullptr);
+}
+
 }  // extern "C"
 
 // -------------------------------------------------------------- context ---
@@ -331,6 +365,36 @@ struct abc_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // whole generation
   cudaEvent_t es0 = nullptr, es1 = nullptr;  // one simulator launch
   cudaEvent_t ew0 = nullptr, ew1 = nullptr;  // the weight pass
+  // surrogate (delayed-acceptance pre-screen)
+  MlpState mlp{};
+  float* grad = nullptr;
+  float* RX = nullptr;            // ring of inputs [cap][8]
+  float* RY = nullptr;            // ring of summaries [cap][4]
+  long long* ring_head = nullptr; // samples appended so far
+  int64_t ring_cap = 0;
+  int64_t ring_host = 0;
+  float* ystat = nullptr;         // mean[4], std[4]
+  float* Yp = nullptr;            // predictions [M][4]
+  float* rho = nullptr;           // pass probability per slot
+  uint8_t* sflag = nullptr;
+  float* cmp_u = nullptr;         // compacted simulated slots
+  float* cmp_s = nullptr;
+  int32_t* cmp_a = nullptr;
+  float* cmp_rho = nullptr;
+  uint8_t* cmp_flag = nullptr;
+  uint32_t* cmp_slot = nullptr;
+  double* cmp_d = nullptr;
+  int32_t* ard = nullptr;         // final A, R, D [3][M]
+  int* Mc = nullptr;
+  float* rho_pop[2] = {nullptr, nullptr};
+  float* trX = nullptr;
+  float* trT = nullptr;
+  float* loss = nullptr;
+  unsigned long long* audit = nullptr;  // audited, audited with d <= eps
+  void* sscratch = nullptr;       // surrogate scratch (training / inference / screening)
+  size_t sscratch_bytes = 0;
+  uint32_t train_step = 0;
+  cudaEvent_t eq0 = nullptr, eq1 = nullptr, et0 = nullptr, et1 = nullptr;
 
   template <typename T>
   int alloc(T** ptr, size_t count) {
@@ -345,7 +409,7 @@ struct abc_ctx {
   }
   ~abc_ctx() {
     for (void* p : allocs) cudaFree(p);
-    for (cudaEvent_t e : {ev0, ev1, es0, es1, ew0, ew1})
+    for (cudaEvent_t e : {ev0, ev1, es0, es1, ew0, ew1, eq0, eq1, et0, et1})
       if (e) cudaEventDestroy(e);
   }
 };
@@ -381,6 +445,45 @@ int ctx_alloc(abc_ctx* c) {
   }
   ABC_ALLOC(c->scal, 4);
   ABC_ALLOC(c->cnt, 4);
+  if (c->cfg.surrogate) {
+    const int B = c->cfg.surrogate_batch;
+    c->ring_cap = c->cfg.surrogate_ring > 0
+                      ? c->cfg.surrogate_ring
+                      : std::min<int64_t>(int64_t(1) << 21, 16 * std::max<int64_t>(c->N, 4096));
+    ABC_ALLOC(c->mlp.w, kMlpParams);
+    ABC_ALLOC(c->mlp.wb, kMlpParams);
+    ABC_ALLOC(c->mlp.m, kMlpParams);
+    ABC_ALLOC(c->mlp.v, kMlpParams);
+    ABC_ALLOC(c->grad, kMlpParams);
+    ABC_ALLOC(c->RX, 8 * static_cast<size_t>(c->ring_cap));
+    ABC_ALLOC(c->RY, 4 * static_cast<size_t>(c->ring_cap));
+    ABC_ALLOC(c->ring_head, 1);
+    ABC_ALLOC(c->ystat, 8);
+    ABC_ALLOC(c->Yp, 4 * M);
+    ABC_ALLOC(c->rho, M);
+    ABC_ALLOC(c->sflag, M);
+    ABC_ALLOC(c->cmp_u, 8 * M);
+    ABC_ALLOC(c->cmp_s, M);
+    ABC_ALLOC(c->cmp_a, M);
+    ABC_ALLOC(c->cmp_rho, M);
+    ABC_ALLOC(c->cmp_flag, M);
+    ABC_ALLOC(c->cmp_slot, M);
+    ABC_ALLOC(c->cmp_d, M);
+    ABC_ALLOC(c->ard, 3 * std::max(M, N));
+    ABC_ALLOC(c->Mc, 1);
+    ABC_ALLOC(c->rho_pop[0], N);
+    ABC_ALLOC(c->rho_pop[1], N);
+    ABC_ALLOC(c->trX, 8 * static_cast<size_t>(B));
+    ABC_ALLOC(c->trT, 4 * static_cast<size_t>(B));
+    ABC_ALLOC(c->loss, 1);
+    ABC_ALLOC(c->audit, 2);
+    c->sscratch_bytes = std::max({mlp_train_scratch_bytes(B), mlp_infer_scratch_bytes(c->M),
+                                  screen_scratch_bytes(c->M),
+                                  ring_scratch_bytes(std::max(c->M, c->N))});
+    char* ss = nullptr;
+    if ((rc = c->alloc(&ss, c->sscratch_bytes)) != ABC_OK) return rc;
+    c->sscratch = ss;
+  }
 #undef ABC_ALLOC
   size_t sb = std::max({select_scratch_bytes(c->N), prefix_scratch_bytes(c->N),
                         accept_scratch_bytes(c->M), survivors_scratch_bytes(c->N),
@@ -402,9 +505,13 @@ int generation0(abc_ctx* c) {
   if (rc) return rc;
   ABC_CUDA_TRY(cudaEventRecord(c->es0, st));
   rc = launch_simulate(c->p, c->obs, c->u[cur], c->N, nullptr, 0u, ABC_TAG_SIM, nullptr, c->d[cur],
-                       nullptr, st);
+                       nullptr, st, nullptr, nullptr, 128, c->cfg.surrogate ? c->ard : nullptr);
   if (rc) return rc;
   ABC_CUDA_TRY(cudaEventRecord(c->es1, st));
+  if (c->cfg.surrogate &&
+      (rc = ring_append(nullptr, c->N, c->u[cur], c->d[cur], c->ard, c->ring_head, c->ring_cap, c->RX,
+                        c->RY, c->sscratch, st)))
+    return rc;
   if ((rc = launch_fill(c->W[cur], c->N, 1.0 / static_cast<double>(c->N), st))) return rc;
   ABC_CUDA_TRY(cudaMemsetAsync(c->anc[cur], 0xFF, sizeof(int32_t) * c->N, st));
   ABC_CUDA_TRY(cudaMemsetAsync(c->s[cur], 0, sizeof(float) * c->N, st));
@@ -445,39 +552,98 @@ int generation_t(abc_ctx* c) {
                               c->scratch, c->scratch_bytes, st);
   if (rc) return rc;
   ABC_CUDA_TRY(cudaMemsetAsync(c->cnt, 0, 4 * sizeof(int64_t), st));
-  int64_t filled = 0;
-  double ms_sim = 0.0;
+  const bool sur = c->cfg.surrogate != 0;
+  // screen once the surrogate has been trained (from generation surrogate_start)
+  const bool screen = sur && t >= c->cfg.surrogate_start && c->train_step > 0;
+  if (sur) ABC_CUDA_TRY(cudaMemsetAsync(c->audit, 0, 2 * sizeof(unsigned long long), st));
+  int64_t filled = 0, simulated = 0;
+  double ms_sim = 0.0, ms_screen = 0.0;
   int32_t b = 0;
+  unsigned* inf_err = nullptr;
+  unsigned h_inf_err = 0;
   for (b = 0; b < c->cfg.max_batches && filled < c->N; ++b) {
     const uint32_t c1 = (static_cast<uint32_t>(t) << 16) | static_cast<uint32_t>(b);
     rc = launch_propose(c->p, c->u[cur], c->N, c->prefix, paper_beta, eps, eps1, c->cfg.beta_a, bb,
                         c->M, nullptr, c1, c->cfg.max_redraw, c->up, c->sp, c->ap, c->att,
                         c->flag, st);
     if (rc) return rc;
-    ABC_CUDA_TRY(cudaEventRecord(c->es0, st));
-    rc = launch_simulate(c->p, c->obs, c->up, c->M, nullptr, c1, ABC_TAG_SIM, c->flag, c->dp,
-                         nullptr, st);
-    if (rc) return rc;
-    ABC_CUDA_TRY(cudaEventRecord(c->es1, st));
-    rc = launch_accept(c->up, c->dp, c->sp, c->ap, c->flag, c->M, eps, c->N, c->u[nxt], c->d[nxt],
-                       c->s[nxt], c->anc[nxt], c->cnt, c->cnt + 1, c->scratch, c->scratch_bytes,
-                       st);
-    if (rc) return rc;
+    int h_mc = 0;
+    if (screen) {
+      // delayed acceptance: predict, screen, simulate only the compacted slots
+      ABC_CUDA_TRY(cudaEventRecord(c->eq0, st));
+      if ((rc = mlp_infer(c->mlp, c->up, c->M, c->Yp, c->sscratch, c->sscratch_bytes, &inf_err, st)))
+        return rc;
+      if ((rc = screen_and_compact(c->Yp, c->ystat, c->flag, c->M, eps, c->p.k0, c->p.k1, c1,
+                                   c->cfg.surrogate_tau, c->cfg.surrogate_rho_min,
+                                   c->cfg.audit_frac, c->rho, c->sflag, c->up, c->sp, c->ap,
+                                   c->cmp_u, c->cmp_s, c->cmp_a, c->cmp_rho, c->cmp_flag,
+                                   c->cmp_slot, c->Mc, c->sscratch, st,
+                                   reinterpret_cast<unsigned long long*>(c->cnt + 2))))
+        return rc;
+      ABC_CUDA_TRY(cudaEventRecord(c->eq1, st));
+      ABC_CUDA_TRY(cudaMemcpyAsync(&h_mc, c->Mc, sizeof(int), cudaMemcpyDeviceToHost, st));
+      ABC_CUDA_TRY(cudaMemcpyAsync(&h_inf_err, inf_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+      ABC_CUDA_TRY(cudaStreamSynchronize(st));
+      if (h_inf_err) return ABC_E_DEVICE;
+      float mq = 0.f;
+      ABC_CUDA_TRY(cudaEventElapsedTime(&mq, c->eq0, c->eq1));
+      ms_screen += mq;
+      ABC_CUDA_TRY(cudaEventRecord(c->es0, st));
+      rc = launch_simulate(c->p, c->obs, c->cmp_u, h_mc, c->cmp_slot, c1, ABC_TAG_SIM, nullptr,
+                           c->cmp_d, nullptr, st, nullptr, nullptr, 128, c->ard);
+      if (rc) return rc;
+      ABC_CUDA_TRY(cudaEventRecord(c->es1, st));
+      rc = launch_accept(c->cmp_u, c->cmp_d, c->cmp_s, c->cmp_a, c->cmp_flag, h_mc, eps, c->N,
+                         c->u[nxt], c->d[nxt], c->s[nxt], c->anc[nxt], c->cnt, c->cnt + 1,
+                         c->scratch, c->scratch_bytes, st, c->cmp_rho, c->rho_pop[nxt]);
+      if (rc) return rc;
+      if ((rc = audit_count(c->cmp_flag, c->cmp_d, c->Mc, eps, c->audit, st))) return rc;
+      if ((rc = ring_append(nullptr, h_mc, c->cmp_u, c->cmp_d, c->ard, c->ring_head, c->ring_cap,
+                            c->RX, c->RY, c->sscratch, st)))
+        return rc;
+    } else {
+      ABC_CUDA_TRY(cudaEventRecord(c->es0, st));
+      rc = launch_simulate(c->p, c->obs, c->up, c->M, nullptr, c1, ABC_TAG_SIM, c->flag, c->dp,
+                           nullptr, st, nullptr, nullptr, 128, sur ? c->ard : nullptr);
+      if (rc) return rc;
+      ABC_CUDA_TRY(cudaEventRecord(c->es1, st));
+      rc = launch_accept(c->up, c->dp, c->sp, c->ap, c->flag, c->M, eps, c->N, c->u[nxt], c->d[nxt],
+                         c->s[nxt], c->anc[nxt], c->cnt, c->cnt + 1, c->scratch, c->scratch_bytes,
+                         st, nullptr, sur ? c->rho_pop[nxt] : nullptr);
+      if (rc) return rc;
+      if (sur && (rc = ring_append(c->flag, c->M, c->up, c->dp, c->ard, c->ring_head, c->ring_cap,
+                                   c->RX, c->RY, c->sscratch, st)))
+        return rc;
+    }
     ABC_CUDA_TRY(cudaMemcpyAsync(&filled, c->cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     ABC_CUDA_TRY(cudaStreamSynchronize(st));
     float ms = 0.f;
     ABC_CUDA_TRY(cudaEventElapsedTime(&ms, c->es0, c->es1));
     ms_sim += ms;
+    if (screen) simulated += h_mc;
   }
   int64_t h_cnt[3];
   ABC_CUDA_TRY(cudaMemcpyAsync(h_cnt, c->cnt, sizeof h_cnt, cudaMemcpyDeviceToHost, st));
+  unsigned long long h_audit[2] = {0, 0};
+  if (sur) ABC_CUDA_TRY(cudaMemcpyAsync(h_audit, c->audit, sizeof h_audit, cudaMemcpyDeviceToHost, st));
   ABC_CUDA_TRY(cudaStreamSynchronize(st));
   abc_gen_stats g{};
   g.generation = t;
   g.batches = b;
   g.accepted = h_cnt[1];
-  g.exhausted = h_cnt[2];
-  g.sims = static_cast<int64_t>(b) * c->M - h_cnt[2];
+  g.ms_screen = ms_screen;
+  if (screen) {
+    // every slot is exhausted (never simulated), passed, or screened out;
+    // audited slots were screened out and simulated anyway
+    g.exhausted = h_cnt[2];
+    g.sims = simulated;
+    g.audited = static_cast<int64_t>(h_audit[0]);
+    g.audit_accepted = static_cast<int64_t>(h_audit[1]);
+    g.screened = static_cast<int64_t>(b) * c->M - g.exhausted - (simulated - g.audited);
+  } else {
+    g.exhausted = h_cnt[2];
+    g.sims = static_cast<int64_t>(b) * c->M - h_cnt[2];
+  }
   g.sim_days = g.sims * static_cast<int64_t>(c->cfg.model == ABC_MODEL_SAIRD ? c->T : 1);
   g.beta_b = bb;
   g.ms_sim = ms_sim;
@@ -506,6 +672,8 @@ int generation_t(abc_ctx* c) {
       if (tc_err) ABC_CUDA_TRY(cudaMemcpyAsync(&h_err, tc_err, sizeof h_err, cudaMemcpyDeviceToHost, st));
       ABC_CUDA_TRY(cudaMemcpyAsync(&h_nc, c->nc, sizeof(int), cudaMemcpyDeviceToHost, st));
       weighted = true;
+      // delayed acceptance: a proposal simulated with probability rho carries 1/rho
+      if (screen && (rc = rho_correct(c->logW, c->rho_pop[nxt], c->N, st))) return rc;
       rc = launch_normalize(c->logW, c->N, c->W[nxt], ess, c->scratch, c->scratch_bytes, st);
       if (rc) return rc;
     } else {
@@ -529,6 +697,24 @@ int generation_t(abc_ctx* c) {
   g.beta_a = paper_beta ? (h_scal[1] > 0.0 ? static_cast<float>(h_scal[0] / h_scal[1]) : 1.0f)
                         : c->cfg.beta_a;
   c->eps1_host = h_scal[1];
+  if (sur && g.status == ABC_OK && c->cfg.surrogate_steps > 0) {
+    // train on everything simulated so far (the ring keeps the latest pairs)
+    ABC_CUDA_TRY(cudaEventRecord(c->et0, st));
+    if ((rc = ring_stats(c->RY, c->ring_head, c->ring_cap, c->ystat, st))) return rc;
+    if ((rc = mlp_train(c->mlp, c->RX, c->RY, c->ring_head, c->ring_cap, c->ystat,
+                        c->cfg.surrogate_batch, c->cfg.surrogate_steps, c->train_step,
+                        c->cfg.surrogate_lr, c->p.k0, c->p.k1, c->grad, c->trX, c->trT, c->loss,
+                        c->sscratch, c->sscratch_bytes, st)))
+      return rc;
+    ABC_CUDA_TRY(cudaEventRecord(c->et1, st));
+    c->train_step += static_cast<uint32_t>(c->cfg.surrogate_steps);
+    float lh = 0.f, mt = 0.f;
+    ABC_CUDA_TRY(cudaMemcpyAsync(&lh, c->loss, sizeof lh, cudaMemcpyDeviceToHost, st));
+    ABC_CUDA_TRY(cudaStreamSynchronize(st));
+    ABC_CUDA_TRY(cudaEventElapsedTime(&mt, c->et0, c->et1));
+    g.train_loss = lh / (4.0 * c->cfg.surrogate_batch);
+    g.ms_train = mt;
+  }
   c->stats.push_back(g);
   if (g.status == ABC_OK) c->cur = nxt;
   return g.status;
@@ -561,6 +747,19 @@ ABC_API int abc_init(const abc_config* cfg, const int32_t* obs, void* stream, ab
       (rc = weights_tc_prepare()) != ABC_OK) {
     delete c;
     return rc;
+  }
+  if (cfg->surrogate) {
+    if (cudaEventCreate(&c->eq0) != cudaSuccess || cudaEventCreate(&c->eq1) != cudaSuccess ||
+        cudaEventCreate(&c->et0) != cudaSuccess || cudaEventCreate(&c->et1) != cudaSuccess ||
+        cudaMemsetAsync(c->ring_head, 0, sizeof(long long), c->st) != cudaSuccess) {
+      delete c;
+      return ABC_E_CUDA;
+    }
+    if ((rc = mlp_infer_prepare()) != ABC_OK ||
+        (rc = mlp_init(c->mlp, c->p.k0, c->p.k1, c->st)) != ABC_OK) {
+      delete c;
+      return rc;
+    }
   }
   if (c->obs) {
     if (cudaMemcpyAsync(c->obs, obs, sizeof(int32_t) * 3 * (c->T + 1), cudaMemcpyHostToDevice,
@@ -1107,6 +1306,99 @@ ABC_API void abc_batch_free(abc_batch* b) {
   if (!b) return;
   if (b->st) cudaStreamSynchronize(b->st);
   delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- MLP ABI ---
+struct abc_mlp {
+  MlpState s{};
+  void* mem = nullptr;
+  ~abc_mlp() {
+    if (mem) cudaFree(mem);
+  }
+};
+
+extern "C" {
+
+ABC_API int32_t abc_mlp_param_count(void) { return kMlpParams; }
+
+ABC_API int abc_mlp_create(uint64_t seed, abc_mlp** out) {
+  if (!out) return ABC_E_INVAL;
+  *out = nullptr;
+  abc_mlp* m = new (std::nothrow) abc_mlp();
+  if (!m) return ABC_E_NOMEM;
+  const size_t P = kMlpParams;
+  if (cudaMalloc(&m->mem, P * (3 * sizeof(float) + sizeof(__nv_bfloat16)) + 256) != cudaSuccess) {
+    cudaGetLastError();
+    delete m;
+    return ABC_E_NOMEM;
+  }
+  char* b = static_cast<char*>(m->mem);
+  m->s.w = reinterpret_cast<float*>(b);
+  m->s.m = m->s.w + P;
+  m->s.v = m->s.m + P;
+  m->s.wb = reinterpret_cast<__nv_bfloat16*>(m->s.v + P);
+  int rc = mlp_init(m->s, static_cast<uint32_t>(seed & 0xFFFFFFFFu),
+                    static_cast<uint32_t>(seed >> 32), nullptr);
+  if (rc == ABC_OK) rc = mlp_infer_prepare();
+  if (rc == ABC_OK && cudaDeviceSynchronize() != cudaSuccess) rc = ABC_E_CUDA;
+  if (rc != ABC_OK) {
+    delete m;
+    return rc;
+  }
+  *out = m;
+  return ABC_OK;
+}
+
+ABC_API int abc_mlp_set_params(abc_mlp* m, const float* host_params) {
+  if (!m || !host_params) return ABC_E_INVAL;
+  ABC_CUDA_TRY(cudaMemcpy(m->s.w, host_params, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice));
+  const int rc = mlp_refresh_bf16(m->s, nullptr);
+  if (rc) return rc;
+  ABC_CUDA_TRY(cudaDeviceSynchronize());
+  return ABC_OK;
+}
+
+ABC_API int abc_mlp_get_params(abc_mlp* m, float* host_params, uint16_t* host_bf16) {
+  if (!m) return ABC_E_INVAL;
+  if (host_params)
+    ABC_CUDA_TRY(cudaMemcpy(host_params, m->s.w, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost));
+  if (host_bf16)
+    ABC_CUDA_TRY(cudaMemcpy(host_bf16, m->s.wb, 2 * kMlpParams, cudaMemcpyDeviceToHost));
+  return ABC_OK;
+}
+
+ABC_API size_t abc_mlp_scratch_bytes(int32_t batch, int64_t n) {
+  return std::max(mlp_train_scratch_bytes(std::max(batch, 1)), mlp_infer_scratch_bytes(n));
+}
+
+ABC_API int abc_mlp_grad(abc_mlp* m, const float* X, const float* T, int32_t B, float* grad,
+                         float* sse, void* scratch, size_t scratch_bytes, void* stream) {
+  if (!m || !X || !T || !grad || !sse || !scratch || B < 1 || B > (1 << 22)) return ABC_E_INVAL;
+  return mlp_grad(m->s, X, T, B, grad, sse, scratch, scratch_bytes, as_stream(stream));
+}
+
+ABC_API int abc_mlp_adam(abc_mlp* m, const float* grad, int64_t step, float lr, void* stream) {
+  if (!m || !grad || step < 1 || !(lr > 0.0f)) return ABC_E_INVAL;
+  return mlp_adam(m->s, grad, step, lr, as_stream(stream));
+}
+
+ABC_API int abc_mlp_forward(abc_mlp* m, const float* u, int64_t n, float* Y, void* scratch,
+                            size_t scratch_bytes, void* stream) {
+  if (!m || !u || !Y || !scratch || n < 1 || n > kMaxIndex) return ABC_E_INVAL;
+  cudaStream_t st = as_stream(stream);
+  unsigned* err = nullptr;
+  int rc = mlp_infer(m->s, u, n, Y, scratch, scratch_bytes, &err, st);
+  if (rc) return rc;
+  return check_device_error(err, st);
+}
+
+ABC_API void abc_mlp_free(abc_mlp* m) {
+  if (m) {
+    cudaDeviceSynchronize();
+    delete m;
+  }
 }
 
 }  // extern "C"

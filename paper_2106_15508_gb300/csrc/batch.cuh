@@ -56,7 +56,7 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st);
 int launch_simulate(const SimParams&, const int32_t*, const float*, int64_t, const uint32_t*,
                     uint32_t, uint32_t, const uint8_t*, double*, int32_t*, cudaStream_t,
                     const uint32_t* c1_dev = nullptr, const int* off_dev = nullptr,
-                    int threads = 128);
+                    int threads = 128, int32_t* ard_last = nullptr);
 int launch_select(const double*, int64_t, int64_t, double*, void*, size_t, cudaStream_t);
 int launch_resample_prefix(const double*, const double*, int64_t, const double*, int, uint32_t*,
                            uint64_t*, void*, size_t, cudaStream_t);
@@ -67,15 +67,18 @@ int launch_propose(const SimParams&, const float*, int64_t, const uint64_t*, int
                    const int* off_dev = nullptr);
 int launch_accept(const float*, const double*, const float*, const int32_t*, const uint8_t*,
                   int64_t, const double*, int64_t, float*, double*, float*, int32_t*, int64_t*,
-                  int64_t*, void*, size_t, cudaStream_t);
+                  int64_t*, void*, size_t, cudaStream_t, const float* rho_in = nullptr,
+                  float* rho_pop = nullptr);
 int launch_survivors(const float*, const uint32_t*, int64_t, float*, float*, int*, void*,
                      cudaStream_t);
 int launch_weights_fp32(const float*, const float*, int64_t, const float*, const float*,
                         const int*, int64_t, const uint64_t*, double*, void*, size_t,
-                        cudaStream_t, const int* off_dev = nullptr, int mult = 1);
+                        cudaStream_t, const int* off_dev = nullptr, int mult = 1,
+                        const int* rows_dev = nullptr);
 int launch_weights_tc(const float*, const float*, int64_t, const float*, const float*, const int*,
                       int64_t, const uint64_t*, double*, void*, size_t, unsigned**,
-                      cudaStream_t, const int* off_dev = nullptr, int mult = 1);
+                      cudaStream_t, const int* off_dev = nullptr, int mult = 1,
+                      const int* rows_dev = nullptr);
 int launch_normalize(const double*, int64_t, double*, double*, void*, size_t, cudaStream_t);
 int weights_tc_prepare();
 

@@ -353,9 +353,9 @@ __global__ void k_acc_count(const double* __restrict__ dp, const uint8_t* __rest
   for (int e = 0; e < 4; ++e) {
     const int64_t i = base + e;
     if (i < M) {
-      const bool fl = flag[i] != 0;
-      f += fl;
-      c += (!fl && dp[i] <= eps);
+      const uint8_t fl = flag[i];  // 1: redraws exhausted; 2: simulated for an audit only
+      f += (fl == 1);
+      c += (fl == 0 && dp[i] <= eps);
     }
   }
   c = block_sum<int>(c, sm);
@@ -381,7 +381,8 @@ __global__ void k_acc_scatter(const float* __restrict__ up, const double* __rest
                               const uint8_t* __restrict__ flag, int64_t M, const double* eps_p,
                               const int* __restrict__ tile_off, const long long* base_p,
                               int64_t N, float* __restrict__ u_pop, double* __restrict__ d_pop,
-                              float* __restrict__ s_pop, int32_t* __restrict__ anc_pop) {
+                              float* __restrict__ s_pop, int32_t* __restrict__ anc_pop,
+                              const float* __restrict__ rho_in, float* __restrict__ rho_pop) {
   __shared__ int sm[32];
   const double eps = *eps_p;
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile + 4 * threadIdx.x;
@@ -405,6 +406,7 @@ __global__ void k_acc_scatter(const float* __restrict__ up, const double* __rest
       d_pop[pos] = dp[i];
       s_pop[pos] = sp[i];
       anc_pop[pos] = ap[i];
+      if (rho_pop) rho_pop[pos] = rho_in ? rho_in[i] : 1.0f;
     }
     ++pos;
   }
@@ -418,7 +420,8 @@ size_t accept_scratch_bytes(int64_t M) {
 int launch_accept(const float* up, const double* dp, const float* sp, const int32_t* ap,
                   const uint8_t* flag, int64_t M, const double* eps, int64_t N, float* u_pop,
                   double* d_pop, float* s_pop, int32_t* anc_pop, int64_t* filled,
-                  int64_t* counters, void* scratch, size_t bytes, cudaStream_t st) {
+                  int64_t* counters, void* scratch, size_t bytes, cudaStream_t st,
+                  const float* rho_in, float* rho_pop) {
   if (M < 0 || N <= 0) return ABC_E_INVAL;
   if (M == 0) return ABC_OK;
   if (bytes < accept_scratch_bytes(M)) return ABC_E_SCRATCH;
@@ -437,7 +440,7 @@ int launch_accept(const float* up, const double* dp, const float* sp, const int3
   ABC_LAUNCH_CHECK();
   k_acc_scatter<<<static_cast<unsigned>(nt), kTileThr, 0, st>>>(up, dp, sp, ap, flag, M, eps, off,
                                                                 basep, N, u_pop, d_pop, s_pop,
-                                                                anc_pop);
+                                                                anc_pop, rho_in, rho_pop);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

@@ -33,7 +33,7 @@ __device__ __forceinline__ float theta_of(const SimParams& p, int d, float u) {
 // simulated A, R, D as [3][T+1] for days 1..T.
 __device__ U128 saird_path(const SimParams& p, const float th[8], uint32_t c0, uint32_t c1,
                            uint32_t tag, const int32_t* obs, int32_t* traj, int64_t stride,
-                           int64_t col, int32_t* ard) {
+                           int64_t col, int32_t* ard, int32_t* last = nullptr) {
   const float alpha0 = th[0], alpha = th[1], n = th[2], beta = th[3], gamma = th[4],
               delta = th[5], eta = th[6], kappa = th[7];
   // initial state (Sec. 2.2): Ru = 0, I0 = kappa A0, S = P - (A0 + R0 + D0 + I0)
@@ -118,6 +118,11 @@ __device__ U128 saird_path(const SimParams& p, const float th[8], uint32_t c0, u
       acc_sq(acc, D, obs[2 * (T + 1) + day + 1]);
     }
   }
+  if (last) {
+    last[0] = A;
+    last[1] = R;
+    last[2] = D;
+  }
   return acc;
 }
 
@@ -146,7 +151,7 @@ __global__ void k_simulate(SimParams p, const int32_t* __restrict__ obs,
                            const uint32_t* __restrict__ c0_idx, uint32_t c1, uint32_t tag,
                            const uint8_t* __restrict__ skip, double* __restrict__ dist,
                            int32_t* __restrict__ traj, const uint32_t* __restrict__ c1_dev,
-                           const int* __restrict__ off_dev) {
+                           const int* __restrict__ off_dev, int32_t* __restrict__ ard_last) {
   extern __shared__ int32_t s_obs[];
   if (off_dev && *off_dev) return;  // run finished: nothing to simulate
   if (c1_dev) c1 = *c1_dev;         // counter word set on the device (graph launches)
@@ -165,9 +170,20 @@ __global__ void k_simulate(SimParams p, const int32_t* __restrict__ obs,
   const uint32_t c0 = c0_idx ? c0_idx[i] : static_cast<uint32_t>(i);
   if (p.model == ABC_MODEL_GAUSS_TOY) {
     dist[i] = toy_dist(p, th, c0, c1, tag);
+    if (ard_last) {  // the toy has no compartments
+      ard_last[0 * n + i] = 0;
+      ard_last[1 * n + i] = 0;
+      ard_last[2 * n + i] = 0;
+    }
   } else {
-    const U128 a = saird_path(p, th, c0, c1, tag, nobs ? s_obs : nullptr, traj, n, i, nullptr);
+    int32_t last[3];
+    const U128 a = saird_path(p, th, c0, c1, tag, nobs ? s_obs : nullptr, traj, n, i, nullptr, last);
     dist[i] = __dsqrt_rn(u128_to_double(a.hi, a.lo));
+    if (ard_last) {
+      ard_last[0 * n + i] = last[0];
+      ard_last[1 * n + i] = last[1];
+      ard_last[2 * n + i] = last[2];
+    }
   }
 }
 
@@ -222,12 +238,12 @@ __global__ void k_philox(const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t
 int launch_simulate(const SimParams& p, const int32_t* obs, const float* u, int64_t n,
                     const uint32_t* c0_idx, uint32_t c1, uint32_t tag, const uint8_t* skip,
                     double* dist, int32_t* traj, cudaStream_t st, const uint32_t* c1_dev,
-                    const int* off_dev, int threads) {
+                    const int* off_dev, int threads, int32_t* ard_last) {
   if (n <= 0) return ABC_OK;
   if (threads != 64 && threads != 128 && threads != 256 && threads != 512) return ABC_E_INVAL;
   const size_t smem = (p.model == ABC_MODEL_SAIRD && obs) ? sizeof(int32_t) * 3 * (p.T + 1) : 0;
   k_simulate<<<static_cast<unsigned>(ceil_div(n, threads)), threads, smem, st>>>(
-      p, obs, u, n, c0_idx, c1, tag, skip, dist, traj, c1_dev, off_dev);
+      p, obs, u, n, c0_idx, c1, tag, skip, dist, traj, c1_dev, off_dev, ard_last);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

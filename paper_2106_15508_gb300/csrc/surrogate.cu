@@ -1,0 +1,809 @@
+// surrogate.cu -- MLP surrogate u (8) -> 256 -> 256 -> 4 (tanh-form GELU)
+// for delayed-acceptance pre-screening (spec extension; the paper
+// simulates every proposal).
+//
+// Parameters: fp32 master copy (Adam updates it) and a bf16 copy that every
+// product uses (BF16 weights, FP32 accumulation).  Layouts, row = output:
+// W1[256][8], b1[256], W2[256][256], b2[256], W3[4][256], b3[4].
+// Outputs are the standardised summaries y = [log1p d, log1p A_T, log1p R_T,
+// log1p D_T]; the per-output mean and standard deviation live beside the
+// parameters.
+//
+// Training (CUDA cores): a tiled GEMM with arbitrary operand strides and fused
+// epilogues (bias + GELU on the forward layer, GELU' on the backward layer),
+// small kernels for the 8-wide and 4-wide layers, Adam in fp32.
+// Inference: layer 1 on CUDA cores writes the hidden layer as bf16 tiles in
+// the tensor-core operand layout; layer 2 runs on tcgen05 (M = 128, N = 256,
+// K = 256) with bias + GELU + layer 3 fused into the epilogue (one thread per
+// sample reads its 256 accumulators from tensor memory).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "numerics.cuh"
+#include "surrogate.cuh"
+#include "tcgen05.cuh"
+
+namespace abc {
+
+// ---- GELU (tanh form, Hendrycks & Gimpel) -------------------------------
+__device__ __forceinline__ float gelu_f(float x) {
+  const float c = 0.7978845608028654f;
+  const float t = tanhf(c * (x + 0.044715f * x * x * x));
+  return 0.5f * x * (1.0f + t);
+}
+
+__device__ __forceinline__ float gelu_grad_f(float x) {
+  const float c = 0.7978845608028654f;
+  const float t = tanhf(c * (x + 0.044715f * x * x * x));
+  return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * c * (1.0f + 3.0f * 0.044715f * x * x);
+}
+
+// ---- parameters ------------------------------------------------------------
+__global__ void k_mlp_init(float* __restrict__ w, uint32_t k0, uint32_t k1) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kMlpParams) return;
+  // uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights from Philox, zero biases
+  float bound = 0.0f;
+  if (i < kOffB1) bound = 0.35355339f;                       // 1/sqrt(8)
+  else if (i >= kOffW2 && i < kOffB2) bound = 0.0625f;       // 1/sqrt(256)
+  else if (i >= kOffW3 && i < kOffB3) bound = 0.0625f;
+  if (bound == 0.0f) {
+    w[i] = 0.0f;
+    return;
+  }
+  const uint32_t r = philox4x32_10(static_cast<uint32_t>(i), 0u, 0u, kTagMlpInit, k0, k1).x;
+  const float v = (static_cast<float>(r >> 8) + 0.5f) * 0x1p-24f;
+  w[i] = bound * (2.0f * v - 1.0f);
+}
+
+__global__ void k_mlp_to_bf16(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kMlpParams) wb[i] = __float2bfloat16_rn(w[i]);
+}
+
+// ---- generic GEMM: C(m,n) = sum_k A(m,k) B(k,n), fp32 accumulate ---------
+// A(m,k) = A[m*sam + k*sak] (fp32); B(k,n) = B[k*sbk + n*sbn] (bf16 or fp32)
+// epilogue 0: C = acc (+ bias[n]); 1: Z = acc + bias[n], C2 = gelu(Z) too;
+//          2: C = acc * gelu'(aux(m,n))   (aux row-major with ldc)
+constexpr int kGBM = 64, kGBN = 64, kGBK = 16;
+
+template <typename TB>
+__device__ __forceinline__ float ldf(const TB* p);
+template <>
+__device__ __forceinline__ float ldf<float>(const float* p) { return *p; }
+template <>
+__device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+
+template <typename TB>
+__global__ void __launch_bounds__(256)
+k_gemm(int M, int N, int K, const float* __restrict__ A, int64_t sam, int64_t sak,
+       const TB* __restrict__ B, int64_t sbk, int64_t sbn, float* __restrict__ C, int64_t ldc,
+       const float* __restrict__ bias, int epi, const float* __restrict__ aux,
+       float* __restrict__ C2) {
+  __shared__ float As[kGBK][kGBM + 4];
+  __shared__ float Bs[kGBK][kGBN + 4];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * kGBM, n0 = blockIdx.x * kGBN;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += kGBK) {
+    for (int e = threadIdx.x; e < kGBK * kGBM; e += 256) {
+      const int kk = e / kGBM, mm = e % kGBM;
+      const int m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < M && k < K) ? A[m * sam + k * sak] : 0.0f;
+    }
+    for (int e = threadIdx.x; e < kGBK * kGBN; e += 256) {
+      const int kk = e / kGBN, nn = e % kGBN;
+      const int n = n0 + nn, k = k0 + kk;
+      Bs[kk][nn] = (n < N && k < K) ? ldf<TB>(B + k * sbk + n * sbn) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGBK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = __fmaf_rn(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty * 4 + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx * 4 + j;
+      if (n >= N) continue;
+      float v = acc[i][j];
+      if (bias) v += bias[n];
+      if (epi == 2) v *= gelu_grad_f(aux[m * ldc + n]);
+      C[m * ldc + n] = v;
+      if (epi == 1) C2[m * ldc + n] = gelu_f(v);
+    }
+  }
+}
+
+template <typename TB>
+static int gemm(int M, int N, int K, const float* A, int64_t sam, int64_t sak, const TB* B,
+                int64_t sbk, int64_t sbn, float* C, int64_t ldc, const float* bias, int epi,
+                const float* aux, float* C2, cudaStream_t st) {
+  dim3 grid(static_cast<unsigned>((N + kGBN - 1) / kGBN), static_cast<unsigned>((M + kGBM - 1) / kGBM));
+  k_gemm<TB><<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, epi, aux, C2);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+// ---- training pieces -------------------------------------------------------
+// layer 1 forward: Z1 = X W1b^T + b1, H1 = gelu(Z1); X [B][8] fp32
+__global__ void k_l1_fwd(const float* __restrict__ X, int B, const __nv_bfloat16* __restrict__ wb,
+                         const float* __restrict__ w, float* __restrict__ Z1, float* __restrict__ H1) {
+  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= static_cast<int64_t>(B) * kMlpH) return;
+  const int b = static_cast<int>(idx / kMlpH), o = static_cast<int>(idx % kMlpH);
+  float z = w[kOffB1 + o];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) z = __fmaf_rn(__bfloat162float(wb[kOffW1 + o * 8 + k]), X[b * 8 + k], z);
+  Z1[idx] = z;
+  H1[idx] = gelu_f(z);
+}
+
+// layer 3 forward and loss gradient: one warp per sample; dY = 2 (Y - T) / (4 B)
+__global__ void k_l3_fwd_loss(const float* __restrict__ H2, int B,
+                              const __nv_bfloat16* __restrict__ wb, const float* __restrict__ w,
+                              const float* __restrict__ Tg, float* __restrict__ Y,
+                              float* __restrict__ dY, float* __restrict__ loss_part) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= B) return;
+  float y[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k = lane; k < kMlpH; k += 32) {
+    const float h = H2[static_cast<int64_t>(warp) * kMlpH + k];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) y[o] = __fmaf_rn(__bfloat162float(wb[kOffW3 + o * kMlpH + k]), h, y[o]);
+  }
+#pragma unroll
+  for (int o = 0; o < 4; ++o)
+    for (int s = 16; s > 0; s >>= 1) y[o] += __shfl_xor_sync(0xffffffffu, y[o], s);
+  if (lane == 0) {
+    float l = 0.f;
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const float yo = y[o] + w[kOffB3 + o];
+      Y[warp * 4 + o] = yo;
+      if (Tg) {
+        const float e = yo - Tg[warp * 4 + o];
+        dY[warp * 4 + o] = 2.0f * e / (4.0f * static_cast<float>(B));
+        l += e * e;
+      }
+    }
+    if (Tg) loss_part[warp] = l;
+  }
+}
+
+// dZ2 = (dY W3) * gelu'(Z2)
+__global__ void k_l3_bwd(const float* __restrict__ dY, int B, const __nv_bfloat16* __restrict__ wb,
+                         const float* __restrict__ Z2, float* __restrict__ dZ2) {
+  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= static_cast<int64_t>(B) * kMlpH) return;
+  const int b = static_cast<int>(idx / kMlpH), k = static_cast<int>(idx % kMlpH);
+  float g = 0.f;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) g = __fmaf_rn(dY[b * 4 + o], __bfloat162float(wb[kOffW3 + o * kMlpH + k]), g);
+  dZ2[idx] = g * gelu_grad_f(Z2[idx]);
+}
+
+// column sums: out[n] = sum_b M[b][n] (bias gradients), one block per column
+__global__ void k_colsum(const float* __restrict__ Mx, int B, int N, float* __restrict__ out) {
+  __shared__ float sm[32];
+  const int n = blockIdx.x;
+  float s = 0.f;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) s += Mx[static_cast<int64_t>(b) * N + n];
+  s = block_sum<float>(s, sm);
+  if (threadIdx.x == 0) out[n] = s;
+}
+
+__global__ void k_sum(const float* __restrict__ x, int n, float* __restrict__ out) {
+  __shared__ float sm[32];
+  float s = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+  s = block_sum<float>(s, sm);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1,
+                       float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kMlpParams) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+size_t mlp_train_scratch_bytes(int B) {
+  // Z1, H1, Z2, H2, dZ2, dH1 [B][256]; Y, dY [B][4]; loss parts [B]; grads
+  return sizeof(float) * (6 * static_cast<size_t>(B) * kMlpH + 9 * static_cast<size_t>(B) +
+                          kMlpParams + 8) + 1024;
+}
+
+// One forward + backward pass on X [B][8], T [B][4] (standardised targets).
+// Writes the gradients into grad[kMlpParams] and the loss into *loss_dev.
+int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* grad,
+             float* loss_dev, void* scratch, size_t bytes, cudaStream_t st) {
+  if (B <= 0) return ABC_E_INVAL;
+  if (bytes < mlp_train_scratch_bytes(B)) return ABC_E_SCRATCH;
+  float* f = static_cast<float*>(scratch);
+  const size_t BH = static_cast<size_t>(B) * kMlpH;
+  float *Z1 = f, *H1 = f + BH, *Z2 = f + 2 * BH, *H2 = f + 3 * BH, *dZ2 = f + 4 * BH,
+        *dH1 = f + 5 * BH, *Y = f + 6 * BH, *dY = Y + 4 * B, *lp = dY + 4 * B;
+  const __nv_bfloat16* wb = s.wb;
+  const unsigned g1 = static_cast<unsigned>((BH + 255) / 256);
+  k_l1_fwd<<<g1, 256, 0, st>>>(X, B, wb, s.w, Z1, H1);
+  ABC_LAUNCH_CHECK();
+  int rc;
+  // Z2 = H1 W2^T + b2 (B(k,n) = W2[n][k]), H2 = gelu(Z2)
+  if ((rc = gemm<__nv_bfloat16>(B, kMlpH, kMlpH, H1, kMlpH, 1, wb + kOffW2, 1, kMlpH, Z2, kMlpH,
+                                s.w + kOffB2, 1, nullptr, H2, st)))
+    return rc;
+  k_l3_fwd_loss<<<static_cast<unsigned>((B * 32 + 255) / 256), 256, 0, st>>>(H2, B, wb, s.w, T, Y,
+                                                                               dY, lp);
+  ABC_LAUNCH_CHECK();
+  k_sum<<<1, 1024, 0, st>>>(lp, B, loss_dev);
+  ABC_LAUNCH_CHECK();
+  // layer 3 gradients: gW3[o][k] = sum_b dY[b][o] H2[b][k]  (M = 4, N = 256, K = B)
+  if ((rc = gemm<float>(4, kMlpH, B, dY, 1, 4, H2, kMlpH, 1, grad + kOffW3, kMlpH, nullptr, 0,
+                        nullptr, nullptr, st)))
+    return rc;
+  k_colsum<<<4, 256, 0, st>>>(dY, B, 4, grad + kOffB3);
+  ABC_LAUNCH_CHECK();
+  k_l3_bwd<<<g1, 256, 0, st>>>(dY, B, wb, Z2, dZ2);
+  ABC_LAUNCH_CHECK();
+  // gW2 = dZ2^T H1 (M = 256, N = 256, K = B)
+  if ((rc = gemm<float>(kMlpH, kMlpH, B, dZ2, 1, kMlpH, H1, kMlpH, 1, grad + kOffW2, kMlpH, nullptr,
+                        0, nullptr, nullptr, st)))
+    return rc;
+  k_colsum<<<kMlpH, 256, 0, st>>>(dZ2, B, kMlpH, grad + kOffB2);
+  ABC_LAUNCH_CHECK();
+  // dZ1 = (dZ2 W2) * gelu'(Z1)  (B(k,n) = W2[k][n])
+  if ((rc = gemm<__nv_bfloat16>(B, kMlpH, kMlpH, dZ2, kMlpH, 1, wb + kOffW2, kMlpH, 1, dH1, kMlpH,
+                                nullptr, 2, Z1, nullptr, st)))
+    return rc;
+  // gW1 = dZ1^T X (M = 256, N = 8, K = B)
+  if ((rc = gemm<float>(kMlpH, 8, B, dH1, 1, kMlpH, X, 8, 1, grad + kOffW1, 8, nullptr, 0, nullptr,
+                        nullptr, st)))
+    return rc;
+  k_colsum<<<kMlpH, 256, 0, st>>>(dH1, B, kMlpH, grad + kOffB1);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+int mlp_adam(const MlpState& s, const float* grad, int64_t step, float lr, cudaStream_t st) {
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float c1 = 1.0f - std::pow(b1, static_cast<float>(step));
+  const float c2 = 1.0f - std::pow(b2, static_cast<float>(step));
+  const unsigned g = (kMlpParams + 255) / 256;
+  k_adam<<<g, 256, 0, st>>>(s.w, grad, s.m, s.v, lr, b1, b2, eps, c1, c2);
+  ABC_LAUNCH_CHECK();
+  k_mlp_to_bf16<<<g, 256, 0, st>>>(s.w, s.wb);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+int mlp_init(const MlpState& s, uint32_t k0, uint32_t k1, cudaStream_t st) {
+  const unsigned g = (kMlpParams + 255) / 256;
+  k_mlp_init<<<g, 256, 0, st>>>(s.w, k0, k1);
+  ABC_LAUNCH_CHECK();
+  ABC_CUDA_TRY(cudaMemsetAsync(s.m, 0, sizeof(float) * kMlpParams, st));
+  ABC_CUDA_TRY(cudaMemsetAsync(s.v, 0, sizeof(float) * kMlpParams, st));
+  k_mlp_to_bf16<<<g, 256, 0, st>>>(s.w, s.wb);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+int mlp_refresh_bf16(const MlpState& s, cudaStream_t st) {
+  k_mlp_to_bf16<<<(kMlpParams + 255) / 256, 256, 0, st>>>(s.w, s.wb);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+
+// ---- inference on tensor cores ------------------------------------------------
+constexpr int kMlpM = 128;                                  // samples per CTA
+constexpr uint32_t kMlpATile = kMlpM * kMlpH * 2;           // 64 KB: h1 tile
+constexpr uint32_t kMlpBBytes = kMlpH * kMlpH * 2;          // 128 KB: W2
+constexpr size_t kMlpSmem = 1024 + kMlpATile + kMlpBBytes + (4 * kMlpH + kMlpH) * 4 + 256;
+constexpr uint32_t kMlpIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                               (static_cast<uint32_t>(kMlpH >> 3) << 17) |
+                               (static_cast<uint32_t>(kMlpM >> 4) << 24);
+
+// element index of (row r, k) in a K = 256 tile: 8 x 8 core matrices, the 32
+// of a row group consecutive along K (LBO 128 B), row groups 4096 B apart
+__host__ __device__ __forceinline__ int mlp_packed_index(int r, int k) {
+  return ((((r >> 3) << 5) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
+// layer 1 + GELU for n samples (u [8][n]) into packed bf16 tiles of h1
+__global__ void k_mlp_l1_pack(const float* __restrict__ u, int64_t n, int64_t npad,
+                              const __nv_bfloat16* __restrict__ wb, const float* __restrict__ w,
+                              __nv_bfloat16* __restrict__ Hpk) {
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= npad) return;
+  float x[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) x[d] = j < n ? u[d * n + j] : 0.0f;
+  __nv_bfloat16* tile = Hpk + (j / kMlpM) * (kMlpM * kMlpH);
+  const int r = static_cast<int>(j % kMlpM);
+  for (int c = 0; c < kMlpH / 8; ++c) {
+    uint32_t h[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int o = 8 * c + e;
+      float z = w[kOffB1 + o];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) z = __fmaf_rn(__bfloat162float(wb[kOffW1 + o * 8 + k]), x[k], z);
+      h[e] = __bfloat16_as_ushort(__float2bfloat16_rn(j < n ? gelu_f(z) : 0.0f));
+    }
+    uint4 v;
+    v.x = h[0] | (h[1] << 16);
+    v.y = h[2] | (h[3] << 16);
+    v.z = h[4] | (h[5] << 16);
+    v.w = h[6] | (h[7] << 16);
+    *reinterpret_cast<uint4*>(tile + mlp_packed_index(r, 8 * c)) = v;
+  }
+}
+
+// W2 (bf16, [out][in]) as the B operand: rows = out, K = in
+__global__ void k_mlp_pack_w2(const __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ W2pk) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kMlpH * kMlpH) return;
+  const int o = idx / kMlpH, k = idx % kMlpH;
+  W2pk[mlp_packed_index(o, k)] = wb[kOffW2 + o * kMlpH + k];
+}
+
+// Y[j][0..3] = W3 gelu(W2 h1_j + b2) + b3 for 128 samples per CTA
+__global__ void __launch_bounds__(192, 1)
+k_mlp_tc(const uint8_t* __restrict__ Hpk, const uint8_t* __restrict__ W2pk,
+         const float* __restrict__ w, const __nv_bfloat16* __restrict__ wb, int64_t n,
+         float* __restrict__ Y, unsigned* err) {
+  extern __shared__ uint8_t mlp_smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(mlp_smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint8_t* sA = base;
+  uint8_t* sB = base + kMlpATile;
+  float* sW3 = reinterpret_cast<float*>(sB + kMlpBBytes);
+  float* sb2 = sW3 + 4 * kMlpH;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sb2 + kMlpH);
+  uint64_t* full = bars;
+  uint64_t* tfull = bars + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < 4 * kMlpH; i += blockDim.x) sW3[i] = __bfloat162float(wb[kOffW3 + i]);
+  for (int i = threadIdx.x; i < kMlpH; i += blockDim.x) sb2[i] = w[kOffB2 + i];
+  if (threadIdx.x == 0) {
+    mbar_init(full, 1);
+    mbar_init(tfull, 1);
+    fence_mbar_init();
+  }
+  if (warp == 5) {
+    tmem_alloc(tmem_slot, kMlpH);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (warp == 4) {
+    if (lane == 0) {
+      mbar_expect_tx(full, kMlpATile + kMlpBBytes);
+      bulk_g2s(sA, Hpk + static_cast<size_t>(blockIdx.x) * kMlpATile, kMlpATile, full);
+      bulk_g2s(sB, W2pk, kMlpBBytes, full);
+      mbar_wait(full, 0u, err, 21u);  // both copies landed before the CTA can exit
+    }
+  } else if (warp == 5) {
+    if (lane == 0 && mbar_wait(full, 0u, err, 22u)) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+      for (int kk = 0; kk < kMlpH / 16; ++kk)
+        umma_bf16(tmem, smem_desc(a0 + kk * 256, 128, 4096), smem_desc(b0 + kk * 256, 128, 4096),
+                  kMlpIdesc, kk > 0 ? 1u : 0u);
+      umma_commit(tfull);
+      mbar_wait(tfull, 0u, err, 23u);
+    }
+    __syncwarp();
+  } else {
+    // tcgen05.ld is warp-collective: the whole warp reads or none of it
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull, 0u, err, 24u));
+    tc_fence_after();
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * kMlpM + threadIdx.x;
+    float y[4] = {0.f, 0.f, 0.f, 0.f};
+    if (ok) {
+      for (int c = 0; c < kMlpH / 32; ++c) {
+        float v[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = c * 32 + i;
+          const float h = gelu_f(v[i] + sb2[col]);
+#pragma unroll
+          for (int o = 0; o < 4; ++o) y[o] = __fmaf_rn(h, sW3[o * kMlpH + col], y[o]);
+        }
+      }
+    }
+    if (j < n) {
+#pragma unroll
+      for (int o = 0; o < 4; ++o) Y[j * 4 + o] = y[o] + w[kOffB3 + o];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 5) tmem_dealloc(tmem, kMlpH);
+}
+
+size_t mlp_infer_scratch_bytes(int64_t n) {
+  const int64_t npad = ceil_div(std::max<int64_t>(n, 1), kMlpM) * kMlpM;
+  return align256(static_cast<size_t>(npad) * kMlpH * 2) + align256(kMlpBBytes) + align256(16);
+}
+
+int mlp_infer_prepare() {
+  ABC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(kMlpSmem)));
+  return ABC_OK;
+}
+
+// Y [n][4] (standardised outputs) for u [8][n]; the error word lives in scratch
+int mlp_infer(const MlpState& s, const float* u, int64_t n, float* Y, void* scratch, size_t bytes,
+              unsigned** err_out, cudaStream_t st) {
+  if (n <= 0) return ABC_OK;
+  if (bytes < mlp_infer_scratch_bytes(n)) return ABC_E_SCRATCH;
+  const int64_t npad = ceil_div(n, kMlpM) * kMlpM;
+  char* b = static_cast<char*>(scratch);
+  auto* Hpk = reinterpret_cast<__nv_bfloat16*>(b);
+  auto* W2pk = reinterpret_cast<__nv_bfloat16*>(b + align256(static_cast<size_t>(npad) * kMlpH * 2));
+  auto* err = reinterpret_cast<unsigned*>(b + align256(static_cast<size_t>(npad) * kMlpH * 2) +
+                                          align256(kMlpBBytes));
+  if (err_out) *err_out = err;
+  ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
+  k_mlp_pack_w2<<<(kMlpH * kMlpH + 255) / 256, 256, 0, st>>>(s.wb, W2pk);
+  ABC_LAUNCH_CHECK();
+  k_mlp_l1_pack<<<static_cast<unsigned>(ceil_div(npad, 128)), 128, 0, st>>>(u, n, npad, s.wb, s.w,
+                                                                           Hpk);
+  ABC_LAUNCH_CHECK();
+  k_mlp_tc<<<static_cast<unsigned>(npad / kMlpM), 192, kMlpSmem, st>>>(
+      reinterpret_cast<const uint8_t*>(Hpk), reinterpret_cast<const uint8_t*>(W2pk), s.w, s.wb, n,
+      Y, err);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+// ---- screening (delayed acceptance) ---------------------------------------------
+// For each proposal with pflag 0: y0 = mean + std * Y[i][0] predicts log1p d;
+// rho = clamp(1 / (1 + exp(-(log1p eps - y0) / tau)), rho_min, 1) in fp32
+// with the library's own exp and log1p (every step correctly rounded, so the
+// decision is reproducible off the device); simulated and acceptable when
+// U < rho (SCREEN stream), else simulated for the audit with probability
+// audit_frac (AUDIT stream) and never accepted.
+// sflag: 0 acceptable, 1 exhausted (not simulated), 2 audit only, 3 screened out
+__device__ __forceinline__ float screen_rho(float y, const float* ystat, float le, float tau,
+                                            float rho_min) {
+  const float y0 = __fadd_rn(ystat[0], __fmul_rn(ystat[4], y));
+  const float z = __fdiv_rn(__fsub_rn(le, y0), tau);
+  const float r = __fdiv_rn(1.0f, __fadd_rn(1.0f, dev_exp(-z)));
+  return fminf(fmaxf(r, rho_min), 1.0f);  // a NaN prediction gets rho_min
+}
+
+__global__ void k_screen(const float* __restrict__ Y, const float* __restrict__ ystat,
+                         const uint8_t* __restrict__ pflag, int64_t M, const double* eps_p,
+                         uint32_t k0, uint32_t k1, uint32_t c1, float tau, float rho_min,
+                         float audit_frac, float* __restrict__ rho, uint8_t* __restrict__ sflag,
+                         unsigned long long* __restrict__ exhausted) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool ex = i < M && pflag && pflag[i];
+  if (exhausted) {
+    const unsigned nx = __popc(__ballot_sync(0xffffffffu, ex));
+    if ((threadIdx.x & 31) == 0 && nx) atomicAdd(exhausted, static_cast<unsigned long long>(nx));
+  }
+  if (i >= M) return;
+  if (ex) {
+    sflag[i] = 1;
+    rho[i] = 1.0f;
+    return;
+  }
+  const float le = dev_log1p(__double2float_rn(*eps_p));
+  const float r = screen_rho(Y[i * 4], ystat, le, tau, rho_min);
+  rho[i] = r;
+  const float u1 = unif(philox4x32_10(static_cast<uint32_t>(i), c1, 0u, kTagScreen, k0, k1).x);
+  if (u1 < r) {
+    sflag[i] = 0;
+    return;
+  }
+  const float u2 = unif(philox4x32_10(static_cast<uint32_t>(i), c1, 0u, kTagAudit, k0, k1).x);
+  sflag[i] = u2 < audit_frac ? 2 : 3;
+}
+
+int screen(const float* Y, const float* ystat, const uint8_t* pflag, int64_t M, const double* eps,
+           uint32_t k0, uint32_t k1, uint32_t c1, float tau, float rho_min, float audit_frac,
+           float* rho, uint8_t* sflag, cudaStream_t st, unsigned long long* exhausted) {
+  if (M <= 0) return ABC_OK;
+  k_screen<<<static_cast<unsigned>(ceil_div(M, 256)), 256, 0, st>>>(Y, ystat, pflag, M, eps, k0, k1,
+                                                                     c1, tau, rho_min, audit_frac,
+                                                                     rho, sflag, exhausted);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+// compaction of the simulated slots (sflag 0 or 2), in slot order
+constexpr int kCTile = 1024;
+
+__global__ void k_cmp_count(const uint8_t* __restrict__ sflag, int64_t M, int* __restrict__ cnt) {
+  __shared__ int sm[32];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kCTile + 4 * threadIdx.x;
+  int c = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) c += (base + e < M && (sflag[base + e] == 0 || sflag[base + e] == 2));
+  c = block_sum<int>(c, sm);
+  if (threadIdx.x == 0) cnt[blockIdx.x] = c;
+}
+
+__global__ void k_cmp_scan(const int* __restrict__ cnt, int ntiles, int* __restrict__ off,
+                           int* __restrict__ total) {
+  __shared__ int sm[32];
+  __shared__ int last;
+  int carry = 0;
+  for (int b = 0; b < ntiles; b += blockDim.x) {
+    const int i = b + threadIdx.x;
+    const int v = i < ntiles ? cnt[i] : 0;
+    const int inc = block_incl_scan<int>(v, sm);
+    if (i < ntiles) off[i] = carry + inc - v;
+    if (threadIdx.x == blockDim.x - 1) last = inc;
+    __syncthreads();
+    carry += last;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_cmp_scatter(const uint8_t* __restrict__ sflag, int64_t M, const int* __restrict__ off,
+                              const float* __restrict__ up, const float* __restrict__ sp,
+                              const int32_t* __restrict__ ap, const float* __restrict__ rho,
+                              float* __restrict__ cu, float* __restrict__ cs,
+                              int32_t* __restrict__ ca, float* __restrict__ crho,
+                              uint8_t* __restrict__ cflag, uint32_t* __restrict__ cslot,
+                              const int* __restrict__ Mc_dev) {
+  __shared__ int sm[32];
+  // the compacted list is [8][Mc] with stride Mc, the layout every consumer
+  // (simulator, acceptance, training ring) reads with n = Mc
+  const int64_t stride = *Mc_dev;
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kCTile + 4 * threadIdx.x;
+  bool keep[4];
+  int c = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    keep[e] = base + e < M && (sflag[base + e] == 0 || sflag[base + e] == 2);
+    c += keep[e];
+  }
+  const int inc = block_incl_scan<int>(c, sm);
+  int64_t pos = off[blockIdx.x] + inc - c;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (!keep[e]) continue;
+    const int64_t i = base + e;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) cu[d * stride + pos] = up[d * M + i];
+    cs[pos] = sp[i];
+    ca[pos] = ap[i];
+    crho[pos] = rho[i];
+    cflag[pos] = sflag[i];
+    cslot[pos] = static_cast<uint32_t>(i);
+    ++pos;
+  }
+}
+
+int screen_and_compact(const float* Y, const float* ystat, const uint8_t* pflag, int64_t M,
+                       const double* eps, uint32_t k0, uint32_t k1, uint32_t c1, float tau,
+                       float rho_min, float audit_frac, float* rho, uint8_t* sflag,
+                       const float* up, const float* sp, const int32_t* ap, float* cu, float* cs,
+                       int32_t* ca, float* crho, uint8_t* cflag, uint32_t* cslot, int* Mc_dev,
+                       void* scratch, cudaStream_t st, unsigned long long* exhausted) {
+  const int64_t nt = ceil_div(M, kCTile);
+  int* cnt = static_cast<int*>(scratch);
+  int* off = cnt + align256(4 * nt) / 4;
+  int rc = screen(Y, ystat, pflag, M, eps, k0, k1, c1, tau, rho_min, audit_frac, rho, sflag, st,
+                  exhausted);
+  if (rc) return rc;
+  k_cmp_count<<<static_cast<unsigned>(nt), 256, 0, st>>>(sflag, M, cnt);
+  ABC_LAUNCH_CHECK();
+  k_cmp_scan<<<1, 1024, 0, st>>>(cnt, static_cast<int>(nt), off, Mc_dev);
+  ABC_LAUNCH_CHECK();
+  k_cmp_scatter<<<static_cast<unsigned>(nt), 256, 0, st>>>(sflag, M, off, up, sp, ap, rho, cu, cs, ca,
+                                                           crho, cflag, cslot, Mc_dev);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+size_t screen_scratch_bytes(int64_t M) { return 2 * align256(4 * ceil_div(std::max<int64_t>(M, 1), kCTile)); }
+
+// ---- training data ring ----------------------------------------------------------
+// Appends n simulated samples (u [8][n] stride n, d, final A, R, D [3][n])
+// as x = u and y = [log1p d, log1p A_T, log1p R_T, log1p D_T] at ring
+// positions (*head + i) mod cap; valid (nullable) selects samples in order.
+__global__ void k_ring_count(const uint8_t* __restrict__ invalid, int64_t n, int* __restrict__ cnt) {
+  __shared__ int sm[32];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kCTile + 4 * threadIdx.x;
+  int c = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) c += (base + e < n && (!invalid || invalid[base + e] == 0));
+  c = block_sum<int>(c, sm);
+  if (threadIdx.x == 0) cnt[blockIdx.x] = c;
+}
+
+__global__ void k_ring_put(const uint8_t* __restrict__ invalid, int64_t n, const int* __restrict__ off,
+                           const float* __restrict__ u, const double* __restrict__ d,
+                           const int32_t* __restrict__ ard, const long long* __restrict__ head,
+                           int64_t cap, float* __restrict__ RX, float* __restrict__ RY) {
+  __shared__ int sm[32];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kCTile + 4 * threadIdx.x;
+  bool keep[4];
+  int c = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    keep[e] = base + e < n && (!invalid || invalid[base + e] == 0);
+    c += keep[e];
+  }
+  const int inc = block_incl_scan<int>(c, sm);
+  int64_t pos = off[blockIdx.x] + inc - c;
+  const long long h = *head;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (!keep[e]) continue;
+    const int64_t i = base + e;
+    const int64_t r = (h + pos) % cap;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) RX[r * 8 + k] = u[k * n + i];
+    RY[r * 4 + 0] = static_cast<float>(log1p(d[i]));
+    RY[r * 4 + 1] = log1pf(static_cast<float>(ard[0 * n + i]));
+    RY[r * 4 + 2] = log1pf(static_cast<float>(ard[1 * n + i]));
+    RY[r * 4 + 3] = log1pf(static_cast<float>(ard[2 * n + i]));
+    ++pos;
+  }
+}
+
+__global__ void k_ring_advance(long long* head, const int* added) { *head += *added; }
+
+int ring_append(const uint8_t* invalid, int64_t n, const float* u, const double* d,
+                const int32_t* ard, long long* head, int64_t cap, float* RX, float* RY,
+                void* scratch, cudaStream_t st) {
+  if (n <= 0) return ABC_OK;
+  const int64_t nt = ceil_div(n, kCTile);
+  int* cnt = static_cast<int*>(scratch);
+  int* off = cnt + align256(4 * nt) / 4;
+  int* added = off + align256(4 * nt) / 4;
+  k_ring_count<<<static_cast<unsigned>(nt), 256, 0, st>>>(invalid, n, cnt);
+  ABC_LAUNCH_CHECK();
+  k_cmp_scan<<<1, 1024, 0, st>>>(cnt, static_cast<int>(nt), off, added);
+  ABC_LAUNCH_CHECK();
+  k_ring_put<<<static_cast<unsigned>(nt), 256, 0, st>>>(invalid, n, off, u, d, ard, head, cap, RX, RY);
+  ABC_LAUNCH_CHECK();
+  k_ring_advance<<<1, 1, 0, st>>>(head, added);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+size_t ring_scratch_bytes(int64_t n) { return 3 * align256(4 * ceil_div(std::max<int64_t>(n, 1), kCTile)); }
+
+// mean and standard deviation of each output over the filled ring (fp64)
+__global__ void k_ring_stats(const float* __restrict__ RY, const long long* __restrict__ head,
+                             int64_t cap, float* __restrict__ ystat) {
+  __shared__ double sm[32];
+  const int64_t m = *head < cap ? *head : cap;
+  for (int o = 0; o < 4; ++o) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+      const double y = RY[i * 4 + o];
+      s1 += y;
+      s2 += y * y;
+    }
+    s1 = block_sum<double>(s1, sm);
+    s2 = block_sum<double>(s2, sm);
+    if (threadIdx.x == 0) {
+      const double mean = m > 0 ? s1 / static_cast<double>(m) : 0.0;
+      const double var = m > 1 ? s2 / static_cast<double>(m) - mean * mean : 1.0;
+      ystat[o] = static_cast<float>(mean);
+      ystat[4 + o] = static_cast<float>(var > 1e-12 ? sqrt(var) : 1.0);
+    }
+    __syncthreads();
+  }
+}
+
+// a minibatch of B samples drawn uniformly from the filled ring (TRAIN stream)
+__global__ void k_ring_batch(const float* __restrict__ RX, const float* __restrict__ RY,
+                             const long long* __restrict__ head, int64_t cap,
+                             const float* __restrict__ ystat, int B, uint32_t step, uint32_t k0,
+                             uint32_t k1, float* __restrict__ X, float* __restrict__ T) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  const int64_t m = *head < cap ? *head : cap;
+  const u32x4 r = philox4x32_10(static_cast<uint32_t>(i), step, 0u, kTagTrain, k0, k1);
+  const uint64_t U = (static_cast<uint64_t>(r.y) << 32) | r.x;
+  const int64_t src = m > 0 ? static_cast<int64_t>(__umul64hi(U, static_cast<uint64_t>(m))) : 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) X[i * 8 + k] = RX[src * 8 + k];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) T[i * 4 + o] = (RY[src * 4 + o] - ystat[o]) / ystat[4 + o];
+}
+
+int mlp_train(const MlpState& s, const float* RX, const float* RY, const long long* head,
+              int64_t cap, const float* ystat, int B, int steps, uint32_t step0, float lr,
+              uint32_t k0, uint32_t k1, float* grad, float* X, float* T, float* loss_dev,
+              void* scratch, size_t bytes, cudaStream_t st) {
+  int rc;
+  for (int k = 0; k < steps; ++k) {
+    k_ring_batch<<<(B + 255) / 256, 256, 0, st>>>(RX, RY, head, cap, ystat, B, step0 + k, k0, k1, X, T);
+    ABC_LAUNCH_CHECK();
+    if ((rc = mlp_grad(s, X, T, B, grad, loss_dev, scratch, bytes, st))) return rc;
+    if ((rc = mlp_adam(s, grad, static_cast<int64_t>(step0) + k + 1, lr, st))) return rc;
+  }
+  return ABC_OK;
+}
+
+// audited (cflag 2) and audited-with-d<=eps counts over the compacted list
+__global__ void k_audit_count(const uint8_t* __restrict__ cflag, const double* __restrict__ cd,
+                              const int* __restrict__ Mc, const double* __restrict__ eps_p,
+                              unsigned long long* __restrict__ counts) {
+  const double eps = *eps_p;
+  const int m = *Mc;
+  unsigned long long a = 0, b = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    if (cflag[i] == 2) {
+      ++a;
+      b += cd[i] <= eps;
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (a || b)) {
+    atomicAdd(&counts[0], a);
+    atomicAdd(&counts[1], b);
+  }
+}
+
+int audit_count(const uint8_t* cflag, const double* cd, const int* Mc, const double* eps,
+                unsigned long long* counts, cudaStream_t st) {
+  k_audit_count<<<152, 256, 0, st>>>(cflag, cd, Mc, eps, counts);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+// delayed-acceptance correction of importance weights: log W -= log rho
+__global__ void k_rho_correct(double* __restrict__ logW, const float* __restrict__ rho, int64_t n) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) logW[i] -= log(static_cast<double>(rho[i]));
+}
+
+int rho_correct(double* logW, const float* rho, int64_t n, cudaStream_t st) {
+  k_rho_correct<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, st>>>(logW, rho, n);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+int ring_stats(const float* RY, const long long* head, int64_t cap, float* ystat, cudaStream_t st) {
+  k_ring_stats<<<1, 1024, 0, st>>>(RY, head, cap, ystat);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+}  // namespace abc

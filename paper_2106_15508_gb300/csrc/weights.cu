@@ -27,10 +27,14 @@ __global__ void __launch_bounds__(kWThreads)
 k_weights_fp32(const float* __restrict__ up, const float* __restrict__ s, int64_t rows,
                const float* __restrict__ cu, const float* __restrict__ cc,
                const int* __restrict__ nc_p, int64_t ncap, int64_t chunk_cols,
-               float2* __restrict__ part, const int* __restrict__ off_dev) {
+               float2* __restrict__ part, const int* __restrict__ off_dev,
+               const int* __restrict__ rows_dev) {
   __shared__ float su[8][kWTile];
   __shared__ float sc[kWTile];
   if (off_dev && *off_dev) return;  // run finished or its generation stopped
+  // rows is the stride (capacity); rows_dev, when given, the rows in use
+  const int64_t nrows = rows_dev ? static_cast<int64_t>(*rows_dev) : rows;
+  if (static_cast<int64_t>(blockIdx.x) * (kWThreads * kWRows) >= nrows) return;
   const int64_t nc = *nc_p;
   const int64_t c_begin = static_cast<int64_t>(blockIdx.y) * chunk_cols;
   const int64_t c_end = nc < c_begin + chunk_cols ? nc : c_begin + chunk_cols;
@@ -39,7 +43,7 @@ k_weights_fp32(const float* __restrict__ up, const float* __restrict__ s, int64_
 #pragma unroll
   for (int r = 0; r < kWRows; ++r) {
     const int64_t j = row0 + r * kWThreads;
-    const bool live = j < rows;
+    const bool live = j < nrows;
     // kernel variance floored at 1e-30 so that 1/(2 s) stays finite
     const float sj = live ? fmaxf(s[j], kSMin) : 1.0f;
 #pragma unroll
@@ -99,16 +103,16 @@ k_weights_fp32(const float* __restrict__ up, const float* __restrict__ s, int64_
 #pragma unroll
   for (int r = 0; r < kWRows; ++r) {
     const int64_t j = row0 + r * kWThreads;
-    if (j < rows) part[static_cast<int64_t>(blockIdx.y) * rows + j] = make_float2(m[r], S[r]);
+    if (j < nrows) part[static_cast<int64_t>(blockIdx.y) * rows + j] = make_float2(m[r], S[r]);
   }
 }
 
 __global__ void k_weights_combine(const float2* __restrict__ part, int nchunks,
                                   const float* __restrict__ s, int64_t rows,
                                   const uint64_t* __restrict__ total_p, double* __restrict__ logW,
-                                  const int* __restrict__ off_dev) {
+                                  const int* __restrict__ off_dev, const int* __restrict__ rows_dev) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= rows || (off_dev && *off_dev)) return;
+  if (j >= (rows_dev ? static_cast<int64_t>(*rows_dev) : rows) || (off_dev && *off_dev)) return;
   const double sj = static_cast<double>(fmaxf(s[j], kSMin));
   double M = -INFINITY;
   for (int c = 0; c < nchunks; ++c) M = fmax(M, static_cast<double>(part[static_cast<int64_t>(c) * rows + j].x));
@@ -138,7 +142,7 @@ size_t weights_fp32_scratch_bytes(int64_t rows, int64_t ncap, int mult) {
 int launch_weights_fp32(const float* up, const float* s, int64_t rows, const float* cu,
                         const float* cc, const int* nc_dev, int64_t ncap,
                         const uint64_t* total_p, double* logW, void* scratch, size_t bytes,
-                        cudaStream_t st, const int* off_dev, int mult) {
+                        cudaStream_t st, const int* off_dev, int mult, const int* rows_dev) {
   if (rows <= 0) return ABC_OK;
   if (bytes < weights_fp32_scratch_bytes(rows, ncap, mult)) return ABC_E_SCRATCH;
   const int nch = weight_chunks(rows, ncap, mult);
@@ -146,10 +150,11 @@ int launch_weights_fp32(const float* up, const float* s, int64_t rows, const flo
   float2* part = static_cast<float2*>(scratch);
   dim3 grid(static_cast<unsigned>(ceil_div(rows, kWThreads * kWRows)), static_cast<unsigned>(nch));
   k_weights_fp32<<<grid, kWThreads, 0, st>>>(up, s, rows, cu, cc, nc_dev, ncap, chunk_cols, part,
-                                             off_dev);
+                                             off_dev, rows_dev);
   ABC_LAUNCH_CHECK();
   k_weights_combine<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(part, nch, s, rows,
-                                                                                total_p, logW, off_dev);
+                                                                                total_p, logW, off_dev,
+                                                                                rows_dev);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

@@ -3,8 +3,8 @@
 //   log W_j = 4 ln(2 pi s_j) - ln sum_k (q_k / total) exp(-|u'_j - u_k|^2 / (2 s_j))
 //
 // The exponent (base 2) of every pair is an inner product of a row feature
-// vector and a column feature vector.  With centred coordinates x = u' - 1/2,
-// y = u - 1/2 and L_j = log2(e) / (2 s_j):
+// vector and a column feature vector.  With coordinates centred on the mean
+// m of the survivor columns, x = u' - m, y = u - m, and L_j = log2(e) / (2 s_j):
 //   e_jk = [2 L_j x_j, -L_j, 1] . [y_k, |y_k|^2, c_k]   (10 features)
 //          - L_j |x_j|^2                               (row constant, fp64)
 // with c_k = log2(q_k) - 32.  A single bf16 copy of these features would
@@ -13,7 +13,9 @@
 // significant bits) and the six products with i + j <= 2 are kept: K = 60
 // used of 64.  Products of bf16 values are exact and accumulate in fp32 in
 // tensor memory, so the remaining error is the fp32 accumulation of terms of
-// size ~L_j |y|^2 (stated in the tests, not a parity gate).
+// size L_j (2 |x_j| |y| + |y|^2); centring on the cloud keeps |x| and |y| at
+// its spread.  Rows whose error bound exceeds kTcBoundMax go through the FP32
+// direct-difference kernel instead (see the split below).
 //
 // Kernel structure (one CTA = 128 rows, one SM):
 //   warp 4  : bulk-copy producer (cp.async.bulk, mbarrier complete_tx):
@@ -33,6 +35,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace abc {
 
@@ -58,148 +61,6 @@ constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
 // element index of (row r, k) inside a packed tile
 __host__ __device__ __forceinline__ int packed_index(int r, int k) {
   return ((((r >> 3) << 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
-}
-
-// ---- PTX wrappers -----------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// wait for the phase of the given parity; gives up after ~2 s and records
-// the failure (code) in *err
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err,
-                                          unsigned code) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > 2000000000ull) {
-      atomicCAS(err, 0u, code);
-      return false;
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                   smem_u32(slot)),
-               "r"(ncols)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// shared-memory matrix descriptor: start >> 4 (bits 0-13), leading byte
-// offset >> 4 (16-29), stride byte offset >> 4 (32-45), the fixed 0b001 at
-// bits 46-48, base offset 0, relative LBO, no swizzle (bits 61-63 = 0)
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
-  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
-  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
-  d |= 1ull << 46;
-  return d;
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-// 32 consecutive fp32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ float ex2(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
 }
 
 // ---- operand packing -------------------------------------------------------
@@ -245,18 +106,20 @@ __device__ __forceinline__ void store_packed_row(__nv_bfloat16* tile, int r, con
 
 // rows: features [2 L x (8), -L, 1]; rowc[j] = -L |x|^2 (fp64)
 __global__ void k_tc_pack_rows(const float* __restrict__ up, const float* __restrict__ s,
-                               int64_t rows, int64_t rows_pad, __nv_bfloat16* __restrict__ Apk,
-                               double* __restrict__ rowc) {
+                               int64_t rows, int64_t rows_pad, const float* __restrict__ centre,
+                               __nv_bfloat16* __restrict__ Apk, double* __restrict__ rowc,
+                               const int* __restrict__ rows_dev) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= rows_pad) return;
+  const int64_t nrows = rows_dev ? static_cast<int64_t>(*rows_dev) : rows;
   float f[10];
-  if (j < rows) {
+  if (j < nrows) {
     const float sj = fmaxf(s[j], kSMinTc);
     const float L = 1.4426950408889634f / (2.0f * sj);
     double xx = 0.0;
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
-      const float x = up[static_cast<int64_t>(d) * rows + j] - 0.5f;
+      const float x = up[static_cast<int64_t>(d) * rows + j] - centre[d];
       f[d] = 2.0f * L * x;
       xx += static_cast<double>(x) * static_cast<double>(x);
     }
@@ -270,23 +133,69 @@ __global__ void k_tc_pack_rows(const float* __restrict__ up, const float* __rest
   store_packed_row<true>(Apk + (j / kTcM) * (kTcM * kTcK), static_cast<int>(j % kTcM), f);
 }
 
-// columns: features [y (8), |y|^2, c_k]; columns at or beyond nc are padding
-// with c = -1e30 (their exponentials vanish)
+// centre of the survivor columns: per-block fp64 sums in a fixed order
+// (block b takes columns b * 256 + t + i * 256 * gridDim), then one block
+// adds the partial sums in block order, so the centre is deterministic
+constexpr int kCtrBlocks = 152;
+
+__global__ void k_col_sum(const float* __restrict__ cu, const int* __restrict__ nc_p, int64_t ncap,
+                          double* __restrict__ part) {
+  __shared__ double sm[32];
+  const int64_t nc = *nc_p;
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < nc;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x)
+#pragma unroll
+    for (int d = 0; d < 8; ++d) acc[d] += static_cast<double>(cu[static_cast<int64_t>(d) * ncap + k]);
+#pragma unroll 1
+  for (int d = 0; d < 8; ++d) {
+    const double v = block_sum<double>(acc[d], sm);
+    if (threadIdx.x == 0) part[blockIdx.x * 8 + d] = v;
+  }
+}
+
+// centre[d] = mean over the nc columns (1/2 when there are none); clears the
+// radius word that the column packing raises
+__global__ void k_col_centre(const double* __restrict__ part, int nparts,
+                             const int* __restrict__ nc_p, float* __restrict__ centre,
+                             unsigned* __restrict__ y2max) {
+  const int d = threadIdx.x;
+  if (d == 0) *y2max = 0u;
+  if (d >= 8) return;
+  double acc = 0.0;
+  for (int b = 0; b < nparts; ++b) acc += part[b * 8 + d];
+  const int nc = *nc_p;
+  centre[d] = nc > 0 ? static_cast<float>(acc / static_cast<double>(nc)) : 0.5f;
+}
+
+// columns: features [y (8), |y|^2, c_k] with y = u - centre; columns at or
+// beyond nc are padding with c = -1e30 (their exponentials vanish).  y2max
+// receives max_k |y_k|^2 (bit pattern of a non-negative float).
 __global__ void k_tc_pack_cols(const float* __restrict__ cu, const float* __restrict__ cc,
                                const int* __restrict__ nc_p, int64_t ncap, int64_t cols_pad,
-                               __nv_bfloat16* __restrict__ Bpk) {
+                               const float* __restrict__ centre, __nv_bfloat16* __restrict__ Bpk,
+                               unsigned* __restrict__ y2max) {
   const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (k >= cols_pad) return;
   const int64_t nc = *nc_p;
-  float f[10];
+  float yy = 0.0f;
   if (k < nc) {
-    float yy = 0.0f;
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
-      const float y = cu[static_cast<int64_t>(d) * ncap + k] - 0.5f;
-      f[d] = y;
+      const float y = cu[static_cast<int64_t>(d) * ncap + k] - centre[d];
       yy = __fmaf_rn(y, y, yy);
     }
+  }
+  unsigned mb = __float_as_uint(yy);
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned v = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = v > mb ? v : mb;
+  }
+  if ((threadIdx.x & 31) == 0 && mb) atomicMax(y2max, mb);
+  if (k >= cols_pad) return;
+  float f[10];
+  if (k < nc) {
+#pragma unroll
+    for (int d = 0; d < 8; ++d) f[d] = cu[static_cast<int64_t>(d) * ncap + k] - centre[d];
     f[8] = yy;
     f[9] = cc[k];
   } else {
@@ -327,9 +236,13 @@ __device__ __forceinline__ TcSmem tc_carve(uint8_t* raw) {
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
              const int* __restrict__ nc_p, int64_t rows, int tiles_per_chunk,
-             float2* __restrict__ part, unsigned* err, const int* __restrict__ off_dev) {
+             float2* __restrict__ part, unsigned* err, const int* __restrict__ off_dev,
+             const int* __restrict__ rows_dev) {
   extern __shared__ uint8_t tc_smem_raw[];
   if (off_dev && *off_dev) return;  // run finished or its generation stopped (block-uniform)
+  // rows is the stride (capacity); rows_dev, when given, the rows in use
+  const int64_t nrows = rows_dev ? static_cast<int64_t>(*rows_dev) : rows;
+  if (static_cast<int64_t>(blockIdx.x) * kTcM >= nrows) return;
   const TcSmem sm = tc_carve(tc_smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nc = *nc_p;
@@ -338,7 +251,7 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
   const int te = min(ntot, tb + tiles_per_chunk);
   const int64_t row0 = static_cast<int64_t>(blockIdx.x) * kTcM;
   if (tb >= te) {  // no column tile in this chunk: neutral partials
-    if (threadIdx.x < kTcM && row0 + threadIdx.x < rows)
+    if (threadIdx.x < kTcM && row0 + threadIdx.x < nrows)
       part[static_cast<int64_t>(blockIdx.y) * rows + row0 + threadIdx.x] = make_float2(-INFINITY, 0.0f);
     return;
   }
@@ -421,7 +334,8 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
       const uint32_t tph = static_cast<uint32_t>(t >> 1) & 1u;
-      if (!mbar_wait(&sm.tfull[b], tph, err, 7u)) break;
+      // warp-uniform: tcgen05.ld below is warp-collective
+      if (!__all_sync(0xffffffffu, mbar_wait(&sm.tfull[b], tph, err, 7u))) break;
       tc_fence_after();
       float ts = 0.0f;
 #pragma unroll 1
@@ -448,7 +362,7 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
       cS = (tt - S) - y;
       S = tt;
     }
-    if (row0 + r < rows) part[static_cast<int64_t>(blockIdx.y) * rows + row0 + r] = make_float2(m, S);
+    if (row0 + r < nrows) part[static_cast<int64_t>(blockIdx.y) * rows + row0 + r] = make_float2(m, S);
   }
   tc_fence_before();
   __syncthreads();
@@ -459,9 +373,10 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
 __global__ void k_weights_tc_combine(const float2* __restrict__ part, int nchunks,
                                      const float* __restrict__ s, const double* __restrict__ rowc,
                                      int64_t rows, const uint64_t* __restrict__ total_p,
-                                     double* __restrict__ logW, const int* __restrict__ off_dev) {
+                                     double* __restrict__ logW, const int* __restrict__ off_dev,
+                                     const int* __restrict__ rows_dev) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= rows || (off_dev && *off_dev)) return;
+  if (j >= (rows_dev ? static_cast<int64_t>(*rows_dev) : rows) || (off_dev && *off_dev)) return;
   const double sj = static_cast<double>(fmaxf(s[j], kSMinTc));
   double M = -INFINITY;
   for (int c = 0; c < nchunks; ++c)
@@ -513,7 +428,7 @@ k_tc_probe(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
       mbar_wait(&sm.tfull[0], 0u, err, 10u);
     }
   } else if (warp < 4) {
-    const bool ok = mbar_wait(&sm.tfull[0], 0u, err, 11u);
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&sm.tfull[0], 0u, err, 11u));
     tc_fence_after();
     if (ok) {
       for (int c = 0; c < kTcN / 32; ++c) {
@@ -567,17 +482,19 @@ int weights_tc_prepare() {
   return ABC_OK;
 }
 
-size_t weights_tc_scratch_bytes(int64_t rows, int64_t ncap, int mult) {
+static size_t tc_rows_scratch_bytes(int64_t rows, int64_t ncap, int mult) {
   return tc_layout(rows, ncap, mult).total;
 }
 
-// cu/cc/nc_dev: compacted survivor columns (capacity ncap).  The error word
-// is written into the scratch area; err_host (nullable) receives it when
-// sync_err is set.
-int launch_weights_tc(const float* up, const float* s, int64_t rows, const float* cu,
-                      const float* cc, const int* nc_dev, int64_t ncap, const uint64_t* total_p,
-                      double* logW, void* scratch, size_t bytes, unsigned** err_dev,
-                      cudaStream_t st, const int* off_dev, int mult) {
+// Rows up/s (stride rows; rows_dev of them in use) against the columns that
+// the caller packed into the layout's B area (k_tc_pack_cols, capacity ncap)
+// with the same centre.  The error word is written into the scratch area and
+// its address returned in *err_dev.
+static int launch_weights_tc_rows(const float* up, const float* s, int64_t rows,
+                      const float* centre, const int* nc_dev, int64_t ncap,
+                      const uint64_t* total_p, double* logW, void* scratch, size_t bytes,
+                      unsigned** err_dev, cudaStream_t st, const int* off_dev, int mult,
+                      const int* rows_dev) {
   if (rows <= 0) return ABC_OK;
   const TcLayout l = tc_layout(rows, ncap, mult);
   if (bytes < l.total) return ABC_E_SCRATCH;
@@ -598,12 +515,8 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   if (err_dev) *err_dev = err;
   ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
   const int64_t rpad = ceil_div(rows, kTcM) * kTcM;
-  const int64_t cpad = ceil_div(std::max<int64_t>(ncap, 1), kTcN) * kTcN;
-  k_tc_pack_rows<<<static_cast<unsigned>(ceil_div(rpad, 128)), 128, 0, st>>>(up, s, rows, rpad, Apk,
-                                                                            rowc);
-  ABC_LAUNCH_CHECK();
-  k_tc_pack_cols<<<static_cast<unsigned>(ceil_div(cpad, 128)), 128, 0, st>>>(cu, cc, nc_dev, ncap,
-                                                                            cpad, Bpk);
+  k_tc_pack_rows<<<static_cast<unsigned>(ceil_div(rpad, 128)), 128, 0, st>>>(
+      up, s, rows, rpad, centre, Apk, rowc, rows_dev);
   ABC_LAUNCH_CHECK();
   const int nch = tc_chunks(rows, ncap, mult);
   const int tiles = static_cast<int>(ceil_div(std::max<int64_t>(ncap, 1), kTcN));
@@ -611,10 +524,229 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   dim3 grid(static_cast<unsigned>(rpad / kTcM), static_cast<unsigned>(nch));
   k_weights_tc<<<grid, kTcThreads, kTcSmem, st>>>(reinterpret_cast<const uint8_t*>(Apk),
                                                   reinterpret_cast<const uint8_t*>(Bpk), nc_dev,
-                                                  rows, per, part, err, off_dev);
+                                                  rows, per, part, err, off_dev, rows_dev);
   ABC_LAUNCH_CHECK();
   k_weights_tc_combine<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(
-      part, nch, s, rowc, rows, total_p, logW, off_dev);
+      part, nch, s, rowc, rows, total_p, logW, off_dev, rows_dev);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+// ---- split by error bound: tensor cores where it is small, FP32 elsewhere --
+// The tensor-core exponent of row j is an fp32 sum of up to 64 products of
+// total size L_j (2 |x_j| Y + Y^2) + |c| <= L_j (2 |x_j| Y + Y^2) + 32, with
+// Y^2 = max_k |y_k|^2 over the columns, so its log W error is at most
+//     B_j = 2^-24 (64 (L_j (2 |x_j| Y + Y^2) + 32) + 160)   (natural log)
+// including the fp32 row sums.  Rows with B_j <= kTcBoundMax (the value of
+// B at s = 1e-3 with |x|, |y| <= sqrt 2, 0.0166) run on tcgen05, the rest on
+// the FP32 direct-difference kernel.  The partition, both passes and the
+// scatter back run on the device with the row counts in device memory (no
+// host round trip, so it also runs inside graphs).
+constexpr float kTcBoundMax = 0x1p-24f * (64.0f * (6.0f * 721.34752f + 32.0f) + 160.0f);
+constexpr int kPartTile = 1024;
+
+__device__ __forceinline__ bool tc_row(const float* __restrict__ up, int64_t rows, int64_t j,
+                                       float sj, const float* __restrict__ centre, float y2) {
+  const float L = 1.4426950408889634f / (2.0f * fmaxf(sj, kSMinTc));
+  float xx = 0.0f;
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const float x = up[static_cast<int64_t>(d) * rows + j] - centre[d];
+    xx = __fmaf_rn(x, x, xx);
+  }
+  const float mag = L * (2.0f * sqrtf(xx) * sqrtf(y2) + y2) + 32.0f;
+  return 0x1p-24f * (64.0f * mag + 160.0f) <= kTcBoundMax;
+}
+constexpr int kFp32Mult = 8;  // column chunks of the FP32 share (its rows are few)
+
+int launch_weights_fp32(const float*, const float*, int64_t, const float*, const float*, const int*,
+                        int64_t, const uint64_t*, double*, void*, size_t, cudaStream_t,
+                        const int*, int, const int*);
+size_t weights_fp32_scratch_bytes(int64_t, int64_t, int);
+
+__global__ void k_part_count(const float* __restrict__ up, const float* __restrict__ s,
+                             int64_t rows, const float* __restrict__ centre,
+                             const unsigned* __restrict__ y2max, int* __restrict__ cnt) {
+  __shared__ int sm[32];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kPartTile;
+  const float y2 = __uint_as_float(*y2max);
+  int c = 0;
+  for (int e = threadIdx.x; e < kPartTile; e += blockDim.x) {
+    const int64_t j = base + e;
+    c += (j < rows && !tc_row(up, rows, j, s[j], centre, y2));
+  }
+  c = block_sum<int>(c, sm);
+  if (threadIdx.x == 0) cnt[blockIdx.x] = c;
+}
+
+// exclusive offsets of the small rows per tile; counts[0] = small, [1] = large
+__global__ void k_part_scan(const int* __restrict__ cnt, int ntiles, int64_t rows,
+                            int* __restrict__ off, int* __restrict__ counts) {
+  __shared__ int sm[32];
+  __shared__ int last;
+  int carry = 0;
+  for (int b = 0; b < ntiles; b += blockDim.x) {
+    const int i = b + threadIdx.x;
+    const int v = i < ntiles ? cnt[i] : 0;
+    const int inc = block_incl_scan<int>(v, sm);
+    if (i < ntiles) off[i] = carry + inc - v;
+    if (threadIdx.x == blockDim.x - 1) last = inc;
+    __syncthreads();
+    carry += last;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    counts[0] = carry;
+    counts[1] = static_cast<int>(rows - carry);
+  }
+}
+
+// gathers both row sets (SoA, stride rows) with their original indices
+__global__ void k_part_scatter(const float* __restrict__ up, const float* __restrict__ s,
+                               int64_t rows, const float* __restrict__ centre,
+                               const unsigned* __restrict__ y2max, const int* __restrict__ off,
+                               int* __restrict__ idx_s, int* __restrict__ idx_l,
+                               float* __restrict__ u_s, float* __restrict__ s_s,
+                               float* __restrict__ u_l, float* __restrict__ s_l) {
+  __shared__ int sm[32];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kPartTile + 4 * threadIdx.x;
+  const float y2 = __uint_as_float(*y2max);
+  bool small[4];
+  int c = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    small[e] = base + e < rows && !tc_row(up, rows, base + e, s[base + e], centre, y2);
+    c += small[e];
+  }
+  const int inc = block_incl_scan<int>(c, sm);
+  int64_t ps = off[blockIdx.x] + inc - c;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int64_t j = base + e;
+    if (j >= rows) break;
+    if (small[e]) {
+      idx_s[ps] = static_cast<int>(j);
+#pragma unroll
+      for (int d = 0; d < 8; ++d) u_s[d * rows + ps] = up[d * rows + j];
+      s_s[ps] = s[j];
+      ++ps;
+    } else {
+      const int64_t pl = j - ps;  // rows before j that are large
+      idx_l[pl] = static_cast<int>(j);
+#pragma unroll
+      for (int d = 0; d < 8; ++d) u_l[d * rows + pl] = up[d * rows + j];
+      s_l[pl] = s[j];
+    }
+  }
+}
+
+__global__ void k_part_back(const int* __restrict__ idx_s, const int* __restrict__ idx_l,
+                            const double* __restrict__ lw_s, const double* __restrict__ lw_l,
+                            const int* __restrict__ counts, double* __restrict__ logW,
+                            const int* __restrict__ off_dev) {
+  if (off_dev && *off_dev) return;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < counts[0]) logW[idx_s[i]] = lw_s[i];
+  if (i < counts[1]) logW[idx_l[i]] = lw_l[i];
+}
+
+struct HyLayout {
+  size_t tc, fp, cnt, off, counts, idx_s, idx_l, u_s, s_s, u_l, s_l, lw_s, lw_l, ctr, total;
+};
+
+static HyLayout hy_layout(int64_t rows, int64_t ncap, int mult) {
+  HyLayout l{};
+  const int64_t nt = ceil_div(std::max<int64_t>(rows, 1), kPartTile);
+  const size_t R = static_cast<size_t>(rows);
+  size_t o = 0;
+  l.tc = o;
+  o += align256(tc_rows_scratch_bytes(rows, ncap, mult));
+  l.fp = o;
+  o += align256(weights_fp32_scratch_bytes(rows, ncap, kFp32Mult));
+  l.cnt = o;
+  o += align256(4 * nt);
+  l.off = o;
+  o += align256(4 * nt);
+  l.counts = o;
+  o += align256(8);
+  l.idx_s = o;
+  o += align256(4 * R);
+  l.idx_l = o;
+  o += align256(4 * R);
+  l.u_s = o;
+  o += align256(32 * R);
+  l.s_s = o;
+  o += align256(4 * R);
+  l.u_l = o;
+  o += align256(32 * R);
+  l.s_l = o;
+  o += align256(4 * R);
+  l.lw_s = o;
+  o += align256(8 * R);
+  l.lw_l = o;
+  o += align256(8 * R);
+  l.ctr = o;  // column partial sums, centre[8], radius word
+  o += align256(sizeof(double) * 8 * kCtrBlocks) + align256(8 * sizeof(float)) + align256(4);
+  l.total = o;
+  return l;
+}
+
+size_t weights_tc_scratch_bytes(int64_t rows, int64_t ncap, int mult) {
+  return hy_layout(rows, ncap, mult).total;
+}
+
+int launch_weights_tc(const float* up, const float* s, int64_t rows, const float* cu,
+                      const float* cc, const int* nc_dev, int64_t ncap, const uint64_t* total_p,
+                      double* logW, void* scratch, size_t bytes, unsigned** err_dev,
+                      cudaStream_t st, const int* off_dev, int mult, const int* rows_dev) {
+  if (rows <= 0) return ABC_OK;
+  if (rows_dev) return ABC_E_INVAL;  // the split works on full row sets only
+  const HyLayout l = hy_layout(rows, ncap, mult);
+  if (bytes < l.total) return ABC_E_SCRATCH;
+  char* b = static_cast<char*>(scratch);
+  int* cnt = reinterpret_cast<int*>(b + l.cnt);
+  int* off = reinterpret_cast<int*>(b + l.off);
+  int* counts = reinterpret_cast<int*>(b + l.counts);
+  int* idx_s = reinterpret_cast<int*>(b + l.idx_s);
+  int* idx_l = reinterpret_cast<int*>(b + l.idx_l);
+  float* u_s = reinterpret_cast<float*>(b + l.u_s);
+  float* s_s = reinterpret_cast<float*>(b + l.s_s);
+  float* u_l = reinterpret_cast<float*>(b + l.u_l);
+  float* s_l = reinterpret_cast<float*>(b + l.s_l);
+  double* lw_s = reinterpret_cast<double*>(b + l.lw_s);
+  double* lw_l = reinterpret_cast<double*>(b + l.lw_l);
+  auto* cpart = reinterpret_cast<double*>(b + l.ctr);
+  auto* centre = reinterpret_cast<float*>(b + l.ctr + align256(sizeof(double) * 8 * kCtrBlocks));
+  auto* y2max = reinterpret_cast<unsigned*>(b + l.ctr + align256(sizeof(double) * 8 * kCtrBlocks) +
+                                            align256(8 * sizeof(float)));
+  // centre and radius of the columns; the columns are packed once, centred
+  const TcLayout tl = tc_layout(rows, ncap, mult);
+  auto* Bpk = reinterpret_cast<__nv_bfloat16*>(b + l.tc + tl.bpk);
+  const int64_t cpad = ceil_div(std::max<int64_t>(ncap, 1), kTcN) * kTcN;
+  k_col_sum<<<kCtrBlocks, 256, 0, st>>>(cu, nc_dev, ncap, cpart);
+  ABC_LAUNCH_CHECK();
+  k_col_centre<<<1, 32, 0, st>>>(cpart, kCtrBlocks, nc_dev, centre, y2max);
+  ABC_LAUNCH_CHECK();
+  k_tc_pack_cols<<<static_cast<unsigned>(ceil_div(cpad, 128)), 128, 0, st>>>(
+      cu, cc, nc_dev, ncap, cpad, centre, Bpk, y2max);
+  ABC_LAUNCH_CHECK();
+  // rows split by their error bound
+  const int64_t nt = ceil_div(rows, kPartTile);
+  k_part_count<<<static_cast<unsigned>(nt), 256, 0, st>>>(up, s, rows, centre, y2max, cnt);
+  ABC_LAUNCH_CHECK();
+  k_part_scan<<<1, 1024, 0, st>>>(cnt, static_cast<int>(nt), rows, off, counts);
+  ABC_LAUNCH_CHECK();
+  k_part_scatter<<<static_cast<unsigned>(nt), 256, 0, st>>>(up, s, rows, centre, y2max, off, idx_s,
+                                                            idx_l, u_s, s_s, u_l, s_l);
+  ABC_LAUNCH_CHECK();
+  int rc = launch_weights_fp32(u_s, s_s, rows, cu, cc, nc_dev, ncap, total_p, lw_s, b + l.fp,
+                               l.cnt - l.fp, st, off_dev, kFp32Mult, counts + 0);
+  if (rc) return rc;
+  rc = launch_weights_tc_rows(u_l, s_l, rows, centre, nc_dev, ncap, total_p, lw_l, b + l.tc,
+                              l.fp - l.tc, err_dev, st, off_dev, mult, counts + 1);
+  if (rc) return rc;
+  k_part_back<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(idx_s, idx_l, lw_s, lw_l,
+                                                                         counts, logW, off_dev);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }
