@@ -308,6 +308,9 @@ typedef struct {
   double train_loss;        /* surrogate minibatch loss after the generation        */
   double ms_screen;         /* device time of the screening inference               */
   double ms_train;          /* device time of the surrogate training                */
+  int64_t rows_tc;          /* weight rows on the tensor cores (the rest on FP32)    */
+  double ms_tc;             /* device time of the tensor-core weight kernel          */
+  double ms_fp32;           /* device time of the FP32 weight kernel                 */
 } abc_gen_stats;
 
 /* Validate cfg, allocate every device buffer (owned by the context), copy

@@ -66,7 +66,8 @@ class AbcGenStats(C.Structure):
         ("launches", C.c_int64), ("ms", C.c_double), ("ms_sim", C.c_double),
         ("ms_weights", C.c_double), ("screened", C.c_int64), ("audited", C.c_int64),
         ("audit_accepted", C.c_int64), ("train_loss", C.c_double), ("ms_screen", C.c_double),
-        ("ms_train", C.c_double),
+        ("ms_train", C.c_double), ("rows_tc", C.c_int64), ("ms_tc", C.c_double),
+        ("ms_fp32", C.c_double),
     ]
 
     def as_dict(self):

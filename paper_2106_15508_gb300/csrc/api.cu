@@ -365,6 +365,7 @@ struct abc_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // whole generation
   cudaEvent_t es0 = nullptr, es1 = nullptr;  // one simulator launch
   cudaEvent_t ew0 = nullptr, ew1 = nullptr;  // the weight pass
+  cudaEvent_t ek[4] = {nullptr, nullptr, nullptr, nullptr};  // its TC / FP32 kernels
   // surrogate (delayed-acceptance pre-screen)
   MlpState mlp{};
   float* grad = nullptr;
@@ -409,7 +410,8 @@ struct abc_ctx {
   }
   ~abc_ctx() {
     for (void* p : allocs) cudaFree(p);
-    for (cudaEvent_t e : {ev0, ev1, es0, es1, ew0, ew1, eq0, eq1, et0, et1})
+    for (cudaEvent_t e : {ev0, ev1, es0, es1, ew0, ew1, eq0, eq1, et0, et1, ek[0], ek[1], ek[2],
+                          ek[3]})
       if (e) cudaEventDestroy(e);
   }
 };
@@ -648,6 +650,12 @@ int generation_t(abc_ctx* c) {
   g.beta_b = bb;
   g.ms_sim = ms_sim;
   int h_nc = 0;
+  int h_counts[2] = {0, 0};
+  WeightTiming wt;
+  wt.tc0 = c->ek[0];
+  wt.tc1 = c->ek[1];
+  wt.fp0 = c->ek[2];
+  wt.fp1 = c->ek[3];
   bool weighted = false;
   unsigned* tc_err = nullptr;
   unsigned h_err = 0;
@@ -662,15 +670,18 @@ int generation_t(abc_ctx* c) {
       if (c->cfg.weight_prec == ABC_P_BF16_TC)
         rc = launch_weights_tc(c->u[nxt], c->s[nxt], c->N, c->cu, c->cc, c->nc, c->N,
                                c->prefix + (c->N - 1), c->logW, c->scratch, c->scratch_bytes,
-                               &tc_err, st);
+                               &tc_err, st, nullptr, 1, nullptr,
+                               AncInfo{c->anc[nxt], c->u[cur], c->q, c->N}, &wt);
       else
         rc = launch_weights_fp32(c->u[nxt], c->s[nxt], c->N, c->cu, c->cc, c->nc, c->N,
                                  c->prefix + (c->N - 1), c->logW, c->scratch, c->scratch_bytes,
-                                 st);
+                                 st, nullptr, 1, nullptr, &wt);
       if (rc) return rc;
       ABC_CUDA_TRY(cudaEventRecord(c->ew1, st));
       if (tc_err) ABC_CUDA_TRY(cudaMemcpyAsync(&h_err, tc_err, sizeof h_err, cudaMemcpyDeviceToHost, st));
       ABC_CUDA_TRY(cudaMemcpyAsync(&h_nc, c->nc, sizeof(int), cudaMemcpyDeviceToHost, st));
+      if (wt.counts)
+        ABC_CUDA_TRY(cudaMemcpyAsync(h_counts, wt.counts, sizeof h_counts, cudaMemcpyDeviceToHost, st));
       weighted = true;
       // delayed acceptance: a proposal simulated with probability rho carries 1/rho
       if (screen && (rc = rho_correct(c->logW, c->rho_pop[nxt], c->N, st))) return rc;
@@ -690,6 +701,17 @@ int generation_t(abc_ctx* c) {
     ABC_CUDA_TRY(cudaEventElapsedTime(&ms, c->ew0, c->ew1));
     g.ms_weights = ms;
     g.pairs = c->N * static_cast<int64_t>(h_nc);
+    // per-kernel split of the pass (FP32 only: every row on the FP32 kernel)
+    const bool tc = c->cfg.weight_prec == ABC_P_BF16_TC;
+    g.rows_tc = tc ? h_counts[1] : 0;
+    if (tc && h_counts[1] > 0) {
+      ABC_CUDA_TRY(cudaEventElapsedTime(&ms, c->ek[0], c->ek[1]));
+      g.ms_tc = ms;
+    }
+    if (!tc || h_counts[0] > 0) {
+      ABC_CUDA_TRY(cudaEventElapsedTime(&ms, c->ek[2], c->ek[3]));
+      g.ms_fp32 = ms;
+    }
   }
   g.eps = h_scal[0];
   g.eps1 = h_scal[1];
@@ -772,6 +794,8 @@ ABC_API int abc_init(const abc_config* cfg, const int32_t* obs, void* stream, ab
       cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
       cudaEventCreate(&c->es0) != cudaSuccess || cudaEventCreate(&c->es1) != cudaSuccess ||
       cudaEventCreate(&c->ew0) != cudaSuccess || cudaEventCreate(&c->ew1) != cudaSuccess ||
+      cudaEventCreate(&c->ek[0]) != cudaSuccess || cudaEventCreate(&c->ek[1]) != cudaSuccess ||
+      cudaEventCreate(&c->ek[2]) != cudaSuccess || cudaEventCreate(&c->ek[3]) != cudaSuccess ||
       cudaStreamSynchronize(c->st) != cudaSuccess) {
     delete c;
     return ABC_E_CUDA;

@@ -167,7 +167,7 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
     if (v.weight_prec == ABC_P_BF16_TC)
       rc = launch_weights_tc(v.u_nxt, v.s_nxt, v.N, v.cu, v.cc, v.nc, v.N, v.prefix + (v.N - 1),
                              v.logW, v.scratch, v.scratch_bytes, &br.tc_err, st, &r->off,
-                             br.w_mult);
+                             br.w_mult, nullptr, AncInfo{v.a_nxt, v.u_cur, v.q, v.N});
     else
       rc = launch_weights_fp32(v.u_nxt, v.s_nxt, v.N, v.cu, v.cc, v.nc, v.N, v.prefix + (v.N - 1),
                                v.logW, v.scratch, v.scratch_bytes, st, &r->off, br.w_mult);

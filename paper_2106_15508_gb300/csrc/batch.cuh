@@ -74,11 +74,12 @@ int launch_survivors(const float*, const uint32_t*, int64_t, float*, float*, int
 int launch_weights_fp32(const float*, const float*, int64_t, const float*, const float*,
                         const int*, int64_t, const uint64_t*, double*, void*, size_t,
                         cudaStream_t, const int* off_dev = nullptr, int mult = 1,
-                        const int* rows_dev = nullptr);
+                        const int* rows_dev = nullptr, const WeightTiming* wt = nullptr);
 int launch_weights_tc(const float*, const float*, int64_t, const float*, const float*, const int*,
                       int64_t, const uint64_t*, double*, void*, size_t, unsigned**,
                       cudaStream_t, const int* off_dev = nullptr, int mult = 1,
-                      const int* rows_dev = nullptr);
+                      const int* rows_dev = nullptr, const AncInfo& ai = AncInfo(),
+                      WeightTiming* wt = nullptr);
 int launch_normalize(const double*, int64_t, double*, double*, void*, size_t, cudaStream_t);
 int weights_tc_prepare();
 

@@ -55,7 +55,7 @@ int64_t launch_count();  // launches counted so far (no increment)
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // round up to 256 bytes so that sub-buffers of one scratch area stay aligned
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -101,5 +101,24 @@ __device__ __forceinline__ T block_sum(T v, T* smem) {
   __syncthreads();
   return r;
 }
+
+// Where the rows of a weight pass came from (all members nullable together):
+// row j was proposed from particle anc[j] of the previous population
+// u_prev [8][n_prev], whose quantised stage-prior weight q_prev[anc[j]] is
+// non-zero (the ancestor was drawn in proportion to it).
+// Optional timing of the two kernels of a weight pass: events recorded
+// around the tensor-core kernel (tc0/tc1) and the FP32 kernel (fp0/fp1);
+// counts (out) points at the device pair [FP32 rows, tensor-core rows].
+struct WeightTiming {
+  cudaEvent_t tc0 = nullptr, tc1 = nullptr, fp0 = nullptr, fp1 = nullptr;
+  const int* counts = nullptr;
+};
+
+struct AncInfo {
+  const int32_t* anc = nullptr;
+  const float* u_prev = nullptr;
+  const uint32_t* q_prev = nullptr;
+  int64_t n_prev = 0;
+};
 
 }  // namespace abc

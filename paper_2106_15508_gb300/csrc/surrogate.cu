@@ -89,17 +89,23 @@ k_gemm(int M, int N, int K, const float* __restrict__ A, int64_t sam, int64_t sa
   __shared__ float Bs[kGBK][kGBN + 4];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.y * kGBM, n0 = blockIdx.x * kGBN;
+  // split-K: slice z of gridDim.z covers K [kb, ke) and writes its partial
+  // product to C + z * M * ldc (summed by k_splitk_sum)
+  const int kper = (((K + gridDim.z - 1) / gridDim.z) + kGBK - 1) / kGBK * kGBK;
+  const int kb = blockIdx.z * kper;
+  const int ke = K < kb + kper ? K : kb + kper;
+  C += static_cast<int64_t>(blockIdx.z) * M * ldc;
   float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += kGBK) {
+  for (int k0 = kb; k0 < ke; k0 += kGBK) {
     for (int e = threadIdx.x; e < kGBK * kGBM; e += 256) {
       const int kk = e / kGBM, mm = e % kGBM;
       const int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < M && k < K) ? A[m * sam + k * sak] : 0.0f;
+      As[kk][mm] = (m < M && k < ke) ? A[m * sam + k * sak] : 0.0f;
     }
     for (int e = threadIdx.x; e < kGBK * kGBN; e += 256) {
       const int kk = e / kGBN, nn = e % kGBN;
       const int n = n0 + nn, k = k0 + kk;
-      Bs[kk][nn] = (n < N && k < K) ? ldf<TB>(B + k * sbk + n * sbn) : 0.0f;
+      Bs[kk][nn] = (n < N && k < ke) ? ldf<TB>(B + k * sbk + n * sbn) : 0.0f;
     }
     __syncthreads();
 #pragma unroll
@@ -133,13 +139,41 @@ k_gemm(int M, int N, int K, const float* __restrict__ A, int64_t sam, int64_t sa
   }
 }
 
+// out[i] = sum_z P[z * n + i], z in order (deterministic split-K reduction)
+__global__ void k_splitk_sum(const float* __restrict__ P, int splits, int64_t n,
+                             float* __restrict__ out) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float v = 0.0f;
+  for (int z = 0; z < splits; ++z) v += P[z * n + i];
+  out[i] = v;
+}
+
+constexpr int kMaxSplits = 64;
+
+// C = A B (+ epilogue).  A product with few output tiles and a long K (the
+// weight gradients, K = batch) is split along K over up to 64 slices whose
+// partial products go to `part` (splits x M x ldc floats) and are summed in
+// slice order; only the plain epilogue (0, no bias) is split.
 template <typename TB>
 static int gemm(int M, int N, int K, const float* A, int64_t sam, int64_t sak, const TB* B,
                 int64_t sbk, int64_t sbn, float* C, int64_t ldc, const float* bias, int epi,
-                const float* aux, float* C2, cudaStream_t st) {
+                const float* aux, float* C2, cudaStream_t st, float* part = nullptr) {
   dim3 grid(static_cast<unsigned>((N + kGBN - 1) / kGBN), static_cast<unsigned>((M + kGBM - 1) / kGBM));
-  k_gemm<TB><<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, epi, aux, C2);
+  int splits = 1;
+  if (part && epi == 0 && !bias) {
+    const int tiles = static_cast<int>(grid.x * grid.y);
+    splits = std::min(kMaxSplits, std::max(1, std::min(304 / tiles, K / 256)));
+  }
+  grid.z = static_cast<unsigned>(splits);
+  k_gemm<TB><<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, splits > 1 ? part : C, ldc,
+                                   bias, epi, aux, C2);
   ABC_LAUNCH_CHECK();
+  if (splits > 1) {
+    const int64_t n = static_cast<int64_t>(M) * ldc;
+    k_splitk_sum<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(part, splits, n, C);
+    ABC_LAUNCH_CHECK();
+  }
   return ABC_OK;
 }
 
@@ -233,9 +267,10 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
 }
 
 size_t mlp_train_scratch_bytes(int B) {
-  // Z1, H1, Z2, H2, dZ2, dH1 [B][256]; Y, dY [B][4]; loss parts [B]; grads
+  // Z1, H1, Z2, H2, dZ2, dH1 [B][256]; Y, dY [B][4]; loss parts [B];
+  // split-K partials (64 x 256 x 256)
   return sizeof(float) * (6 * static_cast<size_t>(B) * kMlpH + 9 * static_cast<size_t>(B) +
-                          kMlpParams + 8) + 1024;
+                          static_cast<size_t>(kMaxSplits) * kMlpH * kMlpH + 8) + 1024;
 }
 
 // One forward + backward pass on X [B][8], T [B][4] (standardised targets).
@@ -247,7 +282,7 @@ int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* gr
   float* f = static_cast<float*>(scratch);
   const size_t BH = static_cast<size_t>(B) * kMlpH;
   float *Z1 = f, *H1 = f + BH, *Z2 = f + 2 * BH, *H2 = f + 3 * BH, *dZ2 = f + 4 * BH,
-        *dH1 = f + 5 * BH, *Y = f + 6 * BH, *dY = Y + 4 * B, *lp = dY + 4 * B;
+        *dH1 = f + 5 * BH, *Y = f + 6 * BH, *dY = Y + 4 * B, *lp = dY + 4 * B, *sk = lp + B;
   const __nv_bfloat16* wb = s.wb;
   const unsigned g1 = static_cast<unsigned>((BH + 255) / 256);
   k_l1_fwd<<<g1, 256, 0, st>>>(X, B, wb, s.w, Z1, H1);
@@ -264,7 +299,7 @@ int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* gr
   ABC_LAUNCH_CHECK();
   // layer 3 gradients: gW3[o][k] = sum_b dY[b][o] H2[b][k]  (M = 4, N = 256, K = B)
   if ((rc = gemm<float>(4, kMlpH, B, dY, 1, 4, H2, kMlpH, 1, grad + kOffW3, kMlpH, nullptr, 0,
-                        nullptr, nullptr, st)))
+                        nullptr, nullptr, st, sk)))
     return rc;
   k_colsum<<<4, 256, 0, st>>>(dY, B, 4, grad + kOffB3);
   ABC_LAUNCH_CHECK();
@@ -272,7 +307,7 @@ int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* gr
   ABC_LAUNCH_CHECK();
   // gW2 = dZ2^T H1 (M = 256, N = 256, K = B)
   if ((rc = gemm<float>(kMlpH, kMlpH, B, dZ2, 1, kMlpH, H1, kMlpH, 1, grad + kOffW2, kMlpH, nullptr,
-                        0, nullptr, nullptr, st)))
+                        0, nullptr, nullptr, st, sk)))
     return rc;
   k_colsum<<<kMlpH, 256, 0, st>>>(dZ2, B, kMlpH, grad + kOffB2);
   ABC_LAUNCH_CHECK();
@@ -282,7 +317,7 @@ int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* gr
     return rc;
   // gW1 = dZ1^T X (M = 256, N = 8, K = B)
   if ((rc = gemm<float>(kMlpH, 8, B, dH1, 1, kMlpH, X, 8, 1, grad + kOffW1, 8, nullptr, 0, nullptr,
-                        nullptr, st)))
+                        nullptr, st, sk)))
     return rc;
   k_colsum<<<kMlpH, 256, 0, st>>>(dH1, B, kMlpH, grad + kOffB1);
   ABC_LAUNCH_CHECK();

@@ -18,12 +18,15 @@
 // direct-difference kernel instead (see the split below).
 //
 // Kernel structure (one CTA = 128 rows, one SM):
-//   warp 4  : bulk-copy producer (cp.async.bulk, mbarrier complete_tx):
+//   warp 8  : bulk-copy producer (cp.async.bulk, mbarrier complete_tx):
 //             the row tile once, then 256-column tiles through a 4-stage ring
-//   warp 5  : tcgen05.mma issuer (one thread), M = 128, N = 256, K = 4 x 16,
+//   warp 9  : tcgen05.mma issuer (one thread), M = 128, N = 256, K = 4 x 16,
 //             fp32 accumulators double-buffered in TMEM (2 x 256 columns)
-//   warps 0-3: epilogue, one thread per row (TMEM lane): tcgen05.ld 32
-//             columns at a time, online max and sum of 2^(e - m)
+//   warps 0-7: epilogue, one thread per row (TMEM lane) and column half:
+//             warps w and w + 4 share TMEM lanes 32 w .. 32 w + 31 and take
+//             alternate 32-column chunks (tcgen05.ld), each keeping an online
+//             max and sum of 2^(e - m); two warps per lane quarter keep the
+//             exponential unit busy while the other waits on TMEM
 // Operands are packed by a prep kernel in the canonical K-major layout
 // without swizzle: 8 x 8 bf16 core matrices (128 contiguous bytes), the 8
 // core matrices of a row group consecutive along K (LBO = 128 B), row groups
@@ -46,7 +49,11 @@ constexpr int kTcStages = 4;                        // column-tile ring
 constexpr uint32_t kATile = kTcM * kTcK * 2;        // 16 KB
 constexpr uint32_t kBTile = kTcN * kTcK * 2;        // 32 KB
 constexpr uint32_t kTmemCols = 512;                 // two 256-column accumulators
-constexpr int kTcThreads = 192;                     // 6 warps
+constexpr int kTcEpiWarps = 8;                      // two epilogue warps per TMEM lane quarter
+constexpr int kTcProducer = kTcEpiWarps;            // warp 8: bulk-copy producer
+constexpr int kTcIssuer = kTcEpiWarps + 1;          // warp 9: MMA issuer, owns the TMEM
+constexpr int kTcThreads = 32 * (kTcEpiWarps + 2);  // 10 warps
+constexpr int kProbeThreads = 192;                  // probe: 4 epilogue warps, producer, issuer
 constexpr size_t kTcSmem = 1024 + kATile + kTcStages * kBTile + 256;
 constexpr float kSMinTc = 1e-30f;
 constexpr float kPadLogit = -1.0e30f;
@@ -235,7 +242,7 @@ __device__ __forceinline__ TcSmem tc_carve(uint8_t* raw) {
 
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
-             const int* __restrict__ nc_p, int64_t rows, int tiles_per_chunk,
+             const int* __restrict__ nc_p, int64_t rows,
              float2* __restrict__ part, unsigned* err, const int* __restrict__ off_dev,
              const int* __restrict__ rows_dev) {
   extern __shared__ uint8_t tc_smem_raw[];
@@ -247,12 +254,15 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nc = *nc_p;
   const int ntot = static_cast<int>((nc + kTcN - 1) / kTcN);
+  // the column tiles in use (nc is known only on the device) split over grid.y
+  const int tiles_per_chunk = (ntot + static_cast<int>(gridDim.y) - 1) / static_cast<int>(gridDim.y);
   const int tb = static_cast<int>(blockIdx.y) * tiles_per_chunk;
   const int te = min(ntot, tb + tiles_per_chunk);
   const int64_t row0 = static_cast<int64_t>(blockIdx.x) * kTcM;
-  if (tb >= te) {  // no column tile in this chunk: neutral partials
-    if (threadIdx.x < kTcM && row0 + threadIdx.x < nrows)
-      part[static_cast<int64_t>(blockIdx.y) * rows + row0 + threadIdx.x] = make_float2(-INFINITY, 0.0f);
+  if (tb >= te) {  // no column tile in this chunk: neutral partials (both halves)
+    const int g = threadIdx.x / kTcM, r = threadIdx.x % kTcM;
+    if (g < 2 && row0 + r < nrows)
+      part[(2 * static_cast<int64_t>(blockIdx.y) + g) * rows + row0 + r] = make_float2(-INFINITY, 0.0f);
     return;
   }
   const int ntiles = te - tb;
@@ -263,12 +273,12 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&sm.tfull[i], 1);
-      mbar_init(&sm.tempty[i], kTcM);
+      mbar_init(&sm.tempty[i], 32 * kTcEpiWarps);
     }
     mbar_init(sm.afull, 1);
     fence_mbar_init();
   }
-  if (warp == 5) {
+  if (warp == kTcIssuer) {
     tmem_alloc(sm.tmem_slot, kTmemCols);
     tmem_relinquish();
   }
@@ -277,7 +287,7 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
   tc_fence_after();
   const uint32_t tmem = *sm.tmem_slot;
 
-  if (warp == 4) {
+  if (warp == kTcProducer) {
     // ---------------- producer ----------------
     if (lane == 0) {
       mbar_expect_tx(sm.afull, kATile);
@@ -297,7 +307,7 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
       for (int t = issued > kTcStages ? issued - kTcStages : 0; t < issued; ++t)
         mbar_wait(&sm.full[t % kTcStages], static_cast<uint32_t>(t / kTcStages) & 1u, err, 2u);
     }
-  } else if (warp == 5) {
+  } else if (warp == kTcIssuer) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       int last = -1;
@@ -328,8 +338,12 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     __syncwarp();
   } else {
     // ---------------- epilogue: thread = row = TMEM lane ----------------
-    const int r = threadIdx.x;
-    const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its row quarter); the two
+    // warps of a quarter take alternate 32-column chunks of every tile and
+    // keep separate (m, S) partials (column half g of the chunk)
+    const int g = warp >> 2, q = warp & 3;
+    const int r = q * 32 + lane;
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(q * 32) << 16);
     float m = -INFINITY, S = 0.0f, cS = 0.0f;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
@@ -339,7 +353,7 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
       tc_fence_after();
       float ts = 0.0f;
 #pragma unroll 1
-      for (int c = 0; c < kTcN / 32; ++c) {
+      for (int c = g; c < kTcN / 32; c += 2) {
         float v[32];
         tmem_ld32(lane_base + static_cast<uint32_t>(b * kTcN + c * 32), v);
         float cm = v[0];
@@ -362,12 +376,13 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
       cS = (tt - S) - y;
       S = tt;
     }
-    if (row0 + r < nrows) part[static_cast<int64_t>(blockIdx.y) * rows + row0 + r] = make_float2(m, S);
+    if (row0 + r < nrows)
+      part[(2 * static_cast<int64_t>(blockIdx.y) + g) * rows + row0 + r] = make_float2(m, S);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 5) tmem_dealloc(tmem, kTmemCols);
+  if (warp == kTcIssuer) tmem_dealloc(tmem, kTmemCols);
 }
 
 __global__ void k_weights_tc_combine(const float2* __restrict__ part, int nchunks,
@@ -392,7 +407,7 @@ __global__ void k_weights_tc_combine(const float2* __restrict__ part, int nchunk
 
 // one 128 x 256 x 64 product with the weight kernel's operand layout and
 // descriptors (diagnostic): D[i][n] = sum_k A[i][k] B[n][k]
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kProbeThreads, 1)
 k_tc_probe(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
            float* __restrict__ D, unsigned* err) {
   extern __shared__ uint8_t tc_smem_raw[];
@@ -469,7 +484,7 @@ static TcLayout tc_layout(int64_t rows, int64_t ncap, int mult) {
   l.rowc = o;
   o += align256(sizeof(double) * static_cast<size_t>(rows));
   l.part = o;
-  o += align256(sizeof(float2) * static_cast<size_t>(tc_chunks(rows, ncap, mult)) * rows);
+  o += align256(sizeof(float2) * 2 * static_cast<size_t>(tc_chunks(rows, ncap, mult)) * rows);
   l.err = o;
   o += align256(sizeof(unsigned));
   l.total = o;
@@ -494,7 +509,7 @@ static int launch_weights_tc_rows(const float* up, const float* s, int64_t rows,
                       const float* centre, const int* nc_dev, int64_t ncap,
                       const uint64_t* total_p, double* logW, void* scratch, size_t bytes,
                       unsigned** err_dev, cudaStream_t st, const int* off_dev, int mult,
-                      const int* rows_dev) {
+                      const int* rows_dev, const WeightTiming* wt) {
   if (rows <= 0) return ABC_OK;
   const TcLayout l = tc_layout(rows, ncap, mult);
   if (bytes < l.total) return ABC_E_SCRATCH;
@@ -519,61 +534,84 @@ static int launch_weights_tc_rows(const float* up, const float* s, int64_t rows,
       up, s, rows, rpad, centre, Apk, rowc, rows_dev);
   ABC_LAUNCH_CHECK();
   const int nch = tc_chunks(rows, ncap, mult);
-  const int tiles = static_cast<int>(ceil_div(std::max<int64_t>(ncap, 1), kTcN));
-  const int per = static_cast<int>(ceil_div(tiles, nch));
   dim3 grid(static_cast<unsigned>(rpad / kTcM), static_cast<unsigned>(nch));
+  if (wt && wt->tc0) ABC_CUDA_TRY(cudaEventRecord(wt->tc0, st));
   k_weights_tc<<<grid, kTcThreads, kTcSmem, st>>>(reinterpret_cast<const uint8_t*>(Apk),
                                                   reinterpret_cast<const uint8_t*>(Bpk), nc_dev,
-                                                  rows, per, part, err, off_dev, rows_dev);
+                                                  rows, part, err, off_dev, rows_dev);
   ABC_LAUNCH_CHECK();
+  if (wt && wt->tc1) ABC_CUDA_TRY(cudaEventRecord(wt->tc1, st));
   k_weights_tc_combine<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(
-      part, nch, s, rowc, rows, total_p, logW, off_dev, rows_dev);
+      part, 2 * nch, s, rowc, rows, total_p, logW, off_dev, rows_dev);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }
 
 // ---- split by error bound: tensor cores where it is small, FP32 elsewhere --
-// The tensor-core exponent of row j is an fp32 sum of up to 64 products of
-// total size L_j (2 |x_j| Y + Y^2) + |c| <= L_j (2 |x_j| Y + Y^2) + 32, with
-// Y^2 = max_k |y_k|^2 over the columns, so its log W error is at most
-//     B_j = 2^-24 (64 (L_j (2 |x_j| Y + Y^2) + 32) + 160)   (natural log)
-// including the fp32 row sums.  Rows with B_j <= kTcBoundMax (the value of
-// B at s = 1e-3 with |x|, |y| <= sqrt 2, 0.0166) run on tcgen05, the rest on
-// the FP32 direct-difference kernel.  The partition, both passes and the
-// scatter back run on the device with the row counts in device memory (no
-// host round trip, so it also runs inside graphs).
+// The tensor-core exponent of pair (j, k) is an fp32 sum of up to 64 products
+// of total size L_j (2 |x_j| |y_k| + |y_k|^2) + |c_k| <= L_j (2 |x_j| |y_k| +
+// |y_k|^2) + 32, so with |y_k| <= Y_j over the columns that can matter the
+// row's log W error is at most
+//     B_j = 2^-24 (64 (L_j (2 |x_j| Y_j + Y_j^2) + 32) + 160)   (natural log)
+// including the fp32 row sums.  Y_j is the largest column radius
+// (max_k |y_k|), or, when the row's ancestor a is known, |x_j| + R_j with
+//     R_j^2 = |u'_j - u_a|^2 + (60 - c_a) / L_j:
+// the ancestor's own exponent e_a = c_a - L_j |u'_j - u_a|^2 bounds the row
+// maximum from below and c_k < 0, so a column farther than R_j has e_jk <
+// max - 60; its error grows at most like L_j |y_k|^2 2^-18 while its deficit
+// grows like L_j (|y_k| - |x_j|)^2, so it stays far inside the 60-bit margin
+// and the column carries under ~2^-59 of the maximum term.  Rows with B_j <= kTcBoundMax (the
+// value of B at s = 1e-3 with |x|, |y| <= sqrt 2, 0.0166) run on tcgen05, the
+// rest on the FP32 direct-difference kernel.  The partition, both passes and
+// the scatter back run on the device with the row counts in device memory
+// (no host round trip, so it also runs inside graphs).
 constexpr float kTcBoundMax = 0x1p-24f * (64.0f * (6.0f * 721.34752f + 32.0f) + 160.0f);
 constexpr int kPartTile = 1024;
 
 __device__ __forceinline__ bool tc_row(const float* __restrict__ up, int64_t rows, int64_t j,
-                                       float sj, const float* __restrict__ centre, float y2) {
+                                       float sj, const float* __restrict__ centre, float y2,
+                                       const AncInfo& ai) {
   const float L = 1.4426950408889634f / (2.0f * fmaxf(sj, kSMinTc));
-  float xx = 0.0f;
+  float xx = 0.0f, dd = 0.0f;
+  const int32_t a = ai.anc ? ai.anc[j] : -1;
 #pragma unroll
   for (int d = 0; d < 8; ++d) {
-    const float x = up[static_cast<int64_t>(d) * rows + j] - centre[d];
+    const float u = up[static_cast<int64_t>(d) * rows + j];
+    const float x = u - centre[d];
     xx = __fmaf_rn(x, x, xx);
+    if (a >= 0) {
+      const float e = u - ai.u_prev[static_cast<int64_t>(d) * ai.n_prev + a];
+      dd = __fmaf_rn(e, e, dd);
+    }
   }
-  const float mag = L * (2.0f * sqrtf(xx) * sqrtf(y2) + y2) + 32.0f;
+  const float X = sqrtf(xx);
+  float Y = sqrtf(y2);
+  if (a >= 0 && ai.q_prev[a] > 0u) {
+    const float ca = static_cast<float>(log2(static_cast<double>(ai.q_prev[a])) - 32.0);
+    // 1.001: margin for the fp32 rounding of this estimate
+    Y = fminf(Y, 1.001f * (X + sqrtf(dd + (60.0f - ca) / L)));
+  }
+  const float mag = L * (2.0f * X * Y + Y * Y) + 32.0f;
   return 0x1p-24f * (64.0f * mag + 160.0f) <= kTcBoundMax;
 }
 constexpr int kFp32Mult = 8;  // column chunks of the FP32 share (its rows are few)
 
 int launch_weights_fp32(const float*, const float*, int64_t, const float*, const float*, const int*,
                         int64_t, const uint64_t*, double*, void*, size_t, cudaStream_t,
-                        const int*, int, const int*);
+                        const int*, int, const int*, const WeightTiming*);
 size_t weights_fp32_scratch_bytes(int64_t, int64_t, int);
 
 __global__ void k_part_count(const float* __restrict__ up, const float* __restrict__ s,
                              int64_t rows, const float* __restrict__ centre,
-                             const unsigned* __restrict__ y2max, int* __restrict__ cnt) {
+                             const unsigned* __restrict__ y2max, AncInfo ai,
+                             int* __restrict__ cnt) {
   __shared__ int sm[32];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kPartTile;
   const float y2 = __uint_as_float(*y2max);
   int c = 0;
   for (int e = threadIdx.x; e < kPartTile; e += blockDim.x) {
     const int64_t j = base + e;
-    c += (j < rows && !tc_row(up, rows, j, s[j], centre, y2));
+    c += (j < rows && !tc_row(up, rows, j, s[j], centre, y2, ai));
   }
   c = block_sum<int>(c, sm);
   if (threadIdx.x == 0) cnt[blockIdx.x] = c;
@@ -604,7 +642,8 @@ __global__ void k_part_scan(const int* __restrict__ cnt, int ntiles, int64_t row
 // gathers both row sets (SoA, stride rows) with their original indices
 __global__ void k_part_scatter(const float* __restrict__ up, const float* __restrict__ s,
                                int64_t rows, const float* __restrict__ centre,
-                               const unsigned* __restrict__ y2max, const int* __restrict__ off,
+                               const unsigned* __restrict__ y2max, AncInfo ai,
+                               const int* __restrict__ off,
                                int* __restrict__ idx_s, int* __restrict__ idx_l,
                                float* __restrict__ u_s, float* __restrict__ s_s,
                                float* __restrict__ u_l, float* __restrict__ s_l) {
@@ -615,7 +654,7 @@ __global__ void k_part_scatter(const float* __restrict__ up, const float* __rest
   int c = 0;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    small[e] = base + e < rows && !tc_row(up, rows, base + e, s[base + e], centre, y2);
+    small[e] = base + e < rows && !tc_row(up, rows, base + e, s[base + e], centre, y2, ai);
     c += small[e];
   }
   const int inc = block_incl_scan<int>(c, sm);
@@ -698,7 +737,8 @@ size_t weights_tc_scratch_bytes(int64_t rows, int64_t ncap, int mult) {
 int launch_weights_tc(const float* up, const float* s, int64_t rows, const float* cu,
                       const float* cc, const int* nc_dev, int64_t ncap, const uint64_t* total_p,
                       double* logW, void* scratch, size_t bytes, unsigned** err_dev,
-                      cudaStream_t st, const int* off_dev, int mult, const int* rows_dev) {
+                      cudaStream_t st, const int* off_dev, int mult, const int* rows_dev,
+                      const AncInfo& ai, WeightTiming* wt) {
   if (rows <= 0) return ABC_OK;
   if (rows_dev) return ABC_E_INVAL;  // the split works on full row sets only
   const HyLayout l = hy_layout(rows, ncap, mult);
@@ -732,22 +772,23 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   ABC_LAUNCH_CHECK();
   // rows split by their error bound
   const int64_t nt = ceil_div(rows, kPartTile);
-  k_part_count<<<static_cast<unsigned>(nt), 256, 0, st>>>(up, s, rows, centre, y2max, cnt);
+  k_part_count<<<static_cast<unsigned>(nt), 256, 0, st>>>(up, s, rows, centre, y2max, ai, cnt);
   ABC_LAUNCH_CHECK();
   k_part_scan<<<1, 1024, 0, st>>>(cnt, static_cast<int>(nt), rows, off, counts);
   ABC_LAUNCH_CHECK();
-  k_part_scatter<<<static_cast<unsigned>(nt), 256, 0, st>>>(up, s, rows, centre, y2max, off, idx_s,
-                                                            idx_l, u_s, s_s, u_l, s_l);
+  k_part_scatter<<<static_cast<unsigned>(nt), 256, 0, st>>>(up, s, rows, centre, y2max, ai, off,
+                                                            idx_s, idx_l, u_s, s_s, u_l, s_l);
   ABC_LAUNCH_CHECK();
   int rc = launch_weights_fp32(u_s, s_s, rows, cu, cc, nc_dev, ncap, total_p, lw_s, b + l.fp,
-                               l.cnt - l.fp, st, off_dev, kFp32Mult, counts + 0);
+                               l.cnt - l.fp, st, off_dev, kFp32Mult, counts + 0, wt);
   if (rc) return rc;
   rc = launch_weights_tc_rows(u_l, s_l, rows, centre, nc_dev, ncap, total_p, lw_l, b + l.tc,
-                              l.fp - l.tc, err_dev, st, off_dev, mult, counts + 1);
+                              l.fp - l.tc, err_dev, st, off_dev, mult, counts + 1, wt);
   if (rc) return rc;
   k_part_back<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(idx_s, idx_l, lw_s, lw_l,
                                                                          counts, logW, off_dev);
   ABC_LAUNCH_CHECK();
+  if (wt) wt->counts = counts;
   return ABC_OK;
 }
 
@@ -756,7 +797,7 @@ int launch_tc_probe(const void* Apk, const void* Bpk, float* D, unsigned* err, c
   ABC_CUDA_TRY(cudaFuncSetAttribute(k_tc_probe, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(kTcSmem)));
   ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
-  k_tc_probe<<<1, kTcThreads, kTcSmem, st>>>(static_cast<const uint8_t*>(Apk),
+  k_tc_probe<<<1, kProbeThreads, kTcSmem, st>>>(static_cast<const uint8_t*>(Apk),
                                              static_cast<const uint8_t*>(Bpk), D, err);
   ABC_LAUNCH_CHECK();
   return ABC_OK;

@@ -304,13 +304,14 @@ def logw_tolerance(s, olw):
     """Bound on |log W_fp32 - log W_fp64| for the FP32 CUDA-core path.
 
     With a = 4 ln(2 pi s) and LSE = a - log W (natural log) the kernel's
-    per-column exponent e = c_k - D log2(e)/(2 s) carries at most ~8 ulp of
-    the magnitudes involved (fp32 differences: 1, pairwise squares and sums:
-    3, the scale 1/(2s): 2, the fused product-add: 1, rounding of c_k: 1),
-    i.e. <= 8 * 2^-24 * (|LSE| + |a|) after the ln 2 < 1 change of base, with
-    a factor 2 margin; summing 2^(e - m) in fp32 tiles of 128 terms plus a
-    Kahan fold adds <= 130 * 2^-24 relative to the row sum, i.e. absolute in
-    log W; the fp64 combine adds ~1e-15.  Together:
+    per-column exponent e = c_k - D log2(e)/(2 s) carries at most ~10 ulp of
+    the magnitudes involved (fp32 differences: 1, squares and sums in two
+    fp32x2 lanes of four terms plus the final add: 5, the scale 1/(2s): 2,
+    the fused product-add: 1, rounding of c_k: 1), i.e. <= 10 * 2^-24 *
+    (|LSE| + |a|) after the ln 2 < 1 change of base, with a factor 1.6
+    margin; summing 2^(e - m) (ex2.approx, ~2 ulp per term) in fp32 tiles of
+    128 terms plus a Kahan fold adds <= 132 * 2^-24 relative to the row sum,
+    i.e. absolute in log W; the fp64 combine adds ~1e-15.  Together:
         |d log W| <= 2^-24 (16 (|LSE| + |a|) + 160).
     That is about 1e-6 of the magnitudes of the two terms that are subtracted
     plus a 1e-5 floor from the fp32 row sums."""

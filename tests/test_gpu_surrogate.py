@@ -163,7 +163,7 @@ def test_mlp_forward_tc_vs_oracle(n):
     assert np.all(err <= bound), REPORT["mlp_forward_%d" % n]
 
 
-@pytest.mark.parametrize("Bn", [37, 300])
+@pytest.mark.parametrize("Bn", [37, 300, 2048])
 def test_mlp_gradient_vs_oracle(Bn):
     """Training pass on CUDA cores: bf16 weights, fp32 activations and sums.
     Every gradient is a sum over the batch of products the fp32 kernels form
