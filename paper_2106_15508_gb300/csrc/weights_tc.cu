@@ -57,6 +57,11 @@ constexpr int kProbeThreads = 192;                  // probe: 4 epilogue warps, 
 constexpr size_t kTcSmem = 1024 + kATile + kTcStages * kBTile + 256;
 constexpr float kSMinTc = 1e-30f;
 constexpr float kPadLogit = -1.0e30f;
+constexpr int kCandCap = 32;          // listed columns per (row, partial slot)
+constexpr float kCandMargin = 45.0f;  // log2 units: listed = within 45 bits of the maximum
+// error bound of the tensor-core exponent up to which its row value is kept:
+// the value of B at s = 1e-3 with |x|, |y| <= sqrt 2 (0.0166, natural log)
+constexpr float kTcBoundMax = 0x1p-24f * (64.0f * (6.0f * 721.34752f + 32.0f) + 160.0f);
 
 // instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B bf16
 // (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
@@ -111,28 +116,73 @@ __device__ __forceinline__ void store_packed_row(__nv_bfloat16* tile, int r, con
   }
 }
 
-// rows: features [2 L x (8), -L, 1]; rowc[j] = -L |x|^2 (fp64)
+// Row features [2 L x (8), -L, 1] and rowc[j] = -L |x|^2 (fp64), for every
+// row.  Also the row's class and refinement data.  The tensor-core
+// exponent of pair (j, k) is an fp32 sum of up to 64 products of total size
+// L_j (2 |x_j| |y_k| + |y_k|^2) + |c_k| <= L_j (2 |x_j| |y_k| + |y_k|^2) + 32,
+// so over the columns with |y_k| <= Y_j its error is at most
+//     delta_j = 2^-24 64 (L_j (2 |x_j| Y_j + Y_j^2) + 32)   (log2 units)
+// and the row's log W error at most B_j = 2^-24 (64 (L_j (2 |x_j| Y_j +
+// Y_j^2) + 32) + 160) (natural log, with the fp32 row sums).  Y_j is the
+// largest column radius, or, when the row's ancestor a is known,
+// |x_j| + R_j with R_j^2 = |u'_j - u_a|^2 + (60 - c_a) / L_j: the ancestor's
+// exponent e_a = c_a - L_j |u'_j - u_a|^2 bounds the maximum from below and
+// c_k < 0, so a column beyond R_j sits 60 bits under the maximum, and its own
+// error (a fraction ~2^-18 of L_j |y_k|^2, against a deficit of order
+// L_j (|y_k| - |x_j|)^2) keeps it there.
+//   class 0: B_j <= kTcBoundMax, the tensor-core value is kept;
+//   class 1: the epilogue lists the columns whose exponent may lie within
+//            kCandMargin bits of the row maximum and k_tc_refine recomputes
+//            the row exactly from them (rinfo = (ancestor lower bound of the
+//            maximum in the accumulator frame, delta_j));
+//   class 2: delta_j not finite: the FP32 kernel recomputes the row.
 __global__ void k_tc_pack_rows(const float* __restrict__ up, const float* __restrict__ s,
                                int64_t rows, int64_t rows_pad, const float* __restrict__ centre,
+                               const unsigned* __restrict__ y2max, AncInfo ai,
                                __nv_bfloat16* __restrict__ Apk, double* __restrict__ rowc,
-                               const int* __restrict__ rows_dev) {
+                               float2* __restrict__ rinfo, uint8_t* __restrict__ rcls) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= rows_pad) return;
-  const int64_t nrows = rows_dev ? static_cast<int64_t>(*rows_dev) : rows;
   float f[10];
-  if (j < nrows) {
+  if (j < rows) {
     const float sj = fmaxf(s[j], kSMinTc);
     const float L = 1.4426950408889634f / (2.0f * sj);
     double xx = 0.0;
+    float xxf = 0.0f, dd = 0.0f;
+    const int32_t a = ai.anc ? ai.anc[j] : -1;
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
-      const float x = up[static_cast<int64_t>(d) * rows + j] - centre[d];
+      const float u = up[static_cast<int64_t>(d) * rows + j];
+      const float x = u - centre[d];
       f[d] = 2.0f * L * x;
       xx += static_cast<double>(x) * static_cast<double>(x);
+      xxf = __fmaf_rn(x, x, xxf);
+      if (a >= 0) {
+        const float e = u - ai.u_prev[static_cast<int64_t>(d) * ai.n_prev + a];
+        dd = __fmaf_rn(e, e, dd);
+      }
     }
     f[8] = -L;
     f[9] = 1.0f;
     rowc[j] = -static_cast<double>(L) * xx;
+    // error bound over the columns that can matter
+    const float X = sqrtf(xxf);
+    float Y = sqrtf(__uint_as_float(*y2max));
+    float lb = -INFINITY;
+    if (a >= 0 && ai.q_prev[a] > 0u) {
+      const double ca = log2(static_cast<double>(ai.q_prev[a])) - 32.0;
+      // 1.001: margin for the fp32 rounding of this estimate
+      Y = fminf(Y, 1.001f * (X + sqrtf(dd + (60.0f - static_cast<float>(ca)) / L)));
+      // the ancestor's exponent in the accumulator frame (e - rowc), less a
+      // rounding margin: a lower bound of the row maximum there
+      const double ea = ca - static_cast<double>(L) * static_cast<double>(dd) + static_cast<double>(L) * xx;
+      lb = static_cast<float>(ea - (1.0 + 1e-3 * fabs(ea) + 1e-6 * static_cast<double>(L) * xx));
+    }
+    const float mag = L * (2.0f * X * Y + Y * Y) + 32.0f;
+    const float delta = 0x1p-24f * 64.0f * mag;
+    const float B = 0x1p-24f * (64.0f * mag + 160.0f);
+    rinfo[j] = make_float2(lb, delta);
+    rcls[j] = B <= kTcBoundMax ? 0 : (isfinite(delta) && delta < 1e30f ? 1 : 2);
   } else {
 #pragma unroll
     for (int d = 0; d < 10; ++d) f[d] = 0.0f;
@@ -244,12 +294,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
              const int* __restrict__ nc_p, int64_t rows,
              float2* __restrict__ part, unsigned* err, const int* __restrict__ off_dev,
-             const int* __restrict__ rows_dev) {
+             const float2* __restrict__ rinfo, const uint8_t* __restrict__ rcls,
+             int* __restrict__ cand, int* __restrict__ ccnt) {
   extern __shared__ uint8_t tc_smem_raw[];
   if (off_dev && *off_dev) return;  // run finished or its generation stopped (block-uniform)
-  // rows is the stride (capacity); rows_dev, when given, the rows in use
-  const int64_t nrows = rows_dev ? static_cast<int64_t>(*rows_dev) : rows;
-  if (static_cast<int64_t>(blockIdx.x) * kTcM >= nrows) return;
+  const int64_t nrows = rows;
   const TcSmem sm = tc_carve(tc_smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nc = *nc_p;
@@ -261,8 +310,11 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
   const int64_t row0 = static_cast<int64_t>(blockIdx.x) * kTcM;
   if (tb >= te) {  // no column tile in this chunk: neutral partials (both halves)
     const int g = threadIdx.x / kTcM, r = threadIdx.x % kTcM;
-    if (g < 2 && row0 + r < nrows)
-      part[(2 * static_cast<int64_t>(blockIdx.y) + g) * rows + row0 + r] = make_float2(-INFINITY, 0.0f);
+    if (g < 2 && row0 + r < nrows) {
+      const int64_t slot = 2 * static_cast<int64_t>(blockIdx.y) + g;
+      part[slot * rows + row0 + r] = make_float2(-INFINITY, 0.0f);
+      ccnt[slot * rows + row0 + r] = 0;
+    }
     return;
   }
   const int ntiles = te - tb;
@@ -345,6 +397,21 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     const int r = q * 32 + lane;
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(q * 32) << 16);
     float m = -INFINITY, S = 0.0f, cS = 0.0f;
+    // class-1 rows list the columns that may lie within kCandMargin bits of
+    // the row maximum: lb is a lower bound of the maximum (the ancestor's
+    // exponent, or the largest value seen so far less its error), so a column
+    // with v < lb - delta - margin is at least margin bits under it
+    const int64_t row = row0 + r;
+    const int64_t slot = 2 * static_cast<int64_t>(blockIdx.y) + g;
+    const bool refine = row < nrows && rcls[row] == 1;
+    float lb = -INFINITY, dl = 0.0f;
+    if (refine) {
+      const float2 ri = rinfo[row];
+      lb = ri.x;
+      dl = ri.y;
+    }
+    int* lst = cand + (slot * rows + row) * kCandCap;
+    int nlist = 0;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
       const uint32_t tph = static_cast<uint32_t>(t >> 1) & 1u;
@@ -359,6 +426,19 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
         float cm = v[0];
 #pragma unroll
         for (int i = 1; i < 32; ++i) cm = fmaxf(cm, v[i]);
+        if (refine) {
+          lb = fmaxf(lb, cm - dl);
+          const float thr = lb - dl - kCandMargin;
+          if (cm > thr) {
+            const int col0 = (tb + t) * kTcN + c * 32;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (v[i] > thr && col0 + i < nc) {
+                if (nlist < kCandCap) lst[nlist] = col0 + i;
+                ++nlist;
+              }
+          }
+        }
         if (cm > m) {
           const float f = ex2(m - cm);
           S *= f;
@@ -376,8 +456,10 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
       cS = (tt - S) - y;
       S = tt;
     }
-    if (row0 + r < nrows)
-      part[(2 * static_cast<int64_t>(blockIdx.y) + g) * rows + row0 + r] = make_float2(m, S);
+    if (row < nrows) {
+      part[slot * rows + row] = make_float2(m, S);
+      ccnt[slot * rows + row] = refine ? nlist : 0;
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -459,141 +541,62 @@ k_tc_probe(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
   if (warp == 5) tmem_dealloc(tmem, kTmemCols);
 }
 
-// ---- host side -----------------------------------------------------------------
-// column chunks: about two CTAs per SM in total, times a tuning multiplier
-static int tc_chunks(int64_t rows, int64_t ncap, int mult) {
-  const int64_t gx = ceil_div(std::max<int64_t>(rows, 1), kTcM);
-  const int64_t tiles = std::max<int64_t>(1, ceil_div(ncap, kTcN));
-  const int64_t want = std::max<int64_t>(1, ceil_div(2 * 152, gx)) * std::max(1, mult);
-  return static_cast<int>(std::min<int64_t>(want, tiles));
-}
-
-struct TcLayout {
-  size_t apk, bpk, rowc, part, err, total;
-};
-
-static TcLayout tc_layout(int64_t rows, int64_t ncap, int mult) {
-  TcLayout l{};
-  const int64_t rpad = ceil_div(std::max<int64_t>(rows, 1), kTcM) * kTcM;
-  const int64_t cpad = ceil_div(std::max<int64_t>(ncap, 1), kTcN) * kTcN;
-  size_t o = 0;
-  l.apk = o;
-  o += align256(static_cast<size_t>(rpad) * kTcK * 2);
-  l.bpk = o;
-  o += align256(static_cast<size_t>(cpad) * kTcK * 2);
-  l.rowc = o;
-  o += align256(sizeof(double) * static_cast<size_t>(rows));
-  l.part = o;
-  o += align256(sizeof(float2) * 2 * static_cast<size_t>(tc_chunks(rows, ncap, mult)) * rows);
-  l.err = o;
-  o += align256(sizeof(unsigned));
-  l.total = o;
-  return l;
-}
-
-int weights_tc_prepare() {
-  ABC_CUDA_TRY(cudaFuncSetAttribute(k_weights_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(kTcSmem)));
-  return ABC_OK;
-}
-
-static size_t tc_rows_scratch_bytes(int64_t rows, int64_t ncap, int mult) {
-  return tc_layout(rows, ncap, mult).total;
-}
-
-// Rows up/s (stride rows; rows_dev of them in use) against the columns that
-// the caller packed into the layout's B area (k_tc_pack_cols, capacity ncap)
-// with the same centre.  The error word is written into the scratch area and
-// its address returned in *err_dev.
-static int launch_weights_tc_rows(const float* up, const float* s, int64_t rows,
-                      const float* centre, const int* nc_dev, int64_t ncap,
-                      const uint64_t* total_p, double* logW, void* scratch, size_t bytes,
-                      unsigned** err_dev, cudaStream_t st, const int* off_dev, int mult,
-                      const int* rows_dev, const WeightTiming* wt) {
-  if (rows <= 0) return ABC_OK;
-  const TcLayout l = tc_layout(rows, ncap, mult);
-  if (bytes < l.total) return ABC_E_SCRATCH;
-  // the kernel's shared-memory opt-in is a function attribute: set it unless
-  // the stream is being captured (contexts set it when they are created)
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  ABC_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
-  if (cs == cudaStreamCaptureStatusNone) {
-    const int rc = weights_tc_prepare();
-    if (rc) return rc;
-  }
-  char* b = static_cast<char*>(scratch);
-  auto* Apk = reinterpret_cast<__nv_bfloat16*>(b + l.apk);
-  auto* Bpk = reinterpret_cast<__nv_bfloat16*>(b + l.bpk);
-  auto* rowc = reinterpret_cast<double*>(b + l.rowc);
-  auto* part = reinterpret_cast<float2*>(b + l.part);
-  auto* err = reinterpret_cast<unsigned*>(b + l.err);
-  if (err_dev) *err_dev = err;
-  ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
-  const int64_t rpad = ceil_div(rows, kTcM) * kTcM;
-  k_tc_pack_rows<<<static_cast<unsigned>(ceil_div(rpad, 128)), 128, 0, st>>>(
-      up, s, rows, rpad, centre, Apk, rowc, rows_dev);
-  ABC_LAUNCH_CHECK();
-  const int nch = tc_chunks(rows, ncap, mult);
-  dim3 grid(static_cast<unsigned>(rpad / kTcM), static_cast<unsigned>(nch));
-  if (wt && wt->tc0) ABC_CUDA_TRY(cudaEventRecord(wt->tc0, st));
-  k_weights_tc<<<grid, kTcThreads, kTcSmem, st>>>(reinterpret_cast<const uint8_t*>(Apk),
-                                                  reinterpret_cast<const uint8_t*>(Bpk), nc_dev,
-                                                  rows, part, err, off_dev, rows_dev);
-  ABC_LAUNCH_CHECK();
-  if (wt && wt->tc1) ABC_CUDA_TRY(cudaEventRecord(wt->tc1, st));
-  k_weights_tc_combine<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(
-      part, 2 * nch, s, rowc, rows, total_p, logW, off_dev, rows_dev);
-  ABC_LAUNCH_CHECK();
-  return ABC_OK;
-}
-
-// ---- split by error bound: tensor cores where it is small, FP32 elsewhere --
-// The tensor-core exponent of pair (j, k) is an fp32 sum of up to 64 products
-// of total size L_j (2 |x_j| |y_k| + |y_k|^2) + |c_k| <= L_j (2 |x_j| |y_k| +
-// |y_k|^2) + 32, so with |y_k| <= Y_j over the columns that can matter the
-// row's log W error is at most
-//     B_j = 2^-24 (64 (L_j (2 |x_j| Y_j + Y_j^2) + 32) + 160)   (natural log)
-// including the fp32 row sums.  Y_j is the largest column radius
-// (max_k |y_k|), or, when the row's ancestor a is known, |x_j| + R_j with
-//     R_j^2 = |u'_j - u_a|^2 + (60 - c_a) / L_j:
-// the ancestor's own exponent e_a = c_a - L_j |u'_j - u_a|^2 bounds the row
-// maximum from below and c_k < 0, so a column farther than R_j has e_jk <
-// max - 60; its error grows at most like L_j |y_k|^2 2^-18 while its deficit
-// grows like L_j (|y_k| - |x_j|)^2, so it stays far inside the 60-bit margin
-// and the column carries under ~2^-59 of the maximum term.  Rows with B_j <= kTcBoundMax (the
-// value of B at s = 1e-3 with |x|, |y| <= sqrt 2, 0.0166) run on tcgen05, the
-// rest on the FP32 direct-difference kernel.  The partition, both passes and
-// the scatter back run on the device with the row counts in device memory
-// (no host round trip, so it also runs inside graphs).
-constexpr float kTcBoundMax = 0x1p-24f * (64.0f * (6.0f * 721.34752f + 32.0f) + 160.0f);
-constexpr int kPartTile = 1024;
-
-__device__ __forceinline__ bool tc_row(const float* __restrict__ up, int64_t rows, int64_t j,
-                                       float sj, const float* __restrict__ centre, float y2,
-                                       const AncInfo& ai) {
-  const float L = 1.4426950408889634f / (2.0f * fmaxf(sj, kSMinTc));
-  float xx = 0.0f, dd = 0.0f;
-  const int32_t a = ai.anc ? ai.anc[j] : -1;
-#pragma unroll
-  for (int d = 0; d < 8; ++d) {
-    const float u = up[static_cast<int64_t>(d) * rows + j];
-    const float x = u - centre[d];
-    xx = __fmaf_rn(x, x, xx);
-    if (a >= 0) {
-      const float e = u - ai.u_prev[static_cast<int64_t>(d) * ai.n_prev + a];
-      dd = __fmaf_rn(e, e, dd);
+// ---- exact recomputation of class-1 rows -------------------------------------
+// One thread per row: the listed columns of every partial slot (at most
+// kCandCap each; more sends the row to the FP32 kernel as class 2), exponents
+// from direct differences as in the FP32 kernel, maximum and fp64 sum.
+// Unlisted columns lie at least kCandMargin bits under the maximum: together
+// at most nc 2^-45 of the row sum.
+__global__ void k_tc_refine(const float* __restrict__ up, const float* __restrict__ s,
+                            int64_t rows, uint8_t* __restrict__ rcls, const int* __restrict__ cand,
+                            const int* __restrict__ ccnt, int nslots, const float* __restrict__ cu,
+                            const float* __restrict__ cc, int64_t ncap,
+                            const uint64_t* __restrict__ total_p, double* __restrict__ logW,
+                            const int* __restrict__ off_dev) {
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= rows || (off_dev && *off_dev) || rcls[j] != 1) return;
+  for (int sl = 0; sl < nslots; ++sl)
+    if (ccnt[static_cast<int64_t>(sl) * rows + j] > kCandCap) {
+      rcls[j] = 2;
+      return;
     }
+  float x[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) x[d] = up[static_cast<int64_t>(d) * rows + j];
+  const float sj = fmaxf(s[j], kSMinTc);
+  const float ninv = -1.4426950408889634f / (2.0f * sj);
+  auto expo = [&](int k) {
+    float q[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const float a = x[2 * h] - cu[static_cast<int64_t>(2 * h) * ncap + k];
+      const float b = x[2 * h + 1] - cu[static_cast<int64_t>(2 * h + 1) * ncap + k];
+      q[h] = __fmaf_rn(a, a, b * b);
+    }
+    return __fmaf_rn((q[0] + q[1]) + (q[2] + q[3]), ninv, cc[k]);
+  };
+  float m = -INFINITY;
+  for (int sl = 0; sl < nslots; ++sl) {
+    const int n = ccnt[static_cast<int64_t>(sl) * rows + j];
+    const int* l = cand + (static_cast<int64_t>(sl) * rows + j) * kCandCap;
+    for (int i = 0; i < n; ++i) m = fmaxf(m, expo(l[i]));
   }
-  const float X = sqrtf(xx);
-  float Y = sqrtf(y2);
-  if (a >= 0 && ai.q_prev[a] > 0u) {
-    const float ca = static_cast<float>(log2(static_cast<double>(ai.q_prev[a])) - 32.0);
-    // 1.001: margin for the fp32 rounding of this estimate
-    Y = fminf(Y, 1.001f * (X + sqrtf(dd + (60.0f - ca) / L)));
+  double S = 0.0;
+  for (int sl = 0; sl < nslots; ++sl) {
+    const int n = ccnt[static_cast<int64_t>(sl) * rows + j];
+    const int* l = cand + (static_cast<int64_t>(sl) * rows + j) * kCandCap;
+    for (int i = 0; i < n; ++i) S += exp2(static_cast<double>(expo(l[i]) - m));
   }
-  const float mag = L * (2.0f * X * Y + Y * Y) + 32.0f;
-  return 0x1p-24f * (64.0f * mag + 160.0f) <= kTcBoundMax;
+  if (!(S > 0.0)) {  // nothing listed (cannot happen: the maximum is listed)
+    rcls[j] = 2;
+    return;
+  }
+  const double lse2 = static_cast<double>(m) + log2(S) + 32.0 - log2(static_cast<double>(*total_p));
+  logW[j] = 4.0 * log(6.283185307179586 * static_cast<double>(sj)) - 0.6931471805599453 * lse2;
 }
+
+// ---- class-2 rows through the FP32 kernel ----------------------------------------
+constexpr int kPartTile = 1024;
 constexpr int kFp32Mult = 8;  // column chunks of the FP32 share (its rows are few)
 
 int launch_weights_fp32(const float*, const float*, int64_t, const float*, const float*, const int*,
@@ -601,25 +604,21 @@ int launch_weights_fp32(const float*, const float*, int64_t, const float*, const
                         const int*, int, const int*, const WeightTiming*);
 size_t weights_fp32_scratch_bytes(int64_t, int64_t, int);
 
-__global__ void k_part_count(const float* __restrict__ up, const float* __restrict__ s,
-                             int64_t rows, const float* __restrict__ centre,
-                             const unsigned* __restrict__ y2max, AncInfo ai,
-                             int* __restrict__ cnt) {
+__global__ void k_fb_count(const uint8_t* __restrict__ rcls, int64_t rows, int* __restrict__ cnt) {
   __shared__ int sm[32];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kPartTile;
-  const float y2 = __uint_as_float(*y2max);
   int c = 0;
   for (int e = threadIdx.x; e < kPartTile; e += blockDim.x) {
     const int64_t j = base + e;
-    c += (j < rows && !tc_row(up, rows, j, s[j], centre, y2, ai));
+    c += (j < rows && rcls[j] == 2);
   }
   c = block_sum<int>(c, sm);
   if (threadIdx.x == 0) cnt[blockIdx.x] = c;
 }
 
-// exclusive offsets of the small rows per tile; counts[0] = small, [1] = large
-__global__ void k_part_scan(const int* __restrict__ cnt, int ntiles, int64_t rows,
-                            int* __restrict__ off, int* __restrict__ counts) {
+// exclusive offsets of the class-2 rows per tile; counts[0] = class 2, [1] = the rest
+__global__ void k_fb_scan(const int* __restrict__ cnt, int ntiles, int64_t rows,
+                          int* __restrict__ off, int* __restrict__ counts) {
   __shared__ int sm[32];
   __shared__ int last;
   int carry = 0;
@@ -639,129 +638,144 @@ __global__ void k_part_scan(const int* __restrict__ cnt, int ntiles, int64_t row
   }
 }
 
-// gathers both row sets (SoA, stride rows) with their original indices
-__global__ void k_part_scatter(const float* __restrict__ up, const float* __restrict__ s,
-                               int64_t rows, const float* __restrict__ centre,
-                               const unsigned* __restrict__ y2max, AncInfo ai,
-                               const int* __restrict__ off,
-                               int* __restrict__ idx_s, int* __restrict__ idx_l,
-                               float* __restrict__ u_s, float* __restrict__ s_s,
-                               float* __restrict__ u_l, float* __restrict__ s_l) {
+// gathers the class-2 rows (SoA, stride rows) with their original indices
+__global__ void k_fb_scatter(const uint8_t* __restrict__ rcls, const float* __restrict__ up,
+                             const float* __restrict__ s, int64_t rows, const int* __restrict__ off,
+                             int* __restrict__ idx, float* __restrict__ u_f,
+                             float* __restrict__ s_f) {
   __shared__ int sm[32];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kPartTile + 4 * threadIdx.x;
-  const float y2 = __uint_as_float(*y2max);
-  bool small[4];
+  bool fb[4];
   int c = 0;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    small[e] = base + e < rows && !tc_row(up, rows, base + e, s[base + e], centre, y2, ai);
-    c += small[e];
+    fb[e] = base + e < rows && rcls[base + e] == 2;
+    c += fb[e];
   }
   const int inc = block_incl_scan<int>(c, sm);
-  int64_t ps = off[blockIdx.x] + inc - c;
+  int64_t p = off[blockIdx.x] + inc - c;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
+    if (!fb[e]) continue;
     const int64_t j = base + e;
-    if (j >= rows) break;
-    if (small[e]) {
-      idx_s[ps] = static_cast<int>(j);
+    idx[p] = static_cast<int>(j);
 #pragma unroll
-      for (int d = 0; d < 8; ++d) u_s[d * rows + ps] = up[d * rows + j];
-      s_s[ps] = s[j];
-      ++ps;
-    } else {
-      const int64_t pl = j - ps;  // rows before j that are large
-      idx_l[pl] = static_cast<int>(j);
-#pragma unroll
-      for (int d = 0; d < 8; ++d) u_l[d * rows + pl] = up[d * rows + j];
-      s_l[pl] = s[j];
-    }
+    for (int d = 0; d < 8; ++d) u_f[d * rows + p] = up[d * rows + j];
+    s_f[p] = s[j];
+    ++p;
   }
 }
 
-__global__ void k_part_back(const int* __restrict__ idx_s, const int* __restrict__ idx_l,
-                            const double* __restrict__ lw_s, const double* __restrict__ lw_l,
-                            const int* __restrict__ counts, double* __restrict__ logW,
-                            const int* __restrict__ off_dev) {
+__global__ void k_fb_back(const int* __restrict__ idx, const double* __restrict__ lw_f,
+                          const int* __restrict__ counts, double* __restrict__ logW,
+                          const int* __restrict__ off_dev) {
   if (off_dev && *off_dev) return;
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i < counts[0]) logW[idx_s[i]] = lw_s[i];
-  if (i < counts[1]) logW[idx_l[i]] = lw_l[i];
+  if (i < counts[0]) logW[idx[i]] = lw_f[i];
 }
 
-struct HyLayout {
-  size_t tc, fp, cnt, off, counts, idx_s, idx_l, u_s, s_s, u_l, s_l, lw_s, lw_l, ctr, total;
+// ---- host side -----------------------------------------------------------------
+// column chunks: about two CTAs per SM in total, times a tuning multiplier
+static int tc_chunks(int64_t rows, int64_t ncap, int mult) {
+  const int64_t gx = ceil_div(std::max<int64_t>(rows, 1), kTcM);
+  const int64_t tiles = std::max<int64_t>(1, ceil_div(ncap, kTcN));
+  const int64_t want = std::max<int64_t>(1, ceil_div(2 * 152, gx)) * std::max(1, mult);
+  return static_cast<int>(std::min<int64_t>(want, tiles));
+}
+
+struct TcLayout {
+  size_t apk, bpk, rowc, part, err, rinfo, rcls, cand, ccnt, fp, cnt, off, counts, idx, u_f, s_f,
+      lw_f, ctr, total;
 };
 
-static HyLayout hy_layout(int64_t rows, int64_t ncap, int mult) {
-  HyLayout l{};
+static TcLayout tc_layout(int64_t rows, int64_t ncap, int mult) {
+  TcLayout l{};
+  const int64_t rpad = ceil_div(std::max<int64_t>(rows, 1), kTcM) * kTcM;
+  const int64_t cpad = ceil_div(std::max<int64_t>(ncap, 1), kTcN) * kTcN;
+  const size_t R = static_cast<size_t>(std::max<int64_t>(rows, 1));
+  const size_t slots = 2 * static_cast<size_t>(tc_chunks(rows, ncap, mult));
   const int64_t nt = ceil_div(std::max<int64_t>(rows, 1), kPartTile);
-  const size_t R = static_cast<size_t>(rows);
   size_t o = 0;
-  l.tc = o;
-  o += align256(tc_rows_scratch_bytes(rows, ncap, mult));
-  l.fp = o;
-  o += align256(weights_fp32_scratch_bytes(rows, ncap, kFp32Mult));
-  l.cnt = o;
-  o += align256(4 * nt);
-  l.off = o;
-  o += align256(4 * nt);
-  l.counts = o;
-  o += align256(8);
-  l.idx_s = o;
-  o += align256(4 * R);
-  l.idx_l = o;
-  o += align256(4 * R);
-  l.u_s = o;
-  o += align256(32 * R);
-  l.s_s = o;
-  o += align256(4 * R);
-  l.u_l = o;
-  o += align256(32 * R);
-  l.s_l = o;
-  o += align256(4 * R);
-  l.lw_s = o;
-  o += align256(8 * R);
-  l.lw_l = o;
-  o += align256(8 * R);
-  l.ctr = o;  // column partial sums, centre[8], radius word
-  o += align256(sizeof(double) * 8 * kCtrBlocks) + align256(8 * sizeof(float)) + align256(4);
+  auto take = [&](size_t& field, size_t bytes) {
+    field = o;
+    o += align256(bytes);
+  };
+  take(l.apk, static_cast<size_t>(rpad) * kTcK * 2);
+  take(l.bpk, static_cast<size_t>(cpad) * kTcK * 2);
+  take(l.rowc, sizeof(double) * R);
+  take(l.part, sizeof(float2) * slots * R);
+  take(l.err, sizeof(unsigned));
+  take(l.rinfo, sizeof(float2) * R);
+  take(l.rcls, R);
+  take(l.cand, sizeof(int) * slots * R * kCandCap);
+  take(l.ccnt, sizeof(int) * slots * R);
+  take(l.fp, weights_fp32_scratch_bytes(rows, ncap, kFp32Mult));
+  take(l.cnt, 4 * static_cast<size_t>(nt));
+  take(l.off, 4 * static_cast<size_t>(nt));
+  take(l.counts, 8);
+  take(l.idx, 4 * R);
+  take(l.u_f, 32 * R);
+  take(l.s_f, 4 * R);
+  take(l.lw_f, 8 * R);
+  take(l.ctr, sizeof(double) * 8 * kCtrBlocks + 256 + 256);  // column sums, centre, radius
   l.total = o;
   return l;
 }
 
-size_t weights_tc_scratch_bytes(int64_t rows, int64_t ncap, int mult) {
-  return hy_layout(rows, ncap, mult).total;
+int weights_tc_prepare() {
+  ABC_CUDA_TRY(cudaFuncSetAttribute(k_weights_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(kTcSmem)));
+  return ABC_OK;
 }
 
+size_t weights_tc_scratch_bytes(int64_t rows, int64_t ncap, int mult) {
+  return tc_layout(rows, ncap, mult).total;
+}
+
+// Every row on the tensor cores; class-1 rows (error bound above
+// kTcBoundMax) recomputed exactly from their listed columns, class-2 rows
+// (and class-1 rows whose lists overflowed) by the FP32 kernel.  All
+// decisions and counts stay on the device (graph-capturable).
 int launch_weights_tc(const float* up, const float* s, int64_t rows, const float* cu,
                       const float* cc, const int* nc_dev, int64_t ncap, const uint64_t* total_p,
                       double* logW, void* scratch, size_t bytes, unsigned** err_dev,
                       cudaStream_t st, const int* off_dev, int mult, const int* rows_dev,
                       const AncInfo& ai, WeightTiming* wt) {
   if (rows <= 0) return ABC_OK;
-  if (rows_dev) return ABC_E_INVAL;  // the split works on full row sets only
-  const HyLayout l = hy_layout(rows, ncap, mult);
+  if (rows_dev) return ABC_E_INVAL;  // full row sets only
+  const TcLayout l = tc_layout(rows, ncap, mult);
   if (bytes < l.total) return ABC_E_SCRATCH;
+  // the kernel's shared-memory opt-in is a function attribute: set it unless
+  // the stream is being captured (contexts set it when they are created)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  ABC_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+  if (cs == cudaStreamCaptureStatusNone) {
+    const int rc = weights_tc_prepare();
+    if (rc) return rc;
+  }
   char* b = static_cast<char*>(scratch);
-  int* cnt = reinterpret_cast<int*>(b + l.cnt);
-  int* off = reinterpret_cast<int*>(b + l.off);
-  int* counts = reinterpret_cast<int*>(b + l.counts);
-  int* idx_s = reinterpret_cast<int*>(b + l.idx_s);
-  int* idx_l = reinterpret_cast<int*>(b + l.idx_l);
-  float* u_s = reinterpret_cast<float*>(b + l.u_s);
-  float* s_s = reinterpret_cast<float*>(b + l.s_s);
-  float* u_l = reinterpret_cast<float*>(b + l.u_l);
-  float* s_l = reinterpret_cast<float*>(b + l.s_l);
-  double* lw_s = reinterpret_cast<double*>(b + l.lw_s);
-  double* lw_l = reinterpret_cast<double*>(b + l.lw_l);
+  auto* Apk = reinterpret_cast<__nv_bfloat16*>(b + l.apk);
+  auto* Bpk = reinterpret_cast<__nv_bfloat16*>(b + l.bpk);
+  auto* rowc = reinterpret_cast<double*>(b + l.rowc);
+  auto* part = reinterpret_cast<float2*>(b + l.part);
+  auto* err = reinterpret_cast<unsigned*>(b + l.err);
+  auto* rinfo = reinterpret_cast<float2*>(b + l.rinfo);
+  auto* rcls = reinterpret_cast<uint8_t*>(b + l.rcls);
+  auto* cand = reinterpret_cast<int*>(b + l.cand);
+  auto* ccnt = reinterpret_cast<int*>(b + l.ccnt);
+  auto* cnt = reinterpret_cast<int*>(b + l.cnt);
+  auto* off = reinterpret_cast<int*>(b + l.off);
+  auto* counts = reinterpret_cast<int*>(b + l.counts);
+  auto* idx = reinterpret_cast<int*>(b + l.idx);
+  auto* u_f = reinterpret_cast<float*>(b + l.u_f);
+  auto* s_f = reinterpret_cast<float*>(b + l.s_f);
+  auto* lw_f = reinterpret_cast<double*>(b + l.lw_f);
   auto* cpart = reinterpret_cast<double*>(b + l.ctr);
-  auto* centre = reinterpret_cast<float*>(b + l.ctr + align256(sizeof(double) * 8 * kCtrBlocks));
-  auto* y2max = reinterpret_cast<unsigned*>(b + l.ctr + align256(sizeof(double) * 8 * kCtrBlocks) +
-                                            align256(8 * sizeof(float)));
-  // centre and radius of the columns; the columns are packed once, centred
-  const TcLayout tl = tc_layout(rows, ncap, mult);
-  auto* Bpk = reinterpret_cast<__nv_bfloat16*>(b + l.tc + tl.bpk);
+  auto* centre = reinterpret_cast<float*>(b + l.ctr + sizeof(double) * 8 * kCtrBlocks);
+  auto* y2max = reinterpret_cast<unsigned*>(b + l.ctr + sizeof(double) * 8 * kCtrBlocks + 256);
+  if (err_dev) *err_dev = err;
+  ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
+  // columns: centre, radius, packed once (centred)
   const int64_t cpad = ceil_div(std::max<int64_t>(ncap, 1), kTcN) * kTcN;
   k_col_sum<<<kCtrBlocks, 256, 0, st>>>(cu, nc_dev, ncap, cpart);
   ABC_LAUNCH_CHECK();
@@ -770,23 +784,41 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   k_tc_pack_cols<<<static_cast<unsigned>(ceil_div(cpad, 128)), 128, 0, st>>>(
       cu, cc, nc_dev, ncap, cpad, centre, Bpk, y2max);
   ABC_LAUNCH_CHECK();
-  // rows split by their error bound
+  // rows: features, classes, refinement data
+  const int64_t rpad = ceil_div(rows, kTcM) * kTcM;
+  k_tc_pack_rows<<<static_cast<unsigned>(ceil_div(rpad, 128)), 128, 0, st>>>(
+      up, s, rows, rpad, centre, y2max, ai, Apk, rowc, rinfo, rcls);
+  ABC_LAUNCH_CHECK();
+  // every row on the tensor cores
+  const int nch = tc_chunks(rows, ncap, mult);
+  dim3 grid(static_cast<unsigned>(rpad / kTcM), static_cast<unsigned>(nch));
+  if (wt && wt->tc0) ABC_CUDA_TRY(cudaEventRecord(wt->tc0, st));
+  k_weights_tc<<<grid, kTcThreads, kTcSmem, st>>>(reinterpret_cast<const uint8_t*>(Apk),
+                                                  reinterpret_cast<const uint8_t*>(Bpk), nc_dev,
+                                                  rows, part, err, off_dev, rinfo, rcls, cand,
+                                                  ccnt);
+  ABC_LAUNCH_CHECK();
+  if (wt && wt->tc1) ABC_CUDA_TRY(cudaEventRecord(wt->tc1, st));
+  k_weights_tc_combine<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(
+      part, 2 * nch, s, rowc, rows, total_p, logW, off_dev, nullptr);
+  ABC_LAUNCH_CHECK();
+  // class 1: exact from the listed columns (overflow -> class 2)
+  k_tc_refine<<<static_cast<unsigned>(ceil_div(rows, 128)), 128, 0, st>>>(
+      up, s, rows, rcls, cand, ccnt, 2 * nch, cu, cc, ncap, total_p, logW, off_dev);
+  ABC_LAUNCH_CHECK();
+  // class 2: the FP32 kernel
   const int64_t nt = ceil_div(rows, kPartTile);
-  k_part_count<<<static_cast<unsigned>(nt), 256, 0, st>>>(up, s, rows, centre, y2max, ai, cnt);
+  k_fb_count<<<static_cast<unsigned>(nt), 256, 0, st>>>(rcls, rows, cnt);
   ABC_LAUNCH_CHECK();
-  k_part_scan<<<1, 1024, 0, st>>>(cnt, static_cast<int>(nt), rows, off, counts);
+  k_fb_scan<<<1, 1024, 0, st>>>(cnt, static_cast<int>(nt), rows, off, counts);
   ABC_LAUNCH_CHECK();
-  k_part_scatter<<<static_cast<unsigned>(nt), 256, 0, st>>>(up, s, rows, centre, y2max, ai, off,
-                                                            idx_s, idx_l, u_s, s_s, u_l, s_l);
+  k_fb_scatter<<<static_cast<unsigned>(nt), 256, 0, st>>>(rcls, up, s, rows, off, idx, u_f, s_f);
   ABC_LAUNCH_CHECK();
-  int rc = launch_weights_fp32(u_s, s_s, rows, cu, cc, nc_dev, ncap, total_p, lw_s, b + l.fp,
+  int rc = launch_weights_fp32(u_f, s_f, rows, cu, cc, nc_dev, ncap, total_p, lw_f, b + l.fp,
                                l.cnt - l.fp, st, off_dev, kFp32Mult, counts + 0, wt);
   if (rc) return rc;
-  rc = launch_weights_tc_rows(u_l, s_l, rows, centre, nc_dev, ncap, total_p, lw_l, b + l.tc,
-                              l.fp - l.tc, err_dev, st, off_dev, mult, counts + 1, wt);
-  if (rc) return rc;
-  k_part_back<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(idx_s, idx_l, lw_s, lw_l,
-                                                                         counts, logW, off_dev);
+  k_fb_back<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(idx, lw_f, counts, logW,
+                                                                       off_dev);
   ABC_LAUNCH_CHECK();
   if (wt) wt->counts = counts;
   return ABC_OK;

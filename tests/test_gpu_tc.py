@@ -5,7 +5,8 @@
    product and partial sum exact in fp32, so D must equal A B^T exactly.
 2. abc_weights with ABC_P_BF16_TC against the fp64 oracle: the error is
    stated (written to the parity report) and bounded by the error model of
-   the fp32 tensor-memory accumulation (logw_tc_bound).
+   the fp32 tensor-memory accumulation (logw_tc_bound); rows whose model
+   bound is too large are recomputed exactly and take the FP32 bound.
 3. A generation of the context on the tensor-core path reproduces the
    oracle's proposals and distances bit for bit; its weights follow (2).
 """
@@ -102,12 +103,15 @@ def tc_row_bound(up, s, u, q):
 
 def logw_tc_bound(up, s, olw, u, q):
     """Rows whose bound B_j is at most TC_BOUND_MAX (the bound at s = 1e-3
-    with |x|, |y| <= sqrt 2) run on tcgen05 and take B_j; the others run on
-    the FP32 path and take its tolerance.  A row within 1% of the cut may be
-    on either side (the library evaluates B_j in fp32)."""
+    with |x|, |y| <= sqrt 2) keep their tensor-core value and take B_j.  The
+    others are recomputed exactly from the columns that can lie within 45
+    bits of the row maximum (or by the FP32 kernel): they take the FP32
+    tolerance plus the dropped columns' share, at most nc 2^-45 of the row
+    sum.  A row within 1% of the cut may be on either side (the library
+    evaluates B_j in fp32)."""
     from test_gpu_parity import logw_tolerance
     B = tc_row_bound(up, s, u, q)
-    fp = logw_tolerance(s, olw)
+    fp = logw_tolerance(s, olw) + int(np.sum(q > 0)) * 2.0**-45
     return np.where(B <= 1.01 * TC_BOUND_MAX, np.maximum(B, fp), fp)
 
 
@@ -135,7 +139,7 @@ def _state_errors(name, lw, olw, s, up, u, q):
                         max_err_over_bound=float((err / bound).max()),
                         tv_normalised_W=float(0.5 * np.abs(W - Wg).sum()),
                         rows=int(len(err)),
-                        fraction_fp32=float(np.mean(tc_row_bound(up, s, u, q) > TC_BOUND_MAX)))
+                        fraction_exact=float(np.mean(tc_row_bound(up, s, u, q) > TC_BOUND_MAX)))
     print(name, REPORT[name])
     assert np.all(np.isfinite(lw))
     assert np.all(err <= bound), REPORT[name]
@@ -144,7 +148,7 @@ def _state_errors(name, lw, olw, s, up, u, q):
 @pytest.mark.parametrize("rows,n,slo,shi", [(4096, 4096, 1e-4, 0.3), (777, 5003, 1e-4, 0.3),
                                              (130, 300, 1e-4, 0.3),
                                              (1000, 2000, 2e-3, 0.3),     # every row on tcgen05
-                                             (1000, 2000, 1e-7, 9e-4)])   # mostly FP32
+                                             (1000, 2000, 1e-7, 9e-4)])   # mostly recomputed
 def test_weights_tc_vs_oracle(rows, n, slo, shi):
     up = IN.clustered_particles(rows, rows, 0.5, 0.15)
     u = IN.clustered_particles(n, n + 1, 0.5, 0.15)
@@ -153,6 +157,38 @@ def test_weights_tc_vs_oracle(rows, n, slo, shi):
     lw, tot = _weights(up, s, u, q, G.ABC_P_BF16_TC)
     olw = O.weights(up, s, u, q, tot, nthreads=8)
     _state_errors("weights_tc_%dx%d_s%g" % (rows, n, slo), lw, olw, s, up, u, q)
+
+
+def test_weights_tc_tiny_steps_recomputed():
+    """Steps of 1e-20..1e-9 (far below any tensor-core precision): every row
+    is recomputed exactly from the few columns near it."""
+    rows, n = 600, 3001
+    up = IN.clustered_particles(rows, 31, 0.5, 0.15)
+    u = IN.clustered_particles(n, 32, 0.5, 0.15)
+    s = IN.step_sizes(rows, 33, 1e-20, 1e-9)
+    q = IN.quantised_weights(n, 34)
+    lw, tot = _weights(up, s, u, q, G.ABC_P_BF16_TC)
+    olw = O.weights(up, s, u, q, tot, nthreads=8)
+    _state_errors("weights_tc_tiny_s", lw, olw, s, up, u, q)
+
+
+def test_weights_tc_dense_cluster_falls_back_to_fp32():
+    """Two dense column clusters far apart put the centre between them, so
+    rows inside one cluster have large error bounds while thousands of
+    columns lie within the listing margin: the lists overflow and the rows
+    go through the FP32 kernel."""
+    r = np.random.default_rng(35)
+    n = 6000
+    u = np.empty((8, n), np.float32)
+    u[:, :3000] = np.clip(0.9 + 0.01 * r.standard_normal((8, 3000)), 0, 1)
+    u[:, 3000:] = np.clip(0.1 + 0.01 * r.standard_normal((8, 3000)), 0, 1)
+    rows = 700
+    up = np.clip(0.9 + 0.01 * r.standard_normal((8, rows)), 0, 1).astype(np.float32)
+    s = np.exp(r.uniform(np.log(5e-5), np.log(2e-4), rows)).astype(np.float32)
+    q = IN.quantised_weights(n, 36, zero_frac=0.0)
+    lw, tot = _weights(up, s, u, q, G.ABC_P_BF16_TC)
+    olw = O.weights(up, s, u, q, tot, nthreads=8)
+    _state_errors("weights_tc_dense_cluster", lw, olw, s, up, u, q)
 
 
 def test_weights_tc_full_size_sampled_rows():
