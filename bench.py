@@ -104,6 +104,17 @@ def synthetic_obs(G, WL, cfg, torch):
     return obs.cpu().numpy(), th.cpu().numpy()
 
 
+def _nvtx(torch, name):
+    """Push (name) or pop (None) an NVTX range; a no-op where torch lacks NVTX."""
+    try:
+        if name is None:
+            torch.cuda.nvtx.range_pop()
+        else:
+            torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -153,6 +164,9 @@ def run_gpu(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
+            # NVTX range "timed" (host calls outside the events): lets a profiler
+            # keep the timed generations only
+            _nvtx(torch, "timed")
             e0.record(stream)
             for k in range(args.steps):
                 if k:
@@ -162,6 +176,7 @@ def run_gpu(args):
                     raise RuntimeError("timed generation stopped: %s" % G.strerror(rc))
                 stats.append(G.abc_get_stats(ctx, G.abc_generations(ctx) - 1))
             e1.record(stream)
+            _nvtx(torch, None)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         if ws > 1:
@@ -381,6 +396,104 @@ def cpu_baseline(stats, w):
                           n_sim, w.T, t_sim, rows, cols, t_w, days, pairs)}
 
 
+def run_eps_final(args):
+    """Wall-time to eps_final per run.  The runs of the batched workload
+    (importance weights) first run G generations each in plain contexts;
+    eps_final of a run is its tolerance at generation G.  The same runs then
+    reach eps_final (1) batched: one graph launch per generation of all runs
+    (bit-identical results, so the same G generations), (2) with the
+    surrogate pre-screen in their own contexts (generations until eps <=
+    eps_final, at most 3 G).  Reported: mean wall-time per run of each form
+    (host clock around device-synchronised generations)."""
+    import numpy as np
+    import torch
+
+    import paper_2106_15508_gb300 as G
+    from paper_2106_15508_gb300 import build as B
+    from paper_2106_15508_gb300 import workloads as WL
+
+    B.build()
+    G.lib()
+    runs = WL.batched_runs(args.runs, weight_prec=args.prec)
+    cfgs = [w.config() for w in runs]
+    obs = [synthetic_obs(G, WL, c, torch)[0] for c in cfgs]
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    gens = args.generations
+    # plain
+    eps_final, t_plain, sims_plain = [], [], []
+    for c, o in zip(cfgs, obs):
+        ctx = G.abc_init(c, o, stream=sp)
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            G.abc_run(ctx, gens + 1)
+            torch.cuda.synchronize()
+            t_plain.append(time.perf_counter() - t0)
+            st = [G.abc_get_stats(ctx, t) for t in range(G.abc_generations(ctx))]
+            eps_final.append(st[-1].eps)
+            sims_plain.append(sum(x.sims for x in st))
+        finally:
+            G.abc_free(ctx)
+    # batched
+    b = G.abc_batch_init(cfgs, obs, stream=sp)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.abc_batch_run(b, gens + 1)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        last = G.abc_batch_generations(b) - 1
+        eps_b = [G.abc_batch_get_stats(b, r, last).eps for r in range(len(cfgs))]
+    finally:
+        G.abc_batch_free(b)
+    # surrogate
+    t_sur, gens_sur, sims_sur, frr, reached = [], [], [], [], 0
+    for c, o, ef in zip(cfgs, obs, eps_final):
+        sc = G.config(**{f: getattr(c, f) if not hasattr(getattr(c, f), "_length_")
+                         else list(getattr(c, f)) for f, _ in c._fields_})
+        sc.surrogate, sc.surrogate_start, sc.surrogate_steps = 1, 2, args.surrogate_steps
+        sc.surrogate_batch, sc.surrogate_tau = 4096, args.surrogate_tau
+        sc.surrogate_rho_min, sc.audit_frac = 0.05, 0.01
+        ctx = G.abc_init(sc, o, stream=sp)
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc = G.abc_generation(ctx)  # stage 0
+            n = 1
+            while rc == G.ABC_OK and n < 3 * gens + 1:
+                rc = G.abc_generation(ctx)
+                n += 1
+                if G.abc_get_stats(ctx, n - 1).eps <= ef:
+                    break
+            torch.cuda.synchronize()
+            t_sur.append(time.perf_counter() - t0)
+            st = [G.abc_get_stats(ctx, t) for t in range(G.abc_generations(ctx))]
+            reached += st[-1].eps <= ef
+            gens_sur.append(len(st) - 1)
+            sims_sur.append(sum(x.sims for x in st))
+            aud = sum(x.audited for x in st)
+            frr.append(sum(x.audit_accepted for x in st) / aud if aud else 0.0)
+        finally:
+            G.abc_free(ctx)
+    R = len(cfgs)
+    per = lambda xs: float(np.mean(xs)) if len(xs) else None
+    return {"metric": "wall-time to eps_final per run", "unit": "s", "higher_is_better": False,
+            "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "eps_final_%d_runs" % R, "generations": gens,
+                       "weights": "importance O(N^2), " + ("bf16 tcgen05" if args.prec else "fp32"),
+                       "particles": [w.N for w in runs], "days": [w.T for w in runs]},
+            "plain_s_per_run": per(t_plain),
+            "batched_s_per_run": t_batch / R,
+            "batched_same_eps": bool(np.all(np.array(eps_b) == np.array(eps_final))),
+            "surrogate_s_per_run": per(t_sur),
+            "surrogate_reached": reached, "surrogate_generations": per(gens_sur),
+            "sims_per_run": {"plain": per(sims_plain), "surrogate": per(sims_sur)},
+            "surrogate_false_rejection_rate": per(frr),
+            "surrogate_settings": {"steps": args.surrogate_steps, "batch": 4096,
+                                   "tau": args.surrogate_tau, "rho_min": 0.05, "audit": 0.01}}
+
+
 def run_reference(args):
     """The oracle arm: each step is a bounded sample of one generation of the
     same workload on the host cores; value extrapolated to the full step."""
@@ -443,10 +556,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--prec", type=int, default=1,
-                    help="1: tcgen05 (bf16 x3 split, fp32 accumulation; FP32 path below s=1e-3); "
-                         "0: FP32 CUDA cores only")
+                    help="1: tcgen05 (bf16 x3 split, fp32 accumulation; rows with a large "
+                         "error bound recomputed exactly); 0: FP32 CUDA cores only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batched"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "eps_final"])
+    ap.add_argument("--generations", type=int, default=8)
+    ap.add_argument("--surrogate-steps", type=int, default=32)
+    ap.add_argument("--surrogate-tau", type=float, default=0.5)
     ap.add_argument("--particles", type=int, default=0,
                     help="override the particle count (smaller cases for profiling)")
     ap.add_argument("--runs", type=int, default=64)
@@ -458,6 +574,8 @@ def main():
         line = run_reference(args)
     elif args.workload == "batched":
         line = run_batched(args)
+    elif args.workload == "eps_final":
+        line = run_eps_final(args)
     else:
         line = run_gpu(args)
     if line is not None:

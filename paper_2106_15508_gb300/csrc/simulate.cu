@@ -54,6 +54,10 @@ __device__ U128 saird_path(const SimParams& p, const float th[8], uint32_t c0, u
   const float pA = -dev_expm1(-lamA);
   const float fI = lamI > 0.0f ? __fdiv_rn(gamma, lamI) : 0.0f;
   const float fA = lamA > 0.0f ? __fdiv_rn(beta, lamA) : 0.0f;
+  // the four exits of I and A have fixed probabilities: their binomial
+  // constants are computed once per particle (bit-identical draws)
+  const BinomConst cI = binom_const(pI), cfI = binom_const(fI);
+  const BinomConst cA = binom_const(pA), cfA = binom_const(fA);
   const int T = p.T;
   if (traj) {
     int32_t* t0 = traj + col;
@@ -77,11 +81,11 @@ __device__ U128 saird_path(const SimParams& p, const float th[8], uint32_t c0, u
       const float t = __fdiv_rn(__fmul_rn(g, __int2float_rn(I)), Pf);
       const float pSI = -dev_expm1(-t);
       k1 = dev_binomial(S, pSI, unif(b0.x), unif(b0.y));
-      const int32_t LI = dev_binomial(I, pI, unif(b0.z), unif(b0.w));
-      k2 = dev_binomial(LI, fI, unif(b1.x), unif(b1.y));
+      const int32_t LI = dev_binomial_c(I, cI, unif(b0.z), unif(b0.w));
+      k2 = dev_binomial_c(LI, cfI, unif(b1.x), unif(b1.y));
       k5 = LI - k2;
-      const int32_t LA = dev_binomial(A, pA, unif(b1.z), unif(b1.w));
-      k3 = dev_binomial(LA, fA, unif(b2.x), unif(b2.y));
+      const int32_t LA = dev_binomial_c(A, cA, unif(b1.z), unif(b1.w));
+      k3 = dev_binomial_c(LA, cfA, unif(b2.x), unif(b2.y));
       k4 = LA - k3;
     } else {
       // the paper's floor(Normal(h, sqrt h)) flows in h order (Sec. 2.2)
