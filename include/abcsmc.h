@@ -171,7 +171,8 @@ ABC_API int abc_select_kth(const double* d, int64_t n, int64_t k, double* out, v
 
 /* A5 stage prior, weights and prefix (Eq. 9-11): survivors d_j <= *eps;
  * r_j = *eps - d_j (mode ABC_W_PAPER) or W_j (ABC_W_IMPORTANCE), 0 for
- * non-survivors; q_j = floor(r_j / max r * (2^32 - 1)) (q_j = 1 for every
+ * non-survivors; q_j = floor(r_j * s) with s = (2^32 - 1) / max r in fp64
+ * (the largest weight gets 2^32 - 1 exactly, none more; q_j = 1 for every
  * survivor when max r is 0); prefix = inclusive sum of q as u64, so the
  * total is prefix[n-1].  d, W: device double[n] (W unused in paper mode,
  * may be NULL); eps: device double[1]; q: device u32[n]; prefix: device

@@ -522,7 +522,8 @@ OR_API int64_t or_rank(double alpha, int64_t n) {
 /*
  * Stage prior and its weights (Eq. 9-10): survivors are d_j <= eps.
  * mode 0 (paper): r_j = eps - d_j; mode 1 (importance): r_j = W_j.
- * q_j = floor(r_j / max r * (2^32 - 1)); prefix = inclusive sum of q (u64).
+ * q_j = floor(r_j * s) with s = (2^32 - 1) / max r (the largest weight gets
+ * 2^32 - 1 exactly, no value exceeds it); prefix = inclusive sum of q (u64).
  * When max r is zero or not finite every survivor gets q_j = 1.  Returns
  * the total.
  */
@@ -535,12 +536,16 @@ OR_API uint64_t or_resample_prefix(const double* d, const double* W, int64_t n, 
     if (r > rmax) rmax = r;
   }
   uint64_t tot = 0;
+  /* scale = (2^32 - 1) / max r once; the largest weight maps to 2^32 - 1
+   * exactly, every other to floor(r * scale) (at most 2^32 - 1) */
+  const double scale = 4294967295.0 / rmax;
   for (int64_t j = 0; j < n; ++j) {
     uint32_t qj;
     if (rmax > 0.0 && isfinite(rmax)) {
       double r = 0.0;
       if (d[j] <= eps) r = mode == 0 ? eps - d[j] : W[j];
-      qj = (uint32_t)floor(r / rmax * 4294967295.0);
+      const double v = r == rmax ? 4294967295.0 : floor(r * scale);
+      qj = (uint32_t)(v < 4294967295.0 ? v : 4294967295.0);
     } else {
       qj = d[j] <= eps ? 1u : 0u;
     }

@@ -109,9 +109,14 @@ __global__ void k_quantize(const double* __restrict__ d, const double* __restric
                            const double* eps_p, int mode, const unsigned long long* rmax_bits,
                            uint32_t* __restrict__ q, unsigned long long* tile_sum) {
   __shared__ unsigned long long sm[32];
+  __shared__ double s_scale;
   const double eps = *eps_p;
   const double rmax = __longlong_as_double(static_cast<long long>(*rmax_bits));
   const bool proper = rmax > 0.0 && isfinite(rmax);
+  // scale = (2^32 - 1) / max r, one correctly rounded division per block
+  if (threadIdx.x == 0) s_scale = proper ? __ddiv_rn(4294967295.0, rmax) : 0.0;
+  __syncthreads();
+  const double scale = s_scale;
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile;
   unsigned long long s = 0;
 #pragma unroll
@@ -121,7 +126,9 @@ __global__ void k_quantize(const double* __restrict__ d, const double* __restric
       uint32_t qi;
       if (proper) {
         const double r = stage_weight(d[i], W ? W[i] : 0.0, eps, mode);
-        qi = static_cast<uint32_t>(floor(__dmul_rn(__ddiv_rn(r, rmax), 4294967295.0)));
+        // the largest weight maps to 2^32 - 1 exactly, none above it
+        const double v = r == rmax ? 4294967295.0 : floor(__dmul_rn(r, scale));
+        qi = static_cast<uint32_t>(v < 4294967295.0 ? v : 4294967295.0);
       } else {
         qi = d[i] <= eps ? 1u : 0u;
       }
@@ -134,17 +141,32 @@ __global__ void k_quantize(const double* __restrict__ d, const double* __restric
 }
 
 // exclusive scan of per-tile totals by one block, in chunks of blockDim.x
+// exclusive scan of the tile sums in one block; each thread takes 16
+// consecutive values per round (a round covers 16 x blockDim tiles)
+constexpr int kScanPer = 16;
+
 template <typename T>
-__global__ void k_scan_tiles(const T* __restrict__ in, int64_t ntiles, T* __restrict__ out,
-                             T* total) {
+__global__ void __launch_bounds__(1024, 1)
+k_scan_tiles(const T* __restrict__ in, int64_t ntiles, T* __restrict__ out, T* total) {
   __shared__ T sm[32];
+  __shared__ T last;
   T carry = 0;
-  for (int64_t b = 0; b < ntiles; b += blockDim.x) {
-    const int64_t i = b + threadIdx.x;
-    const T v = i < ntiles ? in[i] : T(0);
-    const T inc = block_incl_scan<T>(v, sm);
-    if (i < ntiles) out[i] = carry + inc - v;
-    __shared__ T last;
+  for (int64_t b = 0; b < ntiles; b += static_cast<int64_t>(blockDim.x) * kScanPer) {
+    const int64_t i0 = b + static_cast<int64_t>(threadIdx.x) * kScanPer;
+    T v[kScanPer];
+    T s = 0;
+#pragma unroll
+    for (int e = 0; e < kScanPer; ++e) {
+      v[e] = i0 + e < ntiles ? in[i0 + e] : T(0);
+      s += v[e];
+    }
+    const T inc = block_incl_scan<T>(s, sm);
+    T run = carry + inc - s;
+#pragma unroll
+    for (int e = 0; e < kScanPer; ++e) {
+      if (i0 + e < ntiles) out[i0 + e] = run;
+      run += v[e];
+    }
     if (threadIdx.x == blockDim.x - 1) last = inc;
     __syncthreads();
     carry += last;
@@ -521,20 +543,24 @@ __global__ void k_nz_max(const double* __restrict__ lw, int64_t n, double* part)
   }
 }
 
-// mode 0: exp(lw - M) summed; mode 1: (exp(lw - M) / S)^2 summed, W written
+// mode 0: w = exp(lw - M) written to W and summed (the only exponentials:
+// fp64 is slow on this GPU); mode 1: W scaled by 1/S in place, W^2 summed
 __global__ void k_nz_sum(const double* __restrict__ lw, int64_t n, const double* stat, int mode,
                          double* __restrict__ W, double* part) {
   __shared__ double sm[32];
   const double M = stat[0];
   const bool uniform = !(M > -__longlong_as_double(0x7ff0000000000000ll));
-  const double S = stat[1];
+  const double inv = mode == 1 ? (uniform ? 1.0 / static_cast<double>(n) : 1.0 / stat[1]) : 0.0;
   double acc = 0.0;
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const double li = lw[i];
-    double w = uniform ? 1.0 : (li == li ? exp(li - M) : 0.0);
-    if (mode == 1) {
-      w = uniform ? 1.0 / static_cast<double>(n) : w / S;
+    double w;
+    if (mode == 0) {
+      const double li = lw[i];
+      w = uniform ? 1.0 : (li == li ? exp(li - M) : 0.0);
+      W[i] = w;
+    } else {
+      w = uniform ? inv : W[i] * inv;
       W[i] = w;
       w = w * w;
     }

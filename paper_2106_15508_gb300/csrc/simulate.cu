@@ -150,7 +150,8 @@ __device__ double toy_dist(const SimParams& p, const float th[8], uint32_t c0, u
   return __dsqrt_rn(acc);
 }
 
-__global__ void k_simulate(SimParams p, const int32_t* __restrict__ obs,
+__global__ void __launch_bounds__(256, 4)
+k_simulate(SimParams p, const int32_t* __restrict__ obs,
                            const float* __restrict__ u, int64_t n,
                            const uint32_t* __restrict__ c0_idx, uint32_t c1, uint32_t tag,
                            const uint8_t* __restrict__ skip, double* __restrict__ dist,
@@ -244,7 +245,9 @@ int launch_simulate(const SimParams& p, const int32_t* obs, const float* u, int6
                     double* dist, int32_t* traj, cudaStream_t st, const uint32_t* c1_dev,
                     const int* off_dev, int threads, int32_t* ard_last) {
   if (n <= 0) return ABC_OK;
-  if (threads != 64 && threads != 128 && threads != 256 && threads != 512) return ABC_E_INVAL;
+  // 64 registers per thread (__launch_bounds__(256, 4)): up to 8 CTAs of
+  // 128 threads per SM; blocks of at most 256 threads
+  if (threads != 64 && threads != 128 && threads != 256) return ABC_E_INVAL;
   const size_t smem = (p.model == ABC_MODEL_SAIRD && obs) ? sizeof(int32_t) * 3 * (p.T + 1) : 0;
   k_simulate<<<static_cast<unsigned>(ceil_div(n, threads)), threads, smem, st>>>(
       p, obs, u, n, c0_idx, c1, tag, skip, dist, traj, c1_dev, off_dev, ard_last);

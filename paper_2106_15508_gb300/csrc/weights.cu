@@ -72,14 +72,16 @@ k_weights_fp32(const float* __restrict__ up, const float* __restrict__ s, int64_
   if (off_dev && *off_dev) return;  // run finished or its generation stopped
   // rows is the stride (capacity); rows_dev, when given, the rows in use
   const int64_t nrows = rows_dev ? static_cast<int64_t>(*rows_dev) : rows;
-  if (static_cast<int64_t>(blockIdx.x) * (kWThreads * kWRows) >= nrows) return;
   const int64_t nc = *nc_p;
   // the columns in use (nc, known only on the device) split evenly over grid.y
   const int64_t chunk_cols = ceil_div(ceil_div(nc, static_cast<int64_t>(gridDim.y)),
                                       static_cast<int64_t>(kWTile)) * kWTile;
   const int64_t c_begin = static_cast<int64_t>(blockIdx.y) * chunk_cols;
   const int64_t c_end = nc < c_begin + chunk_cols ? nc : c_begin + chunk_cols;
-  const int64_t row0 = static_cast<int64_t>(blockIdx.x) * (kWThreads * kWRows) + threadIdx.x;
+  // row blocks of 512 rows, grid-strided (the grid may be smaller than the
+  // capacity when the rows in use are counted on the device)
+  for (int64_t rb = blockIdx.x; rb * (kWThreads * kWRows) < nrows; rb += gridDim.x) {
+  const int64_t row0 = rb * (kWThreads * kWRows) + threadIdx.x;
   unsigned long long x[kWRows][4];
   float ninv[kWRows], m[kWRows], S[kWRows], cS[kWRows], t[kWRows];
 #pragma unroll
@@ -152,6 +154,8 @@ k_weights_fp32(const float* __restrict__ up, const float* __restrict__ s, int64_
     const int64_t j = row0 + r * kWThreads;
     if (j < nrows) part[static_cast<int64_t>(blockIdx.y) * rows + j] = make_float2(m[r], S[r]);
   }
+  __syncthreads();  // the shared tiles are refilled for the next row block
+  }
 }
 
 __global__ void k_weights_combine(const float2* __restrict__ part, int nchunks,
@@ -195,7 +199,11 @@ int launch_weights_fp32(const float* up, const float* s, int64_t rows, const flo
   if (bytes < weights_fp32_scratch_bytes(rows, ncap, mult)) return ABC_E_SCRATCH;
   const int nch = weight_chunks(rows, ncap, mult);
   float2* part = static_cast<float2*>(scratch);
-  dim3 grid(static_cast<unsigned>(ceil_div(rows, kWThreads * kWRows)), static_cast<unsigned>(nch));
+  // with a device-side row count the rows in use are often few: a capped,
+  // grid-strided grid keeps the launch from spawning thousands of idle CTAs
+  int64_t gx = ceil_div(rows, kWThreads * kWRows);
+  if (rows_dev) gx = std::min<int64_t>(gx, 304);
+  dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(nch));
   if (wt && wt->fp0) ABC_CUDA_TRY(cudaEventRecord(wt->fp0, st));
   k_weights_fp32<<<grid, kWThreads, 0, st>>>(up, s, rows, cu, cc, nc_dev, ncap, part,
                                              off_dev, rows_dev);
