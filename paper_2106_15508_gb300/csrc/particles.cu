@@ -87,22 +87,32 @@ int launch_select(const double* d, int64_t n, int64_t k, double* out, void* scra
 }
 
 // ------------------------------------------------- A5 weights and prefix ---
+// Distances, tolerances, weights and stage weights are >= 0 (or +inf) and
+// never NaN, so their IEEE bit patterns order like their values: the
+// comparisons and maxima run on the integer pipes (fp64 is slow here).
+__device__ __forceinline__ unsigned long long dbits(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x));
+}
+
 __device__ __forceinline__ double stage_weight(double d, double w, double eps, int mode) {
-  if (!(d <= eps)) return 0.0;
+  if (dbits(d) > dbits(eps)) return 0.0;  // d > eps
   return mode == ABC_W_PAPER ? __dsub_rn(eps, d) : w;
 }
 
 __global__ void k_rmax(const double* __restrict__ d, const double* __restrict__ W, int64_t n,
                        const double* eps_p, int mode, unsigned long long* rmax_bits) {
   const double eps = *eps_p;
-  double m = 0.0;
+  unsigned long long m = 0ull;
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    m = fmax(m, stage_weight(d[i], W ? W[i] : 0.0, eps, mode));
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  // r >= 0, so the IEEE bit pattern orders like the value
-  if ((threadIdx.x & 31) == 0)
-    atomicMax(rmax_bits, static_cast<unsigned long long>(__double_as_longlong(m)));
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const unsigned long long r = dbits(stage_weight(d[i], W ? W[i] : 0.0, eps, mode));
+    m = r > m ? r : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(rmax_bits, m);
 }
 
 __global__ void k_quantize(const double* __restrict__ d, const double* __restrict__ W, int64_t n,
@@ -111,8 +121,9 @@ __global__ void k_quantize(const double* __restrict__ d, const double* __restric
   __shared__ unsigned long long sm[32];
   __shared__ double s_scale;
   const double eps = *eps_p;
-  const double rmax = __longlong_as_double(static_cast<long long>(*rmax_bits));
-  const bool proper = rmax > 0.0 && isfinite(rmax);
+  const unsigned long long rmb = *rmax_bits;
+  const double rmax = __longlong_as_double(static_cast<long long>(rmb));
+  const bool proper = rmb > 0ull && rmb < 0x7ff0000000000000ull;  // 0 < max r < inf
   // scale = (2^32 - 1) / max r, one correctly rounded division per block
   if (threadIdx.x == 0) s_scale = proper ? __ddiv_rn(4294967295.0, rmax) : 0.0;
   __syncthreads();
@@ -126,11 +137,11 @@ __global__ void k_quantize(const double* __restrict__ d, const double* __restric
       uint32_t qi;
       if (proper) {
         const double r = stage_weight(d[i], W ? W[i] : 0.0, eps, mode);
-        // the largest weight maps to 2^32 - 1 exactly, none above it
-        const double v = r == rmax ? 4294967295.0 : floor(__dmul_rn(r, scale));
-        qi = static_cast<uint32_t>(v < 4294967295.0 ? v : 4294967295.0);
+        // the largest weight maps to 2^32 - 1 exactly; otherwise floor(r s),
+        // the truncating conversion saturating at 2^32 - 1 (r s >= 0)
+        qi = dbits(r) == rmb ? 0xFFFFFFFFu : __double2uint_rz(__dmul_rn(r, scale));
       } else {
-        qi = d[i] <= eps ? 1u : 0u;
+        qi = dbits(d[i]) <= dbits(eps) ? 1u : 0u;
       }
       q[i] = qi;
       s += qi;
