@@ -239,7 +239,9 @@ def run_gpu(args):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
-    exp_peak = n_sm * MUFU_EX2_PER_CLK_PER_SM * sm_mhz * 1e6
+    # the exp unit's rate, measured on this GPU by the library's probe
+    exp_peak = G.abc_ex2_probe()
+    exp_nominal = n_sm * MUFU_EX2_PER_CLK_PER_SM * sm_mhz * 1e6
     # the weight pass splits into the tensor-core kernel and the FP32 kernel
     # (rows whose tensor-core error bound is too large); the roofline line is
     # for the one with the larger device time, timed by events around it
@@ -267,8 +269,11 @@ def run_gpu(args):
                    "theta_star": [round(float(x), 6) for x in theta_star]},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9,
                      "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": achieved / exp_peak,
-                     "peak_source": "%d SMs x %d MUFU ex2/clk x %.0f MHz (%s max clock)" % (
-                         n_sm, MUFU_EX2_PER_CLK_PER_SM, sm_mhz, src),
+                     "peak_source": "measured ex2.approx.f32 rate (abc_ex2_probe: saturating "
+                                    "microbenchmark on this GPU); %d SMs x %d ex2/clk x "
+                                    "%.0f MHz would be %.0f Gexp/s" % (
+                                        n_sm, MUFU_EX2_PER_CLK_PER_SM, sm_mhz,
+                                        exp_nominal / 1e9),
                      "traffic": None},
         "weight_kernels": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in kern.items()},
         "weight_pass_gexp_s": pairs / (wms / 1e3) / 1e9 if wms > 0 else 0.0,
@@ -424,7 +429,8 @@ def run_eps_final(args):
 
     B.build()
     G.lib()
-    runs = WL.batched_runs(args.runs, weight_prec=args.prec)
+    runs = (WL.stress_runs(args.runs, weight_prec=args.prec) if args.stress
+            else WL.batched_runs(args.runs, weight_prec=args.prec))
     cfgs = [w.config() for w in runs]
     obs = [synthetic_obs(G, WL, c, torch)[0] for c in cfgs]
     stream = torch.cuda.Stream()
@@ -459,7 +465,7 @@ def run_eps_final(args):
         G.abc_batch_free(b)
     # surrogate
     t_sur, gens_sur, sims_sur, frr, reached = [], [], [], [], 0
-    for c, o, ef in zip(cfgs, obs, eps_final):
+    for c, o, ef in zip([] if args.no_surrogate else cfgs, obs, eps_final):
         sc = G.config(**{f: getattr(c, f) if not hasattr(getattr(c, f), "_length_")
                          else list(getattr(c, f)) for f, _ in c._fields_})
         sc.surrogate, sc.surrogate_start, sc.surrogate_steps = 1, 2, args.surrogate_steps
@@ -490,7 +496,8 @@ def run_eps_final(args):
     per = lambda xs: float(np.mean(xs)) if len(xs) else None
     return {"metric": "wall-time to eps_final per run", "unit": "s", "higher_is_better": False,
             "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": "eps_final_%d_runs" % R, "generations": gens,
+            "config": {"workload": ("stress_" if args.stress else "") + "eps_final_%d_runs" % R,
+                       "generations": gens,
                        "weights": "importance O(N^2), " + ("bf16 tcgen05" if args.prec else "fp32"),
                        "particles": [w.N for w in runs], "days": [w.T for w in runs]},
             "plain_s_per_run": per(t_plain),
@@ -632,6 +639,9 @@ def main():
     ap.add_argument("--generations", type=int, default=8)
     ap.add_argument("--surrogate-steps", type=int, default=32)
     ap.add_argument("--surrogate-tau", type=float, default=0.5)
+    ap.add_argument("--stress", action="store_true",
+                    help="eps_final on the stress runs (2^20 particles, 365 days, P 3.3e8)")
+    ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--particles", type=int, default=0,
                     help="override the particle count (smaller cases for profiling)")
     ap.add_argument("--runs", type=int, default=64)

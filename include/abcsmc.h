@@ -254,6 +254,14 @@ ABC_API int abc_weights(const float* up, const float* s, int64_t rows, const flo
  * Synchronises the stream; ABC_E_DEVICE if a wait timed out. */
 ABC_API int abc_tc_probe(const void* A, const void* B, float* D, void* stream);
 
+/* Measurement helper (no counterpart in the paper): the sustained rate of
+ * ex2.approx.f32 on this GPU in exponentials per second, from a saturating
+ * microbenchmark (eight independent chains per thread, 8 blocks of 256 per
+ * SM, best of three timed launches).  The tensor-core weight kernel is bound
+ * by this unit; bench.py quotes its roofline against this rate.
+ * Synchronises the stream. */
+ABC_API int abc_ex2_probe(double* ex2_per_second, void* stream);
+
 /* A10 normalisation (fp64): W_j = exp(logW_j - max) / sum, *ess = 1 / sum W^2;
  * all -inf gives W = 1/n, ess = n.  logW: device double[n]; W: device
  * double[n]; ess: device double[1]. */

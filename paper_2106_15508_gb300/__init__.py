@@ -28,7 +28,8 @@ TAG_OBS, TAG_OBS_THETA = 7, 8
 EXPORTS = (
     "abc_config_default", "abc_philox", "abc_synth_obs", "abc_prior", "abc_simulate",
     "abc_select_scratch_bytes", "abc_select_kth", "abc_prefix_scratch_bytes",
-    "abc_resample_prefix", "abc_resample_prefix_noalloc", "abc_propose", "abc_accept_scratch_bytes", "abc_accept_append",
+    "abc_resample_prefix", "abc_resample_prefix_noalloc", "abc_propose",
+    "abc_accept_scratch_bytes", "abc_accept_append",
     "abc_weights_scratch_bytes", "abc_weights", "abc_tc_probe", "abc_normalize_scratch_bytes",
     "abc_normalize",
     "abc_init", "abc_generation", "abc_run", "abc_get_population", "abc_get_stats",
@@ -36,7 +37,8 @@ EXPORTS = (
     "abc_batch_init", "abc_batch_generation", "abc_batch_run", "abc_batch_runs",
     "abc_batch_generations", "abc_batch_get_stats", "abc_batch_get_population",
     "abc_batch_autotune", "abc_batch_tuning", "abc_batch_free",
-    "abc_screen", "abc_mlp_param_count", "abc_mlp_create", "abc_mlp_set_params", "abc_mlp_get_params",
+    "abc_screen", "abc_ex2_probe",
+    "abc_mlp_param_count", "abc_mlp_create", "abc_mlp_set_params", "abc_mlp_get_params",
     "abc_mlp_scratch_bytes", "abc_mlp_grad", "abc_mlp_adam", "abc_mlp_forward", "abc_mlp_free",
 )
 
@@ -126,6 +128,7 @@ _SIGS = {
     "abc_batch_tuning": (C.c_int, [_V, _I32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "abc_batch_free": (None, [_V]),
     "abc_screen": (C.c_int, [_V, _V, _V, _V, _I64, _V, C.c_uint32, _V, _V, _V]),
+    "abc_ex2_probe": (C.c_int, [C.POINTER(C.c_double), _V]),
     "abc_mlp_param_count": (C.c_int32, []),
     "abc_mlp_create": (C.c_int, [C.c_uint64, C.POINTER(C.c_void_p)]),
     "abc_mlp_set_params": (C.c_int, [_V, _V]),
@@ -412,6 +415,13 @@ MLP_ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
 def abc_screen(cfg, Y, ystat, flag, M, eps, c1, rho, sflag, stream=None):
     return _check(lib().abc_screen(C.byref(cfg), _ptr(Y), _ptr(ystat), _ptr(flag), M, _ptr(eps), c1,
                                    _ptr(rho), _ptr(sflag), _stream(stream)), "abc_screen")
+
+
+def abc_ex2_probe(stream=None):
+    """Sustained ex2.approx.f32 rate of this GPU (exponentials per second)."""
+    r = C.c_double()
+    _check(lib().abc_ex2_probe(C.byref(r), _stream(stream)), "abc_ex2_probe")
+    return r.value
 
 
 def abc_mlp_create(seed=1):

@@ -31,6 +31,7 @@ size_t accept_scratch_bytes(int64_t);
 size_t survivors_scratch_bytes(int64_t);
 size_t weights_fp32_scratch_bytes(int64_t, int64_t, int mult = 1);
 size_t weights_tc_scratch_bytes(int64_t, int64_t, int mult = 1);
+int ex2_probe(double* rate, cudaStream_t st);
 int launch_tc_probe(const void*, const void*, float*, unsigned*, cudaStream_t);
 size_t normalize_scratch_bytes(int64_t);
 int launch_fill(double*, int64_t, double, cudaStream_t);
@@ -300,6 +301,11 @@ ABC_API int abc_tc_probe(const void* A, const void* B, float* D, void* stream) {
   cudaFreeAsync(err, st);
   cudaStreamSynchronize(st);
   return rc;
+}
+
+ABC_API int abc_ex2_probe(double* ex2_per_second, void* stream) {
+  if (!ex2_per_second) return ABC_E_INVAL;
+  return ex2_probe(ex2_per_second, as_stream(stream));
 }
 
 ABC_API size_t abc_normalize_scratch_bytes(int64_t n) { return normalize_scratch_bytes(n); }

@@ -18,15 +18,16 @@
 // direct-difference kernel instead (see the split below).
 //
 // Kernel structure (one CTA = 128 rows, one SM):
-//   warp 8  : bulk-copy producer (cp.async.bulk, mbarrier complete_tx):
+//   warp 16 : bulk-copy producer (cp.async.bulk, mbarrier complete_tx):
 //             the row tile once, then 256-column tiles through a 4-stage ring
-//   warp 9  : tcgen05.mma issuer (one thread), M = 128, N = 256, K = 4 x 16,
+//   warp 17 : tcgen05.mma issuer (one thread), M = 128, N = 256, K = 4 x 16,
 //             fp32 accumulators double-buffered in TMEM (2 x 256 columns)
-//   warps 0-7: epilogue, one thread per row (TMEM lane) and column half:
-//             warps w and w + 4 share TMEM lanes 32 w .. 32 w + 31 and take
-//             alternate 32-column chunks (tcgen05.ld), each keeping an online
-//             max and sum of 2^(e - m); two warps per lane quarter keep the
-//             exponential unit busy while the other waits on TMEM
+//   warps 0-15: epilogue, one thread per row (TMEM lane) and column group:
+//             warps w, w + 4, w + 8, w + 12 share TMEM lanes 32 (w % 4) ..
+//             and take every fourth 32-column chunk (tcgen05.ld), each
+//             keeping an online max and sum of 2^(e - m); four warps per lane
+//             quarter keep the exponential unit busy while others wait on
+//             TMEM (two per quarter reached 0.84 of this kernel's rate)
 // Operands are packed by a prep kernel in the canonical K-major layout
 // without swizzle: 8 x 8 bf16 core matrices (128 contiguous bytes), the 8
 // core matrices of a row group consecutive along K (LBO = 128 B), row groups
@@ -49,10 +50,11 @@ constexpr int kTcStages = 4;                        // column-tile ring
 constexpr uint32_t kATile = kTcM * kTcK * 2;        // 16 KB
 constexpr uint32_t kBTile = kTcN * kTcK * 2;        // 32 KB
 constexpr uint32_t kTmemCols = 512;                 // two 256-column accumulators
-constexpr int kTcEpiWarps = 8;                      // two epilogue warps per TMEM lane quarter
-constexpr int kTcProducer = kTcEpiWarps;            // warp 8: bulk-copy producer
-constexpr int kTcIssuer = kTcEpiWarps + 1;          // warp 9: MMA issuer, owns the TMEM
-constexpr int kTcThreads = 32 * (kTcEpiWarps + 2);  // 10 warps
+constexpr int kTcGroups = 4;                        // epilogue warps per TMEM lane quarter
+constexpr int kTcEpiWarps = 4 * kTcGroups;          // epilogue warps
+constexpr int kTcProducer = kTcEpiWarps;            // bulk-copy producer warp
+constexpr int kTcIssuer = kTcEpiWarps + 1;          // MMA issuer warp, owns the TMEM
+constexpr int kTcThreads = 32 * (kTcEpiWarps + 2);
 constexpr int kProbeThreads = 192;                  // probe: 4 epilogue warps, producer, issuer
 constexpr size_t kTcSmem = 1024 + kATile + kTcStages * kBTile + 256;
 constexpr float kSMinTc = 1e-30f;
@@ -310,8 +312,8 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
   const int64_t row0 = static_cast<int64_t>(blockIdx.x) * kTcM;
   if (tb >= te) {  // no column tile in this chunk: neutral partials (both halves)
     const int g = threadIdx.x / kTcM, r = threadIdx.x % kTcM;
-    if (g < 2 && row0 + r < nrows) {
-      const int64_t slot = 2 * static_cast<int64_t>(blockIdx.y) + g;
+    if (g < kTcGroups && row0 + r < nrows) {
+      const int64_t slot = kTcGroups * static_cast<int64_t>(blockIdx.y) + g;
       part[slot * rows + row0 + r] = make_float2(-INFINITY, 0.0f);
       ccnt[slot * rows + row0 + r] = 0;
     }
@@ -390,9 +392,9 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     __syncwarp();
   } else {
     // ---------------- epilogue: thread = row = TMEM lane ----------------
-    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its row quarter); the two
-    // warps of a quarter take alternate 32-column chunks of every tile and
-    // keep separate (m, S) partials (column half g of the chunk)
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its row quarter); the
+    // kTcGroups warps of a quarter take every kTcGroups-th 32-column chunk
+    // of a tile and keep separate (m, S) partials (column group g)
     const int g = warp >> 2, q = warp & 3;
     const int r = q * 32 + lane;
     const uint32_t lane_base = tmem + (static_cast<uint32_t>(q * 32) << 16);
@@ -402,7 +404,7 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     // exponent, or the largest value seen so far less its error), so a column
     // with v < lb - delta - margin is at least margin bits under it
     const int64_t row = row0 + r;
-    const int64_t slot = 2 * static_cast<int64_t>(blockIdx.y) + g;
+    const int64_t slot = kTcGroups * static_cast<int64_t>(blockIdx.y) + g;
     const bool refine = row < nrows && rcls[row] == 1;
     float lb = -INFINITY, dl = 0.0f;
     if (refine) {
@@ -420,7 +422,7 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
       tc_fence_after();
       float ts = 0.0f;
 #pragma unroll 1
-      for (int c = g; c < kTcN / 32; c += 2) {
+      for (int c = g; c < kTcN / 32; c += kTcGroups) {
         float v[32];
         tmem_ld32(lane_base + static_cast<uint32_t>(b * kTcN + c * 32), v);
         float cm = v[0];
@@ -693,7 +695,7 @@ static TcLayout tc_layout(int64_t rows, int64_t ncap, int mult) {
   const int64_t rpad = ceil_div(std::max<int64_t>(rows, 1), kTcM) * kTcM;
   const int64_t cpad = ceil_div(std::max<int64_t>(ncap, 1), kTcN) * kTcN;
   const size_t R = static_cast<size_t>(std::max<int64_t>(rows, 1));
-  const size_t slots = 2 * static_cast<size_t>(tc_chunks(rows, ncap, mult));
+  const size_t slots = kTcGroups * static_cast<size_t>(tc_chunks(rows, ncap, mult));
   const int64_t nt = ceil_div(std::max<int64_t>(rows, 1), kPartTile);
   size_t o = 0;
   auto take = [&](size_t& field, size_t bytes) {
@@ -800,11 +802,11 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   ABC_LAUNCH_CHECK();
   if (wt && wt->tc1) ABC_CUDA_TRY(cudaEventRecord(wt->tc1, st));
   k_weights_tc_combine<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(
-      part, 2 * nch, s, rowc, rows, total_p, logW, off_dev, nullptr);
+      part, kTcGroups * nch, s, rowc, rows, total_p, logW, off_dev, nullptr);
   ABC_LAUNCH_CHECK();
   // class 1: exact from the listed columns (overflow -> class 2)
   k_tc_refine<<<static_cast<unsigned>(ceil_div(rows, 128)), 128, 0, st>>>(
-      up, s, rows, rcls, cand, ccnt, 2 * nch, cu, cc, ncap, total_p, logW, off_dev);
+      up, s, rows, rcls, cand, ccnt, kTcGroups * nch, cu, cc, ncap, total_p, logW, off_dev);
   ABC_LAUNCH_CHECK();
   // class 2: the FP32 kernel
   const int64_t nt = ceil_div(rows, kPartTile);
@@ -822,6 +824,56 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   ABC_LAUNCH_CHECK();
   if (wt) wt->counts = counts;
   return ABC_OK;
+}
+
+// ---- exponential-rate probe (measurement helper) ----------------------------
+// Eight independent ex2.approx chains per thread, y <- 2^(y - 1) (stays in
+// (1/2, 1]), full occupancy: the sustained MUFU exponential rate that the
+// weight kernel's roofline is quoted against.
+__global__ void __launch_bounds__(256) k_ex2_probe(int iters, float* __restrict__ sink) {
+  float y[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) y[k] = 0.5f + 0.01f * static_cast<float>(threadIdx.x & 7) + 0.001f * k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) y[k] = ex2(y[k] - 1.0f);
+  }
+  float acc = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc += y[k];
+  if (acc == 1234.5f) sink[threadIdx.x] = acc;  // never true; keeps the chains live
+}
+
+int ex2_probe(double* rate, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  ABC_CUDA_TRY(cudaGetDevice(&dev));
+  ABC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  float* sink = nullptr;
+  ABC_CUDA_TRY(cudaMalloc(&sink, 256 * sizeof(float)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = ABC_OK;
+  const int iters = 4096, blocks = sms * 8;
+  float best = 1e30f;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = ABC_E_CUDA;
+  for (int rep = 0; rc == ABC_OK && rep < 4; ++rep) {
+    cudaEventRecord(e0, st);
+    k_ex2_probe<<<blocks, 256, 0, st>>>(iters, sink);
+    count_launch();
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      rc = ABC_E_CUDA;
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;  // the first launch warms up
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (rc == ABC_OK)
+    *rate = static_cast<double>(blocks) * 256.0 * iters * 8.0 / (static_cast<double>(best) * 1e-3);
+  return rc;
 }
 
 // Apk/Bpk: packed bf16 tiles (16 KB, 32 KB); D: 128 x 256 fp32; err: u32

@@ -71,5 +71,12 @@ def batched_runs(n_runs=64, seed=0, weight_prec=ABC_P_FP32):
                             weight_prec=weight_prec))
     return out
 
-__all__ = ["Workload", "SMALL", "LARGE", "WORKLOADS", "batched_runs", "OBS_BOX_LO", "OBS_BOX_HI",
+def stress_runs(n_runs=32, weight_prec=ABC_P_BF16_TC):
+    """Stress workload: n_runs concurrent runs of 2^20 particles, 365 days,
+    P = 3.3e8, seeds 1..n_runs, paper Beta schedule, importance weights."""
+    return [Workload("stress_run%d" % r, N=1 << 20, T=365, P=330_000_000, G=25, seed=r + 1,
+                     weight_prec=weight_prec) for r in range(n_runs)]
+
+
+__all__ = ["Workload", "SMALL", "LARGE", "WORKLOADS", "batched_runs", "stress_runs", "OBS_BOX_LO", "OBS_BOX_HI",
            "SAIRD_THETA_MAX", "initial_active", "ABC_W_PAPER", "ABC_P_BF16_TC"]
