@@ -421,13 +421,22 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
       if (!__all_sync(0xffffffffu, mbar_wait(&sm.tfull[b], tph, err, 7u))) break;
       tc_fence_after();
       float ts = 0.0f;
-#pragma unroll 1
-      for (int c = g; c < kTcN / 32; c += kTcGroups) {
-        float v[32];
-        tmem_ld32(lane_base + static_cast<uint32_t>(b * kTcN + c * 32), v);
-        float cm = v[0];
+      // this thread's two 32-column chunks of the tile (c = g, g + 4), both
+      // loads in flight before one wait
+      static_assert(kTcN / 32 == 2 * kTcGroups, "two chunks per epilogue thread");
+      float vv[2][32];
+      tmem_ld32x2(lane_base + static_cast<uint32_t>(b * kTcN + g * 32),
+                  lane_base + static_cast<uint32_t>(b * kTcN + (g + kTcGroups) * 32), vv[0],
+                  vv[1]);
 #pragma unroll
-        for (int i = 1; i < 32; ++i) cm = fmaxf(cm, v[i]);
+      for (int h = 0; h < 2; ++h) {
+        const int c = g + h * kTcGroups;
+        const float (&v)[32] = vv[h];
+        // chunk maximum with three-input max instructions
+        float cm = max3(v[0], v[1], v[2]);
+#pragma unroll
+        for (int i = 3; i < 31; i += 2) cm = max3(cm, v[i], v[i + 1]);
+        cm = fmaxf(cm, v[31]);
         if (refine) {
           lb = fmaxf(lb, cm - dl);
           const float thr = lb - dl - kCandMargin;
@@ -448,8 +457,22 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
           ts *= f;
           m = cm;
         }
+        // v - m and the running sum in packed fp32x2 (two columns per
+        // instruction); the exponentials one by one on the MUFU
+        // (four independent accumulators keep the add chain short)
+        const unsigned long long m2 = f2_pack(m, m);
+        unsigned long long acc[4];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) ts += ex2(v[i] - m);
+        for (int a = 0; a < 4; ++a) acc[a] = f2_pack(0.0f, 0.0f);
+#pragma unroll
+        for (int i = 0; i < 32; i += 2) {
+          float d0, d1;
+          f2_unpack(f2_sub(f2_pack(v[i], v[i + 1]), m2), d0, d1);
+          acc[(i >> 1) & 3] = f2_add(acc[(i >> 1) & 3], f2_pack(ex2(d0), ex2(d1)));
+        }
+        float a0, a1;
+        f2_unpack(f2_add(f2_add(acc[0], acc[1]), f2_add(acc[2], acc[3])), a0, a1);
+        ts += a0 + a1;
       }
       tc_fence_before();
       mbar_arrive(&sm.tempty[b]);
