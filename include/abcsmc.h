@@ -79,6 +79,8 @@ extern "C" {
 #define ABC_TAG_AUDIT 6
 #define ABC_TAG_OBS 7
 #define ABC_TAG_OBS_THETA 8
+#define ABC_TAG_PREDICT 11
+#define ABC_TAG_PREDICT_SIM 12
 
 /* ---- configuration ----------------------------------------------------- */
 typedef struct {
@@ -254,6 +256,23 @@ ABC_API int abc_weights(const float* up, const float* s, int64_t rows, const flo
  * Synchronises the stream; ABC_E_DEVICE if a wait timed out. */
 ABC_API int abc_tc_probe(const void* A, const void* B, float* D, void* stream);
 
+/* Posterior-predictive simulation (Sec. 4.2: the learned samples simulated
+ * from day zero over the training window plus the days ahead, summarised
+ * per day by the median and the central 99% range).  R draws from the
+ * population u (device float [8][N]) in proportion to W (device double[N];
+ * NULL: equal weights), quantised and drawn like the stage prior
+ * (Eq. 10-11) with Philox block (j, 0, 0, ABC_TAG_PREDICT); each draw is
+ * simulated for `days` days (cfg n_days and observations are not used) with
+ * counters (j, 0, 4 day + block, ABC_TAG_PREDICT_SIM); out (device int32
+ * [days + 1][3][nq], series A, R, D) receives for every day and series the
+ * order statistic of rank ceil(quant[i] R), clamped to [1, R] (the lower
+ * order statistic, as Eq. 8).  quant: host double[nq], levels in (0, 1].
+ * SAIRD model only.  Synchronises the stream. */
+ABC_API size_t abc_predict_scratch_bytes(int64_t N, int64_t R, int32_t days, int32_t nq);
+ABC_API int abc_predict(const abc_config* cfg, const float* u, const double* W, int64_t N,
+                        int64_t R, int32_t days, const double* quant, int32_t nq, int32_t* out,
+                        void* scratch, size_t scratch_bytes, void* stream);
+
 /* Measurement helper (no counterpart in the paper): the sustained rate of
  * ex2.approx.f32 on this GPU in exponentials per second, from a saturating
  * microbenchmark (eight independent chains per thread, 8 blocks of 256 per
@@ -341,6 +360,11 @@ ABC_API int abc_get_population(abc_ctx* ctx, float* u, double* dist, double* W, 
 /* Stats of generation t (0 <= t < abc_generations(ctx)). */
 ABC_API int abc_get_stats(abc_ctx* ctx, int32_t t, abc_gen_stats* out);
 ABC_API int32_t abc_generations(const abc_ctx* ctx);
+/* abc_predict on the context's current population (its weights, its
+ * model and key); out_host: host int32 [days + 1][3][nq].  Allocates its
+ * scratch for the call. */
+ABC_API int abc_predict_population(abc_ctx* ctx, int64_t R, int32_t days, const double* quant,
+                                   int32_t nq, int32_t* out_host);
 /* Checkpoint: serialise (or restore) the generation index, eps_1 and the
  * population.  Philox is stateless, so a restored context continues
  * bit-identically.  get: *len is in/out (call with buf NULL for the size). */

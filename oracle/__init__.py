@@ -16,6 +16,7 @@ _lib = None
 
 TAG_PRIOR, TAG_ANCESTOR, TAG_BETA, TAG_WALK, TAG_SIM, TAG_SCREEN, TAG_AUDIT = 0, 1, 2, 3, 4, 5, 6
 TAG_OBS, TAG_OBS_THETA = 7, 8
+TAG_PREDICT, TAG_PREDICT_SIM = 11, 12
 
 SAIRD_THETA_MAX = np.array([1, 100, 2, 1, 1, 1, 1, 2], np.float32)  # Eq. 2
 OBS_BOX_LO = np.array([0.2, 10, 0.5, 0.02, 0.05, 0.005, 0.2, 0.5], np.float32)
@@ -330,6 +331,21 @@ def mlp_backward(params, x, t):
     loss = f(*ptrs, _p(x, C.c_double), _p(t, C.c_double), C.c_int64(len(x)),
              *[_p(grads[k], C.c_double) for k in MLP_ORDER])
     return loss, grads
+
+
+def predict(m: OracleModel, u, W, R, days, quant):
+    """Posterior-predictive order statistics: int32 [days + 1][3 (A, R, D)][nq]."""
+    u = np.ascontiguousarray(u, np.float32)
+    N = u.shape[1]
+    Wc = None if W is None else np.ascontiguousarray(W, np.float64)
+    qv = np.ascontiguousarray(quant, np.float64)
+    out = np.zeros((days + 1, 3, len(qv)), np.int32)
+    rc = lib().or_predict(m.ref(), _p(u, C.c_float), _p(Wc, C.c_double), C.c_int64(N),
+                          C.c_int64(R), C.c_int32(days), _p(qv, C.c_double), C.c_int32(len(qv)),
+                          _p(out, C.c_int32))
+    if rc != 0:
+        raise ValueError("or_predict: bad arguments")
+    return out
 
 
 def screen(m: OracleModel, Y, ystat, flag, eps, c1, tau, rho_min, audit_frac):

@@ -69,7 +69,8 @@ static void philox_ctr(const uint32_t key[2], uint32_t c0, uint32_t c1, uint32_t
 
 /* Stream tags: the fourth counter word. */
 enum { TAG_PRIOR = 0, TAG_ANCESTOR = 1, TAG_BETA = 2, TAG_WALK = 3, TAG_SIM = 4,
-       TAG_SCREEN = 5, TAG_AUDIT = 6, TAG_OBS = 7, TAG_OBS_THETA = 8 };
+       TAG_SCREEN = 5, TAG_AUDIT = 6, TAG_OBS = 7, TAG_OBS_THETA = 8, TAG_PREDICT = 11,
+       TAG_PREDICT_SIM = 12 };
 
 /* u32 -> (0,1): the top 23 bits plus one half, times 2^-23.  Every step is
  * exact in fp32 and the result lies in [2^-24, 1 - 2^-24] (with 24 bits the
@@ -798,6 +799,69 @@ OR_API int32_t or_generation(const or_model* m, const or_smc* c, int32_t t, doub
   }
   free(q); free(prefix); free(up); free(sp); free(ap); free(att); free(fl); free(dp);
   return st->status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Posterior-predictive simulation (Sec. 4.2).                                */
+/* ------------------------------------------------------------------------ */
+static int cmp_i32(const void* a, const void* b) {
+  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return (x > y) - (x < y);
+}
+
+/*
+ * Sec. 4.2 predicts case data by simulating the learned parameter samples
+ * from day zero over the training window plus the days ahead, and reports
+ * per day the median and the central 99% range.  Here: R draws from the
+ * population u [8][N] in proportion to its weights W (NULL: equal weights;
+ * quantised and drawn like the stage prior, Eq. 10-11, with the PREDICT
+ * stream: block (j, 0, 0, PREDICT), U = w1 2^32 + w0), each simulated for
+ * `days` days with the PREDICT_SIM stream (c0 = j, c1 = 0); for every day
+ * 0..days and series A, R, D the order statistic of rank k = ceil(q R),
+ * clamped to [1, R] (the lower order statistic, as Eq. 8), for each level
+ * q of quant[nq].  out: [days + 1][3][nq].
+ */
+OR_API int or_predict(const or_model* m0, const float* u, const double* W, int64_t N, int64_t R,
+                      int32_t days, const double* quant, int32_t nq, int32_t* out) {
+  if (N < 1 || R < 1 || days < 0 || nq < 1) return -1;
+  or_model m = *m0;
+  m.T = days;
+  m.obs = NULL;
+  double* d0 = (double*)calloc((size_t)N, sizeof(double));
+  uint32_t* q = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
+  uint64_t* prefix = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)N);
+  float* ur = (float*)malloc(sizeof(float) * 8 * (size_t)R);
+  int32_t* traj = (int32_t*)malloc(sizeof(int32_t) * (size_t)(days + 1) * 6 * (size_t)R);
+  int32_t* col = (int32_t*)malloc(sizeof(int32_t) * (size_t)R);
+  /* weights W (importance form: every particle survives eps = 0 with d = 0),
+   * or all equal (paper form with eps = d: every stage weight 0, q = 1) */
+  uint64_t total = or_resample_prefix(d0, W, N, 0.0, W ? 1 : 0, q, prefix);
+  for (int64_t j = 0; j < R; ++j) {
+    uint32_t w[4];
+    philox_ctr(m.key, (uint32_t)j, 0u, 0u, TAG_PREDICT, w);
+    int64_t a = draw_ancestor(prefix, N, total, w[0], w[1]);
+    for (int d = 0; d < 8; ++d) ur[(int64_t)d * R + j] = u[(int64_t)d * N + a];
+  }
+  for (int64_t j = 0; j < R; ++j) {
+    float ui[8], th[8];
+    for (int d = 0; d < 8; ++d) ui[d] = ur[(int64_t)d * R + j];
+    theta_from_u(&m, ui, th);
+    simulate_saird(&m, th, (uint32_t)j, 0u, TAG_PREDICT_SIM, traj, R, j, NULL);
+  }
+  static const int series[3] = {2, 3, 4}; /* A, R, D */
+  for (int32_t t = 0; t <= days; ++t)
+    for (int c = 0; c < 3; ++c) {
+      memcpy(col, traj + ((int64_t)t * 6 + series[c]) * R, sizeof(int32_t) * (size_t)R);
+      qsort(col, (size_t)R, sizeof(int32_t), cmp_i32);
+      for (int32_t i = 0; i < nq; ++i) {
+        int64_t k = (int64_t)ceil(quant[i] * (double)R);
+        if (k < 1) k = 1;
+        if (k > R) k = R;
+        out[((int64_t)t * 3 + c) * nq + i] = col[k - 1];
+      }
+    }
+  free(d0); free(q); free(prefix); free(ur); free(traj); free(col);
+  return 0;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -37,7 +37,8 @@ EXPORTS = (
     "abc_batch_init", "abc_batch_generation", "abc_batch_run", "abc_batch_runs",
     "abc_batch_generations", "abc_batch_get_stats", "abc_batch_get_population",
     "abc_batch_autotune", "abc_batch_tuning", "abc_batch_free",
-    "abc_screen", "abc_ex2_probe",
+    "abc_screen", "abc_ex2_probe", "abc_predict_scratch_bytes", "abc_predict",
+    "abc_predict_population",
     "abc_mlp_param_count", "abc_mlp_create", "abc_mlp_set_params", "abc_mlp_get_params",
     "abc_mlp_scratch_bytes", "abc_mlp_grad", "abc_mlp_adam", "abc_mlp_forward", "abc_mlp_free",
 )
@@ -129,6 +130,9 @@ _SIGS = {
     "abc_batch_free": (None, [_V]),
     "abc_screen": (C.c_int, [_V, _V, _V, _V, _I64, _V, C.c_uint32, _V, _V, _V]),
     "abc_ex2_probe": (C.c_int, [C.POINTER(C.c_double), _V]),
+    "abc_predict_scratch_bytes": (_SZ, [_I64, _I64, _I32, _I32]),
+    "abc_predict": (C.c_int, [_V, _V, _V, _I64, _I64, _I32, _V, _I32, _V, _V, _SZ, _V]),
+    "abc_predict_population": (C.c_int, [_V, _I64, _I32, _V, _I32, _V]),
     "abc_mlp_param_count": (C.c_int32, []),
     "abc_mlp_create": (C.c_int, [C.c_uint64, C.POINTER(C.c_void_p)]),
     "abc_mlp_set_params": (C.c_int, [_V, _V]),
@@ -422,6 +426,30 @@ def abc_ex2_probe(stream=None):
     r = C.c_double()
     _check(lib().abc_ex2_probe(C.byref(r), _stream(stream)), "abc_ex2_probe")
     return r.value
+
+
+def abc_predict_scratch_bytes(N, R, days, nq):
+    return lib().abc_predict_scratch_bytes(N, R, days, nq)
+
+
+def abc_predict(cfg, u, W, N, R, days, quant, out, scratch, scratch_bytes, stream=None):
+    """Posterior-predictive order statistics into out (device int32
+    [days + 1][3][nq]); quant: host sequence of levels in (0, 1]."""
+    import numpy as np
+    q = np.ascontiguousarray(quant, np.float64)
+    return _check(lib().abc_predict(C.byref(cfg), _ptr(u), _ptr(W), N, R, days, q.ctypes.data,
+                                    len(q), _ptr(out), _ptr(scratch), scratch_bytes,
+                                    _stream(stream)), "abc_predict")
+
+
+def abc_predict_population(ctx, R, days, quant):
+    """abc_predict on the context's population; returns int32 [days + 1][3][nq]."""
+    import numpy as np
+    q = np.ascontiguousarray(quant, np.float64)
+    out = np.zeros((days + 1, 3, len(q)), np.int32)
+    _check(lib().abc_predict_population(ctx, R, days, q.ctypes.data, len(q), out.ctypes.data),
+           "abc_predict_population")
+    return out
 
 
 def abc_mlp_create(seed=1):

@@ -32,6 +32,10 @@ size_t survivors_scratch_bytes(int64_t);
 size_t weights_fp32_scratch_bytes(int64_t, int64_t, int mult = 1);
 size_t weights_tc_scratch_bytes(int64_t, int64_t, int mult = 1);
 int ex2_probe(double* rate, cudaStream_t st);
+size_t predict_scratch_bytes(int64_t N, int64_t R, int32_t days, int32_t nq);
+int launch_predict(const SimParams& p, const float* u, const double* W, int64_t N, int64_t R,
+                   int32_t days, const double* quant, int32_t nq, int32_t* out, void* scratch,
+                   size_t bytes, cudaStream_t st);
 int launch_tc_probe(const void*, const void*, float*, unsigned*, cudaStream_t);
 size_t normalize_scratch_bytes(int64_t);
 int launch_fill(double*, int64_t, double, cudaStream_t);
@@ -301,6 +305,33 @@ ABC_API int abc_tc_probe(const void* A, const void* B, float* D, void* stream) {
   cudaFreeAsync(err, st);
   cudaStreamSynchronize(st);
   return rc;
+}
+
+static int check_predict(const abc_config* cfg, int64_t N, int64_t R, int32_t days,
+                         const double* quant, int32_t nq) {
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (cfg->model != ABC_MODEL_SAIRD) return ABC_E_INVAL;
+  if (N < 1 || N > kMaxIndex || R < 1 || R > kMaxIndex || days < 0 || days > 100000) return ABC_E_INVAL;
+  if (!quant || nq < 1 || nq > 64) return ABC_E_INVAL;
+  for (int i = 0; i < nq; ++i)
+    if (!(quant[i] > 0.0 && quant[i] <= 1.0)) return ABC_E_INVAL;
+  return ABC_OK;
+}
+
+ABC_API size_t abc_predict_scratch_bytes(int64_t N, int64_t R, int32_t days, int32_t nq) {
+  if (N < 1 || R < 1 || days < 0 || nq < 1) return 0;
+  return predict_scratch_bytes(N, R, days, nq);
+}
+
+ABC_API int abc_predict(const abc_config* cfg, const float* u, const double* W, int64_t N,
+                        int64_t R, int32_t days, const double* quant, int32_t nq, int32_t* out,
+                        void* scratch, size_t scratch_bytes, void* stream) {
+  int rc = check_predict(cfg, N, R, days, quant, nq);
+  if (rc) return rc;
+  if (!u || !out || !scratch) return ABC_E_INVAL;
+  return launch_predict(make_params(*cfg), u, W, N, R, days, quant, nq, out, scratch,
+                        scratch_bytes, as_stream(stream));
 }
 
 ABC_API int abc_ex2_probe(double* ex2_per_second, void* stream) {
@@ -856,6 +887,29 @@ ABC_API int abc_get_stats(abc_ctx* c, int32_t t, abc_gen_stats* out) {
   if (!c || !out || t < 0 || t >= static_cast<int32_t>(c->stats.size())) return ABC_E_INVAL;
   *out = c->stats[static_cast<size_t>(t)];
   return ABC_OK;
+}
+
+ABC_API int abc_predict_population(abc_ctx* c, int64_t R, int32_t days, const double* quant,
+                                   int32_t nq, int32_t* out_host) {
+  if (!c || !out_host) return ABC_E_INVAL;
+  int rc = check_predict(&c->cfg, c->N, R, days, quant, nq);
+  if (rc) return rc;
+  const size_t sb = predict_scratch_bytes(c->N, R, days, nq);
+  const size_t ob = sizeof(int32_t) * static_cast<size_t>(days + 1) * 3 * nq;
+  char* buf = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&buf), sb + align256(ob), c->st) != cudaSuccess)
+    return ABC_E_NOMEM;
+  auto* out = reinterpret_cast<int32_t*>(buf + sb);
+  const bool weighted = c->cfg.weight_mode == ABC_W_IMPORTANCE;
+  rc = launch_predict(c->p, c->u[c->cur], weighted ? c->W[c->cur] : nullptr, c->N, R, days, quant,
+                      nq, out, buf, sb, c->st);
+  if (rc == ABC_OK &&
+      (cudaMemcpyAsync(out_host, out, ob, cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+       cudaStreamSynchronize(c->st) != cudaSuccess))
+    rc = ABC_E_CUDA;
+  cudaFreeAsync(buf, c->st);
+  cudaStreamSynchronize(c->st);
+  return rc;
 }
 
 ABC_API int32_t abc_generations(const abc_ctx* c) { return c ? c->gen : 0; }
