@@ -64,6 +64,15 @@ extern "C" {
 #define ABC_SIM_PAPER_NORMAL 1  /* the paper's floor(Normal(h, sqrt h)) flows (Sec. 2.2) */
 #define ABC_BETA_PAPER 0        /* s ~ Beta(eps_t/eps_1, 2t)  (Eq. 16)                    */
 #define ABC_BETA_FIXED 1        /* s ~ Beta(beta_a, beta_b)                               */
+/* Real-shape rules (Sec. 3.2 names the mean-variance and mode-concentration
+ * parameterisations beside Eq. 16 without their schedules; here the location
+ * follows eps_t/eps_1 as a_t does and the spread follows the stage count as
+ * b_t = 2t does).  Sampled by the Gamma ratio X/(X+Y) with Marsaglia-Tsang
+ * Gamma variates; t is the stage, ratio = (float)(eps_t / eps_1), 1 when
+ * eps_1 = 0. */
+#define ABC_BETA_REAL 2         /* s ~ Beta(beta_p1, beta_p2), real shapes in [2^-20, 2^20] */
+#define ABC_BETA_MEAN_VAR 3     /* mean p1 ratio, variance p2 / t; a + b at least 1/16    */
+#define ABC_BETA_MODE_CONC 4    /* mode p1 ratio, concentration a + b = p2 t              */
 #define ABC_W_PAPER 0           /* resampling weights eps_t - d (Eq. 10), W = 1/N         */
 #define ABC_W_IMPORTANCE 1      /* importance weights with the O(N^2) kernel sum          */
 #define ABC_P_FP32 0            /* O(N^2) weight sum on CUDA cores in fp32                */
@@ -123,6 +132,14 @@ typedef struct {
   float surrogate_rho_min;  /* floor of the pass probability (0 < rho_min <= 1)          */
   float audit_frac;         /* audit probability of a screened-out proposal             */
   int32_t surrogate_ring;   /* training pairs kept; 0 = min(2^21, 16 N)                 */
+  /* Real-shape Beta rules: REAL (a, b) = (p1, p2), both in [2^-20, 2^20];
+   * MEAN_VAR 0 < p1 < 1 (stage-1 mean), 0 < p2 <= 1 (stage-1 variance);
+   * MODE_CONC 0 <= p1 <= 1 (stage-1 mode), 2 <= p2 <= 2^20 (stage-1
+   * concentration).  (1/3, 1/18) and (0, 3) give Beta(1, 2) at stage 1, the
+   * paper's a_1 = 1, b_1 = 2.  Shapes derived at later stages are clamped to
+   * [2^-20, 2^20]. */
+  float beta_p1;
+  float beta_p2;
   int32_t pad_end;
 } abc_config;
 
@@ -206,9 +223,15 @@ ABC_API int abc_resample_prefix_noalloc(const double* d, const double* W, int64_
  * a), s ~ Beta(a_t, b) (BETA stream, c2 = a << 8 | block), z ~ N(0, I8)
  * (WALK stream), u' = u_anc + sqrt(s) z; the first u' inside [0,1]^8 is kept,
  * else flag = 1.  a_t = beta_a, or in paper mode (cfg->beta_mode) a_t =
- * (float)(*eps / *eps1) (1 when *eps1 is 0) and b = beta_b as given.
+ * (float)(*eps / *eps1) (1 when *eps1 is 0) and b = beta_b as given (integer
+ * b, product form).  Under the real-shape rules (ABC_BETA_REAL, _MEAN_VAR,
+ * _MODE_CONC) beta_a and beta_b are ignored: the shapes follow from
+ * cfg->beta_p1, cfg->beta_p2, the ratio and the stage t = c1 >> 16 (t >= 1
+ * for the last two), and s is drawn by the Gamma ratio (BETA stream, c2 =
+ * a << 8 | block, blocks 0..63 for X and 64..127 for Y).
  * u: device float [8][n]; prefix: device u64[n]; eps, eps1: device double[1]
- * (read only in paper mode; may be NULL otherwise); outputs: device
+ * (read by the paper, mean-variance and mode-concentration rules; may be
+ * NULL otherwise); outputs: device
  * u_out [8][slots], s_out[slots], anc_out, attempts_out (int32), flag_out (u8). */
 ABC_API int abc_propose(const abc_config* cfg, const float* u, int64_t n, const uint64_t* prefix,
                 const double* eps, const double* eps1, float beta_a, int32_t beta_b,
@@ -339,6 +362,8 @@ typedef struct {
   int64_t rows_tc;          /* weight rows on the tensor cores (the rest on FP32)    */
   double ms_tc;             /* device time of the tensor-core weight kernel          */
   double ms_fp32;           /* device time of the FP32 weight kernel                 */
+  float beta_bf;            /* b_t as fp32 (beta_b is 0 under the real-shape rules)  */
+  int32_t pad_s;
 } abc_gen_stats;
 
 /* Validate cfg, allocate every device buffer (owned by the context), copy

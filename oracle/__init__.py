@@ -36,7 +36,8 @@ class Smc(C.Structure):
     _fields_ = [
         ("N", C.c_int32), ("M", C.c_int32), ("pad", C.c_int32), ("alpha", C.c_double),
         ("beta_mode", C.c_int32),
-        ("beta_a", C.c_float), ("beta_b", C.c_int32), ("weight_mode", C.c_int32),
+        ("beta_a", C.c_float), ("beta_b", C.c_int32), ("beta_p1", C.c_float),
+        ("beta_p2", C.c_float), ("weight_mode", C.c_int32),
         ("max_batches", C.c_int32), ("max_redraw", C.c_int32), ("nthreads", C.c_int32),
     ]
 
@@ -44,7 +45,8 @@ class Smc(C.Structure):
 class GenStats(C.Structure):
     _fields_ = [
         ("eps", C.c_double), ("eps1", C.c_double), ("ess", C.c_double), ("beta_a", C.c_float),
-        ("beta_b", C.c_int32), ("batches", C.c_int64), ("sims", C.c_int64),
+        ("beta_b", C.c_int32), ("beta_bf", C.c_float), ("pad", C.c_int32),
+        ("batches", C.c_int64), ("sims", C.c_int64),
         ("exhausted", C.c_int64), ("accepted_total", C.c_int64), ("total", C.c_uint64),
         ("status", C.c_int32),
     ]
@@ -71,6 +73,16 @@ def lib():
         L.or_beta.restype = C.c_float
         L.or_beta.argtypes = [C.POINTER(C.c_uint32), C.c_float, C.c_int32, C.c_uint32,
                               C.c_uint32, C.c_uint32]
+        L.or_gamma_log.restype = C.c_float
+        L.or_gamma_log.argtypes = [C.POINTER(C.c_uint32), C.c_float, C.c_uint32, C.c_uint32,
+                                   C.c_uint32, C.c_uint32]
+        L.or_beta_real.restype = C.c_float
+        L.or_beta_real.argtypes = [C.POINTER(C.c_uint32), C.c_float, C.c_float, C.c_uint32,
+                                   C.c_uint32, C.c_uint32]
+        L.or_beta_shape.restype = None
+        L.or_beta_shape.argtypes = [C.c_int32, C.c_float, C.c_int32, C.c_float, C.c_int32,
+                                    C.c_float, C.c_float, C.POINTER(C.c_float),
+                                    C.POINTER(C.c_int32)]
         L.or_kth.restype = C.c_double
         L.or_kth.argtypes = [C.POINTER(C.c_double), C.c_int64, C.c_int64]
         L.or_rank.restype = C.c_int64
@@ -154,6 +166,28 @@ def beta(key, a, b, c0, c1, attempt):
     return lib().or_beta(_p(k, C.c_uint32), float(np.float32(a)), int(b), c0, c1, attempt)
 
 
+def gamma_log(key, alpha, c0, c1, attempt, blk0=0):
+    k = np.ascontiguousarray(key, np.uint32)
+    return lib().or_gamma_log(_p(k, C.c_uint32), float(np.float32(alpha)), c0, c1, attempt, blk0)
+
+
+def beta_real(key, a, b, c0, c1, attempt):
+    k = np.ascontiguousarray(key, np.uint32)
+    return lib().or_beta_real(_p(k, C.c_uint32), float(np.float32(a)), float(np.float32(b)),
+                              c0, c1, attempt)
+
+
+BETA_PAPER, BETA_FIXED, BETA_REAL, BETA_MEAN_VAR, BETA_MODE_CONC = 0, 1, 2, 3, 4
+
+
+def beta_shape(mode, ratio, t, fa=2.0, fb=5, p1=0.0, p2=0.0):
+    """(a, b, integer b or 0) of stage t under a step-size Beta rule."""
+    out = (C.c_float * 2)()
+    bi = C.c_int32()
+    lib().or_beta_shape(mode, float(np.float32(ratio)), t, fa, fb, p1, p2, out, C.byref(bi))
+    return float(out[0]), float(out[1]), int(bi.value)
+
+
 def simulate(m: OracleModel, u, c1=0, tag=TAG_SIM, c0_idx=None, skip=None, traj=False,
              nthreads=1):
     u = np.ascontiguousarray(u, np.float32)
@@ -206,7 +240,9 @@ def resample_prefix(d, W, eps, mode):
 
 
 def propose(m: OracleModel, u, prefix, total, beta_a, beta_b, slots, c1, max_redraw=64,
-            c0_idx=None, nthreads=1):
+            c0_idx=None, nthreads=1, beta_bf=0.0):
+    """beta_b >= 1: s ~ Beta(beta_a, beta_b) by the product form; beta_b = 0:
+    s ~ Beta(beta_a, beta_bf) by the Gamma ratio."""
     u = np.ascontiguousarray(u, np.float32)
     prefix = np.ascontiguousarray(prefix, np.uint64)
     n = u.shape[1]
@@ -217,7 +253,8 @@ def propose(m: OracleModel, u, prefix, total, beta_a, beta_b, slots, c1, max_red
     fl = np.zeros(slots, np.uint8)
     c0 = None if c0_idx is None else np.ascontiguousarray(c0_idx, np.uint32)
     lib().or_propose(m.ref(), _p(u, C.c_float), C.c_int64(n), _p(prefix, C.c_uint64),
-                     C.c_uint64(total), C.c_float(beta_a), C.c_int32(beta_b), C.c_int64(slots),
+                     C.c_uint64(total), C.c_float(beta_a), C.c_int32(beta_b),
+                     C.c_float(beta_bf), C.c_int64(slots),
                      _p(c0, C.c_uint32), C.c_uint32(c1), C.c_int32(max_redraw), _p(up, C.c_float),
                      _p(s, C.c_float), _p(anc, C.c_int32), _p(att, C.c_int32), _p(fl, C.c_uint8),
                      C.c_int(nthreads))
@@ -245,10 +282,11 @@ def normalize(logW):
 
 
 def make_smc(N, M=None, alpha=0.5, beta_mode=0, beta_a=2.0, beta_b=5, weight_mode=0,
-             max_batches=64, max_redraw=64, nthreads=1):
+             max_batches=64, max_redraw=64, nthreads=1, beta_p1=0.0, beta_p2=0.0):
     c = Smc()
     c.N, c.M = N, (N if M is None else M)
     c.alpha, c.beta_mode, c.beta_a, c.beta_b = alpha, beta_mode, beta_a, beta_b
+    c.beta_p1, c.beta_p2 = beta_p1, beta_p2
     c.weight_mode, c.max_batches, c.max_redraw, c.nthreads = (weight_mode, max_batches,
                                                               max_redraw, nthreads)
     return c

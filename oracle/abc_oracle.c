@@ -586,13 +586,117 @@ OR_API float or_beta(const uint32_t key[2], float a, int32_t b, uint32_t c0, uin
 }
 
 /*
+ * log of a Gamma(alpha, 1) variate, alpha > 0, by Marsaglia and Tsang's
+ * squeeze-and-reject method ("A simple method for generating gamma
+ * variables", ACM TOMS 26(3), 2000): with d = alpha - 1/3 and c = 1/sqrt(9d),
+ * x ~ N(0,1) and v = (1 + c x)^3, the candidate d v is kept when v > 0 and
+ * U < 1 - 0.0331 x^4 (squeeze) or log U < x^2/2 + d (1 - v + log v).  For
+ * alpha < 1 the variate is Gamma(alpha + 1) U'^(1/alpha), taken in logs.
+ * Iteration i (i < 64) reads Philox block (c0, c1, attempt << 8 | (blk0 + i),
+ * BETA): words 0 and 1 give x (Box-Muller), word 2 gives U, word 3 of the
+ * accepting block gives U'.  The acceptance test never reads word 3, so U' is
+ * uniform and independent of the accepted candidate.  If all 64 iterations
+ * reject (probability below 0.05^64) the candidate is d (v = 1).
+ */
+OR_API float or_gamma_log(const uint32_t key[2], float alpha, uint32_t c0, uint32_t c1,
+                          uint32_t attempt, uint32_t blk0) {
+  const float al = alpha < 1.0f ? alpha + 1.0f : alpha;
+  const float d = al - 0x1.555556p-2f;            /* fp32 nearest to 1/3 */
+  const float c = 1.0f / sqrtf(9.0f * d);
+  uint32_t w[4] = {0, 0, 0, 0};
+  float lg = or_logf(d);
+  for (uint32_t i = 0; i < 64u; ++i) {
+    philox_ctr(key, c0, c1, (attempt << 8) | (blk0 + i), TAG_BETA, w);
+    const float x = or_normal(or_uniform(w[0]), or_uniform(w[1]));
+    float v = 1.0f + c * x;
+    if (!(v > 0.0f)) continue;
+    v = (v * v) * v;
+    const float U = or_uniform(w[2]);
+    const float x2 = x * x;
+    int keep = U < 1.0f - 0.0331f * (x2 * x2);
+    if (!keep) keep = or_logf(U) < 0.5f * x2 + d * ((1.0f - v) + or_logf(v));
+    if (keep) {
+      lg = or_logf(d * v);
+      break;
+    }
+  }
+  if (alpha < 1.0f) lg = lg + or_logf(or_uniform(w[3])) / alpha;
+  return lg;
+}
+
+/* s ~ Beta(a, b) for real a, b > 0: X / (X + Y) with X ~ Gamma(a) (blocks
+ * 0..63) and Y ~ Gamma(b) (blocks 64..127), as 1 / (1 + exp(log Y - log X)). */
+OR_API float or_beta_real(const uint32_t key[2], float a, float b, uint32_t c0, uint32_t c1,
+                          uint32_t attempt) {
+  const float lx = or_gamma_log(key, a, c0, c1, attempt, 0u);
+  const float ly = or_gamma_log(key, b, c0, c1, attempt, 64u);
+  return 1.0f / (1.0f + or_expf(ly - lx));
+}
+
+/*
+ * Step-size Beta shapes of stage t >= 1 (Eq. 16 and the two alternatives that
+ * Sec. 3.2 names).  ratio = eps_t / eps_1 rounded to fp32 (1 when eps_1 = 0).
+ *   mode 0 (paper):  a = ratio, integer b = 2t;
+ *   mode 1 (fixed):  a = fa, integer b = fb;
+ *   mode 2 (real):   a = p1, b = p2;
+ *   mode 3 (mean-variance): mean mu = p1 ratio, variance v = p2 / t;
+ *       nu = mu (1 - mu) / v - 1 (= a + b), at least 1/16; a = mu nu,
+ *       b = (1 - mu) nu;
+ *   mode 4 (mode-concentration): mode w = p1 ratio, concentration
+ *       k = p2 t; a = w (k - 2) + 1, b = (1 - w) (k - 2) + 1.
+ * Modes 3 and 4 clamp a and b to [2^-20, 2^20].  out[0] = a, out[1] = b;
+ * *bint = the integer b of modes 0 and 1 (product sampler), 0 for the
+ * real-shape modes (Gamma-ratio sampler).
+ */
+OR_API void or_beta_shape(int32_t mode, float ratio, int32_t t, float fa, int32_t fb, float p1,
+                          float p2, float out[2], int32_t* bint) {
+  float a = 1.0f, b = 1.0f;
+  int32_t bi = 0;
+  if (mode == 0) {
+    a = ratio;
+    bi = 2 * t;
+    b = (float)bi;
+  } else if (mode == 1) {
+    a = fa;
+    bi = fb;
+    b = (float)bi;
+  } else if (mode == 2) {
+    a = p1;
+    b = p2;
+  } else {
+    if (mode == 3) {
+      const float mu = p1 * ratio;
+      const float v = p2 / (float)t;
+      float nu = (mu * (1.0f - mu)) / v - 1.0f;
+      if (!(nu >= 0.0625f)) nu = 0.0625f;
+      a = mu * nu;
+      b = (1.0f - mu) * nu;
+    } else {
+      const float w = p1 * ratio;
+      const float k2 = p2 * (float)t - 2.0f;
+      a = w * k2 + 1.0f;
+      b = (1.0f - w) * k2 + 1.0f;
+    }
+    if (!(a >= 0x1p-20f)) a = 0x1p-20f;
+    if (!(b >= 0x1p-20f)) b = 0x1p-20f;
+    if (a > 0x1p20f) a = 0x1p20f;
+    if (b > 0x1p20f) b = 0x1p20f;
+  }
+  out[0] = a;
+  out[1] = b;
+  *bint = bi;
+}
+
+/*
  * BDSS perturbation (Eq. 16-17) with the categorical ancestor draw (Eq. 11)
  * and a prior-support check: for slot j of batch c1 = (t << 16) | batch,
  * attempt a = 0..max_redraw-1 draws (ancestor, s, z) afresh until
  * u' = u_anc + sqrt(s) z lies in [0,1]^8.  On exhaustion flag = 1.
+ * s ~ Beta(beta_a, beta_b) by the product form when beta_b >= 1, else
+ * Beta(beta_a, beta_bf) by the Gamma ratio.
  */
 OR_API void or_propose(const or_model* m, const float* u, int64_t n, const uint64_t* prefix,
-                       uint64_t total, float beta_a, int32_t beta_b, int64_t slots,
+                       uint64_t total, float beta_a, int32_t beta_b, float beta_bf, int64_t slots,
                        const uint32_t* c0_idx, uint32_t c1, int32_t max_redraw, float* u_out,
                        float* s_out, int32_t* anc_out, int32_t* attempts_out, uint8_t* flag_out,
                        int nthreads) {
@@ -611,7 +715,8 @@ OR_API void or_propose(const or_model* m, const float* u, int64_t n, const uint6
       uint32_t w[4];
       philox_ctr(m->key, j, c1, (uint32_t)a, TAG_ANCESTOR, w);
       anc = draw_ancestor(prefix, n, total, w[0], w[1]);
-      s = or_beta(m->key, beta_a, beta_b, j, c1, (uint32_t)a);
+      s = beta_b > 0 ? or_beta(m->key, beta_a, beta_b, j, c1, (uint32_t)a)
+                     : or_beta_real(m->key, beta_a, beta_bf, j, c1, (uint32_t)a);
       float sd = sqrtf(s);
       ok = 1;
       for (int blk = 0; blk < 4; ++blk) {
@@ -701,9 +806,10 @@ typedef struct {
   int32_t M;            /* proposals per batch ("parallel simulations")    */
   int32_t pad;
   double alpha;         /* survival ratio (Eq. 8), 0.5 in the paper         */
-  int32_t beta_mode;    /* 0: Beta(eps_t/eps_1, 2t) (Eq. 16); 1: fixed      */
-  float beta_a;
-  int32_t beta_b;
+  int32_t beta_mode;    /* 0: Beta(eps_t/eps_1, 2t) (Eq. 16); 1: fixed;     */
+  float beta_a;         /* 2: real shapes; 3: mean-variance; 4: mode-       */
+  int32_t beta_b;       /* concentration (or_beta_shape)                    */
+  float beta_p1, beta_p2;
   int32_t weight_mode;  /* 0: eps - d (Eq. 10); 1: importance weights       */
   int32_t max_batches;
   int32_t max_redraw;
@@ -715,7 +821,9 @@ typedef struct {
   double eps1;          /* eps_1                                            */
   double ess;
   float beta_a;
-  int32_t beta_b;
+  int32_t beta_b;       /* integer b (product sampler), 0 for real shapes   */
+  float beta_bf;        /* b as fp32                                        */
+  int32_t pad;
   int64_t batches, sims, exhausted, accepted_total;
   uint64_t total;       /* resampling total                                  */
   int32_t status;       /* 0 ok, 1 batch budget exhausted                   */
@@ -744,17 +852,14 @@ OR_API int32_t or_generation(const or_model* m, const or_smc* c, int32_t t, doub
   double eps1 = t == 1 ? eps : eps1_in;
   st->eps = eps;
   st->eps1 = eps1;
-  float ba;
+  float shape[2];
   int32_t bb;
-  if (c->beta_mode == 0) {
-    ba = eps1 > 0.0 ? (float)(eps / eps1) : 1.0f;
-    bb = 2 * t;
-  } else {
-    ba = c->beta_a;
-    bb = c->beta_b;
-  }
+  const float ratio = eps1 > 0.0 ? (float)(eps / eps1) : 1.0f;
+  or_beta_shape(c->beta_mode, ratio, t, c->beta_a, c->beta_b, c->beta_p1, c->beta_p2, shape, &bb);
+  const float ba = shape[0];
   st->beta_a = ba;
   st->beta_b = bb;
+  st->beta_bf = shape[1];
   uint32_t* q = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
   uint64_t* prefix = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)N);
   uint64_t total = or_resample_prefix(d, W, N, eps, c->weight_mode, q, prefix);
@@ -769,8 +874,8 @@ OR_API int32_t or_generation(const or_model* m, const or_smc* c, int32_t t, doub
   int32_t b;
   for (b = 0; b < c->max_batches && filled < N; ++b) {
     uint32_t c1 = ((uint32_t)t << 16) | (uint32_t)b;
-    or_propose(m, u, N, prefix, total, ba, bb, M, NULL, c1, c->max_redraw, up, sp, ap, att, fl,
-               c->nthreads);
+    or_propose(m, u, N, prefix, total, ba, bb, shape[1], M, NULL, c1, c->max_redraw, up, sp, ap,
+               att, fl, c->nthreads);
     or_simulate(m, up, M, NULL, c1, TAG_SIM, fl, dp, NULL, c->nthreads);
     st->sims += M;
     for (int64_t j = 0; j < M; ++j) {

@@ -18,7 +18,7 @@ ABC_E_TOO_LARGE = -7
 ABC_NOALLOC_MAX_N = 1 << 24
 ABC_MODEL_SAIRD, ABC_MODEL_GAUSS_TOY = 0, 1
 ABC_SIM_BINOMIAL, ABC_SIM_PAPER_NORMAL = 0, 1
-ABC_BETA_PAPER, ABC_BETA_FIXED = 0, 1
+ABC_BETA_PAPER, ABC_BETA_FIXED, ABC_BETA_REAL, ABC_BETA_MEAN_VAR, ABC_BETA_MODE_CONC = 0, 1, 2, 3, 4
 ABC_W_PAPER, ABC_W_IMPORTANCE = 0, 1
 ABC_P_FP32, ABC_P_BF16_TC = 0, 1
 TAG_PRIOR, TAG_ANCESTOR, TAG_BETA, TAG_WALK, TAG_SIM, TAG_SCREEN, TAG_AUDIT = 0, 1, 2, 3, 4, 5, 6
@@ -56,7 +56,7 @@ class AbcConfig(C.Structure):
         ("surrogate", C.c_int32), ("surrogate_start", C.c_int32), ("surrogate_steps", C.c_int32),
         ("surrogate_batch", C.c_int32), ("surrogate_lr", C.c_float), ("surrogate_tau", C.c_float),
         ("surrogate_rho_min", C.c_float), ("audit_frac", C.c_float), ("surrogate_ring", C.c_int32),
-        ("pad_end", C.c_int32),
+        ("beta_p1", C.c_float), ("beta_p2", C.c_float), ("pad_end", C.c_int32),
     ]
 
 
@@ -70,7 +70,7 @@ class AbcGenStats(C.Structure):
         ("ms_weights", C.c_double), ("screened", C.c_int64), ("audited", C.c_int64),
         ("audit_accepted", C.c_int64), ("train_loss", C.c_double), ("ms_screen", C.c_double),
         ("ms_train", C.c_double), ("rows_tc", C.c_int64), ("ms_tc", C.c_double),
-        ("ms_fp32", C.c_double),
+        ("ms_fp32", C.c_double), ("beta_bf", C.c_float), ("pad_s", C.c_int32),
     ]
 
     def as_dict(self):

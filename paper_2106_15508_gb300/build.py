@@ -7,7 +7,8 @@ dynamically (so the process shares one runtime with PyTorch).
 Numerics flags: -fmad=false (the simulator and proposal kernels reproduce a
 CPU specification bit for bit, so a*b+c must never be fused implicitly;
 explicit __fmaf_rn is unaffected), IEEE division and square root, no
-flush-to-zero (the defaults; --use_fast_math is never used).
+flush-to-zero (the defaults; --use_fast_math is never used); host code with
+-ffp-contract=off for the same reason (shape rules evaluated on both sides).
 """
 import os
 import shutil
@@ -43,7 +44,7 @@ def cuda_lib_dir() -> str:
 def _compile(src: str, extra=()) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), "-std=c++17", "-O3", *ARCH, "-lineinfo", "-fmad=false", "-prec-div=true",
-           "-prec-sqrt=true", "-ftz=false", "-Xcompiler", "-fPIC,-fvisibility=hidden",
+           "-prec-sqrt=true", "-ftz=false", "-Xcompiler", "-fPIC,-fvisibility=hidden,-ffp-contract=off",
            "-c", os.path.join(CSRC, src), "-o", obj, *extra]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

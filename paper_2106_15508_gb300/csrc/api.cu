@@ -74,13 +74,31 @@ int check_config(const abc_config* c) {
   return ABC_OK;
 }
 
+BetaRule beta_rule(const abc_config& c) {
+  return BetaRule{c.beta_mode, c.beta_a, c.beta_b, c.beta_p1, c.beta_p2};
+}
+
+// (a_t, b_t as fp32, integer b_t or 0) of stage t >= 1 as the proposal kernel
+// derives them, for the generation statistics
+void stage_shapes(const abc_config& c, double eps, double eps1, int32_t t, int32_t bb,
+                  abc_gen_stats* g) {
+  const float ratio = eps1 > 0.0 ? static_cast<float>(eps / eps1) : 1.0f;
+  const BetaRule r = beta_rule(c);
+  if (c.beta_mode >= ABC_BETA_REAL) {
+    beta_real_shape(r, ratio, t, &g->beta_a, &g->beta_bf);
+    g->beta_b = 0;
+  } else {
+    g->beta_a = c.beta_mode == ABC_BETA_PAPER ? ratio : c.beta_a;
+    g->beta_b = bb;
+    g->beta_bf = static_cast<float>(bb);
+  }
+}
+
 int check_smc(const abc_config* c) {
   if (c->n_particles < 1 || c->batch_size < 0) return ABC_E_INVAL;
   if (!(c->survival_alpha > 0.0 && c->survival_alpha <= 1.0)) return ABC_E_INVAL;
-  if (c->beta_mode != ABC_BETA_PAPER && c->beta_mode != ABC_BETA_FIXED) return ABC_E_INVAL;
-  if (c->beta_mode == ABC_BETA_FIXED &&
-      (!(c->beta_a > 0.0f) || c->beta_b < 1 || c->beta_b > 1024))
-    return ABC_E_INVAL;
+  if (!beta_rule_ok(beta_rule(*c))) return ABC_E_INVAL;
+  if (c->beta_mode == ABC_BETA_FIXED && (c->beta_b < 1 || c->beta_b > 1024)) return ABC_E_INVAL;
   if (c->weight_mode != ABC_W_PAPER && c->weight_mode != ABC_W_IMPORTANCE) return ABC_E_INVAL;
   if (c->weight_prec != ABC_P_FP32 && c->weight_prec != ABC_P_BF16_TC) return ABC_E_INVAL;
   if (c->max_batches < 1 || c->max_batches > 65535) return ABC_E_INVAL;
@@ -219,11 +237,12 @@ ABC_API int abc_propose(const abc_config* cfg, const float* u, int64_t n, const 
   if (!u || !prefix || n < 1 || n > kMaxIndex || slots < 0 || slots > kMaxIndex) return ABC_E_INVAL;
   if (slots > 0 && (!u_out || !s_out || !anc_out || !attempts_out || !flag_out)) return ABC_E_INVAL;
   if (cfg->max_redraw < 1 || cfg->max_redraw > (1 << 23)) return ABC_E_INVAL;
-  const int paper = cfg->beta_mode == ABC_BETA_PAPER;
-  if (!paper && !(beta_a > 0.0f)) return ABC_E_INVAL;
-  return launch_propose(make_params(*cfg), u, n, prefix, paper, eps, eps1, beta_a, beta_b, slots,
-                        c0_idx, c1, cfg->max_redraw, u_out, s_out, anc_out, attempts_out,
-                        flag_out, as_stream(stream));
+  BetaRule rule = beta_rule(*cfg);
+  rule.a = beta_a;
+  rule.b = beta_b;
+  return launch_propose(make_params(*cfg), u, n, prefix, rule, eps, eps1, slots, c0_idx, c1,
+                        cfg->max_redraw, u_out, s_out, anc_out, attempts_out, flag_out,
+                        as_stream(stream));
 }
 
 ABC_API size_t abc_accept_scratch_bytes(int64_t M) { return accept_scratch_bytes(M); }
@@ -577,8 +596,10 @@ int generation_t(abc_ctx* c) {
   const int32_t t = c->gen;
   const int cur = c->cur, nxt = 1 - c->cur;
   const int paper_beta = c->cfg.beta_mode == ABC_BETA_PAPER;
-  const int32_t bb = paper_beta ? 2 * t : c->cfg.beta_b;
+  const int32_t bb = paper_beta ? 2 * t : c->cfg.beta_mode == ABC_BETA_FIXED ? c->cfg.beta_b : 0;
   if (bb > 1024 || t > 32767) return ABC_E_INVAL;
+  BetaRule rule = beta_rule(c->cfg);
+  rule.b = bb;
   double* eps = c->scal + 0;
   double* eps1 = c->scal + 1;
   double* ess = c->scal + 2;
@@ -602,9 +623,8 @@ int generation_t(abc_ctx* c) {
   unsigned h_inf_err = 0;
   for (b = 0; b < c->cfg.max_batches && filled < c->N; ++b) {
     const uint32_t c1 = (static_cast<uint32_t>(t) << 16) | static_cast<uint32_t>(b);
-    rc = launch_propose(c->p, c->u[cur], c->N, c->prefix, paper_beta, eps, eps1, c->cfg.beta_a, bb,
-                        c->M, nullptr, c1, c->cfg.max_redraw, c->up, c->sp, c->ap, c->att,
-                        c->flag, st);
+    rc = launch_propose(c->p, c->u[cur], c->N, c->prefix, rule, eps, eps1, c->M, nullptr, c1,
+                        c->cfg.max_redraw, c->up, c->sp, c->ap, c->att, c->flag, st);
     if (rc) return rc;
     int h_mc = 0;
     if (screen) {
@@ -684,7 +704,6 @@ int generation_t(abc_ctx* c) {
     g.sims = static_cast<int64_t>(b) * c->M - h_cnt[2];
   }
   g.sim_days = g.sims * static_cast<int64_t>(c->cfg.model == ABC_MODEL_SAIRD ? c->T : 1);
-  g.beta_b = bb;
   g.ms_sim = ms_sim;
   int h_nc = 0;
   int h_counts[2] = {0, 0};
@@ -753,8 +772,7 @@ int generation_t(abc_ctx* c) {
   g.eps = h_scal[0];
   g.eps1 = h_scal[1];
   g.ess = g.status == ABC_OK ? h_scal[2] : 0.0;
-  g.beta_a = paper_beta ? (h_scal[1] > 0.0 ? static_cast<float>(h_scal[0] / h_scal[1]) : 1.0f)
-                        : c->cfg.beta_a;
+  stage_shapes(c->cfg, h_scal[0], h_scal[1], t, bb, &g);
   c->eps1_host = h_scal[1];
   if (sur && g.status == ABC_OK && c->cfg.surrogate_steps > 0) {
     // train on everything simulated so far (the ring keeps the latest pairs)
@@ -1008,9 +1026,7 @@ RunCtxView ctx_view(abc_ctx* c) {
   v.M = c->M;
   int64_t k = static_cast<int64_t>(std::ceil(c->cfg.survival_alpha * static_cast<double>(c->N)));
   v.rank = std::min<int64_t>(std::max<int64_t>(k, 1), c->N);
-  v.paper_beta = c->cfg.beta_mode == ABC_BETA_PAPER;
-  v.fixed_b = c->cfg.beta_b;
-  v.beta_a = c->cfg.beta_a;
+  v.beta = beta_rule(c->cfg);
   v.max_redraw = c->cfg.max_redraw;
   v.weight_mode = c->cfg.weight_mode;
   v.weight_prec = c->cfg.weight_prec;
@@ -1243,10 +1259,7 @@ ABC_API int abc_batch_generation(abc_batch* b) {
     g.eps = d.eps;
     g.eps1 = d.eps1;
     g.ess = d.status == ABC_OK ? d.ess : 0.0;
-    g.beta_a = c->cfg.beta_mode == ABC_BETA_PAPER
-                   ? (d.eps1 > 0.0 ? static_cast<float>(d.eps / d.eps1) : 1.0f)
-                   : c->cfg.beta_a;
-    g.beta_b = d.beta_b;
+    stage_shapes(c->cfg, d.eps, d.eps1, g.generation, d.beta_b, &g);
     g.batches = d.batches;
     g.accepted = d.accepted;
     g.exhausted = d.exhausted;

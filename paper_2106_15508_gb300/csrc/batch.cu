@@ -35,6 +35,7 @@ __global__ void k_run_start(RunDev* r, int paper_beta, int fixed_b, cudaGraphCon
   r->off = r->done;
   r->b = 0;
   r->c1 = r->t << 16;
+  // integer b of the product form (0 under the real-shape rules)
   r->beta_b = paper_beta ? static_cast<int>(2 * r->t) : fixed_b;
   r->filled = 0;
   r->accepted = 0;
@@ -115,7 +116,8 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
     if (cs != cudaStreamCaptureStatusActive) return ABC_E_CUDA;
     ABC_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
   }
-  k_run_start<<<1, 32, 0, st>>>(r, v.paper_beta, v.fixed_b, h);
+  const int fixed_b = v.beta.mode == ABC_BETA_FIXED ? v.beta.b : 0;
+  k_run_start<<<1, 32, 0, st>>>(r, v.beta.mode == ABC_BETA_PAPER, fixed_b, h);
   ABC_LAUNCH_CHECK();
   {
     cudaStreamCaptureStatus cs;
@@ -138,9 +140,9 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
   ABC_CUDA_TRY(cudaStreamBeginCaptureToGraph(body_st, body, nullptr, nullptr, 0,
                                              cudaStreamCaptureModeRelaxed));
   l_body0 = launch_count();
-  rc = launch_propose(v.p, v.u_cur, v.N, v.prefix, v.paper_beta, &r->eps, &r->eps1, v.beta_a,
-                      std::max(1, v.fixed_b), v.M, nullptr, 0u, v.max_redraw, v.up, v.sp, v.ap,
-                      v.att, v.flag, body_st, &r->c1, &r->beta_b, &r->off);
+  rc = launch_propose(v.p, v.u_cur, v.N, v.prefix, v.beta, &r->eps, &r->eps1, v.M, nullptr, 0u,
+                      v.max_redraw, v.up, v.sp, v.ap, v.att, v.flag, body_st, &r->c1, &r->beta_b,
+                      &r->off);
   if (!rc)
     rc = launch_simulate(v.p, v.obs, v.up, v.M, nullptr, 0u, ABC_TAG_SIM, v.flag, v.dp, nullptr,
                          body_st, &r->c1, &r->off, br.sim_threads);

@@ -26,8 +26,8 @@ struct RunDev {
 struct RunCtxView {
   SimParams p;
   int64_t N, M, rank;
-  int paper_beta, fixed_b, max_redraw, weight_mode, weight_prec;
-  float beta_a;
+  BetaRule beta;
+  int max_redraw, weight_mode, weight_prec;
   const int32_t* obs;
   float *u_cur, *u_nxt, *s_cur, *s_nxt, *up, *sp, *cu, *cc;
   double *d_cur, *d_nxt, *W_cur, *W_nxt, *dp, *logW;
@@ -60,8 +60,9 @@ int launch_simulate(const SimParams&, const int32_t*, const float*, int64_t, con
 int launch_select(const double*, int64_t, int64_t, double*, void*, size_t, cudaStream_t);
 int launch_resample_prefix(const double*, const double*, int64_t, const double*, int, uint32_t*,
                            uint64_t*, void*, size_t, cudaStream_t);
-int launch_propose(const SimParams&, const float*, int64_t, const uint64_t*, int, const double*,
-                   const double*, float, int, int64_t, const uint32_t*, uint32_t, int, float*,
+bool beta_rule_ok(const BetaRule&);
+int launch_propose(const SimParams&, const float*, int64_t, const uint64_t*, const BetaRule&,
+                   const double*, const double*, int64_t, const uint32_t*, uint32_t, int, float*,
                    float*, int32_t*, int32_t*, uint8_t*, cudaStream_t,
                    const uint32_t* c1_dev = nullptr, const int* beta_b_dev = nullptr,
                    const int* off_dev = nullptr);

@@ -114,6 +114,54 @@ struct WeightTiming {
   const int* counts = nullptr;
 };
 
+// Step-size Beta rule of stage t (Eq. 16 and the mean-variance and
+// mode-concentration parameterisations of Sec. 3.2): mode ABC_BETA_*, the
+// fixed shapes (a, b) and the real-shape parameters p1, p2.
+struct BetaRule {
+  int32_t mode;
+  float a;
+  int32_t b;
+  float p1, p2;
+};
+
+// Shapes of a real-shape rule (ABC_BETA_REAL, _MEAN_VAR, _MODE_CONC) at stage
+// t >= 1 with ratio = eps_t / eps_1 in fp32:
+//   real:  (p1, p2);
+//   mean-variance: mu = p1 ratio, v = p2 / t, nu = max(mu (1 - mu) / v - 1,
+//     1/16), (a, b) = (mu nu, (1 - mu) nu);
+//   mode-concentration: w = p1 ratio, k = p2 t, (a, b) = (w (k - 2) + 1,
+//     (1 - w) (k - 2) + 1);
+// the last two clamped to [2^-20, 2^20].  Plain fp32 operations, each
+// rounded once (the library is built without contraction on host and device).
+__host__ __device__ inline void beta_real_shape(const BetaRule& r, float ratio, int32_t t,
+                                                float* a_out, float* b_out) {
+  float a, b;
+  if (r.mode == ABC_BETA_REAL) {
+    a = r.p1;
+    b = r.p2;
+  } else {
+    if (r.mode == ABC_BETA_MEAN_VAR) {
+      const float mu = r.p1 * ratio;
+      const float v = r.p2 / static_cast<float>(t);
+      float nu = (mu * (1.0f - mu)) / v - 1.0f;
+      if (!(nu >= 0.0625f)) nu = 0.0625f;
+      a = mu * nu;
+      b = (1.0f - mu) * nu;
+    } else {
+      const float w = r.p1 * ratio;
+      const float k2 = r.p2 * static_cast<float>(t) - 2.0f;
+      a = w * k2 + 1.0f;
+      b = (1.0f - w) * k2 + 1.0f;
+    }
+    if (!(a >= 0x1p-20f)) a = 0x1p-20f;
+    if (!(b >= 0x1p-20f)) b = 0x1p-20f;
+    if (a > 0x1p20f) a = 0x1p20f;
+    if (b > 0x1p20f) b = 0x1p20f;
+  }
+  *a_out = a;
+  *b_out = b;
+}
+
 struct AncInfo {
   const int32_t* anc = nullptr;
   const float* u_prev = nullptr;

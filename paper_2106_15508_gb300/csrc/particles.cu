@@ -283,10 +283,27 @@ int launch_resample_prefix_noalloc(const double* d, const double* W, int64_t n,
 }
 
 // -------------------------------------------------------- A6-A7 propose ---
+bool beta_rule_ok(const BetaRule& r) {
+  const auto finite = [](float x) { return x == x && x - x == 0.0f; };
+  switch (r.mode) {
+    case ABC_BETA_PAPER:
+      return true;
+    case ABC_BETA_FIXED:
+      return r.a > 0.0f && finite(r.a);
+    case ABC_BETA_REAL:
+      return r.p1 >= 0x1p-20f && r.p1 <= 0x1p20f && r.p2 >= 0x1p-20f && r.p2 <= 0x1p20f;
+    case ABC_BETA_MEAN_VAR:
+      return r.p1 > 0.0f && r.p1 < 1.0f && r.p2 > 0.0f && r.p2 <= 1.0f;
+    case ABC_BETA_MODE_CONC:
+      return r.p1 >= 0.0f && r.p1 <= 1.0f && r.p2 >= 2.0f && r.p2 <= 0x1p20f;
+    default:
+      return false;
+  }
+}
+
 __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
-                          const uint64_t* __restrict__ prefix, int paper_beta,
-                          const double* eps_p, const double* eps1_p, float beta_a, int beta_b,
-                          int64_t slots, const uint32_t* __restrict__ c0_idx, uint32_t c1,
+                          const uint64_t* __restrict__ prefix, BetaRule rule,
+                          const double* eps_p, const double* eps1_p, int64_t slots, const uint32_t* __restrict__ c0_idx, uint32_t c1,
                           int max_redraw, float* __restrict__ u_out, float* __restrict__ s_out,
                           int32_t* __restrict__ anc_out, int32_t* __restrict__ att_out,
                           uint8_t* __restrict__ flag_out, const uint32_t* __restrict__ c1_dev,
@@ -295,15 +312,19 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
   if (i >= slots) return;
   if (off_dev && *off_dev) return;          // run finished
   if (c1_dev) c1 = *c1_dev;                 // set on the device (graph launches)
-  if (beta_b_dev) beta_b = *beta_b_dev;
+  const int beta_b = beta_b_dev ? *beta_b_dev : rule.b;
   const uint32_t j = c0_idx ? c0_idx[i] : static_cast<uint32_t>(i);
   const unsigned long long total = prefix[n - 1];
-  float a_t = beta_a;
-  if (paper_beta) {
-    // Eq. 16: a_t = eps_t / eps_1 (1 when eps_1 is zero)
+  float a_t = rule.a, b_t = 0.0f;
+  float ratio = 1.0f;
+  if (rule.mode != ABC_BETA_FIXED && rule.mode != ABC_BETA_REAL) {
+    // Eq. 16: eps_t / eps_1 (1 when eps_1 is zero)
     const double e1 = *eps1_p;
-    a_t = e1 > 0.0 ? __double2float_rn(__ddiv_rn(*eps_p, e1)) : 1.0f;
+    ratio = e1 > 0.0 ? __double2float_rn(__ddiv_rn(*eps_p, e1)) : 1.0f;
   }
+  if (rule.mode == ABC_BETA_PAPER) a_t = ratio;
+  const bool real_shape = rule.mode >= ABC_BETA_REAL;
+  if (real_shape) beta_real_shape(rule, ratio, static_cast<int32_t>(c1 >> 16), &a_t, &b_t);
   float up[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   float s = 0.0f;
   int64_t anc = 0;
@@ -321,17 +342,23 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
       else lo = mid + 1;
     }
     anc = lo;
-    // Eq. 16: s ~ Beta(a_t, b) as exp(sum_m log(U_m) / (a_t + m))
-    float acc = 0.0f;
-    u32x4 wb{0u, 0u, 0u, 0u};
-    for (int m = 0; m < beta_b; ++m) {
-      if ((m & 3) == 0)
-        wb = philox4x32_10(j, c1, (static_cast<uint32_t>(a) << 8) | static_cast<uint32_t>(m >> 2),
-                           ABC_TAG_BETA, p.k0, p.k1);
-      const uint32_t wm = (m & 3) == 0 ? wb.x : (m & 3) == 1 ? wb.y : (m & 3) == 2 ? wb.z : wb.w;
-      acc = __fadd_rn(acc, __fdiv_rn(dev_log(unif(wm)), __fadd_rn(a_t, __int2float_rn(m))));
+    if (real_shape) {
+      // real shapes: the Gamma ratio
+      s = dev_beta_real(a_t, b_t, j, c1, static_cast<uint32_t>(a), p.k0, p.k1);
+    } else {
+      // Eq. 16: s ~ Beta(a_t, b) as exp(sum_m log(U_m) / (a_t + m))
+      float acc = 0.0f;
+      u32x4 wb{0u, 0u, 0u, 0u};
+      for (int m = 0; m < beta_b; ++m) {
+        if ((m & 3) == 0)
+          wb = philox4x32_10(j, c1,
+                             (static_cast<uint32_t>(a) << 8) | static_cast<uint32_t>(m >> 2),
+                             ABC_TAG_BETA, p.k0, p.k1);
+        const uint32_t wm = (m & 3) == 0 ? wb.x : (m & 3) == 1 ? wb.y : (m & 3) == 2 ? wb.z : wb.w;
+        acc = __fadd_rn(acc, __fdiv_rn(dev_log(unif(wm)), __fadd_rn(a_t, __int2float_rn(m))));
+      }
+      s = dev_exp(acc);
     }
-    s = dev_exp(acc);
     const float sd = __fsqrt_rn(s);
     // Eq. 17: u' = u_anc + sqrt(s) z; the support check covers all 8 coordinates
     ok = true;
@@ -358,17 +385,24 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
 }
 
 int launch_propose(const SimParams& p, const float* u, int64_t n, const uint64_t* prefix,
-                   int paper_beta, const double* eps, const double* eps1, float beta_a,
-                   int beta_b, int64_t slots, const uint32_t* c0_idx, uint32_t c1, int max_redraw,
-                   float* u_out, float* s_out, int32_t* anc_out, int32_t* att_out,
-                   uint8_t* flag_out, cudaStream_t st, const uint32_t* c1_dev,
-                   const int* beta_b_dev, const int* off_dev) {
-  if (n <= 0 || slots < 0 || beta_b < 1 || beta_b > 1024 || max_redraw < 1) return ABC_E_INVAL;
-  if (paper_beta && (!eps || !eps1)) return ABC_E_INVAL;
+                   const BetaRule& rule, const double* eps, const double* eps1, int64_t slots,
+                   const uint32_t* c0_idx, uint32_t c1, int max_redraw, float* u_out,
+                   float* s_out, int32_t* anc_out, int32_t* att_out, uint8_t* flag_out,
+                   cudaStream_t st, const uint32_t* c1_dev, const int* beta_b_dev,
+                   const int* off_dev) {
+  if (n <= 0 || slots < 0 || max_redraw < 1 || !beta_rule_ok(rule)) return ABC_E_INVAL;
+  const bool integer_b = rule.mode == ABC_BETA_PAPER || rule.mode == ABC_BETA_FIXED;
+  if (integer_b && !beta_b_dev && (rule.b < 1 || rule.b > 1024)) return ABC_E_INVAL;
+  if (rule.mode != ABC_BETA_FIXED && rule.mode != ABC_BETA_REAL && (!eps || !eps1))
+    return ABC_E_INVAL;
+  // the scheduled real-shape rules read the stage t = c1 >> 16 >= 1
+  if ((rule.mode == ABC_BETA_MEAN_VAR || rule.mode == ABC_BETA_MODE_CONC) && !c1_dev &&
+      (c1 >> 16) == 0)
+    return ABC_E_INVAL;
   if (slots == 0) return ABC_OK;
   k_propose<<<static_cast<unsigned>(ceil_div(slots, 128)), 128, 0, st>>>(
-      p, u, n, prefix, paper_beta, eps, eps1, beta_a, beta_b, slots, c0_idx, c1, max_redraw,
-      u_out, s_out, anc_out, att_out, flag_out, c1_dev, beta_b_dev, off_dev);
+      p, u, n, prefix, rule, eps, eps1, slots, c0_idx, c1, max_redraw, u_out, s_out, anc_out,
+      att_out, flag_out, c1_dev, beta_b_dev, off_dev);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

@@ -23,7 +23,8 @@ def oracle_smc(cfg, nthreads=8):
     return O.make_smc(cfg.n_particles, M=cfg.batch_size or cfg.n_particles,
                       alpha=cfg.survival_alpha, beta_mode=cfg.beta_mode, beta_a=cfg.beta_a,
                       beta_b=cfg.beta_b, weight_mode=cfg.weight_mode,
-                      max_batches=cfg.max_batches, max_redraw=cfg.max_redraw, nthreads=nthreads)
+                      max_batches=cfg.max_batches, max_redraw=cfg.max_redraw, nthreads=nthreads,
+                      beta_p1=cfg.beta_p1, beta_p2=cfg.beta_p2)
 
 
 def saird_config(N, T, P, seed=1, **kw):

@@ -52,8 +52,9 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(abc_config), offsetof(abc_config, population),
          offsetof(abc_config, seed), offsetof(abc_config, survival_alpha),
          offsetof(abc_config, max_redraw), sizeof(abc_gen_stats));
-  printf("%zu %zu %zu\n", offsetof(abc_gen_stats, eps), offsetof(abc_gen_stats, batches),
-         offsetof(abc_gen_stats, ms_weights));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(abc_gen_stats, eps), offsetof(abc_gen_stats, batches),
+         offsetof(abc_gen_stats, ms_weights), offsetof(abc_gen_stats, beta_bf),
+         offsetof(abc_config, beta_p2));
   return 0;
 }
 """
@@ -67,7 +68,8 @@ int main(void) {
     want = [ctypes.sizeof(G.AbcConfig), G.AbcConfig.population.offset, G.AbcConfig.seed.offset,
             G.AbcConfig.survival_alpha.offset, G.AbcConfig.max_redraw.offset,
             ctypes.sizeof(G.AbcGenStats), G.AbcGenStats.eps.offset, G.AbcGenStats.batches.offset,
-            G.AbcGenStats.ms_weights.offset]
+            G.AbcGenStats.ms_weights.offset, G.AbcGenStats.beta_bf.offset,
+            G.AbcConfig.beta_p2.offset]
     assert got == want
 
 
@@ -84,6 +86,13 @@ def test_defaults_and_argument_checks_without_gpu(lib):
     assert lib.abc_prior(ctypes.byref(bad), 10, None, None) == -1
     bad = G.config(beta_mode=G.ABC_BETA_FIXED, beta_b=0)
     assert lib.abc_init(ctypes.byref(bad), None, None, ctypes.byref(h)) == -1
+    # real-shape rules: parameters outside their ranges
+    for mode, p1, p2 in [(G.ABC_BETA_REAL, 0.0, 1.0), (G.ABC_BETA_REAL, 1.0, 2.0 ** 21),
+                         (G.ABC_BETA_MEAN_VAR, 1.0, 0.01), (G.ABC_BETA_MEAN_VAR, 0.3, 0.0),
+                         (G.ABC_BETA_MODE_CONC, 1.5, 3.0), (G.ABC_BETA_MODE_CONC, 0.5, 1.9),
+                         (5, 0.5, 3.0)]:
+        bad = G.config(beta_mode=mode, beta_p1=p1, beta_p2=p2)
+        assert lib.abc_init(ctypes.byref(bad), None, None, ctypes.byref(h)) == -1, (mode, p1, p2)
     assert lib.abc_select_kth(None, 10, 1, None, None, 0, None) == -1
     assert lib.abc_select_scratch_bytes(1 << 20) > 0
     assert lib.abc_weights_scratch_bytes(4096, 4096) >= 4096 * 9 * 4
