@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 METRIC = "sim-days/s; wall-time to ε_final per run, surrogate+batched vs plain"
 UNIT = "sim-days/s"
 MUFU_EX2_PER_CLK_PER_SM = 16  # 32-bit exp2 issue rate of one SM (4 SMSPs x 4 lanes)
+TC_K_USED = 60  # split-bf16 products per pair in the tensor-core weight GEMM (10 features x 6)
 
 
 def _peaks():
@@ -253,8 +254,43 @@ def run_gpu(args):
         pk = sum(r * (s.pairs // N) for r, s in zip(rows_k, stats))
         kern[name] = {"ms": ms_k / args.steps, "pairs": pk / args.steps,
                       "gexp_s": pk / (ms_k / 1e3) / 1e9 if ms_k > 0 else 0.0}
+    # the tensor-core kernel does two kinds of work: the split-bf16 GEMM over
+    # every (row, column) pair (2 x 60 flops: 10 features x 6 split products)
+    # and one exponential per pair of the rows whose sums it keeps (rows_exp;
+    # the other rows only get candidate lists).  Its roofline is whichever of
+    # the two lower bounds on its time is larger.
+    tc_ms = kern["k_weights_tc"]["ms"]
+    tc_flops = sum(2 * TC_K_USED * s.rows_tc * (s.pairs // N) for s in stats) / args.steps
+    tc_exps = sum(s.rows_exp * (s.pairs // N) for s in stats) / args.steps
+    kern["k_weights_tc"].update({"exp_pairs": tc_exps, "tflops": tc_flops / (tc_ms / 1e3) / 1e12
+                                 if tc_ms > 0 else 0.0})
     dom = max(kern, key=lambda k: kern[k]["ms"])
     achieved = kern[dom]["gexp_s"] * 1e9
+    exp_src = ("measured ex2.approx.f32 rate (abc_ex2_probe: saturating microbenchmark on "
+               "this GPU); %d SMs x %d ex2/clk x %.0f MHz would be %.0f Gexp/s" % (
+                   n_sm, MUFU_EX2_PER_CLK_PER_SM, sm_mhz, exp_nominal / 1e9))
+    if dom == "k_weights_tc" and tc_ms > 0:
+        tc_peak = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])) * 1e12
+        t_tensor = tc_flops / tc_peak
+        t_exp = tc_exps / exp_peak
+        if t_tensor >= t_exp:
+            a = tc_flops / (tc_ms / 1e3)
+            roofline = {"bound": "tensor", "kernel": dom, "achieved": a / 1e12,
+                        "peak": tc_peak / 1e12, "unit": "TFLOP/s", "frac": a / tc_peak,
+                        "peak_source": "%s bf16 dense GEMM, sustained (cuBLAS, %s)" % (
+                            src, "MEASURED_PEAKS.json" if src == "measured" else "recipe"),
+                        "work": "2 x 60 flops per (row, column) pair",
+                        "exp_frac": tc_exps / (tc_ms / 1e3) / exp_peak, "traffic": None}
+        else:
+            a = tc_exps / (tc_ms / 1e3)
+            roofline = {"bound": "alu", "kernel": dom, "achieved": a / 1e9,
+                        "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": a / exp_peak,
+                        "peak_source": exp_src, "work": "one exp2 per pair of the kept rows",
+                        "tensor_frac": tc_flops / (tc_ms / 1e3) / tc_peak, "traffic": None}
+    else:
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9,
+                    "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": achieved / exp_peak,
+                    "peak_source": exp_src, "work": "one exp2 per pair", "traffic": None}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -267,14 +303,7 @@ def run_gpu(args):
                    [g_first + k for k in range(args.steps)],
                    "l2": "flushed between steps (256 MB write)",
                    "theta_star": [round(float(x), 6) for x in theta_star]},
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9,
-                     "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": achieved / exp_peak,
-                     "peak_source": "measured ex2.approx.f32 rate (abc_ex2_probe: saturating "
-                                    "microbenchmark on this GPU); %d SMs x %d ex2/clk x "
-                                    "%.0f MHz would be %.0f Gexp/s" % (
-                                        n_sm, MUFU_EX2_PER_CLK_PER_SM, sm_mhz,
-                                        exp_nominal / 1e9),
-                     "traffic": None},
+        "roofline": roofline,
         "weight_kernels": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in kern.items()},
         "weight_pass_gexp_s": pairs / (wms / 1e3) / 1e9 if wms > 0 else 0.0,
         "phases_ms": {"weights": wms / args.steps, "simulator": sim_ms / args.steps,
@@ -284,7 +313,8 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
         "generations": [{"t": s.generation, "eps": s.eps, "ess": s.ess, "batches": s.batches,
-                         "sim_days": s.sim_days, "ms": s.ms} for s in stats],
+                         "sim_days": s.sim_days, "ms": s.ms, "rows_exp": s.rows_exp,
+                         "rows_tc": s.rows_tc, "ms_tc": s.ms_tc} for s in stats],
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(stats, w)

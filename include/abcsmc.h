@@ -364,6 +364,8 @@ typedef struct {
   double ms_fp32;           /* device time of the FP32 weight kernel                 */
   float beta_bf;            /* b_t as fp32 (beta_b is 0 under the real-shape rules)  */
   int32_t pad_s;
+  int64_t rows_exp;         /* rows whose tensor-core sums were kept (error bound    */
+                            /*   small enough); the rest of rows_tc were refined    */
 } abc_gen_stats;
 
 /* Validate cfg, allocate every device buffer (owned by the context), copy

@@ -706,7 +706,7 @@ int generation_t(abc_ctx* c) {
   g.sim_days = g.sims * static_cast<int64_t>(c->cfg.model == ABC_MODEL_SAIRD ? c->T : 1);
   g.ms_sim = ms_sim;
   int h_nc = 0;
-  int h_counts[2] = {0, 0};
+  int h_counts[4] = {0, 0, 0, 0};
   WeightTiming wt;
   wt.tc0 = c->ek[0];
   wt.tc1 = c->ek[1];
@@ -760,6 +760,7 @@ int generation_t(abc_ctx* c) {
     // per-kernel split of the pass (FP32 only: every row on the FP32 kernel)
     const bool tc = c->cfg.weight_prec == ABC_P_BF16_TC;
     g.rows_tc = tc ? h_counts[1] : 0;
+    g.rows_exp = tc ? h_counts[2] : 0;
     if (tc && h_counts[1] > 0) {
       ABC_CUDA_TRY(cudaEventElapsedTime(&ms, c->ek[0], c->ek[1]));
       g.ms_tc = ms;

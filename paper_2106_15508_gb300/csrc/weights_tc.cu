@@ -138,58 +138,147 @@ __device__ __forceinline__ void store_packed_row(__nv_bfloat16* tile, int r, con
 //            the row exactly from them (rinfo = (ancestor lower bound of the
 //            maximum in the accumulator frame, delta_j));
 //   class 2: delta_j not finite: the FP32 kernel recomputes the row.
+// The packed operand is written afterwards by k_tc_pack_sorted, in class order.
 __global__ void k_tc_pack_rows(const float* __restrict__ up, const float* __restrict__ s,
-                               int64_t rows, int64_t rows_pad, const float* __restrict__ centre,
+                               int64_t rows, const float* __restrict__ centre,
                                const unsigned* __restrict__ y2max, AncInfo ai,
-                               __nv_bfloat16* __restrict__ Apk, double* __restrict__ rowc,
-                               float2* __restrict__ rinfo, uint8_t* __restrict__ rcls) {
+                               double* __restrict__ rowc, float2* __restrict__ rinfo,
+                               uint8_t* __restrict__ rcls) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= rows_pad) return;
+  if (j >= rows) return;
+  const float sj = fmaxf(s[j], kSMinTc);
+  const float L = 1.4426950408889634f / (2.0f * sj);
+  double xx = 0.0;
+  float xxf = 0.0f, dd = 0.0f;
+  const int32_t a = ai.anc ? ai.anc[j] : -1;
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const float u = up[static_cast<int64_t>(d) * rows + j];
+    const float x = u - centre[d];
+    xx += static_cast<double>(x) * static_cast<double>(x);
+    xxf = __fmaf_rn(x, x, xxf);
+    if (a >= 0) {
+      const float e = u - ai.u_prev[static_cast<int64_t>(d) * ai.n_prev + a];
+      dd = __fmaf_rn(e, e, dd);
+    }
+  }
+  rowc[j] = -static_cast<double>(L) * xx;
+  // error bound over the columns that can matter
+  const float X = sqrtf(xxf);
+  float Y = sqrtf(__uint_as_float(*y2max));
+  float lb = -INFINITY;
+  if (a >= 0 && ai.q_prev[a] > 0u) {
+    const double ca = log2(static_cast<double>(ai.q_prev[a])) - 32.0;
+    // 1.001: margin for the fp32 rounding of this estimate
+    Y = fminf(Y, 1.001f * (X + sqrtf(dd + (60.0f - static_cast<float>(ca)) / L)));
+    // the ancestor's exponent in the accumulator frame (e - rowc), less a
+    // rounding margin: a lower bound of the row maximum there
+    const double ea =
+        ca - static_cast<double>(L) * static_cast<double>(dd) + static_cast<double>(L) * xx;
+    lb = static_cast<float>(ea - (1.0 + 1e-3 * fabs(ea) + 1e-6 * static_cast<double>(L) * xx));
+  }
+  const float mag = L * (2.0f * X * Y + Y * Y) + 32.0f;
+  const float delta = 0x1p-24f * 64.0f * mag;
+  const float B = 0x1p-24f * (64.0f * mag + 160.0f);
+  rinfo[j] = make_float2(lb, delta);
+  rcls[j] = B <= kTcBoundMax ? 0 : (isfinite(delta) && delta < 1e30f ? 1 : 2);
+}
+
+// ---- rows sorted by class ------------------------------------------------------
+// The epilogue's work depends on the row class: exponential sums for class 0,
+// candidate lists for class 1, nothing for class 2.  A row is a TMEM lane, so
+// a warp runs the union of its 32 rows' work; the tensor-core pass therefore
+// takes the rows in class order (stable within a class): perm[p] = original
+// row at position p.  Counts per tile of kClsTile rows, then offsets, then
+// the scatter.
+constexpr int kClsTile = 1024;
+
+__global__ void k_cls_count(const uint8_t* __restrict__ rcls, int64_t rows, int* __restrict__ cnt3) {
+  __shared__ int sm[32];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kClsTile;
+  int c[3] = {0, 0, 0};
+  for (int e = threadIdx.x; e < kClsTile; e += blockDim.x) {
+    const int64_t j = base + e;
+    if (j < rows) {
+      const int v = rcls[j];
+      c[0] += v == 0;
+      c[1] += v == 1;
+      c[2] += v == 2;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int v = block_sum<int>(c[k], sm);
+    if (threadIdx.x == 0) cnt3[3 * blockIdx.x + k] = v;
+  }
+}
+
+// off3[3 i + k] = first position of tile i's class-k rows; ncls[0..2] = rows
+// per class
+__global__ void k_cls_scan(const int* __restrict__ cnt3, int ntiles, int* __restrict__ off3,
+                           int* __restrict__ ncls) {
+  __shared__ int sm[32];
+  __shared__ int last;
+  int base = 0;
+#pragma unroll 1
+  for (int k = 0; k < 3; ++k) {
+    int carry = 0;
+    for (int b = 0; b < ntiles; b += blockDim.x) {
+      const int i = b + threadIdx.x;
+      const int v = i < ntiles ? cnt3[3 * i + k] : 0;
+      const int inc = block_incl_scan<int>(v, sm);
+      if (i < ntiles) off3[3 * i + k] = base + carry + inc - v;
+      if (threadIdx.x == blockDim.x - 1) last = inc;
+      __syncthreads();
+      carry += last;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) ncls[k] = carry;
+    base += carry;
+  }
+}
+
+__global__ void k_cls_scatter(const uint8_t* __restrict__ rcls, int64_t rows,
+                              const int* __restrict__ off3, int* __restrict__ perm) {
+  __shared__ int sm[32];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * kClsTile + 4 * threadIdx.x;
+  int cl[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) cl[e] = base + e < rows ? rcls[base + e] : 3;
+#pragma unroll 1
+  for (int k = 0; k < 3; ++k) {
+    int c = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) c += cl[e] == k;
+    const int inc = block_incl_scan<int>(c, sm);
+    int p = off3[3 * blockIdx.x + k] + inc - c;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (cl[e] == k) perm[p++] = static_cast<int>(base + e);
+  }
+}
+
+// packed row features [2 L x (8), -L, 1] at sorted position p (zeros for the
+// padding positions p >= rows)
+__global__ void k_tc_pack_sorted(const float* __restrict__ up, const float* __restrict__ s,
+                                 int64_t rows, int64_t rows_pad, const float* __restrict__ centre,
+                                 const int* __restrict__ perm, __nv_bfloat16* __restrict__ Apk) {
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= rows_pad) return;
   float f[10];
-  if (j < rows) {
+  if (p < rows) {
+    const int64_t j = perm[p];
     const float sj = fmaxf(s[j], kSMinTc);
     const float L = 1.4426950408889634f / (2.0f * sj);
-    double xx = 0.0;
-    float xxf = 0.0f, dd = 0.0f;
-    const int32_t a = ai.anc ? ai.anc[j] : -1;
 #pragma unroll
-    for (int d = 0; d < 8; ++d) {
-      const float u = up[static_cast<int64_t>(d) * rows + j];
-      const float x = u - centre[d];
-      f[d] = 2.0f * L * x;
-      xx += static_cast<double>(x) * static_cast<double>(x);
-      xxf = __fmaf_rn(x, x, xxf);
-      if (a >= 0) {
-        const float e = u - ai.u_prev[static_cast<int64_t>(d) * ai.n_prev + a];
-        dd = __fmaf_rn(e, e, dd);
-      }
-    }
+    for (int d = 0; d < 8; ++d) f[d] = 2.0f * L * (up[static_cast<int64_t>(d) * rows + j] - centre[d]);
     f[8] = -L;
     f[9] = 1.0f;
-    rowc[j] = -static_cast<double>(L) * xx;
-    // error bound over the columns that can matter
-    const float X = sqrtf(xxf);
-    float Y = sqrtf(__uint_as_float(*y2max));
-    float lb = -INFINITY;
-    if (a >= 0 && ai.q_prev[a] > 0u) {
-      const double ca = log2(static_cast<double>(ai.q_prev[a])) - 32.0;
-      // 1.001: margin for the fp32 rounding of this estimate
-      Y = fminf(Y, 1.001f * (X + sqrtf(dd + (60.0f - static_cast<float>(ca)) / L)));
-      // the ancestor's exponent in the accumulator frame (e - rowc), less a
-      // rounding margin: a lower bound of the row maximum there
-      const double ea = ca - static_cast<double>(L) * static_cast<double>(dd) + static_cast<double>(L) * xx;
-      lb = static_cast<float>(ea - (1.0 + 1e-3 * fabs(ea) + 1e-6 * static_cast<double>(L) * xx));
-    }
-    const float mag = L * (2.0f * X * Y + Y * Y) + 32.0f;
-    const float delta = 0x1p-24f * 64.0f * mag;
-    const float B = 0x1p-24f * (64.0f * mag + 160.0f);
-    rinfo[j] = make_float2(lb, delta);
-    rcls[j] = B <= kTcBoundMax ? 0 : (isfinite(delta) && delta < 1e30f ? 1 : 2);
   } else {
 #pragma unroll
     for (int d = 0; d < 10; ++d) f[d] = 0.0f;
   }
-  store_packed_row<true>(Apk + (j / kTcM) * (kTcM * kTcK), static_cast<int>(j % kTcM), f);
+  store_packed_row<true>(Apk + (p / kTcM) * (kTcM * kTcK), static_cast<int>(p % kTcM), f);
 }
 
 // centre of the survivor columns: per-block fp64 sums in a fixed order
@@ -297,7 +386,7 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
              const int* __restrict__ nc_p, int64_t rows,
              float2* __restrict__ part, unsigned* err, const int* __restrict__ off_dev,
              const float2* __restrict__ rinfo, const uint8_t* __restrict__ rcls,
-             int* __restrict__ cand, int* __restrict__ ccnt) {
+             int* __restrict__ cand, int* __restrict__ ccnt, const int* __restrict__ perm) {
   extern __shared__ uint8_t tc_smem_raw[];
   if (off_dev && *off_dev) return;  // run finished or its generation stopped (block-uniform)
   const int64_t nrows = rows;
@@ -314,8 +403,9 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     const int g = threadIdx.x / kTcM, r = threadIdx.x % kTcM;
     if (g < kTcGroups && row0 + r < nrows) {
       const int64_t slot = kTcGroups * static_cast<int64_t>(blockIdx.y) + g;
-      part[slot * rows + row0 + r] = make_float2(-INFINITY, 0.0f);
-      ccnt[slot * rows + row0 + r] = 0;
+      const int64_t row = perm[row0 + r];
+      part[slot * rows + row] = make_float2(-INFINITY, 0.0f);
+      ccnt[slot * rows + row] = 0;
     }
     return;
   }
@@ -403,16 +493,24 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     // the row maximum: lb is a lower bound of the maximum (the ancestor's
     // exponent, or the largest value seen so far less its error), so a column
     // with v < lb - delta - margin is at least margin bits under it
-    const int64_t row = row0 + r;
+    // rows come in class order: position row0 + r holds original row perm[.]
+    const int64_t row = row0 + r < nrows ? perm[row0 + r] : -1;
     const int64_t slot = kTcGroups * static_cast<int64_t>(blockIdx.y) + g;
-    const bool refine = row < nrows && rcls[row] == 1;
+    const int cls = row >= 0 ? rcls[row] : 3;
+    const bool refine = cls == 1;
+    // warp-uniform work selection: exponential sums serve the class-0 rows,
+    // candidate lists the class-1 rows (whose sums k_tc_refine recomputes);
+    // class-2 and padding rows need neither.  Sorted rows make nearly every
+    // warp single-class.
+    const bool w_exp = __any_sync(0xffffffffu, cls == 0);
+    const bool w_cand = __any_sync(0xffffffffu, refine);
     float lb = -INFINITY, dl = 0.0f;
     if (refine) {
       const float2 ri = rinfo[row];
       lb = ri.x;
       dl = ri.y;
     }
-    int* lst = cand + (slot * rows + row) * kCandCap;
+    int* lst = cand + (slot * rows + (refine ? row : 0)) * kCandCap;
     int nlist = 0;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t & 1;
@@ -424,55 +522,58 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
       // this thread's two 32-column chunks of the tile (c = g, g + 4), both
       // loads in flight before one wait
       static_assert(kTcN / 32 == 2 * kTcGroups, "two chunks per epilogue thread");
-      float vv[2][32];
-      tmem_ld32x2(lane_base + static_cast<uint32_t>(b * kTcN + g * 32),
-                  lane_base + static_cast<uint32_t>(b * kTcN + (g + kTcGroups) * 32), vv[0],
-                  vv[1]);
+      if (w_exp || w_cand) {
+        float vv[2][32];
+        tmem_ld32x2(lane_base + static_cast<uint32_t>(b * kTcN + g * 32),
+                    lane_base + static_cast<uint32_t>(b * kTcN + (g + kTcGroups) * 32), vv[0],
+                    vv[1]);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = g + h * kTcGroups;
-        const float (&v)[32] = vv[h];
-        // chunk maximum with three-input max instructions
-        float cm = max3(v[0], v[1], v[2]);
+        for (int h = 0; h < 2; ++h) {
+          const int c = g + h * kTcGroups;
+          const float (&v)[32] = vv[h];
+          // chunk maximum with three-input max instructions
+          float cm = max3(v[0], v[1], v[2]);
 #pragma unroll
-        for (int i = 3; i < 31; i += 2) cm = max3(cm, v[i], v[i + 1]);
-        cm = fmaxf(cm, v[31]);
-        if (refine) {
-          lb = fmaxf(lb, cm - dl);
-          const float thr = lb - dl - kCandMargin;
-          if (cm > thr) {
-            const int col0 = (tb + t) * kTcN + c * 32;
+          for (int i = 3; i < 31; i += 2) cm = max3(cm, v[i], v[i + 1]);
+          cm = fmaxf(cm, v[31]);
+          if (refine) {
+            lb = fmaxf(lb, cm - dl);
+            const float thr = lb - dl - kCandMargin;
+            if (cm > thr) {
+              const int col0 = (tb + t) * kTcN + c * 32;
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-              if (v[i] > thr && col0 + i < nc) {
-                if (nlist < kCandCap) lst[nlist] = col0 + i;
-                ++nlist;
-              }
+              for (int i = 0; i < 32; ++i)
+                if (v[i] > thr && col0 + i < nc) {
+                  if (nlist < kCandCap) lst[nlist] = col0 + i;
+                  ++nlist;
+                }
+            }
           }
-        }
-        if (cm > m) {
-          const float f = ex2(m - cm);
-          S *= f;
-          cS *= f;
-          ts *= f;
-          m = cm;
-        }
-        // v - m and the running sum in packed fp32x2 (two columns per
-        // instruction); the exponentials one by one on the MUFU
-        // (four independent accumulators keep the add chain short)
-        const unsigned long long m2 = f2_pack(m, m);
-        unsigned long long acc[4];
+          if (!w_exp) continue;
+          if (cm > m) {
+            const float f = ex2(m - cm);
+            S *= f;
+            cS *= f;
+            ts *= f;
+            m = cm;
+          }
+          // v - m and the running sum in packed fp32x2 (two columns per
+          // instruction); the exponentials one by one on the MUFU
+          // (four independent accumulators keep the add chain short)
+          const unsigned long long m2 = f2_pack(m, m);
+          unsigned long long acc[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a] = f2_pack(0.0f, 0.0f);
+          for (int a = 0; a < 4; ++a) acc[a] = f2_pack(0.0f, 0.0f);
 #pragma unroll
-        for (int i = 0; i < 32; i += 2) {
-          float d0, d1;
-          f2_unpack(f2_sub(f2_pack(v[i], v[i + 1]), m2), d0, d1);
-          acc[(i >> 1) & 3] = f2_add(acc[(i >> 1) & 3], f2_pack(ex2(d0), ex2(d1)));
+          for (int i = 0; i < 32; i += 2) {
+            float d0, d1;
+            f2_unpack(f2_sub(f2_pack(v[i], v[i + 1]), m2), d0, d1);
+            acc[(i >> 1) & 3] = f2_add(acc[(i >> 1) & 3], f2_pack(ex2(d0), ex2(d1)));
+          }
+          float a0, a1;
+          f2_unpack(f2_add(f2_add(acc[0], acc[1]), f2_add(acc[2], acc[3])), a0, a1);
+          ts += a0 + a1;
         }
-        float a0, a1;
-        f2_unpack(f2_add(f2_add(acc[0], acc[1]), f2_add(acc[2], acc[3])), a0, a1);
-        ts += a0 + a1;
       }
       tc_fence_before();
       mbar_arrive(&sm.tempty[b]);
@@ -481,8 +582,8 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
       cS = (tt - S) - y;
       S = tt;
     }
-    if (row < nrows) {
-      part[slot * rows + row] = make_float2(m, S);
+    if (row >= 0) {
+      if (cls == 0) part[slot * rows + row] = make_float2(m, S);
       ccnt[slot * rows + row] = refine ? nlist : 0;
     }
   }
@@ -492,13 +593,15 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
   if (warp == kTcIssuer) tmem_dealloc(tmem, kTmemCols);
 }
 
+// class-0 rows: log W from the partials (k_tc_refine and the FP32 kernel write
+// the other rows)
 __global__ void k_weights_tc_combine(const float2* __restrict__ part, int nchunks,
                                      const float* __restrict__ s, const double* __restrict__ rowc,
                                      int64_t rows, const uint64_t* __restrict__ total_p,
                                      double* __restrict__ logW, const int* __restrict__ off_dev,
-                                     const int* __restrict__ rows_dev) {
+                                     const uint8_t* __restrict__ rcls) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= (rows_dev ? static_cast<int64_t>(*rows_dev) : rows) || (off_dev && *off_dev)) return;
+  if (j >= rows || (off_dev && *off_dev) || rcls[j] != 0) return;
   const double sj = static_cast<double>(fmaxf(s[j], kSMinTc));
   double M = -INFINITY;
   for (int c = 0; c < nchunks; ++c)
@@ -710,7 +813,7 @@ static int tc_chunks(int64_t rows, int64_t ncap, int mult) {
 
 struct TcLayout {
   size_t apk, bpk, rowc, part, err, rinfo, rcls, cand, ccnt, fp, cnt, off, counts, idx, u_f, s_f,
-      lw_f, ctr, total;
+      lw_f, ctr, cnt3, off3, perm, total;
 };
 
 static TcLayout tc_layout(int64_t rows, int64_t ncap, int mult) {
@@ -737,12 +840,16 @@ static TcLayout tc_layout(int64_t rows, int64_t ncap, int mult) {
   take(l.fp, weights_fp32_scratch_bytes(rows, ncap, kFp32Mult));
   take(l.cnt, 4 * static_cast<size_t>(nt));
   take(l.off, 4 * static_cast<size_t>(nt));
-  take(l.counts, 8);
+  take(l.counts, 8 * sizeof(int));
   take(l.idx, 4 * R);
   take(l.u_f, 32 * R);
   take(l.s_f, 4 * R);
   take(l.lw_f, 8 * R);
   take(l.ctr, sizeof(double) * 8 * kCtrBlocks + 256 + 256);  // column sums, centre, radius
+  const size_t ncls_tiles = static_cast<size_t>(ceil_div(std::max<int64_t>(rows, 1), kClsTile));
+  take(l.cnt3, 3 * 4 * ncls_tiles);
+  take(l.off3, 3 * 4 * ncls_tiles);
+  take(l.perm, 4 * R);
   l.total = o;
   return l;
 }
@@ -798,6 +905,9 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   auto* cpart = reinterpret_cast<double*>(b + l.ctr);
   auto* centre = reinterpret_cast<float*>(b + l.ctr + sizeof(double) * 8 * kCtrBlocks);
   auto* y2max = reinterpret_cast<unsigned*>(b + l.ctr + sizeof(double) * 8 * kCtrBlocks + 256);
+  auto* cnt3 = reinterpret_cast<int*>(b + l.cnt3);
+  auto* off3 = reinterpret_cast<int*>(b + l.off3);
+  auto* perm = reinterpret_cast<int*>(b + l.perm);
   if (err_dev) *err_dev = err;
   ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
   // columns: centre, radius, packed once (centred)
@@ -809,10 +919,21 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   k_tc_pack_cols<<<static_cast<unsigned>(ceil_div(cpad, 128)), 128, 0, st>>>(
       cu, cc, nc_dev, ncap, cpad, centre, Bpk, y2max);
   ABC_LAUNCH_CHECK();
-  // rows: features, classes, refinement data
+  // rows: classes and refinement data, then the packed features in class
+  // order (counts[2..4]: rows of class 0, 1, 2 before the refinement)
   const int64_t rpad = ceil_div(rows, kTcM) * kTcM;
-  k_tc_pack_rows<<<static_cast<unsigned>(ceil_div(rpad, 128)), 128, 0, st>>>(
-      up, s, rows, rpad, centre, y2max, ai, Apk, rowc, rinfo, rcls);
+  k_tc_pack_rows<<<static_cast<unsigned>(ceil_div(rows, 128)), 128, 0, st>>>(
+      up, s, rows, centre, y2max, ai, rowc, rinfo, rcls);
+  ABC_LAUNCH_CHECK();
+  const int64_t ncl = ceil_div(rows, kClsTile);
+  k_cls_count<<<static_cast<unsigned>(ncl), 256, 0, st>>>(rcls, rows, cnt3);
+  ABC_LAUNCH_CHECK();
+  k_cls_scan<<<1, 1024, 0, st>>>(cnt3, static_cast<int>(ncl), off3, counts + 2);
+  ABC_LAUNCH_CHECK();
+  k_cls_scatter<<<static_cast<unsigned>(ncl), kClsTile / 4, 0, st>>>(rcls, rows, off3, perm);
+  ABC_LAUNCH_CHECK();
+  k_tc_pack_sorted<<<static_cast<unsigned>(ceil_div(rpad, 128)), 128, 0, st>>>(
+      up, s, rows, rpad, centre, perm, Apk);
   ABC_LAUNCH_CHECK();
   // every row on the tensor cores
   const int nch = tc_chunks(rows, ncap, mult);
@@ -821,11 +942,11 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   k_weights_tc<<<grid, kTcThreads, kTcSmem, st>>>(reinterpret_cast<const uint8_t*>(Apk),
                                                   reinterpret_cast<const uint8_t*>(Bpk), nc_dev,
                                                   rows, part, err, off_dev, rinfo, rcls, cand,
-                                                  ccnt);
+                                                  ccnt, perm);
   ABC_LAUNCH_CHECK();
   if (wt && wt->tc1) ABC_CUDA_TRY(cudaEventRecord(wt->tc1, st));
   k_weights_tc_combine<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(
-      part, kTcGroups * nch, s, rowc, rows, total_p, logW, off_dev, nullptr);
+      part, kTcGroups * nch, s, rowc, rows, total_p, logW, off_dev, rcls);
   ABC_LAUNCH_CHECK();
   // class 1: exact from the listed columns (overflow -> class 2)
   k_tc_refine<<<static_cast<unsigned>(ceil_div(rows, 128)), 128, 0, st>>>(
