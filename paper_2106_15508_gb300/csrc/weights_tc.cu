@@ -531,22 +531,32 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
         for (int h = 0; h < 2; ++h) {
           const int c = g + h * kTcGroups;
           const float (&v)[32] = vv[h];
-          // chunk maximum with three-input max instructions
-          float cm = max3(v[0], v[1], v[2]);
+          // maxima of the four 8-column groups and of the chunk (three-input
+          // max instructions)
+          float gm[4];
 #pragma unroll
-          for (int i = 3; i < 31; i += 2) cm = max3(cm, v[i], v[i + 1]);
-          cm = fmaxf(cm, v[31]);
+          for (int k = 0; k < 4; ++k)
+            gm[k] = max3(max3(v[8 * k], v[8 * k + 1], v[8 * k + 2]),
+                         max3(v[8 * k + 3], v[8 * k + 4], v[8 * k + 5]),
+                         fmaxf(v[8 * k + 6], v[8 * k + 7]));
+          const float cm = fmaxf(max3(gm[0], gm[1], gm[2]), gm[3]);
           if (refine) {
             lb = fmaxf(lb, cm - dl);
             const float thr = lb - dl - kCandMargin;
             if (cm > thr) {
+              // only the groups above the threshold are scanned (candidates
+              // are rare: a few per row among all columns)
               const int col0 = (tb + t) * kTcN + c * 32;
 #pragma unroll
-              for (int i = 0; i < 32; ++i)
-                if (v[i] > thr && col0 + i < nc) {
-                  if (nlist < kCandCap) lst[nlist] = col0 + i;
-                  ++nlist;
-                }
+              for (int k = 0; k < 4; ++k) {
+                if (!(gm[k] > thr)) continue;
+#pragma unroll
+                for (int i = 8 * k; i < 8 * k + 8; ++i)
+                  if (v[i] > thr && col0 + i < nc) {
+                    if (nlist < kCandCap) lst[nlist] = col0 + i;
+                    ++nlist;
+                  }
+              }
             }
           }
           if (!w_exp) continue;
