@@ -31,6 +31,11 @@ METRIC = "sim-days/s; wall-time to ε_final per run, surrogate+batched vs plain"
 UNIT = "sim-days/s"
 MUFU_EX2_PER_CLK_PER_SM = 16  # 32-bit exp2 issue rate of one SM (4 SMSPs x 4 lanes)
 TC_K_USED = 60  # split-bf16 products per pair in the tensor-core weight GEMM (10 features x 6)
+# thread-level instructions per particle-day of k_simulate: ncu smsp__inst_executed.sum x
+# smsp__thread_inst_executed_per_inst_executed.ratio / (particles x days) for one launch of
+# the timed generation of the 262,144-particle, 120-day, P = 1e7 workload
+SIM_THREAD_INST_PER_DAY = 927.0
+SIM_DRAM_BYTES_PER_DAY = 8.73e6 / (262144 * 120)  # same capture, DRAM read + write
 
 
 def _peaks():
@@ -264,18 +269,36 @@ def run_gpu(args):
     tc_exps = sum(s.rows_exp * (s.pairs // N) for s in stats) / args.steps
     kern["k_weights_tc"].update({"exp_pairs": tc_exps, "tflops": tc_flops / (tc_ms / 1e3) / 1e12
                                  if tc_ms > 0 else 0.0})
-    dom = max(kern, key=lambda k: kern[k]["ms"])
-    achieved = kern[dom]["gexp_s"] * 1e9
     exp_src = ("measured ex2.approx.f32 rate (abc_ex2_probe: saturating microbenchmark on "
                "this GPU); %d SMs x %d ex2/clk x %.0f MHz would be %.0f Gexp/s" % (
                    n_sm, MUFU_EX2_PER_CLK_PER_SM, sm_mhz, exp_nominal / 1e9))
-    if dom == "k_weights_tc" and tc_ms > 0:
+    # the simulator: issue-slot roofline at the lane level (SMs x 4 warp
+    # instructions per clock x 32 lanes at the median SM clock under load)
+    sim_step_ms = sim_ms / args.steps
+    sim_days_step = sim_days / args.steps
+    n_sim_launches = sum(s.batches for s in stats) / args.steps
+    clk_mhz = float(clk.get("sm_mhz") or sm_mhz) if isinstance(clk, dict) else sm_mhz
+    lane_peak = n_sm * 4 * 32 * clk_mhz * 1e6
+    sim_rate = SIM_THREAD_INST_PER_DAY * sim_days_step / (sim_step_ms / 1e3) if sim_step_ms > 0 \
+        else 0.0
+    sim_roof = {"bound": "alu", "kernel": "k_simulate", "achieved": sim_rate / 1e12,
+                "peak": lane_peak / 1e12, "unit": "Tinst/s (thread-level)",
+                "frac": sim_rate / lane_peak,
+                "peak_source": "%d SMs x 4 warp-instructions/clk x 32 lanes x %.0f MHz (median "
+                               "SM clock sampled under load)" % (n_sm, clk_mhz),
+                "work": "%.0f thread instructions per particle-day (ncu, timed generation)"
+                        % SIM_THREAD_INST_PER_DAY,
+                "traffic": SIM_DRAM_BYTES_PER_DAY * sim_days_step / n_sim_launches
+                if n_sim_launches else None,
+                "traffic_note": "bytes per launch scaled from a 262,144-particle capture"}
+    tc_roof = None
+    if tc_ms > 0:
         tc_peak = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])) * 1e12
         t_tensor = tc_flops / tc_peak
         t_exp = tc_exps / exp_peak
         if t_tensor >= t_exp:
             a = tc_flops / (tc_ms / 1e3)
-            roofline = {"bound": "tensor", "kernel": dom, "achieved": a / 1e12,
+            tc_roof = {"bound": "tensor", "kernel": "k_weights_tc", "achieved": a / 1e12,
                         "peak": tc_peak / 1e12, "unit": "TFLOP/s", "frac": a / tc_peak,
                         "peak_source": "%s bf16 dense GEMM, sustained (cuBLAS, %s)" % (
                             src, "MEASURED_PEAKS.json" if src == "measured" else "recipe"),
@@ -283,14 +306,20 @@ def run_gpu(args):
                         "exp_frac": tc_exps / (tc_ms / 1e3) / exp_peak, "traffic": None}
         else:
             a = tc_exps / (tc_ms / 1e3)
-            roofline = {"bound": "alu", "kernel": dom, "achieved": a / 1e9,
-                        "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": a / exp_peak,
-                        "peak_source": exp_src, "work": "one exp2 per pair of the kept rows",
-                        "tensor_frac": tc_flops / (tc_ms / 1e3) / tc_peak, "traffic": None}
-    else:
-        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9,
-                    "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": achieved / exp_peak,
-                    "peak_source": exp_src, "work": "one exp2 per pair", "traffic": None}
+            tc_roof = {"bound": "alu", "kernel": "k_weights_tc", "achieved": a / 1e9,
+                       "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": a / exp_peak,
+                       "peak_source": exp_src, "work": "one exp2 per pair of the kept rows",
+                       "tensor_frac": tc_flops / (tc_ms / 1e3) / tc_peak, "traffic": None}
+    fp32_ms = kern["k_weights_fp32"]["ms"]
+    fp32_roof = {"bound": "alu", "kernel": "k_weights_fp32",
+                 "achieved": kern["k_weights_fp32"]["gexp_s"], "peak": exp_peak / 1e9,
+                 "unit": "Gexp/s", "frac": kern["k_weights_fp32"]["gexp_s"] * 1e9 / exp_peak,
+                 "peak_source": exp_src, "work": "one exp2 per pair", "traffic": None}
+    # the roofline line is the dominant kernel's: the largest device time per step
+    cands = [(sim_step_ms, sim_roof), (fp32_ms, fp32_roof)]
+    if tc_roof is not None:
+        cands.append((tc_ms, tc_roof))
+    roofline = max(cands, key=lambda c: c[0])[1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -305,6 +334,8 @@ def run_gpu(args):
                    "theta_star": [round(float(x), 6) for x in theta_star]},
         "roofline": roofline,
         "weight_kernels": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in kern.items()},
+        "rooflines": {"k_simulate": sim_roof, "k_weights_tc": tc_roof,
+                      "k_weights_fp32": fp32_roof if fp32_ms > 0 else None},
         "weight_pass_gexp_s": pairs / (wms / 1e3) / 1e9 if wms > 0 else 0.0,
         "phases_ms": {"weights": wms / args.steps, "simulator": sim_ms / args.steps,
                       "rest": (rank_ms - wms - sim_ms) / args.steps},

@@ -30,10 +30,15 @@ __device__ __forceinline__ float theta_of(const SimParams& p, int d, float u) {
 
 // One SAIRD trajectory.  obs (nullable) is [3][T+1] for the distance; traj
 // (nullable) is [T+1][6][stride] at column col; ard (nullable) receives the
-// simulated A, R, D as [3][T+1] for days 1..T.
+// simulated A, R, D as [3][T+1] for days 1..T.  mask: the warp's lanes that
+// run a trajectory (all of them call this together, for the same T); bq:
+// the warp's queue of kBinvQueue inversion jobs in shared memory.
+constexpr int kBinvQueue = 96;  // three draws per lane per batch
+
 __device__ U128 saird_path(const SimParams& p, const float th[8], uint32_t c0, uint32_t c1,
                            uint32_t tag, const int32_t* obs, int32_t* traj, int64_t stride,
-                           int64_t col, int32_t* ard, int32_t* last = nullptr) {
+                           int64_t col, int32_t* ard, unsigned mask, BinvJob* bq,
+                           int32_t* last = nullptr) {
   const float alpha0 = th[0], alpha = th[1], n = th[2], beta = th[3], gamma = th[4],
               delta = th[5], eta = th[6], kappa = th[7];
   // initial state (Sec. 2.2): Ru = 0, I0 = kappa A0, S = P - (A0 + R0 + D0 + I0)
@@ -80,12 +85,38 @@ __device__ U128 saird_path(const SimParams& p, const float th[8], uint32_t c0, u
     if (p.sampler == ABC_SIM_BINOMIAL) {
       const float t = __fdiv_rn(__fmul_rn(g, __int2float_rn(I)), Pf);
       const float pSI = -dev_expm1(-t);
-      k1 = dev_binomial(S, pSI, unif(b0.x), unif(b0.y));
-      const int32_t LI = dev_binomial_c(I, cI, unif(b0.z), unif(b0.w));
-      k2 = dev_binomial_c(LI, cfI, unif(b1.x), unif(b1.y));
+      // the same five draws as dev_binomial / dev_binomial_c, in two batches
+      // of independent draws (S->I, I exit, A exit; then the two splits);
+      // each batch's inversion loops run together, spread over the warp
+      BinvJob e{0, 0.0f, 0.0f, 0.0f};
+      bool f1, fI, fA;
+      int nq = 0;
+      k1 = binom_front(S, pSI, unif(b0.x), unif(b0.y), f1, e);
+      const int q1 = binv_push(mask, k1 < 0, e, bq, nq);
+      int32_t LI = binom_front_c(I, cI, unif(b0.z), unif(b0.w), fI, e);
+      const int qI = binv_push(mask, LI < 0, e, bq, nq);
+      int32_t LA = binom_front_c(A, cA, unif(b1.z), unif(b1.w), fA, e);
+      const int qA = binv_push(mask, LA < 0, e, bq, nq);
+      if (nq) {  // warp-uniform
+        binv_drain(mask, bq, nq);
+        if (k1 < 0) k1 = f1 ? S - bq[q1].n : bq[q1].n;
+        if (LI < 0) LI = fI ? I - bq[qI].n : bq[qI].n;
+        if (LA < 0) LA = fA ? A - bq[qA].n : bq[qA].n;
+        __syncwarp(mask);  // the queue is refilled below
+      }
+      bool f2, f3;
+      nq = 0;
+      k2 = binom_front_c(LI, cfI, unif(b1.x), unif(b1.y), f2, e);
+      const int q2 = binv_push(mask, k2 < 0, e, bq, nq);
+      k3 = binom_front_c(LA, cfA, unif(b2.x), unif(b2.y), f3, e);
+      const int q3 = binv_push(mask, k3 < 0, e, bq, nq);
+      if (nq) {
+        binv_drain(mask, bq, nq);
+        if (k2 < 0) k2 = f2 ? LI - bq[q2].n : bq[q2].n;
+        if (k3 < 0) k3 = f3 ? LA - bq[q3].n : bq[q3].n;
+        __syncwarp(mask);
+      }
       k5 = LI - k2;
-      const int32_t LA = dev_binomial_c(A, cA, unif(b1.z), unif(b1.w));
-      k3 = dev_binomial_c(LA, cfA, unif(b2.x), unif(b2.y));
       k4 = LA - k3;
     } else {
       // the paper's floor(Normal(h, sqrt h)) flows in h order (Sec. 2.2)
@@ -162,10 +193,16 @@ k_simulate(SimParams p, const int32_t* __restrict__ obs,
   if (c1_dev) c1 = *c1_dev;         // counter word set on the device (graph launches)
   const int nobs = (p.model == ABC_MODEL_SAIRD && obs) ? 3 * (p.T + 1) : 0;
   for (int i = threadIdx.x; i < nobs; i += blockDim.x) s_obs[i] = obs[i];
+  // the warps' inversion queues follow the observations (16-byte aligned)
+  BinvJob* bq = reinterpret_cast<BinvJob*>(s_obs + ((nobs + 3) & ~3)) +
+                (threadIdx.x >> 5) * kBinvQueue;
   __syncthreads();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool live = i < n && !(skip && skip[i]);
+  // lanes that simulate (the block size is a multiple of 32)
+  const unsigned mask = __ballot_sync(0xffffffffu, live);
   if (i >= n) return;
-  if (skip && skip[i]) {
+  if (!live) {
     dist[i] = __longlong_as_double(0x7ff0000000000000ll);
     return;
   }
@@ -182,7 +219,8 @@ k_simulate(SimParams p, const int32_t* __restrict__ obs,
     }
   } else {
     int32_t last[3];
-    const U128 a = saird_path(p, th, c0, c1, tag, nobs ? s_obs : nullptr, traj, n, i, nullptr, last);
+    const U128 a = saird_path(p, th, c0, c1, tag, nobs ? s_obs : nullptr, traj, n, i, nullptr,
+                              mask, bq, last);
     dist[i] = __dsqrt_rn(u128_to_double(a.hi, a.lo));
     if (ard_last) {
       ard_last[0 * n + i] = last[0];
@@ -206,6 +244,7 @@ __global__ void k_prior(SimParams p, int64_t n, float* __restrict__ u) {
 __global__ void k_synth_obs(SimParams p, float4 lo0, float4 lo1, float4 hi0, float4 hi1,
                             int32_t* __restrict__ obs, float* __restrict__ theta_star,
                             int32_t* __restrict__ attempts) {
+  __shared__ BinvJob bq[kBinvQueue];
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const float lo[8] = {lo0.x, lo0.y, lo0.z, lo0.w, lo1.x, lo1.y, lo1.z, lo1.w};
   const float hi[8] = {hi0.x, hi0.y, hi0.z, hi0.w, hi1.x, hi1.y, hi1.z, hi1.w};
@@ -221,7 +260,8 @@ __global__ void k_synth_obs(SimParams p, float4 lo0, float4 lo1, float4 hi0, flo
     obs[0 * (T + 1)] = p.A0;
     obs[1 * (T + 1)] = p.R0;
     obs[2 * (T + 1)] = p.D0;
-    saird_path(p, th, 0u, static_cast<uint32_t>(a), ABC_TAG_OBS, nullptr, nullptr, 0, 0, obs);
+    saird_path(p, th, 0u, static_cast<uint32_t>(a), ABC_TAG_OBS, nullptr, nullptr, 0, 0, obs, 1u,
+               bq);
     for (int d = 0; d < 8; ++d) theta_star[d] = th[d];
     if (obs[0 * (T + 1) + T] > p.A0) break;
   }
@@ -248,7 +288,9 @@ int launch_simulate(const SimParams& p, const int32_t* obs, const float* u, int6
   // 64 registers per thread (__launch_bounds__(256, 4)): up to 8 CTAs of
   // 128 threads per SM; blocks of at most 256 threads
   if (threads != 64 && threads != 128 && threads != 256) return ABC_E_INVAL;
-  const size_t smem = (p.model == ABC_MODEL_SAIRD && obs) ? sizeof(int32_t) * 3 * (p.T + 1) : 0;
+  const size_t nobs = (p.model == ABC_MODEL_SAIRD && obs) ? 3 * static_cast<size_t>(p.T + 1) : 0;
+  const size_t smem = sizeof(int32_t) * ((nobs + 3) & ~static_cast<size_t>(3)) +
+                      sizeof(BinvJob) * kBinvQueue * static_cast<size_t>(threads / 32);
   k_simulate<<<static_cast<unsigned>(ceil_div(n, threads)), threads, smem, st>>>(
       p, obs, u, n, c0_idx, c1, tag, skip, dist, traj, c1_dev, off_dev, ard_last);
   ABC_LAUNCH_CHECK();
