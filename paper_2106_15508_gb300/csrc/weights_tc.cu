@@ -604,14 +604,16 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
 }
 
 // class-0 rows: log W from the partials (k_tc_refine and the FP32 kernel write
-// the other rows)
+// the other rows).  Thread p takes sorted position p < n0 (the class-0 rows
+// come first), so the fp64 work runs in converged warps.
 __global__ void k_weights_tc_combine(const float2* __restrict__ part, int nchunks,
                                      const float* __restrict__ s, const double* __restrict__ rowc,
                                      int64_t rows, const uint64_t* __restrict__ total_p,
                                      double* __restrict__ logW, const int* __restrict__ off_dev,
-                                     const uint8_t* __restrict__ rcls) {
-  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= rows || (off_dev && *off_dev) || rcls[j] != 0) return;
+                                     const int* __restrict__ perm, const int* __restrict__ n0_p) {
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= *n0_p || (off_dev && *off_dev)) return;
+  const int64_t j = perm[p];
   const double sj = static_cast<double>(fmaxf(s[j], kSMinTc));
   double M = -INFINITY;
   for (int c = 0; c < nchunks; ++c)
@@ -682,7 +684,8 @@ k_tc_probe(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
 // ---- exact recomputation of class-1 rows -------------------------------------
 // One thread per row: the listed columns of every partial slot (at most
 // kCandCap each; more sends the row to the FP32 kernel as class 2), exponents
-// from direct differences as in the FP32 kernel, maximum and fp64 sum.
+// from direct differences as in the FP32 kernel, maximum, fp32 exponentials
+// and an fp64 sum.
 // Unlisted columns lie at least kCandMargin bits under the maximum: together
 // at most nc 2^-45 of the row sum.
 __global__ void k_tc_refine(const float* __restrict__ up, const float* __restrict__ s,
@@ -723,7 +726,9 @@ __global__ void k_tc_refine(const float* __restrict__ up, const float* __restric
   for (int sl = 0; sl < nslots; ++sl) {
     const int n = ccnt[static_cast<int64_t>(sl) * rows + j];
     const int* l = cand + (static_cast<int64_t>(sl) * rows + j) * kCandCap;
-    for (int i = 0; i < n; ++i) S += exp2(static_cast<double>(expo(l[i]) - m));
+    // fp32 exponentials (terms in (0, 1], ~2 ulp each, as in the FP32
+    // kernel) summed in fp64: GB300's fp64 exponentials would bound this pass
+    for (int i = 0; i < n; ++i) S += static_cast<double>(exp2f(expo(l[i]) - m));
   }
   if (!(S > 0.0)) {  // nothing listed (cannot happen: the maximum is listed)
     rcls[j] = 2;
@@ -956,7 +961,7 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   ABC_LAUNCH_CHECK();
   if (wt && wt->tc1) ABC_CUDA_TRY(cudaEventRecord(wt->tc1, st));
   k_weights_tc_combine<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(
-      part, kTcGroups * nch, s, rowc, rows, total_p, logW, off_dev, rcls);
+      part, kTcGroups * nch, s, rowc, rows, total_p, logW, off_dev, perm, counts + 2);
   ABC_LAUNCH_CHECK();
   // class 1: exact from the listed columns (overflow -> class 2)
   k_tc_refine<<<static_cast<unsigned>(ceil_div(rows, 128)), 128, 0, st>>>(
