@@ -304,6 +304,16 @@ ABC_API int abc_predict(const abc_config* cfg, const float* u, const double* W, 
  * Synchronises the stream. */
 ABC_API int abc_ex2_probe(double* ex2_per_second, void* stream);
 
+/* Stable LSD radix sort (no counterpart in the paper; the weight pass uses it
+ * to put its rows and columns in spatial order): keys_out / vals_out = the n
+ * pairs (keys[i], vals ? vals[i] : i) ordered by the low `bits` bits of the
+ * key (1 <= bits <= 32), equal keys in input order.  keys, vals, keys_out,
+ * vals_out: device arrays of n uint32 / int32 (the outputs must not alias the
+ * inputs); 0 <= n <= 2^30.  Scratch is allocated on the stream and freed
+ * after the sort (stream-ordered); ABC_E_NOMEM if that fails. */
+ABC_API int abc_radix_sort(const uint32_t* keys, const int32_t* vals, int64_t n, int32_t bits,
+                           uint32_t* keys_out, int32_t* vals_out, void* stream);
+
 /* A10 normalisation (fp64): W_j = exp(logW_j - max) / sum, *ess = 1 / sum W^2;
  * all -inf gives W = 1/n, ess = n.  logW: device double[n]; W: device
  * double[n]; ess: device double[1]. */

@@ -353,6 +353,25 @@ ABC_API int abc_predict(const abc_config* cfg, const float* u, const double* W, 
                         scratch_bytes, as_stream(stream));
 }
 
+ABC_API int abc_radix_sort(const uint32_t* keys, const int32_t* vals, int64_t n, int32_t bits,
+                           uint32_t* keys_out, int32_t* vals_out, void* stream) {
+  if (n < 0 || n > (int64_t(1) << 30) || bits < 1 || bits > 32) return ABC_E_INVAL;
+  if (n == 0) return ABC_OK;
+  if (!keys || !keys_out || !vals_out || keys == keys_out ||
+      (vals && reinterpret_cast<const void*>(vals) == reinterpret_cast<const void*>(vals_out)))
+    return ABC_E_INVAL;
+  cudaStream_t st = as_stream(stream);
+  const size_t sb = radix_sort_scratch_bytes(n);
+  void* buf = nullptr;
+  if (cudaMallocAsync(&buf, sb, st) != cudaSuccess) {
+    cudaGetLastError();
+    return ABC_E_NOMEM;
+  }
+  const int rc = launch_radix_sort(keys, vals, keys_out, vals_out, n, nullptr, bits, buf, sb, st);
+  cudaFreeAsync(buf, st);
+  return rc;
+}
+
 ABC_API int abc_ex2_probe(double* ex2_per_second, void* stream) {
   if (!ex2_per_second) return ABC_E_INVAL;
   return ex2_probe(ex2_per_second, as_stream(stream));

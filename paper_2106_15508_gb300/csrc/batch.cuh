@@ -61,6 +61,10 @@ int launch_select(const double*, int64_t, int64_t, double*, void*, size_t, cudaS
 int launch_resample_prefix(const double*, const double*, int64_t, const double*, int, uint32_t*,
                            uint64_t*, void*, size_t, cudaStream_t);
 bool beta_rule_ok(const BetaRule&);
+size_t radix_sort_scratch_bytes(int64_t cap);
+int launch_radix_sort(const uint32_t* kin, const int32_t* vin, uint32_t* kout, int32_t* vout,
+                      int64_t cap, const int* n_dev, int bits, void* scratch, size_t bytes,
+                      cudaStream_t st);
 int launch_propose(const SimParams&, const float*, int64_t, const uint64_t*, const BetaRule&,
                    const double*, const double*, int64_t, const uint32_t*, uint32_t, int, float*,
                    float*, int32_t*, int32_t*, uint8_t*, cudaStream_t,

@@ -38,6 +38,7 @@
 
 #include <algorithm>
 
+#include "batch.cuh"
 #include "common.cuh"
 #include "tcgen05.cuh"
 
@@ -56,7 +57,12 @@ constexpr int kTcProducer = kTcEpiWarps;            // bulk-copy producer warp
 constexpr int kTcIssuer = kTcEpiWarps + 1;          // MMA issuer warp, owns the TMEM
 constexpr int kTcThreads = 32 * (kTcEpiWarps + 2);
 constexpr int kProbeThreads = 192;                  // probe: 4 epilogue warps, producer, issuer
-constexpr size_t kTcSmem = 1024 + kATile + kTcStages * kBTile + 256;
+// column-tile mask of a CTA's chunk (tile pruning of class-1 row tiles):
+// up to 32 * kMaskWords column tiles per chunk, else no pruning
+constexpr int kMaskWords = 2048;
+constexpr size_t kTcSmem = 1024 + kATile + kTcStages * kBTile + 256 + 4 * kMaskWords + 16;
+constexpr int kRowBox = 18;  // per row tile: lo[8], hi[8], max R^2, prunable flag
+constexpr int kColBox = 16;  // per column tile: lo[8], hi[8]
 constexpr float kSMinTc = 1e-30f;
 constexpr float kPadLogit = -1.0e30f;
 constexpr int kCandCap = 32;          // listed columns per (row, partial slot)
@@ -139,11 +145,16 @@ __device__ __forceinline__ void store_packed_row(__nv_bfloat16* tile, int r, con
 //            maximum in the accumulator frame, delta_j));
 //   class 2: delta_j not finite: the FP32 kernel recomputes the row.
 // The packed operand is written afterwards by k_tc_pack_sorted, in class order.
+//
+// For class-1 rows also the radius R_j beyond which no column can be listed
+// (rrad2 = R_j^2; +inf without an ancestor), and the sort key
+// class << 16 | morton16(u'_j) (class-1 rows in spatial order).
 __global__ void k_tc_pack_rows(const float* __restrict__ up, const float* __restrict__ s,
                                int64_t rows, const float* __restrict__ centre,
                                const unsigned* __restrict__ y2max, AncInfo ai,
                                double* __restrict__ rowc, float2* __restrict__ rinfo,
-                               uint8_t* __restrict__ rcls) {
+                               uint8_t* __restrict__ rcls, float* __restrict__ rrad2,
+                               const unsigned* __restrict__ cbox, uint32_t* __restrict__ rkey) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= rows) return;
   const float sj = fmaxf(s[j], kSMinTc);
@@ -167,21 +178,221 @@ __global__ void k_tc_pack_rows(const float* __restrict__ up, const float* __rest
   const float X = sqrtf(xxf);
   float Y = sqrtf(__uint_as_float(*y2max));
   float lb = -INFINITY;
+  double mlb = 0.0, Ldd_ca = 0.0;
   if (a >= 0 && ai.q_prev[a] > 0u) {
     const double ca = log2(static_cast<double>(ai.q_prev[a])) - 32.0;
     // 1.001: margin for the fp32 rounding of this estimate
     Y = fminf(Y, 1.001f * (X + sqrtf(dd + (60.0f - static_cast<float>(ca)) / L)));
     // the ancestor's exponent in the accumulator frame (e - rowc), less a
     // rounding margin: a lower bound of the row maximum there
-    const double ea =
-        ca - static_cast<double>(L) * static_cast<double>(dd) + static_cast<double>(L) * xx;
-    lb = static_cast<float>(ea - (1.0 + 1e-3 * fabs(ea) + 1e-6 * static_cast<double>(L) * xx));
+    const double Ldd = static_cast<double>(L) * static_cast<double>(dd);
+    const double Lxx = static_cast<double>(L) * xx;
+    const double ea = ca - Ldd + Lxx;
+    // margin: 1 for the log2, 2^-19 of the two products for the fp32 inputs
+    // (dd, x and L carry a few 2^-24 relative each)
+    mlb = 1.0 + 0x1p-19 * (Ldd + Lxx);
+    lb = static_cast<float>(ea - mlb);
+    Ldd_ca = Ldd - ca;
   }
   const float mag = L * (2.0f * X * Y + Y * Y) + 32.0f;
   const float delta = 0x1p-24f * 64.0f * mag;
   const float B = 0x1p-24f * (64.0f * mag + 160.0f);
   rinfo[j] = make_float2(lb, delta);
-  rcls[j] = B <= kTcBoundMax ? 0 : (isfinite(delta) && delta < 1e30f ? 1 : 2);
+  const uint8_t cls = B <= kTcBoundMax ? 0 : (isfinite(delta) && delta < 1e30f ? 1 : 2);
+  rcls[j] = cls;
+  // Candidate radius.  The epilogue lists column k only if its accumulator
+  // value exceeds lb - delta - kCandMargin (lb only rises), and that value is
+  // at most the exact one plus the pair's error 2^-18 (L (2 X |y_k| + |y_k|^2)
+  // + 32) with |y_k| <= X + d.  The exact exponent is c_k - L d^2 <= -L d^2
+  // (c_k <= 0), d = |u'_j - u_k|.  Listing therefore needs
+  //   L (1 - e) d^2 - 4 e L X d - C < 0,  e = 2^-18,
+  //   C = L dd - c_a + mlb + delta + kCandMargin + 3 e L X^2 + 32 e,
+  // i.e. d < (4 e L X + sqrt((4 e L X)^2 + 4 L (1 - e) C)) / (2 L (1 - e)).
+  float r2 = __int_as_float(0x7f800000);
+  if (cls == 1 && lb > -__int_as_float(0x7f800000)) {
+    const double e = 0x1p-18, Ld = static_cast<double>(L), Xd = static_cast<double>(X);
+    const double C = Ldd_ca + mlb + static_cast<double>(delta) + kCandMargin +
+                     3.0 * e * Ld * Xd * Xd + 32.0 * e;
+    const double bq = 4.0 * e * Ld * Xd;
+    const double dmax = (bq + sqrt(bq * bq + 4.0 * Ld * (1.0 - e) * C)) / (2.0 * Ld * (1.0 - e));
+    r2 = static_cast<float>(1.01 * dmax * dmax + 1e-12);
+  }
+  rrad2[j] = r2;
+  // sort key: class, then (class 1) the 2-bit-per-coordinate Morton code of
+  // u'_j in the columns' box
+  uint32_t key = static_cast<uint32_t>(cls) << 16;
+  if (cls == 1) {
+    uint32_t mc = 0u;
+    int q[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const float lo = __uint_as_float(cbox[d]), hi = __uint_as_float(cbox[8 + d]);
+      const float w = hi - lo;
+      const float t = w > 0.0f ? (up[static_cast<int64_t>(d) * rows + j] - lo) / w : 0.0f;
+      q[d] = min(max(static_cast<int>(t * 4.0f), 0), 3);
+    }
+#pragma unroll
+    for (int b = 1; b >= 0; --b)
+#pragma unroll
+      for (int d = 0; d < 8; ++d) mc = (mc << 1) | static_cast<uint32_t>((q[d] >> b) & 1);
+    key |= mc;
+  }
+  rkey[j] = key;
+}
+
+// ---- columns in spatial order, tile boxes ------------------------------------------
+// The box of the columns (min and max per coordinate; unit-cube coordinates
+// are non-negative, so their bit patterns order like their values), then a
+// 2-bit-per-coordinate Morton key per column, the sorted column arrays, and
+// per 256-column tile the box of its columns.  Rows get the same key in
+// k_tc_pack_rows; sorted rows and columns make the boxes of class-1 row tiles
+// and of column tiles small, and k_weights_tc skips the column tiles that
+// lie beyond every candidate radius of a row tile.
+__global__ void k_col_box(const float* __restrict__ cu, const int* __restrict__ nc_p,
+                          int64_t ncap, unsigned* __restrict__ box) {
+  const int64_t nc = *nc_p;
+  unsigned lo[8], hi[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    lo[d] = 0x7f800000u;
+    hi[d] = 0u;
+  }
+  for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < nc;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x)
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const unsigned v = __float_as_uint(fmaxf(cu[static_cast<int64_t>(d) * ncap + k], 0.0f));
+      lo[d] = min(lo[d], v);
+      hi[d] = max(hi[d], v);
+    }
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+      hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&box[d], lo[d]);
+      atomicMax(&box[8 + d], hi[d]);
+    }
+  }
+}
+
+__global__ void k_col_keys(const float* __restrict__ cu, const int* __restrict__ nc_p,
+                           int64_t ncap, const unsigned* __restrict__ box,
+                           uint32_t* __restrict__ key) {
+  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= *nc_p) return;
+  int q[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const float lo = __uint_as_float(box[d]), hi = __uint_as_float(box[8 + d]);
+    const float w = hi - lo;
+    const float t = w > 0.0f ? (cu[static_cast<int64_t>(d) * ncap + k] - lo) / w : 0.0f;
+    q[d] = min(max(static_cast<int>(t * 4.0f), 0), 3);
+  }
+  uint32_t mc = 0u;
+#pragma unroll
+  for (int b = 1; b >= 0; --b)
+#pragma unroll
+    for (int d = 0; d < 8; ++d) mc = (mc << 1) | static_cast<uint32_t>((q[d] >> b) & 1);
+  key[k] = mc;
+}
+
+// cu_s[d][p] = cu[d][cperm[p]], cc_s[p] = cc[cperm[p]] for p < nc
+__global__ void k_col_gather(const float* __restrict__ cu, const float* __restrict__ cc,
+                             const int* __restrict__ cperm, const int* __restrict__ nc_p,
+                             int64_t ncap, float* __restrict__ cu_s, float* __restrict__ cc_s) {
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= *nc_p) return;
+  const int64_t k = cperm[p];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) cu_s[static_cast<int64_t>(d) * ncap + p] = cu[static_cast<int64_t>(d) * ncap + k];
+  cc_s[p] = cc[k];
+}
+
+// per column tile of kTcN sorted columns: lo[8], hi[8] (an empty tile gets
+// lo = +inf, hi = -inf, which no box test passes)
+__global__ void __launch_bounds__(kTcN)
+k_col_boxes(const float* __restrict__ cu_s, const int* __restrict__ nc_p, int64_t ncap,
+            float* __restrict__ cbox) {
+  __shared__ float smin[8][kTcN / 32], smax[8][kTcN / 32];
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * kTcN + threadIdx.x;
+  const bool ok = p < *nc_p;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    float lo = ok ? cu_s[static_cast<int64_t>(d) * ncap + p] : __int_as_float(0x7f800000);
+    float hi = ok ? lo : -__int_as_float(0x7f800000);
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      smin[d][w] = lo;
+      smax[d][w] = hi;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const int d = threadIdx.x;
+    float lo = smin[d][0], hi = smax[d][0];
+    for (int i = 1; i < kTcN / 32; ++i) {
+      lo = fminf(lo, smin[d][i]);
+      hi = fmaxf(hi, smax[d][i]);
+    }
+    cbox[static_cast<int64_t>(blockIdx.x) * kColBox + d] = lo;
+    cbox[static_cast<int64_t>(blockIdx.x) * kColBox + 8 + d] = hi;
+  }
+}
+
+// per row tile of kTcM sorted positions: lo[8], hi[8] of u', the largest
+// candidate radius^2, and a flag: 1 when every row of the tile is class 1 or
+// 2 (the tile starts at or after the class-0 rows), so that its column
+// tiles may be skipped
+__global__ void __launch_bounds__(kTcM)
+k_row_boxes(const float* __restrict__ up, int64_t rows, const int* __restrict__ perm,
+            const int* __restrict__ n0_p, const float* __restrict__ rrad2,
+            float* __restrict__ rbox) {
+  __shared__ float smin[8][kTcM / 32], smax[8][kTcM / 32], sr[kTcM / 32];
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * kTcM + threadIdx.x;
+  const bool ok = p < rows;
+  const int64_t j = ok ? perm[p] : 0;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float r = ok ? rrad2[j] : 0.0f;
+  for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+  if (lane == 0) sr[w] = r;
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    float lo = ok ? up[static_cast<int64_t>(d) * rows + j] : __int_as_float(0x7f800000);
+    float hi = ok ? lo : -__int_as_float(0x7f800000);
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+      smin[d][w] = lo;
+      smax[d][w] = hi;
+    }
+  }
+  __syncthreads();
+  float* rb = rbox + static_cast<int64_t>(blockIdx.x) * kRowBox;
+  if (threadIdx.x < 8) {
+    const int d = threadIdx.x;
+    float lo = smin[d][0], hi = smax[d][0];
+    for (int i = 1; i < kTcM / 32; ++i) {
+      lo = fminf(lo, smin[d][i]);
+      hi = fmaxf(hi, smax[d][i]);
+    }
+    rb[d] = lo;
+    rb[8 + d] = hi;
+  }
+  if (threadIdx.x == 0) {
+    float rm = sr[0];
+    for (int i = 1; i < kTcM / 32; ++i) rm = fmaxf(rm, sr[i]);
+    rb[16] = rm;
+    rb[17] = static_cast<int64_t>(blockIdx.x) * kTcM >= *n0_p ? 1.0f : 0.0f;
+  }
 }
 
 // ---- rows sorted by class ------------------------------------------------------
@@ -238,26 +449,6 @@ __global__ void k_cls_scan(const int* __restrict__ cnt3, int ntiles, int* __rest
   }
 }
 
-__global__ void k_cls_scatter(const uint8_t* __restrict__ rcls, int64_t rows,
-                              const int* __restrict__ off3, int* __restrict__ perm) {
-  __shared__ int sm[32];
-  const int64_t base = static_cast<int64_t>(blockIdx.x) * kClsTile + 4 * threadIdx.x;
-  int cl[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) cl[e] = base + e < rows ? rcls[base + e] : 3;
-#pragma unroll 1
-  for (int k = 0; k < 3; ++k) {
-    int c = 0;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) c += cl[e] == k;
-    const int inc = block_incl_scan<int>(c, sm);
-    int p = off3[3 * blockIdx.x + k] + inc - c;
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-      if (cl[e] == k) perm[p++] = static_cast<int>(base + e);
-  }
-}
-
 // packed row features [2 L x (8), -L, 1] at sorted position p (zeros for the
 // padding positions p >= rows)
 __global__ void k_tc_pack_sorted(const float* __restrict__ up, const float* __restrict__ s,
@@ -303,13 +494,15 @@ __global__ void k_col_sum(const float* __restrict__ cu, const int* __restrict__ 
 }
 
 // centre[d] = mean over the nc columns (1/2 when there are none); clears the
-// radius word that the column packing raises
+// radius word that the column packing raises and the column box
 __global__ void k_col_centre(const double* __restrict__ part, int nparts,
                              const int* __restrict__ nc_p, float* __restrict__ centre,
-                             unsigned* __restrict__ y2max) {
+                             unsigned* __restrict__ y2max, unsigned* __restrict__ box) {
   const int d = threadIdx.x;
   if (d == 0) *y2max = 0u;
   if (d >= 8) return;
+  box[d] = 0x7f800000u;  // min of the column box, filled by k_col_box
+  box[8 + d] = 0u;       // max
   double acc = 0.0;
   for (int b = 0; b < nparts; ++b) acc += part[b * 8 + d];
   const int nc = *nc_p;
@@ -364,6 +557,8 @@ struct TcSmem {
   uint64_t* tempty;
   uint64_t* afull;
   uint32_t* tmem_slot;
+  uint32_t* mask;  // kMaskWords words
+  int* ntiles;     // set bits of mask
 };
 
 __device__ __forceinline__ TcSmem tc_carve(uint8_t* raw) {
@@ -378,6 +573,8 @@ __device__ __forceinline__ TcSmem tc_carve(uint8_t* raw) {
   m.tempty = bars + 2 * kTcStages + 2;
   m.afull = bars + 2 * kTcStages + 4;
   m.tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kTcStages + 5);
+  m.mask = reinterpret_cast<uint32_t*>(base + kATile + kTcStages * kBTile + 256);
+  m.ntiles = reinterpret_cast<int*>(m.mask + kMaskWords);
   return m;
 }
 
@@ -386,7 +583,8 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
              const int* __restrict__ nc_p, int64_t rows,
              float2* __restrict__ part, unsigned* err, const int* __restrict__ off_dev,
              const float2* __restrict__ rinfo, const uint8_t* __restrict__ rcls,
-             int* __restrict__ cand, int* __restrict__ ccnt, const int* __restrict__ perm) {
+             int* __restrict__ cand, int* __restrict__ ccnt, const int* __restrict__ perm,
+             const float* __restrict__ rbox, const float* __restrict__ cbox) {
   extern __shared__ uint8_t tc_smem_raw[];
   if (off_dev && *off_dev) return;  // run finished or its generation stopped (block-uniform)
   const int64_t nrows = rows;
@@ -409,7 +607,62 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     }
     return;
   }
-  const int ntiles = te - tb;
+  // the column tiles this CTA visits: all of [tb, te), or, for a row tile of
+  // class-1 rows only, those whose box lies within the tile's largest
+  // candidate radius of the row box (the others cannot hold a candidate)
+  const int span = te - tb;
+  const bool use_mask = rbox && span <= 32 * kMaskWords;
+  const float* rb = rbox ? rbox + static_cast<int64_t>(blockIdx.x) * kRowBox : nullptr;
+  const bool prune = use_mask && rb[17] != 0.0f;
+  if (threadIdx.x == 0) *sm.ntiles = 0;
+  __syncthreads();
+  if (use_mask) {
+    for (int i0 = warp * 32; i0 < span; i0 += kTcThreads) {
+      const int i = i0 + lane;
+      bool keep = i < span;
+      if (keep && prune) {
+        const float* cb = cbox + static_cast<int64_t>(tb + i) * kColBox;
+        float d2 = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+          const float gap = fmaxf(fmaxf(cb[d] - rb[8 + d], rb[d] - cb[8 + d]), 0.0f);
+          d2 = __fmaf_rn(gap, gap, d2);
+        }
+        // rounding margin on the box distance; empty boxes give +inf
+        keep = d2 * (1.0f - 0x1p-16f) <= rb[16];
+      }
+      const unsigned bits = __ballot_sync(0xffffffffu, keep);
+      if (lane == 0) {
+        sm.mask[i0 >> 5] = bits;
+        atomicAdd(sm.ntiles, __popc(bits));
+      }
+    }
+  }
+  __syncthreads();
+  const int ntiles = use_mask ? *sm.ntiles : span;
+  // the t-th visited column tile
+  struct TileIter {
+    const uint32_t* m;
+    int tb, span, w;
+    uint32_t bits;
+    bool dense;
+    int t;
+    __device__ int next() {
+      if (dense) return t < span ? tb + t++ : -1;
+      while (bits == 0u) {
+        if (++w >= (span + 31) >> 5) return -1;
+        bits = m[w];
+      }
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1u;
+      return tb + w * 32 + b;
+    }
+  };
+  auto tiles = [&]() {
+    TileIter it{sm.mask, tb, span, 0, use_mask ? sm.mask[0] : 0u, !use_mask, 0};
+    if (use_mask && span <= 0) it.bits = 0u;
+    return it;
+  };
   if (threadIdx.x == 0) {
     for (int i = 0; i < kTcStages; ++i) {
       mbar_init(&sm.full[i], 1);
@@ -437,12 +690,14 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
       mbar_expect_tx(sm.afull, kATile);
       bulk_g2s(sm.a, Apk + static_cast<size_t>(blockIdx.x) * kATile, kATile, sm.afull);
       int issued = 0;
+      TileIter it = tiles();
       for (int t = 0; t < ntiles; ++t) {
+        const int tile = it.next();
         const int st = t % kTcStages;
         const uint32_t ph = static_cast<uint32_t>(t / kTcStages) & 1u;
         if (!mbar_wait(&sm.empty[st], ph ^ 1u, err, 1u)) break;
         mbar_expect_tx(&sm.full[st], kBTile);
-        bulk_g2s(sm.b + st * kBTile, Bpk + static_cast<size_t>(tb + t) * kBTile, kBTile,
+        bulk_g2s(sm.b + st * kBTile, Bpk + static_cast<size_t>(tile) * kBTile, kBTile,
                  &sm.full[st]);
         issued = t + 1;
       }
@@ -512,7 +767,9 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     }
     int* lst = cand + (slot * rows + (refine ? row : 0)) * kCandCap;
     int nlist = 0;
+    TileIter it = tiles();
     for (int t = 0; t < ntiles; ++t) {
+      const int tile = it.next();
       const int b = t & 1;
       const uint32_t tph = static_cast<uint32_t>(t >> 1) & 1u;
       // warp-uniform: tcgen05.ld below is warp-collective
@@ -546,7 +803,7 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
             if (cm > thr) {
               // only the groups above the threshold are scanned (candidates
               // are rare: a few per row among all columns)
-              const int col0 = (tb + t) * kTcN + c * 32;
+              const int col0 = tile * kTcN + c * 32;
 #pragma unroll
               for (int k = 0; k < 4; ++k) {
                 if (!(gm[k] > thr)) continue;
@@ -828,7 +1085,8 @@ static int tc_chunks(int64_t rows, int64_t ncap, int mult) {
 
 struct TcLayout {
   size_t apk, bpk, rowc, part, err, rinfo, rcls, cand, ccnt, fp, cnt, off, counts, idx, u_f, s_f,
-      lw_f, ctr, cnt3, off3, perm, total;
+      lw_f, ctr, cnt3, off3, perm, rrad2, rkey, rkey_s, ckey, ckey_s, cperm, cu_s, cc_s, cbox,
+      rbox, box, sort, total;
 };
 
 static TcLayout tc_layout(int64_t rows, int64_t ncap, int mult) {
@@ -865,6 +1123,19 @@ static TcLayout tc_layout(int64_t rows, int64_t ncap, int mult) {
   take(l.cnt3, 3 * 4 * ncls_tiles);
   take(l.off3, 3 * 4 * ncls_tiles);
   take(l.perm, 4 * R);
+  const size_t C = static_cast<size_t>(std::max<int64_t>(ncap, 1));
+  take(l.rrad2, 4 * R);
+  take(l.rkey, 4 * R);
+  take(l.rkey_s, 4 * R);
+  take(l.ckey, 4 * C);
+  take(l.ckey_s, 4 * C);
+  take(l.cperm, 4 * C);
+  take(l.cu_s, 32 * C);
+  take(l.cc_s, 4 * C);
+  take(l.cbox, sizeof(float) * kColBox * static_cast<size_t>(cpad / kTcN));
+  take(l.rbox, sizeof(float) * kRowBox * static_cast<size_t>(rpad / kTcM));
+  take(l.box, 16 * sizeof(unsigned));
+  take(l.sort, radix_sort_scratch_bytes(std::max<int64_t>(rows, ncap)));
   l.total = o;
   return l;
 }
@@ -923,32 +1194,63 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   auto* cnt3 = reinterpret_cast<int*>(b + l.cnt3);
   auto* off3 = reinterpret_cast<int*>(b + l.off3);
   auto* perm = reinterpret_cast<int*>(b + l.perm);
+  auto* rrad2 = reinterpret_cast<float*>(b + l.rrad2);
+  auto* rkey = reinterpret_cast<uint32_t*>(b + l.rkey);
+  auto* rkey_s = reinterpret_cast<uint32_t*>(b + l.rkey_s);
+  auto* ckey = reinterpret_cast<uint32_t*>(b + l.ckey);
+  auto* ckey_s = reinterpret_cast<uint32_t*>(b + l.ckey_s);
+  auto* cperm = reinterpret_cast<int*>(b + l.cperm);
+  auto* cu_s = reinterpret_cast<float*>(b + l.cu_s);
+  auto* cc_s = reinterpret_cast<float*>(b + l.cc_s);
+  auto* cbox = reinterpret_cast<float*>(b + l.cbox);
+  auto* rbox = reinterpret_cast<float*>(b + l.rbox);
+  auto* box = reinterpret_cast<unsigned*>(b + l.box);
+  void* sort_scr = b + l.sort;
+  const size_t sort_bytes = l.total - l.sort;
   if (err_dev) *err_dev = err;
   ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
-  // columns: centre, radius, packed once (centred)
+  // columns: centre and box, spatial order, packed once (centred), tile boxes
   const int64_t cpad = ceil_div(std::max<int64_t>(ncap, 1), kTcN) * kTcN;
   k_col_sum<<<kCtrBlocks, 256, 0, st>>>(cu, nc_dev, ncap, cpart);
   ABC_LAUNCH_CHECK();
-  k_col_centre<<<1, 32, 0, st>>>(cpart, kCtrBlocks, nc_dev, centre, y2max);
+  k_col_centre<<<1, 32, 0, st>>>(cpart, kCtrBlocks, nc_dev, centre, y2max, box);
+  ABC_LAUNCH_CHECK();
+  k_col_box<<<kCtrBlocks, 256, 0, st>>>(cu, nc_dev, ncap, box);
+  ABC_LAUNCH_CHECK();
+  k_col_keys<<<static_cast<unsigned>(ceil_div(ncap, 256)), 256, 0, st>>>(cu, nc_dev, ncap, box,
+                                                                         ckey);
+  ABC_LAUNCH_CHECK();
+  int rc = launch_radix_sort(ckey, nullptr, ckey_s, cperm, ncap, nc_dev, 16, sort_scr, sort_bytes,
+                             st);
+  if (rc) return rc;
+  k_col_gather<<<static_cast<unsigned>(ceil_div(ncap, 256)), 256, 0, st>>>(cu, cc, cperm, nc_dev,
+                                                                           ncap, cu_s, cc_s);
   ABC_LAUNCH_CHECK();
   k_tc_pack_cols<<<static_cast<unsigned>(ceil_div(cpad, 128)), 128, 0, st>>>(
-      cu, cc, nc_dev, ncap, cpad, centre, Bpk, y2max);
+      cu_s, cc_s, nc_dev, ncap, cpad, centre, Bpk, y2max);
   ABC_LAUNCH_CHECK();
-  // rows: classes and refinement data, then the packed features in class
-  // order (counts[2..4]: rows of class 0, 1, 2 before the refinement)
+  k_col_boxes<<<static_cast<unsigned>(cpad / kTcN), kTcN, 0, st>>>(cu_s, nc_dev, ncap, cbox);
+  ABC_LAUNCH_CHECK();
+  // rows: classes, refinement data and sort keys; the class counts
+  // (counts[2..4]: rows of class 0, 1, 2 before the refinement); the rows in
+  // key order (class, then class-1 rows in spatial order); the packed
+  // features in that order; the row-tile boxes
   const int64_t rpad = ceil_div(rows, kTcM) * kTcM;
   k_tc_pack_rows<<<static_cast<unsigned>(ceil_div(rows, 128)), 128, 0, st>>>(
-      up, s, rows, centre, y2max, ai, rowc, rinfo, rcls);
+      up, s, rows, centre, y2max, ai, rowc, rinfo, rcls, rrad2, box, rkey);
   ABC_LAUNCH_CHECK();
   const int64_t ncl = ceil_div(rows, kClsTile);
   k_cls_count<<<static_cast<unsigned>(ncl), 256, 0, st>>>(rcls, rows, cnt3);
   ABC_LAUNCH_CHECK();
   k_cls_scan<<<1, 1024, 0, st>>>(cnt3, static_cast<int>(ncl), off3, counts + 2);
   ABC_LAUNCH_CHECK();
-  k_cls_scatter<<<static_cast<unsigned>(ncl), kClsTile / 4, 0, st>>>(rcls, rows, off3, perm);
-  ABC_LAUNCH_CHECK();
+  rc = launch_radix_sort(rkey, nullptr, rkey_s, perm, rows, nullptr, 18, sort_scr, sort_bytes, st);
+  if (rc) return rc;
   k_tc_pack_sorted<<<static_cast<unsigned>(ceil_div(rpad, 128)), 128, 0, st>>>(
       up, s, rows, rpad, centre, perm, Apk);
+  ABC_LAUNCH_CHECK();
+  k_row_boxes<<<static_cast<unsigned>(rpad / kTcM), kTcM, 0, st>>>(up, rows, perm, counts + 2,
+                                                                  rrad2, rbox);
   ABC_LAUNCH_CHECK();
   // every row on the tensor cores
   const int nch = tc_chunks(rows, ncap, mult);
@@ -957,7 +1259,7 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   k_weights_tc<<<grid, kTcThreads, kTcSmem, st>>>(reinterpret_cast<const uint8_t*>(Apk),
                                                   reinterpret_cast<const uint8_t*>(Bpk), nc_dev,
                                                   rows, part, err, off_dev, rinfo, rcls, cand,
-                                                  ccnt, perm);
+                                                  ccnt, perm, rbox, cbox);
   ABC_LAUNCH_CHECK();
   if (wt && wt->tc1) ABC_CUDA_TRY(cudaEventRecord(wt->tc1, st));
   k_weights_tc_combine<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(
@@ -965,7 +1267,7 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   ABC_LAUNCH_CHECK();
   // class 1: exact from the listed columns (overflow -> class 2)
   k_tc_refine<<<static_cast<unsigned>(ceil_div(rows, 128)), 128, 0, st>>>(
-      up, s, rows, rcls, cand, ccnt, kTcGroups * nch, cu, cc, ncap, total_p, logW, off_dev);
+      up, s, rows, rcls, cand, ccnt, kTcGroups * nch, cu_s, cc_s, ncap, total_p, logW, off_dev);
   ABC_LAUNCH_CHECK();
   // class 2: the FP32 kernel
   const int64_t nt = ceil_div(rows, kPartTile);
@@ -975,8 +1277,8 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   ABC_LAUNCH_CHECK();
   k_fb_scatter<<<static_cast<unsigned>(nt), 256, 0, st>>>(rcls, up, s, rows, off, idx, u_f, s_f);
   ABC_LAUNCH_CHECK();
-  int rc = launch_weights_fp32(u_f, s_f, rows, cu, cc, nc_dev, ncap, total_p, lw_f, b + l.fp,
-                               l.cnt - l.fp, st, off_dev, kFp32Mult, counts + 0, wt);
+  rc = launch_weights_fp32(u_f, s_f, rows, cu, cc, nc_dev, ncap, total_p, lw_f, b + l.fp,
+                           l.cnt - l.fp, st, off_dev, kFp32Mult, counts + 0, wt);
   if (rc) return rc;
   k_fb_back<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(idx, lw_f, counts, logW,
                                                                        off_dev);
