@@ -251,21 +251,25 @@ def run_gpu(args):
     # the weight pass splits into the tensor-core kernel and the FP32 kernel
     # (rows whose tensor-core error bound is too large); the roofline line is
     # for the one with the larger device time, timed by events around it
+    # rows off the tensor cores: the FP32 kernel (FP32 precision) or, in the
+    # BF16 precision, the per-row kernel for the rare class-2 rows
+    fb_name = "k_fb_rows" if args.prec else "k_weights_fp32"
     kern = {}
     for name, ms_k, rows_k in (("k_weights_tc", sum(s.ms_tc for s in stats),
                                 [s.rows_tc for s in stats]),
-                               ("k_weights_fp32", sum(s.ms_fp32 for s in stats),
+                               (fb_name, sum(s.ms_fp32 for s in stats),
                                 [N - s.rows_tc for s in stats])):
         pk = sum(r * (s.pairs // N) for r, s in zip(rows_k, stats))
         kern[name] = {"ms": ms_k / args.steps, "pairs": pk / args.steps,
                       "gexp_s": pk / (ms_k / 1e3) / 1e9 if ms_k > 0 else 0.0}
     # the tensor-core kernel does two kinds of work: the split-bf16 GEMM over
-    # every (row, column) pair (2 x 60 flops: 10 features x 6 split products)
-    # and one exponential per pair of the rows whose sums it keeps (rows_exp;
-    # the other rows only get candidate lists).  Its roofline is whichever of
-    # the two lower bounds on its time is larger.
+    # the 128 x 256 tiles it visits (2 x 60 flops per pair: 10 features x 6
+    # split products; class-1 row tiles skip the column tiles beyond their
+    # candidate radius) and one exponential per pair of the rows whose sums it
+    # keeps (rows_exp; the other rows only get candidate lists).  Its roofline
+    # is whichever of the two lower bounds on its time is larger.
     tc_ms = kern["k_weights_tc"]["ms"]
-    tc_flops = sum(2 * TC_K_USED * s.rows_tc * (s.pairs // N) for s in stats) / args.steps
+    tc_flops = sum(2 * TC_K_USED * 128 * 256 * s.tiles_tc for s in stats) / args.steps
     tc_exps = sum(s.rows_exp * (s.pairs // N) for s in stats) / args.steps
     kern["k_weights_tc"].update({"exp_pairs": tc_exps, "tflops": tc_flops / (tc_ms / 1e3) / 1e12
                                  if tc_ms > 0 else 0.0})
@@ -302,7 +306,8 @@ def run_gpu(args):
                         "peak": tc_peak / 1e12, "unit": "TFLOP/s", "frac": a / tc_peak,
                         "peak_source": "%s bf16 dense GEMM, sustained (cuBLAS, %s)" % (
                             src, "MEASURED_PEAKS.json" if src == "measured" else "recipe"),
-                        "work": "2 x 60 flops per (row, column) pair",
+                        "work": "2 x 60 flops per (row, column) pair of the visited tiles",
+                        "tiles_per_step": sum(s.tiles_tc for s in stats) / args.steps,
                         "exp_frac": tc_exps / (tc_ms / 1e3) / exp_peak, "traffic": None}
         else:
             a = tc_exps / (tc_ms / 1e3)
@@ -310,10 +315,10 @@ def run_gpu(args):
                        "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": a / exp_peak,
                        "peak_source": exp_src, "work": "one exp2 per pair of the kept rows",
                        "tensor_frac": tc_flops / (tc_ms / 1e3) / tc_peak, "traffic": None}
-    fp32_ms = kern["k_weights_fp32"]["ms"]
-    fp32_roof = {"bound": "alu", "kernel": "k_weights_fp32",
-                 "achieved": kern["k_weights_fp32"]["gexp_s"], "peak": exp_peak / 1e9,
-                 "unit": "Gexp/s", "frac": kern["k_weights_fp32"]["gexp_s"] * 1e9 / exp_peak,
+    fp32_ms = kern[fb_name]["ms"]
+    fp32_roof = {"bound": "alu", "kernel": fb_name,
+                 "achieved": kern[fb_name]["gexp_s"], "peak": exp_peak / 1e9,
+                 "unit": "Gexp/s", "frac": kern[fb_name]["gexp_s"] * 1e9 / exp_peak,
                  "peak_source": exp_src, "work": "one exp2 per pair", "traffic": None}
     # the roofline line is the dominant kernel's: the largest device time per step
     cands = [(sim_step_ms, sim_roof), (fp32_ms, fp32_roof)]
@@ -335,7 +340,7 @@ def run_gpu(args):
         "roofline": roofline,
         "weight_kernels": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in kern.items()},
         "rooflines": {"k_simulate": sim_roof, "k_weights_tc": tc_roof,
-                      "k_weights_fp32": fp32_roof if fp32_ms > 0 else None},
+                      fb_name: fp32_roof if fp32_ms > 0 else None},
         "weight_pass_gexp_s": pairs / (wms / 1e3) / 1e9 if wms > 0 else 0.0,
         "phases_ms": {"weights": wms / args.steps, "simulator": sim_ms / args.steps,
                       "rest": (rank_ms - wms - sim_ms) / args.steps},

@@ -726,6 +726,7 @@ int generation_t(abc_ctx* c) {
   g.ms_sim = ms_sim;
   int h_nc = 0;
   int h_counts[4] = {0, 0, 0, 0};
+  unsigned long long h_tiles = 0;
   WeightTiming wt;
   wt.tc0 = c->ek[0];
   wt.tc1 = c->ek[1];
@@ -757,6 +758,8 @@ int generation_t(abc_ctx* c) {
       ABC_CUDA_TRY(cudaMemcpyAsync(&h_nc, c->nc, sizeof(int), cudaMemcpyDeviceToHost, st));
       if (wt.counts)
         ABC_CUDA_TRY(cudaMemcpyAsync(h_counts, wt.counts, sizeof h_counts, cudaMemcpyDeviceToHost, st));
+      if (wt.tiles)
+        ABC_CUDA_TRY(cudaMemcpyAsync(&h_tiles, wt.tiles, sizeof h_tiles, cudaMemcpyDeviceToHost, st));
       weighted = true;
       // delayed acceptance: a proposal simulated with probability rho carries 1/rho
       if (screen && (rc = rho_correct(c->logW, c->rho_pop[nxt], c->N, st))) return rc;
@@ -780,6 +783,7 @@ int generation_t(abc_ctx* c) {
     const bool tc = c->cfg.weight_prec == ABC_P_BF16_TC;
     g.rows_tc = tc ? h_counts[1] : 0;
     g.rows_exp = tc ? h_counts[2] : 0;
+    g.tiles_tc = tc ? static_cast<int64_t>(h_tiles) : 0;
     if (tc && h_counts[1] > 0) {
       ABC_CUDA_TRY(cudaEventElapsedTime(&ms, c->ek[0], c->ek[1]));
       g.ms_tc = ms;

@@ -9,13 +9,16 @@
 
 namespace abc {
 
-// Model parameters as the kernels see them (by value, ~140 bytes).
+// Model parameters as the kernels see them (by value, ~220 bytes).
 struct SimParams {
   int32_t model, sampler, T, pad;
   int32_t A0, R0, D0, pad2;
   int64_t P;
   float lo[8], hi[8], x_obs[8];
   uint32_t k0, k1;  // Philox key
+  // the key of each of the ten Philox rounds (k + r * Weyl constant), read
+  // from the kernel-parameter bank by the simulator's generator
+  uint32_t rk0[10], rk1[10];
 };
 
 inline SimParams make_params(const abc_config& c) {
@@ -34,6 +37,10 @@ inline SimParams make_params(const abc_config& c) {
   }
   p.k0 = static_cast<uint32_t>(c.seed & 0xFFFFFFFFull);
   p.k1 = static_cast<uint32_t>(c.seed >> 32) ^ c.run_id;
+  for (int r = 0; r < 10; ++r) {
+    p.rk0[r] = p.k0 + static_cast<uint32_t>(r) * 0x9E3779B9u;
+    p.rk1[r] = p.k1 + static_cast<uint32_t>(r) * 0xBB67AE85u;
+  }
   return p;
 }
 
@@ -112,6 +119,7 @@ __device__ __forceinline__ T block_sum(T v, T* smem) {
 struct WeightTiming {
   cudaEvent_t tc0 = nullptr, tc1 = nullptr, fp0 = nullptr, fp1 = nullptr;
   const int* counts = nullptr;
+  const unsigned long long* tiles = nullptr;  // tile products of the tensor-core kernel
 };
 
 // Step-size Beta rule of stage t (Eq. 16 and the mean-variance and

@@ -72,9 +72,9 @@ __device__ U128 saird_path(const SimParams& p, const float th[8], uint32_t c0, u
   U128 acc{0ull, 0ull};
   for (int day = 0; day < T; ++day) {
     const uint32_t cb = static_cast<uint32_t>(day) * 4u;
-    const u32x4 b0 = philox4x32_10(c0, c1, cb + 0u, tag, p.k0, p.k1);
-    const u32x4 b1 = philox4x32_10(c0, c1, cb + 1u, tag, p.k0, p.k1);
-    const u32x4 b2 = philox4x32_10(c0, c1, cb + 2u, tag, p.k0, p.k1);
+    const u32x4 b0 = philox4x32_10_rk(c0, c1, cb + 0u, tag, p.rk0, p.rk1);
+    const u32x4 b1 = philox4x32_10_rk(c0, c1, cb + 1u, tag, p.rk0, p.rk1);
+    const u32x4 b2 = philox4x32_10_rk(c0, c1, cb + 2u, tag, p.rk0, p.rk1);
     // g = alpha0 + alpha / (1 + (A+R+D)^n)  (Eq. 4), x^n = exp(n log x)
     const int32_t x = A + R + D;
     float xn;

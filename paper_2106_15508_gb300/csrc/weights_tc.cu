@@ -399,9 +399,9 @@ k_row_boxes(const float* __restrict__ up, int64_t rows, const int* __restrict__ 
 // The epilogue's work depends on the row class: exponential sums for class 0,
 // candidate lists for class 1, nothing for class 2.  A row is a TMEM lane, so
 // a warp runs the union of its 32 rows' work; the tensor-core pass therefore
-// takes the rows in class order (stable within a class): perm[p] = original
-// row at position p.  Counts per tile of kClsTile rows, then offsets, then
-// the scatter.
+// takes the rows in class order (class-1 rows in spatial order, the others
+// in index order): perm[p] = original row at position p, from a stable radix
+// sort of the keys k_tc_pack_rows writes.  Here: the rows per class.
 constexpr int kClsTile = 1024;
 
 __global__ void k_cls_count(const uint8_t* __restrict__ rcls, int64_t rows, int* __restrict__ cnt3) {
@@ -424,28 +424,16 @@ __global__ void k_cls_count(const uint8_t* __restrict__ rcls, int64_t rows, int*
   }
 }
 
-// off3[3 i + k] = first position of tile i's class-k rows; ncls[0..2] = rows
-// per class
-__global__ void k_cls_scan(const int* __restrict__ cnt3, int ntiles, int* __restrict__ off3,
-                           int* __restrict__ ncls) {
+// ncls[0..2] = rows per class (sums of the per-tile counts, in tile order)
+__global__ void k_cls_total(const int* __restrict__ cnt3, int ntiles, int* __restrict__ ncls) {
   __shared__ int sm[32];
-  __shared__ int last;
-  int base = 0;
 #pragma unroll 1
   for (int k = 0; k < 3; ++k) {
-    int carry = 0;
-    for (int b = 0; b < ntiles; b += blockDim.x) {
-      const int i = b + threadIdx.x;
-      const int v = i < ntiles ? cnt3[3 * i + k] : 0;
-      const int inc = block_incl_scan<int>(v, sm);
-      if (i < ntiles) off3[3 * i + k] = base + carry + inc - v;
-      if (threadIdx.x == blockDim.x - 1) last = inc;
-      __syncthreads();
-      carry += last;
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) ncls[k] = carry;
-    base += carry;
+    int acc = 0;
+    for (int i = threadIdx.x; i < ntiles; i += blockDim.x) acc += cnt3[3 * i + k];
+    acc = block_sum<int>(acc, sm);
+    if (threadIdx.x == 0) ncls[k] = acc;
+    __syncthreads();
   }
 }
 
@@ -544,7 +532,11 @@ __global__ void k_tc_pack_cols(const float* __restrict__ cu, const float* __rest
     for (int d = 0; d < 9; ++d) f[d] = 0.0f;
     f[9] = kPadLogit;
   }
-  store_packed_row<false>(Bpk + (k / kTcN) * (kTcN * kTcK), static_cast<int>(k % kTcN), f);
+  // inside a tile, column k goes to accumulator column (k mod 8) * 32 + k / 8
+  // (k tile-local): consecutive sorted columns, which are spatial neighbours,
+  // spread over the eight 32-column chunks and so over the candidate slots
+  const int kt = static_cast<int>(k % kTcN);
+  store_packed_row<false>(Bpk + (k / kTcN) * (kTcN * kTcK), (kt % 8) * 32 + kt / 8, f);
 }
 
 // ---- main kernel -------------------------------------------------------------
@@ -584,7 +576,8 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
              float2* __restrict__ part, unsigned* err, const int* __restrict__ off_dev,
              const float2* __restrict__ rinfo, const uint8_t* __restrict__ rcls,
              int* __restrict__ cand, int* __restrict__ ccnt, const int* __restrict__ perm,
-             const float* __restrict__ rbox, const float* __restrict__ cbox) {
+             const float* __restrict__ rbox, const float* __restrict__ cbox,
+             unsigned long long* __restrict__ tile_count) {
   extern __shared__ uint8_t tc_smem_raw[];
   if (off_dev && *off_dev) return;  // run finished or its generation stopped (block-uniform)
   const int64_t nrows = rows;
@@ -640,6 +633,7 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
   }
   __syncthreads();
   const int ntiles = use_mask ? *sm.ntiles : span;
+  if (threadIdx.x == 0) atomicAdd(tile_count, static_cast<unsigned long long>(ntiles));
   // the t-th visited column tile
   struct TileIter {
     const uint32_t* m;
@@ -803,14 +797,15 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
             if (cm > thr) {
               // only the groups above the threshold are scanned (candidates
               // are rare: a few per row among all columns)
-              const int col0 = tile * kTcN + c * 32;
+              // accumulator column c * 32 + i holds sorted column tile * kTcN + i * 8 + c
+              const int col0 = tile * kTcN + c;
 #pragma unroll
               for (int k = 0; k < 4; ++k) {
                 if (!(gm[k] > thr)) continue;
 #pragma unroll
                 for (int i = 8 * k; i < 8 * k + 8; ++i)
-                  if (v[i] > thr && col0 + i < nc) {
-                    if (nlist < kCandCap) lst[nlist] = col0 + i;
+                  if (v[i] > thr && col0 + 8 * i < nc) {
+                    if (nlist < kCandCap) lst[nlist] = col0 + 8 * i;
                     ++nlist;
                   }
               }
@@ -997,12 +992,7 @@ __global__ void k_tc_refine(const float* __restrict__ up, const float* __restric
 
 // ---- class-2 rows through the FP32 kernel ----------------------------------------
 constexpr int kPartTile = 1024;
-constexpr int kFp32Mult = 8;  // column chunks of the FP32 share (its rows are few)
 
-int launch_weights_fp32(const float*, const float*, int64_t, const float*, const float*, const int*,
-                        int64_t, const uint64_t*, double*, void*, size_t, cudaStream_t,
-                        const int*, int, const int*, const WeightTiming*);
-size_t weights_fp32_scratch_bytes(int64_t, int64_t, int);
 
 __global__ void k_fb_count(const uint8_t* __restrict__ rcls, int64_t rows, int* __restrict__ cnt) {
   __shared__ int sm[32];
@@ -1066,6 +1056,78 @@ __global__ void k_fb_scatter(const uint8_t* __restrict__ rcls, const float* __re
   }
 }
 
+// class-2 rows (compacted, counts[0] of them; rare: list overflow or a
+// non-finite bound): one CTA per row, grid-strided.  Exponents from direct
+// differences as in k_tc_refine; per thread an online maximum and a
+// compensated fp32 sum of 2^(e - m) (ex2 ~2 ulp per term); per warp a
+// shuffle merge, then the eight warp partials merged in fp64 in warp order.
+constexpr int kFbThreads = 256;
+
+__global__ void __launch_bounds__(kFbThreads)
+k_fb_rows(const float* __restrict__ u_f, const float* __restrict__ s_f, int64_t rcap,
+          const int* __restrict__ counts, const float* __restrict__ cu,
+          const float* __restrict__ cc, const int* __restrict__ nc_p, int64_t ncap,
+          const uint64_t* __restrict__ total_p, double* __restrict__ lw_f,
+          const int* __restrict__ off_dev) {
+  __shared__ float wm[kFbThreads / 32];
+  __shared__ float ws[kFbThreads / 32];
+  if (off_dev && *off_dev) return;
+  const int64_t n2 = counts[0];
+  const int64_t nc = *nc_p;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t r = blockIdx.x; r < n2; r += gridDim.x) {
+    float x[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) x[d] = u_f[static_cast<int64_t>(d) * rcap + r];
+    const float sj = fmaxf(s_f[r], kSMinTc);
+    const float ninv = -1.4426950408889634f / (2.0f * sj);
+    float m = -INFINITY, S = 0.0f, cS = 0.0f;
+    for (int64_t k = threadIdx.x; k < nc; k += kFbThreads) {
+      float q[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const float a = x[2 * h] - cu[static_cast<int64_t>(2 * h) * ncap + k];
+        const float b = x[2 * h + 1] - cu[static_cast<int64_t>(2 * h + 1) * ncap + k];
+        q[h] = __fmaf_rn(a, a, b * b);
+      }
+      const float e = __fmaf_rn((q[0] + q[1]) + (q[2] + q[3]), ninv, cc[k]);
+      if (e > m) {
+        const float f = ex2(m - e);  // 0 while m is -inf
+        S *= f;
+        cS *= f;
+        m = e;
+      }
+      const float y = ex2(e - m) - cS;
+      const float t = S + y;
+      cS = (t - S) - y;
+      S = t;
+    }
+    // warp merge of (m, S)
+    for (int o = 16; o > 0; o >>= 1) {
+      const float m2 = __shfl_down_sync(0xffffffffu, m, o);
+      const float s2 = __shfl_down_sync(0xffffffffu, S, o);
+      const float M = fmaxf(m, m2);
+      if (M > -INFINITY) S = (S > 0.0f ? S * ex2(m - M) : 0.0f) + (s2 > 0.0f ? s2 * ex2(m2 - M) : 0.0f);
+      m = M;
+    }
+    if (lane == 0) {
+      wm[warp] = m;
+      ws[warp] = S;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double M = -INFINITY;
+      for (int w = 0; w < kFbThreads / 32; ++w) M = fmax(M, static_cast<double>(wm[w]));
+      double tot = 0.0;
+      for (int w = 0; w < kFbThreads / 32; ++w)
+        if (ws[w] > 0.0f) tot += static_cast<double>(ws[w]) * exp2(static_cast<double>(wm[w]) - M);
+      const double lse2 = M + log2(tot) + 32.0 - log2(static_cast<double>(*total_p));
+      lw_f[r] = 4.0 * log(6.283185307179586 * static_cast<double>(sj)) - 0.6931471805599453 * lse2;
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_fb_back(const int* __restrict__ idx, const double* __restrict__ lw_f,
                           const int* __restrict__ counts, double* __restrict__ logW,
                           const int* __restrict__ off_dev) {
@@ -1084,9 +1146,9 @@ static int tc_chunks(int64_t rows, int64_t ncap, int mult) {
 }
 
 struct TcLayout {
-  size_t apk, bpk, rowc, part, err, rinfo, rcls, cand, ccnt, fp, cnt, off, counts, idx, u_f, s_f,
-      lw_f, ctr, cnt3, off3, perm, rrad2, rkey, rkey_s, ckey, ckey_s, cperm, cu_s, cc_s, cbox,
-      rbox, box, sort, total;
+  size_t apk, bpk, rowc, part, err, rinfo, rcls, cand, ccnt, cnt, off, counts, idx, u_f, s_f,
+      lw_f, ctr, cnt3, perm, rrad2, rkey, rkey_s, ckey, ckey_s, cperm, cu_s, cc_s, cbox,
+      rbox, box, sort, tiles, total;
 };
 
 static TcLayout tc_layout(int64_t rows, int64_t ncap, int mult) {
@@ -1110,7 +1172,6 @@ static TcLayout tc_layout(int64_t rows, int64_t ncap, int mult) {
   take(l.rcls, R);
   take(l.cand, sizeof(int) * slots * R * kCandCap);
   take(l.ccnt, sizeof(int) * slots * R);
-  take(l.fp, weights_fp32_scratch_bytes(rows, ncap, kFp32Mult));
   take(l.cnt, 4 * static_cast<size_t>(nt));
   take(l.off, 4 * static_cast<size_t>(nt));
   take(l.counts, 8 * sizeof(int));
@@ -1121,7 +1182,6 @@ static TcLayout tc_layout(int64_t rows, int64_t ncap, int mult) {
   take(l.ctr, sizeof(double) * 8 * kCtrBlocks + 256 + 256);  // column sums, centre, radius
   const size_t ncls_tiles = static_cast<size_t>(ceil_div(std::max<int64_t>(rows, 1), kClsTile));
   take(l.cnt3, 3 * 4 * ncls_tiles);
-  take(l.off3, 3 * 4 * ncls_tiles);
   take(l.perm, 4 * R);
   const size_t C = static_cast<size_t>(std::max<int64_t>(ncap, 1));
   take(l.rrad2, 4 * R);
@@ -1135,6 +1195,7 @@ static TcLayout tc_layout(int64_t rows, int64_t ncap, int mult) {
   take(l.cbox, sizeof(float) * kColBox * static_cast<size_t>(cpad / kTcN));
   take(l.rbox, sizeof(float) * kRowBox * static_cast<size_t>(rpad / kTcM));
   take(l.box, 16 * sizeof(unsigned));
+  take(l.tiles, sizeof(unsigned long long));
   take(l.sort, radix_sort_scratch_bytes(std::max<int64_t>(rows, ncap)));
   l.total = o;
   return l;
@@ -1192,7 +1253,6 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   auto* centre = reinterpret_cast<float*>(b + l.ctr + sizeof(double) * 8 * kCtrBlocks);
   auto* y2max = reinterpret_cast<unsigned*>(b + l.ctr + sizeof(double) * 8 * kCtrBlocks + 256);
   auto* cnt3 = reinterpret_cast<int*>(b + l.cnt3);
-  auto* off3 = reinterpret_cast<int*>(b + l.off3);
   auto* perm = reinterpret_cast<int*>(b + l.perm);
   auto* rrad2 = reinterpret_cast<float*>(b + l.rrad2);
   auto* rkey = reinterpret_cast<uint32_t*>(b + l.rkey);
@@ -1205,10 +1265,12 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   auto* cbox = reinterpret_cast<float*>(b + l.cbox);
   auto* rbox = reinterpret_cast<float*>(b + l.rbox);
   auto* box = reinterpret_cast<unsigned*>(b + l.box);
+  auto* tiles = reinterpret_cast<unsigned long long*>(b + l.tiles);
   void* sort_scr = b + l.sort;
   const size_t sort_bytes = l.total - l.sort;
   if (err_dev) *err_dev = err;
   ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
+  ABC_CUDA_TRY(cudaMemsetAsync(tiles, 0, sizeof(unsigned long long), st));
   // columns: centre and box, spatial order, packed once (centred), tile boxes
   const int64_t cpad = ceil_div(std::max<int64_t>(ncap, 1), kTcN) * kTcN;
   k_col_sum<<<kCtrBlocks, 256, 0, st>>>(cu, nc_dev, ncap, cpart);
@@ -1242,7 +1304,7 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   const int64_t ncl = ceil_div(rows, kClsTile);
   k_cls_count<<<static_cast<unsigned>(ncl), 256, 0, st>>>(rcls, rows, cnt3);
   ABC_LAUNCH_CHECK();
-  k_cls_scan<<<1, 1024, 0, st>>>(cnt3, static_cast<int>(ncl), off3, counts + 2);
+  k_cls_total<<<1, 1024, 0, st>>>(cnt3, static_cast<int>(ncl), counts + 2);
   ABC_LAUNCH_CHECK();
   rc = launch_radix_sort(rkey, nullptr, rkey_s, perm, rows, nullptr, 18, sort_scr, sort_bytes, st);
   if (rc) return rc;
@@ -1259,7 +1321,7 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   k_weights_tc<<<grid, kTcThreads, kTcSmem, st>>>(reinterpret_cast<const uint8_t*>(Apk),
                                                   reinterpret_cast<const uint8_t*>(Bpk), nc_dev,
                                                   rows, part, err, off_dev, rinfo, rcls, cand,
-                                                  ccnt, perm, rbox, cbox);
+                                                  ccnt, perm, rbox, cbox, tiles);
   ABC_LAUNCH_CHECK();
   if (wt && wt->tc1) ABC_CUDA_TRY(cudaEventRecord(wt->tc1, st));
   k_weights_tc_combine<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(
@@ -1277,13 +1339,18 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   ABC_LAUNCH_CHECK();
   k_fb_scatter<<<static_cast<unsigned>(nt), 256, 0, st>>>(rcls, up, s, rows, off, idx, u_f, s_f);
   ABC_LAUNCH_CHECK();
-  rc = launch_weights_fp32(u_f, s_f, rows, cu, cc, nc_dev, ncap, total_p, lw_f, b + l.fp,
-                           l.cnt - l.fp, st, off_dev, kFp32Mult, counts + 0, wt);
-  if (rc) return rc;
+  if (wt && wt->fp0) ABC_CUDA_TRY(cudaEventRecord(wt->fp0, st));
+  k_fb_rows<<<static_cast<unsigned>(std::min<int64_t>(rows, 8 * 152)), kFbThreads, 0, st>>>(
+      u_f, s_f, rows, counts, cu, cc, nc_dev, ncap, total_p, lw_f, off_dev);
+  ABC_LAUNCH_CHECK();
+  if (wt && wt->fp1) ABC_CUDA_TRY(cudaEventRecord(wt->fp1, st));
   k_fb_back<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(idx, lw_f, counts, logW,
                                                                        off_dev);
   ABC_LAUNCH_CHECK();
-  if (wt) wt->counts = counts;
+  if (wt) {
+    wt->counts = counts;
+    wt->tiles = tiles;
+  }
   return ABC_OK;
 }
 
