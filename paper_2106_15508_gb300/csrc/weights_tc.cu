@@ -14,8 +14,14 @@
 // used of 64.  Products of bf16 values are exact and accumulate in fp32 in
 // tensor memory, so the remaining error is the fp32 accumulation of terms of
 // size L_j (2 |x_j| |y| + |y|^2); centring on the cloud keeps |x| and |y| at
-// its spread.  Rows whose error bound exceeds kTcBoundMax go through the FP32
-// direct-difference kernel instead (see the split below).
+// its spread.  Rows are classified by that error bound (k_tc_pack_rows):
+// class 0 keeps its tensor-core sum, class 1 is recomputed exactly from the
+// columns the epilogue lists (k_tc_refine), class 2 (list overflow or a
+// non-finite bound) by a direct-difference kernel (k_fb_rows).
+//
+// Order: columns in spatial order (a stable radix sort of Morton keys),
+// rows by class and class-1 rows in spatial order; a CTA of class-1 rows
+// visits only the column tiles whose box lies within its candidate radius.
 //
 // Kernel structure (one CTA = 128 rows, one SM):
 //   warp 16 : bulk-copy producer (cp.async.bulk, mbarrier complete_tx):
@@ -24,11 +30,10 @@
 //             fp32 accumulators double-buffered in TMEM (2 x 256 columns)
 //   warps 0-15: epilogue, one thread per row (TMEM lane) and column group:
 //             warps w, w + 4, w + 8, w + 12 share TMEM lanes 32 (w % 4) ..
-//             and take every fourth 32-column chunk (tcgen05.ld), each
-//             keeping an online max and sum of 2^(e - m); four warps per lane
-//             quarter keep the exponential unit busy while others wait on
-//             TMEM (two per quarter reached 0.84 of this kernel's rate)
-// Operands are packed by a prep kernel in the canonical K-major layout
+//             and take every fourth 32-column chunk (tcgen05.ld); class-0
+//             warps keep an online max and sum of 2^(e - m), class-1 warps
+//             the chunk maxima and their candidate lists
+// Operands are packed by prep kernels in the canonical K-major layout
 // without swizzle: 8 x 8 bf16 core matrices (128 contiguous bytes), the 8
 // core matrices of a row group consecutive along K (LBO = 128 B), row groups
 // 1024 B apart (SBO).  Every mbarrier wait is bounded in time; on time-out
@@ -143,7 +148,7 @@ __device__ __forceinline__ void store_packed_row(__nv_bfloat16* tile, int r, con
 //            kCandMargin bits of the row maximum and k_tc_refine recomputes
 //            the row exactly from them (rinfo = (ancestor lower bound of the
 //            maximum in the accumulator frame, delta_j));
-//   class 2: delta_j not finite: the FP32 kernel recomputes the row.
+//   class 2: delta_j not finite: k_fb_rows recomputes the row.
 // The packed operand is written afterwards by k_tc_pack_sorted, in class order.
 //
 // For class-1 rows also the radius R_j beyond which no column can be listed
@@ -855,7 +860,7 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
   if (warp == kTcIssuer) tmem_dealloc(tmem, kTmemCols);
 }
 
-// class-0 rows: log W from the partials (k_tc_refine and the FP32 kernel write
+// class-0 rows: log W from the partials (k_tc_refine and k_fb_rows write
 // the other rows).  Thread p takes sorted position p < n0 (the class-0 rows
 // come first), so the fp64 work runs in converged warps.
 __global__ void k_weights_tc_combine(const float2* __restrict__ part, int nchunks,
@@ -935,7 +940,7 @@ k_tc_probe(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
 
 // ---- exact recomputation of class-1 rows -------------------------------------
 // One thread per row: the listed columns of every partial slot (at most
-// kCandCap each; more sends the row to the FP32 kernel as class 2), exponents
+// kCandCap each; more sends the row to k_fb_rows as class 2), exponents
 // from direct differences as in the FP32 kernel, maximum, fp32 exponentials
 // and an fp64 sum.
 // Unlisted columns lie at least kCandMargin bits under the maximum: together
@@ -990,7 +995,7 @@ __global__ void k_tc_refine(const float* __restrict__ up, const float* __restric
   logW[j] = 4.0 * log(6.283185307179586 * static_cast<double>(sj)) - 0.6931471805599453 * lse2;
 }
 
-// ---- class-2 rows through the FP32 kernel ----------------------------------------
+// ---- class-2 rows: compaction, one CTA per row, scatter back ----------------------
 constexpr int kPartTile = 1024;
 
 
@@ -1213,7 +1218,7 @@ size_t weights_tc_scratch_bytes(int64_t rows, int64_t ncap, int mult) {
 
 // Every row on the tensor cores; class-1 rows (error bound above
 // kTcBoundMax) recomputed exactly from their listed columns, class-2 rows
-// (and class-1 rows whose lists overflowed) by the FP32 kernel.  All
+// (and class-1 rows whose lists overflowed) by k_fb_rows.  All
 // decisions and counts stay on the device (graph-capturable).
 int launch_weights_tc(const float* up, const float* s, int64_t rows, const float* cu,
                       const float* cc, const int* nc_dev, int64_t ncap, const uint64_t* total_p,
@@ -1331,7 +1336,7 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   k_tc_refine<<<static_cast<unsigned>(ceil_div(rows, 128)), 128, 0, st>>>(
       up, s, rows, rcls, cand, ccnt, kTcGroups * nch, cu_s, cc_s, ncap, total_p, logW, off_dev);
   ABC_LAUNCH_CHECK();
-  // class 2: the FP32 kernel
+  // class 2: one CTA per row
   const int64_t nt = ceil_div(rows, kPartTile);
   k_fb_count<<<static_cast<unsigned>(nt), 256, 0, st>>>(rcls, rows, cnt);
   ABC_LAUNCH_CHECK();
