@@ -211,9 +211,20 @@ def run_gpu(args):
         clk = clocks.stop()
         sim_days = sum(s.sim_days for s in stats)
         launches = sum(s.launches for s in stats)
-        # end to end through the C ABI with pinned host buffers
-        hbuf = torch.empty(len(blob), dtype=torch.uint8, pin_memory=True)
-        hbuf.numpy()[:] = np.frombuffer(blob, np.uint8)
+        # end to end through the C ABI with pinned host buffers, over the same
+        # generations as the device-timed loop: step k uploads the state
+        # before generation g_first + k (captured in an untimed replay) and
+        # reads the new population back
+        G.abc_set_state(ctx, blob)
+        blobs = []
+        for _ in range(args.steps):
+            blobs.append(G.abc_get_state(ctx))
+            G.abc_generation(ctx)
+        hbufs = []
+        for b_ in blobs:
+            hb = torch.empty(len(b_), dtype=torch.uint8, pin_memory=True)
+            hb.numpy()[:] = np.frombuffer(b_, np.uint8)
+            hbufs.append(hb)
         pop_h = dict(u=torch.empty((8, N), dtype=torch.float32, pin_memory=True),
                      d=torch.empty(N, dtype=torch.float64, pin_memory=True),
                      W=torch.empty(N, dtype=torch.float64, pin_memory=True),
@@ -222,8 +233,8 @@ def run_gpu(args):
         e2e_days = 0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            G.abc_set_state_ptr(ctx, hbuf.data_ptr(), len(blob))
+        for k in range(args.steps):
+            G.abc_set_state_ptr(ctx, hbufs[k].data_ptr(), hbufs[k].numel())
             G.abc_generation(ctx)
             e2e_days += G.abc_get_stats(ctx, G.abc_generations(ctx) - 1).sim_days
             G.abc_get_population(ctx, pop_h["u"].data_ptr(), pop_h["d"].data_ptr(),

@@ -355,7 +355,7 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
                              (static_cast<uint32_t>(a) << 8) | static_cast<uint32_t>(m >> 2),
                              ABC_TAG_BETA, p.k0, p.k1);
         const uint32_t wm = (m & 3) == 0 ? wb.x : (m & 3) == 1 ? wb.y : (m & 3) == 2 ? wb.z : wb.w;
-        acc = __fadd_rn(acc, __fdiv_rn(dev_log(unif(wm)), __fadd_rn(a_t, __int2float_rn(m))));
+        acc = __fadd_rn(acc, __fdiv_rn(dev_log_pos(unif(wm)), __fadd_rn(a_t, __int2float_rn(m))));
       }
       s = dev_exp(acc);
     }

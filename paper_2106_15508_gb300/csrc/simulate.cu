@@ -79,15 +79,15 @@ __device__ U128 saird_path(const SimParams& p, const float th[8], uint32_t c0, u
     const int32_t x = A + R + D;
     float xn;
     if (x == 0) xn = n > 0.0f ? 0.0f : 1.0f;
-    else xn = dev_exp(__fmul_rn(n, dev_log(__int2float_rn(x))));
+    else xn = dev_exp(__fmul_rn(n, dev_log_pos(__int2float_rn(x))));
     const float g = __fadd_rn(alpha0, __fdiv_rn(alpha, __fadd_rn(1.0f, xn)));
     int32_t k1, k2, k3, k4, k5;
     if (p.sampler == ABC_SIM_BINOMIAL) {
       const float t = __fdiv_rn(__fmul_rn(g, __int2float_rn(I)), Pf);
       const float pSI = -dev_expm1(-t);
-      // the same five draws as dev_binomial / dev_binomial_c, in two batches
-      // of independent draws (S->I, I exit, A exit; then the two splits);
-      // each batch's inversion loops run together, spread over the warp
+      // the five binomial draws, in two batches of independent draws (S->I,
+      // I exit, A exit; then the two splits); each batch's inversion loops
+      // run together, spread over the warp
       BinvJob e{0, 0.0f, 0.0f, 0.0f};
       bool f1, fI, fA;
       int nq = 0;

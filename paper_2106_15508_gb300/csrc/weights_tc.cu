@@ -182,22 +182,22 @@ __global__ void k_tc_pack_rows(const float* __restrict__ up, const float* __rest
   // error bound over the columns that can matter
   const float X = sqrtf(xxf);
   float Y = sqrtf(__uint_as_float(*y2max));
-  float lb = -INFINITY;
-  double mlb = 0.0, Ldd_ca = 0.0;
+  // (fp32 from here on: GB300's fp64 rate would bound this pass; every
+  // estimate below carries a margin far above its fp32 rounding)
+  float lb = -INFINITY, mlb = 0.0f, ca = 0.0f;
   if (a >= 0 && ai.q_prev[a] > 0u) {
-    const double ca = log2(static_cast<double>(ai.q_prev[a])) - 32.0;
+    ca = log2f(static_cast<float>(ai.q_prev[a])) - 32.0f;
     // 1.001: margin for the fp32 rounding of this estimate
-    Y = fminf(Y, 1.001f * (X + sqrtf(dd + (60.0f - static_cast<float>(ca)) / L)));
+    Y = fminf(Y, 1.001f * (X + sqrtf(dd + (60.0f - ca) / L)));
     // the ancestor's exponent in the accumulator frame (e - rowc), less a
     // rounding margin: a lower bound of the row maximum there
-    const double Ldd = static_cast<double>(L) * static_cast<double>(dd);
-    const double Lxx = static_cast<double>(L) * xx;
-    const double ea = ca - Ldd + Lxx;
-    // margin: 1 for the log2, 2^-19 of the two products for the fp32 inputs
-    // (dd, x and L carry a few 2^-24 relative each)
-    mlb = 1.0 + 0x1p-19 * (Ldd + Lxx);
-    lb = static_cast<float>(ea - mlb);
-    Ldd_ca = Ldd - ca;
+    const float Ldd = L * dd, Lxx = L * xxf;
+    const float ea = (ca - Ldd) + Lxx;
+    // margin: 1 for the log2 (and its fp32 rounding), 2^-19 of the two
+    // products for the fp32 inputs and sums (dd, x, L and ea carry a few
+    // 2^-24 relative each)
+    mlb = 1.0f + 0x1p-19f * (Ldd + Lxx);
+    lb = ea - mlb;
   }
   const float mag = L * (2.0f * X * Y + Y * Y) + 32.0f;
   const float delta = 0x1p-24f * 64.0f * mag;
@@ -212,15 +212,18 @@ __global__ void k_tc_pack_rows(const float* __restrict__ up, const float* __rest
   // (c_k <= 0), d = |u'_j - u_k|.  Listing therefore needs
   //   L (1 - e) d^2 - 4 e L X d - C < 0,  e = 2^-18,
   //   C = L dd - c_a + mlb + delta + kCandMargin + 3 e L X^2 + 32 e,
-  // i.e. d < (4 e L X + sqrt((4 e L X)^2 + 4 L (1 - e) C)) / (2 L (1 - e)).
+  // i.e., divided by L (no overflow for large L), d < dmax =
+  //   (4 e X + sqrt((4 e X)^2 + 4 (1 - e) C / L)) / (2 (1 - e)).
+  // 1.01 dmax^2 covers the fp32 rounding; a non-finite radius means no
+  // skipping.
   float r2 = __int_as_float(0x7f800000);
   if (cls == 1 && lb > -__int_as_float(0x7f800000)) {
-    const double e = 0x1p-18, Ld = static_cast<double>(L), Xd = static_cast<double>(X);
-    const double C = Ldd_ca + mlb + static_cast<double>(delta) + kCandMargin +
-                     3.0 * e * Ld * Xd * Xd + 32.0 * e;
-    const double bq = 4.0 * e * Ld * Xd;
-    const double dmax = (bq + sqrt(bq * bq + 4.0 * Ld * (1.0 - e) * C)) / (2.0 * Ld * (1.0 - e));
-    r2 = static_cast<float>(1.01 * dmax * dmax + 1e-12);
+    const float e = 0x1p-18f;
+    const float CL = dd + (mlb - ca + delta + kCandMargin + 32.0f * e) / L + 3.0f * e * X * X;
+    const float bq = 4.0f * e * X;
+    const float dmax = (bq + sqrtf(bq * bq + 4.0f * (1.0f - e) * CL)) / (2.0f * (1.0f - e));
+    const float v = 1.01f * dmax * dmax + 1e-12f;
+    if (v >= 0.0f && v < __int_as_float(0x7f800000)) r2 = v;
   }
   rrad2[j] = r2;
   // sort key: class, then (class 1) the 2-bit-per-coordinate Morton code of
