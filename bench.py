@@ -274,13 +274,13 @@ def run_gpu(args):
         kern[name] = {"ms": ms_k / args.steps, "pairs": pk / args.steps,
                       "gexp_s": pk / (ms_k / 1e3) / 1e9 if ms_k > 0 else 0.0}
     # the tensor-core kernel does two kinds of work: the split-bf16 GEMM over
-    # the 128 x 256 tiles it visits (2 x 60 flops per pair: 10 features x 6
+    # the tiles it visits (2 x 60 flops per pair: 10 features x 6
     # split products; class-1 row tiles skip the column tiles beyond their
     # candidate radius) and one exponential per pair of the rows whose sums it
     # keeps (rows_exp; the other rows only get candidate lists).  Its roofline
     # is whichever of the two lower bounds on its time is larger.
     tc_ms = kern["k_weights_tc"]["ms"]
-    tc_flops = sum(2 * TC_K_USED * 128 * 256 * s.tiles_tc for s in stats) / args.steps
+    tc_flops = sum(2 * TC_K_USED * s.pairs_tc for s in stats) / args.steps
     tc_exps = sum(s.rows_exp * (s.pairs // N) for s in stats) / args.steps
     kern["k_weights_tc"].update({"exp_pairs": tc_exps, "tflops": tc_flops / (tc_ms / 1e3) / 1e12
                                  if tc_ms > 0 else 0.0})
@@ -318,7 +318,7 @@ def run_gpu(args):
                         "peak_source": "%s bf16 dense GEMM, sustained (cuBLAS, %s)" % (
                             src, "MEASURED_PEAKS.json" if src == "measured" else "recipe"),
                         "work": "2 x 60 flops per (row, column) pair of the visited tiles",
-                        "tiles_per_step": sum(s.tiles_tc for s in stats) / args.steps,
+                        "pairs_per_step": sum(s.pairs_tc for s in stats) / args.steps,
                         "exp_frac": tc_exps / (tc_ms / 1e3) / exp_peak, "traffic": None}
         else:
             a = tc_exps / (tc_ms / 1e3)

@@ -376,9 +376,9 @@ typedef struct {
   int32_t pad_s;
   int64_t rows_exp;         /* rows whose tensor-core sums were kept (error bound    */
                             /*   small enough); the rest of rows_tc were refined    */
-  int64_t tiles_tc;         /* 128 x 256 tile products the tensor-core kernel ran    */
-                            /*   (column tiles beyond every candidate radius of a   */
-                            /*   class-1 row tile are skipped)                      */
+  int64_t pairs_tc;         /* (row, column) pairs in the tiles the tensor-core      */
+                            /*   kernel multiplied (column tiles beyond every       */
+                            /*   candidate radius of a class-1 row tile are skipped) */
 } abc_gen_stats;
 
 /* Validate cfg, allocate every device buffer (owned by the context), copy

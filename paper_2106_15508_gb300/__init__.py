@@ -71,7 +71,7 @@ class AbcGenStats(C.Structure):
         ("audit_accepted", C.c_int64), ("train_loss", C.c_double), ("ms_screen", C.c_double),
         ("ms_train", C.c_double), ("rows_tc", C.c_int64), ("ms_tc", C.c_double),
         ("ms_fp32", C.c_double), ("beta_bf", C.c_float), ("pad_s", C.c_int32),
-        ("rows_exp", C.c_int64), ("tiles_tc", C.c_int64),
+        ("rows_exp", C.c_int64), ("pairs_tc", C.c_int64),
     ]
 
     def as_dict(self):

@@ -31,6 +31,7 @@ size_t accept_scratch_bytes(int64_t);
 size_t survivors_scratch_bytes(int64_t);
 size_t weights_fp32_scratch_bytes(int64_t, int64_t, int mult = 1);
 size_t weights_tc_scratch_bytes(int64_t, int64_t, int mult = 1);
+int64_t weights_tc_tile_pairs();
 int ex2_probe(double* rate, cudaStream_t st);
 size_t predict_scratch_bytes(int64_t N, int64_t R, int32_t days, int32_t nq);
 int launch_predict(const SimParams& p, const float* u, const double* W, int64_t N, int64_t R,
@@ -783,7 +784,7 @@ int generation_t(abc_ctx* c) {
     const bool tc = c->cfg.weight_prec == ABC_P_BF16_TC;
     g.rows_tc = tc ? h_counts[1] : 0;
     g.rows_exp = tc ? h_counts[2] : 0;
-    g.tiles_tc = tc ? static_cast<int64_t>(h_tiles) : 0;
+    g.pairs_tc = tc ? static_cast<int64_t>(h_tiles) * weights_tc_tile_pairs() : 0;
     if (tc && h_counts[1] > 0) {
       ABC_CUDA_TRY(cudaEventElapsedTime(&ms, c->ek[0], c->ek[1]));
       g.ms_tc = ms;

@@ -1215,6 +1215,8 @@ int weights_tc_prepare() {
   return ABC_OK;
 }
 
+int64_t weights_tc_tile_pairs() { return static_cast<int64_t>(kTcM) * kTcN; }
+
 size_t weights_tc_scratch_bytes(int64_t rows, int64_t ncap, int mult) {
   return tc_layout(rows, ncap, mult).total;
 }

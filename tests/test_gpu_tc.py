@@ -172,11 +172,11 @@ def test_weights_tc_tiny_steps_recomputed():
     _state_errors("weights_tc_tiny_s", lw, olw, s, up, u, q)
 
 
-def test_weights_tc_dense_cluster_falls_back_to_fp32():
+def test_weights_tc_dense_cluster_falls_back_to_direct_rows():
     """Two dense column clusters far apart put the centre between them, so
     rows inside one cluster have large error bounds while thousands of
     columns lie within the listing margin: the lists overflow and the rows
-    go through the FP32 kernel."""
+    go through the per-row direct-difference kernel."""
     r = np.random.default_rng(35)
     n = 6000
     u = np.empty((8, n), np.float32)
