@@ -398,12 +398,14 @@ def run_batched(args):
         for _ in range(args.warmup):
             G.abc_batch_generation(b)
         torch.cuda.synchronize()
+        _nvtx(torch, "timed")
         t0 = time.perf_counter()
         first = G.abc_batch_generations(b)
         for _ in range(args.steps):
             G.abc_batch_generation(b)
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
+        _nvtx(torch, None)
         days = launches = 0
         for r in range(len(cfgs)):
             for t in range(first, G.abc_batch_generations(b)):

@@ -126,7 +126,7 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
     const cudaGraphEdgeData* edges = nullptr;
     size_t ndeps = 0;
     ABC_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &edges, &ndeps));
-    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};  // the rest zero
     np.conditional.handle = h;
     np.conditional.type = cudaGraphCondTypeWhile;
     np.conditional.size = 1;
