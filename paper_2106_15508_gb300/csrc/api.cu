@@ -1128,10 +1128,20 @@ int batch_destroy_graph(abc_batch* b) {
 int batch_build_graph(abc_batch* b) {
   batch_destroy_graph(b);
   const size_t R = b->runs.size();
+  // branches in decreasing particle-days (N T): the longest runs are
+  // captured, and so launched, first, which shortens the tail of the graph
+  std::vector<size_t> order(R);
+  for (size_t r = 0; r < R; ++r) order[r] = r;
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+    const abc_ctx* cx = b->runs[x];
+    const abc_ctx* cy = b->runs[y];
+    return cx->N * std::max(cx->T, 1) > cy->N * std::max(cy->T, 1);
+  });
   ABC_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
   int rc = ABC_OK;
   cudaError_t e = cudaEventRecord(b->evs[0], b->cap);
-  for (size_t r = 0; r < R && rc == ABC_OK && e == cudaSuccess; ++r) {
+  for (size_t i = 0; i < R && rc == ABC_OK && e == cudaSuccess; ++i) {
+    const size_t r = order[i];
     e = cudaStreamWaitEvent(b->rs[r], b->evs[0], 0);
     if (e == cudaSuccess) rc = batch_capture_run(b->br[r], b->rs[r], b->body);
     if (rc == ABC_OK && e == cudaSuccess) e = cudaEventRecord(b->evs[1 + r], b->rs[r]);

@@ -1068,8 +1068,8 @@ __global__ void k_fb_scatter(const uint8_t* __restrict__ rcls, const float* __re
 // non-finite bound): one CTA per row, grid-strided.  Exponents from direct
 // differences as in k_tc_refine; per thread an online maximum and a
 // compensated fp32 sum of 2^(e - m) (ex2 ~2 ulp per term); per warp a
-// shuffle merge, then the eight warp partials merged in fp64 in warp order.
-constexpr int kFbThreads = 256;
+// shuffle merge, then the warp partials merged in fp64 in warp order.
+constexpr int kFbThreads = 1024;  // one row per CTA: the rows are few, their columns many
 
 __global__ void __launch_bounds__(kFbThreads)
 k_fb_rows(const float* __restrict__ u_f, const float* __restrict__ s_f, int64_t rcap,
@@ -1350,7 +1350,7 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   k_fb_scatter<<<static_cast<unsigned>(nt), 256, 0, st>>>(rcls, up, s, rows, off, idx, u_f, s_f);
   ABC_LAUNCH_CHECK();
   if (wt && wt->fp0) ABC_CUDA_TRY(cudaEventRecord(wt->fp0, st));
-  k_fb_rows<<<static_cast<unsigned>(std::min<int64_t>(rows, 8 * 152)), kFbThreads, 0, st>>>(
+  k_fb_rows<<<static_cast<unsigned>(std::min<int64_t>(rows, 2 * 152)), kFbThreads, 0, st>>>(
       u_f, s_f, rows, counts, cu, cc, nc_dev, ncap, total_p, lw_f, off_dev);
   ABC_LAUNCH_CHECK();
   if (wt && wt->fp1) ABC_CUDA_TRY(cudaEventRecord(wt->fp1, st));
