@@ -34,7 +34,7 @@ class Model(C.Structure):
 
 class Smc(C.Structure):
     _fields_ = [
-        ("N", C.c_int32), ("M", C.c_int32), ("pad", C.c_int32), ("alpha", C.c_double),
+        ("N", C.c_int32), ("M", C.c_int32), ("max_total", C.c_int32), ("alpha", C.c_double),
         ("beta_mode", C.c_int32),
         ("beta_a", C.c_float), ("beta_b", C.c_int32), ("beta_p1", C.c_float),
         ("beta_p2", C.c_float), ("weight_mode", C.c_int32),
@@ -282,9 +282,10 @@ def normalize(logW):
 
 
 def make_smc(N, M=None, alpha=0.5, beta_mode=0, beta_a=2.0, beta_b=5, weight_mode=0,
-             max_batches=64, max_redraw=64, nthreads=1, beta_p1=0.0, beta_p2=0.0):
+             max_batches=64, max_redraw=64, nthreads=1, beta_p1=0.0, beta_p2=0.0, max_total=0):
     c = Smc()
     c.N, c.M = N, (N if M is None else M)
+    c.max_total = max_total
     c.alpha, c.beta_mode, c.beta_a, c.beta_b = alpha, beta_mode, beta_a, beta_b
     c.beta_p1, c.beta_p2 = beta_p1, beta_p2
     c.weight_mode, c.max_batches, c.max_redraw, c.nthreads = (weight_mode, max_batches,
@@ -320,14 +321,30 @@ def generation(m: OracleModel, c: Smc, t: int, eps1: float, pop: Population):
     return new, st
 
 
+def batches_gen0(c: Smc):
+    """Simulation batches that generation 0 stands for: its N prior draws in
+    batches of M parallel simulations (Sec. 4.1 counts simulation runs)."""
+    return -(-c.N // c.M)
+
+
 def run(m: OracleModel, c: Smc, G: int):
-    """Generations 0..G-1; returns the final population and per-generation stats."""
+    """Generations 0..G-1; returns the final population and per-generation stats.
+
+    A generation that exhausts its batch budget ends the run.  With
+    c.max_total > 0 the run also ends after the first generation at whose end
+    the simulation batches so far (generation 0 counting batches_gen0) reach
+    max_total: Sec. 4.1 stops each trial on the stage that reached 1000
+    simulation runs, and lets that stage finish."""
     pop = generation0(m, c)
     stats = []
     eps1 = 0.0
+    total = batches_gen0(c)
     for t in range(1, G):
+        if c.max_total > 0 and total >= c.max_total:
+            break
         new, st = generation(m, c, t, eps1, pop)
         stats.append(st)
+        total += st.batches
         if st.status != 0:
             break
         eps1 = st.eps1

@@ -636,7 +636,10 @@ OR_API float or_beta_real(const uint32_t key[2], float a, float b, uint32_t c0, 
 /*
  * Step-size Beta shapes of stage t >= 1 (Eq. 16 and the two alternatives that
  * Sec. 3.2 names).  ratio = eps_t / eps_1 rounded to fp32 (1 when eps_1 = 0).
- *   mode 0 (paper):  a = ratio, integer b = 2t;
+ *   mode 0 (paper):  a = ratio, integer b = 2t while 2t <= 1024 (the
+ *       product form reads one uniform per unit of b and its counter
+ *       space holds 1024); from stage 513 on the same Beta(ratio, 2t) is
+ *       drawn by the Gamma ratio, a and b clamped to [2^-20, 2^20];
  *   mode 1 (fixed):  a = fa, integer b = fb;
  *   mode 2 (real):   a = p1, b = p2;
  *   mode 3 (mean-variance): mean mu = p1 ratio, variance v = p2 / t;
@@ -656,6 +659,11 @@ OR_API void or_beta_shape(int32_t mode, float ratio, int32_t t, float fa, int32_
     a = ratio;
     bi = 2 * t;
     b = (float)bi;
+    if (bi > 1024) {
+      bi = 0;
+      if (!(a >= 0x1p-20f)) a = 0x1p-20f;
+      if (a > 0x1p20f) a = 0x1p20f;
+    }
   } else if (mode == 1) {
     a = fa;
     bi = fb;
@@ -804,7 +812,8 @@ OR_API double or_normalize(const double* logW, int64_t n, double* W) {
 typedef struct {
   int32_t N;            /* population (samples kept per stage)             */
   int32_t M;            /* proposals per batch ("parallel simulations")    */
-  int32_t pad;
+  int32_t max_total;    /* run budget in batches (Sec. 4.1), 0: none; the   */
+                        /* driver (oracle run()) applies it                 */
   double alpha;         /* survival ratio (Eq. 8), 0.5 in the paper         */
   int32_t beta_mode;    /* 0: Beta(eps_t/eps_1, 2t) (Eq. 16); 1: fixed;     */
   float beta_a;         /* 2: real shapes; 3: mean-variance; 4: mode-       */

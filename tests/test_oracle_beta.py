@@ -92,6 +92,30 @@ def test_shape_paper_and_fixed():
     assert (np.float32(a), b, bi) == (np.float32(0.7), 3.5, 0)
 
 
+def test_shape_paper_beyond_1024_uses_the_gamma_ratio():
+    """Eq. 16's b = 2t: the product form up to stage 512 (1024 uniforms),
+    then the same Beta(ratio, 2t) by the Gamma ratio, a clamped like the
+    real-shape rules."""
+    a, b, bi = O.beta_shape(O.BETA_PAPER, 0.25, 512)
+    assert (np.float32(a), b, bi) == (np.float32(0.25), 1024.0, 1024)
+    a, b, bi = O.beta_shape(O.BETA_PAPER, 0.25, 513)
+    assert (np.float32(a), b, bi) == (np.float32(0.25), 1026.0, 0)
+    a, b, bi = O.beta_shape(O.BETA_PAPER, 0.0, 2000)
+    assert (a, b, bi) == (2.0 ** -20, 4000.0, 0)
+
+
+@pytest.mark.parametrize("a,b", [(0.2, 1026), (0.9, 1500)])
+def test_beta_real_at_paper_shapes_beyond_1024(a, b):
+    """The shapes the paper schedule reaches after stage 512 (small a, b in
+    the thousands): the Gamma ratio against scipy's Beta."""
+    s = np.array([O.beta_real(KEY, a, float(b), j, 23, 0) for j in range(8000)], np.float64)
+    B = st.beta(a, b)
+    ok = s > 1e-30  # below this fp32 resolves nothing that the KS test could use
+    assert abs(np.mean(~ok) - B.cdf(1e-30)) < 0.02
+    lo = B.cdf(1e-30)
+    assert st.kstest(s[ok], lambda x: (B.cdf(x) - lo) / (1 - lo)).pvalue > 1e-3
+
+
 @pytest.mark.parametrize("p1,p2,ratio,t", [(0.3, 0.01, 1.0, 1), (0.3, 0.05, 0.5, 3),
                                            (0.6, 0.02, 0.9, 2), (0.1, 0.001, 0.2, 5)])
 def test_shape_mean_variance_moments(p1, p2, ratio, t):
