@@ -452,6 +452,53 @@ def run_batched(args):
             "autotune": tuning}
 
 
+def run_sweep_bench(args):
+    """Parallelism sweep (Sec. 4.1): levels x trials runs of 1000 samples,
+    120 days, P = 1e7, each stopped on the stage that reached 1000 simulation
+    runs; a step is one whole sweep.  Reports the simulated particle-days per
+    second over the sweep and the per-level summary of the last sweep."""
+    import torch
+
+    import paper_2106_15508_gb300 as G
+    from paper_2106_15508_gb300 import build as B
+    from paper_2106_15508_gb300 import sweep as S
+    from paper_2106_15508_gb300 import workloads as WL
+
+    B.build()
+    G.lib()
+    levels = tuple(args.levels) if args.levels else S.LEVELS
+    cfgs = S.sweep_configs(levels, args.trials)
+    obs = synthetic_obs(G, WL, cfgs[0], torch)[0]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        S.run_sweep(cfgs, obs, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    days = launches = 0
+    for _ in range(args.steps):
+        flush.fill_(1)  # L2 flush between steps
+        curves = S.run_sweep(cfgs, obs, stream=stream.cuda_stream)
+        days += sum(c.sim_days for c in curves)
+        launches += sum(c.launches for c in curves)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    clk = clocks.stop()
+    summ = S.summarise(curves)
+    return {"metric": METRIC, "value": days / secs, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "sweep_levels%s_trials%d_n1000_t120_p1e7_budget1000" % (
+                           "-".join(str(m) for m in levels), args.trials),
+                       "step": "one whole sweep (every trial to its stopping stage)",
+                       "l2": "flushed between steps (256 MB write)"},
+            "gpu_launches": launches, "clocks": clk,
+            "sweep": {str(k): v for k, v in summ.items()}}
+
+
 def cpu_baseline(stats, w):
     """The oracle as it stands on the host cores, on a bounded sample of the
     step: a batch of simulations and a block of weight rows, each timed,
@@ -713,7 +760,10 @@ def main():
                          "error bound recomputed exactly); 0: FP32 CUDA cores only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="single",
-                    choices=["single", "batched", "eps_final", "passes"])
+                    choices=["single", "batched", "eps_final", "passes", "sweep"])
+    ap.add_argument("--levels", type=int, nargs="*", default=None,
+                    help="sweep: simulations per batch (default 10 100 1000 10000 100000)")
+    ap.add_argument("--trials", type=int, default=10, help="sweep: trials per level")
     ap.add_argument("--pass-n", type=int, default=1 << 28)
     ap.add_argument("--generations", type=int, default=8)
     ap.add_argument("--surrogate-steps", type=int, default=32)
@@ -736,6 +786,8 @@ def main():
         line = run_eps_final(args)
     elif args.workload == "passes":
         line = run_passes(args)
+    elif args.workload == "sweep":
+        line = run_sweep_bench(args)
     else:
         line = run_gpu(args)
     if line is not None:

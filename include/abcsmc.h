@@ -49,6 +49,7 @@ extern "C" {
 #define ABC_OK 0
 #define ABC_STOP_BUDGET 1       /* a generation used max_batches batches before N acceptances */
 #define ABC_STOP_TARGET 2       /* abc_run reached eps_target                           */
+#define ABC_STOP_TOTAL 3        /* the run used max_total_batches batches (Sec. 4.1)     */
 #define ABC_E_INVAL (-1)        /* bad argument or configuration                         */
 #define ABC_E_NOMEM (-2)        /* device allocation failed                              */
 #define ABC_E_CUDA (-3)         /* a CUDA runtime call or kernel launch failed           */
@@ -140,7 +141,13 @@ typedef struct {
    * [2^-20, 2^20]. */
   float beta_p1;
   float beta_p2;
-  int32_t pad_end;
+  /* Run budget (Sec. 4.1: each trial stops on the stage that reached 1000
+   * simulation runs, a simulation run being one batch of M parallel
+   * simulations, and that stage finishes): generation 0 counts ceil(N / M)
+   * batches, generation t its own; once a generation ends with the count at
+   * or above max_total_batches, later generations do not run
+   * (ABC_STOP_TOTAL).  0: no budget. */
+  int32_t max_total_batches;
 } abc_config;
 
 /* Fill a config with the paper's defaults (SAIRD, binomial flows, alpha 0.5,
@@ -386,10 +393,12 @@ typedef struct {
 ABC_API int abc_init(const abc_config* cfg, const int32_t* obs, void* stream, abc_ctx** out);
 /* Run one generation: the first call runs stage 0 (prior); later calls
  * run t = 1, 2, ...  Returns ABC_STOP_BUDGET (population unchanged) when
- * max_batches batches did not yield N acceptances. */
+ * max_batches batches did not yield N acceptances, and ABC_STOP_TOTAL
+ * (nothing runs) once the run budget max_total_batches is used up. */
 ABC_API int abc_generation(abc_ctx* ctx);
 /* Run generations until n_generations exist or eps_t <= eps_target
- * (eps_target <= 0 disables it); returns the last generation's status. */
+ * (eps_target <= 0 disables it) or the run budget is used up; returns the
+ * last generation's status (ABC_STOP_TOTAL for the budget). */
 ABC_API int abc_run(abc_ctx* ctx, int32_t n_generations, double eps_target);
 /* Copy the population: u [8][N] float, dist, W double[N], s float[N] and
  * anc int32[N] (ancestor index in the previous population, -1 at t = 0);
@@ -452,7 +461,10 @@ ABC_API void abc_mlp_free(abc_mlp* m);
  * GPU.  Results equal those of separate contexts with the same configs bit
  * for bit (same kernels, same Philox counters).  A run whose generation uses
  * up its batch budget stops (status ABC_STOP_BUDGET in its stats) and is
- * skipped afterwards; the others continue. */
+ * skipped afterwards; the others continue.  A run whose run budget
+ * (max_total_batches) is used up stops the same way after its last
+ * generation (status ABC_OK there; the start kernel of the next launch
+ * skips it). */
 typedef struct abc_batch abc_batch;
 /* cfgs: host array of n_runs configs; obs: host array of n_runs host
  * pointers to int32 [3][T_r+1] series (entries may be NULL for the toy). */
@@ -460,7 +472,10 @@ ABC_API int abc_batch_init(const abc_config* cfgs, int32_t n_runs, const int32_t
                            void* stream, abc_batch** out);
 /* First call: stage 0 of every run; later calls: one graph launch. */
 ABC_API int abc_batch_generation(abc_batch* b);
+/* Generations until n_generations exist or no run is active. */
 ABC_API int abc_batch_run(abc_batch* b, int32_t n_generations);
+/* Runs that have not stopped (budget, run budget); before stage 0 all. */
+ABC_API int32_t abc_batch_active(const abc_batch* b);
 ABC_API int32_t abc_batch_runs(const abc_batch* b);
 ABC_API int32_t abc_batch_generations(const abc_batch* b);
 ABC_API int abc_batch_get_stats(abc_batch* b, int32_t run, int32_t t, abc_gen_stats* out);

@@ -13,7 +13,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libabcsmc.so")
 
-ABC_OK, ABC_STOP_BUDGET, ABC_STOP_TARGET = 0, 1, 2
+ABC_OK, ABC_STOP_BUDGET, ABC_STOP_TARGET, ABC_STOP_TOTAL = 0, 1, 2, 3
 ABC_E_TOO_LARGE = -7
 ABC_NOALLOC_MAX_N = 1 << 24
 ABC_MODEL_SAIRD, ABC_MODEL_GAUSS_TOY = 0, 1
@@ -35,7 +35,7 @@ EXPORTS = (
     "abc_init", "abc_generation", "abc_run", "abc_get_population", "abc_get_stats",
     "abc_generations", "abc_get_state", "abc_set_state", "abc_free", "abc_strerror",
     "abc_batch_init", "abc_batch_generation", "abc_batch_run", "abc_batch_runs",
-    "abc_batch_generations", "abc_batch_get_stats", "abc_batch_get_population",
+    "abc_batch_generations", "abc_batch_active", "abc_batch_get_stats", "abc_batch_get_population",
     "abc_batch_autotune", "abc_batch_tuning", "abc_batch_free",
     "abc_screen", "abc_ex2_probe", "abc_radix_sort", "abc_predict_scratch_bytes", "abc_predict",
     "abc_predict_population",
@@ -56,7 +56,7 @@ class AbcConfig(C.Structure):
         ("surrogate", C.c_int32), ("surrogate_start", C.c_int32), ("surrogate_steps", C.c_int32),
         ("surrogate_batch", C.c_int32), ("surrogate_lr", C.c_float), ("surrogate_tau", C.c_float),
         ("surrogate_rho_min", C.c_float), ("audit_frac", C.c_float), ("surrogate_ring", C.c_int32),
-        ("beta_p1", C.c_float), ("beta_p2", C.c_float), ("pad_end", C.c_int32),
+        ("beta_p1", C.c_float), ("beta_p2", C.c_float), ("max_total_batches", C.c_int32),
     ]
 
 
@@ -124,6 +124,7 @@ _SIGS = {
     "abc_batch_run": (C.c_int, [_V, _I32]),
     "abc_batch_runs": (C.c_int32, [_V]),
     "abc_batch_generations": (C.c_int32, [_V]),
+    "abc_batch_active": (C.c_int32, [_V]),
     "abc_batch_get_stats": (C.c_int, [_V, _I32, _I32, C.POINTER(AbcGenStats)]),
     "abc_batch_get_population": (C.c_int, [_V, _I32, _V, _V, _V, _V, _V, _I32]),
     "abc_batch_autotune": (C.c_int, [_V, C.c_char_p]),
@@ -305,12 +306,13 @@ def abc_init(cfg, obs_host, stream=None):
 
 
 def abc_generation(ctx):
-    return _check(lib().abc_generation(ctx), "abc_generation", ok=(ABC_OK, ABC_STOP_BUDGET))
+    return _check(lib().abc_generation(ctx), "abc_generation",
+                  ok=(ABC_OK, ABC_STOP_BUDGET, ABC_STOP_TOTAL))
 
 
 def abc_run(ctx, n_generations, eps_target=0.0):
     return _check(lib().abc_run(ctx, n_generations, eps_target), "abc_run",
-                  ok=(ABC_OK, ABC_STOP_BUDGET, ABC_STOP_TARGET))
+                  ok=(ABC_OK, ABC_STOP_BUDGET, ABC_STOP_TARGET, ABC_STOP_TOTAL))
 
 
 def abc_get_population(ctx, u=None, dist=None, W=None, s=None, anc=None, on_device=False):
@@ -383,6 +385,10 @@ def abc_batch_runs(b):
 
 def abc_batch_generations(b):
     return lib().abc_batch_generations(b)
+
+
+def abc_batch_active(b):
+    return lib().abc_batch_active(b)
 
 
 def abc_batch_get_stats(b, run, t):

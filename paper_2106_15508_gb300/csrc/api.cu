@@ -85,7 +85,7 @@ void stage_shapes(const abc_config& c, double eps, double eps1, int32_t t, int32
                   abc_gen_stats* g) {
   const float ratio = eps1 > 0.0 ? static_cast<float>(eps / eps1) : 1.0f;
   const BetaRule r = beta_rule(c);
-  if (c.beta_mode >= ABC_BETA_REAL) {
+  if (c.beta_mode >= ABC_BETA_REAL || (c.beta_mode == ABC_BETA_PAPER && bb == 0)) {
     beta_real_shape(r, ratio, t, &g->beta_a, &g->beta_bf);
     g->beta_b = 0;
   } else {
@@ -103,6 +103,7 @@ int check_smc(const abc_config* c) {
   if (c->weight_mode != ABC_W_PAPER && c->weight_mode != ABC_W_IMPORTANCE) return ABC_E_INVAL;
   if (c->weight_prec != ABC_P_FP32 && c->weight_prec != ABC_P_BF16_TC) return ABC_E_INVAL;
   if (c->max_batches < 1 || c->max_batches > 65535) return ABC_E_INVAL;
+  if (c->max_total_batches < 0) return ABC_E_INVAL;
   if (c->max_redraw < 1 || c->max_redraw > (1 << 23)) return ABC_E_INVAL;
   if (c->surrogate) {
     if (c->surrogate != 1 || c->surrogate_start < 1 || c->surrogate_steps < 0 ||
@@ -156,6 +157,7 @@ ABC_API const char* abc_strerror(int code) {
     case ABC_OK: return "ok";
     case ABC_STOP_BUDGET: return "generation stopped: batch budget used before N acceptances";
     case ABC_STOP_TARGET: return "run stopped: tolerance target reached";
+    case ABC_STOP_TOTAL: return "run stopped: run budget of batches used";
     case ABC_E_INVAL: return "invalid argument or configuration";
     case ABC_E_NOMEM: return "device allocation failed";
     case ABC_E_CUDA: return "CUDA runtime error";
@@ -413,6 +415,7 @@ struct abc_ctx {
   int cur = 0;
   int32_t gen = 0;
   double eps1_host = 0.0;
+  int64_t batches_total = 0;  // run budget count (Sec. 4.1 simulation runs)
   std::vector<abc_gen_stats> stats;
   std::vector<void*> allocs;
   // device buffers
@@ -616,8 +619,10 @@ int generation_t(abc_ctx* c) {
   const int32_t t = c->gen;
   const int cur = c->cur, nxt = 1 - c->cur;
   const int paper_beta = c->cfg.beta_mode == ABC_BETA_PAPER;
-  const int32_t bb = paper_beta ? 2 * t : c->cfg.beta_mode == ABC_BETA_FIXED ? c->cfg.beta_b : 0;
-  if (bb > 1024 || t > 32767) return ABC_E_INVAL;
+  // paper schedule: integer b = 2t up to stage 512, then 0 (the Gamma ratio)
+  const int32_t bb = paper_beta ? (t <= 512 ? 2 * t : 0)
+                                : c->cfg.beta_mode == ABC_BETA_FIXED ? c->cfg.beta_b : 0;
+  if (t > 32767) return ABC_E_INVAL;
   BetaRule rule = beta_rule(c->cfg);
   rule.b = bb;
   double* eps = c->scal + 0;
@@ -886,10 +891,17 @@ ABC_API int abc_init(const abc_config* cfg, const int32_t* obs, void* stream, ab
 
 ABC_API int abc_generation(abc_ctx* c) {
   if (!c) return ABC_E_INVAL;
+  // run budget: the generation that reached it was the last
+  if (c->gen > 0 && c->cfg.max_total_batches > 0 &&
+      c->batches_total >= c->cfg.max_total_batches)
+    return ABC_STOP_TOTAL;
   ABC_CUDA_TRY(cudaEventRecord(c->ev0, c->st));
   const int64_t l0 = g_launches.load();
-  const int rc = c->gen == 0 ? generation0(c) : generation_t(c);
+  const bool first = c->gen == 0;
+  const int rc = first ? generation0(c) : generation_t(c);
   if (rc < 0) return rc;
+  // stage 0 stands for its N prior draws in batches of M simulations
+  c->batches_total += first ? ceil_div(c->N, c->M) : c->stats.back().batches;
   c->stats.back().launches = g_launches.load() - l0;
   ABC_CUDA_TRY(cudaEventRecord(c->ev1, c->st));
   ABC_CUDA_TRY(cudaEventSynchronize(c->ev1));
@@ -965,6 +977,7 @@ struct StateHeader {
   uint32_t run_id;
   int32_t gen;
   double eps1;
+  int64_t batches_total;  // run budget count
 };
 }  // namespace
 
@@ -979,13 +992,14 @@ ABC_API int abc_get_state(abc_ctx* c, void* buf, size_t* len) {
   }
   if (*len < need || c->gen == 0) return ABC_E_INVAL;
   StateHeader h{};
-  std::memcpy(h.magic, "ABCSMC01", 8);
+  std::memcpy(h.magic, "ABCSMC02", 8);
   h.N = c->N;
   h.T = c->T;
   h.seed = c->cfg.seed;
   h.run_id = c->cfg.run_id;
   h.gen = c->gen;
   h.eps1 = c->eps1_host;
+  h.batches_total = c->batches_total;
   char* p = static_cast<char*>(buf);
   std::memcpy(p, &h, sizeof h);
   p += sizeof h;
@@ -1011,8 +1025,8 @@ ABC_API int abc_set_state(abc_ctx* c, const void* buf, size_t len) {
   const size_t N = static_cast<size_t>(c->N);
   const size_t need = sizeof(StateHeader) + N * (8 * sizeof(float) + 2 * sizeof(double) +
                                                  sizeof(float) + sizeof(int32_t));
-  if (std::memcmp(h.magic, "ABCSMC01", 8) != 0 || h.N != c->N || h.T != c->T || len < need ||
-      h.gen < 1)
+  if (std::memcmp(h.magic, "ABCSMC02", 8) != 0 || h.N != c->N || h.T != c->T || len < need ||
+      h.gen < 1 || h.gen > 32767 || h.batches_total < 0)
     return ABC_E_STATE;
   const char* p = static_cast<const char*>(buf) + sizeof h;
   const int k = c->cur;
@@ -1029,6 +1043,7 @@ ABC_API int abc_set_state(abc_ctx* c, const void* buf, size_t len) {
   ABC_CUDA_TRY(cudaStreamSynchronize(c->st));
   c->gen = h.gen;
   c->eps1_host = h.eps1;
+  c->batches_total = h.batches_total;
   c->stats.resize(static_cast<size_t>(h.gen));
   return ABC_OK;
 }
@@ -1222,6 +1237,7 @@ ABC_API int abc_batch_init(const abc_config* cfgs, int32_t n_runs, const int32_t
   for (int32_t r = 0; r < n_runs; ++r) {
     std::memset(&b->host[r], 0, sizeof(RunDev));
     b->host[r].max_batches = cfgs[r].max_batches;
+    b->host[r].max_total = cfgs[r].max_total_batches;
     b->br[r].v = ctx_view(b->runs[r]);
     b->br[r].dev = b->dev + r;
   }
@@ -1254,6 +1270,10 @@ ABC_API int abc_batch_generation(abc_batch* b) {
       if (rc != ABC_OK) return rc < 0 ? rc : ABC_E_CUDA;
       b->stats[r].push_back(b->runs[r]->stats.back());
       b->host[r].t = 1;
+      b->host[r].batches_total = b->runs[r]->batches_total;
+      // a run budget used up by stage 0 alone: no generation runs
+      if (b->host[r].max_total > 0 && b->host[r].batches_total >= b->host[r].max_total)
+        b->host[r].done = 1;
     }
     ABC_CUDA_TRY(cudaMemcpyAsync(b->dev, b->host.data(), sizeof(RunDev) * R,
                                  cudaMemcpyHostToDevice, b->st));
@@ -1261,8 +1281,7 @@ ABC_API int abc_batch_generation(abc_batch* b) {
     b->gen = 1;
     return ABC_OK;
   }
-  for (size_t r = 0; r < R; ++r)
-    if (b->runs[r]->cfg.beta_mode == ABC_BETA_PAPER && 2 * b->gen > 1024) return ABC_E_INVAL;
+  if (b->gen > 32767) return ABC_E_INVAL;  // the stage fills 16 counter bits
   if (!b->exec) {
     const int rc = batch_build_graph(b);
     if (rc) return rc;
@@ -1303,6 +1322,7 @@ ABC_API int abc_batch_generation(abc_batch* b) {
     g.launches = b->br[r].fixed_launches + d.batches * b->br[r].body_launches;
     g.ms = ms;  // the whole graph (all runs)
     b->stats[r].push_back(g);
+    c->batches_total = d.batches_total;
     if (d.status == ABC_OK) {
       c->gen += 1;
       c->eps1_host = d.eps1;
@@ -1315,11 +1335,19 @@ ABC_API int abc_batch_generation(abc_batch* b) {
 
 ABC_API int abc_batch_run(abc_batch* b, int32_t n_generations) {
   if (!b) return ABC_E_INVAL;
-  while (b->gen < n_generations) {
+  while (b->gen < n_generations && (b->gen == 0 || abc_batch_active(b) > 0)) {
     const int rc = abc_batch_generation(b);
     if (rc != ABC_OK) return rc;
   }
   return ABC_OK;
+}
+
+ABC_API int32_t abc_batch_active(const abc_batch* b) {
+  if (!b) return 0;
+  if (b->gen == 0) return static_cast<int32_t>(b->runs.size());
+  int32_t n = 0;
+  for (const RunDev& d : b->host) n += d.done ? 0 : 1;
+  return n;
 }
 
 ABC_API int32_t abc_batch_runs(const abc_batch* b) {

@@ -13,7 +13,9 @@
 // branches of runs of different sizes and horizons overlap on the GPU.  All
 // Philox counters (generation, batch) are read from per-run device state, so
 // one instantiated graph serves every generation.  A run whose generation
-// exhausts its batch budget stops: its later branches are skipped by a flag.
+// exhausts its batch budget stops: its later branches are skipped by a flag,
+// and so are those of a run whose run budget (batches over all generations)
+// is used up.
 //
 // Launch shapes (simulator block size, column chunks of the weight pass) are
 // picked per shape class by a small autotuner that times the candidates on
@@ -35,8 +37,9 @@ __global__ void k_run_start(RunDev* r, int paper_beta, int fixed_b, cudaGraphCon
   r->off = r->done;
   r->b = 0;
   r->c1 = r->t << 16;
-  // integer b of the product form (0 under the real-shape rules)
-  r->beta_b = paper_beta ? static_cast<int>(2 * r->t) : fixed_b;
+  // integer b of the product form (0: the Gamma ratio, under the real-shape
+  // rules and for the paper's b = 2t above 1024)
+  r->beta_b = paper_beta ? (r->t <= 512u ? static_cast<int>(2 * r->t) : 0) : fixed_b;
   r->filled = 0;
   r->accepted = 0;
   r->exhausted = 0;
@@ -62,6 +65,9 @@ __global__ void k_run_finish(RunDev* r, long long N) {
   r->status = ok ? ABC_OK : ABC_STOP_BUDGET;
   r->off = ok ? 0 : 1;
   if (!ok) r->done = 1;
+  // run budget (Sec. 4.1): this generation is kept, later ones are skipped
+  r->batches_total += r->batches;
+  if (ok && r->max_total > 0 && r->batches_total >= r->max_total) r->done = 1;
 }
 
 // the new population becomes the current one (skipped when the run is off)

@@ -19,6 +19,9 @@ struct RunDev {
   long long accepted;
   long long exhausted;
   long long batches;
+  long long batches_total;  // run budget count: ceil(N / M) for stage 0, then every batch
+  int32_t max_total;        // run budget (0: none)
+  int32_t pad;
   double eps, eps1, ess;
 };
 

@@ -144,7 +144,13 @@ struct BetaRule {
 __host__ __device__ inline void beta_real_shape(const BetaRule& r, float ratio, int32_t t,
                                                 float* a_out, float* b_out) {
   float a, b;
-  if (r.mode == ABC_BETA_REAL) {
+  if (r.mode == ABC_BETA_PAPER) {
+    // Eq. 16 beyond the product form's 1024 uniforms (stage 513 on)
+    a = ratio;
+    if (!(a >= 0x1p-20f)) a = 0x1p-20f;
+    if (a > 0x1p20f) a = 0x1p20f;
+    b = static_cast<float>(2 * t);
+  } else if (r.mode == ABC_BETA_REAL) {
     a = r.p1;
     b = r.p2;
   } else {

@@ -323,7 +323,10 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
     ratio = e1 > 0.0 ? __double2float_rn(__ddiv_rn(*eps_p, e1)) : 1.0f;
   }
   if (rule.mode == ABC_BETA_PAPER) a_t = ratio;
-  const bool real_shape = rule.mode >= ABC_BETA_REAL;
+  // the Gamma ratio: the real-shape rules, and the paper schedule once b =
+  // 2t passes 1024 (integer b 0)
+  const bool real_shape =
+      rule.mode >= ABC_BETA_REAL || (rule.mode == ABC_BETA_PAPER && beta_b == 0);
   if (real_shape) beta_real_shape(rule, ratio, static_cast<int32_t>(c1 >> 16), &a_t, &b_t);
   float up[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   float s = 0.0f;
@@ -391,8 +394,13 @@ int launch_propose(const SimParams& p, const float* u, int64_t n, const uint64_t
                    cudaStream_t st, const uint32_t* c1_dev, const int* beta_b_dev,
                    const int* off_dev) {
   if (n <= 0 || slots < 0 || max_redraw < 1 || !beta_rule_ok(rule)) return ABC_E_INVAL;
-  const bool integer_b = rule.mode == ABC_BETA_PAPER || rule.mode == ABC_BETA_FIXED;
-  if (integer_b && !beta_b_dev && (rule.b < 1 || rule.b > 1024)) return ABC_E_INVAL;
+  if (rule.mode == ABC_BETA_FIXED && !beta_b_dev && (rule.b < 1 || rule.b > 1024))
+    return ABC_E_INVAL;
+  // paper schedule: integer b in 1..1024, or 0 for Beta(a_t, 2t) by the
+  // Gamma ratio at the stage t = c1 >> 16 >= 1
+  if (rule.mode == ABC_BETA_PAPER && !beta_b_dev &&
+      (rule.b < 0 || rule.b > 1024 || (rule.b == 0 && !c1_dev && (c1 >> 16) == 0)))
+    return ABC_E_INVAL;
   if (rule.mode != ABC_BETA_FIXED && rule.mode != ABC_BETA_REAL && (!eps || !eps1))
     return ABC_E_INVAL;
   // the scheduled real-shape rules read the stage t = c1 >> 16 >= 1

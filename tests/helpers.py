@@ -24,7 +24,7 @@ def oracle_smc(cfg, nthreads=8):
                       alpha=cfg.survival_alpha, beta_mode=cfg.beta_mode, beta_a=cfg.beta_a,
                       beta_b=cfg.beta_b, weight_mode=cfg.weight_mode,
                       max_batches=cfg.max_batches, max_redraw=cfg.max_redraw, nthreads=nthreads,
-                      beta_p1=cfg.beta_p1, beta_p2=cfg.beta_p2)
+                      beta_p1=cfg.beta_p1, beta_p2=cfg.beta_p2, max_total=cfg.max_total_batches)
 
 
 def saird_config(N, T, P, seed=1, **kw):
@@ -42,12 +42,13 @@ def oracle_obs(cfg):
     return obs, th, att
 
 
-def state_blob(cfg, gen, eps1, pop):
-    """abc_set_state layout: magic, N, T, seed, run_id, gen, eps1, then u
-    [8][N] f32, dist f64, W f64, s f32, anc i32."""
+def state_blob(cfg, gen, eps1, pop, batches_total=0):
+    """abc_set_state layout: magic, N, T, seed, run_id, gen, eps1, the run
+    budget count, then u [8][N] f32, dist f64, W f64, s f32, anc i32."""
     N = cfg.n_particles
     T = cfg.n_days if cfg.model == G.ABC_MODEL_SAIRD else 0
-    head = struct.pack("<8sqqQIid", b"ABCSMC01", N, T, cfg.seed, cfg.run_id, gen, eps1)
+    head = struct.pack("<8sqqQIidq", b"ABCSMC02", N, T, cfg.seed, cfg.run_id, gen, eps1,
+                       batches_total)
     return b"".join([head, np.ascontiguousarray(pop.u, np.float32).tobytes(),
                      np.ascontiguousarray(pop.d, np.float64).tobytes(),
                      np.ascontiguousarray(pop.W, np.float64).tobytes(),

@@ -52,9 +52,9 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(abc_config), offsetof(abc_config, population),
          offsetof(abc_config, seed), offsetof(abc_config, survival_alpha),
          offsetof(abc_config, max_redraw), sizeof(abc_gen_stats));
-  printf("%zu %zu %zu %zu %zu\n", offsetof(abc_gen_stats, eps), offsetof(abc_gen_stats, batches),
+  printf("%zu %zu %zu %zu %zu %zu\n", offsetof(abc_gen_stats, eps), offsetof(abc_gen_stats, batches),
          offsetof(abc_gen_stats, ms_weights), offsetof(abc_gen_stats, beta_bf),
-         offsetof(abc_config, beta_p2));
+         offsetof(abc_config, beta_p2), offsetof(abc_config, max_total_batches));
   return 0;
 }
 """
@@ -69,7 +69,7 @@ int main(void) {
             G.AbcConfig.survival_alpha.offset, G.AbcConfig.max_redraw.offset,
             ctypes.sizeof(G.AbcGenStats), G.AbcGenStats.eps.offset, G.AbcGenStats.batches.offset,
             G.AbcGenStats.ms_weights.offset, G.AbcGenStats.beta_bf.offset,
-            G.AbcConfig.beta_p2.offset]
+            G.AbcConfig.beta_p2.offset, G.AbcConfig.max_total_batches.offset]
     assert got == want
 
 

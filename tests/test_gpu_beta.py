@@ -75,6 +75,35 @@ def test_propose_real_shape_rules_bitexact(mode, p1, p2, t):
     assert np.array_equal(host(outs["flag"]), o["flag"])
 
 
+@pytest.mark.parametrize("t,eps", [(513, 1.5), (2000, 0.0)])
+def test_propose_paper_schedule_beyond_1024_bitexact(t, eps):
+    """Eq. 16 after stage 512: integer b 0 selects Beta(eps/eps1, 2t) by the
+    Gamma ratio (ratio 0 clamped to 2^-20)."""
+    n, slots = 2000, 3001
+    cfg = saird_config(n, 10, 1000, seed=13, beta_mode=G.ABC_BETA_PAPER)
+    m = oracle_model(cfg)
+    u = IN.clustered_particles(n, 5, 0.5, 0.2)
+    q = IN.quantised_weights(n, 6)
+    pre = np.cumsum(q.astype(np.uint64))
+    eps1 = 4.0
+    c1 = (t << 16) | 5
+    outs = dict(u=torch.empty((8, slots), dtype=torch.float32, device="cuda"),
+                s=torch.empty(slots, dtype=torch.float32, device="cuda"),
+                anc=torch.empty(slots, dtype=torch.int32, device="cuda"),
+                att=torch.empty(slots, dtype=torch.int32, device="cuda"),
+                flag=torch.empty(slots, dtype=torch.uint8, device="cuda"))
+    G.abc_propose(cfg, dev(u), n, dev(pre), dev(np.array([eps])), dev(np.array([eps1])),
+                  0.0, 0, slots, None, c1, outs["u"], outs["s"], outs["anc"], outs["att"],
+                  outs["flag"])
+    a, b, bi = O.beta_shape(G.ABC_BETA_PAPER, np.float32(eps / eps1), t)
+    assert bi == 0 and b == 2 * t
+    o = O.propose(m, u, pre, int(pre[-1]), a, 0, slots, c1, nthreads=8, beta_bf=b)
+    assert np.array_equal(host(outs["anc"]), o["anc"])
+    assert np.array_equal(host(outs["s"]).view(np.uint32), o["s"].view(np.uint32))
+    assert np.array_equal(host(outs["u"]).view(np.uint32), o["u"].view(np.uint32))
+    assert np.array_equal(host(outs["flag"]), o["flag"])
+
+
 def test_propose_rejects_stage_zero_for_scheduled_rules():
     cfg = saird_config(64, 10, 1000, beta_mode=G.ABC_BETA_MODE_CONC, beta_p1=0.2, beta_p2=10.0)
     u = np.full((8, 64), 0.5, np.float32)
