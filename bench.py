@@ -472,7 +472,7 @@ def run_sweep_bench(args):
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
-        S.run_sweep(cfgs, obs, stream=stream.cuda_stream)
+        S.run_sweep(cfgs, obs, stream=stream.cuda_stream, grouping=args.grouping)
     torch.cuda.synchronize()
     clocks = Clocks(0)
     clocks.start()
@@ -480,13 +480,16 @@ def run_sweep_bench(args):
     days = launches = 0
     for _ in range(args.steps):
         flush.fill_(1)  # L2 flush between steps
-        curves = S.run_sweep(cfgs, obs, stream=stream.cuda_stream)
+        curves = S.run_sweep(cfgs, obs, stream=stream.cuda_stream, grouping=args.grouping)
         days += sum(c.sim_days for c in curves)
         launches += sum(c.launches for c in curves)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
     clk = clocks.stop()
     summ = S.summarise(curves)
+    if args.grouping == "level":
+        for M, v in summ.items():
+            v["level_s"] = next(c.group_s for c in curves if c.M == M)
     return {"metric": METRIC, "value": days / secs, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -494,6 +497,7 @@ def run_sweep_bench(args):
             "config": {"workload": "sweep_levels%s_trials%d_n1000_t120_p1e7_budget1000" % (
                            "-".join(str(m) for m in levels), args.trials),
                        "step": "one whole sweep (every trial to its stopping stage)",
+                       "grouping": args.grouping,
                        "l2": "flushed between steps (256 MB write)"},
             "gpu_launches": launches, "clocks": clk,
             "sweep": {str(k): v for k, v in summ.items()}}
@@ -764,6 +768,8 @@ def main():
     ap.add_argument("--levels", type=int, nargs="*", default=None,
                     help="sweep: simulations per batch (default 10 100 1000 10000 100000)")
     ap.add_argument("--trials", type=int, default=10, help="sweep: trials per level")
+    ap.add_argument("--grouping", default="all", choices=["all", "level"],
+                    help="sweep: one batch of all runs, or one batch per level")
     ap.add_argument("--pass-n", type=int, default=1 << 28)
     ap.add_argument("--generations", type=int, default=8)
     ap.add_argument("--surrogate-steps", type=int, default=32)

@@ -9,10 +9,10 @@ levels by the best tolerance, the simulation runs needed to reach it and the
 spread of both over the trials (Sec. 4, evaluation metrics).
 
 Here every trial is one run of a graph-captured batch (abc_batch_*), with
-the run budget in abc_config.max_total_batches; the trials of one level
-advance together, one graph launch per stage.  A level is one batch of its
-own, so that long runs (100k simulations per batch: one batch per stage,
-about a thousand stages) carry no branches of runs that stopped long ago.
+the run budget in abc_config.max_total_batches; the runs of a batch advance
+together, one graph launch per stage, their branches overlapping on the GPU.
+By default the whole sweep is one batch: the low levels' runs are chains of
+small, latency-bound batches that then overlap the high levels' large ones.
 Synthetic observations stand in for the Italy series.
 
 This module holds host logic only (configs, the driver loop, the summary);
@@ -41,6 +41,7 @@ class Curve:
     sim_days: int      # simulated particle-days, stage 0 included
     launches: int      # kernels launched for the run
     status: int        # of the last stage: ABC_OK, or ABC_STOP_BUDGET
+    group_s: float = 0.0  # wall time of the batch the run was part of
 
 
 def sweep_configs(levels=LEVELS, trials=10, N=1000, budget=1000, T=120, P=10_000_000, seed=1,
@@ -77,21 +78,28 @@ def _curve(b, r, cfg, trial):
                  launches, status)
 
 
-def run_sweep(cfgs, obs, stream=None, max_stages=32767):
-    """Runs every config (grouped by M, one batch per group, in order of
-    first appearance) on the observed series obs (host int32 [3][T+1]) until
-    each run has stopped; returns the curves in config order."""
+def run_sweep(cfgs, obs, stream=None, max_stages=32767, grouping="all"):
+    """Runs every config on the observed series obs (host int32 [3][T+1])
+    until each run has stopped, as one batch ("all") or one batch per level
+    ("level", in order of first appearance); returns the curves in config
+    order.  A trial's index counts the earlier configs of its level."""
+    import time
+
     groups = {}
     for i, c in enumerate(cfgs):
-        groups.setdefault(c.batch_size, []).append(i)
+        groups.setdefault(0 if grouping == "all" else c.batch_size, []).append(i)
     curves = [None] * len(cfgs)
-    for M, idx in groups.items():
+    for idx in groups.values():
         sub = [cfgs[i] for i in idx]
+        t0 = time.perf_counter()
         b = abc_batch_init(sub, [obs] * len(sub), stream=stream)
         try:
             abc_batch_run(b, max_stages + 1)
+            secs = time.perf_counter() - t0
             for k, i in enumerate(idx):
-                curves[i] = _curve(b, k, cfgs[i], k)
+                trial = sum(c.batch_size == cfgs[i].batch_size for c in cfgs[:i])
+                curves[i] = _curve(b, k, cfgs[i], trial)
+                curves[i].group_s = secs
         finally:
             abc_batch_free(b)
     return curves
@@ -100,7 +108,8 @@ def run_sweep(cfgs, obs, stream=None, max_stages=32767):
 def summarise(curves):
     """Per level (ascending M): the best tolerance of each trial (its
     smallest eps_t), the simulation runs at the first stage that reached it,
-    the runs in all, with medians, quartiles and the spread of log10 of the
+    the runs in all, the runs at the first stage within a factor 2 of the
+    trial's best, with medians, quartiles and the spread of log10 of the
     best tolerance over the trials; trials that ended on a stage which used
     up its per-stage batch budget are counted as stuck."""
     out = {}
@@ -111,6 +120,8 @@ def summarise(curves):
         to_best = np.array([c.runs[int(np.argmax(c.eps == c.eps.min()))] for c in done],
                            np.float64)
         total = np.array([c.runs[-1] if len(c.runs) else 0 for c in cs], np.float64)
+        to_2x = np.array([c.runs[int(np.argmax(c.eps <= 2.0 * c.eps.min()))] for c in done],
+                         np.float64)
 
         def q(a, p):
             return float(np.percentile(a, p)) if len(a) else math.nan
@@ -122,7 +133,8 @@ def summarise(curves):
                   "best_eps_q75": q(best, 75),
                   "log10_best_eps_std": float(lb.std()) if len(lb) else math.nan,
                   "runs_to_best_median": q(to_best, 50), "runs_to_best_q25": q(to_best, 25),
-                  "runs_to_best_q75": q(to_best, 75), "runs_total_median": q(total, 50),
+                  "runs_to_best_q75": q(to_best, 75), "runs_to_2x_best_median": q(to_2x, 50),
+                  "runs_total_median": q(total, 50),
                   "stages_median": q(np.array([len(c.eps) for c in cs], np.float64), 50),
                   "sim_days": int(sum(c.sim_days for c in cs))}
     return out

@@ -39,10 +39,13 @@ def test_summary_on_known_curves():
     # best tolerances 20 and 10; first stage reaching them at 700 and 1200 runs
     assert a["best_eps_median"] == 15.0
     assert a["runs_to_best_median"] == 950.0
+    # within 2x of the best (40 and 20): 700 and 1200 runs
+    assert a["runs_to_2x_best_median"] == 950.0
     assert a["runs_total_median"] == 1100.0           # totals 1100, 1200, 0
     assert a["stages_median"] == 2.0
     assert math.isclose(a["log10_best_eps_std"], np.std(np.log10([20.0, 10.0])))
     assert a["sim_days"] == 12
     b = s[100]
     assert b["best_eps_median"] == 4.0 and b["runs_to_best_median"] == 12.0
+    assert b["runs_to_2x_best_median"] == 12.0
     assert b["log10_best_eps_std"] == 0.0
