@@ -768,8 +768,8 @@ def main():
     ap.add_argument("--levels", type=int, nargs="*", default=None,
                     help="sweep: simulations per batch (default 10 100 1000 10000 100000)")
     ap.add_argument("--trials", type=int, default=10, help="sweep: trials per level")
-    ap.add_argument("--grouping", default="all", choices=["all", "level"],
-                    help="sweep: one batch of all runs, or one batch per level")
+    ap.add_argument("--grouping", default="all", choices=["all", "level", "run"],
+                    help="sweep: one batch of all runs, one per level, or one per run")
     ap.add_argument("--pass-n", type=int, default=1 << 28)
     ap.add_argument("--generations", type=int, default=8)
     ap.add_argument("--surrogate-steps", type=int, default=32)

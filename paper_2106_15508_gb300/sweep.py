@@ -80,16 +80,21 @@ def _curve(b, r, cfg, trial):
 
 def run_sweep(cfgs, obs, stream=None, max_stages=32767, grouping="all"):
     """Runs every config on the observed series obs (host int32 [3][T+1])
-    until each run has stopped, as one batch ("all") or one batch per level
-    ("level", in order of first appearance); returns the curves in config
-    order.  A trial's index counts the earlier configs of its level."""
+    until each run has stopped; returns the curves in config order (a
+    trial's index counts the earlier configs of its level).  grouping:
+    "all", one batch of every run; "level", one batch per level, one after
+    another; "run", one batch per run, each driven by a host thread of its
+    own, so that no run waits at a stage boundary for the slowest run of its
+    batch."""
     import time
 
     groups = {}
     for i, c in enumerate(cfgs):
-        groups.setdefault(0 if grouping == "all" else c.batch_size, []).append(i)
+        key = 0 if grouping == "all" else c.batch_size if grouping == "level" else i
+        groups.setdefault(key, []).append(i)
     curves = [None] * len(cfgs)
-    for idx in groups.values():
+
+    def one(idx):
         sub = [cfgs[i] for i in idx]
         t0 = time.perf_counter()
         b = abc_batch_init(sub, [obs] * len(sub), stream=stream)
@@ -102,6 +107,15 @@ def run_sweep(cfgs, obs, stream=None, max_stages=32767, grouping="all"):
                 curves[i].group_s = secs
         finally:
             abc_batch_free(b)
+
+    if grouping == "run":
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=len(groups)) as ex:
+            for f in [ex.submit(one, idx) for idx in groups.values()]:
+                f.result()
+    else:
+        for idx in groups.values():
+            one(idx)
     return curves
 
 

@@ -23,16 +23,17 @@ def _setup():
     G.lib()
 
 
-def test_reduced_sweep_matches_oracle_runs():
+@pytest.mark.parametrize("grouping", ["all", "level", "run"])
+def test_reduced_sweep_matches_oracle_runs(grouping):
     cfgs = S.sweep_configs(levels=(8, 32, 256), trials=3, N=64, budget=24, T=30, P=100_000,
                            max_batches=4096)
     obs, _, _ = oracle_obs(cfgs[0])
-    curves = S.run_sweep(cfgs, obs)
+    curves = S.run_sweep(cfgs, obs, grouping=grouping)
     for cfg, cv in zip(cfgs, curves):
         _, ost = O.run(oracle_model(cfg, obs), oracle_smc(cfg), 10_000)
         ok = [s for s in ost if s.status == 0]
         runs = -(-cfg.n_particles // cfg.batch_size) + np.cumsum([s.batches for s in ost])
-        assert cv.M == cfg.batch_size
+        assert cv.M == cfg.batch_size and cv.trial == cfg.run_id % 3
         assert np.array_equal(cv.eps, np.array([s.eps for s in ok]))
         assert np.array_equal(cv.runs, runs[:len(ok)])
         assert cv.status == (ost[-1].status if ost else G.ABC_OK)
