@@ -63,7 +63,8 @@ extern "C" {
 #define ABC_MODEL_GAUSS_TOY 1   /* x ~ N(theta, I8), distance ||x - x_obs|| (test model)  */
 #define ABC_SIM_BINOMIAL 0      /* exact-count binomial competing risks (default)        */
 #define ABC_SIM_PAPER_NORMAL 1  /* the paper's floor(Normal(h, sqrt h)) flows (Sec. 2.2) */
-#define ABC_BETA_PAPER 0        /* s ~ Beta(eps_t/eps_1, 2t)  (Eq. 16)                    */
+#define ABC_BETA_PAPER 0        /* s ~ Beta(eps_t/eps_1, 2t)  (Eq. 16); product form up  */
+                                /*   to t = 512, the Gamma ratio from t = 513 on          */
 #define ABC_BETA_FIXED 1        /* s ~ Beta(beta_a, beta_b)                               */
 /* Real-shape rules (Sec. 3.2 names the mean-variance and mode-concentration
  * parameterisations beside Eq. 16 without their schedules; here the location
@@ -231,7 +232,9 @@ ABC_API int abc_resample_prefix_noalloc(const double* d, const double* W, int64_
  * (WALK stream), u' = u_anc + sqrt(s) z; the first u' inside [0,1]^8 is kept,
  * else flag = 1.  a_t = beta_a, or in paper mode (cfg->beta_mode) a_t =
  * (float)(*eps / *eps1) (1 when *eps1 is 0) and b = beta_b as given (integer
- * b, product form).  Under the real-shape rules (ABC_BETA_REAL, _MEAN_VAR,
+ * b, product form; in paper mode 0 means Beta(a_t, 2t) by the Gamma ratio,
+ * a_t clamped to [2^-20, 2^20], t = c1 >> 16 >= 1, as generations from 513
+ * on draw it).  Under the real-shape rules (ABC_BETA_REAL, _MEAN_VAR,
  * _MODE_CONC) beta_a and beta_b are ignored: the shapes follow from
  * cfg->beta_p1, cfg->beta_p2, the ratio and the stage t = c1 >> 16 (t >= 1
  * for the last two), and s is drawn by the Gamma ratio (BETA stream, c2 =
