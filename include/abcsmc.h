@@ -314,6 +314,17 @@ ABC_API int abc_predict(const abc_config* cfg, const float* u, const double* W, 
  * Synchronises the stream. */
 ABC_API int abc_ex2_probe(double* ex2_per_second, void* stream);
 
+/* Self-check (no counterpart in the paper): the simulator and the logarithm
+ * replace two correctly rounded divisions on bounded operand domains by a
+ * shorter sequence (the hardware reciprocal approximation, one Newton step
+ * and Markstein's remainder correction).  which = 0 enumerates the
+ * logarithm's domain (n = m - 1, d = m + 1, every float m in
+ * [sqrt(2)/2, sqrt(2)], 8.4e6 pairs); which = 1 BINV's (a / k, every float a
+ * in [2^-100, 2^100], k = 2..111, 1.8e11 pairs).  *mismatches receives the
+ * count of pairs whose quotient differs in any bit from __fdiv_rn (0
+ * expected).  ABC_E_INVAL for another which.  Synchronises the stream. */
+ABC_API int abc_numerics_check(int32_t which, uint64_t* mismatches, void* stream);
+
 /* Stable LSD radix sort (no counterpart in the paper; the weight pass uses it
  * to put its rows and columns in spatial order): keys_out / vals_out = the n
  * pairs (keys[i], vals ? vals[i] : i) ordered by the low `bits` bits of the

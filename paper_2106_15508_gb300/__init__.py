@@ -37,7 +37,7 @@ EXPORTS = (
     "abc_batch_init", "abc_batch_generation", "abc_batch_run", "abc_batch_runs",
     "abc_batch_generations", "abc_batch_active", "abc_batch_get_stats", "abc_batch_get_population",
     "abc_batch_autotune", "abc_batch_tuning", "abc_batch_free",
-    "abc_screen", "abc_ex2_probe", "abc_radix_sort", "abc_predict_scratch_bytes", "abc_predict",
+    "abc_screen", "abc_ex2_probe", "abc_numerics_check", "abc_radix_sort", "abc_predict_scratch_bytes", "abc_predict",
     "abc_predict_population",
     "abc_mlp_param_count", "abc_mlp_create", "abc_mlp_set_params", "abc_mlp_get_params",
     "abc_mlp_scratch_bytes", "abc_mlp_grad", "abc_mlp_adam", "abc_mlp_forward", "abc_mlp_free",
@@ -132,6 +132,7 @@ _SIGS = {
     "abc_batch_free": (None, [_V]),
     "abc_screen": (C.c_int, [_V, _V, _V, _V, _I64, _V, C.c_uint32, _V, _V, _V]),
     "abc_ex2_probe": (C.c_int, [C.POINTER(C.c_double), _V]),
+    "abc_numerics_check": (C.c_int, [_I32, C.POINTER(C.c_uint64), _V]),
     "abc_radix_sort": (C.c_int, [_V, _V, _I64, _I32, _V, _V, _V]),
     "abc_predict_scratch_bytes": (_SZ, [_I64, _I64, _I32, _I32]),
     "abc_predict": (C.c_int, [_V, _V, _V, _I64, _I64, _I32, _V, _I32, _V, _V, _SZ, _V]),
@@ -433,6 +434,14 @@ def abc_ex2_probe(stream=None):
     """Sustained ex2.approx.f32 rate of this GPU (exponentials per second)."""
     r = C.c_double()
     _check(lib().abc_ex2_probe(C.byref(r), _stream(stream)), "abc_ex2_probe")
+    return r.value
+
+
+def abc_numerics_check(which, stream=None):
+    """Operand pairs of check `which` whose short division differs from
+    __fdiv_rn (0 expected)."""
+    r = C.c_uint64()
+    _check(lib().abc_numerics_check(which, C.byref(r), _stream(stream)), "abc_numerics_check")
     return r.value
 
 

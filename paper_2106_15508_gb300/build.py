@@ -21,7 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libabcsmc.so")
 SOURCES = ["api.cu", "simulate.cu", "particles.cu", "weights.cu", "weights_tc.cu", "batch.cu",
-           "surrogate.cu", "predict.cu", "sort.cu"]
+           "surrogate.cu", "predict.cu", "sort.cu", "numcheck.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -33,6 +33,7 @@ size_t weights_fp32_scratch_bytes(int64_t, int64_t, int mult = 1);
 size_t weights_tc_scratch_bytes(int64_t, int64_t, int mult = 1);
 int64_t weights_tc_tile_pairs();
 int ex2_probe(double* rate, cudaStream_t st);
+int numerics_check(int which, unsigned long long* bad_host, cudaStream_t st);
 size_t predict_scratch_bytes(int64_t N, int64_t R, int32_t days, int32_t nq);
 int launch_predict(const SimParams& p, const float* u, const double* W, int64_t N, int64_t R,
                    int32_t days, const double* quant, int32_t nq, int32_t* out, void* scratch,
@@ -378,6 +379,14 @@ ABC_API int abc_radix_sort(const uint32_t* keys, const int32_t* vals, int64_t n,
 ABC_API int abc_ex2_probe(double* ex2_per_second, void* stream) {
   if (!ex2_per_second) return ABC_E_INVAL;
   return ex2_probe(ex2_per_second, as_stream(stream));
+}
+
+ABC_API int abc_numerics_check(int32_t which, uint64_t* mismatches, void* stream) {
+  if (!mismatches) return ABC_E_INVAL;
+  unsigned long long bad = 0;
+  const int rc = numerics_check(which, &bad, as_stream(stream));
+  *mismatches = bad;
+  return rc;
 }
 
 ABC_API size_t abc_normalize_scratch_bytes(int64_t n) { return normalize_scratch_bytes(n); }

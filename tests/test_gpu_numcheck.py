@@ -1,0 +1,29 @@
+"""The short division sequence (reciprocal approximation, one Newton step,
+Markstein's remainder correction) that the logarithm and the BINV loop use
+on bounded operand domains equals CUDA's correctly rounded __fdiv_rn on
+every operand pair of those domains, enumerated on the device."""
+import pytest
+
+import paper_2106_15508_gb300 as G
+from paper_2106_15508_gb300 import build as B
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    G.lib()
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_division_domains_are_exact(which):
+    assert G.abc_numerics_check(which) == 0
+
+
+def test_unknown_check_is_rejected():
+    with pytest.raises(G.AbcError):
+        G.abc_numerics_check(7)
