@@ -316,8 +316,8 @@ ABC_API int abc_ex2_probe(double* ex2_per_second, void* stream);
 
 /* Self-check (no counterpart in the paper): the simulator and the logarithm
  * replace two correctly rounded divisions on bounded operand domains by a
- * shorter sequence (the hardware reciprocal approximation, one Newton step
- * and Markstein's remainder correction).  which = 0 enumerates the
+ * shorter sequence (the quotient by the hardware reciprocal approximation,
+ * corrected once by its exact remainder, after Markstein).  which = 0 enumerates the
  * logarithm's domain (n = m - 1, d = m + 1, every float m in
  * [sqrt(2)/2, sqrt(2)], 8.4e6 pairs); which = 1 BINV's (a / k, every float a
  * in [2^-100, 2^100], k = 2..111, 1.8e11 pairs).  *mismatches receives the

@@ -1,5 +1,5 @@
-"""The short division sequence (reciprocal approximation, one Newton step,
-Markstein's remainder correction) that the logarithm and the BINV loop use
+"""The short division sequence (the quotient by the reciprocal approximation,
+corrected once by its exact remainder, after Markstein) that the logarithm and the BINV loop use
 on bounded operand domains equals CUDA's correctly rounded __fdiv_rn on
 every operand pair of those domains, enumerated on the device."""
 import pytest
