@@ -320,9 +320,12 @@ ABC_API int abc_ex2_probe(double* ex2_per_second, void* stream);
  * corrected once by its exact remainder, after Markstein).  which = 0 enumerates the
  * logarithm's domain (n = m - 1, d = m + 1, every float m in
  * [sqrt(2)/2, sqrt(2)], 8.4e6 pairs); which = 1 BINV's (a / k, every float a
- * in [2^-100, 2^100], k = 2..111, 1.8e11 pairs).  *mismatches receives the
- * count of pairs whose quotient differs in any bit from __fdiv_rn (0
- * expected).  ABC_E_INVAL for another which.  Synchronises the stream. */
+ * in [2^-100, 2^100], k = 2..111, 1.8e11 pairs); which = 2 the square root
+ * that replaces __fsqrt_rn in the binomial and Box-Muller draws the same way
+ * (every float in [2^-24, 2^32), 4.7e8 values).  *mismatches receives the
+ * count of operands whose result differs in any bit from CUDA's correctly
+ * rounded one (0 expected).  ABC_E_INVAL for another which.  Synchronises
+ * the stream. */
 ABC_API int abc_numerics_check(int32_t which, uint64_t* mismatches, void* stream);
 
 /* Stable LSD radix sort (no counterpart in the paper; the weight pass uses it

@@ -1,7 +1,8 @@
 // numcheck.cu -- device-side exhaustive checks of the short arithmetic
-// sequences that stand in for CUDA's correctly rounded operations on bounded
-// domains (numerics.cuh): each check runs both on every operand of the
-// domain on this GPU and counts the results that differ in any bit.
+// sequences that stand in for CUDA's correctly rounded division and square
+// root on bounded domains (div_nr, sqrt_nr in numerics.cuh): each check runs
+// both on every operand of the domain on this GPU and counts the results
+// that differ in any bit.
 #include <cstring>
 
 #include "common.cuh"
@@ -43,6 +44,18 @@ static uint32_t bits_of(float x) {
   return b;
 }
 
+// domain 2: every float x in [2^-24, 2^32) (the square roots of the
+// binomial draw and of the Box-Muller radius)
+__global__ void k_check_sqrt(uint32_t lo, uint32_t hi, unsigned long long* bad) {
+  unsigned long long c = 0;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t b = lo + blockIdx.x * blockDim.x + threadIdx.x; b <= hi && b >= lo; b += stride) {
+    const float x = __uint_as_float(b);
+    c += __float_as_uint(sqrt_nr(x)) != __float_as_uint(__fsqrt_rn(x));
+  }
+  if (c) atomicAdd(bad, c);
+}
+
 int numerics_check(int which, unsigned long long* bad_host, cudaStream_t st) {
   uint32_t lo, hi;
   if (which == 0) {
@@ -51,6 +64,9 @@ int numerics_check(int which, unsigned long long* bad_host, cudaStream_t st) {
   } else if (which == 1) {
     lo = bits_of(0x1p-100f);
     hi = bits_of(0x1p100f);
+  } else if (which == 2) {
+    lo = bits_of(0x1p-24f);
+    hi = bits_of(0x1p32f) - 1u;
   } else {
     return ABC_E_INVAL;
   }
@@ -60,7 +76,8 @@ int numerics_check(int which, unsigned long long* bad_host, cudaStream_t st) {
   if (cudaMemsetAsync(bad, 0, sizeof *bad, st) != cudaSuccess) rc = ABC_E_CUDA;
   if (rc == ABC_OK) {
     if (which == 0) k_check_div_log<<<152 * 8, 256, 0, st>>>(lo, hi, bad);
-    else k_check_div_binv<<<152 * 8, 256, 0, st>>>(lo, hi, bad);
+    else if (which == 1) k_check_div_binv<<<152 * 8, 256, 0, st>>>(lo, hi, bad);
+    else k_check_sqrt<<<152 * 8, 256, 0, st>>>(lo, hi, bad);
     if (cudaGetLastError() != cudaSuccess) rc = ABC_E_CUDA;
   }
   if (rc == ABC_OK &&

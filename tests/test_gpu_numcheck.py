@@ -1,7 +1,10 @@
 """The short division sequence (the quotient by the reciprocal approximation,
 corrected once by its exact remainder, after Markstein) that the logarithm and the BINV loop use
 on bounded operand domains equals CUDA's correctly rounded __fdiv_rn on
-every operand pair of those domains, enumerated on the device."""
+every operand pair of those domains, and the square root of the binomial and
+Box-Muller draws (reciprocal-square-root approximation, one remainder
+correction) equals __fsqrt_rn on [2^-24, 2^32); all enumerated on the
+device."""
 import pytest
 
 import paper_2106_15508_gb300 as G
@@ -19,8 +22,8 @@ def _setup():
     G.lib()
 
 
-@pytest.mark.parametrize("which", [0, 1])
-def test_division_domains_are_exact(which):
+@pytest.mark.parametrize("which", [0, 1, 2])
+def test_short_sequences_are_exact_on_their_domains(which):
     assert G.abc_numerics_check(which) == 0
 
 
