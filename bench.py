@@ -784,6 +784,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.workload in ("batched", "sweep"):
+        # a batch's graph runs one branch per run: give the process more
+        # hardware work queues than the default 8, before CUDA starts
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     if args.impl == "reference":
         line = run_reference(args)
     elif args.workload == "batched":

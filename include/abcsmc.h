@@ -481,7 +481,9 @@ ABC_API void abc_mlp_free(abc_mlp* m);
  * skipped afterwards; the others continue.  A run whose run budget
  * (max_total_batches) is used up stops the same way after its last
  * generation (status ABC_OK there; the start kernel of the next launch
- * skips it). */
+ * skips it).  The branches share the process's hardware work queues: with
+ * many runs, set CUDA_DEVICE_MAX_CONNECTIONS (e.g. 32; the default is 8)
+ * before the first CUDA call. */
 typedef struct abc_batch abc_batch;
 /* cfgs: host array of n_runs configs; obs: host array of n_runs host
  * pointers to int32 [3][T_r+1] series (entries may be NULL for the toy). */

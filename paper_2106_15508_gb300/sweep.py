@@ -176,6 +176,10 @@ def main(argv=None):
     ap.add_argument("--population", type=int, default=10_000_000)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
+    # one graph branch per run: more hardware work queues than the default 8
+    # (read when CUDA starts, so set before the first CUDA call)
+    import os
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     build()
     cfgs = sweep_configs(a.levels, a.trials, a.samples, a.budget, a.days, a.population)
     obs = torch.empty((3, a.days + 1), dtype=torch.int32, device="cuda")
