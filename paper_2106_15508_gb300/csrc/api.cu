@@ -105,6 +105,7 @@ int check_smc(const abc_config* c) {
   if (c->weight_prec != ABC_P_FP32 && c->weight_prec != ABC_P_BF16_TC) return ABC_E_INVAL;
   if (c->max_batches < 1 || c->max_batches > 65535) return ABC_E_INVAL;
   if (c->max_total_batches < 0) return ABC_E_INVAL;
+  if (c->spec_batches < 0 || c->spec_batches > 256) return ABC_E_INVAL;
   if (c->max_redraw < 1 || c->max_redraw > (1 << 23)) return ABC_E_INVAL;
   if (c->surrogate) {
     if (c->surrogate != 1 || c->surrogate_start < 1 || c->surrogate_steps < 0 ||
@@ -151,6 +152,7 @@ ABC_API void abc_config_default(abc_config* c) {
   c->surrogate_rho_min = 0.05f;
   c->audit_frac = 0.01f;
   c->surrogate_ring = 0;
+  c->spec_batches = 1;
 }
 
 ABC_API const char* abc_strerror(int code) {
@@ -506,8 +508,13 @@ struct abc_ctx {
 
 namespace {
 
+// batches per device loop round of graph-captured batches (spec_batches)
+int spec_k(const abc_config& c) { return c.spec_batches > 1 ? c.spec_batches : 1; }
+
 int ctx_alloc(abc_ctx* c) {
-  const size_t N = static_cast<size_t>(c->N), M = static_cast<size_t>(c->M);
+  const size_t N = static_cast<size_t>(c->N);
+  // the proposal buffers hold the slots of spec_batches batches
+  const size_t M = static_cast<size_t>(c->M) * static_cast<size_t>(spec_k(c->cfg));
   int rc = ABC_OK;
 #define ABC_ALLOC(ptr, n) \
   if ((rc = c->alloc(&(ptr), (n))) != ABC_OK) return rc
@@ -577,6 +584,8 @@ int ctx_alloc(abc_ctx* c) {
 #undef ABC_ALLOC
   size_t sb = std::max({select_scratch_bytes(c->N), prefix_scratch_bytes(c->N),
                         accept_scratch_bytes(c->M), survivors_scratch_bytes(c->N),
+                        spec_k(c->cfg) > 1 ? accept_spec_scratch_bytes(c->M, spec_k(c->cfg))
+                                           : size_t(0),
                         normalize_scratch_bytes(c->N)});
   if (c->cfg.weight_mode == ABC_W_IMPORTANCE)  // room for the tuner's chunk multipliers (<= 4)
     sb = std::max(sb, c->cfg.weight_prec == ABC_P_BF16_TC ? weights_tc_scratch_bytes(c->N, c->N, 4)
@@ -855,6 +864,10 @@ ABC_API int abc_init(const abc_config* cfg, const int32_t* obs, void* stream, ab
   c->N = cfg->n_particles;
   c->M = cfg->batch_size > 0 ? cfg->batch_size : cfg->n_particles;
   c->T = cfg->model == ABC_MODEL_SAIRD ? cfg->n_days : 0;
+  if (c->M * spec_k(*cfg) > kMaxIndex) {
+    delete c;
+    return ABC_E_INVAL;
+  }
   if ((rc = ctx_alloc(c)) != ABC_OK) {
     delete c;
     return rc;
@@ -1073,6 +1086,7 @@ RunCtxView ctx_view(abc_ctx* c) {
   v.p = c->p;
   v.N = c->N;
   v.M = c->M;
+  v.K = spec_k(c->cfg);
   int64_t k = static_cast<int64_t>(std::ceil(c->cfg.survival_alpha * static_cast<double>(c->N)));
   v.rank = std::min<int64_t>(std::max<int64_t>(k, 1), c->N);
   v.beta = beta_rule(c->cfg);
@@ -1328,7 +1342,7 @@ ABC_API int abc_batch_generation(abc_batch* b) {
     g.exhausted = d.exhausted;
     g.sims = d.batches * c->M - d.exhausted;
     g.sim_days = g.sims * static_cast<int64_t>(c->cfg.model == ABC_MODEL_SAIRD ? c->T : 1);
-    g.launches = b->br[r].fixed_launches + d.batches * b->br[r].body_launches;
+    g.launches = b->br[r].fixed_launches + d.rounds * b->br[r].body_launches;
     g.ms = ms;  // the whole graph (all runs)
     b->stats[r].push_back(g);
     c->batches_total = d.batches_total;

@@ -32,11 +32,16 @@
 
 namespace abc {
 
-__global__ void k_run_start(RunDev* r, int paper_beta, int fixed_b, cudaGraphConditionalHandle h) {
+__global__ void k_run_start(RunDev* r, int paper_beta, int fixed_b, int K,
+                            cudaGraphConditionalHandle h) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   r->off = r->done;
   r->b = 0;
   r->c1 = r->t << 16;
+  // batches of the first round (K at most, within the batch budget)
+  r->k_lim = K < r->max_batches ? K : r->max_batches;
+  r->used = 1;
+  r->rounds = 0;
   // integer b of the product form (0: the Gamma ratio, under the real-shape
   // rules and for the paper's b = 2t above 1024)
   r->beta_b = paper_beta ? (r->t <= 512u ? static_cast<int>(2 * r->t) : 0) : fixed_b;
@@ -49,11 +54,17 @@ __global__ void k_run_start(RunDev* r, int paper_beta, int fixed_b, cudaGraphCon
   cudaGraphSetConditional(h, r->done ? 0u : 1u);
 }
 
-__global__ void k_run_cond(RunDev* r, long long N, cudaGraphConditionalHandle h) {
+// after a round: advance by the batches it used (1, or up to K when several
+// batches run per round: the one that filled N is the last counted)
+__global__ void k_run_cond(RunDev* r, long long N, int K, cudaGraphConditionalHandle h) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  r->batches += 1;
-  r->b += 1;
+  const int used = r->used;
+  r->rounds += 1;
+  r->batches += used;
+  r->b += static_cast<uint32_t>(used);
   r->c1 = (r->t << 16) | r->b;
+  const int left = r->max_batches - static_cast<int>(r->b);
+  r->k_lim = K < left ? K : left;
   const bool more = r->filled < N && r->b < static_cast<uint32_t>(r->max_batches);
   cudaGraphSetConditional(h, more ? 1u : 0u);
 }
@@ -123,7 +134,7 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
     ABC_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
   }
   const int fixed_b = v.beta.mode == ABC_BETA_FIXED ? v.beta.b : 0;
-  k_run_start<<<1, 32, 0, st>>>(r, v.beta.mode == ABC_BETA_PAPER, fixed_b, h);
+  k_run_start<<<1, 32, 0, st>>>(r, v.beta.mode == ABC_BETA_PAPER, fixed_b, v.K, h);
   ABC_LAUNCH_CHECK();
   {
     cudaStreamCaptureStatus cs;
@@ -142,23 +153,32 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
     ABC_CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1,
                                                      cudaStreamSetCaptureDependencies));
   }
-  // loop body: one batch of M proposals
+  // loop body: one batch of M proposals, or K batches (K M slots, batch c1 +
+  // slot / M) accepted in (batch, slot) order
   ABC_CUDA_TRY(cudaStreamBeginCaptureToGraph(body_st, body, nullptr, nullptr, 0,
                                              cudaStreamCaptureModeRelaxed));
   l_body0 = launch_count();
-  rc = launch_propose(v.p, v.u_cur, v.N, v.prefix, v.beta, &r->eps, &r->eps1, v.M, nullptr, 0u,
+  const bool spec = v.K > 1;
+  const int64_t slots = v.M * v.K;
+  rc = launch_propose(v.p, v.u_cur, v.N, v.prefix, v.beta, &r->eps, &r->eps1, slots, nullptr, 0u,
                       v.max_redraw, v.up, v.sp, v.ap, v.att, v.flag, body_st, &r->c1, &r->beta_b,
-                      &r->off);
+                      &r->off, spec ? v.M : 0, spec ? &r->k_lim : nullptr);
   if (!rc)
-    rc = launch_simulate(v.p, v.obs, v.up, v.M, nullptr, 0u, ABC_TAG_SIM, v.flag, v.dp, nullptr,
-                         body_st, &r->c1, &r->off, br.sim_threads);
-  if (!rc)
+    rc = launch_simulate(v.p, v.obs, v.up, slots, nullptr, 0u, ABC_TAG_SIM, v.flag, v.dp, nullptr,
+                         body_st, &r->c1, &r->off, br.sim_threads, nullptr, spec ? v.M : 0);
+  if (!rc && spec)
+    rc = launch_accept_spec(v.up, v.dp, v.sp, v.ap, v.flag, v.M, v.K, &r->k_lim, &r->eps, v.N,
+                            v.u_nxt, v.d_nxt, v.s_nxt, v.a_nxt,
+                            reinterpret_cast<int64_t*>(&r->filled),
+                            reinterpret_cast<int64_t*>(&r->accepted), &r->used, v.scratch,
+                            v.scratch_bytes, body_st);
+  else if (!rc)
     rc = launch_accept(v.up, v.dp, v.sp, v.ap, v.flag, v.M, &r->eps, v.N, v.u_nxt, v.d_nxt,
                        v.s_nxt, v.a_nxt, reinterpret_cast<int64_t*>(&r->filled),
                        reinterpret_cast<int64_t*>(&r->accepted), v.scratch, v.scratch_bytes,
                        body_st);
   if (!rc) {
-    k_run_cond<<<1, 32, 0, body_st>>>(r, v.N, h);
+    k_run_cond<<<1, 32, 0, body_st>>>(r, v.N, v.K, h);
     count_launch();
     if (cudaGetLastError() != cudaSuccess) rc = ABC_E_CUDA;
   }

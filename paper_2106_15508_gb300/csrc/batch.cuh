@@ -20,7 +20,10 @@ struct RunDev {
   long long exhausted;
   long long batches;
   long long batches_total;  // run budget count: ceil(N / M) for stage 0, then every batch
+  long long rounds;         // device loop rounds of this generation
   int32_t max_total;        // run budget (0: none)
+  int32_t k_lim;            // batches proposed in this round (several: spec_batches)
+  int32_t used;             // batches the round used (up to the one that filled N)
   int32_t pad;
   double eps, eps1, ess;
 };
@@ -29,6 +32,7 @@ struct RunDev {
 struct RunCtxView {
   SimParams p;
   int64_t N, M, rank;
+  int K;  // batches per device loop round (spec_batches)
   BetaRule beta;
   int max_redraw, weight_mode, weight_prec;
   const int32_t* obs;
@@ -59,7 +63,7 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st);
 int launch_simulate(const SimParams&, const int32_t*, const float*, int64_t, const uint32_t*,
                     uint32_t, uint32_t, const uint8_t*, double*, int32_t*, cudaStream_t,
                     const uint32_t* c1_dev = nullptr, const int* off_dev = nullptr,
-                    int threads = 128, int32_t* ard_last = nullptr);
+                    int threads = 128, int32_t* ard_last = nullptr, int64_t m_sub = 0);
 int launch_select(const double*, int64_t, int64_t, double*, void*, size_t, cudaStream_t);
 int launch_resample_prefix(const double*, const double*, int64_t, const double*, int, uint32_t*,
                            uint64_t*, void*, size_t, cudaStream_t);
@@ -72,7 +76,13 @@ int launch_propose(const SimParams&, const float*, int64_t, const uint64_t*, con
                    const double*, const double*, int64_t, const uint32_t*, uint32_t, int, float*,
                    float*, int32_t*, int32_t*, uint8_t*, cudaStream_t,
                    const uint32_t* c1_dev = nullptr, const int* beta_b_dev = nullptr,
-                   const int* off_dev = nullptr);
+                   const int* off_dev = nullptr, int64_t m_sub = 0,
+                   const int* k_lim_dev = nullptr);
+size_t accept_spec_scratch_bytes(int64_t M, int K);
+int launch_accept_spec(const float*, const double*, const float*, const int32_t*,
+                       const uint8_t*, int64_t M, int K, const int* k_lim_dev, const double*,
+                       int64_t N, float*, double*, float*, int32_t*, int64_t* filled,
+                       int64_t* counters, int* used_out, void*, size_t, cudaStream_t);
 int launch_accept(const float*, const double*, const float*, const int32_t*, const uint8_t*,
                   int64_t, const double*, int64_t, float*, double*, float*, int32_t*, int64_t*,
                   int64_t*, void*, size_t, cudaStream_t, const float* rho_in = nullptr,

@@ -307,13 +307,26 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
                           int max_redraw, float* __restrict__ u_out, float* __restrict__ s_out,
                           int32_t* __restrict__ anc_out, int32_t* __restrict__ att_out,
                           uint8_t* __restrict__ flag_out, const uint32_t* __restrict__ c1_dev,
-                          const int* __restrict__ beta_b_dev, const int* __restrict__ off_dev) {
+                          const int* __restrict__ beta_b_dev, const int* __restrict__ off_dev,
+                          int64_t m_sub, const int* __restrict__ k_lim_dev) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= slots) return;
   if (off_dev && *off_dev) return;          // run finished
   if (c1_dev) c1 = *c1_dev;                 // set on the device (graph launches)
+  // slots of several batches at once (m_sub > 0): slot i is slot is of batch
+  // c1 + kb; batches at or beyond *k_lim_dev are not drawn (flag 3)
+  int64_t is = i;
+  if (m_sub > 0) {
+    const int64_t kb = i / m_sub;
+    is = i - kb * m_sub;
+    if (k_lim_dev && kb >= *k_lim_dev) {
+      flag_out[i] = 3;
+      return;
+    }
+    c1 += static_cast<uint32_t>(kb);
+  }
   const int beta_b = beta_b_dev ? *beta_b_dev : rule.b;
-  const uint32_t j = c0_idx ? c0_idx[i] : static_cast<uint32_t>(i);
+  const uint32_t j = c0_idx ? c0_idx[is] : static_cast<uint32_t>(is);
   const unsigned long long total = prefix[n - 1];
   float a_t = rule.a, b_t = 0.0f;
   float ratio = 1.0f;
@@ -392,8 +405,9 @@ int launch_propose(const SimParams& p, const float* u, int64_t n, const uint64_t
                    const uint32_t* c0_idx, uint32_t c1, int max_redraw, float* u_out,
                    float* s_out, int32_t* anc_out, int32_t* att_out, uint8_t* flag_out,
                    cudaStream_t st, const uint32_t* c1_dev, const int* beta_b_dev,
-                   const int* off_dev) {
-  if (n <= 0 || slots < 0 || max_redraw < 1 || !beta_rule_ok(rule)) return ABC_E_INVAL;
+                   const int* off_dev, int64_t m_sub, const int* k_lim_dev) {
+  if (n <= 0 || slots < 0 || max_redraw < 1 || !beta_rule_ok(rule) || m_sub < 0)
+    return ABC_E_INVAL;
   if (rule.mode == ABC_BETA_FIXED && !beta_b_dev && (rule.b < 1 || rule.b > 1024))
     return ABC_E_INVAL;
   // paper schedule: integer b in 1..1024, or 0 for Beta(a_t, 2t) by the
@@ -410,7 +424,7 @@ int launch_propose(const SimParams& p, const float* u, int64_t n, const uint64_t
   if (slots == 0) return ABC_OK;
   k_propose<<<static_cast<unsigned>(ceil_div(slots, 128)), 128, 0, st>>>(
       p, u, n, prefix, rule, eps, eps1, slots, c0_idx, c1, max_redraw, u_out, s_out, anc_out,
-      att_out, flag_out, c1_dev, beta_b_dev, off_dev);
+      att_out, flag_out, c1_dev, beta_b_dev, off_dev, m_sub, k_lim_dev);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }
@@ -437,8 +451,9 @@ __global__ void k_acc_count(const double* __restrict__ dp, const uint8_t* __rest
   f = block_sum<int>(f, smf);
   if (threadIdx.x == 0) {
     tile_cnt[blockIdx.x] = c;
-    if (f) atomicAdd(reinterpret_cast<unsigned long long*>(&counters[1]),
-                     static_cast<unsigned long long>(f));
+    if (f && counters)
+      atomicAdd(reinterpret_cast<unsigned long long*>(&counters[1]),
+                static_cast<unsigned long long>(f));
   }
 }
 
@@ -516,6 +531,95 @@ int launch_accept(const float* up, const double* dp, const float* sp, const int3
   k_acc_scatter<<<static_cast<unsigned>(nt), kTileThr, 0, st>>>(up, dp, sp, ap, flag, M, eps, off,
                                                                 basep, N, u_pop, d_pop, s_pop,
                                                                 anc_pop, rho_in, rho_pop);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+// ---- several batches accepted at once (graph-captured batches) -----------
+// Batches b .. b + K - 1 of M slots each were proposed and simulated
+// together; the sequential rule accepts them in (batch, slot) order and
+// stops after the batch in which N is reached.  k_spec_count counts each
+// batch's acceptances and exhausted slots; k_spec_finish finds that batch,
+// adds the counts of the batches up to it (accepted, exhausted) and sets the
+// number of batches used; the scatter stores the first N acceptances of the
+// whole range in order, which are those of the used batches.
+__global__ void __launch_bounds__(256)
+k_spec_count(const double* __restrict__ dp, const uint8_t* __restrict__ flag, int64_t M,
+             const double* eps_p, int* __restrict__ sub_acc, int* __restrict__ sub_exh) {
+  __shared__ int sm[32];
+  __shared__ int smf[32];
+  const double eps = *eps_p;
+  const int64_t b0 = static_cast<int64_t>(blockIdx.x) * M;
+  int c = 0, f = 0;
+  for (int64_t j = threadIdx.x; j < M; j += blockDim.x) {
+    const uint8_t fl = flag[b0 + j];
+    f += (fl == 1);
+    c += (fl == 0 && dp[b0 + j] <= eps);
+  }
+  c = block_sum<int>(c, sm);
+  f = block_sum<int>(f, smf);
+  if (threadIdx.x == 0) {
+    sub_acc[blockIdx.x] = c;
+    sub_exh[blockIdx.x] = f;
+  }
+}
+
+__global__ void k_spec_finish(const int* __restrict__ sub_acc, const int* __restrict__ sub_exh,
+                              const int* k_lim_dev, long long* filled, long long* base_out,
+                              long long* counters, int* used_out, int64_t N) {
+  const int klim = *k_lim_dev;
+  const long long f0 = *filled;
+  *base_out = f0;
+  long long f = f0, acc = 0, exh = 0;
+  int used = klim;
+  for (int k = 0; k < klim; ++k) {
+    acc += sub_acc[k];
+    exh += sub_exh[k];
+    f += sub_acc[k];
+    if (f >= N) {
+      used = k + 1;
+      break;
+    }
+  }
+  counters[0] += acc;
+  counters[1] += exh;
+  *filled = f < N ? f : N;
+  *used_out = used;
+}
+
+size_t accept_spec_scratch_bytes(int64_t M, int K) {
+  return accept_scratch_bytes(M * K) + 2 * align256(4 * static_cast<size_t>(K));
+}
+
+int launch_accept_spec(const float* up, const double* dp, const float* sp, const int32_t* ap,
+                       const uint8_t* flag, int64_t M, int K, const int* k_lim_dev,
+                       const double* eps, int64_t N, float* u_pop, double* d_pop, float* s_pop,
+                       int32_t* anc_pop, int64_t* filled, int64_t* counters, int* used_out,
+                       void* scratch, size_t bytes, cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K < 1 || !k_lim_dev || !used_out) return ABC_E_INVAL;
+  if (bytes < accept_spec_scratch_bytes(M, K)) return ABC_E_SCRATCH;
+  const int64_t MK = M * K;
+  const int64_t nt = ceil_div(MK, kTile);
+  char* b = static_cast<char*>(scratch);
+  int* cnt = reinterpret_cast<int*>(b);
+  int* off = reinterpret_cast<int*>(b + align256(4 * nt));
+  int* tot = reinterpret_cast<int*>(b + 2 * align256(4 * nt));
+  long long* basep = reinterpret_cast<long long*>(b + 2 * align256(4 * nt) + align256(8));
+  char* tail = b + accept_scratch_bytes(MK);
+  int* sub_acc = reinterpret_cast<int*>(tail);
+  int* sub_exh = reinterpret_cast<int*>(tail + align256(4 * static_cast<size_t>(K)));
+  k_spec_count<<<static_cast<unsigned>(K), 256, 0, st>>>(dp, flag, M, eps, sub_acc, sub_exh);
+  ABC_LAUNCH_CHECK();
+  k_acc_count<<<static_cast<unsigned>(nt), kTileThr, 0, st>>>(dp, flag, MK, eps, cnt, nullptr);
+  ABC_LAUNCH_CHECK();
+  k_scan_tiles<int><<<1, 1024, 0, st>>>(cnt, nt, off, tot);
+  ABC_LAUNCH_CHECK();
+  k_spec_finish<<<1, 1, 0, st>>>(sub_acc, sub_exh, k_lim_dev, reinterpret_cast<long long*>(filled),
+                                 basep, reinterpret_cast<long long*>(counters), used_out, N);
+  ABC_LAUNCH_CHECK();
+  k_acc_scatter<<<static_cast<unsigned>(nt), kTileThr, 0, st>>>(up, dp, sp, ap, flag, MK, eps, off,
+                                                                basep, N, u_pop, d_pop, s_pop,
+                                                                anc_pop, nullptr, nullptr);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

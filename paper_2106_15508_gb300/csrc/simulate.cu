@@ -187,7 +187,8 @@ k_simulate(SimParams p, const int32_t* __restrict__ obs,
                            const uint32_t* __restrict__ c0_idx, uint32_t c1, uint32_t tag,
                            const uint8_t* __restrict__ skip, double* __restrict__ dist,
                            int32_t* __restrict__ traj, const uint32_t* __restrict__ c1_dev,
-                           const int* __restrict__ off_dev, int32_t* __restrict__ ard_last) {
+                           const int* __restrict__ off_dev, int32_t* __restrict__ ard_last,
+                           int64_t m_sub) {
   extern __shared__ int32_t s_obs[];
   if (off_dev && *off_dev) return;  // run finished: nothing to simulate
   if (c1_dev) c1 = *c1_dev;         // counter word set on the device (graph launches)
@@ -209,7 +210,14 @@ k_simulate(SimParams p, const int32_t* __restrict__ obs,
   float th[8];
 #pragma unroll
   for (int d = 0; d < 8; ++d) th[d] = theta_of(p, d, u[static_cast<int64_t>(d) * n + i]);
-  const uint32_t c0 = c0_idx ? c0_idx[i] : static_cast<uint32_t>(i);
+  // slots of several batches at once (m_sub > 0): slot is of batch c1 + kb
+  int64_t is = i;
+  if (m_sub > 0) {
+    const int64_t kb = i / m_sub;
+    is = i - kb * m_sub;
+    c1 += static_cast<uint32_t>(kb);
+  }
+  const uint32_t c0 = c0_idx ? c0_idx[is] : static_cast<uint32_t>(is);
   if (p.model == ABC_MODEL_GAUSS_TOY) {
     dist[i] = toy_dist(p, th, c0, c1, tag);
     if (ard_last) {  // the toy has no compartments
@@ -283,8 +291,9 @@ __global__ void k_philox(const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t
 int launch_simulate(const SimParams& p, const int32_t* obs, const float* u, int64_t n,
                     const uint32_t* c0_idx, uint32_t c1, uint32_t tag, const uint8_t* skip,
                     double* dist, int32_t* traj, cudaStream_t st, const uint32_t* c1_dev,
-                    const int* off_dev, int threads, int32_t* ard_last) {
+                    const int* off_dev, int threads, int32_t* ard_last, int64_t m_sub) {
   if (n <= 0) return ABC_OK;
+  if (m_sub < 0) return ABC_E_INVAL;
   // 64 registers per thread (__launch_bounds__(256, 4)): up to 8 CTAs of
   // 128 threads per SM; blocks of at most 256 threads
   if (threads != 64 && threads != 128 && threads != 256) return ABC_E_INVAL;
@@ -292,7 +301,7 @@ int launch_simulate(const SimParams& p, const int32_t* obs, const float* u, int6
   const size_t smem = sizeof(int32_t) * ((nobs + 3) & ~static_cast<size_t>(3)) +
                       sizeof(BinvJob) * kBinvQueue * static_cast<size_t>(threads / 32);
   k_simulate<<<static_cast<unsigned>(ceil_div(n, threads)), threads, smem, st>>>(
-      p, obs, u, n, c0_idx, c1, tag, skip, dist, traj, c1_dev, off_dev, ard_last);
+      p, obs, u, n, c0_idx, c1, tag, skip, dist, traj, c1_dev, off_dev, ard_last, m_sub);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

@@ -55,6 +55,7 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", offsetof(abc_gen_stats, eps), offsetof(abc_gen_stats, batches),
          offsetof(abc_gen_stats, ms_weights), offsetof(abc_gen_stats, beta_bf),
          offsetof(abc_config, beta_p2), offsetof(abc_config, max_total_batches));
+  printf("%zu\n", offsetof(abc_config, spec_batches));
   return 0;
 }
 """
@@ -63,13 +64,14 @@ int main(void) {
         open(c, "w").write(prog)
         exe = os.path.join(d, "t")
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
-        a, b = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.splitlines()
-    got = [int(x) for x in a.split()] + [int(x) for x in b.split()]
+        a, b, c = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.splitlines()
+    got = [int(x) for x in a.split()] + [int(x) for x in b.split()] + [int(x) for x in c.split()]
     want = [ctypes.sizeof(G.AbcConfig), G.AbcConfig.population.offset, G.AbcConfig.seed.offset,
             G.AbcConfig.survival_alpha.offset, G.AbcConfig.max_redraw.offset,
             ctypes.sizeof(G.AbcGenStats), G.AbcGenStats.eps.offset, G.AbcGenStats.batches.offset,
             G.AbcGenStats.ms_weights.offset, G.AbcGenStats.beta_bf.offset,
-            G.AbcConfig.beta_p2.offset, G.AbcConfig.max_total_batches.offset]
+            G.AbcConfig.beta_p2.offset, G.AbcConfig.max_total_batches.offset,
+            G.AbcConfig.spec_batches.offset]
     assert got == want
 
 
