@@ -467,7 +467,7 @@ def run_sweep_bench(args):
     B.build()
     G.lib()
     levels = tuple(args.levels) if args.levels else S.LEVELS
-    cfgs = S.sweep_configs(levels, args.trials)
+    cfgs = S.sweep_configs(levels, args.trials, spec_target=args.spec_target)
     obs = synthetic_obs(G, WL, cfgs[0], torch)[0]
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -498,6 +498,8 @@ def run_sweep_bench(args):
                            "-".join(str(m) for m in levels), args.trials),
                        "step": "one whole sweep (every trial to its stopping stage)",
                        "grouping": args.grouping,
+                       "batches_per_round": "about %d simulations in flight, 1 to 64" % (
+                           args.spec_target) if args.spec_target else "1",
                        "l2": "flushed between steps (256 MB write)"},
             "gpu_launches": launches, "clocks": clk,
             "sweep": {str(k): v for k, v in summ.items()}}
@@ -768,6 +770,8 @@ def main():
     ap.add_argument("--levels", type=int, nargs="*", default=None,
                     help="sweep: simulations per batch (default 10 100 1000 10000 100000)")
     ap.add_argument("--trials", type=int, default=10, help="sweep: trials per level")
+    ap.add_argument("--spec-target", type=int, default=16384,
+                    help="sweep: simulations in flight per round of small levels (0: one batch)")
     ap.add_argument("--grouping", default="all", choices=["all", "level", "run"],
                     help="sweep: one batch of all runs, one per level, or one per run")
     ap.add_argument("--pass-n", type=int, default=1 << 28)

@@ -44,14 +44,23 @@ class Curve:
     group_s: float = 0.0  # wall time of the batch the run was part of
 
 
+def spec_for(M, target=16384, cap=64):
+    """Batches per device loop round for M simulations per batch: enough to
+    put about `target` simulations in flight (a batch of M <= 10^4 is a
+    chain of dependent trajectories, latency-bound), at most `cap`."""
+    return max(1, min(cap, -(-target // M)))
+
+
 def sweep_configs(levels=LEVELS, trials=10, N=1000, budget=1000, T=120, P=10_000_000, seed=1,
-                  max_batches=65535):
+                  max_batches=65535, spec_target=16384):
     """One config per (level, trial): N samples, M = level, the run budget,
     the paper's Beta schedule and weights (Eq. 10, 16); run ids 0, 1, ...
-    give every trial its own Philox key."""
+    give every trial its own Philox key.  Small levels run several batches
+    per round (spec_for; results unchanged); spec_target 0 runs one."""
     w = WL.Workload("sweep", N=N, T=T, P=P, G=0, weight_mode=ABC_W_PAPER,
                     max_batches=max_batches, seed=seed)
-    return [w.config(batch_size=M, max_total_batches=budget, run_id=li * trials + k)
+    return [w.config(batch_size=M, max_total_batches=budget, run_id=li * trials + k,
+                     spec_batches=spec_for(M, spec_target) if spec_target else 1)
             for li, M in enumerate(levels) for k in range(trials)]
 
 
