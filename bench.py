@@ -770,7 +770,7 @@ def main():
     ap.add_argument("--levels", type=int, nargs="*", default=None,
                     help="sweep: simulations per batch (default 10 100 1000 10000 100000)")
     ap.add_argument("--trials", type=int, default=10, help="sweep: trials per level")
-    ap.add_argument("--spec-target", type=int, default=16384,
+    ap.add_argument("--spec-target", type=int, default=65536,
                     help="sweep: simulations in flight per round of small levels (0: one batch)")
     ap.add_argument("--grouping", default="all", choices=["all", "level", "run"],
                     help="sweep: one batch of all runs, one per level, or one per run")

@@ -44,7 +44,7 @@ class Curve:
     group_s: float = 0.0  # wall time of the batch the run was part of
 
 
-def spec_for(M, target=16384, cap=64):
+def spec_for(M, target=65536, cap=64):
     """Batches per device loop round for M simulations per batch: enough to
     put about `target` simulations in flight (a batch of M <= 10^4 is a
     chain of dependent trajectories, latency-bound), at most `cap`."""
@@ -52,7 +52,7 @@ def spec_for(M, target=16384, cap=64):
 
 
 def sweep_configs(levels=LEVELS, trials=10, N=1000, budget=1000, T=120, P=10_000_000, seed=1,
-                  max_batches=65535, spec_target=16384):
+                  max_batches=65535, spec_target=65536):
     """One config per (level, trial): N samples, M = level, the run budget,
     the paper's Beta schedule and weights (Eq. 10, 16); run ids 0, 1, ...
     give every trial its own Philox key.  Small levels run several batches

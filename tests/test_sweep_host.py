@@ -18,9 +18,9 @@ def test_sweep_configs_cover_levels_and_trials():
         assert c.weight_mode == G.ABC_W_PAPER and c.beta_mode == G.ABC_BETA_PAPER
         assert c.n_days == 120 and c.population == 10_000_000
         assert c.max_batches == 65535
-    # batches per round: about 16384 simulations in flight, 1 to 64
-    assert [c.spec_batches for c in cfgs[::4]] == [64, 64, 17]
-    assert S.spec_for(100000) == 1 and S.spec_for(10000) == 2
+    # batches per round: about 65536 simulations in flight, 1 to 64
+    assert [c.spec_batches for c in cfgs[::4]] == [64, 64, 64]
+    assert S.spec_for(100000) == 1 and S.spec_for(10000) == 7
     assert all(c.spec_batches == 1 for c in S.sweep_configs(levels=(10,), trials=2,
                                                             spec_target=0))
 
