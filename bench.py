@@ -389,7 +389,7 @@ def run_batched(args):
     try:
         G.abc_batch_generation(b)
         if args.autotune:
-            cache = os.path.join(ROOT, "gpurun_out", "autotune.json")
+            cache = os.path.join(ROOT, "_build", "autotune.json")
             os.makedirs(os.path.dirname(cache), exist_ok=True)
             t0 = time.perf_counter()
             G.abc_batch_autotune(b, cache)

@@ -116,7 +116,7 @@ typedef struct {
   int32_t weight_prec;      /* ABC_P_*                                                  */
   int32_t max_batches;      /* per-generation batch budget (<= 65535)                   */
   int32_t max_redraw;       /* proposal redraws when u' leaves [0,1]^8                   */
-  /* Surrogate pre-screen (spec extension; the paper simulates every
+  /* Surrogate pre-screen (an extension beyond the paper; the paper simulates every
    * proposal): an MLP u -> [log1p d, log1p A_T, log1p R_T, log1p D_T],
    * 8 -> 256 -> 256 -> 4 with GELU, bf16 weights and fp32 accumulation,
    * trained after every generation on the (u, summary) pairs simulated so
@@ -271,7 +271,7 @@ ABC_API int abc_accept_append(const float* up, const double* dp, const float* sp
                       double* d_pop, float* s_pop, int32_t* anc_pop, int64_t* filled,
                       int64_t* counters, void* scratch, size_t scratch_bytes, void* stream);
 
-/* A9 importance weights (spec extension; the paper's weights are
+/* A9 importance weights (an extension beyond the paper; the paper's weights are
  * Eq. 10): for each row j < rows,
  *   logW[j] = 4 log(2 pi s_j) - log sum_k (q_k / total) exp(-|u'_j - u_k|^2 / (2 s_j))
  * = -log sum_k rhat_k N(u'_j; u_k, s_j I8) (uniform prior on the unit cube),
@@ -354,7 +354,7 @@ ABC_API size_t abc_normalize_scratch_bytes(int64_t n);
 ABC_API int abc_normalize(const double* logW, int64_t n, double* W, double* ess, void* scratch,
                   size_t scratch_bytes, void* stream);
 
-/* A11 delayed-acceptance screen (spec extension; the paper simulates
+/* A11 delayed-acceptance screen (an extension beyond the paper; the paper simulates
  * every proposal; two-stage acceptance after Christen & Fox 2005).  For
  * slot i < M with flag[i] == 0 the surrogate's prediction of log1p d is
  * y0 = ystat[0] + ystat[4] * Y[4 i] (fp32 product, then sum) and
@@ -448,7 +448,7 @@ ABC_API int abc_set_state(abc_ctx* ctx, const void* buf, size_t len);
 ABC_API void abc_free(abc_ctx* ctx);
 ABC_API const char* abc_strerror(int code);
 
-/* ---- surrogate MLP (spec extension; the paper has no surrogate) ----
+/* ---- surrogate MLP (an extension beyond the paper; the paper has no surrogate) ----
  * 8 -> 256 -> 256 -> 4 with tanh-form GELU; parameters in one fp32 array
  * (row = output): W1[256][8], b1[256], W2[256][256], b2[256], W3[4][256],
  * b3[4] (69124 values); every product uses their bf16 rounding with fp32
@@ -477,7 +477,7 @@ ABC_API int abc_mlp_forward(abc_mlp* m, const float* u, int64_t n, float* Y, voi
                             size_t scratch_bytes, void* stream);
 ABC_API void abc_mlp_free(abc_mlp* m);
 
-/* ---- batched runs (spec batched form; the paper runs one problem at
+/* ---- batched runs (batched form, an extension; the paper runs one problem at
  * a time) ------------------------------------------------------------------
  * n_runs independent runs (own config, seed, size, horizon and observed
  * series each) advanced together.  After stage 0, every generation of every

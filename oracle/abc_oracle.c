@@ -233,7 +233,7 @@ OR_API float or_normal(float w1, float w2) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Binomial(n, p) from two uniforms (spec: binomial daily transitions; */
+/* Binomial(n, p) from two uniforms (exact-count daily transitions:        */
 /* the paper's tau-leap flows, Sec. 2.2, as exact-count competing risks).    */
 /* ------------------------------------------------------------------------ */
 OR_API int32_t or_binomial(int32_t n, float p, float w1, float w2) {
@@ -749,7 +749,7 @@ OR_API void or_propose(const or_model* m, const float* u, int64_t n, const uint6
 }
 
 /*
- * Importance weight (auxiliary-variable form, spec extension; not in
+ * Importance weight (auxiliary-variable form, an extension beyond the paper; not in
  * the paper): log W_j = log pi(u'_j) - log sum_k rhat_k N(u'_j; u_k, s_j I8),
  * rhat_k = q_k / total, pi uniform on the unit cube.  fp64 throughout.
  * The kernel variance is floored at 1e-30f: a row with a smaller step has
@@ -979,7 +979,7 @@ OR_API int or_predict(const or_model* m0, const float* u, const double* W, int64
 }
 
 /* ------------------------------------------------------------------------ */
-/* Surrogate MLP (spec extension; not in the paper): 8 -> 256 -> 256 -> */
+/* Surrogate MLP (an extension beyond the paper; not in the paper): 8 -> 256 -> 256 -> */
 /* 4 with tanh-form GELU, fp64 throughout, weights given as fp64 copies of   */
 /* the device's bf16 values.  Layout: W1[256][8], W2[256][256], W3[4][256]    */
 /* (row = output), biases b1[256], b2[256], b3[4].                            */
@@ -1090,7 +1090,7 @@ OR_API double or_mlp_backward(const double* W1, const double* b1, const double* 
 }
 
 /*
- * Delayed-acceptance screen (spec extension; not in the paper; the
+ * Delayed-acceptance screen (an extension beyond the paper; not in the paper; the
  * two-stage acceptance of Christen & Fox 2005 with a surrogate first stage).
  * A proposal u' whose surrogate prediction of log1p d is y0 is simulated
  * with probability rho = min(max(sigmoid((log1p eps - y0) / tau), rho_min), 1);

@@ -1,5 +1,5 @@
-// batch.cu -- many independent ABC-SMC runs advanced together (north-star
-// batched form; the paper runs one problem at a time).
+// batch.cu -- many independent ABC-SMC runs advanced together (a batched
+// form, an extension: the paper runs one problem at a time).
 //
 // Each run keeps its own buffers (an abc_ctx).  One generation of every run
 // is one CUDA graph launch: the graph holds an independent branch per run --

@@ -1,5 +1,5 @@
 // surrogate.cu -- MLP surrogate u (8) -> 256 -> 256 -> 4 (tanh-form GELU)
-// for delayed-acceptance pre-screening (spec extension; the paper
+// for delayed-acceptance pre-screening (an extension beyond the paper; the paper
 // simulates every proposal).
 //
 // Parameters: fp32 master copy (Adam updates it) and a bf16 copy that every

@@ -1,4 +1,4 @@
-"""The surrogate pre-screen (delayed acceptance; spec extension, not in
+"""The surrogate pre-screen (delayed acceptance; an extension beyond the paper, not in
 the paper) on the GPU against the oracle.
 
 1. abc_screen equals the oracle's screen rule bit for bit (rho and the

@@ -1,5 +1,5 @@
 """Pins of the oracle's delayed-acceptance screen (surrogate pre-screen;
-spec extension, not in the paper): the pass probability against the
+an extension beyond the paper, not in the paper): the pass probability against the
 logistic function in fp64, its clamps, the exhausted-slot rule, and the
 frequencies of the two Bernoulli draws (pass with probability rho, audit with
 probability audit_frac among the rest) against their binomial laws, plus the
