@@ -149,13 +149,13 @@ typedef struct {
    * or above max_total_batches, later generations do not run
    * (ABC_STOP_TOTAL).  0: no budget. */
   int32_t max_total_batches;
-  /* Batches simulated together per device loop round in graph-captured
-   * batches (abc_batch_*), 1..256 (0 means 1): the batches of a stage
-   * depend on the stage's state only, so K of them are proposed and
-   * simulated at once and accepted in (batch, slot) order; the batches after
-   * the one that fills N are discarded, uncounted.  Results and statistics
-   * equal those of K = 1 bit for bit; small M (latency-bound rounds) run
-   * faster.  Single-run contexts run their batches one at a time. */
+  /* Batches simulated together per round, 1..256 (0 means 1): the batches
+   * of a stage depend on the stage's state only, so K of them are proposed
+   * and simulated at once and accepted in (batch, slot) order; the batches
+   * after the one that fills N are discarded, uncounted.  Results and
+   * statistics equal those of K = 1 bit for bit; small M (latency-bound
+   * rounds) run faster.  The proposal buffers hold K M slots.  Generations
+   * that screen with the surrogate run one batch per round. */
   int32_t spec_batches;
   int32_t pad_end;
 } abc_config;

@@ -430,6 +430,7 @@ struct abc_ctx {
   std::vector<abc_gen_stats> stats;
   std::vector<void*> allocs;
   // device buffers
+  int* spec_dev = nullptr;  // batches of the round, batches it used (spec_batches)
   int32_t* obs = nullptr;
   float* u[2] = {nullptr, nullptr};
   double* d[2] = {nullptr, nullptr};
@@ -526,6 +527,7 @@ int ctx_alloc(abc_ctx* c) {
     ABC_ALLOC(c->s[b], N);
     ABC_ALLOC(c->anc[b], N);
   }
+  ABC_ALLOC(c->spec_dev, 2);
   ABC_ALLOC(c->up, 8 * M);
   ABC_ALLOC(c->dp, M);
   ABC_ALLOC(c->sp, M);
@@ -664,8 +666,38 @@ int generation_t(abc_ctx* c) {
   int32_t b = 0;
   unsigned* inf_err = nullptr;
   unsigned h_inf_err = 0;
-  for (b = 0; b < c->cfg.max_batches && filled < c->N; ++b) {
+  // several batches per round (spec_batches, without the surrogate): K M
+  // slots proposed and simulated together, accepted in (batch, slot) order
+  const int K = sur ? 1 : spec_k(c->cfg);
+  int used = 1;
+  for (b = 0; b < c->cfg.max_batches && filled < c->N; b += used) {
     const uint32_t c1 = (static_cast<uint32_t>(t) << 16) | static_cast<uint32_t>(b);
+    used = 1;
+    if (K > 1) {
+      const int klim = std::min(K, c->cfg.max_batches - b);
+      ABC_CUDA_TRY(cudaMemcpyAsync(c->spec_dev, &klim, sizeof klim, cudaMemcpyHostToDevice, st));
+      rc = launch_propose(c->p, c->u[cur], c->N, c->prefix, rule, eps, eps1, c->M * K, nullptr,
+                          c1, c->cfg.max_redraw, c->up, c->sp, c->ap, c->att, c->flag, st,
+                          nullptr, nullptr, nullptr, c->M, c->spec_dev);
+      if (rc) return rc;
+      ABC_CUDA_TRY(cudaEventRecord(c->es0, st));
+      rc = launch_simulate(c->p, c->obs, c->up, c->M * K, nullptr, c1, ABC_TAG_SIM, c->flag,
+                           c->dp, nullptr, st, nullptr, nullptr, 128, nullptr, c->M);
+      if (rc) return rc;
+      ABC_CUDA_TRY(cudaEventRecord(c->es1, st));
+      rc = launch_accept_spec(c->up, c->dp, c->sp, c->ap, c->flag, c->M, K, c->spec_dev, eps,
+                              c->N, c->u[nxt], c->d[nxt], c->s[nxt], c->anc[nxt], c->cnt,
+                              c->cnt + 1, c->spec_dev + 1, c->scratch, c->scratch_bytes, st);
+      if (rc) return rc;
+      ABC_CUDA_TRY(cudaMemcpyAsync(&filled, c->cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+      ABC_CUDA_TRY(cudaMemcpyAsync(&used, c->spec_dev + 1, sizeof used, cudaMemcpyDeviceToHost,
+                                   st));
+      ABC_CUDA_TRY(cudaStreamSynchronize(st));
+      float ms = 0.f;
+      ABC_CUDA_TRY(cudaEventElapsedTime(&ms, c->es0, c->es1));
+      ms_sim += ms;
+      continue;
+    }
     rc = launch_propose(c->p, c->u[cur], c->N, c->prefix, rule, eps, eps1, c->M, nullptr, c1,
                         c->cfg.max_redraw, c->up, c->sp, c->ap, c->att, c->flag, st);
     if (rc) return rc;

@@ -72,6 +72,29 @@ def test_speculative_rounds_match_oracle():
         G.abc_batch_free(b)
 
 
+@pytest.mark.parametrize("N,M,K,mb,bud,seed", [(64, 8, 16, 4096, 60, 61), (256, 16, 64, 4096, 0, 62),
+                                                (256, 8, 16, 30, 0, 63)])
+def test_context_speculative_rounds_match_oracle(N, M, K, mb, bud, seed):
+    cfg = saird_config(N, 30, 100_000, seed=seed, batch_size=M, spec_batches=K, max_batches=mb,
+                       max_total_batches=bud)
+    obs = oracle_obs(cfg)[0]
+    pop, ost = O.run(oracle_model(cfg, obs), oracle_smc(cfg), 8)
+    ctx = G.abc_init(cfg, obs)
+    try:
+        G.abc_run(ctx, 8)
+        assert G.abc_generations(ctx) == 1 + sum(s.status == 0 for s in ost)
+        for t, s in enumerate(ost, start=1):
+            g = G.abc_get_stats(ctx, t)
+            assert (g.status, g.eps, g.batches, g.accepted, g.exhausted) == \
+                (s.status, s.eps, s.batches, s.accepted_total, s.exhausted), t
+        u = np.zeros((8, N), np.float32)
+        d = np.zeros(N)
+        G.abc_get_population(ctx, u, d)
+        assert _same(u, pop.u) and _same(d, pop.d)
+    finally:
+        G.abc_free(ctx)
+
+
 def test_spec_batches_validated():
     for bad in (-1, 257):
         cfg = saird_config(64, 10, 1000, batch_size=8, spec_batches=bad)
