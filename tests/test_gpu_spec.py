@@ -100,3 +100,38 @@ def test_spec_batches_validated():
         cfg = saird_config(64, 10, 1000, batch_size=8, spec_batches=bad)
         with pytest.raises(G.AbcError):
             G.abc_init(cfg, oracle_obs(saird_config(64, 10, 1000))[0])
+
+
+def _toy(seed, N, M, K):
+    lo, hi = [-10.0] * 8, [10.0] * 8
+    return G.config(model=G.ABC_MODEL_GAUSS_TOY, n_days=1, population=1, init_ard=[0, 0, 0],
+                    theta_lo=lo, theta_hi=hi, x_obs=[0.5] * 8, seed=seed, n_particles=N,
+                    batch_size=M, spec_batches=K, max_batches=4096)
+
+
+def test_speculative_rounds_other_models_and_rules():
+    """The Gaussian toy, the paper's floor-normal flows and a real-shape Beta
+    rule (the stage t = c1 >> 16 must not see the batch offset) under K > 1."""
+    cfgs = [_toy(71, 128, 16, 8),
+            saird_config(128, 30, 100_000, seed=72, batch_size=16, spec_batches=12,
+                         sampler=G.ABC_SIM_PAPER_NORMAL, max_batches=4096),
+            saird_config(128, 30, 100_000, seed=73, batch_size=16, spec_batches=12,
+                         beta_mode=G.ABC_BETA_MODE_CONC, beta_p1=0.2, beta_p2=10.0,
+                         max_batches=4096)]
+    obs = [None, oracle_obs(cfgs[1])[0], oracle_obs(cfgs[2])[0]]
+    b = G.abc_batch_init(cfgs, obs)
+    try:
+        G.abc_batch_run(b, 6)
+        for r, cfg in enumerate(cfgs):
+            m = oracle_model(cfg, obs[r]) if obs[r] is not None else oracle_model(cfg)
+            pop, ost = O.run(m, oracle_smc(cfg), 6)
+            for t, s in enumerate(ost, start=1):
+                g = G.abc_batch_get_stats(b, r, t)
+                assert (g.status, g.eps, g.batches, g.accepted, g.exhausted) == \
+                    (s.status, s.eps, s.batches, s.accepted_total, s.exhausted), (r, t)
+            u = np.zeros((8, cfg.n_particles), np.float32)
+            s_ = np.zeros(cfg.n_particles, np.float32)
+            G.abc_batch_get_population(b, r, u, None, None, s_)
+            assert _same(u, pop.u) and _same(s_, pop.s), r
+    finally:
+        G.abc_batch_free(b)
