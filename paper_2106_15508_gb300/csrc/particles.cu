@@ -351,25 +351,7 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
     const u32x4 wa = philox4x32_10(j, c1, static_cast<uint32_t>(a), ABC_TAG_ANCESTOR, p.k0, p.k1);
     const unsigned long long U = (static_cast<unsigned long long>(wa.y) << 32) | wa.x;
     const unsigned long long x = __umul64hi(U, total);
-    // the first k with prefix[k] > x (prefix[n - 1] = total > x): 16-way
-    // steps while more than 16 candidates are left (15 independent loads per
-    // step instead of four dependent ones), then a binary search
-    int64_t lo = 0, len = n;
-    while (len > 16) {
-      const int64_t step = (len + 15) >> 4;
-      const int64_t last = lo + len - 1;  // prefix[last] > x
-      int c = 0;
-#pragma unroll
-      for (int q = 0; q < 15; ++q) {
-        // probes past the range end stand for its last element (> x)
-        const int64_t pq = lo + step * (q + 1) - 1;
-        const int64_t pr = pq < last ? pq : last;
-        c += (pr < last && prefix[pr] <= x) ? 1 : 0;
-      }
-      lo += step * c;
-      len = step < last + 1 - lo ? step : last + 1 - lo;
-    }
-    int64_t hi = lo + len - 1;
+    int64_t lo = 0, hi = n - 1;
     while (lo < hi) {
       const int64_t mid = lo + ((hi - lo) >> 1);
       if (prefix[mid] > x) hi = mid;
