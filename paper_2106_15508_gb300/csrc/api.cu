@@ -1268,6 +1268,10 @@ ABC_API int abc_batch_init(const abc_config* cfgs, int32_t n_runs, const int32_t
                            void* stream, abc_batch** out) {
   if (!out || !cfgs || n_runs < 1 || n_runs > 4096) return ABC_E_INVAL;
   *out = nullptr;
+  // the graph branches have no screening step: a run that asks for the
+  // surrogate is refused instead of being run unscreened
+  for (int32_t r = 0; r < n_runs; ++r)
+    if (cfgs[r].surrogate) return ABC_E_INVAL;
   abc_batch* b = new (std::nothrow) abc_batch();
   if (!b) return ABC_E_NOMEM;
   b->st = as_stream(stream);
