@@ -226,7 +226,10 @@ ABC_API int abc_resample_prefix(const double* d, const double* W, int64_t n, con
  * fixed array inside the library (257 KB per device, held until the process
  * exits), which is enough for n <= ABC_NOALLOC_MAX_N = 2^24; larger n returns
  * ABC_E_TOO_LARGE.  The first call on a device looks up that array's device
- * address, so make it before any stream capture.  Every call shares the one
+ * address, so make it before any stream capture; the address is kept for the
+ * life of the process, so do not call this entry point again on a device
+ * after cudaDeviceReset() there (the array is reloaded at another address
+ * with the new context).  Every call shares the one
  * array: calls that overlap on the GPU (other streams, other threads) race
  * and must be serialised by the caller.  No device memory is allocated. */
 #define ABC_NOALLOC_MAX_N (1LL << 24)

@@ -66,6 +66,16 @@ def test_noalloc_prefix_matches_allocating_entry_point(mode):
         assert int(pre_na[-1]) == int(q_ref.astype(np.uint64).sum())
 
 
+def test_noalloc_prefix_at_its_maximum_size():
+    # n = 2^24 is the one size whose tile sums fill the whole fixed array;
+    # a small call after it must not see what it left there
+    for n, seed in ((G.ABC_NOALLOC_MAX_N, 13), (4097, 14)):
+        q_ref, pre_ref = _run(n, seed, G.ABC_W_IMPORTANCE, noalloc=False)
+        q_na, pre_na = _run(n, seed, G.ABC_W_IMPORTANCE, noalloc=True)
+        assert np.array_equal(q_na, q_ref)
+        assert np.array_equal(pre_na, pre_ref)
+
+
 def test_noalloc_prefix_rejects_sizes_above_its_scratch():
     n = G.ABC_NOALLOC_MAX_N + 1
     x = torch.zeros(1, dtype=torch.float64, device="cuda")
