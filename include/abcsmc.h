@@ -350,6 +350,23 @@ ABC_API int abc_numerics_check(int32_t which, uint64_t* mismatches, void* stream
 ABC_API int abc_radix_sort(const uint32_t* keys, const int32_t* vals, int64_t n, int32_t bits,
                            uint32_t* keys_out, int32_t* vals_out, void* stream);
 
+/* Test hooks for failure detection (no counterpart in the paper).  Both make
+ * a failure happen on the host side of a call, never a device fault.
+ * abc_set_wait_limit_ns: time limit of the tensor-core weight kernel's
+ * pipeline waits (mbarrier phases of its copy / MMA / epilogue roles) for
+ * launches made from now on; 0 restores the default of 2 s.  A wait that
+ * runs out records an error word and its role stops; the waits for the
+ * CTA's own copies and products before it exits keep the 2 s limit, so
+ * nothing is in flight when it ends, and the call returns ABC_E_DEVICE with
+ * the context still usable.  A shortened limit only serves to test that
+ * path.  abc_inject_alloc_failure: the device allocation of a context
+ * (abc_init) after `after` successful ones fails as if cudaMalloc had,
+ * giving ABC_E_NOMEM with everything allocated so far released; every later
+ * one fails too until the hook is reset with a negative value.  Neither is
+ * thread-safe against concurrent calls in other threads. */
+ABC_API void abc_set_wait_limit_ns(uint64_t ns);
+ABC_API void abc_inject_alloc_failure(int64_t after);
+
 /* A10 normalisation (fp64): W_j = exp(logW_j - max) / sum, *ess = 1 / sum W^2;
  * all -inf gives W = 1/n, ess = n.  logW: device double[n]; W: device
  * double[n]; ess: device double[1]. */

@@ -41,6 +41,7 @@ EXPORTS = (
     "abc_predict_population",
     "abc_mlp_param_count", "abc_mlp_create", "abc_mlp_set_params", "abc_mlp_get_params",
     "abc_mlp_scratch_bytes", "abc_mlp_grad", "abc_mlp_adam", "abc_mlp_forward", "abc_mlp_free",
+    "abc_set_wait_limit_ns", "abc_inject_alloc_failure",
 )
 
 
@@ -147,6 +148,8 @@ _SIGS = {
     "abc_mlp_adam": (C.c_int, [_V, _V, _I64, _F, _V]),
     "abc_mlp_forward": (C.c_int, [_V, _V, _I64, _V, _V, _SZ, _V]),
     "abc_mlp_free": (None, [_V]),
+    "abc_set_wait_limit_ns": (None, [C.c_uint64]),
+    "abc_inject_alloc_failure": (None, [_I64]),
 }
 
 
@@ -429,6 +432,18 @@ MLP_ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
 def abc_screen(cfg, Y, ystat, flag, M, eps, c1, rho, sflag, stream=None):
     return _check(lib().abc_screen(C.byref(cfg), _ptr(Y), _ptr(ystat), _ptr(flag), M, _ptr(eps), c1,
                                    _ptr(rho), _ptr(sflag), _stream(stream)), "abc_screen")
+
+
+def abc_set_wait_limit_ns(ns):
+    """Test hook: time limit of the tensor-core weight kernel's pipeline waits
+    (0 restores the default)."""
+    lib().abc_set_wait_limit_ns(int(ns))
+
+
+def abc_inject_alloc_failure(after):
+    """Test hook: the context allocation after `after` successful ones fails
+    (negative: off)."""
+    lib().abc_inject_alloc_failure(int(after))
 
 
 def abc_ex2_probe(stream=None):

@@ -41,6 +41,7 @@ int launch_predict(const SimParams& p, const float* u, const double* W, int64_t 
 int launch_tc_probe(const void*, const void*, float*, unsigned*, cudaStream_t);
 size_t normalize_scratch_bytes(int64_t);
 int launch_fill(double*, int64_t, double, cudaStream_t);
+void set_tc_wait_limit(uint64_t ns);
 }  // namespace abc
 
 namespace abc {
@@ -50,6 +51,18 @@ int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace abc
 
 using namespace abc;
+
+namespace {
+// Test hook: context allocations left before an injected failure (-1: none).
+// Failure detection is exercised on the host, without making a device fail.
+std::atomic<long long> g_alloc_fail_after{-1};
+bool alloc_fails_now() {
+  long long left = g_alloc_fail_after.load();
+  while (left > 0 && !g_alloc_fail_after.compare_exchange_weak(left, left - 1)) {
+  }
+  return left == 0;
+}
+}  // namespace
 
 namespace {
 
@@ -414,6 +427,12 @@ ABC_API int abc_screen(const abc_config* cfg, const float* Y, const float* ystat
                 cfg->audit_frac, rho, sflag, as_stream(stream), nullptr);
 }
 
+ABC_API void abc_set_wait_limit_ns(uint64_t ns) { set_tc_wait_limit(ns); }
+
+ABC_API void abc_inject_alloc_failure(int64_t after) {
+  g_alloc_fail_after.store(after < 0 ? -1 : after);
+}
+
 }  // extern "C"
 
 // -------------------------------------------------------------- context ---
@@ -491,6 +510,7 @@ struct abc_ctx {
   template <typename T>
   int alloc(T** ptr, size_t count) {
     void* p = nullptr;
+    if (alloc_fails_now()) return ABC_E_NOMEM;
     if (cudaMalloc(&p, std::max<size_t>(count * sizeof(T), 256)) != cudaSuccess) {
       cudaGetLastError();
       return ABC_E_NOMEM;

@@ -43,14 +43,17 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// wait for the phase of the given parity; gives up after ~2 s and records
-// the failure (code) in *err
+// default time limit of a pipeline wait (2 s)
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+// wait for the phase of the given parity; gives up after limit_ns and
+// records the failure (code) in *err
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err,
-                                          unsigned code) {
+                                          unsigned code, uint64_t limit_ns = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(bar, parity)) {
-    if (global_ns() - t0 > 2000000000ull) {
+    if (global_ns() - t0 >= limit_ns) {
       atomicCAS(err, 0u, code);
       return false;
     }

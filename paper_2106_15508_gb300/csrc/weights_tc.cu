@@ -42,6 +42,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "batch.cuh"
 #include "common.cuh"
@@ -69,6 +70,11 @@ constexpr size_t kTcSmem = 1024 + kATile + kTcStages * kBTile + 256 + 4 * kMaskW
 constexpr int kRowBox = 18;  // per row tile: lo[8], hi[8], max R^2, prunable flag
 constexpr int kColBox = 16;  // per column tile: lo[8], hi[8]
 constexpr float kSMinTc = 1e-30f;
+
+// time limit of the weight kernel's pipeline waits; shortened only by the
+// test hook abc_set_wait_limit_ns (failure detection without a GPU fault)
+static std::atomic<unsigned long long> g_tc_wait_ns{kWaitNs};
+void set_tc_wait_limit(uint64_t ns) { g_tc_wait_ns.store(ns ? ns : kWaitNs); }
 constexpr float kPadLogit = -1.0e30f;
 constexpr int kCandCap = 32;          // listed columns per (row, partial slot)
 constexpr float kCandMargin = 45.0f;  // log2 units: listed = within 45 bits of the maximum
@@ -585,7 +591,10 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
              const float2* __restrict__ rinfo, const uint8_t* __restrict__ rcls,
              int* __restrict__ cand, int* __restrict__ ccnt, const int* __restrict__ perm,
              const float* __restrict__ rbox, const float* __restrict__ cbox,
-             unsigned long long* __restrict__ tile_count) {
+             unsigned long long* __restrict__ tile_count, uint64_t wait_ns) {
+  // wait_ns limits the pipeline's waits (kWaitNs unless a test shortened it);
+  // the waits for this CTA's own copies and products before it exits always
+  // keep kWaitNs, so that nothing is in flight when the CTA ends
   extern __shared__ uint8_t tc_smem_raw[];
   if (off_dev && *off_dev) return;  // run finished or its generation stopped (block-uniform)
   const int64_t nrows = rows;
@@ -697,7 +706,7 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
         const int tile = it.next();
         const int st = t % kTcStages;
         const uint32_t ph = static_cast<uint32_t>(t / kTcStages) & 1u;
-        if (!mbar_wait(&sm.empty[st], ph ^ 1u, err, 1u)) break;
+        if (!mbar_wait(&sm.empty[st], ph ^ 1u, err, 1u, wait_ns)) break;
         mbar_expect_tx(&sm.full[st], kBTile);
         bulk_g2s(sm.b + st * kBTile, Bpk + static_cast<size_t>(tile) * kBTile, kBTile,
                  &sm.full[st]);
@@ -712,14 +721,14 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       int last = -1;
-      if (mbar_wait(sm.afull, 0u, err, 3u)) {
+      if (mbar_wait(sm.afull, 0u, err, 3u, wait_ns)) {
         const uint32_t a0 = smem_u32(sm.a);
         for (int t = 0; t < ntiles; ++t) {
           const int st = t % kTcStages, b = t & 1;
           const uint32_t ph = static_cast<uint32_t>(t / kTcStages) & 1u;
           const uint32_t tph = static_cast<uint32_t>(t >> 1) & 1u;
-          if (!mbar_wait(&sm.tempty[b], tph ^ 1u, err, 4u)) break;
-          if (!mbar_wait(&sm.full[st], ph, err, 5u)) break;
+          if (!mbar_wait(&sm.tempty[b], tph ^ 1u, err, 4u, wait_ns)) break;
+          if (!mbar_wait(&sm.full[st], ph, err, 5u, wait_ns)) break;
           tc_fence_after();
           const uint32_t b0 = smem_u32(sm.b + st * kBTile);
           const uint32_t d = tmem + static_cast<uint32_t>(b * kTcN);
@@ -775,7 +784,7 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
       const int b = t & 1;
       const uint32_t tph = static_cast<uint32_t>(t >> 1) & 1u;
       // warp-uniform: tcgen05.ld below is warp-collective
-      if (!__all_sync(0xffffffffu, mbar_wait(&sm.tfull[b], tph, err, 7u))) break;
+      if (!__all_sync(0xffffffffu, mbar_wait(&sm.tfull[b], tph, err, 7u, wait_ns))) break;
       tc_fence_after();
       float ts = 0.0f;
       // this thread's two 32-column chunks of the tile (c = g, g + 4), both
@@ -1331,7 +1340,8 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   k_weights_tc<<<grid, kTcThreads, kTcSmem, st>>>(reinterpret_cast<const uint8_t*>(Apk),
                                                   reinterpret_cast<const uint8_t*>(Bpk), nc_dev,
                                                   rows, part, err, off_dev, rinfo, rcls, cand,
-                                                  ccnt, perm, rbox, cbox, tiles);
+                                                  ccnt, perm, rbox, cbox, tiles,
+                                                  static_cast<uint64_t>(g_tc_wait_ns.load()));
   ABC_LAUNCH_CHECK();
   if (wt && wt->tc1) ABC_CUDA_TRY(cudaEventRecord(wt->tc1, st));
   k_weights_tc_combine<<<static_cast<unsigned>(ceil_div(rows, 256)), 256, 0, st>>>(
