@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libabcsmc.so")
 
 ABC_OK, ABC_STOP_BUDGET, ABC_STOP_TARGET, ABC_STOP_TOTAL = 0, 1, 2, 3
+ABC_E_INVAL, ABC_E_NOMEM, ABC_E_CUDA, ABC_E_DEVICE, ABC_E_SCRATCH, ABC_E_STATE = -1, -2, -3, -4, -5, -6
 ABC_E_TOO_LARGE = -7
 ABC_NOALLOC_MAX_N = 1 << 24
 ABC_MODEL_SAIRD, ABC_MODEL_GAUSS_TOY = 0, 1

@@ -279,12 +279,12 @@ ABC_API int abc_accept_append(const float* up, const double* dp, const float* sp
                        counters, scratch, scratch_bytes, as_stream(stream));
 }
 
-// scratch layout of abc_weights: [cu 8n][cc n][nc][compaction][weight pass]
+// scratch layout of abc_weights: [cu 8n][cc 2n][nc][compaction][weight pass]
 static size_t weights_layout(int64_t rows, int64_t n, size_t* off_cc, size_t* off_nc,
                              size_t* off_comp, size_t* off_w) {
   size_t o = align256(sizeof(float) * 8 * static_cast<size_t>(n));
   *off_cc = o;
-  o += align256(sizeof(float) * static_cast<size_t>(n));
+  o += align256(sizeof(float) * 2 * static_cast<size_t>(n));
   *off_nc = o;
   o += align256(sizeof(int));
   *off_comp = o;
@@ -559,7 +559,7 @@ int ctx_alloc(abc_ctx* c) {
   ABC_ALLOC(c->logW, N);
   if (c->cfg.weight_mode == ABC_W_IMPORTANCE) {
     ABC_ALLOC(c->cu, 8 * N);
-    ABC_ALLOC(c->cc, N);
+    ABC_ALLOC(c->cc, 2 * N);  // c_k as a double-float (hi, lo halves)
     ABC_ALLOC(c->nc, 1);
   }
   ABC_ALLOC(c->scal, 4);

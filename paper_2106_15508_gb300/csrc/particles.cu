@@ -625,7 +625,8 @@ int launch_accept_spec(const float* up, const double* dp, const float* sp, const
 }
 
 // --------------------------------------- survivor columns for the weights -
-// Columns with q_k > 0, in index order: cu [8][nc] and c_k = log2(q_k) - 32.
+// Columns with q_k > 0, in index order: cu [8][nc] and c_k = log2(q_k) - 32
+// as a double-float, hi in cc[0..ncap) and lo in cc[ncap..2 ncap).
 __global__ void k_surv_count(const uint32_t* __restrict__ q, int64_t n, int* __restrict__ cnt) {
   __shared__ int sm[32];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile + 4 * threadIdx.x;
@@ -656,7 +657,11 @@ __global__ void k_surv_scatter(const float* __restrict__ u, const uint32_t* __re
     const int64_t i = base + e;
 #pragma unroll
     for (int d = 0; d < 8; ++d) cu[static_cast<int64_t>(d) * ncap + pos] = u[static_cast<int64_t>(d) * n + i];
-    cc[pos] = static_cast<float>(log2(static_cast<double>(q[i])) - 32.0);
+    // c_k as a double-float: hi in cc[pos], lo in cc[ncap + pos]
+    const double c = log2(static_cast<double>(q[i])) - 32.0;
+    const float ch = __double2float_rn(c);
+    cc[pos] = ch;
+    cc[ncap + pos] = __double2float_rn(c - static_cast<double>(ch));
     ++pos;
   }
 }
@@ -666,7 +671,7 @@ size_t survivors_scratch_bytes(int64_t n) {
   return 2 * align256(4 * nt) + align256(4);
 }
 
-// compacts into cu [8][n] / cc[n] (capacity n); *nc_dev receives the count
+// compacts into cu [8][n] / cc[2 n] (capacity n); *nc_dev receives the count
 int launch_survivors(const float* u, const uint32_t* q, int64_t n, float* cu, float* cc,
                      int* nc_dev, void* scratch, cudaStream_t st) {
   const int64_t nt = ceil_div(n, kTile);

@@ -109,9 +109,9 @@ def logw_tc_bound(up, s, olw, u, q):
     tolerance plus the dropped columns' share, at most nc 2^-45 of the row
     sum.  A row within 1% of the cut may be on either side (the library
     evaluates B_j in fp32)."""
-    from test_gpu_parity import logw_tolerance
+    from test_gpu_parity import logw_tolerance_direct_fp32
     B = tc_row_bound(up, s, u, q)
-    fp = logw_tolerance(s, olw) + int(np.sum(q > 0)) * 2.0**-45
+    fp = logw_tolerance_direct_fp32(s, olw) + int(np.sum(q > 0)) * 2.0**-45
     return np.where(B <= 1.01 * TC_BOUND_MAX, np.maximum(B, fp), fp)
 
 

@@ -226,24 +226,27 @@ def test_gaussian_toy_closed_form_posterior():
     """Conjugate toy (x ~ N(theta, I8), flat box prior, x_obs = 0): the ABC
     posterior at tolerance eps is Y - Z with Y uniform on the eps-ball and
     Z ~ N(0, I8): mean 0, variance 1 + eps^2/10 per coordinate.  Importance
-    weights (mode 1) with a narrow fixed Beta(8, 1000) step; 6 seeds; the
-    weighted moments must agree within 3 Monte-Carlo standard errors."""
+    weights (mode 1) with a narrow fixed Beta(8, 1000) step; 10 independent
+    runs (seeds 1..10).  Per run, the weighted mean and the weighted variance
+    over v0 = 1 + eps^2/10 are averaged over the 8 exchangeable coordinates;
+    over the 10 runs both must lie within 2 Monte-Carlo standard errors
+    (the runs' standard deviation / sqrt 10) of 0 and 1."""
     lo, hi = np.full(8, -10, np.float32), np.full(8, 10, np.float32)
-    ratios, zs, ses = [], [], []
-    for seed in range(1, 7):
+    means, ratios = [], []
+    for seed in range(1, 11):
         m = O.OracleModel(model=1, T=0, P=1, theta_lo=lo, theta_hi=hi, seed=seed)
         c = O.make_smc(2048, beta_mode=1, beta_a=8.0, beta_b=1000, weight_mode=1,
                        max_batches=400, nthreads=4)
         pop, stats = O.run(m, c, 10)
         assert all(s.status == 0 for s in stats)
-        eps, ess = stats[-1].eps, stats[-1].ess
+        eps = stats[-1].eps
         th = lo[:, None] + pop.u * (hi - lo)[:, None]
         mean = (th * pop.W).sum(1)
         var = (th**2 * pop.W).sum(1) - mean**2
-        v0 = 1 + eps**2 / 10
-        ratios.append(var.mean() / v0)
-        ses.append(math.sqrt(2.0 / (ess * 8)))
-        zs.append(mean.mean() / math.sqrt(v0 / ess / 8))
-    se = math.sqrt(sum(s**2 for s in ses)) / len(ses)
-    assert abs(np.mean(ratios) - 1) < 3 * se, (ratios, se)
-    assert abs(np.mean(zs)) * math.sqrt(len(zs)) < 3, zs
+        means.append(mean.mean())
+        ratios.append(var.mean() / (1 + eps**2 / 10))
+    means, ratios = np.array(means), np.array(ratios)
+    se_m = means.std(ddof=1) / math.sqrt(len(means))
+    se_v = ratios.std(ddof=1) / math.sqrt(len(ratios))
+    assert abs(means.mean()) < 2 * se_m, (means, se_m)
+    assert abs(ratios.mean() - 1) < 2 * se_v, (ratios, se_v)
