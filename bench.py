@@ -1,19 +1,23 @@
 """Benchmark: P-ABC-SMC with Beta-distributed step sizes on one GB300.
 
-A step is one SMC generation (Sec. 2.4, 3.2) of the single-run workload at
-scale -- 2^20 particles, population 1e7, 120 days, importance weights with
-the O(N^2) kernel sum, the paper's Beta(eps_t/eps_1, 2t) step schedule --
-on synthetic observations simulated from a seeded theta*: select eps_t,
-stage-prior prefix, batches of proposals (ancestor, Beta step, walk, support
-check), simulation, acceptance, O(N^2) weights, fp64 normalisation.
+A step is one whole run of the single-run workload at scale (Sec. 2.4,
+3.2): 2^20 particles, population 1e7, 120 days, G = 20 generations (stage 0
+and 19 perturbed generations), importance weights with the O(N^2) kernel
+sum, the paper's Beta(eps_t/eps_1, 2t) step schedule, on synthetic
+observations simulated from a seeded theta*.  Every generation runs the whole
+hot path: select eps_t, stage-prior prefix, batches of proposals (ancestor,
+Beta step, walk, support check), simulation, acceptance, O(N^2) weights,
+fp64 normalisation.  Step k is run k (Philox key (seed_lo, seed_hi ^ k)).
 
-value: simulated particle-days per second over K generations with inputs
-resident in HBM (CUDA events on the library's stream).  e2e: the same
-metric through the public C ABI from pinned host buffers: each step loads
-the population with abc_set_state (host to device), runs the generation
-and reads the new population back (device to host).
---impl reference: the CPU oracle on the host cores, on bounded samples of
-the same step, extrapolated to the step's work.
+value: simulated particle-days per second over K runs with inputs resident
+in HBM (CUDA events on the library's stream); ms_per_step is the wall-time
+of one run.  e2e: the same metric through the public C ABI per run --
+abc_init from the pinned host series, abc_run, the final population read
+back to pinned host memory, abc_free.
+cpu_baseline and --impl reference: the CPU oracle on the host cores, each
+step one whole run of the same workload at a bounded sample size (8192
+particles; same days, population, schedule, weights and generations),
+measured, not extrapolated.
 """
 import argparse
 import json
@@ -31,11 +35,12 @@ METRIC = "sim-days/s; wall-time to ε_final per run, surrogate+batched vs plain"
 UNIT = "sim-days/s"
 MUFU_EX2_PER_CLK_PER_SM = 16  # 32-bit exp2 issue rate of one SM (4 SMSPs x 4 lanes)
 TC_K_USED = 60  # split-bf16 products per pair in the tensor-core weight GEMM (10 features x 6)
-# thread-level instructions per particle-day of k_simulate: ncu smsp__inst_executed.sum x
-# smsp__thread_inst_executed_per_inst_executed.ratio / (particles x days) for one launch of
-# the timed generation of the 262,144-particle, 120-day, P = 1e7 workload
-SIM_THREAD_INST_PER_DAY = 927.0
-SIM_DRAM_BYTES_PER_DAY = 8.73e6 / (262144 * 120)  # same capture, DRAM read + write
+K_EFF = 10  # features of the weight pass's inner product (its algorithmic K)
+# k_simulate per particle-day, from one ncu capture of every simulator launch of a whole
+# 20-generation run of the 262,144-particle case of the workload (54 launches, 1.698e9
+# particle-days): smsp__thread_inst_executed.sum / particle-days, and DRAM read + write bytes
+SIM_THREAD_INST_PER_DAY = 984.9
+SIM_DRAM_BYTES_PER_DAY = 0.2786
 
 
 def _peaks():
@@ -142,6 +147,18 @@ def _nvtx(torch, name):
         pass
 
 
+def bench_config(w, G_run, prec):
+    """The config object of the single-run workload, shared by both arms."""
+    return {"workload": w.name, "particles": w.N, "days": w.T, "population": w.P,
+            "generations_per_run": G_run,
+            "step": "one whole run (stage 0 + %d perturbed generations)" % (G_run - 1),
+            "weights": "importance O(N^2), " + (
+                "bf16 tcgen05 (rows with log W error bound <= 0.0166) + exact refinement"
+                if prec else "fp32 (double-float near the row maximum)"),
+            "beta_schedule": "paper (eps_t/eps_1, 2t)",
+            "l2": "flushed between steps (256 MB write)"}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -165,6 +182,7 @@ def run_gpu(args):
     if args.particles:  # a smaller case of the same workload (profiling)
         import dataclasses
         w = dataclasses.replace(w, N=args.particles, name="saird_n%d_t120_p1e7" % args.particles)
+    G_run = args.generations or w.G
     # independent runs per rank (weak scaling, no data-path collective)
     cfg = rank_config(w, rank, weight_prec=args.prec)
     obs, theta_star = synthetic_obs(G, WL, cfg, torch)
@@ -173,198 +191,183 @@ def run_gpu(args):
     ctx = G.abc_init(cfg, obs, stream=sp)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     N = w.N
+
+    def one_run(run_id):
+        G.abc_reset(ctx, run_id)
+        rc = G.abc_run(ctx, G_run)
+        if rc != G.ABC_OK or G.abc_generations(ctx) != G_run:
+            raise RuntimeError("run %d stopped at generation %d: %s" % (
+                run_id, G.abc_generations(ctx), G.strerror(rc)))
+        return [G.abc_get_stats(ctx, t) for t in range(G_run)]
+
     try:
-        # warm-up: stage 0 and W generations
-        G.abc_generation(ctx)
-        for _ in range(args.warmup):
-            rc = G.abc_generation(ctx)
-            if rc != G.ABC_OK:
-                raise RuntimeError("warm-up generation stopped: %s" % G.strerror(rc))
+        for k in range(args.warmup):  # warm-up runs (their own run ids)
+            one_run(1000 + k)
         flush.zero_()  # loads the flush kernel's module before the timed region
         torch.cuda.synchronize()
-        blob = G.abc_get_state(ctx)  # state before the first timed generation
-        g_first = G.abc_generations(ctx)
         clocks = Clocks(local)
         clocks.start()
         time.sleep(0.3)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        stats = []
+        runs = []
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
             # NVTX range "timed" (host calls outside the events): lets a profiler
-            # keep the timed generations only
+            # keep the timed runs only
             _nvtx(torch, "timed")
             e0.record(stream)
             for k in range(args.steps):
                 if k:
                     flush.zero_()  # L2 (129 MB) flushed between steps
-                rc = G.abc_generation(ctx)
-                if rc != G.ABC_OK:
-                    raise RuntimeError("timed generation stopped: %s" % G.strerror(rc))
-                stats.append(G.abc_get_stats(ctx, G.abc_generations(ctx) - 1))
+                runs.append(one_run(k))
             e1.record(stream)
             _nvtx(torch, None)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         clk = clocks.stop()
-        sim_days = sum(s.sim_days for s in stats)
-        launches = sum(s.launches for s in stats)
-        # end to end through the C ABI with pinned host buffers, over the same
-        # generations as the device-timed loop: step k uploads the state
-        # before generation g_first + k (captured in an untimed replay) and
-        # reads the new population back
-        G.abc_set_state(ctx, blob)
-        blobs = []
-        for _ in range(args.steps):
-            blobs.append(G.abc_get_state(ctx))
-            G.abc_generation(ctx)
-        hbufs = []
-        for b_ in blobs:
-            hb = torch.empty(len(b_), dtype=torch.uint8, pin_memory=True)
-            hb.numpy()[:] = np.frombuffer(b_, np.uint8)
-            hbufs.append(hb)
-        pop_h = dict(u=torch.empty((8, N), dtype=torch.float32, pin_memory=True),
-                     d=torch.empty(N, dtype=torch.float64, pin_memory=True),
-                     W=torch.empty(N, dtype=torch.float64, pin_memory=True),
-                     s=torch.empty(N, dtype=torch.float32, pin_memory=True),
-                     anc=torch.empty(N, dtype=torch.int32, pin_memory=True))
-        e2e_days = 0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            G.abc_set_state_ptr(ctx, hbufs[k].data_ptr(), hbufs[k].numel())
-            G.abc_generation(ctx)
-            e2e_days += G.abc_get_stats(ctx, G.abc_generations(ctx) - 1).sim_days
-            G.abc_get_population(ctx, pop_h["u"].data_ptr(), pop_h["d"].data_ptr(),
-                                 pop_h["W"].data_ptr(), pop_h["s"].data_ptr(),
-                                 pop_h["anc"].data_ptr(), on_device=False)
-        e2e_s = time.perf_counter() - t0
-        d2h = sum(t.numel() * t.element_size() for t in pop_h.values())
     finally:
         G.abc_free(ctx)
+    stats = [s for r in runs for s in r]
+    sim_days = sum(s.sim_days for s in stats)
+    launches = sum(s.launches for s in stats)
+    # end to end through the C ABI per run: the observed series from pinned
+    # host memory (abc_init copies it to the device), the whole run, the
+    # final population back to pinned host memory
+    obs_h = torch.from_numpy(np.ascontiguousarray(obs)).pin_memory()
+    pop_h = dict(u=torch.empty((8, N), dtype=torch.float32, pin_memory=True),
+                 d=torch.empty(N, dtype=torch.float64, pin_memory=True),
+                 W=torch.empty(N, dtype=torch.float64, pin_memory=True),
+                 s=torch.empty(N, dtype=torch.float32, pin_memory=True),
+                 anc=torch.empty(N, dtype=torch.int32, pin_memory=True))
+    e2e_days = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        c_k = rank_config(w, rank, weight_prec=args.prec, run_id=k)
+        h = G.abc_init_ptr(c_k, obs_h.data_ptr(), stream=sp)
+        try:
+            if G.abc_run(h, G_run) != G.ABC_OK:
+                raise RuntimeError("e2e run %d stopped" % k)
+            e2e_days += sum(G.abc_get_stats(h, t).sim_days for t in range(G_run))
+            G.abc_get_population(h, pop_h["u"].data_ptr(), pop_h["d"].data_ptr(),
+                                 pop_h["W"].data_ptr(), pop_h["s"].data_ptr(),
+                                 pop_h["anc"].data_ptr(), on_device=False)
+        finally:
+            G.abc_free(h)
+    e2e_s = time.perf_counter() - t0
+    d2h = sum(t.numel() * t.element_size() for t in pop_h.values())
+    h2d = obs_h.numel() * obs_h.element_size()
     rank_ms = ms
     value, e2e_value, ms = job_totals(ms, sim_days, e2e_days, e2e_s, ws)
     if rank != 0:
         return None
+    K = args.steps
     peaks, src = _peaks()
-    # dominant kernel: the O(N^2) weight pass; unit = pair-exponentials
     pairs = sum(s.pairs for s in stats)
     wms = sum(s.ms_weights for s in stats)
     sim_ms = sum(s.ms_sim for s in stats)
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
+    clk_mhz = float(clk.get("sm_mhz") or sm_mhz) if isinstance(clk, dict) else sm_mhz
     # the exp unit's rate, measured on this GPU by the library's probe
     exp_peak = G.abc_ex2_probe()
     exp_nominal = n_sm * MUFU_EX2_PER_CLK_PER_SM * sm_mhz * 1e6
-    # the weight pass splits into the tensor-core kernel and the FP32 kernel
-    # (rows whose tensor-core error bound is too large); the roofline line is
-    # for the one with the larger device time, timed by events around it
-    # rows off the tensor cores: the FP32 kernel (FP32 precision) or, in the
-    # BF16 precision, the per-row kernel for the rare class-2 rows
-    fb_name = "k_fb_rows" if args.prec else "k_weights_fp32"
-    kern = {}
-    for name, ms_k, rows_k in (("k_weights_tc", sum(s.ms_tc for s in stats),
-                                [s.rows_tc for s in stats]),
-                               (fb_name, sum(s.ms_fp32 for s in stats),
-                                [N - s.rows_tc for s in stats])):
-        pk = sum(r * (s.pairs // N) for r, s in zip(rows_k, stats))
-        kern[name] = {"ms": ms_k / args.steps, "pairs": pk / args.steps,
-                      "gexp_s": pk / (ms_k / 1e3) / 1e9 if ms_k > 0 else 0.0}
-    # the tensor-core kernel does two kinds of work: the split-bf16 GEMM over
-    # the tiles it visits (2 x 60 flops per pair: 10 features x 6
-    # split products; class-1 row tiles skip the column tiles beyond their
-    # candidate radius) and one exponential per pair of the rows whose sums it
-    # keeps (rows_exp; the other rows only get candidate lists).  Its roofline
-    # is whichever of the two lower bounds on its time is larger.
-    tc_ms = kern["k_weights_tc"]["ms"]
-    tc_flops = sum(2 * TC_K_USED * s.pairs_tc for s in stats) / args.steps
-    tc_exps = sum(s.rows_exp * (s.pairs // N) for s in stats) / args.steps
-    kern["k_weights_tc"].update({"exp_pairs": tc_exps, "tflops": tc_flops / (tc_ms / 1e3) / 1e12
-                                 if tc_ms > 0 else 0.0})
     exp_src = ("measured ex2.approx.f32 rate (abc_ex2_probe: saturating microbenchmark on "
                "this GPU); %d SMs x %d ex2/clk x %.0f MHz would be %.0f Gexp/s" % (
                    n_sm, MUFU_EX2_PER_CLK_PER_SM, sm_mhz, exp_nominal / 1e9))
-    # the simulator: issue-slot roofline at the lane level (SMs x 4 warp
-    # instructions per clock x 32 lanes at the median SM clock under load)
-    sim_step_ms = sim_ms / args.steps
-    sim_days_step = sim_days / args.steps
-    n_sim_launches = sum(s.batches for s in stats) / args.steps
-    clk_mhz = float(clk.get("sm_mhz") or sm_mhz) if isinstance(clk, dict) else sm_mhz
+    tc_peak = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])) * 1e12
+    fb_name = "k_fb_rows" if args.prec else "k_weights_fp32"
+    roofs = {}
+    # simulator: lane-level issue slots (SMs x 4 warp instructions/clk x 32
+    # lanes at the median SM clock sampled under load); the work unit is the
+    # thread instructions per particle-day counted by ncu over whole runs
     lane_peak = n_sm * 4 * 32 * clk_mhz * 1e6
-    sim_rate = SIM_THREAD_INST_PER_DAY * sim_days_step / (sim_step_ms / 1e3) if sim_step_ms > 0 \
-        else 0.0
-    sim_roof = {"bound": "alu", "kernel": "k_simulate", "achieved": sim_rate / 1e12,
-                "peak": lane_peak / 1e12, "unit": "Tinst/s (thread-level)",
-                "frac": sim_rate / lane_peak,
-                "peak_source": "%d SMs x 4 warp-instructions/clk x 32 lanes x %.0f MHz (median "
-                               "SM clock sampled under load)" % (n_sm, clk_mhz),
-                "work": "%.0f thread instructions per particle-day (ncu, timed generation)"
-                        % SIM_THREAD_INST_PER_DAY,
-                "traffic": SIM_DRAM_BYTES_PER_DAY * sim_days_step / n_sim_launches
-                if n_sim_launches else None,
-                "traffic_note": "bytes per launch scaled from a 262,144-particle capture"}
-    tc_roof = None
+    sim_rate = SIM_THREAD_INST_PER_DAY * sim_days / (sim_ms / 1e3) if sim_ms > 0 else 0.0
+    n_sim_launches = sum(s.batches for s in stats)
+    roofs["k_simulate"] = {
+        "bound": "alu", "kernel": "k_simulate", "achieved": sim_rate / 1e12,
+        "peak": lane_peak / 1e12, "unit": "Tinst/s (thread-level)", "frac": sim_rate / lane_peak,
+        "ms_per_step": sim_ms / K,
+        "peak_source": "%d SMs x 4 warp-instructions/clk x 32 lanes x %.0f MHz (median SM "
+                       "clock sampled under load)" % (n_sm, clk_mhz),
+        "work": "%.1f thread instructions per particle-day (ncu over the simulator launches "
+                "of whole runs)" % SIM_THREAD_INST_PER_DAY,
+        "traffic": SIM_DRAM_BYTES_PER_DAY * sim_days / n_sim_launches if n_sim_launches else None,
+        "traffic_note": "DRAM bytes per launch, per particle-day from the same capture"}
+    # tensor-core weight kernel: the split-bf16 GEMM over the tiles it visits
+    # (2 x 60 flops per pair: 10 features x 6 split products) and one
+    # exponential per pair of the rows whose sums it keeps; its roofline is
+    # the larger of the two lower bounds on its time.  The algorithmic count
+    # of the survey (2 K_eff = 20 flops per pair of all N x N_surv pairs) is
+    # given beside it.
+    tc_ms = sum(s.ms_tc for s in stats)
     if tc_ms > 0:
-        tc_peak = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])) * 1e12
-        t_tensor = tc_flops / tc_peak
-        t_exp = tc_exps / exp_peak
+        tc_flops = sum(2 * TC_K_USED * s.pairs_tc for s in stats)
+        alg_flops = sum(2 * K_EFF * s.pairs for s in stats)
+        tc_exps = sum(s.rows_exp * (s.pairs // N) for s in stats)
+        t_tensor, t_exp = tc_flops / tc_peak, tc_exps / exp_peak
+        common = {"kernel": "k_weights_tc", "ms_per_step": tc_ms / K,
+                  "pairs_per_step": pairs / K,
+                  "visited_pairs_per_step": sum(s.pairs_tc for s in stats) / K,
+                  "kept_row_exps_per_step": tc_exps / K,
+                  "algorithmic_tflops": alg_flops / (tc_ms / 1e3) / 1e12,
+                  "algorithmic_tensor_frac": alg_flops / (tc_ms / 1e3) / tc_peak,
+                  "traffic": None}
         if t_tensor >= t_exp:
             a = tc_flops / (tc_ms / 1e3)
-            tc_roof = {"bound": "tensor", "kernel": "k_weights_tc", "achieved": a / 1e12,
-                        "peak": tc_peak / 1e12, "unit": "TFLOP/s", "frac": a / tc_peak,
-                        "peak_source": "%s bf16 dense GEMM, sustained (cuBLAS, %s)" % (
-                            src, "MEASURED_PEAKS.json" if src == "measured" else "recipe"),
-                        "work": "2 x 60 flops per (row, column) pair of the visited tiles",
-                        "pairs_per_step": sum(s.pairs_tc for s in stats) / args.steps,
-                        "exp_frac": tc_exps / (tc_ms / 1e3) / exp_peak, "traffic": None}
+            roofs["k_weights_tc"] = dict(common, bound="tensor", achieved=a / 1e12,
+                                         peak=tc_peak / 1e12, unit="TFLOP/s", frac=a / tc_peak,
+                                         peak_source="%s bf16 dense GEMM, sustained (cuBLAS)" % src,
+                                         work="2 x 60 flops per pair of the visited tiles",
+                                         exp_frac=tc_exps / (tc_ms / 1e3) / exp_peak)
         else:
             a = tc_exps / (tc_ms / 1e3)
-            tc_roof = {"bound": "alu", "kernel": "k_weights_tc", "achieved": a / 1e9,
-                       "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": a / exp_peak,
-                       "peak_source": exp_src, "work": "one exp2 per pair of the kept rows",
-                       "tensor_frac": tc_flops / (tc_ms / 1e3) / tc_peak, "traffic": None}
-    fp32_ms = kern[fb_name]["ms"]
-    fp32_roof = {"bound": "alu", "kernel": fb_name,
-                 "achieved": kern[fb_name]["gexp_s"], "peak": exp_peak / 1e9,
-                 "unit": "Gexp/s", "frac": kern[fb_name]["gexp_s"] * 1e9 / exp_peak,
-                 "peak_source": exp_src, "work": "one exp2 per pair", "traffic": None}
+            roofs["k_weights_tc"] = dict(common, bound="alu", achieved=a / 1e9,
+                                         peak=exp_peak / 1e9, unit="Gexp/s", frac=a / exp_peak,
+                                         peak_source=exp_src,
+                                         work="one exp2 per pair of the kept rows",
+                                         tensor_frac=tc_flops / (tc_ms / 1e3) / tc_peak)
+    fb_ms = sum(s.ms_fp32 for s in stats)
+    if fb_ms > 0:
+        fb_pairs = sum((N - s.rows_tc) * (s.pairs // N) for s in stats)
+        a = fb_pairs / (fb_ms / 1e3)
+        roofs[fb_name] = {"bound": "alu", "kernel": fb_name, "achieved": a / 1e9,
+                          "peak": exp_peak / 1e9, "unit": "Gexp/s", "frac": a / exp_peak,
+                          "ms_per_step": fb_ms / K, "peak_source": exp_src,
+                          "work": "one exp2 per pair", "traffic": None}
     # the roofline line is the dominant kernel's: the largest device time per step
-    cands = [(sim_step_ms, sim_roof), (fp32_ms, fp32_roof)]
-    if tc_roof is not None:
-        cands.append((tc_ms, tc_roof))
-    roofline = max(cands, key=lambda c: c[0])[1]
+    roofline = max(roofs.values(), key=lambda r: r["ms_per_step"])
+    ess = [s.ess / N for s in stats if s.generation > 0]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "particles": N, "days": w.T, "population": w.P,
-                   "weights": "importance O(N^2), " + (
-                       "bf16 tcgen05 (rows with log W error bound <= 0.0166) + fp32"
-                       if args.prec else "fp32"),
-                   "beta_schedule": "paper (eps_t/eps_1, 2t)", "generations_timed":
-                   [g_first + k for k in range(args.steps)],
-                   "l2": "flushed between steps (256 MB write)",
-                   "theta_star": [round(float(x), 6) for x in theta_star]},
+        "config": dict(bench_config(w, G_run, args.prec),
+                       theta_star=[round(float(x), 6) for x in theta_star]),
         "roofline": roofline,
-        "weight_kernels": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in kern.items()},
-        "rooflines": {"k_simulate": sim_roof, "k_weights_tc": tc_roof,
-                      fb_name: fp32_roof if fp32_ms > 0 else None},
+        "rooflines": roofs,
+        "wall_time_per_run_s": ms / K / 1e3,
+        "pairs_per_step": pairs / K,
+        "ess_over_n": {"median": float(np.median(ess)), "min": float(np.min(ess)),
+                       "max": float(np.max(ess))},
         "weight_pass_gexp_s": pairs / (wms / 1e3) / 1e9 if wms > 0 else 0.0,
-        "phases_ms": {"weights": wms / args.steps, "simulator": sim_ms / args.steps,
-                      "rest": (rank_ms - wms - sim_ms) / args.steps},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(blob),
+        "phases_ms_per_step": {"weights": wms / K, "simulator": sim_ms / K,
+                               "rest": (rank_ms - wms - sim_ms) / K},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
-        "generations": [{"t": s.generation, "eps": s.eps, "ess": s.ess, "batches": s.batches,
-                         "sim_days": s.sim_days, "ms": s.ms, "rows_exp": s.rows_exp,
-                         "rows_tc": s.rows_tc, "ms_tc": s.ms_tc} for s in stats],
+        "generations_of_last_run": [
+            {"t": s.generation, "eps": s.eps, "ess_over_n": s.ess / N, "batches": s.batches,
+             "sim_days": s.sim_days, "pairs": s.pairs, "pairs_tc": s.pairs_tc, "ms": s.ms,
+             "ms_sim": s.ms_sim, "ms_tc": s.ms_tc, "ms_fb": s.ms_fp32, "rows_exp": s.rows_exp}
+            for s in runs[-1]],
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(stats, w)
+        line["cpu_baseline"] = cpu_baseline(w, G_run)
     return line
 
 
@@ -505,42 +508,41 @@ def run_sweep_bench(args):
             "sweep": {str(k): v for k, v in summ.items()}}
 
 
-def cpu_baseline(stats, w):
-    """The oracle as it stands on the host cores, on a bounded sample of the
-    step: a batch of simulations and a block of weight rows, each timed,
-    extrapolated to the average step's simulated days and weight pairs."""
-    import numpy as np
+ORACLE_SAMPLE_N = 8192  # particles of the oracle's sample runs
 
+
+def oracle_sample_run(w, G_run, run_id, cores):
+    """One whole run of the workload by the CPU oracle at ORACLE_SAMPLE_N
+    particles (same days, population, observed series, paper schedule,
+    importance weights and generations), on `cores` threads.  Returns
+    (simulated particle-days, seconds)."""
     import oracle as O
     from paper_2106_15508_gb300 import workloads as WL
 
-    cores = os.cpu_count() or 1
-    m = O.OracleModel(T=w.T, P=w.P, A0=WL.initial_active(w.P), seed=w.seed)
-    obs, _, _ = O.synth_obs(m)
+    A0 = WL.initial_active(w.P)
+    m0 = O.OracleModel(T=w.T, P=w.P, A0=A0, seed=w.seed)
+    obs, _, _ = O.synth_obs(m0)
+    m = O.OracleModel(T=w.T, P=w.P, A0=A0, seed=w.seed, run=run_id)
     m.set_obs(obs)
-    n_sim = 1 << 14
-    u = O.prior(m, n_sim)
+    c = O.make_smc(ORACLE_SAMPLE_N, beta_mode=w.beta_mode, weight_mode=w.weight_mode,
+                   alpha=w.alpha, max_batches=w.max_batches, nthreads=cores)
     t0 = time.perf_counter()
-    O.simulate(m, u, nthreads=cores)
-    t_sim = time.perf_counter() - t0
-    per_day = t_sim / (n_sim * w.T)
-    rows, cols = 256, w.N // 2
-    rng = np.random.default_rng(0)
-    up = rng.uniform(0.3, 0.7, (8, rows)).astype(np.float32)
-    uc = rng.uniform(0.3, 0.7, (8, cols)).astype(np.float32)
-    s = rng.uniform(1e-4, 0.05, rows).astype(np.float32)
-    q = rng.integers(1, 2**32, cols, dtype=np.uint64).astype(np.uint32)
-    t0 = time.perf_counter()
-    O.weights(up, s, uc, q, int(q.astype(np.uint64).sum()), nthreads=cores)
-    t_w = time.perf_counter() - t0
-    per_pair = t_w / (rows * cols)
-    days = sum(x.sim_days for x in stats) / len(stats)
-    pairs = sum(x.pairs for x in stats) / len(stats)
-    step_s = days * per_day + pairs * per_pair
-    return {"value": days / step_s, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d simulations x %d days (%.2f s) and %d weight rows x %d columns "
-                      "(%.2f s), extrapolated to the step's %.3g sim-days and %.3g pairs" % (
-                          n_sim, w.T, t_sim, rows, cols, t_w, days, pairs)}
+    _, stats = O.run(m, c, G_run)
+    secs = time.perf_counter() - t0
+    days = ORACLE_SAMPLE_N * w.T + sum((s.sims - s.exhausted) * w.T for s in stats)
+    return days, secs
+
+
+def cpu_baseline(w, G_run):
+    """The oracle as it stands on the host cores: one sample run (the same
+    function as the reference arm's steps)."""
+    cores = os.cpu_count() or 1
+    days, secs = oracle_sample_run(w, G_run, 0, cores)
+    return {"value": days / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "one whole %d-generation run at %d particles (%.3g sim-days in %.2f s); "
+                      "the O(N^2) weight pass is a smaller share at this size than at %d "
+                      "particles, so this rate is above the oracle's full-size rate" % (
+                          G_run, ORACLE_SAMPLE_N, days, secs, w.N)}
 
 
 def run_eps_final(args):
@@ -567,7 +569,7 @@ def run_eps_final(args):
     obs = [synthetic_obs(G, WL, c, torch)[0] for c in cfgs]
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
-    gens = args.generations
+    gens = args.generations or 8
     # plain
     eps_final, t_plain, sims_plain = [], [], []
     for c, o in zip(cfgs, obs):
@@ -698,57 +700,31 @@ def run_passes(args):
 
 
 def run_reference(args):
-    """The oracle arm: each step is a bounded sample of one generation of the
-    same workload on the host cores; value extrapolated to the full step."""
-    import numpy as np
-
-    import oracle as O
+    """The oracle arm: each step is one whole run of the same workload by the
+    CPU oracle at a bounded sample size (oracle_sample_run), measured."""
     from paper_2106_15508_gb300 import workloads as WL
 
     ws, rank = _dist()
     if rank != 0:
         return None
     w = WL.LARGE
+    G_run = args.generations or w.G
     cores = os.cpu_count() or 1
-    m = O.OracleModel(T=w.T, P=w.P, A0=WL.initial_active(w.P), seed=w.seed)
-    obs, _, _ = O.synth_obs(m)
-    m.set_obs(obs)
-    # the timed generations (4-6) of this workload on the GPU arm simulate two
-    # batches of N and weigh N rows against ~66,650 survivor columns with
-    # q > 0 (6.99e10 pairs per generation, measured); the sample times the
-    # same kernels at that column count
-    n_sim, rows, cols = 1 << 13, 256, 66_650
-    rng = np.random.default_rng(1)
-    uc = rng.uniform(0.3, 0.7, (8, cols)).astype(np.float32)
-    q = rng.integers(1, 2**32, cols, dtype=np.uint64).astype(np.uint32)
-    tot = int(q.astype(np.uint64).sum())
-    step_days, step_pairs = 2 * w.N * w.T, w.N * cols
-
-    def one_step(k):
-        u = O.prior(m, n_sim)
-        t0 = time.perf_counter()
-        O.simulate(m, u, c1=k, nthreads=cores)
-        t_sim = time.perf_counter() - t0
-        up = rng.uniform(0.3, 0.7, (8, rows)).astype(np.float32)
-        s = rng.uniform(1e-4, 0.05, rows).astype(np.float32)
-        t0 = time.perf_counter()
-        O.weights(up, s, uc, q, tot, nthreads=cores)
-        t_w = time.perf_counter() - t0
-        return t_sim / (n_sim * w.T) * step_days + t_w / (rows * cols) * step_pairs
-
     for k in range(args.warmup):
-        one_step(k)
-    secs = [one_step(100 + k) for k in range(args.steps)]
-    step_s = sum(secs) / len(secs)
-    value = step_days / step_s
-    sample = ("per step: %d simulations x %d days and %d weight rows x %d columns, "
-              "extrapolated to %.3g sim-days and %.3g pairs" % (n_sim, w.T, rows, cols,
-                                                               step_days, step_pairs))
+        oracle_sample_run(w, G_run, 1000 + k, cores)
+    days = secs = 0.0
+    for k in range(args.steps):
+        d, t = oracle_sample_run(w, G_run, k, cores)
+        days += d
+        secs += t
+    value = days / secs
+    sample = ("each step one whole %d-generation run at %d particles (of %d), measured; the "
+              "O(N^2) weight pass is a smaller share at this size, so this rate is above the "
+              "oracle's full-size rate" % (G_run, ORACLE_SAMPLE_N, w.N))
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": {"workload": w.name, "particles": w.N, "days": w.T,
-                                            "population": w.P},
+            "data": "synthetic", "config": bench_config(w, G_run, args.prec),
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores,
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -775,7 +751,8 @@ def main():
     ap.add_argument("--grouping", default="all", choices=["all", "level", "run"],
                     help="sweep: one batch of all runs, one per level, or one per run")
     ap.add_argument("--pass-n", type=int, default=1 << 28)
-    ap.add_argument("--generations", type=int, default=8)
+    ap.add_argument("--generations", type=int, default=0,
+                    help="generations per run (single: 20, the workload's G; eps_final: 8)")
     ap.add_argument("--surrogate-steps", type=int, default=32)
     ap.add_argument("--surrogate-tau", type=float, default=0.5)
     ap.add_argument("--stress", action="store_true",

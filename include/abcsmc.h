@@ -446,6 +446,14 @@ ABC_API int abc_generation(abc_ctx* ctx);
  * (eps_target <= 0 disables it) or the run budget is used up; returns the
  * last generation's status (ABC_STOP_TOTAL for the budget). */
 ABC_API int abc_run(abc_ctx* ctx, int32_t n_generations, double eps_target);
+/* Start the context over at stage 0 as a new run with the given run_id (the
+ * Philox key becomes (seed_lo, seed_hi ^ run_id)), keeping its buffers,
+ * observed series and stream: statistics, generation count, run budget
+ * count and eps_1 are cleared, and the surrogate (if any) is re-initialised
+ * from the new key.  The next abc_generation runs stage 0; the results equal
+ * those of a fresh context whose config carries that run_id.  Synchronises
+ * the stream. */
+ABC_API int abc_reset(abc_ctx* ctx, uint32_t run_id);
 /* Copy the population: u [8][N] float, dist, W double[N], s float[N] and
  * anc int32[N] (ancestor index in the previous population, -1 at t = 0);
  * any pointer may be NULL; on_device != 0 means the pointers are device

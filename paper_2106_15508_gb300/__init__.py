@@ -42,7 +42,7 @@ EXPORTS = (
     "abc_predict_population",
     "abc_mlp_param_count", "abc_mlp_create", "abc_mlp_set_params", "abc_mlp_get_params",
     "abc_mlp_scratch_bytes", "abc_mlp_grad", "abc_mlp_adam", "abc_mlp_forward", "abc_mlp_free",
-    "abc_set_wait_limit_ns", "abc_inject_alloc_failure",
+    "abc_set_wait_limit_ns", "abc_inject_alloc_failure", "abc_reset",
 )
 
 
@@ -151,6 +151,7 @@ _SIGS = {
     "abc_mlp_free": (None, [_V]),
     "abc_set_wait_limit_ns": (None, [C.c_uint64]),
     "abc_inject_alloc_failure": (None, [_I64]),
+    "abc_reset": (C.c_int, [_V, _U32]),
 }
 
 
@@ -311,6 +312,15 @@ def abc_init(cfg, obs_host, stream=None):
     return h
 
 
+def abc_init_ptr(cfg, obs_host_ptr, stream=None):
+    """abc_init with the observed series given by host address (e.g. pinned
+    memory; 0 or None for the toy model)."""
+    h = C.c_void_p()
+    _check(lib().abc_init(C.byref(cfg), obs_host_ptr or None, _stream(stream), C.byref(h)),
+           "abc_init")
+    return h
+
+
 def abc_generation(ctx):
     return _check(lib().abc_generation(ctx), "abc_generation",
                   ok=(ABC_OK, ABC_STOP_BUDGET, ABC_STOP_TOTAL))
@@ -319,6 +329,11 @@ def abc_generation(ctx):
 def abc_run(ctx, n_generations, eps_target=0.0):
     return _check(lib().abc_run(ctx, n_generations, eps_target), "abc_run",
                   ok=(ABC_OK, ABC_STOP_BUDGET, ABC_STOP_TARGET, ABC_STOP_TOTAL))
+
+
+def abc_reset(ctx, run_id):
+    """Start the context over at stage 0 as run `run_id`."""
+    return _check(lib().abc_reset(ctx, int(run_id)), "abc_reset")
 
 
 def abc_get_population(ctx, u=None, dist=None, W=None, s=None, anc=None, on_device=False):

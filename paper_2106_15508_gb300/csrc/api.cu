@@ -997,6 +997,27 @@ ABC_API int abc_run(abc_ctx* c, int32_t n_generations, double eps_target) {
   return rc;
 }
 
+ABC_API int abc_reset(abc_ctx* c, uint32_t run_id) {
+  if (!c) return ABC_E_INVAL;
+  ABC_CUDA_TRY(cudaStreamSynchronize(c->st));
+  c->cfg.run_id = run_id;
+  c->p = make_params(c->cfg);
+  c->gen = 0;
+  c->cur = 0;
+  c->eps1_host = 0.0;
+  c->batches_total = 0;
+  c->stats.clear();
+  ABC_CUDA_TRY(cudaMemsetAsync(c->scal, 0, 4 * sizeof(double), c->st));
+  if (c->cfg.surrogate) {
+    c->train_step = 0;
+    ABC_CUDA_TRY(cudaMemsetAsync(c->ring_head, 0, sizeof(long long), c->st));
+    const int rc = mlp_init(c->mlp, c->p.k0, c->p.k1, c->st);
+    if (rc) return rc;
+  }
+  ABC_CUDA_TRY(cudaStreamSynchronize(c->st));
+  return ABC_OK;
+}
+
 ABC_API int abc_get_population(abc_ctx* c, float* u, double* dist, double* W, float* s,
                                int32_t* anc, int32_t on_device) {
   if (!c || c->gen == 0) return ABC_E_INVAL;

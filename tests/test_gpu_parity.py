@@ -501,6 +501,35 @@ def test_checkpoint_resume_is_bit_identical():
         G.abc_free(b)
 
 
+@pytest.mark.parametrize("prec", [G.ABC_P_FP32, G.ABC_P_BF16_TC])
+def test_reset_starts_a_new_run_equal_to_a_fresh_context(prec):
+    """abc_reset(ctx, r) after a run: the next generations equal those of a
+    fresh context whose config carries run_id r, bit for bit, statistics
+    included."""
+    cfg = saird_config(2048, 40, 100_000, seed=6, weight_mode=G.ABC_W_IMPORTANCE,
+                       weight_prec=prec)
+    obs, _, _ = oracle_obs(cfg)
+    fresh_cfg = saird_config(2048, 40, 100_000, seed=6, weight_mode=G.ABC_W_IMPORTANCE,
+                             weight_prec=prec, run_id=7)
+    a = G.abc_init(cfg, obs)
+    b = G.abc_init(fresh_cfg, obs)
+    try:
+        G.abc_run(a, 4)
+        G.abc_reset(a, 7)
+        assert G.abc_generations(a) == 0
+        G.abc_run(a, 4)
+        G.abc_run(b, 4)
+        pa, pb = get_population(a, 2048), get_population(b, 2048)
+        for k in pa:
+            assert np.array_equal(pa[k].view(np.uint8), pb[k].view(np.uint8)), k
+        for t in range(4):
+            sa, sb = G.abc_get_stats(a, t), G.abc_get_stats(b, t)
+            assert (sa.eps, sa.batches, sa.sims, sa.ess) == (sb.eps, sb.batches, sb.sims, sb.ess)
+    finally:
+        G.abc_free(a)
+        G.abc_free(b)
+
+
 def test_batch_budget_stop_keeps_population():
     """M < N with a budget of one batch cannot fill the population: the
     generation reports ABC_STOP_BUDGET and leaves the population unchanged."""
