@@ -134,10 +134,15 @@ def _state_errors(name, lw, olw, s, up, u, q):
     W /= W.sum()
     Wg = np.exp(lw - lw.max())
     Wg /= Wg.sum()
+    relW = np.abs(Wg - W) / np.maximum(W, 1e-300)
+    big = W >= 1e-6 * W.max()  # weights that carry mass
+    ess, essg = 1.0 / np.sum(W**2), 1.0 / np.sum(Wg**2)
     REPORT[name] = dict(max_abs=float(err.max()), median_abs=float(np.median(err)),
                         p99_abs=float(np.quantile(err, 0.99)),
                         max_err_over_bound=float((err / bound).max()),
                         tv_normalised_W=float(0.5 * np.abs(W - Wg).sum()),
+                        max_rel_W=float(relW[big].max()), median_rel_W=float(np.median(relW[big])),
+                        ess_rel_err=float(abs(essg - ess) / ess),
                         rows=int(len(err)),
                         fraction_exact=float(np.mean(tc_row_bound(up, s, u, q) > TC_BOUND_MAX)))
     print(name, REPORT[name])
@@ -263,3 +268,50 @@ def test_late_generation_weights_with_paper_schedule(prec):
         assert abs(ess[0] - ess[1]) <= 1e-3 * ess[1]
     finally:
         G.abc_free(ctx)
+
+
+@pytest.mark.parametrize("t", [1, 2, 4])
+def test_generation_weight_errors_stated(t):
+    """Error of the tensor-core precision against the fp64 oracle on the
+    weights of real generations (the oracle's population after generation
+    t - 1 loaded into a context; 16384 particles, 60 days, P = 1e6, paper
+    schedule): generation 1 has every row on the tensor cores (large steps),
+    later ones a growing share recomputed exactly.  Stated in the report:
+    max / median / p99 of |d log W| and of the relative error of the
+    normalised weights carrying mass, the total variation and the ESS error."""
+    cfg = saird_config(16384, 60, 1_000_000, seed=11, weight_mode=G.ABC_W_IMPORTANCE,
+                       beta_mode=G.ABC_BETA_PAPER, weight_prec=G.ABC_P_BF16_TC)
+    obs, _, _ = oracle_obs(cfg)
+    m, c = oracle_model(cfg, obs), oracle_smc(cfg, nthreads=16)
+    pop = O.generation0(m, c)
+    eps1 = 0.0
+    for k in range(1, t):
+        pop, st = O.generation(m, c, k, eps1, pop)
+        assert st.status == 0
+        eps1 = st.eps1
+    new, st = O.generation(m, c, t, eps1, pop)
+    assert st.status == 0
+    ctx = G.abc_init(cfg, obs)
+    try:
+        G.abc_set_state(ctx, state_blob(cfg, t, eps1, pop))
+        assert G.abc_generation(ctx) == 0
+        gp = get_population(ctx, cfg.n_particles)
+        g = G.abc_get_stats(ctx, t)
+    finally:
+        G.abc_free(ctx)
+    assert np.array_equal(gp["anc"], new.anc) and np.array_equal(gp["d"], new.d)
+    W, Wg = new.W, gp["W"]
+    lw_rel = np.log(np.maximum(Wg, 1e-300)) - np.log(np.maximum(W, 1e-300))
+    big = W >= 1e-6 * W.max()
+    relW = np.abs(Wg - W)[big] / W[big]
+    dlog = np.abs(lw_rel[big] - np.median(lw_rel[big]))
+    REPORT["generation_%d_tc" % t] = dict(
+        rows_tc=int(g.rows_tc), rows_kept=int(g.rows_exp), rows_with_mass=int(big.sum()),
+        max_rel_W=float(relW.max()), median_rel_W=float(np.median(relW)),
+        p99_rel_W=float(np.quantile(relW, 0.99)), max_dlogW=float(dlog.max()),
+        median_dlogW=float(np.median(dlog)), p99_dlogW=float(np.quantile(dlog, 0.99)),
+        tv_normalised_W=float(0.5 * np.abs(Wg - W).sum()),
+        ess_gpu=float(g.ess), ess_oracle=float(st.ess),
+        ess_rel_err=float(abs(g.ess - st.ess) / st.ess))
+    print(REPORT["generation_%d_tc" % t])
+    assert REPORT["generation_%d_tc" % t]["tv_normalised_W"] < 1e-3
