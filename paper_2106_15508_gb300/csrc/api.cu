@@ -504,7 +504,10 @@ struct abc_ctx {
   unsigned long long* audit = nullptr;  // audited, audited with d <= eps
   void* sscratch = nullptr;       // surrogate scratch (training / inference / screening)
   size_t sscratch_bytes = 0;
-  uint32_t train_step = 0;
+  uint32_t* train_step = nullptr; // Adam steps so far (device)
+  int* screen_on = nullptr;       // this generation screens (device)
+  long long* simulated = nullptr; // slots simulated in this generation (device)
+  unsigned* inf_err = nullptr;    // error word of the tensor-core inference (device)
   cudaEvent_t eq0 = nullptr, eq1 = nullptr, et0 = nullptr, et1 = nullptr;
 
   template <typename T>
@@ -596,6 +599,10 @@ int ctx_alloc(abc_ctx* c) {
     ABC_ALLOC(c->trT, 4 * static_cast<size_t>(B));
     ABC_ALLOC(c->loss, 1);
     ABC_ALLOC(c->audit, 2);
+    ABC_ALLOC(c->train_step, 1);
+    ABC_ALLOC(c->screen_on, 1);
+    ABC_ALLOC(c->simulated, 1);
+    ABC_ALLOC(c->inf_err, 1);
     c->sscratch_bytes = std::max({mlp_train_scratch_bytes(B), mlp_infer_scratch_bytes(c->M),
                                   screen_scratch_bytes(c->M),
                                   ring_scratch_bytes(std::max(c->M, c->N))});
@@ -617,6 +624,51 @@ int ctx_alloc(abc_ctx* c) {
   if ((rc = c->alloc(&sc, sb)) != ABC_OK) return rc;
   c->scratch = sc;
   return ABC_OK;
+}
+
+// the surrogate buffers of a context; rho_pop of population buffer `nxt`
+SurView sur_view(abc_ctx* c, int nxt) {
+  SurView v;
+  if (!c->cfg.surrogate) return v;
+  v.on = true;
+  v.mlp = c->mlp;
+  v.ystat = c->ystat;
+  v.Yp = c->Yp;
+  v.rho = c->rho;
+  v.sflag = c->sflag;
+  v.cmp_u = c->cmp_u;
+  v.cmp_s = c->cmp_s;
+  v.cmp_rho = c->cmp_rho;
+  v.cmp_a = c->cmp_a;
+  v.cmp_flag = c->cmp_flag;
+  v.cmp_slot = c->cmp_slot;
+  v.cmp_d = c->cmp_d;
+  v.ard = c->ard;
+  v.Mc = c->Mc;
+  v.rho_pop = c->rho_pop[nxt];
+  v.RX = c->RX;
+  v.RY = c->RY;
+  v.ring_head = c->ring_head;
+  v.ring_cap = c->ring_cap;
+  v.grad = c->grad;
+  v.trX = c->trX;
+  v.trT = c->trT;
+  v.loss = c->loss;
+  v.audit = c->audit;
+  v.inf_err = c->inf_err;
+  v.simulated = c->simulated;
+  v.train_step = c->train_step;
+  v.screen_on = c->screen_on;
+  v.sscratch = c->sscratch;
+  v.sscratch_bytes = c->sscratch_bytes;
+  v.start = c->cfg.surrogate_start;
+  v.steps = c->cfg.surrogate_steps;
+  v.batch = c->cfg.surrogate_batch;
+  v.lr = c->cfg.surrogate_lr;
+  v.tau = c->cfg.surrogate_tau;
+  v.rho_min = c->cfg.surrogate_rho_min;
+  v.audit_frac = c->cfg.audit_frac;
+  return v;
 }
 
 int generation0(abc_ctx* c) {
@@ -678,14 +730,23 @@ int generation_t(abc_ctx* c) {
   if (rc) return rc;
   ABC_CUDA_TRY(cudaMemsetAsync(c->cnt, 0, 4 * sizeof(int64_t), st));
   const bool sur = c->cfg.surrogate != 0;
-  // screen once the surrogate has been trained (from generation surrogate_start)
-  const bool screen = sur && t >= c->cfg.surrogate_start && c->train_step > 0;
-  if (sur) ABC_CUDA_TRY(cudaMemsetAsync(c->audit, 0, 2 * sizeof(unsigned long long), st));
-  int64_t filled = 0, simulated = 0;
-  double ms_sim = 0.0, ms_screen = 0.0;
-  int32_t b = 0;
+  const SurView sv = sur_view(c, nxt);
   unsigned* inf_err = nullptr;
   unsigned h_inf_err = 0;
+  if (sur) {
+    // screening from generation surrogate_start once the surrogate has been
+    // trained (decided on the device); this generation's counters
+    if ((rc = sur_gate(nullptr, static_cast<uint32_t>(t), sv.start, sv.train_step, sv.screen_on,
+                       st)))
+      return rc;
+    ABC_CUDA_TRY(cudaMemsetAsync(c->audit, 0, 2 * sizeof(unsigned long long), st));
+    ABC_CUDA_TRY(cudaMemsetAsync(c->simulated, 0, sizeof(long long), st));
+    inf_err = c->inf_err;
+    ABC_CUDA_TRY(cudaMemsetAsync(inf_err, 0, sizeof(unsigned), st));
+  }
+  int64_t filled = 0;
+  double ms_sim = 0.0, ms_screen = 0.0;
+  int32_t b = 0;
   // several batches per round (spec_batches, without the surrogate): K M
   // slots proposed and simulated together, accepted in (batch, slot) order
   const int K = sur ? 1 : spec_k(c->cfg);
@@ -721,72 +782,55 @@ int generation_t(abc_ctx* c) {
     rc = launch_propose(c->p, c->u[cur], c->N, c->prefix, rule, eps, eps1, c->M, nullptr, c1,
                         c->cfg.max_redraw, c->up, c->sp, c->ap, c->att, c->flag, st);
     if (rc) return rc;
-    int h_mc = 0;
-    if (screen) {
-      // delayed acceptance: predict, screen, simulate only the compacted slots
-      ABC_CUDA_TRY(cudaEventRecord(c->eq0, st));
-      if ((rc = mlp_infer(c->mlp, c->up, c->M, c->Yp, c->sscratch, c->sscratch_bytes, &inf_err, st)))
-        return rc;
-      if ((rc = screen_and_compact(c->Yp, c->ystat, c->flag, c->M, eps, c->p.k0, c->p.k1, c1,
-                                   c->cfg.surrogate_tau, c->cfg.surrogate_rho_min,
-                                   c->cfg.audit_frac, c->rho, c->sflag, c->up, c->sp, c->ap,
-                                   c->cmp_u, c->cmp_s, c->cmp_a, c->cmp_rho, c->cmp_flag,
-                                   c->cmp_slot, c->Mc, c->sscratch, st,
-                                   reinterpret_cast<unsigned long long*>(c->cnt + 2))))
-        return rc;
-      ABC_CUDA_TRY(cudaEventRecord(c->eq1, st));
-      ABC_CUDA_TRY(cudaMemcpyAsync(&h_mc, c->Mc, sizeof(int), cudaMemcpyDeviceToHost, st));
-      ABC_CUDA_TRY(cudaMemcpyAsync(&h_inf_err, inf_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-      ABC_CUDA_TRY(cudaStreamSynchronize(st));
-      if (h_inf_err) return ABC_E_DEVICE;
-      float mq = 0.f;
-      ABC_CUDA_TRY(cudaEventElapsedTime(&mq, c->eq0, c->eq1));
-      ms_screen += mq;
-      ABC_CUDA_TRY(cudaEventRecord(c->es0, st));
-      rc = launch_simulate(c->p, c->obs, c->cmp_u, h_mc, c->cmp_slot, c1, ABC_TAG_SIM, nullptr,
-                           c->cmp_d, nullptr, st, nullptr, nullptr, 128, c->ard);
+    if (sur) {
+      // delayed acceptance (a pass-all until the surrogate is trained):
+      // predict, screen, simulate only the compacted slots
+      const cudaEvent_t ev[3] = {c->eq0, c->es0, c->es1};
+      rc = screened_batch(sv, c->p, c->obs, c->up, c->sp, c->ap, c->flag, c->M, eps, c1, nullptr,
+                          c->N, c->u[nxt], c->d[nxt], c->s[nxt], c->anc[nxt], c->cnt, c->cnt + 1,
+                          reinterpret_cast<unsigned long long*>(c->cnt + 2), c->scratch,
+                          c->scratch_bytes, 128, nullptr, st, ev);
       if (rc) return rc;
-      ABC_CUDA_TRY(cudaEventRecord(c->es1, st));
-      rc = launch_accept(c->cmp_u, c->cmp_d, c->cmp_s, c->cmp_a, c->cmp_flag, h_mc, eps, c->N,
-                         c->u[nxt], c->d[nxt], c->s[nxt], c->anc[nxt], c->cnt, c->cnt + 1,
-                         c->scratch, c->scratch_bytes, st, c->cmp_rho, c->rho_pop[nxt]);
-      if (rc) return rc;
-      if ((rc = audit_count(c->cmp_flag, c->cmp_d, c->Mc, eps, c->audit, st))) return rc;
-      if ((rc = ring_append(nullptr, h_mc, c->cmp_u, c->cmp_d, c->ard, c->ring_head, c->ring_cap,
-                            c->RX, c->RY, c->sscratch, st)))
-        return rc;
     } else {
       ABC_CUDA_TRY(cudaEventRecord(c->es0, st));
       rc = launch_simulate(c->p, c->obs, c->up, c->M, nullptr, c1, ABC_TAG_SIM, c->flag, c->dp,
-                           nullptr, st, nullptr, nullptr, 128, sur ? c->ard : nullptr);
+                           nullptr, st, nullptr, nullptr, 128, nullptr);
       if (rc) return rc;
       ABC_CUDA_TRY(cudaEventRecord(c->es1, st));
       rc = launch_accept(c->up, c->dp, c->sp, c->ap, c->flag, c->M, eps, c->N, c->u[nxt], c->d[nxt],
                          c->s[nxt], c->anc[nxt], c->cnt, c->cnt + 1, c->scratch, c->scratch_bytes,
-                         st, nullptr, sur ? c->rho_pop[nxt] : nullptr);
+                         st);
       if (rc) return rc;
-      if (sur && (rc = ring_append(c->flag, c->M, c->up, c->dp, c->ard, c->ring_head, c->ring_cap,
-                                   c->RX, c->RY, c->sscratch, st)))
-        return rc;
     }
     ABC_CUDA_TRY(cudaMemcpyAsync(&filled, c->cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     ABC_CUDA_TRY(cudaStreamSynchronize(st));
     float ms = 0.f;
     ABC_CUDA_TRY(cudaEventElapsedTime(&ms, c->es0, c->es1));
     ms_sim += ms;
-    if (screen) simulated += h_mc;
+    if (sur) {
+      ABC_CUDA_TRY(cudaEventElapsedTime(&ms, c->eq0, c->es0));
+      ms_screen += ms;
+    }
   }
   int64_t h_cnt[3];
   ABC_CUDA_TRY(cudaMemcpyAsync(h_cnt, c->cnt, sizeof h_cnt, cudaMemcpyDeviceToHost, st));
   unsigned long long h_audit[2] = {0, 0};
-  if (sur) ABC_CUDA_TRY(cudaMemcpyAsync(h_audit, c->audit, sizeof h_audit, cudaMemcpyDeviceToHost, st));
+  long long simulated = 0;
+  if (sur) {
+    ABC_CUDA_TRY(cudaMemcpyAsync(h_audit, c->audit, sizeof h_audit, cudaMemcpyDeviceToHost, st));
+    ABC_CUDA_TRY(cudaMemcpyAsync(&simulated, c->simulated, sizeof simulated,
+                                 cudaMemcpyDeviceToHost, st));
+    ABC_CUDA_TRY(cudaMemcpyAsync(&h_inf_err, inf_err, sizeof h_inf_err, cudaMemcpyDeviceToHost,
+                                 st));
+  }
   ABC_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h_inf_err) return ABC_E_DEVICE;
   abc_gen_stats g{};
   g.generation = t;
   g.batches = b;
   g.accepted = h_cnt[1];
   g.ms_screen = ms_screen;
-  if (screen) {
+  if (sur) {
     // every slot is exhausted (never simulated), passed, or screened out;
     // audited slots were screened out and simulated anyway
     g.exhausted = h_cnt[2];
@@ -838,7 +882,7 @@ int generation_t(abc_ctx* c) {
         ABC_CUDA_TRY(cudaMemcpyAsync(&h_tiles, wt.tiles, sizeof h_tiles, cudaMemcpyDeviceToHost, st));
       weighted = true;
       // delayed acceptance: a proposal simulated with probability rho carries 1/rho
-      if (screen && (rc = rho_correct(c->logW, c->rho_pop[nxt], c->N, st))) return rc;
+      if (sur && (rc = rho_correct(c->logW, sv.rho_pop, c->N, st))) return rc;
       rc = launch_normalize(c->logW, c->N, c->W[nxt], ess, c->scratch, c->scratch_bytes, st);
       if (rc) return rc;
     } else {
@@ -877,14 +921,8 @@ int generation_t(abc_ctx* c) {
   if (sur && g.status == ABC_OK && c->cfg.surrogate_steps > 0) {
     // train on everything simulated so far (the ring keeps the latest pairs)
     ABC_CUDA_TRY(cudaEventRecord(c->et0, st));
-    if ((rc = ring_stats(c->RY, c->ring_head, c->ring_cap, c->ystat, st))) return rc;
-    if ((rc = mlp_train(c->mlp, c->RX, c->RY, c->ring_head, c->ring_cap, c->ystat,
-                        c->cfg.surrogate_batch, c->cfg.surrogate_steps, c->train_step,
-                        c->cfg.surrogate_lr, c->p.k0, c->p.k1, c->grad, c->trX, c->trT, c->loss,
-                        c->sscratch, c->sscratch_bytes, st)))
-      return rc;
+    if ((rc = sur_train(sv, c->p, nullptr, st))) return rc;
     ABC_CUDA_TRY(cudaEventRecord(c->et1, st));
-    c->train_step += static_cast<uint32_t>(c->cfg.surrogate_steps);
     float lh = 0.f, mt = 0.f;
     ABC_CUDA_TRY(cudaMemcpyAsync(&lh, c->loss, sizeof lh, cudaMemcpyDeviceToHost, st));
     ABC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -932,7 +970,10 @@ ABC_API int abc_init(const abc_config* cfg, const int32_t* obs, void* stream, ab
   if (cfg->surrogate) {
     if (cudaEventCreate(&c->eq0) != cudaSuccess || cudaEventCreate(&c->eq1) != cudaSuccess ||
         cudaEventCreate(&c->et0) != cudaSuccess || cudaEventCreate(&c->et1) != cudaSuccess ||
-        cudaMemsetAsync(c->ring_head, 0, sizeof(long long), c->st) != cudaSuccess) {
+        cudaMemsetAsync(c->ring_head, 0, sizeof(long long), c->st) != cudaSuccess ||
+        cudaMemsetAsync(c->train_step, 0, sizeof(uint32_t), c->st) != cudaSuccess ||
+        // compacted slots past a batch's count are read as flags: never 1
+        cudaMemsetAsync(c->cmp_flag, 0, static_cast<size_t>(c->M), c->st) != cudaSuccess) {
       delete c;
       return ABC_E_CUDA;
     }
@@ -1009,7 +1050,7 @@ ABC_API int abc_reset(abc_ctx* c, uint32_t run_id) {
   c->stats.clear();
   ABC_CUDA_TRY(cudaMemsetAsync(c->scal, 0, 4 * sizeof(double), c->st));
   if (c->cfg.surrogate) {
-    c->train_step = 0;
+    ABC_CUDA_TRY(cudaMemsetAsync(c->train_step, 0, sizeof(uint32_t), c->st));
     ABC_CUDA_TRY(cudaMemsetAsync(c->ring_head, 0, sizeof(long long), c->st));
     const int rc = mlp_init(c->mlp, c->p.k0, c->p.k1, c->st);
     if (rc) return rc;
@@ -1191,6 +1232,9 @@ RunCtxView ctx_view(abc_ctx* c) {
   v.nc = c->nc;
   v.scratch = c->scratch;
   v.scratch_bytes = c->scratch_bytes;
+  // the graph writes the new population to buffer 1 and commits it to 0
+  v.sur = sur_view(c, 1);
+  if (v.sur.on) v.K = 1;  // screened generations run one batch per round
   return v;
 }
 
@@ -1309,10 +1353,6 @@ ABC_API int abc_batch_init(const abc_config* cfgs, int32_t n_runs, const int32_t
                            void* stream, abc_batch** out) {
   if (!out || !cfgs || n_runs < 1 || n_runs > 4096) return ABC_E_INVAL;
   *out = nullptr;
-  // the graph branches have no screening step: a run that asks for the
-  // surrogate is refused instead of being run unscreened
-  for (int32_t r = 0; r < n_runs; ++r)
-    if (cfgs[r].surrogate) return ABC_E_INVAL;
   abc_batch* b = new (std::nothrow) abc_batch();
   if (!b) return ABC_E_NOMEM;
   b->st = as_stream(stream);
@@ -1399,9 +1439,10 @@ ABC_API int abc_batch_generation(abc_batch* b) {
   ABC_CUDA_TRY(cudaMemcpy(b->host.data(), b->dev, sizeof(RunDev) * R, cudaMemcpyDeviceToHost));
   int any_err = 0;
   for (size_t r = 0; r < R; ++r) {
-    if (b->br[r].tc_err) {
+    for (unsigned* e : {b->br[r].tc_err, b->br[r].inf_err}) {
+      if (!e) continue;
       unsigned h = 0;
-      ABC_CUDA_TRY(cudaMemcpy(&h, b->br[r].tc_err, sizeof h, cudaMemcpyDeviceToHost));
+      ABC_CUDA_TRY(cudaMemcpy(&h, e, sizeof h, cudaMemcpyDeviceToHost));
       any_err |= h != 0;
     }
     const RunDev& d = b->host[r];
@@ -1418,6 +1459,17 @@ ABC_API int abc_batch_generation(abc_batch* b) {
     g.accepted = d.accepted;
     g.exhausted = d.exhausted;
     g.sims = d.batches * c->M - d.exhausted;
+    if (c->cfg.surrogate) {
+      // screened: the simulated slots and the audit counts of the generation
+      long long sim = 0;
+      unsigned long long aud[2] = {0, 0};
+      ABC_CUDA_TRY(cudaMemcpy(&sim, c->simulated, sizeof sim, cudaMemcpyDeviceToHost));
+      ABC_CUDA_TRY(cudaMemcpy(aud, c->audit, sizeof aud, cudaMemcpyDeviceToHost));
+      g.sims = sim;
+      g.audited = static_cast<int64_t>(aud[0]);
+      g.audit_accepted = static_cast<int64_t>(aud[1]);
+      g.screened = d.batches * c->M - d.exhausted - (sim - g.audited);
+    }
     g.sim_days = g.sims * static_cast<int64_t>(c->cfg.model == ABC_MODEL_SAIRD ? c->T : 1);
     g.launches = b->br[r].fixed_launches + d.rounds * b->br[r].body_launches;
     g.ms = ms;  // the whole graph (all runs)

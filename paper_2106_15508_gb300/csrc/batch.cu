@@ -111,6 +111,51 @@ __global__ void k_run_fill_paper(RunDev* r, double* __restrict__ W, int64_t N) {
   if (i == 0) r->ess = static_cast<double>(N);
 }
 
+int screened_batch(const SurView& s, const SimParams& p, const int32_t* obs, const float* up,
+                   const float* sp, const int32_t* ap, const uint8_t* flag, int64_t M,
+                   const double* eps, uint32_t c1, const uint32_t* c1_dev, int64_t N,
+                   float* u_pop, double* d_pop, float* s_pop, int32_t* a_pop, int64_t* filled,
+                   int64_t* counters, unsigned long long* exhausted, void* scratch,
+                   size_t scratch_bytes, int sim_threads, unsigned** inf_err, cudaStream_t st,
+                   const cudaEvent_t* ev) {
+  int rc;
+  if (ev) ABC_CUDA_TRY(cudaEventRecord(ev[0], st));
+  // predictions of the proposals (the error word is reset once per generation)
+  if ((rc = mlp_infer(s.mlp, up, M, s.Yp, s.sscratch, s.sscratch_bytes, inf_err, st, false,
+                      s.inf_err)))
+    return rc;
+  // delayed acceptance: rho and the pass / audit decision, then the slots to
+  // simulate in slot order (stride M, count *Mc on the device)
+  if ((rc = screen_and_compact(s.Yp, s.ystat, flag, M, eps, p.k0, p.k1, c1, s.tau, s.rho_min,
+                               s.audit_frac, s.rho, s.sflag, up, sp, ap, s.cmp_u, s.cmp_s, s.cmp_a,
+                               s.cmp_rho, s.cmp_flag, s.cmp_slot, s.Mc, s.sscratch, st, exhausted,
+                               c1_dev, s.screen_on, s.simulated)))
+    return rc;
+  // each simulated slot with its own Philox counters; the rest get +inf
+  if (ev) ABC_CUDA_TRY(cudaEventRecord(ev[1], st));
+  if ((rc = launch_simulate(p, obs, s.cmp_u, M, s.cmp_slot, c1, ABC_TAG_SIM, nullptr, s.cmp_d,
+                            nullptr, st, c1_dev, nullptr, sim_threads, s.ard, 0, s.Mc)))
+    return rc;
+  if (ev) ABC_CUDA_TRY(cudaEventRecord(ev[2], st));
+  // audited slots (flag 2) are never accepted; each accepted particle keeps its rho
+  if ((rc = launch_accept(s.cmp_u, s.cmp_d, s.cmp_s, s.cmp_a, s.cmp_flag, M, eps, N, u_pop, d_pop,
+                          s_pop, a_pop, filled, counters, scratch, scratch_bytes, st, s.cmp_rho,
+                          s.rho_pop)))
+    return rc;
+  if ((rc = audit_count(s.cmp_flag, s.cmp_d, s.Mc, eps, s.audit, st))) return rc;
+  return ring_append(nullptr, M, s.cmp_u, s.cmp_d, s.ard, s.ring_head, s.ring_cap, s.RX, s.RY,
+                     s.sscratch, st, s.Mc);
+}
+
+int sur_train(const SurView& s, const SimParams& p, const int* off_dev, cudaStream_t st) {
+  if (s.steps <= 0) return ABC_OK;
+  int rc = ring_stats(s.RY, s.ring_head, s.ring_cap, s.ystat, st);
+  if (rc) return rc;
+  return mlp_train(s.mlp, s.RX, s.RY, s.ring_head, s.ring_cap, s.ystat, s.batch, s.steps,
+                   s.train_step, s.lr, p.k0, p.k1, s.grad, s.trX, s.trT, s.loss, s.sscratch,
+                   s.sscratch_bytes, st, off_dev);
+}
+
 int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
   const int64_t l0 = launch_count();
   int64_t l_body0 = 0, l_body1 = 0;
@@ -136,6 +181,15 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
   const int fixed_b = v.beta.mode == ABC_BETA_FIXED ? v.beta.b : 0;
   k_run_start<<<1, 32, 0, st>>>(r, v.beta.mode == ABC_BETA_PAPER, fixed_b, v.K, h);
   ABC_LAUNCH_CHECK();
+  const SurView& sv = v.sur;
+  if (sv.on) {
+    // screening from generation `start` once trained; this generation's counters
+    if ((rc = sur_gate(&r->t, 0u, sv.start, sv.train_step, sv.screen_on, st))) return rc;
+    ABC_CUDA_TRY(cudaMemsetAsync(sv.audit, 0, 2 * sizeof(unsigned long long), st));
+    ABC_CUDA_TRY(cudaMemsetAsync(sv.simulated, 0, sizeof(long long), st));
+    br.inf_err = sv.inf_err;
+    ABC_CUDA_TRY(cudaMemsetAsync(sv.inf_err, 0, sizeof(unsigned), st));
+  }
   {
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
@@ -163,20 +217,28 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
   rc = launch_propose(v.p, v.u_cur, v.N, v.prefix, v.beta, &r->eps, &r->eps1, slots, nullptr, 0u,
                       v.max_redraw, v.up, v.sp, v.ap, v.att, v.flag, body_st, &r->c1, &r->beta_b,
                       &r->off, spec ? v.M : 0, spec ? &r->k_lim : nullptr);
-  if (!rc)
+  if (!rc && sv.on) {
+    // the surrogate screens the batch (a pass-all until it is trained)
+    rc = screened_batch(sv, v.p, v.obs, v.up, v.sp, v.ap, v.flag, v.M, &r->eps, 0u, &r->c1, v.N,
+                        v.u_nxt, v.d_nxt, v.s_nxt, v.a_nxt, reinterpret_cast<int64_t*>(&r->filled),
+                        reinterpret_cast<int64_t*>(&r->accepted),
+                        reinterpret_cast<unsigned long long*>(&r->exhausted), v.scratch,
+                        v.scratch_bytes, br.sim_threads, nullptr, body_st);
+  } else if (!rc) {
     rc = launch_simulate(v.p, v.obs, v.up, slots, nullptr, 0u, ABC_TAG_SIM, v.flag, v.dp, nullptr,
                          body_st, &r->c1, &r->off, br.sim_threads, nullptr, spec ? v.M : 0);
-  if (!rc && spec)
-    rc = launch_accept_spec(v.up, v.dp, v.sp, v.ap, v.flag, v.M, v.K, &r->k_lim, &r->eps, v.N,
-                            v.u_nxt, v.d_nxt, v.s_nxt, v.a_nxt,
-                            reinterpret_cast<int64_t*>(&r->filled),
-                            reinterpret_cast<int64_t*>(&r->accepted), &r->used, v.scratch,
-                            v.scratch_bytes, body_st);
-  else if (!rc)
-    rc = launch_accept(v.up, v.dp, v.sp, v.ap, v.flag, v.M, &r->eps, v.N, v.u_nxt, v.d_nxt,
-                       v.s_nxt, v.a_nxt, reinterpret_cast<int64_t*>(&r->filled),
-                       reinterpret_cast<int64_t*>(&r->accepted), v.scratch, v.scratch_bytes,
-                       body_st);
+    if (!rc && spec)
+      rc = launch_accept_spec(v.up, v.dp, v.sp, v.ap, v.flag, v.M, v.K, &r->k_lim, &r->eps, v.N,
+                              v.u_nxt, v.d_nxt, v.s_nxt, v.a_nxt,
+                              reinterpret_cast<int64_t*>(&r->filled),
+                              reinterpret_cast<int64_t*>(&r->accepted), &r->used, v.scratch,
+                              v.scratch_bytes, body_st);
+    else if (!rc)
+      rc = launch_accept(v.up, v.dp, v.sp, v.ap, v.flag, v.M, &r->eps, v.N, v.u_nxt, v.d_nxt,
+                         v.s_nxt, v.a_nxt, reinterpret_cast<int64_t*>(&r->filled),
+                         reinterpret_cast<int64_t*>(&r->accepted), v.scratch, v.scratch_bytes,
+                         body_st);
+  }
   if (!rc) {
     k_run_cond<<<1, 32, 0, body_st>>>(r, v.N, v.K, h);
     count_launch();
@@ -200,12 +262,15 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
       rc = launch_weights_fp32(v.u_nxt, v.s_nxt, v.N, v.cu, v.cc, v.nc, v.N, v.prefix + (v.N - 1),
                                v.logW, v.scratch, v.scratch_bytes, st, &r->off, br.w_mult);
     if (rc) return rc;
+    // delayed acceptance: a particle simulated with probability rho carries 1 / rho
+    if (sv.on && (rc = rho_correct(v.logW, sv.rho_pop, v.N, st, &r->off))) return rc;
     if ((rc = launch_normalize(v.logW, v.N, v.W_nxt, &r->ess, v.scratch, v.scratch_bytes, st)))
       return rc;
   } else {
     k_run_fill_paper<<<static_cast<unsigned>(ceil_div(v.N, 256)), 256, 0, st>>>(r, v.W_nxt, v.N);
     ABC_LAUNCH_CHECK();
   }
+  if (sv.on && (rc = sur_train(sv, v.p, &r->off, st))) return rc;
   k_run_commit<<<static_cast<unsigned>(std::min<int64_t>(ceil_div(v.N, 256), 1024)), 256, 0, st>>>(
       r, v.N, v.u_cur, v.u_nxt, v.d_cur, v.d_nxt, v.W_cur, v.W_nxt, v.s_cur, v.s_nxt, v.a_cur,
       v.a_nxt);

@@ -1,6 +1,7 @@
 // batch.cuh -- internal types of the batched (many-run) graph path.
 #pragma once
 #include "common.cuh"
+#include "surrogate.cuh"
 
 namespace abc {
 
@@ -28,6 +29,38 @@ struct RunDev {
   double eps, eps1, ess;
 };
 
+// Buffers and settings of a run's surrogate pre-screen (borrowed from its
+// context); used by single-run contexts and graph branches alike.
+struct SurView {
+  bool on = false;                 // the run uses the surrogate
+  MlpState mlp{};
+  float* ystat = nullptr;          // output means [4], standard deviations [4]
+  float* Yp = nullptr;             // predictions [M][4]
+  float* rho = nullptr;            // pass probability per slot
+  uint8_t* sflag = nullptr;        // 0 acceptable, 1 exhausted, 2 audit only, 3 screened out
+  float *cmp_u = nullptr, *cmp_s = nullptr, *cmp_rho = nullptr;  // compacted slots, stride M
+  int32_t* cmp_a = nullptr;
+  uint8_t* cmp_flag = nullptr;
+  uint32_t* cmp_slot = nullptr;
+  double* cmp_d = nullptr;
+  int32_t* ard = nullptr;          // final A, R, D of each simulated slot [3][M]
+  int* Mc = nullptr;               // simulated slots of the batch
+  float* rho_pop = nullptr;        // rho of each accepted particle of the new population
+  float *RX = nullptr, *RY = nullptr;  // training ring [cap][8], [cap][4]
+  long long* ring_head = nullptr;
+  int64_t ring_cap = 0;
+  float *grad = nullptr, *trX = nullptr, *trT = nullptr, *loss = nullptr;
+  unsigned long long* audit = nullptr;  // audited, audited with d <= eps (this generation)
+  unsigned* inf_err = nullptr;     // error word of the tensor-core inference
+  long long* simulated = nullptr;  // simulated slots (this generation)
+  uint32_t* train_step = nullptr;  // Adam steps so far (device)
+  int* screen_on = nullptr;        // this generation screens
+  void* sscratch = nullptr;
+  size_t sscratch_bytes = 0;
+  int start = 1, steps = 0, batch = 0;
+  float lr = 0.f, tau = 1.f, rho_min = 1.f, audit_frac = 0.f;
+};
+
 // Device buffers and settings of one run (borrowed from its context).
 struct RunCtxView {
   SimParams p;
@@ -45,6 +78,7 @@ struct RunCtxView {
   int* nc;
   void* scratch;
   size_t scratch_bytes;
+  SurView sur;
 };
 
 struct BatchRun {
@@ -53,17 +87,40 @@ struct BatchRun {
   int sim_threads = 128;      // autotuned simulator block size
   int w_mult = 1;             // autotuned column-chunk multiplier of the weight pass
   unsigned* tc_err = nullptr; // error word of the tensor-core pass (when used)
+  unsigned* inf_err = nullptr; // error word of the surrogate's tensor-core inference
   int64_t fixed_launches = 0; // kernels per generation outside the batch loop
   int64_t body_launches = 0;  // kernels per batch
 };
 
 int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st);
 
+// One batch of M proposals (up, sp, ap, flag) screened by the surrogate:
+// inference, screen (a pass-all when *screen_on is 0), compaction of the
+// simulated slots, their simulation with their own counters, acceptance into
+// the new population in slot order, audit counts, training-ring append.
+// c1 / c1_dev: the batch's counter word (host value or device word);
+// filled, counters (accepted, exhausted adjacent) and exhausted: device
+// counters; the screen counts redraw-exhausted slots into *exhausted.  ev
+// (nullable): three events recorded before the inference, before and after
+// the simulation.  No host synchronisation.
+int screened_batch(const SurView& s, const SimParams& p, const int32_t* obs, const float* up,
+                   const float* sp, const int32_t* ap, const uint8_t* flag, int64_t M,
+                   const double* eps, uint32_t c1, const uint32_t* c1_dev, int64_t N,
+                   float* u_pop, double* d_pop, float* s_pop, int32_t* a_pop, int64_t* filled,
+                   int64_t* counters, unsigned long long* exhausted, void* scratch,
+                   size_t scratch_bytes, int sim_threads, unsigned** inf_err, cudaStream_t st,
+                   const cudaEvent_t* ev = nullptr);
+// After a generation: the surrogate's training (ring statistics, `steps`
+// Adam steps on ring minibatches); off_dev (graph branches): a run whose
+// generation stopped does not advance its step count.
+int sur_train(const SurView& s, const SimParams& p, const int* off_dev, cudaStream_t st);
+
 // launchers shared with the single-run context
 int launch_simulate(const SimParams&, const int32_t*, const float*, int64_t, const uint32_t*,
                     uint32_t, uint32_t, const uint8_t*, double*, int32_t*, cudaStream_t,
                     const uint32_t* c1_dev = nullptr, const int* off_dev = nullptr,
-                    int threads = 128, int32_t* ard_last = nullptr, int64_t m_sub = 0);
+                    int threads = 128, int32_t* ard_last = nullptr, int64_t m_sub = 0,
+                    const int* n_dev = nullptr);
 int launch_select(const double*, int64_t, int64_t, double*, void*, size_t, cudaStream_t);
 int launch_resample_prefix(const double*, const double*, int64_t, const double*, int, uint32_t*,
                            uint64_t*, void*, size_t, cudaStream_t);

@@ -188,7 +188,7 @@ k_simulate(SimParams p, const int32_t* __restrict__ obs,
                            const uint8_t* __restrict__ skip, double* __restrict__ dist,
                            int32_t* __restrict__ traj, const uint32_t* __restrict__ c1_dev,
                            const int* __restrict__ off_dev, int32_t* __restrict__ ard_last,
-                           int64_t m_sub) {
+                           int64_t m_sub, const int* __restrict__ n_dev) {
   extern __shared__ int32_t s_obs[];
   if (off_dev && *off_dev) return;  // run finished: nothing to simulate
   if (c1_dev) c1 = *c1_dev;         // counter word set on the device (graph launches)
@@ -199,7 +199,9 @@ k_simulate(SimParams p, const int32_t* __restrict__ obs,
                 (threadIdx.x >> 5) * kBinvQueue;
   __syncthreads();
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const bool live = i < n && !(skip && skip[i]);
+  // n_dev (nullable): the slots in use, counted on the device (a compacted
+  // list of capacity n); the others get distance +inf
+  const bool live = i < n && !(n_dev && i >= *n_dev) && !(skip && skip[i]);
   // lanes that simulate (the block size is a multiple of 32)
   const unsigned mask = __ballot_sync(0xffffffffu, live);
   if (i >= n) return;
@@ -291,7 +293,8 @@ __global__ void k_philox(const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t
 int launch_simulate(const SimParams& p, const int32_t* obs, const float* u, int64_t n,
                     const uint32_t* c0_idx, uint32_t c1, uint32_t tag, const uint8_t* skip,
                     double* dist, int32_t* traj, cudaStream_t st, const uint32_t* c1_dev,
-                    const int* off_dev, int threads, int32_t* ard_last, int64_t m_sub) {
+                    const int* off_dev, int threads, int32_t* ard_last, int64_t m_sub,
+                    const int* n_dev) {
   if (n <= 0) return ABC_OK;
   if (m_sub < 0) return ABC_E_INVAL;
   // 64 registers per thread (__launch_bounds__(256, 4)): up to 8 CTAs of
@@ -301,7 +304,7 @@ int launch_simulate(const SimParams& p, const int32_t* obs, const float* u, int6
   const size_t smem = sizeof(int32_t) * ((nobs + 3) & ~static_cast<size_t>(3)) +
                       sizeof(BinvJob) * kBinvQueue * static_cast<size_t>(threads / 32);
   k_simulate<<<static_cast<unsigned>(ceil_div(n, threads)), threads, smem, st>>>(
-      p, obs, u, n, c0_idx, c1, tag, skip, dist, traj, c1_dev, off_dev, ard_last, m_sub);
+      p, obs, u, n, c0_idx, c1, tag, skip, dist, traj, c1_dev, off_dev, ard_last, m_sub, n_dev);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

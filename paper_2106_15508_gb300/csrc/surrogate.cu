@@ -253,11 +253,18 @@ __global__ void k_sum(const float* __restrict__ x, int n, float* __restrict__ ou
   if (threadIdx.x == 0) *out = s;
 }
 
+// step_dev (nullable): the bias corrections use the step *step_dev + koff + 1
+// counted on the device (graph launches), computed in fp64 and rounded
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, float lr, float b1, float b2, float eps, float c1,
-                       float c2) {
+                       float c2, const uint32_t* __restrict__ step_dev, uint32_t koff) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kMlpParams) return;
+  if (step_dev) {
+    const double t = static_cast<double>(*step_dev) + static_cast<double>(koff) + 1.0;
+    c1 = static_cast<float>(1.0 - pow(0.9, t));
+    c2 = static_cast<float>(1.0 - pow(0.999, t));
+  }
   const float gi = g[i];
   const float mi = b1 * m[i] + (1.0f - b1) * gi;
   const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
@@ -329,7 +336,7 @@ int mlp_adam(const MlpState& s, const float* grad, int64_t step, float lr, cudaS
   const float c1 = 1.0f - std::pow(b1, static_cast<float>(step));
   const float c2 = 1.0f - std::pow(b2, static_cast<float>(step));
   const unsigned g = (kMlpParams + 255) / 256;
-  k_adam<<<g, 256, 0, st>>>(s.w, grad, s.m, s.v, lr, b1, b2, eps, c1, c2);
+  k_adam<<<g, 256, 0, st>>>(s.w, grad, s.m, s.v, lr, b1, b2, eps, c1, c2, nullptr, 0u);
   ABC_LAUNCH_CHECK();
   k_mlp_to_bf16<<<g, 256, 0, st>>>(s.w, s.wb);
   ABC_LAUNCH_CHECK();
@@ -499,19 +506,26 @@ int mlp_infer_prepare() {
   return ABC_OK;
 }
 
+// the error word of mlp_infer(n) inside its scratch
+unsigned* mlp_infer_err(void* scratch, int64_t n) {
+  const int64_t npad = ceil_div(std::max<int64_t>(n, 1), kMlpM) * kMlpM;
+  return reinterpret_cast<unsigned*>(static_cast<char*>(scratch) +
+                                     align256(static_cast<size_t>(npad) * kMlpH * 2) +
+                                     align256(kMlpBBytes));
+}
+
 // Y [n][4] (standardised outputs) for u [8][n]; the error word lives in scratch
 int mlp_infer(const MlpState& s, const float* u, int64_t n, float* Y, void* scratch, size_t bytes,
-              unsigned** err_out, cudaStream_t st) {
+              unsigned** err_out, cudaStream_t st, bool reset_err, unsigned* err_word) {
   if (n <= 0) return ABC_OK;
   if (bytes < mlp_infer_scratch_bytes(n)) return ABC_E_SCRATCH;
   const int64_t npad = ceil_div(n, kMlpM) * kMlpM;
   char* b = static_cast<char*>(scratch);
   auto* Hpk = reinterpret_cast<__nv_bfloat16*>(b);
   auto* W2pk = reinterpret_cast<__nv_bfloat16*>(b + align256(static_cast<size_t>(npad) * kMlpH * 2));
-  auto* err = reinterpret_cast<unsigned*>(b + align256(static_cast<size_t>(npad) * kMlpH * 2) +
-                                          align256(kMlpBBytes));
+  unsigned* err = err_word ? err_word : mlp_infer_err(scratch, n);
   if (err_out) *err_out = err;
-  ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
+  if (reset_err) ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
   k_mlp_pack_w2<<<(kMlpH * kMlpH + 255) / 256, 256, 0, st>>>(s.wb, W2pk);
   ABC_LAUNCH_CHECK();
   k_mlp_l1_pack<<<static_cast<unsigned>(ceil_div(npad, 128)), 128, 0, st>>>(u, n, npad, s.wb, s.w,
@@ -540,11 +554,15 @@ __device__ __forceinline__ float screen_rho(float y, const float* ystat, float l
   return fminf(fmaxf(r, rho_min), 1.0f);  // a NaN prediction gets rho_min
 }
 
+// c1_dev (nullable): the counter word read on the device (graph launches);
+// on_dev (nullable): 0 there means no screening yet (every proposal passes
+// with rho = 1 and no uniform is drawn), as before the surrogate is trained
 __global__ void k_screen(const float* __restrict__ Y, const float* __restrict__ ystat,
                          const uint8_t* __restrict__ pflag, int64_t M, const double* eps_p,
                          uint32_t k0, uint32_t k1, uint32_t c1, float tau, float rho_min,
                          float audit_frac, float* __restrict__ rho, uint8_t* __restrict__ sflag,
-                         unsigned long long* __restrict__ exhausted) {
+                         unsigned long long* __restrict__ exhausted,
+                         const uint32_t* __restrict__ c1_dev, const int* __restrict__ on_dev) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool ex = i < M && pflag && pflag[i];
   if (exhausted) {
@@ -557,6 +575,12 @@ __global__ void k_screen(const float* __restrict__ Y, const float* __restrict__ 
     rho[i] = 1.0f;
     return;
   }
+  if (on_dev && !*on_dev) {
+    sflag[i] = 0;
+    rho[i] = 1.0f;
+    return;
+  }
+  if (c1_dev) c1 = *c1_dev;
   const float le = dev_log1p(__double2float_rn(*eps_p));
   const float r = screen_rho(Y[i * 4], ystat, le, tau, rho_min);
   rho[i] = r;
@@ -571,11 +595,13 @@ __global__ void k_screen(const float* __restrict__ Y, const float* __restrict__ 
 
 int screen(const float* Y, const float* ystat, const uint8_t* pflag, int64_t M, const double* eps,
            uint32_t k0, uint32_t k1, uint32_t c1, float tau, float rho_min, float audit_frac,
-           float* rho, uint8_t* sflag, cudaStream_t st, unsigned long long* exhausted) {
+           float* rho, uint8_t* sflag, cudaStream_t st, unsigned long long* exhausted,
+           const uint32_t* c1_dev, const int* on_dev) {
   if (M <= 0) return ABC_OK;
   k_screen<<<static_cast<unsigned>(ceil_div(M, 256)), 256, 0, st>>>(Y, ystat, pflag, M, eps, k0, k1,
                                                                      c1, tau, rho_min, audit_frac,
-                                                                     rho, sflag, exhausted);
+                                                                     rho, sflag, exhausted, c1_dev,
+                                                                     on_dev);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }
@@ -594,7 +620,7 @@ __global__ void k_cmp_count(const uint8_t* __restrict__ sflag, int64_t M, int* _
 }
 
 __global__ void k_cmp_scan(const int* __restrict__ cnt, int ntiles, int* __restrict__ off,
-                           int* __restrict__ total) {
+                           int* __restrict__ total, long long* __restrict__ acc = nullptr) {
   __shared__ int sm[32];
   __shared__ int last;
   int carry = 0;
@@ -608,7 +634,10 @@ __global__ void k_cmp_scan(const int* __restrict__ cnt, int ntiles, int* __restr
     carry += last;
     __syncthreads();
   }
-  if (threadIdx.x == 0) *total = carry;
+  if (threadIdx.x == 0) {
+    *total = carry;
+    if (acc) *acc += carry;  // running count over the generation's batches
+  }
 }
 
 __global__ void k_cmp_scatter(const uint8_t* __restrict__ sflag, int64_t M, const int* __restrict__ off,
@@ -617,11 +646,11 @@ __global__ void k_cmp_scatter(const uint8_t* __restrict__ sflag, int64_t M, cons
                               float* __restrict__ cu, float* __restrict__ cs,
                               int32_t* __restrict__ ca, float* __restrict__ crho,
                               uint8_t* __restrict__ cflag, uint32_t* __restrict__ cslot,
-                              const int* __restrict__ Mc_dev) {
+                              int64_t stride) {
   __shared__ int sm[32];
-  // the compacted list is [8][Mc] with stride Mc, the layout every consumer
-  // (simulator, acceptance, training ring) reads with n = Mc
-  const int64_t stride = *Mc_dev;
+  // the compacted list is [8][stride] (stride = the batch size M, so that the
+  // consumers -- simulator, acceptance, training ring -- take n = M with the
+  // count Mc on the device)
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kCTile + 4 * threadIdx.x;
   bool keep[4];
   int c = 0;
@@ -652,19 +681,20 @@ int screen_and_compact(const float* Y, const float* ystat, const uint8_t* pflag,
                        float rho_min, float audit_frac, float* rho, uint8_t* sflag,
                        const float* up, const float* sp, const int32_t* ap, float* cu, float* cs,
                        int32_t* ca, float* crho, uint8_t* cflag, uint32_t* cslot, int* Mc_dev,
-                       void* scratch, cudaStream_t st, unsigned long long* exhausted) {
+                       void* scratch, cudaStream_t st, unsigned long long* exhausted,
+                       const uint32_t* c1_dev, const int* on_dev, long long* sim_acc) {
   const int64_t nt = ceil_div(M, kCTile);
   int* cnt = static_cast<int*>(scratch);
   int* off = cnt + align256(4 * nt) / 4;
   int rc = screen(Y, ystat, pflag, M, eps, k0, k1, c1, tau, rho_min, audit_frac, rho, sflag, st,
-                  exhausted);
+                  exhausted, c1_dev, on_dev);
   if (rc) return rc;
   k_cmp_count<<<static_cast<unsigned>(nt), 256, 0, st>>>(sflag, M, cnt);
   ABC_LAUNCH_CHECK();
-  k_cmp_scan<<<1, 1024, 0, st>>>(cnt, static_cast<int>(nt), off, Mc_dev);
+  k_cmp_scan<<<1, 1024, 0, st>>>(cnt, static_cast<int>(nt), off, Mc_dev, sim_acc);
   ABC_LAUNCH_CHECK();
   k_cmp_scatter<<<static_cast<unsigned>(nt), 256, 0, st>>>(sflag, M, off, up, sp, ap, rho, cu, cs, ca,
-                                                           crho, cflag, cslot, Mc_dev);
+                                                           crho, cflag, cslot, M);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }
@@ -675,27 +705,32 @@ size_t screen_scratch_bytes(int64_t M) { return 2 * align256(4 * ceil_div(std::m
 // Appends n simulated samples (u [8][n] stride n, d, final A, R, D [3][n])
 // as x = u and y = [log1p d, log1p A_T, log1p R_T, log1p D_T] at ring
 // positions (*head + i) mod cap; valid (nullable) selects samples in order.
-__global__ void k_ring_count(const uint8_t* __restrict__ invalid, int64_t n, int* __restrict__ cnt) {
+__global__ void k_ring_count(const uint8_t* __restrict__ invalid, int64_t n,
+                             const int* __restrict__ n_dev, int* __restrict__ cnt) {
   __shared__ int sm[32];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kCTile + 4 * threadIdx.x;
+  const int64_t lim = n_dev ? static_cast<int64_t>(*n_dev) : n;
   int c = 0;
 #pragma unroll
-  for (int e = 0; e < 4; ++e) c += (base + e < n && (!invalid || invalid[base + e] == 0));
+  for (int e = 0; e < 4; ++e)
+    c += (base + e < n && base + e < lim && (!invalid || invalid[base + e] == 0));
   c = block_sum<int>(c, sm);
   if (threadIdx.x == 0) cnt[blockIdx.x] = c;
 }
 
-__global__ void k_ring_put(const uint8_t* __restrict__ invalid, int64_t n, const int* __restrict__ off,
+__global__ void k_ring_put(const uint8_t* __restrict__ invalid, int64_t n,
+                           const int* __restrict__ n_dev, const int* __restrict__ off,
                            const float* __restrict__ u, const double* __restrict__ d,
                            const int32_t* __restrict__ ard, const long long* __restrict__ head,
                            int64_t cap, float* __restrict__ RX, float* __restrict__ RY) {
   __shared__ int sm[32];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kCTile + 4 * threadIdx.x;
+  const int64_t lim = n_dev ? static_cast<int64_t>(*n_dev) : n;
   bool keep[4];
   int c = 0;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    keep[e] = base + e < n && (!invalid || invalid[base + e] == 0);
+    keep[e] = base + e < n && base + e < lim && (!invalid || invalid[base + e] == 0);
     c += keep[e];
   }
   const int inc = block_incl_scan<int>(c, sm);
@@ -720,17 +755,18 @@ __global__ void k_ring_advance(long long* head, const int* added) { *head += *ad
 
 int ring_append(const uint8_t* invalid, int64_t n, const float* u, const double* d,
                 const int32_t* ard, long long* head, int64_t cap, float* RX, float* RY,
-                void* scratch, cudaStream_t st) {
+                void* scratch, cudaStream_t st, const int* n_dev) {
   if (n <= 0) return ABC_OK;
   const int64_t nt = ceil_div(n, kCTile);
   int* cnt = static_cast<int*>(scratch);
   int* off = cnt + align256(4 * nt) / 4;
   int* added = off + align256(4 * nt) / 4;
-  k_ring_count<<<static_cast<unsigned>(nt), 256, 0, st>>>(invalid, n, cnt);
+  k_ring_count<<<static_cast<unsigned>(nt), 256, 0, st>>>(invalid, n, n_dev, cnt);
   ABC_LAUNCH_CHECK();
   k_cmp_scan<<<1, 1024, 0, st>>>(cnt, static_cast<int>(nt), off, added);
   ABC_LAUNCH_CHECK();
-  k_ring_put<<<static_cast<unsigned>(nt), 256, 0, st>>>(invalid, n, off, u, d, ard, head, cap, RX, RY);
+  k_ring_put<<<static_cast<unsigned>(nt), 256, 0, st>>>(invalid, n, n_dev, off, u, d, ard, head, cap,
+                                                        RX, RY);
   ABC_LAUNCH_CHECK();
   k_ring_advance<<<1, 1, 0, st>>>(head, added);
   ABC_LAUNCH_CHECK();
@@ -767,9 +803,11 @@ __global__ void k_ring_stats(const float* __restrict__ RY, const long long* __re
 __global__ void k_ring_batch(const float* __restrict__ RX, const float* __restrict__ RY,
                              const long long* __restrict__ head, int64_t cap,
                              const float* __restrict__ ystat, int B, uint32_t step, uint32_t k0,
-                             uint32_t k1, float* __restrict__ X, float* __restrict__ T) {
+                             uint32_t k1, float* __restrict__ X, float* __restrict__ T,
+                             const uint32_t* __restrict__ step_dev) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B) return;
+  if (step_dev) step += *step_dev;  // the run's Adam steps so far (device counter)
   const int64_t m = *head < cap ? *head : cap;
   const u32x4 r = philox4x32_10(static_cast<uint32_t>(i), step, 0u, kTagTrain, k0, k1);
   const uint64_t U = (static_cast<uint64_t>(r.y) << 32) | r.x;
@@ -780,17 +818,48 @@ __global__ void k_ring_batch(const float* __restrict__ RX, const float* __restri
   for (int o = 0; o < 4; ++o) T[i * 4 + o] = (RY[src * 4 + o] - ystat[o]) / ystat[4 + o];
 }
 
+__global__ void k_step_advance(uint32_t* step_dev, uint32_t steps, const int* off_dev) {
+  if (!(off_dev && *off_dev)) *step_dev += steps;
+}
+
+// `steps` Adam steps on minibatches of the ring; the step count lives on the
+// device (*step_dev, advanced here), so the sequence is the same whether the
+// host loop runs once per generation or is captured in a graph
 int mlp_train(const MlpState& s, const float* RX, const float* RY, const long long* head,
-              int64_t cap, const float* ystat, int B, int steps, uint32_t step0, float lr,
+              int64_t cap, const float* ystat, int B, int steps, uint32_t* step_dev, float lr,
               uint32_t k0, uint32_t k1, float* grad, float* X, float* T, float* loss_dev,
-              void* scratch, size_t bytes, cudaStream_t st) {
+              void* scratch, size_t bytes, cudaStream_t st, const int* off_dev) {
   int rc;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const unsigned g = (kMlpParams + 255) / 256;
   for (int k = 0; k < steps; ++k) {
-    k_ring_batch<<<(B + 255) / 256, 256, 0, st>>>(RX, RY, head, cap, ystat, B, step0 + k, k0, k1, X, T);
+    k_ring_batch<<<(B + 255) / 256, 256, 0, st>>>(RX, RY, head, cap, ystat, B,
+                                                  static_cast<uint32_t>(k), k0, k1, X, T, step_dev);
     ABC_LAUNCH_CHECK();
     if ((rc = mlp_grad(s, X, T, B, grad, loss_dev, scratch, bytes, st))) return rc;
-    if ((rc = mlp_adam(s, grad, static_cast<int64_t>(step0) + k + 1, lr, st))) return rc;
+    k_adam<<<g, 256, 0, st>>>(s.w, grad, s.m, s.v, lr, b1, b2, eps, 1.0f, 1.0f, step_dev,
+                              static_cast<uint32_t>(k));
+    ABC_LAUNCH_CHECK();
+    k_mlp_to_bf16<<<g, 256, 0, st>>>(s.w, s.wb);
+    ABC_LAUNCH_CHECK();
   }
+  k_step_advance<<<1, 1, 0, st>>>(step_dev, static_cast<uint32_t>(steps), off_dev);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+// screening from the generation `start` on once the surrogate has been
+// trained: *on = t >= start && *step_dev > 0 (t from t_dev when given)
+__global__ void k_sur_gate(const uint32_t* t_dev, uint32_t t, int start,
+                           const uint32_t* step_dev, int* on) {
+  if (t_dev) t = *t_dev;
+  *on = (t >= static_cast<uint32_t>(start) && *step_dev > 0u) ? 1 : 0;
+}
+
+int sur_gate(const uint32_t* t_dev, uint32_t t, int start, const uint32_t* step_dev, int* on,
+             cudaStream_t st) {
+  k_sur_gate<<<1, 1, 0, st>>>(t_dev, t, start, step_dev, on);
+  ABC_LAUNCH_CHECK();
   return ABC_OK;
 }
 
@@ -824,13 +893,15 @@ int audit_count(const uint8_t* cflag, const double* cd, const int* Mc, const dou
 }
 
 // delayed-acceptance correction of importance weights: log W -= log rho
-__global__ void k_rho_correct(double* __restrict__ logW, const float* __restrict__ rho, int64_t n) {
+__global__ void k_rho_correct(double* __restrict__ logW, const float* __restrict__ rho, int64_t n,
+                              const int* __restrict__ off_dev) {
+  if (off_dev && *off_dev) return;
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i < n) logW[i] -= log(static_cast<double>(rho[i]));
 }
 
-int rho_correct(double* logW, const float* rho, int64_t n, cudaStream_t st) {
-  k_rho_correct<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, st>>>(logW, rho, n);
+int rho_correct(double* logW, const float* rho, int64_t n, cudaStream_t st, const int* off_dev) {
+  k_rho_correct<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, st>>>(logW, rho, n, off_dev);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

@@ -95,14 +95,6 @@ def test_defaults_and_argument_checks_without_gpu(lib):
                          (5, 0.5, 3.0)]:
         bad = G.config(beta_mode=mode, beta_p1=p1, beta_p2=p2)
         assert lib.abc_init(ctypes.byref(bad), None, None, ctypes.byref(h)) == -1, (mode, p1, p2)
-    # batched runs: the graph branches have no screening step, so a run that
-    # asks for the surrogate is refused before any device work
-    plain = G.config(model=G.ABC_MODEL_GAUSS_TOY, n_particles=64)
-    sur = G.config(model=G.ABC_MODEL_GAUSS_TOY, n_particles=64, surrogate=1)
-    arr = (G.AbcConfig * 2)(plain, sur)
-    ptrs = (ctypes.c_void_p * 2)(None, None)
-    assert lib.abc_batch_init(arr, 2, ctypes.cast(ptrs, ctypes.c_void_p), None,
-                              ctypes.byref(h)) == -1
     assert lib.abc_select_kth(None, 10, 1, None, None, 0, None) == -1
     assert lib.abc_select_scratch_bytes(1 << 20) > 0
     assert lib.abc_weights_scratch_bytes(4096, 4096) >= 4096 * 9 * 4

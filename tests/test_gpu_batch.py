@@ -143,3 +143,59 @@ def test_autotune_keeps_results_and_writes_cache(tmp_path):
     finally:
         G.abc_batch_free(a)
         G.abc_batch_free(b)
+
+
+def _sur_batch_cfgs():
+    """Runs with the surrogate pre-screen (delayed acceptance) beside one
+    without: a SAIRD run with importance weights, a SAIRD run with the paper's
+    weights, the Gaussian toy with importance weights, and a plain run."""
+    sur = dict(surrogate=1, surrogate_start=2, surrogate_steps=16, surrogate_batch=1024,
+               surrogate_lr=1e-3, surrogate_tau=0.3, surrogate_rho_min=0.05, audit_frac=0.05)
+    return [
+        saird_config(2048, 40, 100_000, seed=21, weight_mode=G.ABC_W_IMPORTANCE,
+                     weight_prec=G.ABC_P_BF16_TC, **sur),
+        saird_config(3000, 30, 1_000_000, seed=22, weight_mode=G.ABC_W_PAPER,
+                     beta_mode=G.ABC_BETA_FIXED, beta_a=2.0, beta_b=5, **sur),
+        G.config(model=G.ABC_MODEL_GAUSS_TOY, n_days=1, population=1, init_ard=[0, 0, 0],
+                 theta_lo=[-10.0] * 8, theta_hi=[10.0] * 8, seed=23, n_particles=2048,
+                 beta_mode=G.ABC_BETA_FIXED, beta_a=8.0, beta_b=1000,
+                 weight_mode=G.ABC_W_IMPORTANCE, max_batches=400, **sur),
+        saird_config(1024, 50, 100_000, seed=24, weight_mode=G.ABC_W_IMPORTANCE),
+    ]
+
+
+def test_batch_with_surrogate_equals_single_contexts():
+    """The surrogate inside the graph branches (inference, screen, compacted
+    simulation, audits, training ring, 1/rho correction and Adam training
+    after each generation, all with device-side counts): every run equals its
+    own single-run context bit for bit -- populations, tolerances, batches,
+    simulations, screened / audited counts -- through generations that screen."""
+    cfgs = _sur_batch_cfgs()
+    obs = [None if c.model == G.ABC_MODEL_GAUSS_TOY else oracle_obs(c)[0] for c in cfgs]
+    gens = 6
+    b = G.abc_batch_init(cfgs, obs)
+    ctxs = [G.abc_init(c, o) for c, o in zip(cfgs, obs)]
+    try:
+        G.abc_batch_run(b, gens)
+        for ctx in ctxs:
+            G.abc_run(ctx, gens)
+        screened_any = 0
+        for r, (cfg, ctx) in enumerate(zip(cfgs, ctxs)):
+            N = cfg.n_particles
+            gp, sp = _batch_pop(b, r, N), get_population(ctx, N)
+            for k in gp:
+                assert np.array_equal(gp[k].view(np.uint8), sp[k].view(np.uint8)), (r, k)
+            for t in range(gens):
+                g, s = G.abc_batch_get_stats(b, r, t), G.abc_get_stats(ctx, t)
+                assert (g.eps, g.batches, g.sims, g.exhausted, g.accepted) == \
+                       (s.eps, s.batches, s.sims, s.exhausted, s.accepted), (r, t)
+                assert (g.screened, g.audited, g.audit_accepted) == \
+                       (s.screened, s.audited, s.audit_accepted), (r, t)
+                if cfg.weight_mode == G.ABC_W_IMPORTANCE:
+                    assert g.ess == s.ess, (r, t)
+                screened_any += g.screened
+        assert screened_any > 0  # the screen did run in the graph
+    finally:
+        G.abc_batch_free(b)
+        for ctx in ctxs:
+            G.abc_free(ctx)
