@@ -48,7 +48,7 @@ extern "C" {
 /* ---- status codes ------------------------------------------------------ */
 #define ABC_OK 0
 #define ABC_STOP_BUDGET 1       /* a generation used max_batches batches before N acceptances */
-#define ABC_STOP_TARGET 2       /* abc_run reached eps_target                           */
+#define ABC_STOP_TARGET 2       /* abc_run reached eps_target, or the run its eps_stop   */
 #define ABC_STOP_TOTAL 3        /* the run used max_total_batches batches (Sec. 4.1)     */
 #define ABC_E_INVAL (-1)        /* bad argument or configuration                         */
 #define ABC_E_NOMEM (-2)        /* device allocation failed                              */
@@ -157,7 +157,11 @@ typedef struct {
    * rounds) run faster.  The proposal buffers hold K M slots.  Generations
    * that screen with the surrogate run one batch per round. */
   int32_t spec_batches;
-  int32_t pad_end;
+  /* Tolerance target: once a generation t >= 1 ends with eps_t <= eps_stop
+   * the run is finished -- abc_generation returns ABC_STOP_TARGET and runs
+   * nothing, and a batched run stops like one whose run budget is used up.
+   * 0: no target.  (abc_run's eps_target does the same for one call.) */
+  float eps_stop;
 } abc_config;
 
 /* Fill a config with the paper's defaults (SAIRD, binomial flows, alpha 0.5,

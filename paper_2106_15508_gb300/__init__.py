@@ -59,7 +59,7 @@ class AbcConfig(C.Structure):
         ("surrogate_batch", C.c_int32), ("surrogate_lr", C.c_float), ("surrogate_tau", C.c_float),
         ("surrogate_rho_min", C.c_float), ("audit_frac", C.c_float), ("surrogate_ring", C.c_int32),
         ("beta_p1", C.c_float), ("beta_p2", C.c_float), ("max_total_batches", C.c_int32),
-        ("spec_batches", C.c_int32), ("pad_end", C.c_int32),
+        ("spec_batches", C.c_int32), ("eps_stop", C.c_float),
     ]
 
 

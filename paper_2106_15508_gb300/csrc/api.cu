@@ -118,6 +118,7 @@ int check_smc(const abc_config* c) {
   if (c->weight_prec != ABC_P_FP32 && c->weight_prec != ABC_P_BF16_TC) return ABC_E_INVAL;
   if (c->max_batches < 1 || c->max_batches > 65535) return ABC_E_INVAL;
   if (c->max_total_batches < 0) return ABC_E_INVAL;
+  if (!(c->eps_stop >= 0.0f && c->eps_stop < INFINITY)) return ABC_E_INVAL;
   if (c->spec_batches < 0 || c->spec_batches > 256) return ABC_E_INVAL;
   if (c->max_redraw < 1 || c->max_redraw > (1 << 23)) return ABC_E_INVAL;
   if (c->surrogate) {
@@ -1010,6 +1011,10 @@ ABC_API int abc_generation(abc_ctx* c) {
   if (c->gen > 0 && c->cfg.max_total_batches > 0 &&
       c->batches_total >= c->cfg.max_total_batches)
     return ABC_STOP_TOTAL;
+  // tolerance target reached by the last generation
+  if (c->gen > 1 && c->cfg.eps_stop > 0.0f &&
+      c->stats.back().eps <= static_cast<double>(c->cfg.eps_stop))
+    return ABC_STOP_TARGET;
   ABC_CUDA_TRY(cudaEventRecord(c->ev0, c->st));
   const int64_t l0 = g_launches.load();
   const bool first = c->gen == 0;
@@ -1378,6 +1383,7 @@ ABC_API int abc_batch_init(const abc_config* cfgs, int32_t n_runs, const int32_t
     std::memset(&b->host[r], 0, sizeof(RunDev));
     b->host[r].max_batches = cfgs[r].max_batches;
     b->host[r].max_total = cfgs[r].max_total_batches;
+    b->host[r].eps_stop = static_cast<double>(cfgs[r].eps_stop);
     b->br[r].v = ctx_view(b->runs[r]);
     b->br[r].dev = b->dev + r;
   }

@@ -79,6 +79,8 @@ __global__ void k_run_finish(RunDev* r, long long N) {
   // run budget (Sec. 4.1): this generation is kept, later ones are skipped
   r->batches_total += r->batches;
   if (ok && r->max_total > 0 && r->batches_total >= r->max_total) r->done = 1;
+  // tolerance target: this generation is kept, later ones are skipped
+  if (ok && r->eps_stop > 0.0 && r->eps <= r->eps_stop) r->done = 1;
 }
 
 // the new population becomes the current one (skipped when the run is off)

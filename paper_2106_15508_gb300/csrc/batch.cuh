@@ -27,6 +27,7 @@ struct RunDev {
   int32_t used;             // batches the round used (up to the one that filled N)
   int32_t pad;
   double eps, eps1, ess;
+  double eps_stop;          // tolerance target (0: none)
 };
 
 // Buffers and settings of a run's surrogate pre-screen (borrowed from its

@@ -199,3 +199,42 @@ def test_batch_with_surrogate_equals_single_contexts():
         G.abc_batch_free(b)
         for ctx in ctxs:
             G.abc_free(ctx)
+
+
+def test_tolerance_target_stops_runs():
+    """eps_stop: a run whose generation ends at or below its target is done --
+    a single context returns ABC_STOP_TARGET afterwards, and in a graph batch
+    that run stops while the others go on, its population kept."""
+    base = [saird_config(2048, 30, 100_000, seed=31, weight_mode=G.ABC_W_IMPORTANCE),
+            saird_config(1024, 30, 100_000, seed=32, weight_mode=G.ABC_W_IMPORTANCE)]
+    obs = [oracle_obs(c)[0] for c in base]
+    ref = G.abc_init(base[0], obs[0])
+    try:
+        G.abc_run(ref, 6)
+        target = G.abc_get_stats(ref, 3).eps
+        ref_pop = None
+        G.abc_reset(ref, base[0].run_id)
+        G.abc_run(ref, 4)
+        ref_pop = get_population(ref, 2048)
+    finally:
+        G.abc_free(ref)
+    stop = saird_config(2048, 30, 100_000, seed=31, weight_mode=G.ABC_W_IMPORTANCE,
+                        eps_stop=float(np.float32(target) if np.float32(target) >= target
+                                       else np.nextafter(np.float32(target), np.float32(np.inf))))
+    ctx = G.abc_init(stop, obs[0])
+    try:
+        assert G.abc_run(ctx, 10) == G.ABC_STOP_TARGET
+        assert G.abc_generations(ctx) == 4
+        assert G.abc_generation(ctx) == G.ABC_STOP_TARGET
+    finally:
+        G.abc_free(ctx)
+    b = G.abc_batch_init([stop, base[1]], obs)
+    try:
+        G.abc_batch_run(b, 7)
+        assert G.abc_batch_active(b) == 1
+        assert G.abc_batch_generations(b) == 7
+        gp = _batch_pop(b, 0, 2048)
+        for k in gp:
+            assert np.array_equal(gp[k].view(np.uint8), ref_pop[k].view(np.uint8)), k
+    finally:
+        G.abc_batch_free(b)
