@@ -323,7 +323,7 @@ def abc_init_ptr(cfg, obs_host_ptr, stream=None):
 
 def abc_generation(ctx):
     return _check(lib().abc_generation(ctx), "abc_generation",
-                  ok=(ABC_OK, ABC_STOP_BUDGET, ABC_STOP_TOTAL))
+                  ok=(ABC_OK, ABC_STOP_BUDGET, ABC_STOP_TARGET, ABC_STOP_TOTAL))
 
 
 def abc_run(ctx, n_generations, eps_target=0.0):
