@@ -545,15 +545,25 @@ def cpu_baseline(w, G_run):
                           G_run, ORACLE_SAMPLE_N, days, secs, w.N)}
 
 
+def _f32_at_least(x):
+    """The smallest float32 >= x (a tolerance target that x itself meets)."""
+    import numpy as np
+    f = np.float32(x)
+    return float(f if float(f) >= x else np.nextafter(f, np.float32(np.inf)))
+
+
 def run_eps_final(args):
-    """Wall-time to eps_final per run.  The runs of the batched workload
-    (importance weights) first run G generations each in plain contexts;
-    eps_final of a run is its tolerance at generation G.  The same runs then
-    reach eps_final (1) batched: one graph launch per generation of all runs
-    (bit-identical results, so the same G generations), (2) with the
-    surrogate pre-screen in their own contexts (generations until eps <=
-    eps_final, at most 3 G).  Reported: mean wall-time per run of each form
-    (host clock around device-synchronised generations)."""
+    """Wall-time to eps_final per run, four forms of the same runs.
+    (1) plain: each run alone in its own context, one after another, G
+    generations; eps_final of a run is its tolerance at generation G.
+    (2) batched: all runs in one graph launch per generation (bit-identical
+    results, so the same G generations).  (3) surrogate + batched: every run
+    screened by its own surrogate, all runs in one graph, each run stopping
+    at its eps_final (abc_config.eps_stop), at most 3 G generations.  (4)
+    surrogate alone: the screened runs in their own contexts one after
+    another.  Reported: mean wall-time per run of each form (host clock
+    around device-synchronised calls; a batch's time is shared by its runs),
+    simulations per run, false-rejection rate, runs that reached eps_final."""
     import numpy as np
     import torch
 
@@ -570,7 +580,12 @@ def run_eps_final(args):
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
     gens = args.generations or 8
-    # plain
+    R = len(cfgs)
+
+    def stats_of(get, n):
+        return [get(t) for t in range(n)]
+
+    # (1) plain
     eps_final, t_plain, sims_plain = [], [], []
     for c, o in zip(cfgs, obs):
         ctx = G.abc_init(c, o, stream=sp)
@@ -580,12 +595,12 @@ def run_eps_final(args):
             G.abc_run(ctx, gens + 1)
             torch.cuda.synchronize()
             t_plain.append(time.perf_counter() - t0)
-            st = [G.abc_get_stats(ctx, t) for t in range(G.abc_generations(ctx))]
+            st = stats_of(lambda t: G.abc_get_stats(ctx, t), G.abc_generations(ctx))
             eps_final.append(st[-1].eps)
             sims_plain.append(sum(x.sims for x in st))
         finally:
             G.abc_free(ctx)
-    # batched
+    # (2) batched
     b = G.abc_batch_init(cfgs, obs, stream=sp)
     try:
         torch.cuda.synchronize()
@@ -594,55 +609,93 @@ def run_eps_final(args):
         torch.cuda.synchronize()
         t_batch = time.perf_counter() - t0
         last = G.abc_batch_generations(b) - 1
-        eps_b = [G.abc_batch_get_stats(b, r, last).eps for r in range(len(cfgs))]
+        eps_b = [G.abc_batch_get_stats(b, r, last).eps for r in range(R)]
     finally:
         G.abc_batch_free(b)
-    # surrogate
-    t_sur, gens_sur, sims_sur, frr, reached = [], [], [], [], 0
-    for c, o, ef in zip([] if args.no_surrogate else cfgs, obs, eps_final):
+
+    def sur_cfg(c, ef):
         sc = G.config(**{f: getattr(c, f) if not hasattr(getattr(c, f), "_length_")
                          else list(getattr(c, f)) for f, _ in c._fields_})
         sc.surrogate, sc.surrogate_start, sc.surrogate_steps = 1, 2, args.surrogate_steps
-        sc.surrogate_batch, sc.surrogate_tau = 4096, args.surrogate_tau
-        sc.surrogate_rho_min, sc.audit_frac = 0.05, 0.01
+        sc.surrogate_batch, sc.surrogate_tau = args.surrogate_batch, args.surrogate_tau
+        sc.surrogate_lr = 1e-3
+        sc.surrogate_rho_min, sc.audit_frac = args.surrogate_rho_min, 0.01
+        sc.eps_stop = _f32_at_least(ef)
+        return sc
+
+    scfgs = [sur_cfg(c, ef) for c, ef in zip(cfgs, eps_final)]
+
+    def sur_summary(get_stats, ngen):
+        st = stats_of(get_stats, ngen)
+        aud = sum(x.audited for x in st)
+        return dict(eps=st[-1].eps, gens=ngen - 1, sims=sum(x.sims for x in st),
+                    screened=sum(x.screened for x in st), audited=aud,
+                    audit_accepted=sum(x.audit_accepted for x in st),
+                    ms_train=sum(x.ms_train for x in st), ms_screen=sum(x.ms_screen for x in st))
+
+    # (3) surrogate + batched
+    b = G.abc_batch_init(scfgs, obs, stream=sp)
+    sb = []
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.abc_batch_run(b, 3 * gens + 1)
+        torch.cuda.synchronize()
+        t_sur_batch = time.perf_counter() - t0
+        for r in range(R):
+            n = 0
+            while True:
+                try:
+                    G.abc_batch_get_stats(b, r, n)
+                    n += 1
+                except G.AbcError:
+                    break
+            sb.append(sur_summary(lambda t, r=r: G.abc_batch_get_stats(b, r, t), n))
+    finally:
+        G.abc_batch_free(b)
+    # (4) surrogate alone
+    t_sur, ss = [], []
+    for sc, o in zip([] if args.no_surrogate else scfgs, obs):
         ctx = G.abc_init(sc, o, stream=sp)
         try:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            rc = G.abc_generation(ctx)  # stage 0
-            n = 1
-            while rc == G.ABC_OK and n < 3 * gens + 1:
-                rc = G.abc_generation(ctx)
-                n += 1
-                if G.abc_get_stats(ctx, n - 1).eps <= ef:
-                    break
+            G.abc_run(ctx, 3 * gens + 1)
             torch.cuda.synchronize()
             t_sur.append(time.perf_counter() - t0)
-            st = [G.abc_get_stats(ctx, t) for t in range(G.abc_generations(ctx))]
-            reached += st[-1].eps <= ef
-            gens_sur.append(len(st) - 1)
-            sims_sur.append(sum(x.sims for x in st))
-            aud = sum(x.audited for x in st)
-            frr.append(sum(x.audit_accepted for x in st) / aud if aud else 0.0)
+            ss.append(sur_summary(lambda t: G.abc_get_stats(ctx, t), G.abc_generations(ctx)))
         finally:
             G.abc_free(ctx)
-    R = len(cfgs)
     per = lambda xs: float(np.mean(xs)) if len(xs) else None
+    reached = lambda xs: int(sum(x["eps"] <= sc.eps_stop for x, sc in zip(xs, scfgs)))
+    frr = lambda xs: (sum(x["audit_accepted"] for x in xs) / max(1, sum(x["audited"] for x in xs))
+                      if xs else None)
     return {"metric": "wall-time to eps_final per run", "unit": "s", "higher_is_better": False,
             "n_gpus": 1, "data": "synthetic",
             "config": {"workload": ("stress_" if args.stress else "") + "eps_final_%d_runs" % R,
                        "generations": gens,
                        "weights": "importance O(N^2), " + ("bf16 tcgen05" if args.prec else "fp32"),
-                       "particles": [w.N for w in runs], "days": [w.T for w in runs]},
+                       "particles": [w.N for w in runs], "days": [w.T for w in runs],
+                       "populations": [w.P for w in runs]},
             "plain_s_per_run": per(t_plain),
             "batched_s_per_run": t_batch / R,
             "batched_same_eps": bool(np.all(np.array(eps_b) == np.array(eps_final))),
+            "surrogate_batched_s_per_run": t_sur_batch / R,
+            "surrogate_batched_reached": reached(sb),
+            "surrogate_batched_generations": per([x["gens"] for x in sb]),
             "surrogate_s_per_run": per(t_sur),
-            "surrogate_reached": reached, "surrogate_generations": per(gens_sur),
-            "sims_per_run": {"plain": per(sims_plain), "surrogate": per(sims_sur)},
-            "surrogate_false_rejection_rate": per(frr),
-            "surrogate_settings": {"steps": args.surrogate_steps, "batch": 4096,
-                                   "tau": args.surrogate_tau, "rho_min": 0.05, "audit": 0.01}}
+            "surrogate_reached": reached(ss) if ss else None,
+            "surrogate_generations": per([x["gens"] for x in ss]),
+            "sims_per_run": {"plain": per(sims_plain),
+                             "surrogate_batched": per([x["sims"] for x in sb]),
+                             "surrogate": per([x["sims"] for x in ss])},
+            "screened_per_run": {"surrogate_batched": per([x["screened"] for x in sb])},
+            "false_rejection_rate": {"surrogate_batched": frr(sb), "surrogate": frr(ss)},
+            "train_ms_per_run": {"surrogate": per([x["ms_train"] for x in ss])},
+            "screen_ms_per_run": {"surrogate": per([x["ms_screen"] for x in ss])},
+            "surrogate_settings": {"start": 2, "steps": args.surrogate_steps,
+                                   "batch": args.surrogate_batch, "tau": args.surrogate_tau,
+                                   "rho_min": args.surrogate_rho_min, "audit": 0.01, "lr": 1e-3}}
 
 
 def run_passes(args):
@@ -755,6 +808,8 @@ def main():
                     help="generations per run (single: 20, the workload's G; eps_final: 8)")
     ap.add_argument("--surrogate-steps", type=int, default=32)
     ap.add_argument("--surrogate-tau", type=float, default=0.5)
+    ap.add_argument("--surrogate-batch", type=int, default=4096)
+    ap.add_argument("--surrogate-rho-min", type=float, default=0.05)
     ap.add_argument("--stress", action="store_true",
                     help="eps_final on the stress runs (2^20 particles, 365 days, P 3.3e8)")
     ap.add_argument("--no-surrogate", action="store_true")

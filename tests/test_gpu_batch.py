@@ -218,9 +218,11 @@ def test_tolerance_target_stops_runs():
         ref_pop = get_population(ref, 2048)
     finally:
         G.abc_free(ref)
+    f = np.float32(target)  # the smallest float32 at or above the target (compared in fp64)
+    if float(f) < target:
+        f = np.nextafter(f, np.float32(np.inf))
     stop = saird_config(2048, 30, 100_000, seed=31, weight_mode=G.ABC_W_IMPORTANCE,
-                        eps_stop=float(np.float32(target) if np.float32(target) >= target
-                                       else np.nextafter(np.float32(target), np.float32(np.inf))))
+                        eps_stop=float(f))
     ctx = G.abc_init(stop, obs[0])
     try:
         assert G.abc_run(ctx, 10) == G.ABC_STOP_TARGET
