@@ -621,6 +621,8 @@ def run_eps_final(args):
         sc.surrogate_lr = 1e-3
         sc.surrogate_rho_min, sc.audit_frac = args.surrogate_rho_min, 0.01
         sc.eps_stop = _f32_at_least(ef)
+        if args.surrogate_ring_mult > 0:
+            sc.surrogate_ring = args.surrogate_ring_mult * c.n_particles
         return sc
 
     scfgs = [sur_cfg(c, ef) for c, ef in zip(cfgs, eps_final)]
@@ -694,6 +696,7 @@ def run_eps_final(args):
             "train_ms_per_run": {"surrogate": per([x["ms_train"] for x in ss])},
             "screen_ms_per_run": {"surrogate": per([x["ms_screen"] for x in ss])},
             "surrogate_settings": {"start": 2, "steps": args.surrogate_steps,
+                                   "ring_mult": args.surrogate_ring_mult,
                                    "batch": args.surrogate_batch, "tau": args.surrogate_tau,
                                    "rho_min": args.surrogate_rho_min, "audit": 0.01, "lr": 1e-3}}
 
@@ -810,6 +813,8 @@ def main():
     ap.add_argument("--surrogate-tau", type=float, default=0.5)
     ap.add_argument("--surrogate-batch", type=int, default=4096)
     ap.add_argument("--surrogate-rho-min", type=float, default=0.05)
+    ap.add_argument("--surrogate-ring-mult", type=int, default=0,
+                    help="training ring of this many times N samples (0: the library default)")
     ap.add_argument("--stress", action="store_true",
                     help="eps_final on the stress runs (2^20 particles, 365 days, P 3.3e8)")
     ap.add_argument("--no-surrogate", action="store_true")

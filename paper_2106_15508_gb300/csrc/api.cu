@@ -485,7 +485,7 @@ struct abc_ctx {
   long long* ring_head = nullptr; // samples appended so far
   int64_t ring_cap = 0;
   int64_t ring_host = 0;
-  float* ystat = nullptr;         // mean[4], std[4]
+  float* ystat = nullptr;         // output mean[4], sd[4]; input mean[8], sd[8]
   float* Yp = nullptr;            // predictions [M][4]
   float* rho = nullptr;           // pass probability per slot
   uint8_t* sflag = nullptr;
@@ -581,7 +581,7 @@ int ctx_alloc(abc_ctx* c) {
     ABC_ALLOC(c->RX, 8 * static_cast<size_t>(c->ring_cap));
     ABC_ALLOC(c->RY, 4 * static_cast<size_t>(c->ring_cap));
     ABC_ALLOC(c->ring_head, 1);
-    ABC_ALLOC(c->ystat, 8);
+    ABC_ALLOC(c->ystat, 24);
     ABC_ALLOC(c->Yp, 4 * M);
     ABC_ALLOC(c->rho, M);
     ABC_ALLOC(c->sflag, M);
@@ -979,7 +979,8 @@ ABC_API int abc_init(const abc_config* cfg, const int32_t* obs, void* stream, ab
       return ABC_E_CUDA;
     }
     if ((rc = mlp_infer_prepare()) != ABC_OK ||
-        (rc = mlp_init(c->mlp, c->p.k0, c->p.k1, c->st)) != ABC_OK) {
+        (rc = mlp_init(c->mlp, c->p.k0, c->p.k1, c->st)) != ABC_OK ||
+        (rc = stats_init(c->ystat, c->st)) != ABC_OK) {
       delete c;
       return rc;
     }
@@ -1057,7 +1058,8 @@ ABC_API int abc_reset(abc_ctx* c, uint32_t run_id) {
   if (c->cfg.surrogate) {
     ABC_CUDA_TRY(cudaMemsetAsync(c->train_step, 0, sizeof(uint32_t), c->st));
     ABC_CUDA_TRY(cudaMemsetAsync(c->ring_head, 0, sizeof(long long), c->st));
-    const int rc = mlp_init(c->mlp, c->p.k0, c->p.k1, c->st);
+    int rc = mlp_init(c->mlp, c->p.k0, c->p.k1, c->st);
+    if (!rc) rc = stats_init(c->ystat, c->st);
     if (rc) return rc;
   }
   ABC_CUDA_TRY(cudaStreamSynchronize(c->st));

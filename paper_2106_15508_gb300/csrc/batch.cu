@@ -124,7 +124,7 @@ int screened_batch(const SurView& s, const SimParams& p, const int32_t* obs, con
   if (ev) ABC_CUDA_TRY(cudaEventRecord(ev[0], st));
   // predictions of the proposals (the error word is reset once per generation)
   if ((rc = mlp_infer(s.mlp, up, M, s.Yp, s.sscratch, s.sscratch_bytes, inf_err, st, false,
-                      s.inf_err)))
+                      s.inf_err, s.ystat + 8)))
     return rc;
   // delayed acceptance: rho and the pass / audit decision, then the slots to
   // simulate in slot order (stride M, count *Mc on the device)
@@ -151,7 +151,7 @@ int screened_batch(const SurView& s, const SimParams& p, const int32_t* obs, con
 
 int sur_train(const SurView& s, const SimParams& p, const int* off_dev, cudaStream_t st) {
   if (s.steps <= 0) return ABC_OK;
-  int rc = ring_stats(s.RY, s.ring_head, s.ring_cap, s.ystat, st);
+  int rc = ring_stats(s.RX, s.RY, s.ring_head, s.ring_cap, s.ystat, st);
   if (rc) return rc;
   return mlp_train(s.mlp, s.RX, s.RY, s.ring_head, s.ring_cap, s.ystat, s.batch, s.steps,
                    s.train_step, s.lr, p.k0, p.k1, s.grad, s.trX, s.trT, s.loss, s.sscratch,

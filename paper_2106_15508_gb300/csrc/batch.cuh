@@ -35,7 +35,7 @@ struct RunDev {
 struct SurView {
   bool on = false;                 // the run uses the surrogate
   MlpState mlp{};
-  float* ystat = nullptr;          // output means [4], standard deviations [4]
+  float* ystat = nullptr;          // output means, sds [4 + 4]; input means, sds [8 + 8]
   float* Yp = nullptr;             // predictions [M][4]
   float* rho = nullptr;            // pass probability per slot
   uint8_t* sflag = nullptr;        // 0 acceptable, 1 exhausted, 2 audit only, 3 screened out

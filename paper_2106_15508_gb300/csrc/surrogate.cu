@@ -376,15 +376,20 @@ __host__ __device__ __forceinline__ int mlp_packed_index(int r, int k) {
   return ((((r >> 3) << 5) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
 }
 
-// layer 1 + GELU for n samples (u [8][n]) into packed bf16 tiles of h1
+// layer 1 + GELU for n samples (u [8][n]) into packed bf16 tiles of h1;
+// xstat (nullable): input means [8] then standard deviations [8], the
+// network's input being (u - mean) / sd
 __global__ void k_mlp_l1_pack(const float* __restrict__ u, int64_t n, int64_t npad,
                               const __nv_bfloat16* __restrict__ wb, const float* __restrict__ w,
-                              __nv_bfloat16* __restrict__ Hpk) {
+                              __nv_bfloat16* __restrict__ Hpk, const float* __restrict__ xstat) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= npad) return;
   float x[8];
 #pragma unroll
-  for (int d = 0; d < 8; ++d) x[d] = j < n ? u[d * n + j] : 0.0f;
+  for (int d = 0; d < 8; ++d) {
+    x[d] = j < n ? u[d * n + j] : 0.0f;
+    if (xstat) x[d] = __fdiv_rn(__fsub_rn(x[d], xstat[d]), xstat[8 + d]);
+  }
   __nv_bfloat16* tile = Hpk + (j / kMlpM) * (kMlpM * kMlpH);
   const int r = static_cast<int>(j % kMlpM);
   for (int c = 0; c < kMlpH / 8; ++c) {
@@ -516,7 +521,8 @@ unsigned* mlp_infer_err(void* scratch, int64_t n) {
 
 // Y [n][4] (standardised outputs) for u [8][n]; the error word lives in scratch
 int mlp_infer(const MlpState& s, const float* u, int64_t n, float* Y, void* scratch, size_t bytes,
-              unsigned** err_out, cudaStream_t st, bool reset_err, unsigned* err_word) {
+              unsigned** err_out, cudaStream_t st, bool reset_err, unsigned* err_word,
+              const float* xstat) {
   if (n <= 0) return ABC_OK;
   if (bytes < mlp_infer_scratch_bytes(n)) return ABC_E_SCRATCH;
   const int64_t npad = ceil_div(n, kMlpM) * kMlpM;
@@ -529,7 +535,7 @@ int mlp_infer(const MlpState& s, const float* u, int64_t n, float* Y, void* scra
   k_mlp_pack_w2<<<(kMlpH * kMlpH + 255) / 256, 256, 0, st>>>(s.wb, W2pk);
   ABC_LAUNCH_CHECK();
   k_mlp_l1_pack<<<static_cast<unsigned>(ceil_div(npad, 128)), 128, 0, st>>>(u, n, npad, s.wb, s.w,
-                                                                           Hpk);
+                                                                           Hpk, xstat);
   ABC_LAUNCH_CHECK();
   k_mlp_tc<<<static_cast<unsigned>(npad / kMlpM), 192, kMlpSmem, st>>>(
       reinterpret_cast<const uint8_t*>(Hpk), reinterpret_cast<const uint8_t*>(W2pk), s.w, s.wb, n,
@@ -775,27 +781,37 @@ int ring_append(const uint8_t* invalid, int64_t n, const float* u, const double*
 
 size_t ring_scratch_bytes(int64_t n) { return 3 * align256(4 * ceil_div(std::max<int64_t>(n, 1), kCTile)); }
 
-// mean and standard deviation of each output over the filled ring (fp64)
-__global__ void k_ring_stats(const float* __restrict__ RY, const long long* __restrict__ head,
-                             int64_t cap, float* __restrict__ ystat) {
+// mean and standard deviation over the filled ring (fp64), one block per
+// statistic: blocks 0..3 the outputs (ystat[o], ystat[4 + o]), blocks 4..11
+// the inputs (ystat[8 + d], ystat[16 + d]; standard deviations floored at
+// 1e-6 so that a collapsed population keeps finite standardised inputs)
+__global__ void k_ring_stats(const float* __restrict__ RX, const float* __restrict__ RY,
+                             const long long* __restrict__ head, int64_t cap,
+                             float* __restrict__ ystat) {
   __shared__ double sm[32];
   const int64_t m = *head < cap ? *head : cap;
-  for (int o = 0; o < 4; ++o) {
-    double s1 = 0.0, s2 = 0.0;
-    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-      const double y = RY[i * 4 + o];
-      s1 += y;
-      s2 += y * y;
-    }
-    s1 = block_sum<double>(s1, sm);
-    s2 = block_sum<double>(s2, sm);
-    if (threadIdx.x == 0) {
-      const double mean = m > 0 ? s1 / static_cast<double>(m) : 0.0;
-      const double var = m > 1 ? s2 / static_cast<double>(m) - mean * mean : 1.0;
+  const bool out = blockIdx.x < 4;
+  const int o = out ? blockIdx.x : blockIdx.x - 4;
+  const float* src = out ? RY + o : RX + o;
+  const int64_t stride = out ? 4 : 8;
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+    const double y = src[i * stride];
+    s1 += y;
+    s2 += y * y;
+  }
+  s1 = block_sum<double>(s1, sm);
+  s2 = block_sum<double>(s2, sm);
+  if (threadIdx.x == 0) {
+    const double mean = m > 0 ? s1 / static_cast<double>(m) : 0.0;
+    const double var = m > 1 ? s2 / static_cast<double>(m) - mean * mean : 1.0;
+    if (out) {
       ystat[o] = static_cast<float>(mean);
       ystat[4 + o] = static_cast<float>(var > 1e-12 ? sqrt(var) : 1.0);
+    } else {
+      ystat[8 + o] = static_cast<float>(mean);
+      ystat[16 + o] = static_cast<float>(fmax(var > 0.0 ? sqrt(var) : 1.0, 1e-6));
     }
-    __syncthreads();
   }
 }
 
@@ -813,7 +829,7 @@ __global__ void k_ring_batch(const float* __restrict__ RX, const float* __restri
   const uint64_t U = (static_cast<uint64_t>(r.y) << 32) | r.x;
   const int64_t src = m > 0 ? static_cast<int64_t>(__umul64hi(U, static_cast<uint64_t>(m))) : 0;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) X[i * 8 + k] = RX[src * 8 + k];
+  for (int k = 0; k < 8; ++k) X[i * 8 + k] = (RX[src * 8 + k] - ystat[8 + k]) / ystat[16 + k];
 #pragma unroll
   for (int o = 0; o < 4; ++o) T[i * 4 + o] = (RY[src * 4 + o] - ystat[o]) / ystat[4 + o];
 }
@@ -906,8 +922,20 @@ int rho_correct(double* logW, const float* rho, int64_t n, cudaStream_t st, cons
   return ABC_OK;
 }
 
-int ring_stats(const float* RY, const long long* head, int64_t cap, float* ystat, cudaStream_t st) {
-  k_ring_stats<<<1, 1024, 0, st>>>(RY, head, cap, ystat);
+__global__ void k_stats_init(float* ystat) {
+  const int i = threadIdx.x;
+  if (i < 24) ystat[i] = ((i >= 4 && i < 8) || i >= 16) ? 1.0f : 0.0f;
+}
+
+int stats_init(float* ystat, cudaStream_t st) {
+  k_stats_init<<<1, 32, 0, st>>>(ystat);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+int ring_stats(const float* RX, const float* RY, const long long* head, int64_t cap, float* ystat,
+               cudaStream_t st) {
+  k_ring_stats<<<12, 1024, 0, st>>>(RX, RY, head, cap, ystat);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

@@ -40,7 +40,7 @@ int mlp_infer_prepare();
 unsigned* mlp_infer_err(void* scratch, int64_t n);
 int mlp_infer(const MlpState& s, const float* u, int64_t n, float* Y, void* scratch, size_t bytes,
               unsigned** err_out, cudaStream_t st, bool reset_err = true,
-              unsigned* err_word = nullptr);
+              unsigned* err_word = nullptr, const float* xstat = nullptr);
 size_t screen_scratch_bytes(int64_t M);
 int screen(const float* Y, const float* ystat, const uint8_t* pflag, int64_t M, const double* eps,
            uint32_t k0, uint32_t k1, uint32_t c1, float tau, float rho_min, float audit_frac,
@@ -57,7 +57,12 @@ size_t ring_scratch_bytes(int64_t n);
 int ring_append(const uint8_t* invalid, int64_t n, const float* u, const double* d,
                 const int32_t* ard, long long* head, int64_t cap, float* RX, float* RY,
                 void* scratch, cudaStream_t st, const int* n_dev = nullptr);
-int ring_stats(const float* RY, const long long* head, int64_t cap, float* ystat, cudaStream_t st);
+// ystat [24]: output means [4] and standard deviations [4], then input means
+// [8] and standard deviations [8], over the filled ring
+// ystat before any training: means 0, standard deviations 1
+int stats_init(float* ystat, cudaStream_t st);
+int ring_stats(const float* RX, const float* RY, const long long* head, int64_t cap, float* ystat,
+               cudaStream_t st);
 int mlp_train(const MlpState& s, const float* RX, const float* RY, const long long* head,
               int64_t cap, const float* ystat, int B, int steps, uint32_t* step_dev, float lr,
               uint32_t k0, uint32_t k1, float* grad, float* X, float* T, float* loss_dev,
