@@ -494,9 +494,15 @@ ABC_API int abc_mlp_set_params(abc_mlp* m, const float* host_params);
 /* host_params: fp32 master values; host_bf16 (nullable): the bf16 copy's bits */
 ABC_API int abc_mlp_get_params(abc_mlp* m, float* host_params, uint16_t* host_bf16);
 ABC_API size_t abc_mlp_scratch_bytes(int32_t batch, int64_t n);
-/* Gradient of the mean squared error over B samples and 4 outputs (CUDA
- * cores): X device [B][8], T device [B][4]; grad device [69124]; sse device
- * float[1] receives the sum of squared errors. */
+/* Gradient of the mean squared error over B samples and 4 outputs: the
+ * three 256-wide products (layer 2 forward, its input gradient and its
+ * weight gradient) on tcgen05 tensor cores with bf16 operands -- weights,
+ * hidden activations and hidden gradients rounded to bf16 -- and fp32
+ * accumulation; layers 1 and 3 and the bias sums on CUDA cores in fp32; all
+ * reductions in a fixed order (deterministic).  X device [B][8], T device
+ * [B][4]; grad device [69124]; sse device float[1] receives the sum of
+ * squared errors.  Synchronises the stream; ABC_E_DEVICE if a tensor-core
+ * wait timed out. */
 ABC_API int abc_mlp_grad(abc_mlp* m, const float* X, const float* T, int32_t B, float* grad,
                          float* sse, void* scratch, size_t scratch_bytes, void* stream);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step >= 1) on the fp32

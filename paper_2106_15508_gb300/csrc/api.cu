@@ -926,7 +926,9 @@ int generation_t(abc_ctx* c) {
     ABC_CUDA_TRY(cudaEventRecord(c->et1, st));
     float lh = 0.f, mt = 0.f;
     ABC_CUDA_TRY(cudaMemcpyAsync(&lh, c->loss, sizeof lh, cudaMemcpyDeviceToHost, st));
+    ABC_CUDA_TRY(cudaMemcpyAsync(&h_inf_err, inf_err, sizeof h_inf_err, cudaMemcpyDeviceToHost, st));
     ABC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_inf_err) return ABC_E_DEVICE;
     ABC_CUDA_TRY(cudaEventElapsedTime(&mt, c->et0, c->et1));
     g.train_loss = lh / (4.0 * c->cfg.surrogate_batch);
     g.ms_train = mt;
@@ -978,7 +980,7 @@ ABC_API int abc_init(const abc_config* cfg, const int32_t* obs, void* stream, ab
       delete c;
       return ABC_E_CUDA;
     }
-    if ((rc = mlp_infer_prepare()) != ABC_OK ||
+    if ((rc = mlp_infer_prepare()) != ABC_OK || (rc = mlp_train_prepare()) != ABC_OK ||
         (rc = mlp_init(c->mlp, c->p.k0, c->p.k1, c->st)) != ABC_OK ||
         (rc = stats_init(c->ystat, c->st)) != ABC_OK) {
       delete c;
@@ -1662,6 +1664,7 @@ ABC_API int abc_mlp_create(uint64_t seed, abc_mlp** out) {
   int rc = mlp_init(m->s, static_cast<uint32_t>(seed & 0xFFFFFFFFu),
                     static_cast<uint32_t>(seed >> 32), nullptr);
   if (rc == ABC_OK) rc = mlp_infer_prepare();
+  if (rc == ABC_OK) rc = mlp_train_prepare();
   if (rc == ABC_OK && cudaDeviceSynchronize() != cudaSuccess) rc = ABC_E_CUDA;
   if (rc != ABC_OK) {
     delete m;
@@ -1696,7 +1699,10 @@ ABC_API size_t abc_mlp_scratch_bytes(int32_t batch, int64_t n) {
 ABC_API int abc_mlp_grad(abc_mlp* m, const float* X, const float* T, int32_t B, float* grad,
                          float* sse, void* scratch, size_t scratch_bytes, void* stream) {
   if (!m || !X || !T || !grad || !sse || !scratch || B < 1 || B > (1 << 22)) return ABC_E_INVAL;
-  return mlp_grad(m->s, X, T, B, grad, sse, scratch, scratch_bytes, as_stream(stream));
+  cudaStream_t st = as_stream(stream);
+  const int rc = mlp_grad(m->s, X, T, B, grad, sse, scratch, scratch_bytes, st);
+  if (rc) return rc;
+  return check_device_error(mlp_grad_err(scratch, B), st);
 }
 
 ABC_API int abc_mlp_adam(abc_mlp* m, const float* grad, int64_t step, float lr, void* stream) {

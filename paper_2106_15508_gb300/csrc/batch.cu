@@ -155,7 +155,7 @@ int sur_train(const SurView& s, const SimParams& p, const int* off_dev, cudaStre
   if (rc) return rc;
   return mlp_train(s.mlp, s.RX, s.RY, s.ring_head, s.ring_cap, s.ystat, s.batch, s.steps,
                    s.train_step, s.lr, p.k0, p.k1, s.grad, s.trX, s.trT, s.loss, s.sscratch,
-                   s.sscratch_bytes, st, off_dev);
+                   s.sscratch_bytes, st, off_dev, s.inf_err);
 }
 
 int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {

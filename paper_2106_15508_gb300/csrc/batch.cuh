@@ -52,7 +52,7 @@ struct SurView {
   int64_t ring_cap = 0;
   float *grad = nullptr, *trX = nullptr, *trT = nullptr, *loss = nullptr;
   unsigned long long* audit = nullptr;  // audited, audited with d <= eps (this generation)
-  unsigned* inf_err = nullptr;     // error word of the tensor-core inference
+  unsigned* inf_err = nullptr;     // error word of the tensor-core inference and training
   long long* simulated = nullptr;  // simulated slots (this generation)
   uint32_t* train_step = nullptr;  // Adam steps so far (device)
   int* screen_on = nullptr;        // this generation screens

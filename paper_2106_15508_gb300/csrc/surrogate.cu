@@ -178,63 +178,6 @@ static int gemm(int M, int N, int K, const float* A, int64_t sam, int64_t sak, c
 }
 
 // ---- training pieces -------------------------------------------------------
-// layer 1 forward: Z1 = X W1b^T + b1, H1 = gelu(Z1); X [B][8] fp32
-__global__ void k_l1_fwd(const float* __restrict__ X, int B, const __nv_bfloat16* __restrict__ wb,
-                         const float* __restrict__ w, float* __restrict__ Z1, float* __restrict__ H1) {
-  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= static_cast<int64_t>(B) * kMlpH) return;
-  const int b = static_cast<int>(idx / kMlpH), o = static_cast<int>(idx % kMlpH);
-  float z = w[kOffB1 + o];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) z = __fmaf_rn(__bfloat162float(wb[kOffW1 + o * 8 + k]), X[b * 8 + k], z);
-  Z1[idx] = z;
-  H1[idx] = gelu_f(z);
-}
-
-// layer 3 forward and loss gradient: one warp per sample; dY = 2 (Y - T) / (4 B)
-__global__ void k_l3_fwd_loss(const float* __restrict__ H2, int B,
-                              const __nv_bfloat16* __restrict__ wb, const float* __restrict__ w,
-                              const float* __restrict__ Tg, float* __restrict__ Y,
-                              float* __restrict__ dY, float* __restrict__ loss_part) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= B) return;
-  float y[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int k = lane; k < kMlpH; k += 32) {
-    const float h = H2[static_cast<int64_t>(warp) * kMlpH + k];
-#pragma unroll
-    for (int o = 0; o < 4; ++o) y[o] = __fmaf_rn(__bfloat162float(wb[kOffW3 + o * kMlpH + k]), h, y[o]);
-  }
-#pragma unroll
-  for (int o = 0; o < 4; ++o)
-    for (int s = 16; s > 0; s >>= 1) y[o] += __shfl_xor_sync(0xffffffffu, y[o], s);
-  if (lane == 0) {
-    float l = 0.f;
-#pragma unroll
-    for (int o = 0; o < 4; ++o) {
-      const float yo = y[o] + w[kOffB3 + o];
-      Y[warp * 4 + o] = yo;
-      if (Tg) {
-        const float e = yo - Tg[warp * 4 + o];
-        dY[warp * 4 + o] = 2.0f * e / (4.0f * static_cast<float>(B));
-        l += e * e;
-      }
-    }
-    if (Tg) loss_part[warp] = l;
-  }
-}
-
-// dZ2 = (dY W3) * gelu'(Z2)
-__global__ void k_l3_bwd(const float* __restrict__ dY, int B, const __nv_bfloat16* __restrict__ wb,
-                         const float* __restrict__ Z2, float* __restrict__ dZ2) {
-  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= static_cast<int64_t>(B) * kMlpH) return;
-  const int b = static_cast<int>(idx / kMlpH), k = static_cast<int>(idx % kMlpH);
-  float g = 0.f;
-#pragma unroll
-  for (int o = 0; o < 4; ++o) g = __fmaf_rn(dY[b * 4 + o], __bfloat162float(wb[kOffW3 + o * kMlpH + k]), g);
-  dZ2[idx] = g * gelu_grad_f(Z2[idx]);
-}
-
 // column sums: out[n] = sum_b M[b][n] (bias gradients), one block per column
 __global__ void k_colsum(const float* __restrict__ Mx, int B, int N, float* __restrict__ out) {
   __shared__ float sm[32];
@@ -271,64 +214,6 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
   m[i] = mi;
   v[i] = vi;
   w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-}
-
-size_t mlp_train_scratch_bytes(int B) {
-  // Z1, H1, Z2, H2, dZ2, dH1 [B][256]; Y, dY [B][4]; loss parts [B];
-  // split-K partials (64 x 256 x 256)
-  return sizeof(float) * (6 * static_cast<size_t>(B) * kMlpH + 9 * static_cast<size_t>(B) +
-                          static_cast<size_t>(kMaxSplits) * kMlpH * kMlpH + 8) + 1024;
-}
-
-// One forward + backward pass on X [B][8], T [B][4] (standardised targets).
-// Writes the gradients into grad[kMlpParams] and the loss into *loss_dev.
-int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* grad,
-             float* loss_dev, void* scratch, size_t bytes, cudaStream_t st) {
-  if (B <= 0) return ABC_E_INVAL;
-  if (bytes < mlp_train_scratch_bytes(B)) return ABC_E_SCRATCH;
-  float* f = static_cast<float*>(scratch);
-  const size_t BH = static_cast<size_t>(B) * kMlpH;
-  float *Z1 = f, *H1 = f + BH, *Z2 = f + 2 * BH, *H2 = f + 3 * BH, *dZ2 = f + 4 * BH,
-        *dH1 = f + 5 * BH, *Y = f + 6 * BH, *dY = Y + 4 * B, *lp = dY + 4 * B, *sk = lp + B;
-  const __nv_bfloat16* wb = s.wb;
-  const unsigned g1 = static_cast<unsigned>((BH + 255) / 256);
-  k_l1_fwd<<<g1, 256, 0, st>>>(X, B, wb, s.w, Z1, H1);
-  ABC_LAUNCH_CHECK();
-  int rc;
-  // Z2 = H1 W2^T + b2 (B(k,n) = W2[n][k]), H2 = gelu(Z2)
-  if ((rc = gemm<__nv_bfloat16>(B, kMlpH, kMlpH, H1, kMlpH, 1, wb + kOffW2, 1, kMlpH, Z2, kMlpH,
-                                s.w + kOffB2, 1, nullptr, H2, st)))
-    return rc;
-  k_l3_fwd_loss<<<static_cast<unsigned>((B * 32 + 255) / 256), 256, 0, st>>>(H2, B, wb, s.w, T, Y,
-                                                                               dY, lp);
-  ABC_LAUNCH_CHECK();
-  k_sum<<<1, 1024, 0, st>>>(lp, B, loss_dev);
-  ABC_LAUNCH_CHECK();
-  // layer 3 gradients: gW3[o][k] = sum_b dY[b][o] H2[b][k]  (M = 4, N = 256, K = B)
-  if ((rc = gemm<float>(4, kMlpH, B, dY, 1, 4, H2, kMlpH, 1, grad + kOffW3, kMlpH, nullptr, 0,
-                        nullptr, nullptr, st, sk)))
-    return rc;
-  k_colsum<<<4, 256, 0, st>>>(dY, B, 4, grad + kOffB3);
-  ABC_LAUNCH_CHECK();
-  k_l3_bwd<<<g1, 256, 0, st>>>(dY, B, wb, Z2, dZ2);
-  ABC_LAUNCH_CHECK();
-  // gW2 = dZ2^T H1 (M = 256, N = 256, K = B)
-  if ((rc = gemm<float>(kMlpH, kMlpH, B, dZ2, 1, kMlpH, H1, kMlpH, 1, grad + kOffW2, kMlpH, nullptr,
-                        0, nullptr, nullptr, st, sk)))
-    return rc;
-  k_colsum<<<kMlpH, 256, 0, st>>>(dZ2, B, kMlpH, grad + kOffB2);
-  ABC_LAUNCH_CHECK();
-  // dZ1 = (dZ2 W2) * gelu'(Z1)  (B(k,n) = W2[k][n])
-  if ((rc = gemm<__nv_bfloat16>(B, kMlpH, kMlpH, dZ2, kMlpH, 1, wb + kOffW2, kMlpH, 1, dH1, kMlpH,
-                                nullptr, 2, Z1, nullptr, st)))
-    return rc;
-  // gW1 = dZ1^T X (M = 256, N = 8, K = B)
-  if ((rc = gemm<float>(kMlpH, 8, B, dH1, 1, kMlpH, X, 8, 1, grad + kOffW1, 8, nullptr, 0, nullptr,
-                        nullptr, st, sk)))
-    return rc;
-  k_colsum<<<kMlpH, 256, 0, st>>>(dH1, B, kMlpH, grad + kOffB1);
-  ABC_LAUNCH_CHECK();
-  return ABC_OK;
 }
 
 int mlp_adam(const MlpState& s, const float* grad, int64_t step, float lr, cudaStream_t st) {
@@ -542,6 +427,381 @@ int mlp_infer(const MlpState& s, const float* u, int64_t n, float* Y, void* scra
       Y, err);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
+}
+
+// ---- training on tensor cores -------------------------------------------------
+// Packed bf16 operands (8 x 8 core matrices, K-major, 256 K-elements per tile,
+// the inference layout):
+//   R-layout (samples x features): tile t holds samples 128 t .. 128 t + 127,
+//     64 KB, element (b, k) at t * 32768 + mlp_packed_index(b % 128, k);
+//   T-layout (features x samples): tile c holds samples 256 c .. 256 c + 255,
+//     128 KB, element (k, b) at c * 65536 + mlp_packed_index(k, b % 256).
+// One kernel runs the three products of a training step, each a
+// 128 x 256 x 256 UMMA per CTA with operands staged by two bulk copies:
+//   kTrFwd: Z2 = H1 W2^T (A = H1 R-tile, B = W2 packed by output row); the
+//     epilogue adds b2, applies GELU, forms layer 3, the loss and dY, then
+//     back through layer 3 and GELU: dZ2 = (dY W3) gelu'(Z2), written in
+//     both layouts and in fp32, and H2 in fp32;
+//   kTrBwd: dH1 = dZ2 W2 (A = dZ2 R-tile, B = W2^T packed); the epilogue
+//     forms dZ1 = dH1 gelu'(Z1) in fp32;
+//   kTrGw2: gW2 = dZ2^T H1 over one 256-sample tile c (A = rows 128 m .. of
+//     the dZ2 T-tile, B = the H1 T-tile); the epilogue writes the tile's
+//     fp32 partial, summed over tiles in order afterwards (deterministic).
+// Rows past the batch (padding to a multiple of 256) carry dY = 0.
+enum TrMode { kTrFwd = 0, kTrBwd = 1, kTrGw2 = 2 };
+
+struct TrArgs {
+  int B;                      // samples (rows past B are padding)
+  const float* w;             // fp32 parameters (biases)
+  const __nv_bfloat16* wb;    // bf16 parameters (W3)
+  const float* T;             // targets [Bp][4] (kTrFwd)
+  float* H2;                  // [Bp][256] fp32 (kTrFwd)
+  float* dY;                  // [Bp][4] (kTrFwd)
+  float* lossp;               // [Bp] squared errors (kTrFwd)
+  float* dZ2f;                // [Bp][256] fp32 (kTrFwd)
+  __nv_bfloat16* dZ2R;        // R-layout (kTrFwd)
+  __nv_bfloat16* dZ2T;        // T-layout (kTrFwd)
+  const float* Z1;            // [Bp][256] (kTrBwd)
+  float* dZ1;                 // [Bp][256] (kTrBwd)
+  float* gW2p;                // [tiles][256][256] (kTrGw2)
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(192, 1)
+k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bbase, TrArgs a,
+               unsigned* err) {
+  extern __shared__ uint8_t mlp_smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(mlp_smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint8_t* sA = base;
+  uint8_t* sB = base + kMlpATile;
+  float* sW3 = reinterpret_cast<float*>(sB + kMlpBBytes);
+  float* sb2 = sW3 + 4 * kMlpH;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sb2 + kMlpH);
+  uint64_t* full = bars;
+  uint64_t* tfull = bars + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (MODE == kTrFwd) {
+    for (int i = threadIdx.x; i < 4 * kMlpH; i += blockDim.x)
+      sW3[i] = __bfloat162float(a.wb[kOffW3 + i]);
+    for (int i = threadIdx.x; i < kMlpH; i += blockDim.x) sb2[i] = a.w[kOffB2 + i];
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(full, 1);
+    mbar_init(tfull, 1);
+    fence_mbar_init();
+  }
+  if (warp == 5) {
+    tmem_alloc(tmem_slot, kMlpH);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // operand tiles of this CTA
+  const uint8_t* gA;
+  const uint8_t* gB;
+  if (MODE == kTrGw2) {
+    gA = Abase + static_cast<size_t>(blockIdx.y) * (2 * kMlpATile) +
+         static_cast<size_t>(blockIdx.x) * kMlpATile;
+    gB = Bbase + static_cast<size_t>(blockIdx.y) * kMlpBBytes;
+  } else {
+    gA = Abase + static_cast<size_t>(blockIdx.x) * kMlpATile;
+    gB = Bbase;
+  }
+  if (warp == 4) {
+    if (lane == 0) {
+      mbar_expect_tx(full, kMlpATile + kMlpBBytes);
+      bulk_g2s(sA, gA, kMlpATile, full);
+      bulk_g2s(sB, gB, kMlpBBytes, full);
+      mbar_wait(full, 0u, err, 31u);  // both copies landed before the CTA can exit
+    }
+  } else if (warp == 5) {
+    if (lane == 0 && mbar_wait(full, 0u, err, 32u)) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+      for (int kk = 0; kk < kMlpH / 16; ++kk)
+        umma_bf16(tmem, smem_desc(a0 + kk * 256, 128, 4096), smem_desc(b0 + kk * 256, 128, 4096),
+                  kMlpIdesc, kk > 0 ? 1u : 0u);
+      umma_commit(tfull);
+      mbar_wait(tfull, 0u, err, 33u);
+    }
+    __syncwarp();
+  } else {
+    // epilogue: thread = accumulator row (TMEM lane)
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull, 0u, err, 34u));
+    tc_fence_after();
+    const int r = threadIdx.x;  // 0..127
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    if (ok && MODE == kTrFwd) {
+      const int64_t b = static_cast<int64_t>(blockIdx.x) * kMlpM + r;
+      const bool live = b < a.B;
+      float y[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int c = 0; c < kMlpH / 32; ++c) {
+        float v[32];
+        tmem_ld32(lane_base + c * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = c * 32 + i;
+          const float h = gelu_f(v[i] + sb2[col]);
+          a.H2[b * kMlpH + col] = h;
+#pragma unroll
+          for (int o = 0; o < 4; ++o) y[o] = __fmaf_rn(sW3[o * kMlpH + col], h, y[o]);
+        }
+      }
+      float dy[4], l = 0.f;
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const float e = live ? (y[o] + a.w[kOffB3 + o]) - a.T[b * 4 + o] : 0.0f;
+        l += e * e;
+        dy[o] = 2.0f * e / (4.0f * static_cast<float>(a.B));
+        a.dY[b * 4 + o] = dy[o];
+      }
+      a.lossp[b] = l;
+      const int64_t tT = b / 256, bT = b % 256;  // T-layout tile and column of this sample
+      for (int c = 0; c < kMlpH / 32; ++c) {
+        float v[32];
+        tmem_ld32(lane_base + c * 32, v);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          uint32_t hb[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int col = c * 32 + g * 8 + e;
+            float dh = 0.f;
+#pragma unroll
+            for (int o = 0; o < 4; ++o) dh = __fmaf_rn(dy[o], sW3[o * kMlpH + col], dh);
+            const float dz = dh * gelu_grad_f(v[g * 8 + e] + sb2[col]);
+            a.dZ2f[b * kMlpH + col] = dz;
+            const __nv_bfloat16 q = __float2bfloat16_rn(dz);
+            hb[e] = __bfloat16_as_ushort(q);
+            a.dZ2T[tT * (kMlpH * 256) + mlp_packed_index(col, static_cast<int>(bT))] = q;
+          }
+          uint4 pk;
+          pk.x = hb[0] | (hb[1] << 16);
+          pk.y = hb[2] | (hb[3] << 16);
+          pk.z = hb[4] | (hb[5] << 16);
+          pk.w = hb[6] | (hb[7] << 16);
+          *reinterpret_cast<uint4*>(a.dZ2R + (b / kMlpM) * (kMlpM * kMlpH) +
+                                    mlp_packed_index(r, c * 32 + g * 8)) = pk;
+        }
+      }
+    } else if (ok && MODE == kTrBwd) {
+      const int64_t b = static_cast<int64_t>(blockIdx.x) * kMlpM + r;
+      for (int c = 0; c < kMlpH / 32; ++c) {
+        float v[32];
+        tmem_ld32(lane_base + c * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = c * 32 + i;
+          a.dZ1[b * kMlpH + col] = v[i] * gelu_grad_f(a.Z1[b * kMlpH + col]);
+        }
+      }
+    } else if (ok && MODE == kTrGw2) {
+      const int64_t n = static_cast<int64_t>(blockIdx.x) * kMlpM + r;
+      float* out = a.gW2p + static_cast<int64_t>(blockIdx.y) * kMlpH * kMlpH + n * kMlpH;
+      for (int c = 0; c < kMlpH / 32; ++c) {
+        float v[32];
+        tmem_ld32(lane_base + c * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) out[c * 32 + i] = v[i];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 5) tmem_dealloc(tmem, kMlpH);
+}
+
+// layer 1 of a training step: Z1 = X W1^T + b1 (fp32), H1 = gelu(Z1) as bf16
+// in both layouts; rows past B (padding) are zero
+__global__ void k_tr_l1(const float* __restrict__ X, int B, int Bp,
+                        const __nv_bfloat16* __restrict__ wb, const float* __restrict__ w,
+                        float* __restrict__ Z1, __nv_bfloat16* __restrict__ H1R,
+                        __nv_bfloat16* __restrict__ H1T) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= Bp) return;
+  float x[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) x[d] = b < B ? X[b * 8 + d] : 0.0f;
+  const int tR = b / kMlpM, rR = b % kMlpM, tT = b / 256, bT = b % 256;
+  for (int c = 0; c < kMlpH / 8; ++c) {
+    uint32_t hb[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int o = 8 * c + e;
+      float z = w[kOffB1 + o];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) z = __fmaf_rn(__bfloat162float(wb[kOffW1 + o * 8 + k]), x[k], z);
+      const float h = b < B ? gelu_f(z) : 0.0f;
+      Z1[static_cast<int64_t>(b) * kMlpH + o] = z;
+      const __nv_bfloat16 q = __float2bfloat16_rn(h);
+      hb[e] = __bfloat16_as_ushort(q);
+      H1T[static_cast<int64_t>(tT) * (kMlpH * 256) + mlp_packed_index(o, bT)] = q;
+    }
+    uint4 v;
+    v.x = hb[0] | (hb[1] << 16);
+    v.y = hb[2] | (hb[3] << 16);
+    v.z = hb[4] | (hb[5] << 16);
+    v.w = hb[6] | (hb[7] << 16);
+    *reinterpret_cast<uint4*>(H1R + static_cast<int64_t>(tR) * (kMlpM * kMlpH) +
+                              mlp_packed_index(rR, 8 * c)) = v;
+  }
+}
+
+// W2^T (bf16) as the B operand of dH1 = dZ2 W2: rows = input feature k, K = output o
+__global__ void k_mlp_pack_w2t(const __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ Wpk) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kMlpH * kMlpH) return;
+  const int o = idx / kMlpH, k = idx % kMlpH;
+  Wpk[mlp_packed_index(k, o)] = wb[kOffW2 + o * kMlpH + k];
+}
+
+int mlp_train_prepare() {
+  ABC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_train_tc<kTrFwd>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(kMlpSmem)));
+  ABC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_train_tc<kTrBwd>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(kMlpSmem)));
+  ABC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_train_tc<kTrGw2>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(kMlpSmem)));
+  return ABC_OK;
+}
+
+// scratch of one training step on B samples (padded to Bp, a multiple of 256)
+struct TrLayout {
+  size_t Z1, H2, dZ2f, dZ1, dY, lossp, gW2p, sk, H1R, H1T, dZ2R, dZ2T, W2pk, W2Tpk, err, total;
+};
+
+static TrLayout tr_layout(int B) {
+  const size_t Bp = static_cast<size_t>(ceil_div(std::max(B, 1), 256)) * 256;
+  const size_t BH = Bp * kMlpH;
+  TrLayout l{};
+  size_t o = 0;
+  auto take = [&](size_t& f, size_t bytes) {
+    f = o;
+    o += align256(bytes);
+  };
+  take(l.Z1, 4 * BH);
+  take(l.H2, 4 * BH);
+  take(l.dZ2f, 4 * BH);
+  take(l.dZ1, 4 * BH);
+  take(l.dY, 4 * 4 * Bp);
+  take(l.lossp, 4 * Bp);
+  take(l.gW2p, 4 * (Bp / 256) * kMlpH * kMlpH);
+  take(l.sk, 4 * static_cast<size_t>(kMaxSplits) * kMlpH * kMlpH);
+  take(l.H1R, 2 * BH);
+  take(l.H1T, 2 * BH);
+  take(l.dZ2R, 2 * BH);
+  take(l.dZ2T, 2 * BH);
+  take(l.W2pk, 2 * kMlpH * kMlpH);
+  take(l.W2Tpk, 2 * kMlpH * kMlpH);
+  take(l.err, 16);
+  l.total = o + 1024;
+  return l;
+}
+
+size_t mlp_train_scratch_bytes(int B) { return tr_layout(B).total; }
+
+// One forward + backward pass on X [B][8], T [B][4] (standardised targets).
+// The three 256-wide products run on tcgen05 with bf16 operands (weights,
+// H1 and dZ2 rounded to bf16) and fp32 accumulation; layers 1 and 3 and the
+// bias sums on CUDA cores in fp32.  Writes the gradients into
+// grad[kMlpParams] and the sum of squared errors into *loss_dev; a
+// tensor-core wait that timed out sets *err (nullable: the scratch's own).
+int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* grad,
+             float* loss_dev, void* scratch, size_t bytes, cudaStream_t st, unsigned* err) {
+  if (B <= 0) return ABC_E_INVAL;
+  const TrLayout l = tr_layout(B);
+  if (bytes < l.total) return ABC_E_SCRATCH;
+  char* c = static_cast<char*>(scratch);
+  const int Bp = static_cast<int>(ceil_div(B, 256) * 256);
+  float* Z1 = reinterpret_cast<float*>(c + l.Z1);
+  float* H2 = reinterpret_cast<float*>(c + l.H2);
+  float* dZ2f = reinterpret_cast<float*>(c + l.dZ2f);
+  float* dZ1 = reinterpret_cast<float*>(c + l.dZ1);
+  float* dY = reinterpret_cast<float*>(c + l.dY);
+  float* lossp = reinterpret_cast<float*>(c + l.lossp);
+  float* gW2p = reinterpret_cast<float*>(c + l.gW2p);
+  float* sk = reinterpret_cast<float*>(c + l.sk);
+  auto* H1R = reinterpret_cast<__nv_bfloat16*>(c + l.H1R);
+  auto* H1T = reinterpret_cast<__nv_bfloat16*>(c + l.H1T);
+  auto* dZ2R = reinterpret_cast<__nv_bfloat16*>(c + l.dZ2R);
+  auto* dZ2T = reinterpret_cast<__nv_bfloat16*>(c + l.dZ2T);
+  auto* W2pk = reinterpret_cast<__nv_bfloat16*>(c + l.W2pk);
+  auto* W2Tpk = reinterpret_cast<__nv_bfloat16*>(c + l.W2Tpk);
+  if (!err) {
+    err = reinterpret_cast<unsigned*>(c + l.err);
+    ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
+  }
+  const __nv_bfloat16* wb = s.wb;
+  int rc;
+  k_tr_l1<<<static_cast<unsigned>(Bp / 128), 128, 0, st>>>(X, B, Bp, wb, s.w, Z1, H1R, H1T);
+  ABC_LAUNCH_CHECK();
+  k_mlp_pack_w2<<<(kMlpH * kMlpH + 255) / 256, 256, 0, st>>>(wb, W2pk);
+  ABC_LAUNCH_CHECK();
+  k_mlp_pack_w2t<<<(kMlpH * kMlpH + 255) / 256, 256, 0, st>>>(wb, W2Tpk);
+  ABC_LAUNCH_CHECK();
+  TrArgs a{};
+  a.B = B;
+  a.w = s.w;
+  a.wb = wb;
+  a.T = T;
+  a.H2 = H2;
+  a.dY = dY;
+  a.lossp = lossp;
+  a.dZ2f = dZ2f;
+  a.dZ2R = dZ2R;
+  a.dZ2T = dZ2T;
+  a.Z1 = Z1;
+  a.dZ1 = dZ1;
+  a.gW2p = gW2p;
+  // forward through layers 2 and 3, loss, back through layer 3
+  k_mlp_train_tc<kTrFwd><<<static_cast<unsigned>(Bp / kMlpM), 192, kMlpSmem, st>>>(
+      reinterpret_cast<const uint8_t*>(H1R), reinterpret_cast<const uint8_t*>(W2pk), a, err);
+  ABC_LAUNCH_CHECK();
+  k_sum<<<1, 1024, 0, st>>>(lossp, Bp, loss_dev);
+  ABC_LAUNCH_CHECK();
+  // layer 3 gradients: gW3[o][k] = sum_b dY[b][o] H2[b][k] (M = 4, N = 256, K = Bp)
+  if ((rc = gemm<float>(4, kMlpH, Bp, dY, 1, 4, H2, kMlpH, 1, grad + kOffW3, kMlpH, nullptr, 0,
+                        nullptr, nullptr, st, sk)))
+    return rc;
+  k_colsum<<<4, 256, 0, st>>>(dY, Bp, 4, grad + kOffB3);
+  ABC_LAUNCH_CHECK();
+  k_colsum<<<kMlpH, 256, 0, st>>>(dZ2f, Bp, kMlpH, grad + kOffB2);
+  ABC_LAUNCH_CHECK();
+  // dZ1 = (dZ2 W2) gelu'(Z1)
+  k_mlp_train_tc<kTrBwd><<<static_cast<unsigned>(Bp / kMlpM), 192, kMlpSmem, st>>>(
+      reinterpret_cast<const uint8_t*>(dZ2R), reinterpret_cast<const uint8_t*>(W2Tpk), a, err);
+  ABC_LAUNCH_CHECK();
+  // gW2 = dZ2^T H1: one partial per 256-sample tile, summed in tile order
+  k_mlp_train_tc<kTrGw2><<<dim3(2, static_cast<unsigned>(Bp / 256)), 192, kMlpSmem, st>>>(
+      reinterpret_cast<const uint8_t*>(dZ2T), reinterpret_cast<const uint8_t*>(H1T), a, err);
+  ABC_LAUNCH_CHECK();
+  {
+    const int64_t n = static_cast<int64_t>(kMlpH) * kMlpH;
+    k_splitk_sum<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(gW2p, Bp / 256, n,
+                                                                        grad + kOffW2);
+    ABC_LAUNCH_CHECK();
+  }
+  // gW1 = dZ1^T X (M = 256, N = 8, K = B), gb1 = column sums of dZ1
+  if ((rc = gemm<float>(kMlpH, 8, B, dZ1, 1, kMlpH, X, 8, 1, grad + kOffW1, 8, nullptr, 0, nullptr,
+                        nullptr, st, sk)))
+    return rc;
+  k_colsum<<<kMlpH, 256, 0, st>>>(dZ1, Bp, kMlpH, grad + kOffB1);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+// the scratch's own error word of mlp_grad(B)
+unsigned* mlp_grad_err(void* scratch, int B) {
+  return reinterpret_cast<unsigned*>(static_cast<char*>(scratch) + tr_layout(B).err);
 }
 
 // ---- screening (delayed acceptance) ---------------------------------------------
@@ -844,7 +1104,7 @@ __global__ void k_step_advance(uint32_t* step_dev, uint32_t steps, const int* of
 int mlp_train(const MlpState& s, const float* RX, const float* RY, const long long* head,
               int64_t cap, const float* ystat, int B, int steps, uint32_t* step_dev, float lr,
               uint32_t k0, uint32_t k1, float* grad, float* X, float* T, float* loss_dev,
-              void* scratch, size_t bytes, cudaStream_t st, const int* off_dev) {
+              void* scratch, size_t bytes, cudaStream_t st, const int* off_dev, unsigned* err) {
   int rc;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const unsigned g = (kMlpParams + 255) / 256;
@@ -852,7 +1112,7 @@ int mlp_train(const MlpState& s, const float* RX, const float* RY, const long lo
     k_ring_batch<<<(B + 255) / 256, 256, 0, st>>>(RX, RY, head, cap, ystat, B,
                                                   static_cast<uint32_t>(k), k0, k1, X, T, step_dev);
     ABC_LAUNCH_CHECK();
-    if ((rc = mlp_grad(s, X, T, B, grad, loss_dev, scratch, bytes, st))) return rc;
+    if ((rc = mlp_grad(s, X, T, B, grad, loss_dev, scratch, bytes, st, err))) return rc;
     k_adam<<<g, 256, 0, st>>>(s.w, grad, s.m, s.v, lr, b1, b2, eps, 1.0f, 1.0f, step_dev,
                               static_cast<uint32_t>(k));
     ABC_LAUNCH_CHECK();

@@ -33,7 +33,9 @@ int mlp_init(const MlpState& s, uint32_t k0, uint32_t k1, cudaStream_t st);
 int mlp_refresh_bf16(const MlpState& s, cudaStream_t st);
 size_t mlp_train_scratch_bytes(int B);
 int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* grad, float* loss_dev,
-             void* scratch, size_t bytes, cudaStream_t st);
+             void* scratch, size_t bytes, cudaStream_t st, unsigned* err = nullptr);
+unsigned* mlp_grad_err(void* scratch, int B);
+int mlp_train_prepare();
 int mlp_adam(const MlpState& s, const float* grad, int64_t step, float lr, cudaStream_t st);
 size_t mlp_infer_scratch_bytes(int64_t n);
 int mlp_infer_prepare();
@@ -66,7 +68,8 @@ int ring_stats(const float* RX, const float* RY, const long long* head, int64_t 
 int mlp_train(const MlpState& s, const float* RX, const float* RY, const long long* head,
               int64_t cap, const float* ystat, int B, int steps, uint32_t* step_dev, float lr,
               uint32_t k0, uint32_t k1, float* grad, float* X, float* T, float* loss_dev,
-              void* scratch, size_t bytes, cudaStream_t st, const int* off_dev = nullptr);
+              void* scratch, size_t bytes, cudaStream_t st, const int* off_dev = nullptr,
+              unsigned* err = nullptr);
 int sur_gate(const uint32_t* t_dev, uint32_t t, int start, const uint32_t* step_dev, int* on,
              cudaStream_t st);
 int audit_count(const uint8_t* cflag, const double* cd, const int* Mc, const double* eps,

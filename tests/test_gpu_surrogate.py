@@ -3,8 +3,9 @@ the paper) on the GPU against the oracle.
 
 1. abc_screen equals the oracle's screen rule bit for bit (rho and the
    simulate / audit / screened-out decision), ragged sizes included.
-2. The MLP kernels: tensor-core inference, the CUDA-core gradient and Adam
-   against the fp64 oracle, each within a bound derived from its precision.
+2. The MLP kernels: tensor-core inference, the tensor-core gradient and
+   Adam against the fp64 oracle, each within a bound derived from its
+   precision.
 3. A screened generation of the context keeps only proposals the oracle
    would accept, bit-exact and in (batch, slot) order, and its counters add
    up; the toy model's closed-form posterior survives delayed acceptance
@@ -163,12 +164,46 @@ def test_mlp_forward_tc_vs_oracle(n):
     assert np.all(err <= bound), REPORT["mlp_forward_%d" % n]
 
 
+def _abs_backward(p, X, T):
+    """First-order magnitudes of the training pass in fp64: the backward
+    formulas with every factor replaced by its absolute value (|gelu'| <= 1.13,
+    |gelu''| <= 0.8).  Each gradient element's rounding error is a sum of
+    rounding errors of these products, so it is at most a small multiple of
+    the bf16 unit 2^-9 times these magnitudes."""
+    gelu = lambda z: 0.5 * z * (1 + np.tanh(0.7978845608028654 * (z + 0.044715 * z**3)))
+    def gelu_d(z):
+        t = np.tanh(0.7978845608028654 * (z + 0.044715 * z**3))
+        return 0.5 * (1 + t) + 0.5 * z * (1 - t * t) * 0.7978845608028654 * (1 + 3 * 0.044715 * z * z)
+    B = len(X)
+    A = {k: np.abs(v) for k, v in p.items()}
+    z1 = X @ p["W1"].T + p["b1"]
+    h1 = gelu(z1)
+    z2 = h1 @ p["W2"].T + p["b2"]
+    h2 = gelu(z2)
+    y = h2 @ p["W3"].T + p["b3"]
+    dY = np.abs(2 * (y - T) / (4 * B))
+    # |dz2| with the perturbation of gelu' through z2's own magnitude
+    mz2 = np.abs(h1) @ A["W2"].T + A["b2"]
+    dh2 = dY @ A["W3"]
+    dz2 = dh2 * (np.abs(gelu_d(z2)) + 0.8 * mz2)
+    dh1 = dz2 @ A["W2"]
+    dz1 = dh1 * (np.abs(gelu_d(z1)) + 0.8 * (np.abs(X) @ A["W1"].T + A["b1"]))
+    mh2 = np.abs(h2) + 1.13 * mz2
+    dYm = dY + np.abs(mh2 @ A["W3"].T) / (4 * B)
+    return {"W3": dYm.T @ mh2, "b3": dYm.sum(0), "W2": dz2.T @ np.abs(h1), "b2": dz2.sum(0),
+            "W1": dz1.T @ np.abs(X), "b1": dz1.sum(0)}
+
+
 @pytest.mark.parametrize("Bn", [37, 300, 2048])
 def test_mlp_gradient_vs_oracle(Bn):
-    """Training pass on CUDA cores: bf16 weights, fp32 activations and sums.
-    Every gradient is a sum over the batch of products the fp32 kernels form
-    with relative error ~(K + B) 2^-24; bound per array: 2^-24 (B + 600)
-    times the sum of the magnitudes, taken as (B + 600) 2^-24 * max|g| * 64."""
+    """Training pass on tensor cores: the layer-2 forward, input-gradient and
+    weight-gradient products take bf16 operands (weights, hidden activations
+    H1 and hidden gradients dZ2 rounded to bf16, unit u = 2^-9) with fp32
+    accumulation; layers 1 and 3 and the bias sums run in fp32.  Against the
+    fp64 oracle (the same bf16 weights as fp64 values): per array the
+    max-norm error is at most 2e-2 of the gradient's max-norm (the bf16
+    bar), and every element is within 16 u times its first-order magnitude
+    (_abs_backward) plus an fp32 floor."""
     m = G.abc_mlp_create(9)
     try:
         G.abc_mlp_set_params(m, _random_params(6))
@@ -186,16 +221,19 @@ def test_mlp_gradient_vs_oracle(Bn):
         loss = float(host(sse)[0]) / (4 * Bn)
     finally:
         G.abc_mlp_free(m)
-    oloss, og = O.mlp_backward(p, X.astype(np.float64), T.astype(np.float64))
-    assert abs(loss - oloss) <= 1e-5 * oloss
+    Xd, Td = X.astype(np.float64), T.astype(np.float64)
+    oloss, og = O.mlp_backward(p, Xd, Td)
+    mag = _abs_backward(p, Xd, Td)
+    assert abs(loss - oloss) <= 2.0**-6 * oloss
     rep = {}
     for k in O.MLP_ORDER:
+        err = np.abs(got[k] - og[k])
         scale = np.abs(og[k]).max()
-        err = np.abs(got[k] - og[k]).max()
-        tol = (Bn + 600) * 2.0**-24 * 64 * scale
-        rep[k] = float(err / tol)
-        assert err <= tol, (k, err, tol)
-    REPORT["mlp_grad_%d_err_over_tol" % Bn] = rep
+        tol = 16 * 2.0**-9 * mag[k] + 2.0**-20 * scale
+        rep[k] = dict(rel_maxnorm=float(err.max() / scale), max_err_over_tol=float((err / tol).max()))
+        assert err.max() <= 2e-2 * scale, (k, rep[k])
+        assert np.all(err <= tol), (k, rep[k])
+    REPORT["mlp_grad_%d" % Bn] = rep
 
 
 def test_mlp_adam_vs_oracle():
