@@ -621,6 +621,8 @@ def run_eps_final(args):
         sc.surrogate_lr = 1e-3
         sc.surrogate_rho_min, sc.audit_frac = args.surrogate_rho_min, 0.01
         sc.eps_stop = _f32_at_least(ef)
+        # screened-out proposals use up batches: a larger per-stage budget
+        sc.max_batches = max(c.max_batches, 512)
         if args.surrogate_ring_mult > 0:
             sc.surrogate_ring = args.surrogate_ring_mult * c.n_particles
         return sc

@@ -605,6 +605,7 @@ int ctx_alloc(abc_ctx* c) {
     ABC_ALLOC(c->simulated, 1);
     ABC_ALLOC(c->inf_err, 1);
     c->sscratch_bytes = std::max({mlp_train_scratch_bytes(B), mlp_infer_scratch_bytes(c->M),
+                                  ring_stats_scratch_bytes(),
                                   screen_scratch_bytes(c->M),
                                   ring_scratch_bytes(std::max(c->M, c->N))});
     char* ss = nullptr;

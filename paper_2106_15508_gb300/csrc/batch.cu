@@ -151,7 +151,8 @@ int screened_batch(const SurView& s, const SimParams& p, const int32_t* obs, con
 
 int sur_train(const SurView& s, const SimParams& p, const int* off_dev, cudaStream_t st) {
   if (s.steps <= 0) return ABC_OK;
-  int rc = ring_stats(s.RX, s.RY, s.ring_head, s.ring_cap, s.ystat, st);
+  // the statistics' partial sums use the scratch before training reuses it
+  int rc = ring_stats(s.RX, s.RY, s.ring_head, s.ring_cap, s.ystat, s.sscratch, st);
   if (rc) return rc;
   return mlp_train(s.mlp, s.RX, s.RY, s.ring_head, s.ring_cap, s.ystat, s.batch, s.steps,
                    s.train_step, s.lr, p.k0, p.k1, s.grad, s.trX, s.trT, s.loss, s.sscratch,

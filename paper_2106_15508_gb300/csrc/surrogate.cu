@@ -1041,39 +1041,69 @@ int ring_append(const uint8_t* invalid, int64_t n, const float* u, const double*
 
 size_t ring_scratch_bytes(int64_t n) { return 3 * align256(4 * ceil_div(std::max<int64_t>(n, 1), kCTile)); }
 
-// mean and standard deviation over the filled ring (fp64), one block per
-// statistic: blocks 0..3 the outputs (ystat[o], ystat[4 + o]), blocks 4..11
-// the inputs (ystat[8 + d], ystat[16 + d]; standard deviations floored at
-// 1e-6 so that a collapsed population keeps finite standardised inputs)
-__global__ void k_ring_stats(const float* __restrict__ RX, const float* __restrict__ RY,
-                             const long long* __restrict__ head, int64_t cap,
-                             float* __restrict__ ystat) {
+// mean and standard deviation over the filled ring (fp64): each thread sums
+// whole samples (4 outputs, 8 inputs), the blocks write partial sums, and one
+// warp adds them in block order (deterministic).  Outputs: ystat[o],
+// ystat[4 + o]; inputs: ystat[8 + d], ystat[16 + d], standard deviations
+// floored at 1e-6 so that a collapsed population keeps finite standardised
+// inputs.
+constexpr int kStatBlocks = 256;
+
+__global__ void __launch_bounds__(256)
+k_ring_stats_part(const float* __restrict__ RX, const float* __restrict__ RY,
+                  const long long* __restrict__ head, int64_t cap, double* __restrict__ part) {
   __shared__ double sm[32];
   const int64_t m = *head < cap ? *head : cap;
-  const bool out = blockIdx.x < 4;
-  const int o = out ? blockIdx.x : blockIdx.x - 4;
-  const float* src = out ? RY + o : RX + o;
-  const int64_t stride = out ? 4 : 8;
-  double s1 = 0.0, s2 = 0.0;
-  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-    const double y = src[i * stride];
-    s1 += y;
-    s2 += y * y;
+  double s1[12], s2[12];
+#pragma unroll
+  for (int j = 0; j < 12; ++j) s1[j] = s2[j] = 0.0;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < m;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float4 y = *reinterpret_cast<const float4*>(RY + i * 4);
+    const float4 x0 = *reinterpret_cast<const float4*>(RX + i * 8);
+    const float4 x1 = *reinterpret_cast<const float4*>(RX + i * 8 + 4);
+    const float v[12] = {y.x, y.y, y.z, y.w, x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+      const double d = v[j];
+      s1[j] += d;
+      s2[j] += d * d;
+    }
   }
-  s1 = block_sum<double>(s1, sm);
-  s2 = block_sum<double>(s2, sm);
-  if (threadIdx.x == 0) {
-    const double mean = m > 0 ? s1 / static_cast<double>(m) : 0.0;
-    const double var = m > 1 ? s2 / static_cast<double>(m) - mean * mean : 1.0;
-    if (out) {
-      ystat[o] = static_cast<float>(mean);
-      ystat[4 + o] = static_cast<float>(var > 1e-12 ? sqrt(var) : 1.0);
-    } else {
-      ystat[8 + o] = static_cast<float>(mean);
-      ystat[16 + o] = static_cast<float>(fmax(var > 0.0 ? sqrt(var) : 1.0, 1e-6));
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    const double a = block_sum<double>(s1[j], sm);
+    const double b = block_sum<double>(s2[j], sm);
+    if (threadIdx.x == 0) {
+      part[blockIdx.x * 24 + j] = a;
+      part[blockIdx.x * 24 + 12 + j] = b;
     }
   }
 }
+
+__global__ void k_ring_stats_final(const double* __restrict__ part, int nblk,
+                                   const long long* __restrict__ head, int64_t cap,
+                                   float* __restrict__ ystat) {
+  const int j = threadIdx.x;
+  if (j >= 12) return;
+  const int64_t m = *head < cap ? *head : cap;
+  double s1 = 0.0, s2 = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    s1 += part[b * 24 + j];
+    s2 += part[b * 24 + 12 + j];
+  }
+  const double mean = m > 0 ? s1 / static_cast<double>(m) : 0.0;
+  const double var = m > 1 ? s2 / static_cast<double>(m) - mean * mean : 1.0;
+  if (j < 4) {
+    ystat[j] = static_cast<float>(mean);
+    ystat[4 + j] = static_cast<float>(var > 1e-12 ? sqrt(var) : 1.0);
+  } else {
+    ystat[8 + (j - 4)] = static_cast<float>(mean);
+    ystat[16 + (j - 4)] = static_cast<float>(fmax(var > 0.0 ? sqrt(var) : 1.0, 1e-6));
+  }
+}
+
+size_t ring_stats_scratch_bytes() { return align256(sizeof(double) * 24 * kStatBlocks); }
 
 // a minibatch of B samples drawn uniformly from the filled ring (TRAIN stream)
 __global__ void k_ring_batch(const float* __restrict__ RX, const float* __restrict__ RY,
@@ -1194,8 +1224,11 @@ int stats_init(float* ystat, cudaStream_t st) {
 }
 
 int ring_stats(const float* RX, const float* RY, const long long* head, int64_t cap, float* ystat,
-               cudaStream_t st) {
-  k_ring_stats<<<12, 1024, 0, st>>>(RX, RY, head, cap, ystat);
+               void* scratch, cudaStream_t st) {
+  double* part = static_cast<double*>(scratch);
+  k_ring_stats_part<<<kStatBlocks, 256, 0, st>>>(RX, RY, head, cap, part);
+  ABC_LAUNCH_CHECK();
+  k_ring_stats_final<<<1, 32, 0, st>>>(part, kStatBlocks, head, cap, ystat);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

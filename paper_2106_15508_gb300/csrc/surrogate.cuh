@@ -64,7 +64,8 @@ int ring_append(const uint8_t* invalid, int64_t n, const float* u, const double*
 // ystat before any training: means 0, standard deviations 1
 int stats_init(float* ystat, cudaStream_t st);
 int ring_stats(const float* RX, const float* RY, const long long* head, int64_t cap, float* ystat,
-               cudaStream_t st);
+               void* scratch, cudaStream_t st);
+size_t ring_stats_scratch_bytes();
 int mlp_train(const MlpState& s, const float* RX, const float* RY, const long long* head,
               int64_t cap, const float* ystat, int B, int steps, uint32_t* step_dev, float lr,
               uint32_t k0, uint32_t k1, float* grad, float* X, float* T, float* loss_dev,
