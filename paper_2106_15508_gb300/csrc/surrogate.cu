@@ -29,15 +29,27 @@
 namespace abc {
 
 // ---- GELU (tanh form, Hendrycks & Gimpel) -------------------------------
+// tanh by the hardware approximation (tanh.approx.f32, absolute error about
+// 2^-11): the surrogate works at bf16 precision, and this keeps its
+// activations cheap.  Beyond |x| = 5 the tanh form is within 1e-6 of its
+// limits (x and 1 for x > 0, 0 for x < 0), which are used there.
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float gelu_f(float x) {
+  if (!(fabsf(x) < 5.0f)) return x > 0.0f ? x : 0.0f;
   const float c = 0.7978845608028654f;
-  const float t = tanhf(c * (x + 0.044715f * x * x * x));
+  const float t = tanh_fast(c * (x + 0.044715f * x * x * x));
   return 0.5f * x * (1.0f + t);
 }
 
 __device__ __forceinline__ float gelu_grad_f(float x) {
+  if (!(fabsf(x) < 5.0f)) return x > 0.0f ? 1.0f : 0.0f;
   const float c = 0.7978845608028654f;
-  const float t = tanhf(c * (x + 0.044715f * x * x * x));
+  const float t = tanh_fast(c * (x + 0.044715f * x * x * x));
   return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * c * (1.0f + 3.0f * 0.044715f * x * x);
 }
 
@@ -250,7 +262,13 @@ int mlp_refresh_bf16(const MlpState& s, cudaStream_t st) {
 constexpr int kMlpM = 128;                                  // samples per CTA
 constexpr uint32_t kMlpATile = kMlpM * kMlpH * 2;           // 64 KB: h1 tile
 constexpr uint32_t kMlpBBytes = kMlpH * kMlpH * 2;          // 128 KB: W2
-constexpr size_t kMlpSmem = 1024 + kMlpATile + kMlpBBytes + (4 * kMlpH + kMlpH) * 4 + 256;
+// tensor-core MLP kernels: 16 epilogue warps (warp w reads TMEM lanes
+// 32 (w % 4) .. + 31 and columns 64 (w / 4) .. + 63), one bulk-copy warp,
+// one MMA warp
+constexpr int kMlpEpiWarps = 16;
+constexpr int kMlpThreads = 32 * (kMlpEpiWarps + 2);
+constexpr size_t kMlpSmem = 1024 + kMlpATile + kMlpBBytes + (4 * kMlpH + kMlpH) * 4 +
+                            4 * kMlpM * 4 * 4 + 256;
 constexpr uint32_t kMlpIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
                                (static_cast<uint32_t>(kMlpH >> 3) << 17) |
                                (static_cast<uint32_t>(kMlpM >> 4) << 24);
@@ -304,8 +322,11 @@ __global__ void k_mlp_pack_w2(const __nv_bfloat16* __restrict__ wb, __nv_bfloat1
   W2pk[mlp_packed_index(o, k)] = wb[kOffW2 + o * kMlpH + k];
 }
 
+// epilogue barrier of the 16 epilogue warps (named barrier 1)
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
+
 // Y[j][0..3] = W3 gelu(W2 h1_j + b2) + b3 for 128 samples per CTA
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kMlpThreads, 1)
 k_mlp_tc(const uint8_t* __restrict__ Hpk, const uint8_t* __restrict__ W2pk,
          const float* __restrict__ w, const __nv_bfloat16* __restrict__ wb, int64_t n,
          float* __restrict__ Y, unsigned* err) {
@@ -316,7 +337,8 @@ k_mlp_tc(const uint8_t* __restrict__ Hpk, const uint8_t* __restrict__ W2pk,
   uint8_t* sB = base + kMlpATile;
   float* sW3 = reinterpret_cast<float*>(sB + kMlpBBytes);
   float* sb2 = sW3 + 4 * kMlpH;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sb2 + kMlpH);
+  float* sY = sb2 + kMlpH;  // [4 column groups][128 rows][4] partial outputs
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sY + 4 * kMlpM * 4);
   uint64_t* full = bars;
   uint64_t* tfull = bars + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
@@ -328,7 +350,7 @@ k_mlp_tc(const uint8_t* __restrict__ Hpk, const uint8_t* __restrict__ W2pk,
     mbar_init(tfull, 1);
     fence_mbar_init();
   }
-  if (warp == 5) {
+  if (warp == kMlpEpiWarps + 1) {
     tmem_alloc(tmem_slot, kMlpH);
     tmem_relinquish();
   }
@@ -336,14 +358,14 @@ k_mlp_tc(const uint8_t* __restrict__ Hpk, const uint8_t* __restrict__ W2pk,
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  if (warp == 4) {
+  if (warp == kMlpEpiWarps) {
     if (lane == 0) {
       mbar_expect_tx(full, kMlpATile + kMlpBBytes);
       bulk_g2s(sA, Hpk + static_cast<size_t>(blockIdx.x) * kMlpATile, kMlpATile, full);
       bulk_g2s(sB, W2pk, kMlpBBytes, full);
       mbar_wait(full, 0u, err, 21u);  // both copies landed before the CTA can exit
     }
-  } else if (warp == 5) {
+  } else if (warp == kMlpEpiWarps + 1) {
     if (lane == 0 && mbar_wait(full, 0u, err, 22u)) {
       tc_fence_after();
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
@@ -359,12 +381,14 @@ k_mlp_tc(const uint8_t* __restrict__ Hpk, const uint8_t* __restrict__ W2pk,
     // tcgen05.ld is warp-collective: the whole warp reads or none of it
     const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull, 0u, err, 24u));
     tc_fence_after();
-    const int64_t j = static_cast<int64_t>(blockIdx.x) * kMlpM + threadIdx.x;
+    const int q = warp & 3, g = warp >> 2;
+    const int r = q * 32 + lane;
     float y[4] = {0.f, 0.f, 0.f, 0.f};
     if (ok) {
-      for (int c = 0; c < kMlpH / 32; ++c) {
+      for (int cc = 0; cc < 2; ++cc) {
+        const int c = 2 * g + cc;
         float v[32];
-        tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c * 32, v);
+        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + c * 32, v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int col = c * 32 + i;
@@ -374,15 +398,23 @@ k_mlp_tc(const uint8_t* __restrict__ Hpk, const uint8_t* __restrict__ W2pk,
         }
       }
     }
-    if (j < n) {
 #pragma unroll
-      for (int o = 0; o < 4; ++o) Y[j * 4 + o] = y[o] + w[kOffB3 + o];
+    for (int o = 0; o < 4; ++o) sY[(g * kMlpM + r) * 4 + o] = y[o];
+    epi_sync();
+    const int64_t j = static_cast<int64_t>(blockIdx.x) * kMlpM + r;
+    if (g == 0 && j < n) {
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        float t = sY[r * 4 + o];  // column groups added in order
+        for (int gg = 1; gg < 4; ++gg) t += sY[(gg * kMlpM + r) * 4 + o];
+        Y[j * 4 + o] = t + w[kOffB3 + o];
+      }
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 5) tmem_dealloc(tmem, kMlpH);
+  if (warp == kMlpEpiWarps + 1) tmem_dealloc(tmem, kMlpH);
 }
 
 size_t mlp_infer_scratch_bytes(int64_t n) {
@@ -422,7 +454,7 @@ int mlp_infer(const MlpState& s, const float* u, int64_t n, float* Y, void* scra
   k_mlp_l1_pack<<<static_cast<unsigned>(ceil_div(npad, 128)), 128, 0, st>>>(u, n, npad, s.wb, s.w,
                                                                            Hpk, xstat);
   ABC_LAUNCH_CHECK();
-  k_mlp_tc<<<static_cast<unsigned>(npad / kMlpM), 192, kMlpSmem, st>>>(
+  k_mlp_tc<<<static_cast<unsigned>(npad / kMlpM), kMlpThreads, kMlpSmem, st>>>(
       reinterpret_cast<const uint8_t*>(Hpk), reinterpret_cast<const uint8_t*>(W2pk), s.w, s.wb, n,
       Y, err);
   ABC_LAUNCH_CHECK();
@@ -467,7 +499,7 @@ struct TrArgs {
 };
 
 template <int MODE>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kMlpThreads, 1)
 k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bbase, TrArgs a,
                unsigned* err) {
   extern __shared__ uint8_t mlp_smem_raw[];
@@ -477,7 +509,8 @@ k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bb
   uint8_t* sB = base + kMlpATile;
   float* sW3 = reinterpret_cast<float*>(sB + kMlpBBytes);
   float* sb2 = sW3 + 4 * kMlpH;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sb2 + kMlpH);
+  float* sY = sb2 + kMlpH;  // [4 column groups][128 rows][4] partial outputs
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sY + 4 * kMlpM * 4);
   uint64_t* full = bars;
   uint64_t* tfull = bars + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
@@ -492,7 +525,7 @@ k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bb
     mbar_init(tfull, 1);
     fence_mbar_init();
   }
-  if (warp == 5) {
+  if (warp == kMlpEpiWarps + 1) {
     tmem_alloc(tmem_slot, kMlpH);
     tmem_relinquish();
   }
@@ -511,14 +544,14 @@ k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bb
     gA = Abase + static_cast<size_t>(blockIdx.x) * kMlpATile;
     gB = Bbase;
   }
-  if (warp == 4) {
+  if (warp == kMlpEpiWarps) {
     if (lane == 0) {
       mbar_expect_tx(full, kMlpATile + kMlpBBytes);
       bulk_g2s(sA, gA, kMlpATile, full);
       bulk_g2s(sB, gB, kMlpBBytes, full);
       mbar_wait(full, 0u, err, 31u);  // both copies landed before the CTA can exit
     }
-  } else if (warp == 5) {
+  } else if (warp == kMlpEpiWarps + 1) {
     if (lane == 0 && mbar_wait(full, 0u, err, 32u)) {
       tc_fence_after();
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
@@ -531,67 +564,82 @@ k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bb
     }
     __syncwarp();
   } else {
-    // epilogue: thread = accumulator row (TMEM lane)
+    // epilogue: warp w takes accumulator rows 32 (w % 4) .. + 31 (its TMEM
+    // lanes) and columns 64 (w / 4) .. + 63
     const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull, 0u, err, 34u));
     tc_fence_after();
-    const int r = threadIdx.x;  // 0..127
-    const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    if (ok && MODE == kTrFwd) {
+    const int q = warp & 3, g = warp >> 2;
+    const int r = q * 32 + lane;  // 0..127
+    const uint32_t lane_base = tmem + (static_cast<uint32_t>(q * 32) << 16);
+    if (MODE == kTrFwd) {
       const int64_t b = static_cast<int64_t>(blockIdx.x) * kMlpM + r;
       const bool live = b < a.B;
       float y[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int c = 0; c < kMlpH / 32; ++c) {
-        float v[32];
-        tmem_ld32(lane_base + c * 32, v);
+      if (ok) {
+        for (int cc = 0; cc < 2; ++cc) {
+          const int c = 2 * g + cc;
+          float v[32];
+          tmem_ld32(lane_base + c * 32, v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int col = c * 32 + i;
-          const float h = gelu_f(v[i] + sb2[col]);
-          a.H2[b * kMlpH + col] = h;
+          for (int i = 0; i < 32; ++i) {
+            const int col = c * 32 + i;
+            const float h = gelu_f(v[i] + sb2[col]);
+            a.H2[b * kMlpH + col] = h;
 #pragma unroll
-          for (int o = 0; o < 4; ++o) y[o] = __fmaf_rn(sW3[o * kMlpH + col], h, y[o]);
+            for (int o = 0; o < 4; ++o) y[o] = __fmaf_rn(sW3[o * kMlpH + col], h, y[o]);
+          }
         }
       }
+#pragma unroll
+      for (int o = 0; o < 4; ++o) sY[(g * kMlpM + r) * 4 + o] = y[o];
+      epi_sync();
+      // the row's outputs (column groups added in order), loss and dY
       float dy[4], l = 0.f;
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
-        const float e = live ? (y[o] + a.w[kOffB3 + o]) - a.T[b * 4 + o] : 0.0f;
+        float t = sY[r * 4 + o];
+        for (int gg = 1; gg < 4; ++gg) t += sY[(gg * kMlpM + r) * 4 + o];
+        const float e = live ? (t + a.w[kOffB3 + o]) - a.T[b * 4 + o] : 0.0f;
         l += e * e;
         dy[o] = 2.0f * e / (4.0f * static_cast<float>(a.B));
-        a.dY[b * 4 + o] = dy[o];
+        if (g == 0) a.dY[b * 4 + o] = dy[o];
       }
-      a.lossp[b] = l;
+      if (g == 0) a.lossp[b] = l;
       const int64_t tT = b / 256, bT = b % 256;  // T-layout tile and column of this sample
-      for (int c = 0; c < kMlpH / 32; ++c) {
-        float v[32];
-        tmem_ld32(lane_base + c * 32, v);
+      if (ok) {
+        for (int cc = 0; cc < 2; ++cc) {
+          const int c = 2 * g + cc;
+          float v[32];
+          tmem_ld32(lane_base + c * 32, v);
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          uint32_t hb[8];
+          for (int gr = 0; gr < 4; ++gr) {
+            uint32_t hb[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int col = c * 32 + g * 8 + e;
-            float dh = 0.f;
+            for (int e = 0; e < 8; ++e) {
+              const int col = c * 32 + gr * 8 + e;
+              float dh = 0.f;
 #pragma unroll
-            for (int o = 0; o < 4; ++o) dh = __fmaf_rn(dy[o], sW3[o * kMlpH + col], dh);
-            const float dz = dh * gelu_grad_f(v[g * 8 + e] + sb2[col]);
-            a.dZ2f[b * kMlpH + col] = dz;
-            const __nv_bfloat16 q = __float2bfloat16_rn(dz);
-            hb[e] = __bfloat16_as_ushort(q);
-            a.dZ2T[tT * (kMlpH * 256) + mlp_packed_index(col, static_cast<int>(bT))] = q;
+              for (int o = 0; o < 4; ++o) dh = __fmaf_rn(dy[o], sW3[o * kMlpH + col], dh);
+              const float dz = dh * gelu_grad_f(v[gr * 8 + e] + sb2[col]);
+              a.dZ2f[b * kMlpH + col] = dz;
+              const __nv_bfloat16 qz = __float2bfloat16_rn(dz);
+              hb[e] = __bfloat16_as_ushort(qz);
+              a.dZ2T[tT * (kMlpH * 256) + mlp_packed_index(col, static_cast<int>(bT))] = qz;
+            }
+            uint4 pk;
+            pk.x = hb[0] | (hb[1] << 16);
+            pk.y = hb[2] | (hb[3] << 16);
+            pk.z = hb[4] | (hb[5] << 16);
+            pk.w = hb[6] | (hb[7] << 16);
+            *reinterpret_cast<uint4*>(a.dZ2R + (b / kMlpM) * (kMlpM * kMlpH) +
+                                      mlp_packed_index(r, c * 32 + gr * 8)) = pk;
           }
-          uint4 pk;
-          pk.x = hb[0] | (hb[1] << 16);
-          pk.y = hb[2] | (hb[3] << 16);
-          pk.z = hb[4] | (hb[5] << 16);
-          pk.w = hb[6] | (hb[7] << 16);
-          *reinterpret_cast<uint4*>(a.dZ2R + (b / kMlpM) * (kMlpM * kMlpH) +
-                                    mlp_packed_index(r, c * 32 + g * 8)) = pk;
         }
       }
     } else if (ok && MODE == kTrBwd) {
       const int64_t b = static_cast<int64_t>(blockIdx.x) * kMlpM + r;
-      for (int c = 0; c < kMlpH / 32; ++c) {
+      for (int cc = 0; cc < 2; ++cc) {
+        const int c = 2 * g + cc;
         float v[32];
         tmem_ld32(lane_base + c * 32, v);
 #pragma unroll
@@ -603,7 +651,8 @@ k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bb
     } else if (ok && MODE == kTrGw2) {
       const int64_t n = static_cast<int64_t>(blockIdx.x) * kMlpM + r;
       float* out = a.gW2p + static_cast<int64_t>(blockIdx.y) * kMlpH * kMlpH + n * kMlpH;
-      for (int c = 0; c < kMlpH / 32; ++c) {
+      for (int cc = 0; cc < 2; ++cc) {
+        const int c = 2 * g + cc;
         float v[32];
         tmem_ld32(lane_base + c * 32, v);
 #pragma unroll
@@ -614,7 +663,7 @@ k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bb
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 5) tmem_dealloc(tmem, kMlpH);
+  if (warp == kMlpEpiWarps + 1) tmem_dealloc(tmem, kMlpH);
 }
 
 // layer 1 of a training step: Z1 = X W1^T + b1 (fp32), H1 = gelu(Z1) as bf16
@@ -763,7 +812,7 @@ int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* gr
   a.dZ1 = dZ1;
   a.gW2p = gW2p;
   // forward through layers 2 and 3, loss, back through layer 3
-  k_mlp_train_tc<kTrFwd><<<static_cast<unsigned>(Bp / kMlpM), 192, kMlpSmem, st>>>(
+  k_mlp_train_tc<kTrFwd><<<static_cast<unsigned>(Bp / kMlpM), kMlpThreads, kMlpSmem, st>>>(
       reinterpret_cast<const uint8_t*>(H1R), reinterpret_cast<const uint8_t*>(W2pk), a, err);
   ABC_LAUNCH_CHECK();
   k_sum<<<1, 1024, 0, st>>>(lossp, Bp, loss_dev);
@@ -777,11 +826,12 @@ int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* gr
   k_colsum<<<kMlpH, 256, 0, st>>>(dZ2f, Bp, kMlpH, grad + kOffB2);
   ABC_LAUNCH_CHECK();
   // dZ1 = (dZ2 W2) gelu'(Z1)
-  k_mlp_train_tc<kTrBwd><<<static_cast<unsigned>(Bp / kMlpM), 192, kMlpSmem, st>>>(
+  k_mlp_train_tc<kTrBwd><<<static_cast<unsigned>(Bp / kMlpM), kMlpThreads, kMlpSmem, st>>>(
       reinterpret_cast<const uint8_t*>(dZ2R), reinterpret_cast<const uint8_t*>(W2Tpk), a, err);
   ABC_LAUNCH_CHECK();
   // gW2 = dZ2^T H1: one partial per 256-sample tile, summed in tile order
-  k_mlp_train_tc<kTrGw2><<<dim3(2, static_cast<unsigned>(Bp / 256)), 192, kMlpSmem, st>>>(
+  k_mlp_train_tc<kTrGw2><<<dim3(2, static_cast<unsigned>(Bp / 256)), kMlpThreads, kMlpSmem,
+                          st>>>(
       reinterpret_cast<const uint8_t*>(dZ2T), reinterpret_cast<const uint8_t*>(H1T), a, err);
   ABC_LAUNCH_CHECK();
   {
