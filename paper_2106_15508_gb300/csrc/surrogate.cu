@@ -9,9 +9,9 @@
 // log1p D_T]; the per-output mean and standard deviation live beside the
 // parameters.
 //
-// Training (CUDA cores): a tiled GEMM with arbitrary operand strides and fused
-// epilogues (bias + GELU on the forward layer, GELU' on the backward layer),
-// small kernels for the 8-wide and 4-wide layers, Adam in fp32.
+// Training: the three 256-wide products of a step on tcgen05 (bf16 operands,
+// fp32 accumulation) with fused epilogues, layers 1 and 3 and the gradient
+// reductions on CUDA cores, Adam in fp32.
 // Inference: layer 1 on CUDA cores writes the hidden layer as bf16 tiles in
 // the tensor-core operand layout; layer 2 runs on tcgen05 (M = 128, N = 256,
 // K = 256) with bias + GELU + layer 3 fused into the epilogue (one thread per
@@ -76,81 +76,6 @@ __global__ void k_mlp_to_bf16(const float* __restrict__ w, __nv_bfloat16* __rest
   if (i < kMlpParams) wb[i] = __float2bfloat16_rn(w[i]);
 }
 
-// ---- generic GEMM: C(m,n) = sum_k A(m,k) B(k,n), fp32 accumulate ---------
-// A(m,k) = A[m*sam + k*sak] (fp32); B(k,n) = B[k*sbk + n*sbn] (bf16 or fp32)
-// epilogue 0: C = acc (+ bias[n]); 1: Z = acc + bias[n], C2 = gelu(Z) too;
-//          2: C = acc * gelu'(aux(m,n))   (aux row-major with ldc)
-constexpr int kGBM = 64, kGBN = 64, kGBK = 16;
-
-template <typename TB>
-__device__ __forceinline__ float ldf(const TB* p);
-template <>
-__device__ __forceinline__ float ldf<float>(const float* p) { return *p; }
-template <>
-__device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16* p) {
-  return __bfloat162float(*p);
-}
-
-template <typename TB>
-__global__ void __launch_bounds__(256)
-k_gemm(int M, int N, int K, const float* __restrict__ A, int64_t sam, int64_t sak,
-       const TB* __restrict__ B, int64_t sbk, int64_t sbn, float* __restrict__ C, int64_t ldc,
-       const float* __restrict__ bias, int epi, const float* __restrict__ aux,
-       float* __restrict__ C2) {
-  __shared__ float As[kGBK][kGBM + 4];
-  __shared__ float Bs[kGBK][kGBN + 4];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int m0 = blockIdx.y * kGBM, n0 = blockIdx.x * kGBN;
-  // split-K: slice z of gridDim.z covers K [kb, ke) and writes its partial
-  // product to C + z * M * ldc (summed by k_splitk_sum)
-  const int kper = (((K + gridDim.z - 1) / gridDim.z) + kGBK - 1) / kGBK * kGBK;
-  const int kb = blockIdx.z * kper;
-  const int ke = K < kb + kper ? K : kb + kper;
-  C += static_cast<int64_t>(blockIdx.z) * M * ldc;
-  float acc[4][4] = {};
-  for (int k0 = kb; k0 < ke; k0 += kGBK) {
-    for (int e = threadIdx.x; e < kGBK * kGBM; e += 256) {
-      const int kk = e / kGBM, mm = e % kGBM;
-      const int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < M && k < ke) ? A[m * sam + k * sak] : 0.0f;
-    }
-    for (int e = threadIdx.x; e < kGBK * kGBN; e += 256) {
-      const int kk = e / kGBN, nn = e % kGBN;
-      const int n = n0 + nn, k = k0 + kk;
-      Bs[kk][nn] = (n < N && k < ke) ? ldf<TB>(B + k * sbk + n * sbn) : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kGBK; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = __fmaf_rn(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int m = m0 + ty * 4 + i;
-    if (m >= M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n = n0 + tx * 4 + j;
-      if (n >= N) continue;
-      float v = acc[i][j];
-      if (bias) v += bias[n];
-      if (epi == 2) v *= gelu_grad_f(aux[m * ldc + n]);
-      C[m * ldc + n] = v;
-      if (epi == 1) C2[m * ldc + n] = gelu_f(v);
-    }
-  }
-}
-
 // out[i] = sum_z P[z * n + i], z in order (deterministic split-K reduction)
 __global__ void k_splitk_sum(const float* __restrict__ P, int splits, int64_t n,
                              float* __restrict__ out) {
@@ -161,65 +86,26 @@ __global__ void k_splitk_sum(const float* __restrict__ P, int splits, int64_t n,
   out[i] = v;
 }
 
-constexpr int kMaxSplits = 64;
-
-// C = A B (+ epilogue).  A product with few output tiles and a long K (the
-// weight gradients, K = batch) is split along K over up to 64 slices whose
-// partial products go to `part` (splits x M x ldc floats) and are summed in
-// slice order; only the plain epilogue (0, no bias) is split.
-template <typename TB>
-static int gemm(int M, int N, int K, const float* A, int64_t sam, int64_t sak, const TB* B,
-                int64_t sbk, int64_t sbn, float* C, int64_t ldc, const float* bias, int epi,
-                const float* aux, float* C2, cudaStream_t st, float* part = nullptr) {
-  dim3 grid(static_cast<unsigned>((N + kGBN - 1) / kGBN), static_cast<unsigned>((M + kGBM - 1) / kGBM));
-  int splits = 1;
-  if (part && epi == 0 && !bias) {
-    const int tiles = static_cast<int>(grid.x * grid.y);
-    splits = std::min(kMaxSplits, std::max(1, std::min(304 / tiles, K / 256)));
-  }
-  grid.z = static_cast<unsigned>(splits);
-  k_gemm<TB><<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, splits > 1 ? part : C, ldc,
-                                   bias, epi, aux, C2);
-  ABC_LAUNCH_CHECK();
-  if (splits > 1) {
-    const int64_t n = static_cast<int64_t>(M) * ldc;
-    k_splitk_sum<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(part, splits, n, C);
-    ABC_LAUNCH_CHECK();
-  }
-  return ABC_OK;
-}
-
 // ---- training pieces -------------------------------------------------------
-// column sums: out[n] = sum_b M[b][n] (bias gradients), one block per column
-__global__ void k_colsum(const float* __restrict__ Mx, int B, int N, float* __restrict__ out) {
-  __shared__ float sm[32];
-  const int n = blockIdx.x;
-  float s = 0.f;
-  for (int b = threadIdx.x; b < B; b += blockDim.x) s += Mx[static_cast<int64_t>(b) * N + n];
-  s = block_sum<float>(s, sm);
-  if (threadIdx.x == 0) out[n] = s;
-}
-
-__global__ void k_sum(const float* __restrict__ x, int n, float* __restrict__ out) {
-  __shared__ float sm[32];
-  float s = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
-  s = block_sum<float>(s, sm);
-  if (threadIdx.x == 0) *out = s;
-}
-
 // step_dev (nullable): the bias corrections use the step *step_dev + koff + 1
 // counted on the device (graph launches), computed in fp64 and rounded
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                        float* __restrict__ v, float lr, float b1, float b2, float eps, float c1,
                        float c2, const uint32_t* __restrict__ step_dev, uint32_t koff) {
+  __shared__ float sc[2];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= kMlpParams) return;
   if (step_dev) {
-    const double t = static_cast<double>(*step_dev) + static_cast<double>(koff) + 1.0;
-    c1 = static_cast<float>(1.0 - pow(0.9, t));
-    c2 = static_cast<float>(1.0 - pow(0.999, t));
+    // bias corrections, once per block (fp64 powers are slow on this GPU)
+    if (threadIdx.x == 0) {
+      const double t = static_cast<double>(*step_dev) + static_cast<double>(koff) + 1.0;
+      sc[0] = static_cast<float>(1.0 - pow(0.9, t));
+      sc[1] = static_cast<float>(1.0 - pow(0.999, t));
+    }
+    __syncthreads();
+    c1 = sc[0];
+    c2 = sc[1];
   }
+  if (i >= kMlpParams) return;
   const float gi = g[i];
   const float mi = b1 * m[i] + (1.0f - b1) * gi;
   const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
@@ -473,9 +359,10 @@ int mlp_infer(const MlpState& s, const float* u, int64_t n, float* Y, void* scra
 //   kTrFwd: Z2 = H1 W2^T (A = H1 R-tile, B = W2 packed by output row); the
 //     epilogue adds b2, applies GELU, forms layer 3, the loss and dY, then
 //     back through layer 3 and GELU: dZ2 = (dY W3) gelu'(Z2), written in
-//     both layouts and in fp32, and H2 in fp32;
+//     both layouts and in fp32 (feature-major), and H2 in fp32 (feature-major);
 //   kTrBwd: dH1 = dZ2 W2 (A = dZ2 R-tile, B = W2^T packed); the epilogue
-//     forms dZ1 = dH1 gelu'(Z1) in fp32;
+//     recomputes Z1 from X and forms dZ1 = dH1 gelu'(Z1) in fp32
+//     (feature-major);
 //   kTrGw2: gW2 = dZ2^T H1 over one 256-sample tile c (A = rows 128 m .. of
 //     the dZ2 T-tile, B = the H1 T-tile); the epilogue writes the tile's
 //     fp32 partial, summed over tiles in order afterwards (deterministic).
@@ -486,15 +373,16 @@ struct TrArgs {
   int B;                      // samples (rows past B are padding)
   const float* w;             // fp32 parameters (biases)
   const __nv_bfloat16* wb;    // bf16 parameters (W3)
-  const float* T;             // targets [Bp][4] (kTrFwd)
-  float* H2;                  // [Bp][256] fp32 (kTrFwd)
+  int Bp;                     // padded batch (a multiple of 256): the stride of [256][Bp]
+  const float* T;             // targets [B][4] (kTrFwd)
+  float* H2;                  // [256][Bp] fp32 (kTrFwd)
   float* dY;                  // [Bp][4] (kTrFwd)
   float* lossp;               // [Bp] squared errors (kTrFwd)
-  float* dZ2f;                // [Bp][256] fp32 (kTrFwd)
+  float* dZ2f;                // [256][Bp] fp32 (kTrFwd)
   __nv_bfloat16* dZ2R;        // R-layout (kTrFwd)
   __nv_bfloat16* dZ2T;        // T-layout (kTrFwd)
-  const float* Z1;            // [Bp][256] (kTrBwd)
-  float* dZ1;                 // [Bp][256] (kTrBwd)
+  const float* X;             // inputs [B][8] (kTrBwd: Z1 recomputed)
+  float* dZ1;                 // [256][Bp] fp32 (kTrBwd)
   float* gW2p;                // [tiles][256][256] (kTrGw2)
 };
 
@@ -519,6 +407,12 @@ k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bb
     for (int i = threadIdx.x; i < 4 * kMlpH; i += blockDim.x)
       sW3[i] = __bfloat162float(a.wb[kOffW3 + i]);
     for (int i = threadIdx.x; i < kMlpH; i += blockDim.x) sb2[i] = a.w[kOffB2 + i];
+  } else if (MODE == kTrBwd) {
+    // layer 1 (W1 as its bf16 values, b1) to recompute Z1: 9 KB over the
+    // W3 / b2 / partial-output area, which this mode does not use
+    for (int i = threadIdx.x; i < 8 * kMlpH; i += blockDim.x)
+      sW3[i] = __bfloat162float(a.wb[kOffW1 + i]);
+    for (int i = threadIdx.x; i < kMlpH; i += blockDim.x) sW3[8 * kMlpH + i] = a.w[kOffB1 + i];
   }
   if (threadIdx.x == 0) {
     mbar_init(full, 1);
@@ -584,7 +478,7 @@ k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bb
           for (int i = 0; i < 32; ++i) {
             const int col = c * 32 + i;
             const float h = gelu_f(v[i] + sb2[col]);
-            a.H2[b * kMlpH + col] = h;
+            a.H2[static_cast<int64_t>(col) * a.Bp + b] = h;
 #pragma unroll
             for (int o = 0; o < 4; ++o) y[o] = __fmaf_rn(sW3[o * kMlpH + col], h, y[o]);
           }
@@ -621,7 +515,7 @@ k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bb
 #pragma unroll
               for (int o = 0; o < 4; ++o) dh = __fmaf_rn(dy[o], sW3[o * kMlpH + col], dh);
               const float dz = dh * gelu_grad_f(v[gr * 8 + e] + sb2[col]);
-              a.dZ2f[b * kMlpH + col] = dz;
+              a.dZ2f[static_cast<int64_t>(col) * a.Bp + b] = dz;
               const __nv_bfloat16 qz = __float2bfloat16_rn(dz);
               hb[e] = __bfloat16_as_ushort(qz);
               a.dZ2T[tT * (kMlpH * 256) + mlp_packed_index(col, static_cast<int>(bT))] = qz;
@@ -638,6 +532,9 @@ k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bb
       }
     } else if (ok && MODE == kTrBwd) {
       const int64_t b = static_cast<int64_t>(blockIdx.x) * kMlpM + r;
+      float x[8];
+#pragma unroll
+      for (int d = 0; d < 8; ++d) x[d] = b < a.B ? a.X[b * 8 + d] : 0.0f;
       for (int cc = 0; cc < 2; ++cc) {
         const int c = 2 * g + cc;
         float v[32];
@@ -645,7 +542,10 @@ k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bb
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int col = c * 32 + i;
-          a.dZ1[b * kMlpH + col] = v[i] * gelu_grad_f(a.Z1[b * kMlpH + col]);
+          float z = sW3[8 * kMlpH + col];  // Z1 as layer 1 forms it
+#pragma unroll
+          for (int d = 0; d < 8; ++d) z = __fmaf_rn(sW3[col * 8 + d], x[d], z);
+          a.dZ1[static_cast<int64_t>(col) * a.Bp + b] = v[i] * gelu_grad_f(z);
         }
       }
     } else if (ok && MODE == kTrGw2) {
@@ -666,12 +566,11 @@ k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bb
   if (warp == kMlpEpiWarps + 1) tmem_dealloc(tmem, kMlpH);
 }
 
-// layer 1 of a training step: Z1 = X W1^T + b1 (fp32), H1 = gelu(Z1) as bf16
-// in both layouts; rows past B (padding) are zero
+// layer 1 of a training step: H1 = gelu(X W1^T + b1) as bf16 in both
+// layouts; rows past B (padding) are zero
 __global__ void k_tr_l1(const float* __restrict__ X, int B, int Bp,
                         const __nv_bfloat16* __restrict__ wb, const float* __restrict__ w,
-                        float* __restrict__ Z1, __nv_bfloat16* __restrict__ H1R,
-                        __nv_bfloat16* __restrict__ H1T) {
+                        __nv_bfloat16* __restrict__ H1R, __nv_bfloat16* __restrict__ H1T) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= Bp) return;
   float x[8];
@@ -687,7 +586,6 @@ __global__ void k_tr_l1(const float* __restrict__ X, int B, int Bp,
 #pragma unroll
       for (int k = 0; k < 8; ++k) z = __fmaf_rn(__bfloat162float(wb[kOffW1 + o * 8 + k]), x[k], z);
       const float h = b < B ? gelu_f(z) : 0.0f;
-      Z1[static_cast<int64_t>(b) * kMlpH + o] = z;
       const __nv_bfloat16 q = __float2bfloat16_rn(h);
       hb[e] = __bfloat16_as_ushort(q);
       H1T[static_cast<int64_t>(tT) * (kMlpH * 256) + mlp_packed_index(o, bT)] = q;
@@ -723,9 +621,86 @@ int mlp_train_prepare() {
   return ABC_OK;
 }
 
+// Gradient reductions over the (padded) batch, each output summed by one
+// block in a fixed order (deterministic).  Layer 3 and layer 2's bias: block
+// k < 256 forms gW3[o][k] = sum_b dY[b][o] H2[k][b] and gb2[k] = sum_b
+// dZ2[k][b]; block 256 forms gb3[o] = sum_b dY[b][o] and the loss sum.
+__global__ void __launch_bounds__(256)
+k_red_l3(const float* __restrict__ dY, const float* __restrict__ H2T,
+         const float* __restrict__ dZ2T, const float* __restrict__ lossp, int Bp,
+         float* __restrict__ grad, float* __restrict__ loss_dev) {
+  __shared__ float sm[32];
+  const int k = blockIdx.x;
+  if (k < kMlpH) {
+    float g[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    const float* h = H2T + static_cast<int64_t>(k) * Bp;
+    const float* z = dZ2T + static_cast<int64_t>(k) * Bp;
+    for (int b = threadIdx.x; b < Bp; b += blockDim.x) {
+      const float4 dy = *reinterpret_cast<const float4*>(dY + b * 4);
+      const float hv = h[b];
+      g[0] = __fmaf_rn(dy.x, hv, g[0]);
+      g[1] = __fmaf_rn(dy.y, hv, g[1]);
+      g[2] = __fmaf_rn(dy.z, hv, g[2]);
+      g[3] = __fmaf_rn(dy.w, hv, g[3]);
+      g[4] += z[b];
+    }
+#pragma unroll
+    for (int o = 0; o < 5; ++o) {
+      const float t = block_sum<float>(g[o], sm);
+      if (threadIdx.x == 0) {
+        if (o < 4) grad[kOffW3 + o * kMlpH + k] = t;
+        else grad[kOffB2 + k] = t;
+      }
+    }
+  } else {
+    float g[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int b = threadIdx.x; b < Bp; b += blockDim.x) {
+      const float4 dy = *reinterpret_cast<const float4*>(dY + b * 4);
+      g[0] += dy.x;
+      g[1] += dy.y;
+      g[2] += dy.z;
+      g[3] += dy.w;
+      g[4] += lossp[b];
+    }
+#pragma unroll
+    for (int o = 0; o < 5; ++o) {
+      const float t = block_sum<float>(g[o], sm);
+      if (threadIdx.x == 0) {
+        if (o < 4) grad[kOffB3 + o] = t;
+        else *loss_dev = t;
+      }
+    }
+  }
+}
+
+// Layer 1: block o forms gW1[o][k] = sum_b dZ1[o][b] X[b][k] (b < B) and
+// gb1[o] = sum_b dZ1[o][b].
+__global__ void __launch_bounds__(256)
+k_red_l1(const float* __restrict__ dZ1T, const float* __restrict__ X, int B, int Bp,
+         float* __restrict__ grad) {
+  __shared__ float sm[32];
+  const int o = blockIdx.x;
+  float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const float* z = dZ1T + static_cast<int64_t>(o) * Bp;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const float zv = z[b];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) g[k] = __fmaf_rn(zv, X[b * 8 + k], g[k]);  // X: caller's buffer
+    g[8] += zv;
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const float t = block_sum<float>(g[k], sm);
+    if (threadIdx.x == 0) {
+      if (k < 8) grad[kOffW1 + o * 8 + k] = t;
+      else grad[kOffB1 + o] = t;
+    }
+  }
+}
+
 // scratch of one training step on B samples (padded to Bp, a multiple of 256)
 struct TrLayout {
-  size_t Z1, H2, dZ2f, dZ1, dY, lossp, gW2p, sk, H1R, H1T, dZ2R, dZ2T, W2pk, W2Tpk, err, total;
+  size_t H2, dZ2f, dZ1, dY, lossp, gW2p, H1R, H1T, dZ2R, dZ2T, W2pk, W2Tpk, err, total;
 };
 
 static TrLayout tr_layout(int B) {
@@ -737,14 +712,12 @@ static TrLayout tr_layout(int B) {
     f = o;
     o += align256(bytes);
   };
-  take(l.Z1, 4 * BH);
   take(l.H2, 4 * BH);
   take(l.dZ2f, 4 * BH);
   take(l.dZ1, 4 * BH);
   take(l.dY, 4 * 4 * Bp);
   take(l.lossp, 4 * Bp);
   take(l.gW2p, 4 * (Bp / 256) * kMlpH * kMlpH);
-  take(l.sk, 4 * static_cast<size_t>(kMaxSplits) * kMlpH * kMlpH);
   take(l.H1R, 2 * BH);
   take(l.H1T, 2 * BH);
   take(l.dZ2R, 2 * BH);
@@ -771,14 +744,12 @@ int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* gr
   if (bytes < l.total) return ABC_E_SCRATCH;
   char* c = static_cast<char*>(scratch);
   const int Bp = static_cast<int>(ceil_div(B, 256) * 256);
-  float* Z1 = reinterpret_cast<float*>(c + l.Z1);
   float* H2 = reinterpret_cast<float*>(c + l.H2);
   float* dZ2f = reinterpret_cast<float*>(c + l.dZ2f);
   float* dZ1 = reinterpret_cast<float*>(c + l.dZ1);
   float* dY = reinterpret_cast<float*>(c + l.dY);
   float* lossp = reinterpret_cast<float*>(c + l.lossp);
   float* gW2p = reinterpret_cast<float*>(c + l.gW2p);
-  float* sk = reinterpret_cast<float*>(c + l.sk);
   auto* H1R = reinterpret_cast<__nv_bfloat16*>(c + l.H1R);
   auto* H1T = reinterpret_cast<__nv_bfloat16*>(c + l.H1T);
   auto* dZ2R = reinterpret_cast<__nv_bfloat16*>(c + l.dZ2R);
@@ -790,8 +761,7 @@ int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* gr
     ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
   }
   const __nv_bfloat16* wb = s.wb;
-  int rc;
-  k_tr_l1<<<static_cast<unsigned>(Bp / 128), 128, 0, st>>>(X, B, Bp, wb, s.w, Z1, H1R, H1T);
+  k_tr_l1<<<static_cast<unsigned>(Bp / 128), 128, 0, st>>>(X, B, Bp, wb, s.w, H1R, H1T);
   ABC_LAUNCH_CHECK();
   k_mlp_pack_w2<<<(kMlpH * kMlpH + 255) / 256, 256, 0, st>>>(wb, W2pk);
   ABC_LAUNCH_CHECK();
@@ -799,6 +769,7 @@ int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* gr
   ABC_LAUNCH_CHECK();
   TrArgs a{};
   a.B = B;
+  a.Bp = Bp;
   a.w = s.w;
   a.wb = wb;
   a.T = T;
@@ -808,22 +779,15 @@ int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* gr
   a.dZ2f = dZ2f;
   a.dZ2R = dZ2R;
   a.dZ2T = dZ2T;
-  a.Z1 = Z1;
+  a.X = X;
   a.dZ1 = dZ1;
   a.gW2p = gW2p;
   // forward through layers 2 and 3, loss, back through layer 3
   k_mlp_train_tc<kTrFwd><<<static_cast<unsigned>(Bp / kMlpM), kMlpThreads, kMlpSmem, st>>>(
       reinterpret_cast<const uint8_t*>(H1R), reinterpret_cast<const uint8_t*>(W2pk), a, err);
   ABC_LAUNCH_CHECK();
-  k_sum<<<1, 1024, 0, st>>>(lossp, Bp, loss_dev);
-  ABC_LAUNCH_CHECK();
-  // layer 3 gradients: gW3[o][k] = sum_b dY[b][o] H2[b][k] (M = 4, N = 256, K = Bp)
-  if ((rc = gemm<float>(4, kMlpH, Bp, dY, 1, 4, H2, kMlpH, 1, grad + kOffW3, kMlpH, nullptr, 0,
-                        nullptr, nullptr, st, sk)))
-    return rc;
-  k_colsum<<<4, 256, 0, st>>>(dY, Bp, 4, grad + kOffB3);
-  ABC_LAUNCH_CHECK();
-  k_colsum<<<kMlpH, 256, 0, st>>>(dZ2f, Bp, kMlpH, grad + kOffB2);
+  // layer 3 and the layer-2 bias, the loss
+  k_red_l3<<<kMlpH + 1, 256, 0, st>>>(dY, H2, dZ2f, lossp, Bp, grad, loss_dev);
   ABC_LAUNCH_CHECK();
   // dZ1 = (dZ2 W2) gelu'(Z1)
   k_mlp_train_tc<kTrBwd><<<static_cast<unsigned>(Bp / kMlpM), kMlpThreads, kMlpSmem, st>>>(
@@ -840,11 +804,8 @@ int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* gr
                                                                         grad + kOffW2);
     ABC_LAUNCH_CHECK();
   }
-  // gW1 = dZ1^T X (M = 256, N = 8, K = B), gb1 = column sums of dZ1
-  if ((rc = gemm<float>(kMlpH, 8, B, dZ1, 1, kMlpH, X, 8, 1, grad + kOffW1, 8, nullptr, 0, nullptr,
-                        nullptr, st, sk)))
-    return rc;
-  k_colsum<<<kMlpH, 256, 0, st>>>(dZ1, Bp, kMlpH, grad + kOffB1);
+  // layer 1 and its bias
+  k_red_l1<<<kMlpH, 256, 0, st>>>(dZ1, X, B, Bp, grad);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }
