@@ -12,10 +12,10 @@
 // Training: the three 256-wide products of a step on tcgen05 (bf16 operands,
 // fp32 accumulation) with fused epilogues, layers 1 and 3 and the gradient
 // reductions on CUDA cores, Adam in fp32.
-// Inference: one kernel per 128 samples -- layer 1 (CUDA cores) writes the
-// hidden layer as the bf16 A operand in shared memory, layer 2 runs on
-// tcgen05 (M = 128, N = 256, K = 256) and bias + GELU + layer 3 are fused into
-// the epilogue (16 warps over TMEM lane quarters and column groups).
+// Inference: layer 1 on CUDA cores writes the hidden layer as bf16 tiles in
+// the tensor-core operand layout; layer 2 runs on tcgen05 (M = 128, N = 256,
+// K = 256) with bias + GELU + layer 3 fused into the epilogue (one thread per
+// sample reads its 256 accumulators from tensor memory).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -155,8 +155,6 @@ constexpr int kMlpEpiWarps = 16;
 constexpr int kMlpThreads = 32 * (kMlpEpiWarps + 2);
 constexpr size_t kMlpSmem = 1024 + kMlpATile + kMlpBBytes + (4 * kMlpH + kMlpH) * 4 +
                             4 * kMlpM * 4 * 4 + 256;
-// inference also keeps layer 1 (W1 as floats, b1) in shared memory
-constexpr size_t kMlpSmemInf = kMlpSmem + (8 * kMlpH + kMlpH) * 4;
 constexpr uint32_t kMlpIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
                                (static_cast<uint32_t>(kMlpH >> 3) << 17) |
                                (static_cast<uint32_t>(kMlpM >> 4) << 24);
@@ -165,6 +163,41 @@ constexpr uint32_t kMlpIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
 // of a row group consecutive along K (LBO 128 B), row groups 4096 B apart
 __host__ __device__ __forceinline__ int mlp_packed_index(int r, int k) {
   return ((((r >> 3) << 5) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
+// layer 1 + GELU for n samples (u [8][n]) into packed bf16 tiles of h1;
+// xstat (nullable): input means [8] then standard deviations [8], the
+// network's input being (u - mean) / sd
+__global__ void k_mlp_l1_pack(const float* __restrict__ u, int64_t n, int64_t npad,
+                              const __nv_bfloat16* __restrict__ wb, const float* __restrict__ w,
+                              __nv_bfloat16* __restrict__ Hpk, const float* __restrict__ xstat) {
+  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= npad) return;
+  float x[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    x[d] = j < n ? u[d * n + j] : 0.0f;
+    if (xstat) x[d] = __fdiv_rn(__fsub_rn(x[d], xstat[d]), xstat[8 + d]);
+  }
+  __nv_bfloat16* tile = Hpk + (j / kMlpM) * (kMlpM * kMlpH);
+  const int r = static_cast<int>(j % kMlpM);
+  for (int c = 0; c < kMlpH / 8; ++c) {
+    uint32_t h[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int o = 8 * c + e;
+      float z = w[kOffB1 + o];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) z = __fmaf_rn(__bfloat162float(wb[kOffW1 + o * 8 + k]), x[k], z);
+      h[e] = __bfloat16_as_ushort(__float2bfloat16_rn(j < n ? gelu_f(z) : 0.0f));
+    }
+    uint4 v;
+    v.x = h[0] | (h[1] << 16);
+    v.y = h[2] | (h[3] << 16);
+    v.z = h[4] | (h[5] << 16);
+    v.w = h[6] | (h[7] << 16);
+    *reinterpret_cast<uint4*>(tile + mlp_packed_index(r, 8 * c)) = v;
+  }
 }
 
 // W2 (bf16, [out][in]) as the B operand: rows = out, K = in
@@ -178,20 +211,11 @@ __global__ void k_mlp_pack_w2(const __nv_bfloat16* __restrict__ wb, __nv_bfloat1
 // epilogue barrier of the 16 epilogue warps (named barrier 1)
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
 
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Y[j][0..3] = W3 gelu(W2 gelu(W1 x_j + b1) + b2) + b3 for 128 samples per
-// CTA, x_j = (u_j - mean) / sd (xstat nullable: x = u).  The 16 epilogue
-// warps first form the hidden layer h1 = gelu(W1 x + b1) of the CTA's rows in
-// shared memory as the bf16 A operand (rows 0..127, features 64 g .. + 63
-// for thread group g), while the copy warp brings W2; the MMA warp starts
-// once both are there (the generic-proxy writes fenced for the tensor core).
+// Y[j][0..3] = W3 gelu(W2 h1_j + b2) + b3 for 128 samples per CTA
 __global__ void __launch_bounds__(kMlpThreads, 1)
-k_mlp_tc(const float* __restrict__ u, const uint8_t* __restrict__ W2pk,
+k_mlp_tc(const uint8_t* __restrict__ Hpk, const uint8_t* __restrict__ W2pk,
          const float* __restrict__ w, const __nv_bfloat16* __restrict__ wb, int64_t n,
-         const float* __restrict__ xstat, float* __restrict__ Y, unsigned* err) {
+         float* __restrict__ Y, unsigned* err) {
   extern __shared__ uint8_t mlp_smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(mlp_smem_raw) + 1023) &
                                              ~uintptr_t(1023));
@@ -200,22 +224,16 @@ k_mlp_tc(const float* __restrict__ u, const uint8_t* __restrict__ W2pk,
   float* sW3 = reinterpret_cast<float*>(sB + kMlpBBytes);
   float* sb2 = sW3 + 4 * kMlpH;
   float* sY = sb2 + kMlpH;  // [4 column groups][128 rows][4] partial outputs
-  float* sW1 = sY + 4 * kMlpM * 4;
-  float* sb1 = sW1 + 8 * kMlpH;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sb1 + kMlpH);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sY + 4 * kMlpM * 4);
   uint64_t* full = bars;
   uint64_t* tfull = bars + 1;
-  uint64_t* afull = bars + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < 4 * kMlpH; i += blockDim.x) sW3[i] = __bfloat162float(wb[kOffW3 + i]);
   for (int i = threadIdx.x; i < kMlpH; i += blockDim.x) sb2[i] = w[kOffB2 + i];
-  for (int i = threadIdx.x; i < 8 * kMlpH; i += blockDim.x) sW1[i] = __bfloat162float(wb[kOffW1 + i]);
-  for (int i = threadIdx.x; i < kMlpH; i += blockDim.x) sb1[i] = w[kOffB1 + i];
   if (threadIdx.x == 0) {
     mbar_init(full, 1);
     mbar_init(tfull, 1);
-    mbar_init(afull, 32 * kMlpEpiWarps);
     fence_mbar_init();
   }
   if (warp == kMlpEpiWarps + 1) {
@@ -228,12 +246,13 @@ k_mlp_tc(const float* __restrict__ u, const uint8_t* __restrict__ W2pk,
   const uint32_t tmem = *tmem_slot;
   if (warp == kMlpEpiWarps) {
     if (lane == 0) {
-      mbar_expect_tx(full, kMlpBBytes);
+      mbar_expect_tx(full, kMlpATile + kMlpBBytes);
+      bulk_g2s(sA, Hpk + static_cast<size_t>(blockIdx.x) * kMlpATile, kMlpATile, full);
       bulk_g2s(sB, W2pk, kMlpBBytes, full);
-      mbar_wait(full, 0u, err, 21u);  // the copy landed before the CTA can exit
+      mbar_wait(full, 0u, err, 21u);  // both copies landed before the CTA can exit
     }
   } else if (warp == kMlpEpiWarps + 1) {
-    if (lane == 0 && mbar_wait(full, 0u, err, 22u) && mbar_wait(afull, 0u, err, 25u)) {
+    if (lane == 0 && mbar_wait(full, 0u, err, 22u)) {
       tc_fence_after();
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
 #pragma unroll
@@ -245,38 +264,6 @@ k_mlp_tc(const float* __restrict__ u, const uint8_t* __restrict__ W2pk,
     }
     __syncwarp();
   } else {
-    {
-      // layer 1 into the A operand: row ra, features 64 ga .. 64 ga + 63
-      const int ra = threadIdx.x & (kMlpM - 1), ga = threadIdx.x >> 7;
-      const int64_t j = static_cast<int64_t>(blockIdx.x) * kMlpM + ra;
-      float x[8];
-#pragma unroll
-      for (int d = 0; d < 8; ++d) {
-        x[d] = j < n ? u[d * n + j] : 0.0f;
-        if (xstat) x[d] = __fdiv_rn(__fsub_rn(x[d], xstat[d]), xstat[8 + d]);
-      }
-      __nv_bfloat16* tile = reinterpret_cast<__nv_bfloat16*>(sA);
-#pragma unroll 1
-      for (int c = 0; c < 8; ++c) {
-        uint32_t h[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int o = 64 * ga + 8 * c + e;
-          float z = sb1[o];
-#pragma unroll
-          for (int k = 0; k < 8; ++k) z = __fmaf_rn(sW1[o * 8 + k], x[k], z);
-          h[e] = __bfloat16_as_ushort(__float2bfloat16_rn(j < n ? gelu_f(z) : 0.0f));
-        }
-        uint4 v;
-        v.x = h[0] | (h[1] << 16);
-        v.y = h[2] | (h[3] << 16);
-        v.z = h[4] | (h[5] << 16);
-        v.w = h[6] | (h[7] << 16);
-        *reinterpret_cast<uint4*>(tile + mlp_packed_index(ra, 64 * ga + 8 * c)) = v;
-      }
-      fence_proxy_async_smem();  // the tensor core reads what these stores wrote
-      mbar_arrive(afull);
-    }
     // tcgen05.ld is warp-collective: the whole warp reads or none of it
     const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull, 0u, err, 24u));
     tc_fence_after();
@@ -316,17 +303,23 @@ k_mlp_tc(const float* __restrict__ u, const uint8_t* __restrict__ W2pk,
   if (warp == kMlpEpiWarps + 1) tmem_dealloc(tmem, kMlpH);
 }
 
-size_t mlp_infer_scratch_bytes(int64_t) { return align256(kMlpBBytes) + align256(16); }
+size_t mlp_infer_scratch_bytes(int64_t n) {
+  const int64_t npad = ceil_div(std::max<int64_t>(n, 1), kMlpM) * kMlpM;
+  return align256(static_cast<size_t>(npad) * kMlpH * 2) + align256(kMlpBBytes) + align256(16);
+}
 
 int mlp_infer_prepare() {
   ABC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(kMlpSmemInf)));
+                                    static_cast<int>(kMlpSmem)));
   return ABC_OK;
 }
 
 // the error word of mlp_infer(n) inside its scratch
-unsigned* mlp_infer_err(void* scratch, int64_t) {
-  return reinterpret_cast<unsigned*>(static_cast<char*>(scratch) + align256(kMlpBBytes));
+unsigned* mlp_infer_err(void* scratch, int64_t n) {
+  const int64_t npad = ceil_div(std::max<int64_t>(n, 1), kMlpM) * kMlpM;
+  return reinterpret_cast<unsigned*>(static_cast<char*>(scratch) +
+                                     align256(static_cast<size_t>(npad) * kMlpH * 2) +
+                                     align256(kMlpBBytes));
 }
 
 // Y [n][4] (standardised outputs) for u [8][n]; the error word lives in scratch
@@ -336,14 +329,20 @@ int mlp_infer(const MlpState& s, const float* u, int64_t n, float* Y, void* scra
   if (n <= 0) return ABC_OK;
   if (bytes < mlp_infer_scratch_bytes(n)) return ABC_E_SCRATCH;
   const int64_t npad = ceil_div(n, kMlpM) * kMlpM;
-  auto* W2pk = static_cast<__nv_bfloat16*>(scratch);
+  char* b = static_cast<char*>(scratch);
+  auto* Hpk = reinterpret_cast<__nv_bfloat16*>(b);
+  auto* W2pk = reinterpret_cast<__nv_bfloat16*>(b + align256(static_cast<size_t>(npad) * kMlpH * 2));
   unsigned* err = err_word ? err_word : mlp_infer_err(scratch, n);
   if (err_out) *err_out = err;
   if (reset_err) ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
   k_mlp_pack_w2<<<(kMlpH * kMlpH + 255) / 256, 256, 0, st>>>(s.wb, W2pk);
   ABC_LAUNCH_CHECK();
-  k_mlp_tc<<<static_cast<unsigned>(npad / kMlpM), kMlpThreads, kMlpSmemInf, st>>>(
-      u, reinterpret_cast<const uint8_t*>(W2pk), s.w, s.wb, n, xstat, Y, err);
+  k_mlp_l1_pack<<<static_cast<unsigned>(ceil_div(npad, 128)), 128, 0, st>>>(u, n, npad, s.wb, s.w,
+                                                                           Hpk, xstat);
+  ABC_LAUNCH_CHECK();
+  k_mlp_tc<<<static_cast<unsigned>(npad / kMlpM), kMlpThreads, kMlpSmem, st>>>(
+      reinterpret_cast<const uint8_t*>(Hpk), reinterpret_cast<const uint8_t*>(W2pk), s.w, s.wb, n,
+      Y, err);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }
@@ -568,36 +567,37 @@ k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bb
 }
 
 // layer 1 of a training step: H1 = gelu(X W1^T + b1) as bf16 in both
-// layouts, one thread per (sample, 8 features); rows past B (padding) are zero
+// layouts; rows past B (padding) are zero
 __global__ void k_tr_l1(const float* __restrict__ X, int B, int Bp,
                         const __nv_bfloat16* __restrict__ wb, const float* __restrict__ w,
                         __nv_bfloat16* __restrict__ H1R, __nv_bfloat16* __restrict__ H1T) {
-  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= static_cast<int64_t>(Bp) * (kMlpH / 8)) return;
-  // consecutive threads take consecutive samples of one feature chunk
-  const int b = static_cast<int>(idx % Bp), c = static_cast<int>(idx / Bp);
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= Bp) return;
   float x[8];
 #pragma unroll
   for (int d = 0; d < 8; ++d) x[d] = b < B ? X[b * 8 + d] : 0.0f;
   const int tR = b / kMlpM, rR = b % kMlpM, tT = b / 256, bT = b % 256;
-  uint32_t hb[8];
+  for (int c = 0; c < kMlpH / 8; ++c) {
+    uint32_t hb[8];
 #pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    const int o = 8 * c + e;
-    float z = w[kOffB1 + o];
+    for (int e = 0; e < 8; ++e) {
+      const int o = 8 * c + e;
+      float z = w[kOffB1 + o];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) z = __fmaf_rn(__bfloat162float(wb[kOffW1 + o * 8 + k]), x[k], z);
-    const __nv_bfloat16 q = __float2bfloat16_rn(b < B ? gelu_f(z) : 0.0f);
-    hb[e] = __bfloat16_as_ushort(q);
-    H1T[static_cast<int64_t>(tT) * (kMlpH * 256) + mlp_packed_index(o, bT)] = q;
+      for (int k = 0; k < 8; ++k) z = __fmaf_rn(__bfloat162float(wb[kOffW1 + o * 8 + k]), x[k], z);
+      const float h = b < B ? gelu_f(z) : 0.0f;
+      const __nv_bfloat16 q = __float2bfloat16_rn(h);
+      hb[e] = __bfloat16_as_ushort(q);
+      H1T[static_cast<int64_t>(tT) * (kMlpH * 256) + mlp_packed_index(o, bT)] = q;
+    }
+    uint4 v;
+    v.x = hb[0] | (hb[1] << 16);
+    v.y = hb[2] | (hb[3] << 16);
+    v.z = hb[4] | (hb[5] << 16);
+    v.w = hb[6] | (hb[7] << 16);
+    *reinterpret_cast<uint4*>(H1R + static_cast<int64_t>(tR) * (kMlpM * kMlpH) +
+                              mlp_packed_index(rR, 8 * c)) = v;
   }
-  uint4 v;
-  v.x = hb[0] | (hb[1] << 16);
-  v.y = hb[2] | (hb[3] << 16);
-  v.z = hb[4] | (hb[5] << 16);
-  v.w = hb[6] | (hb[7] << 16);
-  *reinterpret_cast<uint4*>(H1R + static_cast<int64_t>(tR) * (kMlpM * kMlpH) +
-                            mlp_packed_index(rR, 8 * c)) = v;
 }
 
 // W2^T (bf16) as the B operand of dH1 = dZ2 W2: rows = input feature k, K = output o
@@ -761,7 +761,7 @@ int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* gr
     ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
   }
   const __nv_bfloat16* wb = s.wb;
-  k_tr_l1<<<static_cast<unsigned>(Bp / 8), 256, 0, st>>>(X, B, Bp, wb, s.w, H1R, H1T);
+  k_tr_l1<<<static_cast<unsigned>(Bp / 128), 128, 0, st>>>(X, B, Bp, wb, s.w, H1R, H1T);
   ABC_LAUNCH_CHECK();
   k_mlp_pack_w2<<<(kMlpH * kMlpH + 255) / 256, 256, 0, st>>>(wb, W2pk);
   ABC_LAUNCH_CHECK();
