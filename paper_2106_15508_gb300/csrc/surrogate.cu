@@ -567,37 +567,36 @@ k_mlp_train_tc(const uint8_t* __restrict__ Abase, const uint8_t* __restrict__ Bb
 }
 
 // layer 1 of a training step: H1 = gelu(X W1^T + b1) as bf16 in both
-// layouts; rows past B (padding) are zero
+// layouts, one thread per (sample, 8 features); rows past B (padding) are zero
 __global__ void k_tr_l1(const float* __restrict__ X, int B, int Bp,
                         const __nv_bfloat16* __restrict__ wb, const float* __restrict__ w,
                         __nv_bfloat16* __restrict__ H1R, __nv_bfloat16* __restrict__ H1T) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= Bp) return;
+  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= static_cast<int64_t>(Bp) * (kMlpH / 8)) return;
+  // consecutive threads take consecutive samples of one feature chunk
+  const int b = static_cast<int>(idx % Bp), c = static_cast<int>(idx / Bp);
   float x[8];
 #pragma unroll
   for (int d = 0; d < 8; ++d) x[d] = b < B ? X[b * 8 + d] : 0.0f;
   const int tR = b / kMlpM, rR = b % kMlpM, tT = b / 256, bT = b % 256;
-  for (int c = 0; c < kMlpH / 8; ++c) {
-    uint32_t hb[8];
+  uint32_t hb[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int o = 8 * c + e;
-      float z = w[kOffB1 + o];
+  for (int e = 0; e < 8; ++e) {
+    const int o = 8 * c + e;
+    float z = w[kOffB1 + o];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) z = __fmaf_rn(__bfloat162float(wb[kOffW1 + o * 8 + k]), x[k], z);
-      const float h = b < B ? gelu_f(z) : 0.0f;
-      const __nv_bfloat16 q = __float2bfloat16_rn(h);
-      hb[e] = __bfloat16_as_ushort(q);
-      H1T[static_cast<int64_t>(tT) * (kMlpH * 256) + mlp_packed_index(o, bT)] = q;
-    }
-    uint4 v;
-    v.x = hb[0] | (hb[1] << 16);
-    v.y = hb[2] | (hb[3] << 16);
-    v.z = hb[4] | (hb[5] << 16);
-    v.w = hb[6] | (hb[7] << 16);
-    *reinterpret_cast<uint4*>(H1R + static_cast<int64_t>(tR) * (kMlpM * kMlpH) +
-                              mlp_packed_index(rR, 8 * c)) = v;
+    for (int k = 0; k < 8; ++k) z = __fmaf_rn(__bfloat162float(wb[kOffW1 + o * 8 + k]), x[k], z);
+    const __nv_bfloat16 q = __float2bfloat16_rn(b < B ? gelu_f(z) : 0.0f);
+    hb[e] = __bfloat16_as_ushort(q);
+    H1T[static_cast<int64_t>(tT) * (kMlpH * 256) + mlp_packed_index(o, bT)] = q;
   }
+  uint4 v;
+  v.x = hb[0] | (hb[1] << 16);
+  v.y = hb[2] | (hb[3] << 16);
+  v.z = hb[4] | (hb[5] << 16);
+  v.w = hb[6] | (hb[7] << 16);
+  *reinterpret_cast<uint4*>(H1R + static_cast<int64_t>(tR) * (kMlpM * kMlpH) +
+                            mlp_packed_index(rR, 8 * c)) = v;
 }
 
 // W2^T (bf16) as the B operand of dH1 = dZ2 W2: rows = input feature k, K = output o
@@ -761,7 +760,7 @@ int mlp_grad(const MlpState& s, const float* X, const float* T, int B, float* gr
     ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
   }
   const __nv_bfloat16* wb = s.wb;
-  k_tr_l1<<<static_cast<unsigned>(Bp / 128), 128, 0, st>>>(X, B, Bp, wb, s.w, H1R, H1T);
+  k_tr_l1<<<static_cast<unsigned>(Bp / 8), 256, 0, st>>>(X, B, Bp, wb, s.w, H1R, H1T);
   ABC_LAUNCH_CHECK();
   k_mlp_pack_w2<<<(kMlpH * kMlpH + 255) / 256, 256, 0, st>>>(wb, W2pk);
   ABC_LAUNCH_CHECK();
