@@ -812,10 +812,10 @@ def main():
     ap.add_argument("--generations", type=int, default=0,
                     help="generations per run (single: 20, the workload's G; eps_final: 8)")
     ap.add_argument("--surrogate-steps", type=int, default=32)
-    ap.add_argument("--surrogate-tau", type=float, default=0.5)
+    ap.add_argument("--surrogate-tau", type=float, default=0.25)
     ap.add_argument("--surrogate-batch", type=int, default=4096)
     ap.add_argument("--surrogate-rho-min", type=float, default=0.05)
-    ap.add_argument("--surrogate-ring-mult", type=int, default=0,
+    ap.add_argument("--surrogate-ring-mult", type=int, default=2,
                     help="training ring of this many times N samples (0: the library default)")
     ap.add_argument("--stress", action="store_true",
                     help="eps_final on the stress runs (2^20 particles, 365 days, P 3.3e8)")
