@@ -534,8 +534,10 @@ ABC_API void abc_mlp_free(abc_mlp* m);
 typedef struct abc_batch abc_batch;
 /* cfgs: host array of n_runs configs; obs: host array of n_runs host
  * pointers to int32 [3][T_r+1] series (entries may be NULL for the toy).
- * A config with surrogate != 0 gives ABC_E_INVAL: the graph branches have
- * no screening step. */
+ * A run with surrogate != 0 screens inside its graph branch (inference,
+ * screen, compaction and simulation of the passed slots per batch; training
+ * after the generation), with the results of a single context of that
+ * config. */
 ABC_API int abc_batch_init(const abc_config* cfgs, int32_t n_runs, const int32_t* const* obs,
                            void* stream, abc_batch** out);
 /* First call: stage 0 of every run; later calls: one graph launch. */
