@@ -39,13 +39,20 @@ class Smc(C.Structure):
         ("beta_a", C.c_float), ("beta_b", C.c_int32), ("beta_p1", C.c_float),
         ("beta_p2", C.c_float), ("weight_mode", C.c_int32),
         ("max_batches", C.c_int32), ("max_redraw", C.c_int32), ("nthreads", C.c_int32),
+        ("mcmc_s0", C.c_float), ("mcmc_adapt", C.c_int32),
     ]
+
+
+class McmcState(C.Structure):
+    """The MCMC baseline's tuned step across generations (s, adaptations
+    made, batches of the run so far)."""
+    _fields_ = [("s", C.c_double), ("k", C.c_int64), ("batches", C.c_int64)]
 
 
 class GenStats(C.Structure):
     _fields_ = [
         ("eps", C.c_double), ("eps1", C.c_double), ("ess", C.c_double), ("beta_a", C.c_float),
-        ("beta_b", C.c_int32), ("beta_bf", C.c_float), ("pad", C.c_int32),
+        ("beta_b", C.c_int32), ("beta_bf", C.c_float), ("mcmc_s", C.c_float),
         ("batches", C.c_int64), ("sims", C.c_int64),
         ("exhausted", C.c_int64), ("accepted_total", C.c_int64), ("total", C.c_uint64),
         ("status", C.c_int32),
@@ -91,6 +98,9 @@ def lib():
         L.or_normalize.restype = C.c_double
         L.or_synth_obs.restype = C.c_int32
         L.or_generation.restype = C.c_int32
+        L.or_mcmc_adapt.restype = C.c_double
+        L.or_mcmc_adapt.argtypes = [C.c_double, C.c_int64, C.c_int64, C.c_int64]
+        L.or_mcmc_window.restype = C.c_int64
     return _lib
 
 
@@ -240,9 +250,10 @@ def resample_prefix(d, W, eps, mode):
 
 
 def propose(m: OracleModel, u, prefix, total, beta_a, beta_b, slots, c1, max_redraw=64,
-            c0_idx=None, nthreads=1, beta_bf=0.0):
+            c0_idx=None, nthreads=1, beta_bf=0.0, s_fixed=0.0):
     """beta_b >= 1: s ~ Beta(beta_a, beta_b) by the product form; beta_b = 0:
-    s ~ Beta(beta_a, beta_bf) by the Gamma ratio."""
+    s ~ Beta(beta_a, beta_bf) by the Gamma ratio; s_fixed > 0: the MCMC
+    baseline's single step s = s_fixed for every slot."""
     u = np.ascontiguousarray(u, np.float32)
     prefix = np.ascontiguousarray(prefix, np.uint64)
     n = u.shape[1]
@@ -254,7 +265,7 @@ def propose(m: OracleModel, u, prefix, total, beta_a, beta_b, slots, c1, max_red
     c0 = None if c0_idx is None else np.ascontiguousarray(c0_idx, np.uint32)
     lib().or_propose(m.ref(), _p(u, C.c_float), C.c_int64(n), _p(prefix, C.c_uint64),
                      C.c_uint64(total), C.c_float(beta_a), C.c_int32(beta_b),
-                     C.c_float(beta_bf), C.c_int64(slots),
+                     C.c_float(beta_bf), C.c_float(s_fixed), C.c_int64(slots),
                      _p(c0, C.c_uint32), C.c_uint32(c1), C.c_int32(max_redraw), _p(up, C.c_float),
                      _p(s, C.c_float), _p(anc, C.c_int32), _p(att, C.c_int32), _p(fl, C.c_uint8),
                      C.c_int(nthreads))
@@ -282,8 +293,10 @@ def normalize(logW):
 
 
 def make_smc(N, M=None, alpha=0.5, beta_mode=0, beta_a=2.0, beta_b=5, weight_mode=0,
-             max_batches=64, max_redraw=64, nthreads=1, beta_p1=0.0, beta_p2=0.0, max_total=0):
+             max_batches=64, max_redraw=64, nthreads=1, beta_p1=0.0, beta_p2=0.0, max_total=0,
+             mcmc_s0=0.1, mcmc_adapt=0):
     c = Smc()
+    c.mcmc_s0, c.mcmc_adapt = mcmc_s0, mcmc_adapt
     c.N, c.M = N, (N if M is None else M)
     c.max_total = max_total
     c.alpha, c.beta_mode, c.beta_a, c.beta_b = alpha, beta_mode, beta_a, beta_b
@@ -310,14 +323,37 @@ def generation0(m: OracleModel, c: Smc):
     return pop
 
 
-def generation(m: OracleModel, c: Smc, t: int, eps1: float, pop: Population):
+MCMC_MODE = 5  # beta_mode of the MCMC baseline (one tuned step, Sec. 2.4.1)
+
+
+def mcmc_start(c: Smc):
+    """The MCMC baseline's step state after generation 0: s = mcmc_s0, no
+    adaptation yet, generation 0 counted as ceil(N / M) batches."""
+    return McmcState(float(np.float32(c.mcmc_s0)), 0, batches_gen0(c))
+
+
+def mcmc_adapt(s, k, acc, sims):
+    return lib().or_mcmc_adapt(float(s), int(k), int(acc), int(sims))
+
+
+def mcmc_window(c: Smc):
+    return lib().or_mcmc_window(C.byref(c))
+
+
+def generation(m: OracleModel, c: Smc, t: int, eps1: float, pop: Population, mcmc=None):
+    """mcmc: the McmcState of an MCMC-baseline run (updated in place)."""
+    if c.beta_mode == MCMC_MODE and mcmc is None:
+        raise ValueError("the MCMC baseline needs its step state")
     new = Population(c.N)
     st = GenStats()
-    lib().or_generation(m.ref(), C.byref(c), C.c_int32(t), C.c_double(eps1),
-                        _p(pop.u, C.c_float), _p(pop.d, C.c_double), _p(pop.W, C.c_double),
-                        _p(new.u, C.c_float), _p(new.d, C.c_double), _p(new.W, C.c_double),
-                        _p(new.s, C.c_float), _p(new.anc, C.c_int32), _p(new.logW, C.c_double),
-                        C.byref(st))
+    rc = lib().or_generation(m.ref(), C.byref(c), C.c_int32(t), C.c_double(eps1),
+                             _p(pop.u, C.c_float), _p(pop.d, C.c_double), _p(pop.W, C.c_double),
+                             _p(new.u, C.c_float), _p(new.d, C.c_double), _p(new.W, C.c_double),
+                             _p(new.s, C.c_float), _p(new.anc, C.c_int32),
+                             _p(new.logW, C.c_double), C.byref(st),
+                             C.byref(mcmc) if mcmc is not None else None)
+    if rc < 0:
+        raise ValueError("or_generation: bad arguments")
     return new, st
 
 
@@ -339,10 +375,11 @@ def run(m: OracleModel, c: Smc, G: int):
     stats = []
     eps1 = 0.0
     total = batches_gen0(c)
+    ms = mcmc_start(c) if c.beta_mode == MCMC_MODE else None
     for t in range(1, G):
         if c.max_total > 0 and total >= c.max_total:
             break
-        new, st = generation(m, c, t, eps1, pop)
+        new, st = generation(m, c, t, eps1, pop, ms)
         stats.append(st)
         total += st.batches
         if st.status != 0:

@@ -702,12 +702,19 @@ OR_API void or_beta_shape(int32_t mode, float ratio, int32_t t, float fa, int32_
  * u' = u_anc + sqrt(s) z lies in [0,1]^8.  On exhaustion flag = 1.
  * s ~ Beta(beta_a, beta_b) by the product form when beta_b >= 1, else
  * Beta(beta_a, beta_bf) by the Gamma ratio.
+ *
+ * s_fixed > 0 selects the single tuned step of the MCMC baseline (Sec.
+ * 2.4.1, Eq. 12): every attempt walks with variance s = s_fixed and no BETA
+ * block is read.  With a uniform prior and a symmetric Gaussian walk the
+ * Metropolis-Hastings ratio of Eq. 13 is 1 inside the support and 0 outside,
+ * so its accept/reject step is this same support check: a proposal outside
+ * [0,1]^8 is rejected and drawn again.
  */
 OR_API void or_propose(const or_model* m, const float* u, int64_t n, const uint64_t* prefix,
-                       uint64_t total, float beta_a, int32_t beta_b, float beta_bf, int64_t slots,
-                       const uint32_t* c0_idx, uint32_t c1, int32_t max_redraw, float* u_out,
-                       float* s_out, int32_t* anc_out, int32_t* attempts_out, uint8_t* flag_out,
-                       int nthreads) {
+                       uint64_t total, float beta_a, int32_t beta_b, float beta_bf, float s_fixed,
+                       int64_t slots, const uint32_t* c0_idx, uint32_t c1, int32_t max_redraw,
+                       float* u_out, float* s_out, int32_t* anc_out, int32_t* attempts_out,
+                       uint8_t* flag_out, int nthreads) {
   (void)nthreads;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
@@ -723,8 +730,11 @@ OR_API void or_propose(const or_model* m, const float* u, int64_t n, const uint6
       uint32_t w[4];
       philox_ctr(m->key, j, c1, (uint32_t)a, TAG_ANCESTOR, w);
       anc = draw_ancestor(prefix, n, total, w[0], w[1]);
-      s = beta_b > 0 ? or_beta(m->key, beta_a, beta_b, j, c1, (uint32_t)a)
-                     : or_beta_real(m->key, beta_a, beta_bf, j, c1, (uint32_t)a);
+      if (s_fixed > 0.0f)
+        s = s_fixed;
+      else
+        s = beta_b > 0 ? or_beta(m->key, beta_a, beta_b, j, c1, (uint32_t)a)
+                       : or_beta_real(m->key, beta_a, beta_bf, j, c1, (uint32_t)a);
       float sd = sqrtf(s);
       ok = 1;
       for (int blk = 0; blk < 4; ++blk) {
@@ -823,7 +833,18 @@ typedef struct {
   int32_t max_batches;
   int32_t max_redraw;
   int32_t nthreads;
+  float mcmc_s0;        /* beta_mode 5 (MCMC baseline): initial step s      */
+  int32_t mcmc_adapt;   /* adaptation window in batches of the run; 0:      */
+                        /* ceil(max_total / 10) (or_mcmc_window)            */
 } or_smc;
+
+/* State of the MCMC baseline's tuned step, carried across generations. */
+typedef struct {
+  double s;             /* current step (variance, unit-cube coordinates)   */
+  int64_t k;            /* adaptations made so far                          */
+  int64_t batches;      /* batches of the run so far (generation 0 counts   */
+                        /* ceil(N / M), as the run budget does)             */
+} or_mcmc_state;
 
 typedef struct {
   double eps;           /* eps_t used by this generation                    */
@@ -832,11 +853,39 @@ typedef struct {
   float beta_a;
   int32_t beta_b;       /* integer b (product sampler), 0 for real shapes   */
   float beta_bf;        /* b as fp32                                        */
-  int32_t pad;
+  float mcmc_s;         /* MCMC baseline: step s after the generation       */
   int64_t batches, sims, exhausted, accepted_total;
   uint64_t total;       /* resampling total                                  */
   int32_t status;       /* 0 ok, 1 batch budget exhausted                   */
 } or_gen_stats;
+
+/*
+ * Step adaptation of the MCMC baseline (Sec. 2.4.1, Eq. 14-15; Sec. 3.1
+ * adapts once per batch of parallel simulations).  A = acc / sims is the
+ * batch's empirical acceptance (Eq. 14): of the sims proposals that passed
+ * the Metropolis-Hastings check and were simulated, acc reached d <= eps_t
+ * (A = 0 when nothing was simulated).  Eq. 15 as printed would turn s
+ * negative whenever A < A_T; it is read as the multiplicative Robbins-Monro
+ * step s_new = s_old (1 + (A - A_T) / ((1 - A_T) (k + 1))) with target
+ * A_T = 0.234 and gain 1 / (k + 1), k the adaptations made so far.  The
+ * factor lies in [1 - A_T / ((1 - A_T) (k + 1)), 1 + 1 / (k + 1)], about
+ * [0.69, 2] at k = 0, so s stays positive; it grows when more than A_T of
+ * the batch is accepted.  Plain fp64 operations, each correctly rounded.
+ */
+OR_API double or_mcmc_adapt(double s, int64_t k, int64_t acc, int64_t sims) {
+  const double A_T = 0.234;
+  const double A = sims > 0 ? (double)acc / (double)sims : 0.0;
+  const double gain = (1.0 - A_T) * (double)(k + 1);
+  return s * (1.0 + (A - A_T) / gain);
+}
+
+/* Adaptation window in batches: mcmc_adapt, or when it is 0 the first 10%
+ * of the run budget (Sec. 2.4.1 and 3.1 adapt during the first 10% of the
+ * simulation runs), 0 without a budget (the step stays at mcmc_s0). */
+OR_API int64_t or_mcmc_window(const or_smc* c) {
+  if (c->mcmc_adapt > 0) return c->mcmc_adapt;
+  return ((int64_t)c->max_total + 9) / 10;
+}
 
 /* Generation 0 (Sec. 2.4): plain ABC from the prior with eps_0 = +inf. */
 OR_API void or_generation0(const or_model* m, const or_smc* c, float* u, double* d, double* W) {
@@ -850,11 +899,18 @@ OR_API void or_generation0(const or_model* m, const or_smc* c, float* u, double*
  * prior and weights (Eq. 9-10), then batches of M proposals (Eq. 11, 16, 17),
  * simulation and acceptance d' <= eps_t, appended in (batch, slot) order
  * until N are filled; then the new weights.
+ *
+ * beta_mode 5 is the MCMC baseline (Sec. 2.4.1, 3.1): each batch walks with
+ * the run's single step s = (float) ms->s (Eq. 12), and after the batch, if
+ * fewer than or_mcmc_window batches of the run came before it, s adapts to
+ * the batch's acceptance (or_mcmc_adapt).  ms (required in that mode, NULL
+ * otherwise) carries s, the adaptation count and the run's batch count
+ * across generations.
  */
 OR_API int32_t or_generation(const or_model* m, const or_smc* c, int32_t t, double eps1_in,
                              const float* u, const double* d, const double* W, float* u_new,
                              double* d_new, double* W_new, float* s_new, int32_t* anc_new,
-                             double* logW_new, or_gen_stats* st) {
+                             double* logW_new, or_gen_stats* st, or_mcmc_state* ms) {
   int64_t N = c->N, M = c->M;
   memset(st, 0, sizeof *st);
   double eps = or_kth(d, N, or_rank(c->alpha, N));
@@ -869,6 +925,14 @@ OR_API int32_t or_generation(const or_model* m, const or_smc* c, int32_t t, doub
   st->beta_a = ba;
   st->beta_b = bb;
   st->beta_bf = shape[1];
+  const int mcmc = c->beta_mode == 5;
+  if (mcmc) {
+    if (!ms) return -1;
+    st->beta_a = (float)ms->s;
+    st->beta_b = 0;
+    st->beta_bf = 0.0f;
+  }
+  const int64_t window = or_mcmc_window(c);
   uint32_t* q = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
   uint64_t* prefix = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)N);
   uint64_t total = or_resample_prefix(d, W, N, eps, c->weight_mode, q, prefix);
@@ -883,14 +947,17 @@ OR_API int32_t or_generation(const or_model* m, const or_smc* c, int32_t t, doub
   int32_t b;
   for (b = 0; b < c->max_batches && filled < N; ++b) {
     uint32_t c1 = ((uint32_t)t << 16) | (uint32_t)b;
-    or_propose(m, u, N, prefix, total, ba, bb, shape[1], M, NULL, c1, c->max_redraw, up, sp, ap,
-               att, fl, c->nthreads);
+    const float s_fixed = mcmc ? (float)ms->s : 0.0f;
+    or_propose(m, u, N, prefix, total, ba, bb, shape[1], s_fixed, M, NULL, c1, c->max_redraw, up,
+               sp, ap, att, fl, c->nthreads);
     or_simulate(m, up, M, NULL, c1, TAG_SIM, fl, dp, NULL, c->nthreads);
     st->sims += M;
+    int64_t acc_b = 0, exh_b = 0;
     for (int64_t j = 0; j < M; ++j) {
-      if (fl[j]) st->exhausted += 1;
+      if (fl[j]) exh_b += 1;
       int acc = !fl[j] && dp[j] <= eps;
       if (!acc) continue;
+      acc_b += 1;
       st->accepted_total += 1;
       if (filled < N) {
         for (int dd = 0; dd < 8; ++dd) u_new[(int64_t)dd * N + filled] = up[(int64_t)dd * M + j];
@@ -900,8 +967,17 @@ OR_API int32_t or_generation(const or_model* m, const or_smc* c, int32_t t, doub
         filled += 1;
       }
     }
+    st->exhausted += exh_b;
+    if (mcmc) {
+      if (ms->batches < window) {
+        ms->s = or_mcmc_adapt(ms->s, ms->k, acc_b, M - exh_b);
+        ms->k += 1;
+      }
+      ms->batches += 1;
+    }
   }
   st->batches = b;
+  if (mcmc) st->mcmc_s = (float)ms->s;
   if (filled < N) {
     st->status = 1;
   } else if (c->weight_mode == 1) {
