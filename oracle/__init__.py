@@ -45,7 +45,7 @@ class Smc(C.Structure):
 
 class McmcState(C.Structure):
     """The MCMC baseline's tuned step across generations (s, adaptations
-    made, batches of the run so far)."""
+    made, batches walked with the step so far)."""
     _fields_ = [("s", C.c_double), ("k", C.c_int64), ("batches", C.c_int64)]
 
 
@@ -328,8 +328,8 @@ MCMC_MODE = 5  # beta_mode of the MCMC baseline (one tuned step, Sec. 2.4.1)
 
 def mcmc_start(c: Smc):
     """The MCMC baseline's step state after generation 0: s = mcmc_s0, no
-    adaptation yet, generation 0 counted as ceil(N / M) batches."""
-    return McmcState(float(np.float32(c.mcmc_s0)), 0, batches_gen0(c))
+    adaptation and no batch walked with the step yet."""
+    return McmcState(float(np.float32(c.mcmc_s0)), 0, 0)
 
 
 def mcmc_adapt(s, k, acc, sims):

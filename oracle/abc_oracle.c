@@ -834,16 +834,16 @@ typedef struct {
   int32_t max_redraw;
   int32_t nthreads;
   float mcmc_s0;        /* beta_mode 5 (MCMC baseline): initial step s      */
-  int32_t mcmc_adapt;   /* adaptation window in batches of the run; 0:      */
-                        /* ceil(max_total / 10) (or_mcmc_window)            */
+  int32_t mcmc_adapt;   /* adaptation window in batches that walk with the  */
+                        /* step; 0: ceil(max_total / 10) (or_mcmc_window)   */
 } or_smc;
 
 /* State of the MCMC baseline's tuned step, carried across generations. */
 typedef struct {
   double s;             /* current step (variance, unit-cube coordinates)   */
   int64_t k;            /* adaptations made so far                          */
-  int64_t batches;      /* batches of the run so far (generation 0 counts   */
-                        /* ceil(N / M), as the run budget does)             */
+  int64_t batches;      /* batches walked with the step so far (those of    */
+                        /* generations t >= 1)                              */
 } or_mcmc_state;
 
 typedef struct {
@@ -879,9 +879,13 @@ OR_API double or_mcmc_adapt(double s, int64_t k, int64_t acc, int64_t sims) {
   return s * (1.0 + (A - A_T) / gain);
 }
 
-/* Adaptation window in batches: mcmc_adapt, or when it is 0 the first 10%
- * of the run budget (Sec. 2.4.1 and 3.1 adapt during the first 10% of the
- * simulation runs), 0 without a budget (the step stays at mcmc_s0). */
+/* Adaptation window in batches: mcmc_adapt, or when it is 0 a tenth of the
+ * run budget (Sec. 2.4.1 and 3.1 adapt during the first 10% of the
+ * simulation runs), 0 without a budget (the step stays at mcmc_s0).  The
+ * window counts the batches that walk with the step, from generation 1 on:
+ * generation 0 draws from the prior and has no step to tune, and counting
+ * its ceil(N / M) batches would close the window before any step was taken
+ * whenever N / M reaches a tenth of the budget (N = 1000 at M = 10). */
 OR_API int64_t or_mcmc_window(const or_smc* c) {
   if (c->mcmc_adapt > 0) return c->mcmc_adapt;
   return ((int64_t)c->max_total + 9) / 10;
@@ -902,9 +906,9 @@ OR_API void or_generation0(const or_model* m, const or_smc* c, float* u, double*
  *
  * beta_mode 5 is the MCMC baseline (Sec. 2.4.1, 3.1): each batch walks with
  * the run's single step s = (float) ms->s (Eq. 12), and after the batch, if
- * fewer than or_mcmc_window batches of the run came before it, s adapts to
- * the batch's acceptance (or_mcmc_adapt).  ms (required in that mode, NULL
- * otherwise) carries s, the adaptation count and the run's batch count
+ * fewer than or_mcmc_window batches walked with the step before it, s
+ * adapts to the batch's acceptance (or_mcmc_adapt).  ms (required in that
+ * mode, NULL otherwise) carries s, the adaptation count and the batch count
  * across generations.
  */
 OR_API int32_t or_generation(const or_model* m, const or_smc* c, int32_t t, double eps1_in,
