@@ -75,6 +75,15 @@ extern "C" {
 #define ABC_BETA_REAL 2         /* s ~ Beta(beta_p1, beta_p2), real shapes in [2^-20, 2^20] */
 #define ABC_BETA_MEAN_VAR 3     /* mean p1 ratio, variance p2 / t; a + b at least 1/16    */
 #define ABC_BETA_MODE_CONC 4    /* mode p1 ratio, concentration a + b = p2 t              */
+/* Not a Beta rule: the paper's comparison method, P-ABC-SMC MCMC (Sec.
+ * 2.4.1, 3.1).  Every proposal walks with the run's single step s (Eq. 12;
+ * a variance in unit-cube coordinates), starting at mcmc_s0 and adapted
+ * after each batch during the adaptation window (Eq. 14-15, see
+ * mcmc_adapt).  With the uniform prior and the symmetric walk the
+ * Metropolis-Hastings ratio of Eq. 13 is the support indicator, so its
+ * accept/reject step is the redraw of proposals outside [0,1]^8.  Runs one
+ * batch per round (spec_batches is ignored) and takes no surrogate. */
+#define ABC_STEP_MCMC 5
 #define ABC_W_PAPER 0           /* resampling weights eps_t - d (Eq. 10), W = 1/N         */
 #define ABC_W_IMPORTANCE 1      /* importance weights with the O(N^2) kernel sum          */
 #define ABC_P_FP32 0            /* O(N^2) weight sum on CUDA cores in fp32                */
@@ -162,6 +171,18 @@ typedef struct {
    * nothing, and a batched run stops like one whose run budget is used up.
    * 0: no target.  (abc_run's eps_target does the same for one call.) */
   float eps_stop;
+  /* ABC_STEP_MCMC: initial step s0 > 0 (variance in unit-cube coordinates),
+   * and the adaptation window in batches that walk with the step (those of
+   * generations t >= 1; generation 0 has no step).  After each such batch
+   * b = 0, 1, ... with b < window, s <- s (1 + (A - A_T) / ((1 - A_T)(k + 1)))
+   * in fp64, A = accepted / simulated slots of the batch (0 if none),
+   * A_T = 0.234, k = adaptations so far; proposals use (float) s.  Eq. 15 as
+   * printed would make s negative whenever A < A_T: this is its reading as
+   * a multiplicative Robbins-Monro step.  mcmc_adapt = 0 gives the paper's
+   * window, 10% of the run budget: ceil(max_total_batches / 10) (0, no
+   * adaptation, without a budget). */
+  float mcmc_s0;
+  int32_t mcmc_adapt;
 } abc_config;
 
 /* Fill a config with the paper's defaults (SAIRD, binomial flows, alpha 0.5,
@@ -254,7 +275,9 @@ ABC_API int abc_resample_prefix_noalloc(const double* d, const double* W, int64_
  * _MODE_CONC) beta_a and beta_b are ignored: the shapes follow from
  * cfg->beta_p1, cfg->beta_p2, the ratio and the stage t = c1 >> 16 (t >= 1
  * for the last two), and s is drawn by the Gamma ratio (BETA stream, c2 =
- * a << 8 | block, blocks 0..63 for X and 64..127 for Y).
+ * a << 8 | block, blocks 0..63 for X and 64..127 for Y).  Under
+ * ABC_STEP_MCMC every slot walks with s = beta_a > 0 and no BETA block is
+ * read (beta_b ignored).
  * u: device float [8][n]; prefix: device u64[n]; eps, eps1: device double[1]
  * (read by the paper, mean-variance and mode-concentration rules; may be
  * NULL otherwise); outputs: device
@@ -408,8 +431,8 @@ typedef struct {
   double eps;               /* eps_t used for acceptance (+inf for t = 0)           */
   double eps1;              /* eps_1 (0 before generation 1)                        */
   double ess;               /* effective sample size of the new population          */
-  float beta_a;             /* step-size Beta shape used (a_t, b_t)                 */
-  int32_t beta_b;
+  float beta_a;             /* step-size Beta shape used (a_t, b_t); ABC_STEP_MCMC:  */
+  int32_t beta_b;           /*   beta_a = s of the first batch, beta_b = 0           */
   int64_t batches;          /* batches of M proposals run                           */
   int64_t sims;             /* simulations run (flagged slots excluded)             */
   int64_t sim_days;         /* particle-days simulated                              */
@@ -430,7 +453,8 @@ typedef struct {
   double ms_tc;             /* device time of the tensor-core weight kernel          */
   double ms_fp32;           /* device time of the FP32 weight kernel                 */
   float beta_bf;            /* b_t as fp32 (beta_b is 0 under the real-shape rules)  */
-  int32_t pad_s;
+  float mcmc_s;             /* ABC_STEP_MCMC: the step s after the generation's      */
+                            /*   batches (beta_a: s of its first batch)              */
   int64_t rows_exp;         /* rows whose tensor-core sums were kept (error bound    */
                             /*   small enough); the rest of rows_tc were refined    */
   int64_t pairs_tc;         /* (row, column) pairs in the tiles the tensor-core      */

@@ -20,6 +20,7 @@ ABC_NOALLOC_MAX_N = 1 << 24
 ABC_MODEL_SAIRD, ABC_MODEL_GAUSS_TOY = 0, 1
 ABC_SIM_BINOMIAL, ABC_SIM_PAPER_NORMAL = 0, 1
 ABC_BETA_PAPER, ABC_BETA_FIXED, ABC_BETA_REAL, ABC_BETA_MEAN_VAR, ABC_BETA_MODE_CONC = 0, 1, 2, 3, 4
+ABC_STEP_MCMC = 5  # the MCMC-tuned single step (the paper's comparison method)
 ABC_W_PAPER, ABC_W_IMPORTANCE = 0, 1
 ABC_P_FP32, ABC_P_BF16_TC = 0, 1
 TAG_PRIOR, TAG_ANCESTOR, TAG_BETA, TAG_WALK, TAG_SIM, TAG_SCREEN, TAG_AUDIT = 0, 1, 2, 3, 4, 5, 6
@@ -59,7 +60,8 @@ class AbcConfig(C.Structure):
         ("surrogate_batch", C.c_int32), ("surrogate_lr", C.c_float), ("surrogate_tau", C.c_float),
         ("surrogate_rho_min", C.c_float), ("audit_frac", C.c_float), ("surrogate_ring", C.c_int32),
         ("beta_p1", C.c_float), ("beta_p2", C.c_float), ("max_total_batches", C.c_int32),
-        ("spec_batches", C.c_int32), ("eps_stop", C.c_float),
+        ("spec_batches", C.c_int32), ("eps_stop", C.c_float), ("mcmc_s0", C.c_float),
+        ("mcmc_adapt", C.c_int32),
     ]
 
 
@@ -73,7 +75,7 @@ class AbcGenStats(C.Structure):
         ("ms_weights", C.c_double), ("screened", C.c_int64), ("audited", C.c_int64),
         ("audit_accepted", C.c_int64), ("train_loss", C.c_double), ("ms_screen", C.c_double),
         ("ms_train", C.c_double), ("rows_tc", C.c_int64), ("ms_tc", C.c_double),
-        ("ms_fp32", C.c_double), ("beta_bf", C.c_float), ("pad_s", C.c_int32),
+        ("ms_fp32", C.c_double), ("beta_bf", C.c_float), ("mcmc_s", C.c_float),
         ("rows_exp", C.c_int64), ("pairs_tc", C.c_int64),
     ]
 

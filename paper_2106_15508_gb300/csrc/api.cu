@@ -99,7 +99,12 @@ void stage_shapes(const abc_config& c, double eps, double eps1, int32_t t, int32
                   abc_gen_stats* g) {
   const float ratio = eps1 > 0.0 ? static_cast<float>(eps / eps1) : 1.0f;
   const BetaRule r = beta_rule(c);
-  if (c.beta_mode >= ABC_BETA_REAL || (c.beta_mode == ABC_BETA_PAPER && bb == 0)) {
+  if (c.beta_mode == ABC_STEP_MCMC) {
+    // the step itself is read from the device (mcmc_stats)
+    g->beta_a = 0.0f;
+    g->beta_b = 0;
+    g->beta_bf = 0.0f;
+  } else if (c.beta_mode >= ABC_BETA_REAL || (c.beta_mode == ABC_BETA_PAPER && bb == 0)) {
     beta_real_shape(r, ratio, t, &g->beta_a, &g->beta_bf);
     g->beta_b = 0;
   } else {
@@ -121,6 +126,9 @@ int check_smc(const abc_config* c) {
   if (!(c->eps_stop >= 0.0f && c->eps_stop < INFINITY)) return ABC_E_INVAL;
   if (c->spec_batches < 0 || c->spec_batches > 256) return ABC_E_INVAL;
   if (c->max_redraw < 1 || c->max_redraw > (1 << 23)) return ABC_E_INVAL;
+  if (c->beta_mode == ABC_STEP_MCMC &&
+      (!(c->mcmc_s0 > 0.0f && c->mcmc_s0 < INFINITY) || c->mcmc_adapt < 0 || c->surrogate))
+    return ABC_E_INVAL;
   if (c->surrogate) {
     if (c->surrogate != 1 || c->surrogate_start < 1 || c->surrogate_steps < 0 ||
         c->surrogate_batch < 32 || c->surrogate_batch > 65536 || !(c->surrogate_lr > 0.0f) ||
@@ -151,6 +159,7 @@ ABC_API void abc_config_default(abc_config* c) {
   c->n_particles = 1000;
   c->survival_alpha = 0.5;
   c->beta_mode = ABC_BETA_PAPER;
+  c->mcmc_s0 = 0.1f;
   c->beta_a = 2.0f;
   c->beta_b = 5;
   c->weight_mode = ABC_W_PAPER;
@@ -510,6 +519,7 @@ struct abc_ctx {
   long long* simulated = nullptr; // slots simulated in this generation (device)
   unsigned* inf_err = nullptr;    // error word of the tensor-core inference (device)
   cudaEvent_t eq0 = nullptr, eq1 = nullptr, et0 = nullptr, et1 = nullptr;
+  McmcDev* mcmc = nullptr;        // ABC_STEP_MCMC: the run's tuned step (device)
 
   template <typename T>
   int alloc(T** ptr, size_t count) {
@@ -533,8 +543,38 @@ struct abc_ctx {
 
 namespace {
 
-// batches per device loop round of graph-captured batches (spec_batches)
-int spec_k(const abc_config& c) { return c.spec_batches > 1 ? c.spec_batches : 1; }
+// batches per device loop round of graph-captured batches (spec_batches);
+// the MCMC baseline's step changes between batches: one per round
+int spec_k(const abc_config& c) {
+  return c.spec_batches > 1 && c.beta_mode != ABC_STEP_MCMC ? c.spec_batches : 1;
+}
+
+// The MCMC baseline's step state after generation 0: s = mcmc_s0, no
+// adaptation and no batch walked with the step yet; the window is
+// mcmc_adapt, or a tenth of the run budget.
+McmcDev mcmc_start(const abc_config& c) {
+  McmcDev m{};
+  m.s = static_cast<double>(c.mcmc_s0);
+  m.k = 0;
+  m.batches = 0;
+  m.window = c.mcmc_adapt > 0 ? c.mcmc_adapt : ceil_div(int64_t(c.max_total_batches), int64_t(10));
+  m.s_f = c.mcmc_s0;
+  m.s_start = c.mcmc_s0;
+  return m;
+}
+
+// beta_a = the step of the generation's first batch, mcmc_s = the step after it
+int mcmc_stats(const abc_ctx* c, abc_gen_stats* g) {
+  if (!c->mcmc) return ABC_OK;
+  McmcDev m{};
+  ABC_CUDA_TRY(cudaMemcpyAsync(&m, c->mcmc, sizeof m, cudaMemcpyDeviceToHost, c->st));
+  ABC_CUDA_TRY(cudaStreamSynchronize(c->st));
+  g->beta_a = m.s_start;
+  g->beta_b = 0;
+  g->beta_bf = 0.0f;
+  g->mcmc_s = m.s_f;
+  return ABC_OK;
+}
 
 int ctx_alloc(abc_ctx* c) {
   const size_t N = static_cast<size_t>(c->N);
@@ -568,6 +608,7 @@ int ctx_alloc(abc_ctx* c) {
   }
   ABC_ALLOC(c->scal, 4);
   ABC_ALLOC(c->cnt, 4);
+  if (c->cfg.beta_mode == ABC_STEP_MCMC) ABC_ALLOC(c->mcmc, 1);
   if (c->cfg.surrogate) {
     const int B = c->cfg.surrogate_batch;
     c->ring_cap = c->cfg.surrogate_ring > 0
@@ -690,6 +731,11 @@ int generation0(abc_ctx* c) {
   if ((rc = launch_fill(c->W[cur], c->N, 1.0 / static_cast<double>(c->N), st))) return rc;
   ABC_CUDA_TRY(cudaMemsetAsync(c->anc[cur], 0xFF, sizeof(int32_t) * c->N, st));
   ABC_CUDA_TRY(cudaMemsetAsync(c->s[cur], 0, sizeof(float) * c->N, st));
+  McmcDev m0{};
+  if (c->mcmc) {
+    m0 = mcmc_start(c->cfg);
+    ABC_CUDA_TRY(cudaMemcpyAsync(c->mcmc, &m0, sizeof m0, cudaMemcpyHostToDevice, st));
+  }
   abc_gen_stats g{};
   g.generation = 0;
   g.status = ABC_OK;
@@ -746,6 +792,8 @@ int generation_t(abc_ctx* c) {
     inf_err = c->inf_err;
     ABC_CUDA_TRY(cudaMemsetAsync(inf_err, 0, sizeof(unsigned), st));
   }
+  if (c->mcmc && (rc = launch_mcmc_begin(c->mcmc, nullptr, st))) return rc;
+  const float* s_fix = c->mcmc ? &c->mcmc->s_f : nullptr;
   int64_t filled = 0;
   double ms_sim = 0.0, ms_screen = 0.0;
   int32_t b = 0;
@@ -782,7 +830,8 @@ int generation_t(abc_ctx* c) {
       continue;
     }
     rc = launch_propose(c->p, c->u[cur], c->N, c->prefix, rule, eps, eps1, c->M, nullptr, c1,
-                        c->cfg.max_redraw, c->up, c->sp, c->ap, c->att, c->flag, st);
+                        c->cfg.max_redraw, c->up, c->sp, c->ap, c->att, c->flag, st, nullptr,
+                        nullptr, nullptr, 0, nullptr, s_fix);
     if (rc) return rc;
     if (sur) {
       // delayed acceptance (a pass-all until the surrogate is trained):
@@ -803,6 +852,11 @@ int generation_t(abc_ctx* c) {
                          c->s[nxt], c->anc[nxt], c->cnt, c->cnt + 1, c->scratch, c->scratch_bytes,
                          st);
       if (rc) return rc;
+      // the MCMC baseline adapts its step to this batch's acceptance
+      if (c->mcmc &&
+          (rc = launch_mcmc_adapt(c->mcmc, reinterpret_cast<const long long*>(c->cnt + 1), c->M,
+                                  nullptr, st)))
+        return rc;
     }
     ABC_CUDA_TRY(cudaMemcpyAsync(&filled, c->cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     ABC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -919,6 +973,7 @@ int generation_t(abc_ctx* c) {
   g.eps1 = h_scal[1];
   g.ess = g.status == ABC_OK ? h_scal[2] : 0.0;
   stage_shapes(c->cfg, h_scal[0], h_scal[1], t, bb, &g);
+  if ((rc = mcmc_stats(c, &g))) return rc;
   c->eps1_host = h_scal[1];
   if (sur && g.status == ABC_OK && c->cfg.surrogate_steps > 0) {
     // train on everything simulated so far (the ring keeps the latest pairs)
@@ -1125,13 +1180,18 @@ struct StateHeader {
   double eps1;
   int64_t batches_total;  // run budget count
 };
+// ABC_STEP_MCMC state after the population: s (f64), k and batches (i64)
+constexpr size_t kMcmcTrailer = sizeof(double) + 2 * sizeof(long long);
 }  // namespace
 
 ABC_API int abc_get_state(abc_ctx* c, void* buf, size_t* len) {
   if (!c || !len) return ABC_E_INVAL;
   const size_t N = static_cast<size_t>(c->N);
-  const size_t need = sizeof(StateHeader) + N * (8 * sizeof(float) + 2 * sizeof(double) +
-                                                 sizeof(float) + sizeof(int32_t));
+  // the MCMC baseline's step state (s, adaptations, batches) trails the population
+  const size_t need = sizeof(StateHeader) +
+                      N * (8 * sizeof(float) + 2 * sizeof(double) + sizeof(float) +
+                           sizeof(int32_t)) +
+                      (c->mcmc ? kMcmcTrailer : 0);
   if (!buf) {
     *len = need;
     return ABC_OK;
@@ -1159,7 +1219,16 @@ ABC_API int abc_get_state(abc_ctx* c, void* buf, size_t* len) {
   ABC_CUDA_TRY(cudaMemcpyAsync(p, c->s[k], N * sizeof(float), cudaMemcpyDeviceToHost, c->st));
   p += N * sizeof(float);
   ABC_CUDA_TRY(cudaMemcpyAsync(p, c->anc[k], N * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+  McmcDev m{};
+  if (c->mcmc)
+    ABC_CUDA_TRY(cudaMemcpyAsync(&m, c->mcmc, sizeof m, cudaMemcpyDeviceToHost, c->st));
   ABC_CUDA_TRY(cudaStreamSynchronize(c->st));
+  if (c->mcmc) {
+    p += N * sizeof(int32_t);
+    const long long kb[2] = {m.k, m.batches};
+    std::memcpy(p, &m.s, sizeof(double));
+    std::memcpy(p + sizeof(double), kb, sizeof kb);
+  }
   *len = need;
   return ABC_OK;
 }
@@ -1169,8 +1238,10 @@ ABC_API int abc_set_state(abc_ctx* c, const void* buf, size_t len) {
   StateHeader h;
   std::memcpy(&h, buf, sizeof h);
   const size_t N = static_cast<size_t>(c->N);
-  const size_t need = sizeof(StateHeader) + N * (8 * sizeof(float) + 2 * sizeof(double) +
-                                                 sizeof(float) + sizeof(int32_t));
+  const size_t need = sizeof(StateHeader) +
+                      N * (8 * sizeof(float) + 2 * sizeof(double) + sizeof(float) +
+                           sizeof(int32_t)) +
+                      (c->mcmc ? kMcmcTrailer : 0);
   if (std::memcmp(h.magic, "ABCSMC02", 8) != 0 || h.N != c->N || h.T != c->T || len < need ||
       h.gen < 1 || h.gen > 32767 || h.batches_total < 0)
     return ABC_E_STATE;
@@ -1185,6 +1256,20 @@ ABC_API int abc_set_state(abc_ctx* c, const void* buf, size_t len) {
   ABC_CUDA_TRY(cudaMemcpyAsync(c->s[k], p, N * sizeof(float), cudaMemcpyHostToDevice, c->st));
   p += N * sizeof(float);
   ABC_CUDA_TRY(cudaMemcpyAsync(c->anc[k], p, N * sizeof(int32_t), cudaMemcpyHostToDevice, c->st));
+  McmcDev m{};
+  if (c->mcmc) {
+    p += N * sizeof(int32_t);
+    long long kb[2];
+    m = mcmc_start(c->cfg);
+    std::memcpy(&m.s, p, sizeof(double));
+    std::memcpy(kb, p + sizeof(double), sizeof kb);
+    if (!(m.s > 0.0 && m.s < INFINITY) || kb[0] < 0 || kb[1] < 0) return ABC_E_STATE;
+    m.k = kb[0];
+    m.batches = kb[1];
+    m.s_f = static_cast<float>(m.s);
+    m.s_start = m.s_f;
+    ABC_CUDA_TRY(cudaMemcpyAsync(c->mcmc, &m, sizeof m, cudaMemcpyHostToDevice, c->st));
+  }
   ABC_CUDA_TRY(cudaMemcpyAsync(c->scal + 1, &h.eps1, sizeof(double), cudaMemcpyHostToDevice, c->st));
   ABC_CUDA_TRY(cudaStreamSynchronize(c->st));
   c->gen = h.gen;
@@ -1211,6 +1296,7 @@ RunCtxView ctx_view(abc_ctx* c) {
   v.N = c->N;
   v.M = c->M;
   v.K = spec_k(c->cfg);
+  v.mcmc = c->mcmc;
   int64_t k = static_cast<int64_t>(std::ceil(c->cfg.survival_alpha * static_cast<double>(c->N)));
   v.rank = std::min<int64_t>(std::max<int64_t>(k, 1), c->N);
   v.beta = beta_rule(c->cfg);
@@ -1466,6 +1552,7 @@ ABC_API int abc_batch_generation(abc_batch* b) {
     g.eps1 = d.eps1;
     g.ess = d.status == ABC_OK ? d.ess : 0.0;
     stage_shapes(c->cfg, d.eps, d.eps1, g.generation, d.beta_b, &g);
+    if (int rc = mcmc_stats(c, &g)) return rc;
     g.batches = d.batches;
     g.accepted = d.accepted;
     g.exhausted = d.exhausted;

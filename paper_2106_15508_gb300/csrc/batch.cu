@@ -184,6 +184,7 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
   const int fixed_b = v.beta.mode == ABC_BETA_FIXED ? v.beta.b : 0;
   k_run_start<<<1, 32, 0, st>>>(r, v.beta.mode == ABC_BETA_PAPER, fixed_b, v.K, h);
   ABC_LAUNCH_CHECK();
+  if (v.mcmc && (rc = launch_mcmc_begin(v.mcmc, &r->off, st))) return rc;
   const SurView& sv = v.sur;
   if (sv.on) {
     // screening from generation `start` once trained; this generation's counters
@@ -219,7 +220,8 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
   const int64_t slots = v.M * v.K;
   rc = launch_propose(v.p, v.u_cur, v.N, v.prefix, v.beta, &r->eps, &r->eps1, slots, nullptr, 0u,
                       v.max_redraw, v.up, v.sp, v.ap, v.att, v.flag, body_st, &r->c1, &r->beta_b,
-                      &r->off, spec ? v.M : 0, spec ? &r->k_lim : nullptr);
+                      &r->off, spec ? v.M : 0, spec ? &r->k_lim : nullptr,
+                      v.mcmc ? &v.mcmc->s_f : nullptr);
   if (!rc && sv.on) {
     // the surrogate screens the batch (a pass-all until it is trained)
     rc = screened_batch(sv, v.p, v.obs, v.up, v.sp, v.ap, v.flag, v.M, &r->eps, 0u, &r->c1, v.N,
@@ -241,6 +243,8 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
                          v.s_nxt, v.a_nxt, reinterpret_cast<int64_t*>(&r->filled),
                          reinterpret_cast<int64_t*>(&r->accepted), v.scratch, v.scratch_bytes,
                          body_st);
+    // the MCMC baseline adapts its step to this batch's acceptance
+    if (!rc && v.mcmc) rc = launch_mcmc_adapt(v.mcmc, &r->accepted, v.M, &r->off, body_st);
   }
   if (!rc) {
     k_run_cond<<<1, 32, 0, body_st>>>(r, v.N, v.K, h);

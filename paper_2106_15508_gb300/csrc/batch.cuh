@@ -80,6 +80,7 @@ struct RunCtxView {
   void* scratch;
   size_t scratch_bytes;
   SurView sur;
+  McmcDev* mcmc;  // ABC_STEP_MCMC: the run's tuned step (else null)
 };
 
 struct BatchRun {
@@ -135,7 +136,13 @@ int launch_propose(const SimParams&, const float*, int64_t, const uint64_t*, con
                    float*, int32_t*, int32_t*, uint8_t*, cudaStream_t,
                    const uint32_t* c1_dev = nullptr, const int* beta_b_dev = nullptr,
                    const int* off_dev = nullptr, int64_t m_sub = 0,
-                   const int* k_lim_dev = nullptr);
+                   const int* k_lim_dev = nullptr, const float* s_fix_dev = nullptr);
+// The MCMC baseline's step (ABC_STEP_MCMC): the start of a generation, and
+// the adaptation after a batch of M slots given the generation's {accepted,
+// exhausted} counters.  off_dev (nullable): a finished run does nothing.
+int launch_mcmc_begin(McmcDev* m, const int* off_dev, cudaStream_t st);
+int launch_mcmc_adapt(McmcDev* m, const long long* acc_exh, int64_t M, const int* off_dev,
+                      cudaStream_t st);
 size_t accept_spec_scratch_bytes(int64_t M, int K);
 int launch_accept_spec(const float*, const double*, const float*, const int32_t*,
                        const uint8_t*, int64_t M, int K, const int* k_lim_dev, const double*,

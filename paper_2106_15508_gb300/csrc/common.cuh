@@ -132,6 +132,19 @@ struct BetaRule {
   float p1, p2;
 };
 
+// The MCMC baseline's single step (ABC_STEP_MCMC, Sec. 2.4.1 and 3.1), kept
+// on the device so that graph-captured batch loops adapt it between batches.
+struct McmcDev {
+  double s;            // current step (variance, unit-cube coordinates)
+  long long k;         // adaptations made so far
+  long long batches;   // batches walked with the step so far (generations >= 1)
+  long long window;    // batches of the run that adapt
+  long long acc_prev;  // the generation's accepted / exhausted counters after
+  long long exh_prev;  //   the previous batch
+  float s_f;           // (float) s, the step the next batch walks with
+  float s_start;       // the step of the generation's first batch
+};
+
 // Shapes of a real-shape rule (ABC_BETA_REAL, _MEAN_VAR, _MODE_CONC) at stage
 // t >= 1 with ratio = eps_t / eps_1 in fp32:
 //   real:  (p1, p2);

@@ -296,6 +296,8 @@ bool beta_rule_ok(const BetaRule& r) {
       return r.p1 > 0.0f && r.p1 < 1.0f && r.p2 > 0.0f && r.p2 <= 1.0f;
     case ABC_BETA_MODE_CONC:
       return r.p1 >= 0.0f && r.p1 <= 1.0f && r.p2 >= 2.0f && r.p2 <= 0x1p20f;
+    case ABC_STEP_MCMC:
+      return true;  // the step is checked where it is given
     default:
       return false;
   }
@@ -308,7 +310,8 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
                           int32_t* __restrict__ anc_out, int32_t* __restrict__ att_out,
                           uint8_t* __restrict__ flag_out, const uint32_t* __restrict__ c1_dev,
                           const int* __restrict__ beta_b_dev, const int* __restrict__ off_dev,
-                          int64_t m_sub, const int* __restrict__ k_lim_dev) {
+                          int64_t m_sub, const int* __restrict__ k_lim_dev,
+                          const float* __restrict__ s_fix_dev) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= slots) return;
   if (off_dev && *off_dev) return;          // run finished
@@ -330,7 +333,10 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
   const unsigned long long total = prefix[n - 1];
   float a_t = rule.a, b_t = 0.0f;
   float ratio = 1.0f;
-  if (rule.mode != ABC_BETA_FIXED && rule.mode != ABC_BETA_REAL) {
+  // the MCMC baseline: one step for every slot and attempt (Eq. 12)
+  const bool fixed_step = rule.mode == ABC_STEP_MCMC;
+  const float s_fix = fixed_step ? (s_fix_dev ? *s_fix_dev : rule.a) : 0.0f;
+  if (rule.mode != ABC_BETA_FIXED && rule.mode != ABC_BETA_REAL && !fixed_step) {
     // Eq. 16: eps_t / eps_1 (1 when eps_1 is zero)
     const double e1 = *eps1_p;
     ratio = e1 > 0.0 ? __double2float_rn(__ddiv_rn(*eps_p, e1)) : 1.0f;
@@ -338,8 +344,8 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
   if (rule.mode == ABC_BETA_PAPER) a_t = ratio;
   // the Gamma ratio: the real-shape rules, and the paper schedule once b =
   // 2t passes 1024 (integer b 0)
-  const bool real_shape =
-      rule.mode >= ABC_BETA_REAL || (rule.mode == ABC_BETA_PAPER && beta_b == 0);
+  const bool real_shape = (rule.mode >= ABC_BETA_REAL && rule.mode <= ABC_BETA_MODE_CONC) ||
+                          (rule.mode == ABC_BETA_PAPER && beta_b == 0);
   if (real_shape) beta_real_shape(rule, ratio, static_cast<int32_t>(c1 >> 16), &a_t, &b_t);
   float up[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   float s = 0.0f;
@@ -358,7 +364,9 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
       else lo = mid + 1;
     }
     anc = lo;
-    if (real_shape) {
+    if (fixed_step) {
+      s = s_fix;
+    } else if (real_shape) {
       // real shapes: the Gamma ratio
       s = dev_beta_real(a_t, b_t, j, c1, static_cast<uint32_t>(a), p.k0, p.k1);
     } else {
@@ -405,8 +413,12 @@ int launch_propose(const SimParams& p, const float* u, int64_t n, const uint64_t
                    const uint32_t* c0_idx, uint32_t c1, int max_redraw, float* u_out,
                    float* s_out, int32_t* anc_out, int32_t* att_out, uint8_t* flag_out,
                    cudaStream_t st, const uint32_t* c1_dev, const int* beta_b_dev,
-                   const int* off_dev, int64_t m_sub, const int* k_lim_dev) {
+                   const int* off_dev, int64_t m_sub, const int* k_lim_dev,
+                   const float* s_fix_dev) {
   if (n <= 0 || slots < 0 || max_redraw < 1 || !beta_rule_ok(rule) || m_sub < 0)
+    return ABC_E_INVAL;
+  // the MCMC baseline's step: the device word, or rule.a > 0 (finite)
+  if (rule.mode == ABC_STEP_MCMC && !s_fix_dev && !(rule.a > 0.0f && rule.a < INFINITY))
     return ABC_E_INVAL;
   if (rule.mode == ABC_BETA_FIXED && !beta_b_dev && (rule.b < 1 || rule.b > 1024))
     return ABC_E_INVAL;
@@ -415,7 +427,8 @@ int launch_propose(const SimParams& p, const float* u, int64_t n, const uint64_t
   if (rule.mode == ABC_BETA_PAPER && !beta_b_dev &&
       (rule.b < 0 || rule.b > 1024 || (rule.b == 0 && !c1_dev && (c1 >> 16) == 0)))
     return ABC_E_INVAL;
-  if (rule.mode != ABC_BETA_FIXED && rule.mode != ABC_BETA_REAL && (!eps || !eps1))
+  if (rule.mode != ABC_BETA_FIXED && rule.mode != ABC_BETA_REAL && rule.mode != ABC_STEP_MCMC &&
+      (!eps || !eps1))
     return ABC_E_INVAL;
   // the scheduled real-shape rules read the stage t = c1 >> 16 >= 1
   if ((rule.mode == ABC_BETA_MEAN_VAR || rule.mode == ABC_BETA_MODE_CONC) && !c1_dev &&
@@ -424,7 +437,60 @@ int launch_propose(const SimParams& p, const float* u, int64_t n, const uint64_t
   if (slots == 0) return ABC_OK;
   k_propose<<<static_cast<unsigned>(ceil_div(slots, 128)), 128, 0, st>>>(
       p, u, n, prefix, rule, eps, eps1, slots, c0_idx, c1, max_redraw, u_out, s_out, anc_out,
-      att_out, flag_out, c1_dev, beta_b_dev, off_dev, m_sub, k_lim_dev);
+      att_out, flag_out, c1_dev, beta_b_dev, off_dev, m_sub, k_lim_dev, s_fix_dev);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+// ------------------------------------------------ MCMC step adaptation ---
+// Start of a generation: its accepted / exhausted counters start at zero,
+// and the step of its first batch is recorded for the statistics.
+__global__ void k_mcmc_begin(McmcDev* m, const int* off_dev) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (off_dev && *off_dev) return;
+  m->acc_prev = 0;
+  m->exh_prev = 0;
+  m->s_start = m->s_f;
+}
+
+// After a batch of M slots (Sec. 3.1 adapts once per batch; Eq. 14-15):
+// the batch's accepted and exhausted counts are the growth of the
+// generation's counters acc_exh = {accepted, exhausted}; A = accepted /
+// simulated (0 if none was simulated); inside the window s <- s (1 + (A -
+// A_T) / ((1 - A_T)(k + 1))), A_T = 0.234, each operation rounded once in
+// fp64 (no contraction).
+__global__ void k_mcmc_adapt(McmcDev* m, const long long* acc_exh, long long M,
+                             const int* off_dev) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (off_dev && *off_dev) return;
+  const long long acc = acc_exh[0], exh = acc_exh[1];
+  const long long acc_b = acc - m->acc_prev, exh_b = exh - m->exh_prev;
+  m->acc_prev = acc;
+  m->exh_prev = exh;
+  if (m->batches < m->window) {
+    const double kTarget = 0.234;
+    const long long sims = M - exh_b;
+    const double A = sims > 0 ? __ddiv_rn(static_cast<double>(acc_b), static_cast<double>(sims))
+                              : 0.0;
+    const double gain = __dmul_rn(__dsub_rn(1.0, kTarget), static_cast<double>(m->k + 1));
+    m->s = __dmul_rn(m->s, __dadd_rn(1.0, __ddiv_rn(__dsub_rn(A, kTarget), gain)));
+    m->k += 1;
+    m->s_f = __double2float_rn(m->s);
+  }
+  m->batches += 1;
+}
+
+int launch_mcmc_begin(McmcDev* m, const int* off_dev, cudaStream_t st) {
+  if (!m) return ABC_E_INVAL;
+  k_mcmc_begin<<<1, 32, 0, st>>>(m, off_dev);
+  ABC_LAUNCH_CHECK();
+  return ABC_OK;
+}
+
+int launch_mcmc_adapt(McmcDev* m, const long long* acc_exh, int64_t M, const int* off_dev,
+                      cudaStream_t st) {
+  if (!m || !acc_exh || M < 1) return ABC_E_INVAL;
+  k_mcmc_adapt<<<1, 32, 0, st>>>(m, acc_exh, M, off_dev);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

@@ -1,8 +1,10 @@
 """Parallelism sweep (Sec. 4.1, experiment setup and Fig. 3).
 
-The paper runs P-ABC-SMC BDSS at five degrees of parallelism (10, 100, 1k,
-10k and 100k simulations per simulation run, i.e. per batch of M parallel
-simulations), ten independent trials each, collecting 1000 samples.  Each
+The paper runs P-ABC-SMC BDSS and its baseline P-ABC-SMC MCMC (one
+MH-tuned step, Sec. 2.4.1 and 3.1) at five degrees of parallelism (10, 100,
+1k, 10k and 100k simulations per simulation run, i.e. per batch of M
+parallel simulations), ten independent trials each, collecting 1000
+samples.  Each
 trial stops on the stage that reached 1000 simulation runs and lets that
 stage finish.  Per stage it records the tolerance reached, and it judges the
 levels by the best tolerance, the simulation runs needed to reach it and the
@@ -23,11 +25,12 @@ import math
 
 import numpy as np
 
-from . import (ABC_OK, ABC_STOP_BUDGET, ABC_W_PAPER, AbcError, abc_batch_free,
+from . import (ABC_OK, ABC_STEP_MCMC, ABC_STOP_BUDGET, ABC_W_PAPER, AbcError, abc_batch_free,
                abc_batch_get_stats, abc_batch_init, abc_batch_run)
 from . import workloads as WL
 
 LEVELS = (10, 100, 1000, 10000, 100000)
+METHODS = ("bdss", "mcmc")
 
 
 @dataclasses.dataclass
@@ -42,6 +45,7 @@ class Curve:
     launches: int      # kernels launched for the run
     status: int        # of the last stage: ABC_OK, or ABC_STOP_BUDGET
     group_s: float = 0.0  # wall time of the batch the run was part of
+    method: str = "bdss"  # "bdss" (Beta step sizes) or "mcmc" (one tuned step)
 
 
 def spec_for(M, target=65536, cap=64):
@@ -52,16 +56,29 @@ def spec_for(M, target=65536, cap=64):
 
 
 def sweep_configs(levels=LEVELS, trials=10, N=1000, budget=1000, T=120, P=10_000_000, seed=1,
-                  max_batches=65535, spec_target=65536):
+                  max_batches=65535, spec_target=65536, method="bdss", mcmc_s0=0.1):
     """One config per (level, trial): N samples, M = level, the run budget,
-    the paper's Beta schedule and weights (Eq. 10, 16); run ids 0, 1, ...
-    give every trial its own Philox key.  Small levels run several batches
-    per round (spec_for; results unchanged); spec_target 0 runs one."""
+    the paper's weights (Eq. 10) and, for method "bdss", its Beta schedule
+    (Eq. 16); for "mcmc" the baseline's single step, started at mcmc_s0 and
+    adapted during the first tenth of the run budget (Sec. 2.4.1, 3.1).
+    Run ids 0, 1, ... give every trial of a method its own Philox key.
+    Small BDSS levels run several batches per round (spec_for; results
+    unchanged); spec_target 0 runs one.  The baseline runs one batch per
+    round (its step changes between batches)."""
+    if method not in METHODS:
+        raise ValueError("method must be one of %s" % (METHODS,))
     w = WL.Workload("sweep", N=N, T=T, P=P, G=0, weight_mode=ABC_W_PAPER,
                     max_batches=max_batches, seed=seed)
+    extra = dict(beta_mode=ABC_STEP_MCMC, mcmc_s0=mcmc_s0, mcmc_adapt=0) \
+        if method == "mcmc" else {}
     return [w.config(batch_size=M, max_total_batches=budget, run_id=li * trials + k,
-                     spec_batches=spec_for(M, spec_target) if spec_target else 1)
+                     spec_batches=spec_for(M, spec_target) if spec_target and method == "bdss"
+                     else 1, **extra)
             for li, M in enumerate(levels) for k in range(trials)]
+
+
+def method_of(cfg):
+    return "mcmc" if cfg.beta_mode == ABC_STEP_MCMC else "bdss"
 
 
 def _curve(b, r, cfg, trial):
@@ -84,7 +101,7 @@ def _curve(b, r, cfg, trial):
             ee.append(st.eps)
         t += 1
     return Curve(cfg.batch_size, trial, np.array(rr, np.int64), np.array(ee, np.float64), days,
-                 launches, status)
+                 launches, status, method=method_of(cfg))
 
 
 def run_sweep(cfgs, obs, stream=None, max_stages=32767, grouping="all"):
@@ -111,7 +128,8 @@ def run_sweep(cfgs, obs, stream=None, max_stages=32767, grouping="all"):
             abc_batch_run(b, max_stages + 1)
             secs = time.perf_counter() - t0
             for k, i in enumerate(idx):
-                trial = sum(c.batch_size == cfgs[i].batch_size for c in cfgs[:i])
+                trial = sum(c.batch_size == cfgs[i].batch_size and
+                            method_of(c) == method_of(cfgs[i]) for c in cfgs[:i])
                 curves[i] = _curve(b, k, cfgs[i], trial)
                 curves[i].group_s = secs
         finally:
@@ -128,8 +146,14 @@ def run_sweep(cfgs, obs, stream=None, max_stages=32767, grouping="all"):
     return curves
 
 
+def summarise_methods(curves):
+    """summarise() for the curves of each method: {method: {M: ...}}."""
+    return {m: summarise([c for c in curves if c.method == m])
+            for m in METHODS if any(c.method == m for c in curves)}
+
+
 def summarise(curves):
-    """Per level (ascending M): the best tolerance of each trial (its
+    """Per level (ascending M) of the curves of one method: the best tolerance of each trial (its
     smallest eps_t), the simulation runs at the first stage that reached it,
     the runs in all, the runs at the first stage within a factor 2 of the
     trial's best, with medians, quartiles and the spread of log10 of the
@@ -183,6 +207,8 @@ def main(argv=None):
     ap.add_argument("--budget", type=int, default=1000)
     ap.add_argument("--days", type=int, default=120)
     ap.add_argument("--population", type=int, default=10_000_000)
+    ap.add_argument("--methods", nargs="+", default=["bdss"], choices=METHODS)
+    ap.add_argument("--mcmc-s0", type=float, default=0.1)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     # one graph branch per run: more hardware work queues than the default 8
@@ -190,7 +216,9 @@ def main(argv=None):
     import os
     os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     build()
-    cfgs = sweep_configs(a.levels, a.trials, a.samples, a.budget, a.days, a.population)
+    cfgs = [c for m in a.methods
+            for c in sweep_configs(a.levels, a.trials, a.samples, a.budget, a.days, a.population,
+                                   method=m, mcmc_s0=a.mcmc_s0)]
     obs = torch.empty((3, a.days + 1), dtype=torch.int32, device="cuda")
     th = torch.empty(8, dtype=torch.float32, device="cuda")
     att = torch.empty(1, dtype=torch.int32, device="cuda")
@@ -199,8 +227,10 @@ def main(argv=None):
     t0 = time.perf_counter()
     curves = run_sweep(cfgs, obs.cpu().numpy())
     secs = time.perf_counter() - t0
-    res = {"seconds": secs, "summary": {str(k): v for k, v in summarise(curves).items()},
-           "curves": [{"M": c.M, "trial": c.trial, "runs": c.runs.tolist(),
+    res = {"seconds": secs,
+           "summary": {m: {str(k): v for k, v in sm.items()}
+                       for m, sm in summarise_methods(curves).items()},
+           "curves": [{"method": c.method, "M": c.M, "trial": c.trial, "runs": c.runs.tolist(),
                        "eps": c.eps.tolist(), "status": c.status} for c in curves]}
     text = json.dumps(res)
     if a.out:

@@ -24,7 +24,8 @@ def oracle_smc(cfg, nthreads=8):
                       alpha=cfg.survival_alpha, beta_mode=cfg.beta_mode, beta_a=cfg.beta_a,
                       beta_b=cfg.beta_b, weight_mode=cfg.weight_mode,
                       max_batches=cfg.max_batches, max_redraw=cfg.max_redraw, nthreads=nthreads,
-                      beta_p1=cfg.beta_p1, beta_p2=cfg.beta_p2, max_total=cfg.max_total_batches)
+                      beta_p1=cfg.beta_p1, beta_p2=cfg.beta_p2, max_total=cfg.max_total_batches,
+                      mcmc_s0=cfg.mcmc_s0, mcmc_adapt=cfg.mcmc_adapt)
 
 
 def saird_config(N, T, P, seed=1, **kw):
@@ -42,9 +43,11 @@ def oracle_obs(cfg):
     return obs, th, att
 
 
-def state_blob(cfg, gen, eps1, pop, batches_total=0):
+def state_blob(cfg, gen, eps1, pop, batches_total=0, mcmc=None):
     """abc_set_state layout: magic, N, T, seed, run_id, gen, eps1, the run
-    budget count, then u [8][N] f32, dist f64, W f64, s f32, anc i32."""
+    budget count, then u [8][N] f32, dist f64, W f64, s f32, anc i32; for
+    the MCMC baseline the step state (s f64, adaptations i64, batches i64)
+    follows (mcmc = (s, k, batches))."""
     N = cfg.n_particles
     T = cfg.n_days if cfg.model == G.ABC_MODEL_SAIRD else 0
     head = struct.pack("<8sqqQIidq", b"ABCSMC02", N, T, cfg.seed, cfg.run_id, gen, eps1,
@@ -53,7 +56,8 @@ def state_blob(cfg, gen, eps1, pop, batches_total=0):
                      np.ascontiguousarray(pop.d, np.float64).tobytes(),
                      np.ascontiguousarray(pop.W, np.float64).tobytes(),
                      np.ascontiguousarray(pop.s, np.float32).tobytes(),
-                     np.ascontiguousarray(pop.anc, np.int32).tobytes()])
+                     np.ascontiguousarray(pop.anc, np.int32).tobytes(),
+                     b"" if mcmc is None else struct.pack("<dqq", *mcmc)])
 
 
 def get_population(ctx, N):

@@ -55,7 +55,8 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", offsetof(abc_gen_stats, eps), offsetof(abc_gen_stats, batches),
          offsetof(abc_gen_stats, ms_weights), offsetof(abc_gen_stats, beta_bf),
          offsetof(abc_config, beta_p2), offsetof(abc_config, max_total_batches));
-  printf("%zu\n", offsetof(abc_config, spec_batches));
+  printf("%zu %zu %zu %zu\n", offsetof(abc_config, spec_batches), offsetof(abc_config, mcmc_s0),
+         offsetof(abc_config, mcmc_adapt), offsetof(abc_gen_stats, mcmc_s));
   return 0;
 }
 """
@@ -71,7 +72,8 @@ int main(void) {
             ctypes.sizeof(G.AbcGenStats), G.AbcGenStats.eps.offset, G.AbcGenStats.batches.offset,
             G.AbcGenStats.ms_weights.offset, G.AbcGenStats.beta_bf.offset,
             G.AbcConfig.beta_p2.offset, G.AbcConfig.max_total_batches.offset,
-            G.AbcConfig.spec_batches.offset]
+            G.AbcConfig.spec_batches.offset, G.AbcConfig.mcmc_s0.offset,
+            G.AbcConfig.mcmc_adapt.offset, G.AbcGenStats.mcmc_s.offset]
     assert got == want
 
 
@@ -92,9 +94,15 @@ def test_defaults_and_argument_checks_without_gpu(lib):
     for mode, p1, p2 in [(G.ABC_BETA_REAL, 0.0, 1.0), (G.ABC_BETA_REAL, 1.0, 2.0 ** 21),
                          (G.ABC_BETA_MEAN_VAR, 1.0, 0.01), (G.ABC_BETA_MEAN_VAR, 0.3, 0.0),
                          (G.ABC_BETA_MODE_CONC, 1.5, 3.0), (G.ABC_BETA_MODE_CONC, 0.5, 1.9),
-                         (5, 0.5, 3.0)]:
+                         (6, 0.5, 3.0)]:
         bad = G.config(beta_mode=mode, beta_p1=p1, beta_p2=p2)
         assert lib.abc_init(ctypes.byref(bad), None, None, ctypes.byref(h)) == -1, (mode, p1, p2)
+    # the MCMC baseline: a positive finite step, a window >= 0, no surrogate
+    assert G.config().mcmc_s0 > 0 and G.config().mcmc_adapt == 0
+    for kw in (dict(mcmc_s0=0.0), dict(mcmc_s0=float("inf")), dict(mcmc_adapt=-1),
+               dict(surrogate=1)):
+        bad = G.config(beta_mode=G.ABC_STEP_MCMC, **kw)
+        assert lib.abc_init(ctypes.byref(bad), None, None, ctypes.byref(h)) == -1, kw
     assert lib.abc_select_kth(None, 10, 1, None, None, 0, None) == -1
     assert lib.abc_select_scratch_bytes(1 << 20) > 0
     assert lib.abc_weights_scratch_bytes(4096, 4096) >= 4096 * 9 * 4

@@ -1,6 +1,7 @@
 """The parallelism sweep (Sec. 4.1) on the GPU: every trial's curve (the
 simulation runs so far and eps_t after each stage) equals the oracle run's
-with the same config, bit for bit, on a reduced sweep."""
+with the same config, bit for bit, on a reduced sweep -- for BDSS and for
+the MCMC baseline arm, alone and in one batch together."""
 import numpy as np
 import pytest
 
@@ -41,3 +42,24 @@ def test_reduced_sweep_matches_oracle_runs(grouping):
             assert cv.runs[-1] >= 24 and (len(ok) == 1 or cv.runs[-2] < 24)
     s = S.summarise(curves)
     assert sorted(s) == [8, 32, 256] and all(v["trials"] == 3 for v in s.values())
+
+
+def test_reduced_sweep_both_methods_match_oracle_runs():
+    """Both arms of the paper's comparison in one graph batch: the baseline's
+    trials adapt their step over a tenth of the run budget (their first 3
+    batches after the prior stage) inside the graph, and every curve equals
+    the oracle's."""
+    cfgs = [c for m in S.METHODS
+            for c in S.sweep_configs(levels=(8, 64), trials=2, N=64, budget=24, T=30,
+                                     P=100_000, max_batches=4096, method=m, mcmc_s0=0.05)]
+    obs, _, _ = oracle_obs(cfgs[0])
+    curves = S.run_sweep(cfgs, obs)
+    for cfg, cv in zip(cfgs, curves):
+        _, ost = O.run(oracle_model(cfg, obs), oracle_smc(cfg), 10_000)
+        ok = [s for s in ost if s.status == 0]
+        runs = -(-cfg.n_particles // cfg.batch_size) + np.cumsum([s.batches for s in ost])
+        assert cv.method == S.method_of(cfg) and cv.trial == cfg.run_id % 2
+        assert np.array_equal(cv.eps, np.array([s.eps for s in ok])), (cv.method, cv.M)
+        assert np.array_equal(cv.runs, runs[:len(ok)])
+    s = S.summarise_methods(curves)
+    assert sorted(s) == ["bdss", "mcmc"] and sorted(s["mcmc"]) == [8, 64]

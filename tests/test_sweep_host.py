@@ -54,3 +54,35 @@ def test_summary_on_known_curves():
     assert b["best_eps_median"] == 4.0 and b["runs_to_best_median"] == 12.0
     assert b["runs_to_2x_best_median"] == 12.0
     assert b["log10_best_eps_std"] == 0.0
+
+
+def test_mcmc_arm_configs():
+    """The baseline arm: the single tuned step with the paper's adaptation
+    window (0 = the first tenth of the run budget), one batch per round, the
+    same levels, trials, budget and run ids as the BDSS arm."""
+    b = S.sweep_configs(levels=(10, 1000), trials=3, N=1000, budget=1000)
+    m = S.sweep_configs(levels=(10, 1000), trials=3, N=1000, budget=1000, method="mcmc",
+                        mcmc_s0=0.05)
+    assert [c.run_id for c in m] == [c.run_id for c in b]
+    assert [c.batch_size for c in m] == [c.batch_size for c in b]
+    for c in m:
+        assert c.beta_mode == G.ABC_STEP_MCMC and math.isclose(c.mcmc_s0, 0.05, rel_tol=1e-7)
+        assert c.mcmc_adapt == 0 and c.max_total_batches == 1000 and c.spec_batches == 1
+        assert S.method_of(c) == "mcmc"
+    assert all(S.method_of(c) == "bdss" for c in b)
+    try:
+        S.sweep_configs(levels=(10,), trials=1, method="abc")
+        raise AssertionError("an unknown method must be refused")
+    except ValueError:
+        pass
+
+
+def test_summary_per_method():
+    curves = [_c(10, 0, [300, 700], [50.0, 20.0]), _c(10, 1, [250], [40.0])]
+    mc = S.Curve(10, 0, np.array([400], np.int64), np.array([60.0]), 0, 0, G.ABC_OK,
+                 method="mcmc")
+    s = S.summarise_methods(curves + [mc])
+    assert sorted(s) == ["bdss", "mcmc"]
+    assert s["bdss"][10]["trials"] == 2 and s["mcmc"][10]["trials"] == 1
+    assert s["mcmc"][10]["best_eps_median"] == 60.0
+    assert S.summarise_methods(curves).keys() == {"bdss"}
