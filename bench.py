@@ -470,7 +470,9 @@ def run_sweep_bench(args):
     B.build()
     G.lib()
     levels = tuple(args.levels) if args.levels else S.LEVELS
-    cfgs = S.sweep_configs(levels, args.trials, spec_target=args.spec_target)
+    cfgs = [c for m in args.methods
+            for c in S.sweep_configs(levels, args.trials, spec_target=args.spec_target, method=m,
+                                     mcmc_s0=args.mcmc_s0)]
     obs = synthetic_obs(G, WL, cfgs[0], torch)[0]
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -489,23 +491,24 @@ def run_sweep_bench(args):
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
     clk = clocks.stop()
-    summ = S.summarise(curves)
+    summ = S.summarise_methods(curves)
     if args.grouping == "level":
-        for M, v in summ.items():
-            v["level_s"] = next(c.group_s for c in curves if c.M == M)
+        for meth, sm in summ.items():
+            for M, v in sm.items():
+                v["level_s"] = next(c.group_s for c in curves if c.M == M and c.method == meth)
     return {"metric": METRIC, "value": days / secs, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "sweep_levels%s_trials%d_n1000_t120_p1e7_budget1000" % (
-                           "-".join(str(m) for m in levels), args.trials),
+            "config": {"workload": "sweep_%s_levels%s_trials%d_n1000_t120_p1e7_budget1000" % (
+                           "-".join(args.methods), "-".join(str(m) for m in levels), args.trials),
                        "step": "one whole sweep (every trial to its stopping stage)",
                        "grouping": args.grouping,
                        "batches_per_round": "about %d simulations in flight, 1 to 64" % (
                            args.spec_target) if args.spec_target else "1",
                        "l2": "flushed between steps (256 MB write)"},
             "gpu_launches": launches, "clocks": clk,
-            "sweep": {str(k): v for k, v in summ.items()}}
+            "sweep": {meth: {str(k): v for k, v in sm.items()} for meth, sm in summ.items()}}
 
 
 ORACLE_SAMPLE_N = 8192  # particles of the oracle's sample runs
@@ -808,6 +811,10 @@ def main():
                     help="sweep: simulations in flight per round of small levels (0: one batch)")
     ap.add_argument("--grouping", default="all", choices=["all", "level", "run"],
                     help="sweep: one batch of all runs, one per level, or one per run")
+    ap.add_argument("--methods", nargs="+", default=["bdss"], choices=["bdss", "mcmc"],
+                    help="sweep: BDSS and/or the MCMC-tuned single-step baseline")
+    ap.add_argument("--mcmc-s0", type=float, default=0.1,
+                    help="sweep: the MCMC baseline's initial step (unit-cube variance)")
     ap.add_argument("--pass-n", type=int, default=1 << 28)
     ap.add_argument("--generations", type=int, default=0,
                     help="generations per run (single: 20, the workload's G; eps_final: 8)")
