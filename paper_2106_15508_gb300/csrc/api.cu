@@ -658,7 +658,8 @@ int ctx_alloc(abc_ctx* c) {
                         accept_scratch_bytes(c->M), survivors_scratch_bytes(c->N),
                         spec_k(c->cfg) > 1 ? accept_spec_scratch_bytes(c->M, spec_k(c->cfg))
                                            : size_t(0),
-                        normalize_scratch_bytes(c->N)});
+                        normalize_scratch_bytes(c->N), sim_order_scratch_bytes(c->N),
+                        sim_order_scratch_bytes(c->M * spec_k(c->cfg))});
   if (c->cfg.weight_mode == ABC_W_IMPORTANCE)  // room for the tuner's chunk multipliers (<= 4)
     sb = std::max(sb, c->cfg.weight_prec == ABC_P_BF16_TC ? weights_tc_scratch_bytes(c->N, c->N, 4)
                                                           : weights_fp32_scratch_bytes(c->N, c->N, 4));
@@ -720,8 +721,11 @@ int generation0(abc_ctx* c) {
   int rc = launch_prior(c->p, c->N, c->u[cur], st);
   if (rc) return rc;
   ABC_CUDA_TRY(cudaEventRecord(c->es0, st));
-  rc = launch_simulate(c->p, c->obs, c->u[cur], c->N, nullptr, 0u, ABC_TAG_SIM, nullptr, c->d[cur],
-                       nullptr, st, nullptr, nullptr, 128, c->cfg.surrogate ? c->ard : nullptr);
+  rc = c->cfg.surrogate
+           ? launch_simulate(c->p, c->obs, c->u[cur], c->N, nullptr, 0u, ABC_TAG_SIM, nullptr,
+                             c->d[cur], nullptr, st, nullptr, nullptr, 128, c->ard)
+           : launch_simulate_ordered(c->p, c->obs, c->u[cur], c->N, 0u, nullptr, c->d[cur],
+                                     c->scratch, c->scratch_bytes, st);
   if (rc) return rc;
   ABC_CUDA_TRY(cudaEventRecord(c->es1, st));
   if (c->cfg.surrogate &&
@@ -812,8 +816,8 @@ int generation_t(abc_ctx* c) {
                           nullptr, nullptr, nullptr, c->M, c->spec_dev);
       if (rc) return rc;
       ABC_CUDA_TRY(cudaEventRecord(c->es0, st));
-      rc = launch_simulate(c->p, c->obs, c->up, c->M * K, nullptr, c1, ABC_TAG_SIM, c->flag,
-                           c->dp, nullptr, st, nullptr, nullptr, 128, nullptr, c->M);
+      rc = launch_simulate_ordered(c->p, c->obs, c->up, c->M * K, c1, c->flag, c->dp, c->scratch,
+                                   c->scratch_bytes, st, nullptr, nullptr, 128, c->M);
       if (rc) return rc;
       ABC_CUDA_TRY(cudaEventRecord(c->es1, st));
       rc = launch_accept_spec(c->up, c->dp, c->sp, c->ap, c->flag, c->M, K, c->spec_dev, eps,
@@ -844,8 +848,8 @@ int generation_t(abc_ctx* c) {
       if (rc) return rc;
     } else {
       ABC_CUDA_TRY(cudaEventRecord(c->es0, st));
-      rc = launch_simulate(c->p, c->obs, c->up, c->M, nullptr, c1, ABC_TAG_SIM, c->flag, c->dp,
-                           nullptr, st, nullptr, nullptr, 128, nullptr);
+      rc = launch_simulate_ordered(c->p, c->obs, c->up, c->M, c1, c->flag, c->dp, c->scratch,
+                                   c->scratch_bytes, st);
       if (rc) return rc;
       ABC_CUDA_TRY(cudaEventRecord(c->es1, st));
       rc = launch_accept(c->up, c->dp, c->sp, c->ap, c->flag, c->M, eps, c->N, c->u[nxt], c->d[nxt],

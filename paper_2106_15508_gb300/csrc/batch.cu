@@ -230,8 +230,9 @@ int batch_capture_run(BatchRun& br, cudaStream_t st, cudaStream_t body_st) {
                         reinterpret_cast<unsigned long long*>(&r->exhausted), v.scratch,
                         v.scratch_bytes, br.sim_threads, nullptr, body_st);
   } else if (!rc) {
-    rc = launch_simulate(v.p, v.obs, v.up, slots, nullptr, 0u, ABC_TAG_SIM, v.flag, v.dp, nullptr,
-                         body_st, &r->c1, &r->off, br.sim_threads, nullptr, spec ? v.M : 0);
+    rc = launch_simulate_ordered(v.p, v.obs, v.up, slots, 0u, v.flag, v.dp, v.scratch,
+                                 v.scratch_bytes, body_st, &r->c1, &r->off, br.sim_threads,
+                                 spec ? v.M : 0);
     if (!rc && spec)
       rc = launch_accept_spec(v.up, v.dp, v.sp, v.ap, v.flag, v.M, v.K, &r->k_lim, &r->eps, v.N,
                               v.u_nxt, v.d_nxt, v.s_nxt, v.a_nxt,

@@ -6,6 +6,7 @@
 // shared memory; every day draws three Philox blocks and five binomial
 // transitions (Sec. 2.2, Eq. 3-5, as exact-count competing risks) and adds
 // the day's squared error to an unsigned 128-bit accumulator (Sec. 2.3).
+#include "batch.cuh"
 #include "common.cuh"
 #include "numerics.cuh"
 
@@ -188,7 +189,8 @@ k_simulate(SimParams p, const int32_t* __restrict__ obs,
                            const uint8_t* __restrict__ skip, double* __restrict__ dist,
                            int32_t* __restrict__ traj, const uint32_t* __restrict__ c1_dev,
                            const int* __restrict__ off_dev, int32_t* __restrict__ ard_last,
-                           int64_t m_sub, const int* __restrict__ n_dev) {
+                           int64_t m_sub, const int* __restrict__ n_dev,
+                           const int32_t* __restrict__ perm) {
   extern __shared__ int32_t s_obs[];
   if (off_dev && *off_dev) return;  // run finished: nothing to simulate
   if (c1_dev) c1 = *c1_dev;         // counter word set on the device (graph launches)
@@ -198,7 +200,10 @@ k_simulate(SimParams p, const int32_t* __restrict__ obs,
   BinvJob* bq = reinterpret_cast<BinvJob*>(s_obs + ((nobs + 3) & ~3)) +
                 (threadIdx.x >> 5) * kBinvQueue;
   __syncthreads();
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  // perm (nullable): thread t runs slot perm[t] (an order that groups similar
+  // trajectories into warps); every slot keeps its own counters and outputs
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t i = perm && t < n ? static_cast<int64_t>(perm[t]) : t;
   // n_dev (nullable): the slots in use, counted on the device (a compacted
   // list of capacity n); the others get distance +inf
   const bool live = i < n && !(n_dev && i >= *n_dev) && !(skip && skip[i]);
@@ -289,12 +294,74 @@ __global__ void k_philox(const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t
   out[4 * i + 3] = r.w;
 }
 
+// ---- simulation order ------------------------------------------------------
+// The lanes of a warp run their trajectories in lockstep, so lanes whose
+// binomial draws fall in different regimes (normal approximation, inversion
+// loop, trivial) serialise.  Slots are therefore simulated in the order of a
+// key that predicts their regime mix.  The key is a heuristic only: every
+// slot keeps its own Philox counters and writes its own outputs, so the
+// order changes no result.
+//
+// Key of a slot: its expected-value path (each day's draws replaced by
+// their means n p; Euler steps of two days, fast-math arithmetic) over the T
+// days; c counts the draws of that path whose n min(p, 1 - p) is below 10
+// (the sampler's inversion regime, trivial draws included) and dpk is the
+// day of its largest I; key = min(c, 511) << 7 | min(dpk, 127).  Skipped
+// slots sort last.
+__global__ void k_sim_order_key(SimParams p, const float* __restrict__ u, int64_t n,
+                                const uint8_t* __restrict__ skip, const int* __restrict__ off_dev,
+                                uint32_t* __restrict__ key) {
+  if (off_dev && *off_dev) return;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (skip && skip[i]) {
+    key[i] = 0xFFFFu;
+    return;
+  }
+  float th[8];
+#pragma unroll
+  for (int d = 0; d < 8; ++d) th[d] = theta_of(p, d, u[static_cast<int64_t>(d) * n + i]);
+  const float a0 = th[0], al = th[1], nn = th[2], be = th[3], ga = th[4], de = th[5],
+              et = th[6], ka = th[7];
+  const float Pf = static_cast<float>(p.P);
+  float A = static_cast<float>(p.A0), R = static_cast<float>(p.R0), D = static_cast<float>(p.D0);
+  float I = ka * A;
+  float S = fmaxf(Pf - (A + R + D + I), 0.0f);
+  const float lamI = ga + be * et, lamA = be + de;
+  const float pI = 1.0f - __expf(-lamI), pA = 1.0f - __expf(-lamA);
+  const float fI = lamI > 0.0f ? __fdividef(ga, lamI) : 0.0f;
+  const float fA = lamA > 0.0f ? __fdividef(be, lamA) : 0.0f;
+  const float qpI = fminf(pI, 1.0f - pI), qpA = fminf(pA, 1.0f - pA);
+  const float qI = fminf(fI, 1.0f - fI), qA = fminf(fA, 1.0f - fA);
+  int c = 0, dpk = 0;
+  float peak = 0.0f;
+  for (int day = 0; day < p.T; day += 2) {
+    const float x = fmaxf(A + R + D, 1.0f);
+    const float g = a0 + __fdividef(al, 1.0f + __expf(nn * __logf(x)));
+    const float pSI = 1.0f - __expf(-g * __fdividef(I, Pf));
+    const float LI = I * pI, LA = A * pA;
+    c += 2 * ((S * fminf(pSI, 1.0f - pSI) < 10.0f) + (I * qpI < 10.0f) + (A * qpA < 10.0f) +
+              (LI * qI < 10.0f) + (LA * qA < 10.0f));
+    const float k1 = S * pSI;
+    S = fmaxf(S - 2.0f * k1, 0.0f);
+    I = fmaxf(I + 2.0f * (k1 - LI), 0.0f);
+    A = fmaxf(A + 2.0f * (LI * fI - LA), 0.0f);
+    R += 2.0f * LA * fA;
+    D += 2.0f * LA * (1.0f - fA);
+    if (I > peak) {
+      peak = I;
+      dpk = day;
+    }
+  }
+  key[i] = (static_cast<uint32_t>(min(c, 511)) << 7) | static_cast<uint32_t>(min(dpk, 127));
+}
+
 // ---- host launchers (called by the C ABI layer) --------------------------
 int launch_simulate(const SimParams& p, const int32_t* obs, const float* u, int64_t n,
                     const uint32_t* c0_idx, uint32_t c1, uint32_t tag, const uint8_t* skip,
                     double* dist, int32_t* traj, cudaStream_t st, const uint32_t* c1_dev,
                     const int* off_dev, int threads, int32_t* ard_last, int64_t m_sub,
-                    const int* n_dev) {
+                    const int* n_dev, const int32_t* perm) {
   if (n <= 0) return ABC_OK;
   if (m_sub < 0) return ABC_E_INVAL;
   // 64 registers per thread (__launch_bounds__(256, 4)): up to 8 CTAs of
@@ -304,9 +371,53 @@ int launch_simulate(const SimParams& p, const int32_t* obs, const float* u, int6
   const size_t smem = sizeof(int32_t) * ((nobs + 3) & ~static_cast<size_t>(3)) +
                       sizeof(BinvJob) * kBinvQueue * static_cast<size_t>(threads / 32);
   k_simulate<<<static_cast<unsigned>(ceil_div(n, threads)), threads, smem, st>>>(
-      p, obs, u, n, c0_idx, c1, tag, skip, dist, traj, c1_dev, off_dev, ard_last, m_sub, n_dev);
+      p, obs, u, n, c0_idx, c1, tag, skip, dist, traj, c1_dev, off_dev, ard_last, m_sub, n_dev,
+      perm);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
+}
+
+namespace {
+struct SimOrderLayout {
+  size_t key, key_s, perm, sort, total;
+};
+SimOrderLayout sim_order_layout(int64_t n) {
+  SimOrderLayout l{};
+  const size_t w = align256(sizeof(uint32_t) * static_cast<size_t>(n));
+  l.key = 0;
+  l.key_s = w;
+  l.perm = 2 * w;
+  l.sort = 3 * w;
+  l.total = l.sort + radix_sort_scratch_bytes(n);
+  return l;
+}
+}  // namespace
+
+size_t sim_order_scratch_bytes(int64_t n) {
+  return n >= kSimOrderMin ? sim_order_layout(n).total : 0;
+}
+
+int launch_simulate_ordered(const SimParams& p, const int32_t* obs, const float* u, int64_t n,
+                            uint32_t c1, const uint8_t* skip, double* dist, void* scratch,
+                            size_t bytes, cudaStream_t st, const uint32_t* c1_dev,
+                            const int* off_dev, int threads, int64_t m_sub) {
+  if (p.model != ABC_MODEL_SAIRD || n < kSimOrderMin || !obs)
+    return launch_simulate(p, obs, u, n, nullptr, c1, ABC_TAG_SIM, skip, dist, nullptr, st,
+                           c1_dev, off_dev, threads, nullptr, m_sub);
+  const SimOrderLayout l = sim_order_layout(n);
+  if (!scratch || bytes < l.total) return ABC_E_SCRATCH;
+  char* b = static_cast<char*>(scratch);
+  uint32_t* key = reinterpret_cast<uint32_t*>(b + l.key);
+  uint32_t* key_s = reinterpret_cast<uint32_t*>(b + l.key_s);
+  int32_t* perm = reinterpret_cast<int32_t*>(b + l.perm);
+  k_sim_order_key<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, st>>>(p, u, n, skip, off_dev,
+                                                                            key);
+  ABC_LAUNCH_CHECK();
+  int rc = launch_radix_sort(key, nullptr, key_s, perm, n, nullptr, 16, b + l.sort,
+                             l.total - l.sort, st);
+  if (rc) return rc;
+  return launch_simulate(p, obs, u, n, nullptr, c1, ABC_TAG_SIM, skip, dist, nullptr, st, c1_dev,
+                         off_dev, threads, nullptr, m_sub, nullptr, perm);
 }
 
 int launch_prior(const SimParams& p, int64_t n, float* u, cudaStream_t st) {

@@ -596,3 +596,34 @@ def test_gaussian_toy_closed_form_on_gpu():
                                  ess_median=float(np.median(ess)))
     assert abs(means.mean()) < 2 * se_m, (means, se_m)
     assert abs(ratios.mean() - 1) < 2 * se_v, (ratios, se_v)
+
+
+@pytest.mark.parametrize("M,K", [(0, 1), (4096, 8)])
+def test_context_ordered_simulation_bitexact(M, K):
+    """Batches of at least 16384 slots are simulated in the order of the
+    regime key (k_sim_order_key, a radix sort, k_simulate through the
+    permutation): 32768 particles with one batch of N slots, and batches of
+    4096 slots run 8 per round (32768 slots in one ordered launch); three
+    generations and stage 0 equal the oracle bit for bit."""
+    cfg = saird_config(32768, 40, 100_000, seed=12, weight_mode=G.ABC_W_PAPER, batch_size=M,
+                       spec_batches=K, max_batches=400)
+    obs, _, _ = oracle_obs(cfg)
+    m, c = oracle_model(cfg, obs), oracle_smc(cfg)
+    ctx = G.abc_init(cfg, obs)
+    try:
+        pop = O.generation0(m, c)
+        G.abc_generation(ctx)
+        gp = get_population(ctx, cfg.n_particles)
+        assert np.array_equal(gp["d"].view(np.uint64), pop.d.view(np.uint64))
+        eps1 = 0.0
+        for t in range(1, 4):
+            new, st = O.generation(m, c, t, eps1, pop)
+            assert G.abc_generation(ctx) == st.status == 0
+            gp = get_population(ctx, cfg.n_particles)
+            for k, ok in (("u", new.u), ("d", new.d), ("s", new.s), ("anc", new.anc)):
+                assert np.array_equal(gp[k].view(np.uint8),
+                                      np.ascontiguousarray(ok).view(np.uint8)), (t, k)
+            _stats_match(G.abc_get_stats(ctx, t), st)
+            eps1, pop = st.eps1, new
+    finally:
+        G.abc_free(ctx)
