@@ -303,33 +303,37 @@ bool beta_rule_ok(const BetaRule& r) {
   }
 }
 
+// Slots per warp of k_propose: the lanes of a warp take the slots of their
+// chunk one after another, each lane moving on to the chunk's next slot when
+// its own is done, so a slot that needs many redraws (attempts vary from 1
+// to max_redraw) holds up one lane instead of 31.  Every slot's attempts use
+// its own counters, so the assignment of slots to lanes changes no result.
+__device__ __forceinline__ int64_t propose_chunk(int64_t slots) {
+  // at least about 2432 warps (16 per SM) before a warp takes more than 32
+  const int64_t mult = slots / (32 * 2432);
+  return 32 * (mult < 1 ? 1 : (mult > 8 ? 8 : mult));
+}
+
 __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
                           const uint64_t* __restrict__ prefix, BetaRule rule,
-                          const double* eps_p, const double* eps1_p, int64_t slots, const uint32_t* __restrict__ c0_idx, uint32_t c1,
-                          int max_redraw, float* __restrict__ u_out, float* __restrict__ s_out,
+                          const double* eps_p, const double* eps1_p, int64_t slots,
+                          const uint32_t* __restrict__ c0_idx, uint32_t c1, int max_redraw,
+                          float* __restrict__ u_out, float* __restrict__ s_out,
                           int32_t* __restrict__ anc_out, int32_t* __restrict__ att_out,
                           uint8_t* __restrict__ flag_out, const uint32_t* __restrict__ c1_dev,
                           const int* __restrict__ beta_b_dev, const int* __restrict__ off_dev,
                           int64_t m_sub, const int* __restrict__ k_lim_dev,
                           const float* __restrict__ s_fix_dev) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= slots) return;
-  if (off_dev && *off_dev) return;          // run finished
-  if (c1_dev) c1 = *c1_dev;                 // set on the device (graph launches)
-  // slots of several batches at once (m_sub > 0): slot i is slot is of batch
-  // c1 + kb; batches at or beyond *k_lim_dev are not drawn (flag 3)
-  int64_t is = i;
-  if (m_sub > 0) {
-    const int64_t kb = i / m_sub;
-    is = i - kb * m_sub;
-    if (k_lim_dev && kb >= *k_lim_dev) {
-      flag_out[i] = 3;
-      return;
-    }
-    c1 += static_cast<uint32_t>(kb);
-  }
+  // the warp's chunk of slots [lo, hi); whole warps return together
+  const int64_t chunk = propose_chunk(slots);
+  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t lo = warp * chunk;
+  if (lo >= slots) return;
+  if (off_dev && *off_dev) return;  // run finished
+  const int64_t hi = lo + chunk < slots ? lo + chunk : slots;
+  if (c1_dev) c1 = *c1_dev;  // set on the device (graph launches)
+  const int k_lim = k_lim_dev ? *k_lim_dev : 0x7fffffff;
   const int beta_b = beta_b_dev ? *beta_b_dev : rule.b;
-  const uint32_t j = c0_idx ? c0_idx[is] : static_cast<uint32_t>(is);
   const unsigned long long total = prefix[n - 1];
   float a_t = rule.a, b_t = 0.0f;
   float ratio = 1.0f;
@@ -343,39 +347,70 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
   }
   if (rule.mode == ABC_BETA_PAPER) a_t = ratio;
   // the Gamma ratio: the real-shape rules, and the paper schedule once b =
-  // 2t passes 1024 (integer b 0)
+  // 2t passes 1024 (integer b 0); the stage c1 >> 16 is the same for every
+  // batch of the launch
   const bool real_shape = (rule.mode >= ABC_BETA_REAL && rule.mode <= ABC_BETA_MODE_CONC) ||
                           (rule.mode == ABC_BETA_PAPER && beta_b == 0);
   if (real_shape) beta_real_shape(rule, ratio, static_cast<int32_t>(c1 >> 16), &a_t, &b_t);
-  float up[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  float s = 0.0f;
-  int64_t anc = 0;
-  bool ok = false;
-  int a;
-  for (a = 0; a < max_redraw; ++a) {
+  const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+  int64_t next = lo;  // the chunk's next slot (the same in every lane)
+  int64_t i = -1;     // this lane's slot, -1 for none
+  uint32_t j = 0, c1s = c1;
+  int a = 0;
+  while (true) {
+    // lanes without a slot take the chunk's next ones, in lane order
+    const unsigned need = __ballot_sync(0xffffffffu, i < 0);
+    if (i < 0) {
+      const int64_t cand = next + __popc(need & lt);
+      if (cand < hi) {
+        i = cand;
+        a = 0;
+        // slots of several batches at once (m_sub > 0): slot i is slot is
+        // of batch c1 + kb; batches at or beyond *k_lim_dev are not drawn
+        // (flag 3)
+        int64_t is = i;
+        c1s = c1;
+        if (m_sub > 0) {
+          const int64_t kb = i / m_sub;
+          is = i - kb * m_sub;
+          c1s = c1 + static_cast<uint32_t>(kb);
+          if (kb >= k_lim) {
+            flag_out[i] = 3;
+            i = -1;
+          }
+        }
+        j = c0_idx ? c0_idx[is] : static_cast<uint32_t>(is);
+      }
+    }
+    next += __popc(need);
+    if (next > hi) next = hi;
+    if (__all_sync(0xffffffffu, i < 0) && next >= hi) break;
+    if (i < 0) continue;
+    // attempt a of slot i
     // Eq. 11: categorical ancestor by inverting the u64 prefix
-    const u32x4 wa = philox4x32_10(j, c1, static_cast<uint32_t>(a), ABC_TAG_ANCESTOR, p.k0, p.k1);
+    const u32x4 wa = philox4x32_10(j, c1s, static_cast<uint32_t>(a), ABC_TAG_ANCESTOR, p.k0, p.k1);
     const unsigned long long U = (static_cast<unsigned long long>(wa.y) << 32) | wa.x;
     const unsigned long long x = __umul64hi(U, total);
-    int64_t lo = 0, hi = n - 1;
-    while (lo < hi) {
-      const int64_t mid = lo + ((hi - lo) >> 1);
-      if (prefix[mid] > x) hi = mid;
-      else lo = mid + 1;
+    int64_t blo = 0, bhi = n - 1;
+    while (blo < bhi) {
+      const int64_t mid = blo + ((bhi - blo) >> 1);
+      if (prefix[mid] > x) bhi = mid;
+      else blo = mid + 1;
     }
-    anc = lo;
+    const int64_t anc = blo;
+    float s;
     if (fixed_step) {
       s = s_fix;
     } else if (real_shape) {
       // real shapes: the Gamma ratio
-      s = dev_beta_real(a_t, b_t, j, c1, static_cast<uint32_t>(a), p.k0, p.k1);
+      s = dev_beta_real(a_t, b_t, j, c1s, static_cast<uint32_t>(a), p.k0, p.k1);
     } else {
       // Eq. 16: s ~ Beta(a_t, b) as exp(sum_m log(U_m) / (a_t + m))
       float acc = 0.0f;
       u32x4 wb{0u, 0u, 0u, 0u};
       for (int m = 0; m < beta_b; ++m) {
         if ((m & 3) == 0)
-          wb = philox4x32_10(j, c1,
+          wb = philox4x32_10(j, c1s,
                              (static_cast<uint32_t>(a) << 8) | static_cast<uint32_t>(m >> 2),
                              ABC_TAG_BETA, p.k0, p.k1);
         const uint32_t wm = (m & 3) == 0 ? wb.x : (m & 3) == 1 ? wb.y : (m & 3) == 2 ? wb.z : wb.w;
@@ -385,10 +420,11 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
     }
     const float sd = __fsqrt_rn(s);
     // Eq. 17: u' = u_anc + sqrt(s) z; the support check covers all 8 coordinates
-    ok = true;
+    float up[8];
+    bool ok = true;
 #pragma unroll
     for (int blk = 0; blk < 4; ++blk) {
-      const u32x4 wz = philox4x32_10(j, c1, (static_cast<uint32_t>(a) << 8) | blk, ABC_TAG_WALK,
+      const u32x4 wz = philox4x32_10(j, c1s, (static_cast<uint32_t>(a) << 8) | blk, ABC_TAG_WALK,
                                      p.k0, p.k1);
       const float z0 = dev_normal(unif(wz.x), unif(wz.y));
       const float z1 = dev_normal(unif(wz.z), unif(wz.w));
@@ -398,14 +434,19 @@ __global__ void k_propose(SimParams p, const float* __restrict__ u, int64_t n,
       up[2 * blk + 1] = v1;
       ok = ok && v0 >= 0.0f && v0 <= 1.0f && v1 >= 0.0f && v1 <= 1.0f;
     }
-    if (ok) break;
-  }
+    if (ok || a + 1 >= max_redraw) {
+      // the first u' inside [0,1]^8, or the last attempt's (redraws exhausted)
 #pragma unroll
-  for (int d = 0; d < 8; ++d) u_out[static_cast<int64_t>(d) * slots + i] = up[d];
-  s_out[i] = s;
-  anc_out[i] = static_cast<int32_t>(anc);
-  att_out[i] = ok ? a + 1 : max_redraw;
-  flag_out[i] = ok ? 0 : 1;
+      for (int d = 0; d < 8; ++d) u_out[static_cast<int64_t>(d) * slots + i] = up[d];
+      s_out[i] = s;
+      anc_out[i] = static_cast<int32_t>(anc);
+      att_out[i] = ok ? a + 1 : max_redraw;
+      flag_out[i] = ok ? 0 : 1;
+      i = -1;
+    } else {
+      ++a;
+    }
+  }
 }
 
 int launch_propose(const SimParams& p, const float* u, int64_t n, const uint64_t* prefix,
@@ -435,7 +476,11 @@ int launch_propose(const SimParams& p, const float* u, int64_t n, const uint64_t
       (c1 >> 16) == 0)
     return ABC_E_INVAL;
   if (slots == 0) return ABC_OK;
-  k_propose<<<static_cast<unsigned>(ceil_div(slots, 128)), 128, 0, st>>>(
+  // one warp per chunk of slots (propose_chunk), four warps per block
+  const int64_t mult = slots / (32 * 2432);
+  const int64_t chunk = 32 * (mult < 1 ? 1 : (mult > 8 ? 8 : mult));
+  const int64_t warps = ceil_div(slots, chunk);
+  k_propose<<<static_cast<unsigned>(ceil_div(warps, 4)), 128, 0, st>>>(
       p, u, n, prefix, rule, eps, eps1, slots, c0_idx, c1, max_redraw, u_out, s_out, anc_out,
       att_out, flag_out, c1_dev, beta_b_dev, off_dev, m_sub, k_lim_dev, s_fix_dev);
   ABC_LAUNCH_CHECK();
