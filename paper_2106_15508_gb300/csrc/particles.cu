@@ -46,22 +46,23 @@ __global__ void k_sel_hist(const double* __restrict__ d, int64_t n, const SelSta
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
+// 256 threads, one per bin: the digit b of the k-th key is the first bin
+// whose inclusive count reaches k (bin 255 if bins 0..254 hold fewer than
+// k keys); k becomes its rank inside that bin
 __global__ void k_sel_pick(SelState* st, unsigned* hist, int shift, double* out) {
-  if (threadIdx.x == 0) {
-    long long k = st->k;
-    int b = 0;
-    long long below = 0;
-    for (b = 0; b < 255; ++b) {
-      if (below + hist[b] >= k) break;
-      below += hist[b];
-    }
-    st->k = k - below;
-    st->prefix |= static_cast<unsigned long long>(b) << shift;
+  __shared__ unsigned long long sm[32];
+  const unsigned long long k = static_cast<unsigned long long>(st->k);
+  const unsigned h = hist[threadIdx.x];
+  const unsigned long long inc = block_incl_scan<unsigned long long>(h, sm);
+  const unsigned long long below = inc - h;
+  const bool pick = threadIdx.x < 255 ? (below < k && inc >= k) : below < k;
+  if (pick) {
+    st->k = static_cast<long long>(k - below);
+    st->prefix |= static_cast<unsigned long long>(threadIdx.x) << shift;
     st->mask |= 255ull << shift;
     if (shift == 0) *out = __longlong_as_double(static_cast<long long>(st->prefix));
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0u;
+  hist[threadIdx.x] = 0u;  // every thread read its bin before the scan's barriers
 }
 
 size_t select_scratch_bytes(int64_t) { return align256(sizeof(SelState)) + align256(256 * 4); }
@@ -843,16 +844,28 @@ __global__ void k_nz_sum(const double* __restrict__ lw, int64_t n, const double*
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-// one block folds the partials: op 0 max -> stat[0], 1 sum -> stat[1], 2 ess
+// one block of kNormBlocks threads folds the partials (np <= kNormBlocks):
+// op 0 max -> stat[0], 1 sum -> stat[1], 2 ess
 __global__ void k_nz_fold(const double* part, int np, int op, double* stat, double* ess,
                           int64_t n) {
+  __shared__ double sm[32];
+  const double ninf = -__longlong_as_double(0x7ff0000000000000ll);
+  double r = op == 0 ? ninf : 0.0;
+  if (static_cast<int>(threadIdx.x) < np) r = part[threadIdx.x];
+  if (op == 0) {
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) r = fmax(r, sm[w]);
+      stat[0] = r;
+    }
+    return;
+  }
+  r = block_sum<double>(r, sm);
   if (threadIdx.x != 0) return;
-  double r = op == 0 ? -__longlong_as_double(0x7ff0000000000000ll) : 0.0;
-  for (int i = 0; i < np; ++i) r = op == 0 ? fmax(r, part[i]) : r + part[i];
-  if (op == 0) stat[0] = r;
-  else if (op == 1) stat[1] = r;
-  else *ess = stat[0] > -__longlong_as_double(0x7ff0000000000000ll) ? 1.0 / r
-                                                                      : static_cast<double>(n);
+  if (op == 1) stat[1] = r;
+  else *ess = stat[0] > ninf ? 1.0 / r : static_cast<double>(n);
 }
 
 size_t normalize_scratch_bytes(int64_t) { return align256(8 * kNormBlocks) + align256(16); }
@@ -867,15 +880,15 @@ int launch_normalize(const double* lw, int64_t n, double* W, double* ess, void* 
   const int g = static_cast<int>(std::min<int64_t>(kNormBlocks, ceil_div(n, 256)));
   k_nz_max<<<g, 256, 0, st>>>(lw, n, part);
   ABC_LAUNCH_CHECK();
-  k_nz_fold<<<1, 32, 0, st>>>(part, g, 0, stat, ess, n);
+  k_nz_fold<<<1, kNormBlocks, 0, st>>>(part, g, 0, stat, ess, n);
   ABC_LAUNCH_CHECK();
   k_nz_sum<<<g, 256, 0, st>>>(lw, n, stat, 0, W, part);
   ABC_LAUNCH_CHECK();
-  k_nz_fold<<<1, 32, 0, st>>>(part, g, 1, stat, ess, n);
+  k_nz_fold<<<1, kNormBlocks, 0, st>>>(part, g, 1, stat, ess, n);
   ABC_LAUNCH_CHECK();
   k_nz_sum<<<g, 256, 0, st>>>(lw, n, stat, 1, W, part);
   ABC_LAUNCH_CHECK();
-  k_nz_fold<<<1, 32, 0, st>>>(part, g, 2, stat, ess, n);
+  k_nz_fold<<<1, kNormBlocks, 0, st>>>(part, g, 2, stat, ess, n);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }
