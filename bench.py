@@ -39,8 +39,8 @@ K_EFF = 10  # features of the weight pass's inner product (its algorithmic K)
 # k_simulate per particle-day, from one ncu capture of every simulator launch of a whole
 # 20-generation run of the 262,144-particle case of the workload (54 launches, 1.698e9
 # particle-days): smsp__thread_inst_executed.sum / particle-days, and DRAM read + write bytes
-SIM_THREAD_INST_PER_DAY = 984.9
-SIM_DRAM_BYTES_PER_DAY = 0.2786
+SIM_THREAD_INST_PER_DAY = 967.9
+SIM_DRAM_BYTES_PER_DAY = 0.3117
 
 
 def _peaks():
