@@ -721,11 +721,9 @@ int generation0(abc_ctx* c) {
   int rc = launch_prior(c->p, c->N, c->u[cur], st);
   if (rc) return rc;
   ABC_CUDA_TRY(cudaEventRecord(c->es0, st));
-  rc = c->cfg.surrogate
-           ? launch_simulate(c->p, c->obs, c->u[cur], c->N, nullptr, 0u, ABC_TAG_SIM, nullptr,
-                             c->d[cur], nullptr, st, nullptr, nullptr, 128, c->ard)
-           : launch_simulate_ordered(c->p, c->obs, c->u[cur], c->N, 0u, nullptr, c->d[cur],
-                                     c->scratch, c->scratch_bytes, st);
+  rc = launch_simulate_ordered(c->p, c->obs, c->u[cur], c->N, 0u, nullptr, c->d[cur], c->scratch,
+                               c->scratch_bytes, st, nullptr, nullptr, 128, 0, nullptr, nullptr,
+                               c->cfg.surrogate ? c->ard : nullptr);
   if (rc) return rc;
   ABC_CUDA_TRY(cudaEventRecord(c->es1, st));
   if (c->cfg.surrogate &&

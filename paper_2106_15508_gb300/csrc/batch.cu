@@ -135,8 +135,9 @@ int screened_batch(const SurView& s, const SimParams& p, const int32_t* obs, con
     return rc;
   // each simulated slot with its own Philox counters; the rest get +inf
   if (ev) ABC_CUDA_TRY(cudaEventRecord(ev[1], st));
-  if ((rc = launch_simulate(p, obs, s.cmp_u, M, s.cmp_slot, c1, ABC_TAG_SIM, nullptr, s.cmp_d,
-                            nullptr, st, c1_dev, nullptr, sim_threads, s.ard, 0, s.Mc)))
+  if ((rc = launch_simulate_ordered(p, obs, s.cmp_u, M, c1, nullptr, s.cmp_d, scratch,
+                                    scratch_bytes, st, c1_dev, nullptr, sim_threads, 0, s.cmp_slot,
+                                    s.Mc, s.ard)))
     return rc;
   if (ev) ABC_CUDA_TRY(cudaEventRecord(ev[2], st));
   // audited slots (flag 2) are never accepted; each accepted particle keeps its rho

@@ -123,17 +123,20 @@ int launch_simulate(const SimParams&, const int32_t*, const float*, int64_t, con
                     const uint32_t* c1_dev = nullptr, const int* off_dev = nullptr,
                     int threads = 128, int32_t* ard_last = nullptr, int64_t m_sub = 0,
                     const int* n_dev = nullptr, const int32_t* perm = nullptr);
-// A batch of n SAIRD slots (the SIM stream, slot index as c0) simulated in
-// the order of a key that groups similar trajectories into warps (same
-// results as launch_simulate); below kSimOrderMin slots, for the toy model
-// or without observations it is launch_simulate.  scratch: at least
-// sim_order_scratch_bytes(n), free until the simulation has run.
+// A batch of n SAIRD slots (the SIM stream; c0 = c0_idx[i] or the slot
+// index) simulated in the order of a key that groups similar trajectories
+// into warps (same results as launch_simulate; with n_dev the first *n_dev
+// slots are ordered among themselves); below kSimOrderMin slots, for the
+// toy model or without observations it is launch_simulate.  scratch: at
+// least sim_order_scratch_bytes(n), free until the simulation has run.
 constexpr int64_t kSimOrderMin = 16384;
 size_t sim_order_scratch_bytes(int64_t n);
 int launch_simulate_ordered(const SimParams& p, const int32_t* obs, const float* u, int64_t n,
                             uint32_t c1, const uint8_t* skip, double* dist, void* scratch,
                             size_t bytes, cudaStream_t st, const uint32_t* c1_dev = nullptr,
-                            const int* off_dev = nullptr, int threads = 128, int64_t m_sub = 0);
+                            const int* off_dev = nullptr, int threads = 128, int64_t m_sub = 0,
+                            const uint32_t* c0_idx = nullptr, const int* n_dev = nullptr,
+                            int32_t* ard_last = nullptr);
 int launch_select(const double*, int64_t, int64_t, double*, void*, size_t, cudaStream_t);
 int launch_resample_prefix(const double*, const double*, int64_t, const double*, int, uint32_t*,
                            uint64_t*, void*, size_t, cudaStream_t);

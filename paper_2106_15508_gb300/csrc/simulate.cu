@@ -202,8 +202,10 @@ k_simulate(SimParams p, const int32_t* __restrict__ obs,
   __syncthreads();
   // perm (nullable): thread t runs slot perm[t] (an order that groups similar
   // trajectories into warps); every slot keeps its own counters and outputs
+  // (with n_dev, over the slots in use only; the others keep their place)
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t i = perm && t < n ? static_cast<int64_t>(perm[t]) : t;
+  int64_t i = t;
+  if (perm && t < n && t < (n_dev ? static_cast<int64_t>(*n_dev) : n)) i = perm[t];
   // n_dev (nullable): the slots in use, counted on the device (a compacted
   // list of capacity n); the others get distance +inf
   const bool live = i < n && !(n_dev && i >= *n_dev) && !(skip && skip[i]);
@@ -310,10 +312,10 @@ __global__ void k_philox(const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t
 // slots sort last.
 __global__ void k_sim_order_key(SimParams p, const float* __restrict__ u, int64_t n,
                                 const uint8_t* __restrict__ skip, const int* __restrict__ off_dev,
-                                uint32_t* __restrict__ key) {
+                                const int* __restrict__ n_dev, uint32_t* __restrict__ key) {
   if (off_dev && *off_dev) return;
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || (n_dev && i >= *n_dev)) return;
   if (skip && skip[i]) {
     key[i] = 0xFFFFu;
     return;
@@ -400,10 +402,11 @@ size_t sim_order_scratch_bytes(int64_t n) {
 int launch_simulate_ordered(const SimParams& p, const int32_t* obs, const float* u, int64_t n,
                             uint32_t c1, const uint8_t* skip, double* dist, void* scratch,
                             size_t bytes, cudaStream_t st, const uint32_t* c1_dev,
-                            const int* off_dev, int threads, int64_t m_sub) {
+                            const int* off_dev, int threads, int64_t m_sub,
+                            const uint32_t* c0_idx, const int* n_dev, int32_t* ard_last) {
   if (p.model != ABC_MODEL_SAIRD || n < kSimOrderMin || !obs)
-    return launch_simulate(p, obs, u, n, nullptr, c1, ABC_TAG_SIM, skip, dist, nullptr, st,
-                           c1_dev, off_dev, threads, nullptr, m_sub);
+    return launch_simulate(p, obs, u, n, c0_idx, c1, ABC_TAG_SIM, skip, dist, nullptr, st,
+                           c1_dev, off_dev, threads, ard_last, m_sub, n_dev);
   const SimOrderLayout l = sim_order_layout(n);
   if (!scratch || bytes < l.total) return ABC_E_SCRATCH;
   char* b = static_cast<char*>(scratch);
@@ -411,13 +414,13 @@ int launch_simulate_ordered(const SimParams& p, const int32_t* obs, const float*
   uint32_t* key_s = reinterpret_cast<uint32_t*>(b + l.key_s);
   int32_t* perm = reinterpret_cast<int32_t*>(b + l.perm);
   k_sim_order_key<<<static_cast<unsigned>(ceil_div(n, 256)), 256, 0, st>>>(p, u, n, skip, off_dev,
-                                                                            key);
+                                                                            n_dev, key);
   ABC_LAUNCH_CHECK();
-  int rc = launch_radix_sort(key, nullptr, key_s, perm, n, nullptr, 16, b + l.sort,
+  int rc = launch_radix_sort(key, nullptr, key_s, perm, n, n_dev, 16, b + l.sort,
                              l.total - l.sort, st);
   if (rc) return rc;
-  return launch_simulate(p, obs, u, n, nullptr, c1, ABC_TAG_SIM, skip, dist, nullptr, st, c1_dev,
-                         off_dev, threads, nullptr, m_sub, nullptr, perm);
+  return launch_simulate(p, obs, u, n, c0_idx, c1, ABC_TAG_SIM, skip, dist, nullptr, st, c1_dev,
+                         off_dev, threads, ard_last, m_sub, n_dev, perm);
 }
 
 int launch_prior(const SimParams& p, int64_t n, float* u, cudaStream_t st) {

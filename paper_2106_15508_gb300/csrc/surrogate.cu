@@ -165,41 +165,6 @@ __host__ __device__ __forceinline__ int mlp_packed_index(int r, int k) {
   return ((((r >> 3) << 5) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
 }
 
-// layer 1 + GELU for n samples (u [8][n]) into packed bf16 tiles of h1;
-// xstat (nullable): input means [8] then standard deviations [8], the
-// network's input being (u - mean) / sd
-__global__ void k_mlp_l1_pack(const float* __restrict__ u, int64_t n, int64_t npad,
-                              const __nv_bfloat16* __restrict__ wb, const float* __restrict__ w,
-                              __nv_bfloat16* __restrict__ Hpk, const float* __restrict__ xstat) {
-  const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= npad) return;
-  float x[8];
-#pragma unroll
-  for (int d = 0; d < 8; ++d) {
-    x[d] = j < n ? u[d * n + j] : 0.0f;
-    if (xstat) x[d] = __fdiv_rn(__fsub_rn(x[d], xstat[d]), xstat[8 + d]);
-  }
-  __nv_bfloat16* tile = Hpk + (j / kMlpM) * (kMlpM * kMlpH);
-  const int r = static_cast<int>(j % kMlpM);
-  for (int c = 0; c < kMlpH / 8; ++c) {
-    uint32_t h[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int o = 8 * c + e;
-      float z = w[kOffB1 + o];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) z = __fmaf_rn(__bfloat162float(wb[kOffW1 + o * 8 + k]), x[k], z);
-      h[e] = __bfloat16_as_ushort(__float2bfloat16_rn(j < n ? gelu_f(z) : 0.0f));
-    }
-    uint4 v;
-    v.x = h[0] | (h[1] << 16);
-    v.y = h[2] | (h[3] << 16);
-    v.z = h[4] | (h[5] << 16);
-    v.w = h[6] | (h[7] << 16);
-    *reinterpret_cast<uint4*>(tile + mlp_packed_index(r, 8 * c)) = v;
-  }
-}
-
 // W2 (bf16, [out][in]) as the B operand: rows = out, K = in
 __global__ void k_mlp_pack_w2(const __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ W2pk) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -211,116 +176,279 @@ __global__ void k_mlp_pack_w2(const __nv_bfloat16* __restrict__ wb, __nv_bfloat1
 // epilogue barrier of the 16 epilogue warps (named barrier 1)
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
 
-// Y[j][0..3] = W3 gelu(W2 h1_j + b2) + b3 for 128 samples per CTA
+// the hidden-layer tile is in shared memory: the 16 epilogue warps and the
+// MMA warp (named barrier 2)
+__device__ __forceinline__ void tile_ready_sync() { asm volatile("bar.sync 2, 544;" ::: "memory"); }
+
+// generic-proxy writes to shared memory made visible to the tensor cores
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// The input layer as a tensor-core product: K = 32 tiles (8 x 8 core
+// matrices, 4 along K, row groups 512 B apart).  The A operand holds each
+// sample's standardised input split into three bf16 parts (x = hi + mid +
+// lo exactly for normal fp32 x: 3 x 8 significant bits), k = 8 s + d for
+// part s of feature d, zeros for s = 3; the B operand holds W1 (bf16) in
+// the three part slots, so the fp32 accumulation over k forms W1 x.
+__host__ __device__ __forceinline__ int mlp_packed_index32(int r, int k) {
+  return ((((r >> 3) << 2) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+constexpr uint32_t kMlpXTile = kMlpM * 32 * 2;    // 8 KB: split inputs of a tile
+constexpr uint32_t kMlpW1Bytes = kMlpH * 32 * 2;  // 16 KB: W1 in the three part slots
+
+__global__ void k_mlp_pack_w1(const __nv_bfloat16* __restrict__ wb,
+                              __nv_bfloat16* __restrict__ W1pk) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kMlpH * 32) return;
+  const int o = idx >> 5, k = idx & 31;
+  W1pk[mlp_packed_index32(o, k)] = (k >> 3) < 3 ? wb[kOffW1 + o * 8 + (k & 7)]
+                                                : __float2bfloat16_rn(0.0f);
+}
+
+// shared memory of the inference kernel: the hidden-layer tile, W2, W1 in
+// the part slots, the split-input tile (reused for the epilogue's partial
+// outputs once the input product has run), b1, b2, W3, barriers
+constexpr size_t kMlpInfSmem = 1024 + kMlpATile + kMlpBBytes + kMlpW1Bytes + kMlpXTile +
+                               (kMlpH + kMlpH + 4 * kMlpH) * 4 + 64;
+
+// the split input tile is ready (named barrier 2), the hidden-layer tile
+// is ready (named barrier 3): the 16 epilogue warps and the MMA warp
+__device__ __forceinline__ void x_ready_sync() { asm volatile("bar.sync 2, 544;" ::: "memory"); }
+__device__ __forceinline__ void h_ready_sync() { asm volatile("bar.sync 3, 544;" ::: "memory"); }
+
+// Y[j][0..3] = W3 gelu(W2 gelu(W1 x_j + b1) + b2) + b3 for u [8][n] (x = the
+// standardised u when xstat is given: (u - mean) / sd).  Persistent CTAs;
+// W2 and the packed W1 are loaded once per CTA by bulk copies.  Per tile of
+// 128 samples:
+//   1. the 16 epilogue warps write the split inputs (warp group g = w / 4
+//      writes part g of the 32 rows of its lane quarter q = w % 4; group 3
+//      the zero part);
+//   2. the MMA warp runs the input layer, 128 x 256 x 32, into TMEM columns
+//      0..255;
+//   3. the epilogue warps add b1, apply GELU, round to bf16 and write the
+//      hidden-layer tile in the UMMA operand layout (warp w: TMEM lanes
+//      32 q .. + 31, columns 64 g .. + 63);
+//   4. the MMA warp runs layer 2, 128 x 256 x 256, into columns 256..511;
+//   5. the epilogue warps add b2, apply GELU and form layer 3, the four
+//      column groups' partial outputs added in order.
+// Every wait is bounded; a wait that gives up records its code in *err and
+// the CTA runs to its end without further waits.
 __global__ void __launch_bounds__(kMlpThreads, 1)
-k_mlp_tc(const uint8_t* __restrict__ Hpk, const uint8_t* __restrict__ W2pk,
-         const float* __restrict__ w, const __nv_bfloat16* __restrict__ wb, int64_t n,
-         float* __restrict__ Y, unsigned* err) {
+k_mlp_infer_tc(const float* __restrict__ u, int64_t n, int64_t ntiles,
+               const uint8_t* __restrict__ W2pk, const uint8_t* __restrict__ W1pk,
+               const float* __restrict__ w, const __nv_bfloat16* __restrict__ wb,
+               const float* __restrict__ xstat, float* __restrict__ Y, unsigned* err) {
   extern __shared__ uint8_t mlp_smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(mlp_smem_raw) + 1023) &
                                              ~uintptr_t(1023));
-  uint8_t* sA = base;
-  uint8_t* sB = base + kMlpATile;
-  float* sW3 = reinterpret_cast<float*>(sB + kMlpBBytes);
-  float* sb2 = sW3 + 4 * kMlpH;
-  float* sY = sb2 + kMlpH;  // [4 column groups][128 rows][4] partial outputs
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sY + 4 * kMlpM * 4);
+  uint8_t* sA = base;                       // hidden layer, K = 256
+  uint8_t* sB = sA + kMlpATile;             // W2
+  uint8_t* sW1 = sB + kMlpBBytes;           // W1, K = 32
+  uint8_t* sX = sW1 + kMlpW1Bytes;          // split inputs, K = 32
+  float* sY = reinterpret_cast<float*>(sX);  // [4 column groups][128 rows][4], after step 2
+  float* sb1 = reinterpret_cast<float*>(sX + kMlpXTile);
+  float* sb2 = sb1 + kMlpH;
+  float4* sW3 = reinterpret_cast<float4*>(sb2 + kMlpH);  // [256] (W3[0..3][col])
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sW3 + kMlpH);
   uint64_t* full = bars;
-  uint64_t* tfull = bars + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  uint64_t* t1full = bars + 1;
+  uint64_t* t2full = bars + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < 4 * kMlpH; i += blockDim.x) sW3[i] = __bfloat162float(wb[kOffW3 + i]);
-  for (int i = threadIdx.x; i < kMlpH; i += blockDim.x) sb2[i] = w[kOffB2 + i];
+  for (int i = threadIdx.x; i < kMlpH; i += blockDim.x) {
+    sb1[i] = w[kOffB1 + i];
+    sb2[i] = w[kOffB2 + i];
+    sW3[i] = make_float4(__bfloat162float(wb[kOffW3 + i]), __bfloat162float(wb[kOffW3 + kMlpH + i]),
+                         __bfloat162float(wb[kOffW3 + 2 * kMlpH + i]),
+                         __bfloat162float(wb[kOffW3 + 3 * kMlpH + i]));
+  }
   if (threadIdx.x == 0) {
     mbar_init(full, 1);
-    mbar_init(tfull, 1);
+    mbar_init(t1full, 1);
+    mbar_init(t2full, 1);
     fence_mbar_init();
   }
   if (warp == kMlpEpiWarps + 1) {
-    tmem_alloc(tmem_slot, kMlpH);
+    tmem_alloc(tmem_slot, 2 * kMlpH);
     tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const uint32_t acc1 = tmem, acc2 = tmem + kMlpH;
   if (warp == kMlpEpiWarps) {
+    // W2 and W1, once per CTA
     if (lane == 0) {
-      mbar_expect_tx(full, kMlpATile + kMlpBBytes);
-      bulk_g2s(sA, Hpk + static_cast<size_t>(blockIdx.x) * kMlpATile, kMlpATile, full);
+      mbar_expect_tx(full, kMlpBBytes + kMlpW1Bytes);
       bulk_g2s(sB, W2pk, kMlpBBytes, full);
-      mbar_wait(full, 0u, err, 21u);  // both copies landed before the CTA can exit
+      bulk_g2s(sW1, W1pk, kMlpW1Bytes, full);
+      mbar_wait(full, 0u, err, 31u);  // the copies landed before the CTA can exit
     }
   } else if (warp == kMlpEpiWarps + 1) {
-    if (lane == 0 && mbar_wait(full, 0u, err, 22u)) {
+    bool ok = lane == 0 ? mbar_wait(full, 0u, err, 32u) : true;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    int committed = -1;
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB), x0 = smem_u32(sX), w0 = smem_u32(sW1);
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      x_ready_sync();
       tc_fence_after();
-      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      if (lane == 0 && ok) {
 #pragma unroll
-      for (int kk = 0; kk < kMlpH / 16; ++kk)
-        umma_bf16(tmem, smem_desc(a0 + kk * 256, 128, 4096), smem_desc(b0 + kk * 256, 128, 4096),
-                  kMlpIdesc, kk > 0 ? 1u : 0u);
-      umma_commit(tfull);
-      mbar_wait(tfull, 0u, err, 23u);
+        for (int kk = 0; kk < 2; ++kk)
+          umma_bf16(acc1, smem_desc(x0 + kk * 256, 128, 512), smem_desc(w0 + kk * 256, 128, 512),
+                    kMlpIdesc, kk > 0 ? 1u : 0u);
+        umma_commit(t1full);
+      }
+      __syncwarp();
+      h_ready_sync();
+      tc_fence_after();
+      if (lane == 0 && ok) {
+#pragma unroll
+        for (int kk = 0; kk < kMlpH / 16; ++kk)
+          umma_bf16(acc2, smem_desc(a0 + kk * 256, 128, 4096),
+                    smem_desc(b0 + kk * 256, 128, 4096), kMlpIdesc, kk > 0 ? 1u : 0u);
+        umma_commit(t2full);
+        committed = it;
+      }
+      __syncwarp();
     }
+    // the last products completed before the tensor memory is released
+    if (lane == 0 && committed >= 0) mbar_wait(t2full, static_cast<uint32_t>(committed) & 1u, err, 33u);
     __syncwarp();
   } else {
-    // tcgen05.ld is warp-collective: the whole warp reads or none of it
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull, 0u, err, 24u));
-    tc_fence_after();
     const int q = warp & 3, g = warp >> 2;
     const int r = q * 32 + lane;
-    float y[4] = {0.f, 0.f, 0.f, 0.f};
-    if (ok) {
-      for (int cc = 0; cc < 2; ++cc) {
-        const int c = 2 * g + cc;
-        float v[32];
-        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + c * 32, v);
+    const uint32_t lanes = static_cast<uint32_t>(q * 32) << 16;
+    bool ok = true;
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int64_t j = t * kMlpM + r;
+      // 1. part g of row r's split input (zeros for g = 3 and padding rows)
+      {
+        uint32_t hv[4] = {0u, 0u, 0u, 0u};
+        if (g < 3 && j < n) {
+          uint32_t pb[8];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int col = c * 32 + i;
-          const float h = gelu_f(v[i] + sb2[col]);
+          for (int d = 0; d < 8; ++d) {
+            float x = u[d * n + j];
+            if (xstat) x = __fdiv_rn(__fsub_rn(x, xstat[d]), xstat[8 + d]);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            const float r1 = __fsub_rn(x, __bfloat162float(hi));
+            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid)));
+            pb[d] = __bfloat16_as_ushort(g == 0 ? hi : (g == 1 ? mid : lo));
+          }
 #pragma unroll
-          for (int o = 0; o < 4; ++o) y[o] = __fmaf_rn(h, sW3[o * kMlpH + col], y[o]);
+          for (int e = 0; e < 4; ++e) hv[e] = pb[2 * e] | (pb[2 * e + 1] << 16);
+        }
+        *reinterpret_cast<uint4*>(sX + 2 * mlp_packed_index32(r, 8 * g)) =
+            make_uint4(hv[0], hv[1], hv[2], hv[3]);
+      }
+      fence_proxy_async_smem();
+      tc_fence_before();  // this thread's reads of the previous tile's TMEM
+      x_ready_sync();
+      // 3. the hidden layer from the input product
+      ok = __all_sync(0xffffffffu, ok && mbar_wait(t1full, static_cast<uint32_t>(it) & 1u, err, 34u));
+      tc_fence_after();
+      if (ok) {
+        for (int cc = 0; cc < 2; ++cc) {
+          const int cb = 2 * g + cc;
+          float v[32];
+          tmem_ld32(acc1 + lanes + cb * 32, v);
+#pragma unroll
+          for (int c8 = 0; c8 < 4; ++c8) {
+            uint32_t hh[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int col = cb * 32 + c8 * 8 + 2 * e;
+              const float h0 = gelu_f(v[c8 * 8 + 2 * e] + sb1[col]);
+              const float h1 = gelu_f(v[c8 * 8 + 2 * e + 1] + sb1[col + 1]);
+              hh[e] = __bfloat16_as_ushort(__float2bfloat16_rn(j < n ? h0 : 0.0f)) |
+                      (static_cast<uint32_t>(__bfloat16_as_ushort(
+                           __float2bfloat16_rn(j < n ? h1 : 0.0f))) << 16);
+            }
+            *reinterpret_cast<uint4*>(sA + 2 * mlp_packed_index(r, cb * 32 + c8 * 8)) =
+                make_uint4(hh[0], hh[1], hh[2], hh[3]);
+          }
         }
       }
-    }
+      fence_proxy_async_smem();
+      tc_fence_before();
+      h_ready_sync();
+      // 5. layer 2's activation and layer 3
+      ok = __all_sync(0xffffffffu, ok && mbar_wait(t2full, static_cast<uint32_t>(it) & 1u, err, 35u));
+      tc_fence_after();
+      float y[4] = {0.f, 0.f, 0.f, 0.f};
+      if (ok) {
+        for (int cc = 0; cc < 2; ++cc) {
+          const int cb = 2 * g + cc;
+          float v[32];
+          tmem_ld32(acc2 + lanes + cb * 32, v);
 #pragma unroll
-    for (int o = 0; o < 4; ++o) sY[(g * kMlpM + r) * 4 + o] = y[o];
-    epi_sync();
-    const int64_t j = static_cast<int64_t>(blockIdx.x) * kMlpM + r;
-    if (g == 0 && j < n) {
-#pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        float t = sY[r * 4 + o];  // column groups added in order
-        for (int gg = 1; gg < 4; ++gg) t += sY[(gg * kMlpM + r) * 4 + o];
-        Y[j * 4 + o] = t + w[kOffB3 + o];
+          for (int i = 0; i < 32; ++i) {
+            const int col = cb * 32 + i;
+            const float hh = gelu_f(v[i] + sb2[col]);
+            const float4 w3 = sW3[col];
+            y[0] = __fmaf_rn(hh, w3.x, y[0]);
+            y[1] = __fmaf_rn(hh, w3.y, y[1]);
+            y[2] = __fmaf_rn(hh, w3.z, y[2]);
+            y[3] = __fmaf_rn(hh, w3.w, y[3]);
+          }
+        }
       }
+#pragma unroll
+      for (int o = 0; o < 4; ++o) sY[(g * kMlpM + r) * 4 + o] = y[o];
+      epi_sync();
+      if (g == 0 && j < n) {
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          float tt = sY[r * 4 + o];  // column groups added in order
+          for (int gg = 1; gg < 4; ++gg) tt += sY[(gg * kMlpM + r) * 4 + o];
+          Y[j * 4 + o] = tt + w[kOffB3 + o];
+        }
+      }
+      epi_sync();  // the partial outputs are read before the next tile's inputs overwrite them
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == kMlpEpiWarps + 1) tmem_dealloc(tmem, kMlpH);
+  if (warp == kMlpEpiWarps + 1) tmem_dealloc(tmem, 2 * kMlpH);
 }
 
-size_t mlp_infer_scratch_bytes(int64_t n) {
-  const int64_t npad = ceil_div(std::max<int64_t>(n, 1), kMlpM) * kMlpM;
-  return align256(static_cast<size_t>(npad) * kMlpH * 2) + align256(kMlpBBytes) + align256(16);
+size_t mlp_infer_scratch_bytes(int64_t) {
+  return align256(kMlpBBytes) + align256(kMlpW1Bytes) + align256(16);
 }
 
 int mlp_infer_prepare() {
-  ABC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(kMlpSmem)));
+  ABC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(kMlpInfSmem)));
   return ABC_OK;
 }
 
-// the error word of mlp_infer(n) inside its scratch
-unsigned* mlp_infer_err(void* scratch, int64_t n) {
-  const int64_t npad = ceil_div(std::max<int64_t>(n, 1), kMlpM) * kMlpM;
-  return reinterpret_cast<unsigned*>(static_cast<char*>(scratch) +
-                                     align256(static_cast<size_t>(npad) * kMlpH * 2) +
-                                     align256(kMlpBBytes));
+// the error word of mlp_infer inside its scratch
+unsigned* mlp_infer_err(void* scratch, int64_t) {
+  return reinterpret_cast<unsigned*>(static_cast<char*>(scratch) + align256(kMlpBBytes) +
+                                     align256(kMlpW1Bytes));
 }
+
+namespace {
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+    else
+      return 1;
+  }
+  return n;
+}
+}  // namespace
 
 // Y [n][4] (standardised outputs) for u [8][n]; the error word lives in scratch
 int mlp_infer(const MlpState& s, const float* u, int64_t n, float* Y, void* scratch, size_t bytes,
@@ -328,21 +456,20 @@ int mlp_infer(const MlpState& s, const float* u, int64_t n, float* Y, void* scra
               const float* xstat) {
   if (n <= 0) return ABC_OK;
   if (bytes < mlp_infer_scratch_bytes(n)) return ABC_E_SCRATCH;
-  const int64_t npad = ceil_div(n, kMlpM) * kMlpM;
-  char* b = static_cast<char*>(scratch);
-  auto* Hpk = reinterpret_cast<__nv_bfloat16*>(b);
-  auto* W2pk = reinterpret_cast<__nv_bfloat16*>(b + align256(static_cast<size_t>(npad) * kMlpH * 2));
+  const int64_t ntiles = ceil_div(n, kMlpM);
+  auto* W2pk = reinterpret_cast<__nv_bfloat16*>(scratch);
+  auto* W1pk = reinterpret_cast<__nv_bfloat16*>(static_cast<char*>(scratch) + align256(kMlpBBytes));
   unsigned* err = err_word ? err_word : mlp_infer_err(scratch, n);
   if (err_out) *err_out = err;
   if (reset_err) ABC_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
   k_mlp_pack_w2<<<(kMlpH * kMlpH + 255) / 256, 256, 0, st>>>(s.wb, W2pk);
   ABC_LAUNCH_CHECK();
-  k_mlp_l1_pack<<<static_cast<unsigned>(ceil_div(npad, 128)), 128, 0, st>>>(u, n, npad, s.wb, s.w,
-                                                                           Hpk, xstat);
+  k_mlp_pack_w1<<<(kMlpH * 32 + 255) / 256, 256, 0, st>>>(s.wb, W1pk);
   ABC_LAUNCH_CHECK();
-  k_mlp_tc<<<static_cast<unsigned>(npad / kMlpM), kMlpThreads, kMlpSmem, st>>>(
-      reinterpret_cast<const uint8_t*>(Hpk), reinterpret_cast<const uint8_t*>(W2pk), s.w, s.wb, n,
-      Y, err);
+  const unsigned grid = static_cast<unsigned>(std::min<int64_t>(ntiles, sm_count()));
+  k_mlp_infer_tc<<<grid, kMlpThreads, kMlpInfSmem, st>>>(
+      u, n, ntiles, reinterpret_cast<const uint8_t*>(W2pk), reinterpret_cast<const uint8_t*>(W1pk),
+      s.w, s.wb, xstat, Y, err);
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }
