@@ -16,7 +16,9 @@ rank; what a generation needs from the other ranks arrives by all-gathers:
     and every rank normalises them (fp64).
 
 Every Philox counter is the one of the unsharded run, so the result equals
-the single-rank generation bit for bit, whatever the number of ranks.
+the single-rank generation bit for bit, whatever the number of ranks.  The
+MCMC baseline (one tuned step, Sec. 2.4.1 and 3.1) adapts its step after
+each batch from the all-gathered batch's counts, on every rank alike.
 
 The local steps come from a backend object (the CUDA library's entry points
 on the rank's GPU, `CudaBackend`); the exchanges from torch.distributed
@@ -28,7 +30,7 @@ import math
 
 import torch
 
-from . import (ABC_BETA_PAPER, ABC_OK, ABC_W_IMPORTANCE, TAG_SIM, abc_accept_append,
+from . import (ABC_BETA_PAPER, ABC_OK, ABC_STEP_MCMC, ABC_W_IMPORTANCE, TAG_SIM, abc_accept_append,
                abc_accept_scratch_bytes, abc_normalize, abc_normalize_scratch_bytes, abc_prefix_scratch_bytes,
                abc_propose, abc_resample_prefix, abc_select_kth, abc_select_scratch_bytes, abc_simulate,
                abc_weights, abc_weights_scratch_bytes)
@@ -78,6 +80,42 @@ class Population:
 
 
 @dataclasses.dataclass
+class McmcStep:
+    """The MCMC baseline's tuned step across generations: s (a variance in
+    unit-cube coordinates, fp64), the adaptations made, the batches walked
+    with the step so far and the adaptation window in batches."""
+    s: float
+    k: int = 0
+    batches: int = 0
+    window: int = 0
+
+    @classmethod
+    def start(cls, cfg):
+        """After generation 0: s = mcmc_s0 (as fp32), the window mcmc_adapt
+        or a tenth of the run budget."""
+        import numpy as np
+        window = cfg.mcmc_adapt if cfg.mcmc_adapt > 0 else -(-cfg.max_total_batches // 10)
+        return cls(float(np.float32(cfg.mcmc_s0)), 0, 0, window)
+
+    def step32(self):
+        import numpy as np
+        return float(np.float32(self.s))
+
+    def adapt(self, accepted, simulated):
+        """After a batch (Eq. 14-15 as the library reads them): inside the
+        window s <- s (1 + (A - A_T) / ((1 - A_T)(k + 1))), A = accepted /
+        simulated (0 if none), A_T = 0.234; IEEE double operations in the
+        library's order."""
+        if self.batches < self.window:
+            a_t = 0.234
+            a = accepted / simulated if simulated > 0 else 0.0
+            gain = (1.0 - a_t) * float(self.k + 1)
+            self.s = self.s * (1.0 + (a - a_t) / gain)
+            self.k += 1
+        self.batches += 1
+
+
+@dataclasses.dataclass
 class GenStats:
     eps: float = 0.0
     eps1: float = 0.0
@@ -88,10 +126,11 @@ class GenStats:
     status: int = ABC_OK
 
 
-def generation(backend, comm, t, eps1, pop, N, M, alpha, weight_mode, max_batches):
+def generation(backend, comm, t, eps1, pop, N, M, alpha, weight_mode, max_batches, mcmc=None):
     """Generation t >= 1 from the (replicated) population `pop`; returns the
     new population (replicated on every rank) and the statistics.  Slots of
-    a batch and rows of the weight pass are split over the ranks."""
+    a batch and rows of the weight pass are split over the ranks.  mcmc: the
+    McmcStep of an MCMC-baseline run (updated in place), else None."""
     st = GenStats()
     k = min(max(math.ceil(alpha * N), 1), N)  # the lower order statistic of rank ceil(alpha N)
     eps = backend.kth(pop.d, k)
@@ -104,7 +143,8 @@ def generation(backend, comm, t, eps1, pop, N, M, alpha, weight_mode, max_batche
     b = 0
     while b < max_batches and filled < N:
         c1 = (t << 16) | b
-        mine = backend.propose(pop.u, prefix, total, eps, eps1, t, c1, lo, hi - lo)
+        mine = backend.propose(pop.u, prefix, total, eps, eps1, t, c1, lo, hi - lo,
+                               s_fixed=mcmc.step32() if mcmc is not None else None)
         d_mine = backend.simulate(mine["u"], c1, lo, hi - lo, mine["flag"])
         batch = {"u": comm.allgather_last(mine["u"], M), "d": comm.allgather_last(d_mine, M),
                  "s": comm.allgather_last(mine["s"], M), "anc": comm.allgather_last(mine["anc"], M),
@@ -112,6 +152,8 @@ def generation(backend, comm, t, eps1, pop, N, M, alpha, weight_mode, max_batche
         filled, acc, exh = backend.accept(batch, eps, new, filled)
         st.accepted += acc
         st.exhausted += exh
+        if mcmc is not None:
+            mcmc.adapt(acc, M - exh)
         b += 1
     st.batches = b
     if filled < N:
@@ -166,7 +208,7 @@ class CudaBackend:
         abc_resample_prefix(d, W, n, self.scal[0:1], mode, q, pre, *self._sc())
         return q, pre, int(pre[-1].item()) & ((1 << 64) - 1)
 
-    def propose(self, u, prefix, total, eps, eps1, t, c1, lo, count):
+    def propose(self, u, prefix, total, eps, eps1, t, c1, lo, count, s_fixed=None):
         self.scal[0], self.scal[1] = eps, eps1
         c0 = torch.arange(lo, lo + count, dtype=torch.int32, device=self.dev)
         out = {"u": torch.empty((8, count), dtype=torch.float32, device=self.dev),
@@ -176,8 +218,10 @@ class CudaBackend:
                "flag": torch.empty(count, dtype=torch.uint8, device=self.dev)}
         paper = self.cfg.beta_mode == ABC_BETA_PAPER
         bb = (2 * t if t <= 512 else 0) if paper else self.cfg.beta_b
+        # the MCMC baseline walks with the run's step (beta_a under ABC_STEP_MCMC)
+        a = s_fixed if self.cfg.beta_mode == ABC_STEP_MCMC else self.cfg.beta_a
         abc_propose(self.cfg, u, u.shape[1], prefix, self.scal[0:1], self.scal[1:2],
-                    self.cfg.beta_a, bb, count, c0, c1, out["u"], out["s"], out["anc"],
+                    a, bb, count, c0, c1, out["u"], out["s"], out["anc"],
                     out["att"], out["flag"])
         self._c0 = c0
         return out
@@ -212,4 +256,4 @@ class CudaBackend:
         return W, float(self.scal[2].item())
 
 
-__all__ = ["block", "Comm", "Population", "GenStats", "generation", "CudaBackend"]
+__all__ = ["block", "Comm", "Population", "GenStats", "McmcStep", "generation", "CudaBackend"]

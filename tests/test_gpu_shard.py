@@ -64,3 +64,40 @@ def test_single_rank_driver_equals_context(weight_mode):
             eps1, pop = st.eps1, new
     finally:
         G.abc_free(ctx)
+
+
+def test_single_rank_driver_mcmc_step_equals_context():
+    """The MCMC baseline through the driver: the step adapts on the host
+    after every batch (McmcStep, IEEE double) and walks on the device as
+    the proposal kernel's fixed step; four generations equal a context whose
+    step adapts on the device, bit for bit, the steps included."""
+    from paper_2106_15508_gb300 import shard
+    N, M = 2048, 700
+    cfg = saird_config(N, 30, 100_000, seed=43, batch_size=M, weight_mode=G.ABC_W_PAPER,
+                       beta_mode=G.ABC_STEP_MCMC, mcmc_s0=0.03, mcmc_adapt=9, max_batches=400)
+    obs = oracle_obs(cfg)[0]
+    ctx = G.abc_init(cfg, obs)
+    try:
+        G.abc_generation(ctx)  # stage 0
+        pop = _device_population(ctx, N)
+        be = shard.CudaBackend(cfg, obs, N, M)
+        comm = shard.Comm(1, 0)
+        mcmc = shard.McmcStep.start(cfg)
+        eps1 = 0.0
+        for t in range(1, 5):
+            s_first = mcmc.step32()
+            new, st = shard.generation(be, comm, t, eps1, pop, N, M, cfg.survival_alpha,
+                                       cfg.weight_mode, cfg.max_batches, mcmc=mcmc)
+            assert G.abc_generation(ctx) == G.ABC_OK and st.status == 0
+            ref = _device_population(ctx, N)
+            g = G.abc_get_stats(ctx, t)
+            assert (st.eps, st.batches, st.accepted, st.exhausted) == \
+                   (g.eps, g.batches, g.accepted, g.exhausted), t
+            assert np.float32(g.beta_a) == np.float32(s_first)
+            assert np.float32(g.mcmc_s) == np.float32(mcmc.s), t
+            for a, b in ((new.u, ref.u), (new.d, ref.d), (new.s, ref.s), (new.anc, ref.anc)):
+                assert torch.equal(a.view(torch.uint8), b.view(torch.uint8)), t
+            eps1, pop = st.eps1, new
+        assert mcmc.k == 9
+    finally:
+        G.abc_free(ctx)

@@ -4,7 +4,8 @@ weights all-gathered.  On CPU ranks (gloo, world sizes 2 and 3) with the
 oracle's steps as the local backend, three generations must equal the
 unsharded oracle's generations bit for bit -- populations, tolerances,
 batch counts, weights -- for the paper's weights and for importance
-weights, with slot and row blocks of unequal sizes."""
+weights, with slot and row blocks of unequal sizes, and for the MCMC
+baseline, whose step adapts after every batch on every rank."""
 import math
 import os
 import socket
@@ -48,14 +49,17 @@ class OracleBackend:
         q, pre, tot = self.O.resample_prefix(d.numpy(), W.numpy(), eps, mode)
         return torch.from_numpy(q.view(np.int32)), torch.from_numpy(pre.view(np.int64)), tot
 
-    def propose(self, u, prefix, total, eps, eps1, t, c1, lo, count):
+    def propose(self, u, prefix, total, eps, eps1, t, c1, lo, count, s_fixed=None):
         c = self.c
         ratio = eps / eps1 if eps1 > 0 else 1.0
-        a, bf, bb = self.O.beta_shape(c.beta_mode, ratio, t, c.beta_a, c.beta_b, c.beta_p1,
-                                      c.beta_p2)
+        if s_fixed is None:
+            a, bf, bb = self.O.beta_shape(c.beta_mode, ratio, t, c.beta_a, c.beta_b, c.beta_p1,
+                                          c.beta_p2)
+        else:
+            a, bf, bb = 0.0, 0.0, 0
         o = self.O.propose(self.m, u.numpy(), prefix.numpy().view(np.uint64), total, a, bb, count,
                            c1, c.max_redraw, c0_idx=np.arange(lo, lo + count, dtype=np.uint32),
-                           beta_bf=bf)
+                           beta_bf=bf, s_fixed=s_fixed or 0.0)
         self._lo = lo
         return {k: torch.from_numpy(np.ascontiguousarray(o[k])) for k in ("u", "s", "anc", "flag")}
 
@@ -86,7 +90,7 @@ class OracleBackend:
         return torch.from_numpy(W), float(ess)
 
 
-def _setup_run(weight_mode):
+def _setup_run(weight_mode, method="bdss"):
     import oracle as O
     from paper_2106_15508_gb300 import workloads as WL
     P, T, N = 100_000, 20, 500
@@ -94,19 +98,23 @@ def _setup_run(weight_mode):
     obs, _, _ = O.synth_obs(m)
     m.set_obs(obs)
     # M = 37 slots per batch: blocks of 19/18 (two ranks) or 13/12/12 (three)
-    c = O.make_smc(N, M=37, beta_mode=0, weight_mode=weight_mode, max_batches=400)
+    mode = O.MCMC_MODE if method == "mcmc" else 0
+    c = O.make_smc(N, M=37, beta_mode=mode, weight_mode=weight_mode, max_batches=400,
+                   mcmc_s0=0.02, mcmc_adapt=40)
     return m, c
 
 
-def _worker(rank, ws, port, weight_mode, out):
+def _worker(rank, ws, port, weight_mode, method, out):
     sys.path.insert(0, ROOT)
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=ws)
     try:
         import oracle as O
         from paper_2106_15508_gb300 import shard
-        m, c = _setup_run(weight_mode)
+        m, c = _setup_run(weight_mode, method)
         pop0 = O.generation0(m, c)
+        ms = O.mcmc_start(c)
+        mcmc = shard.McmcStep(ms.s, 0, 0, O.mcmc_window(c)) if method == "mcmc" else None
         pop = shard.Population(torch.from_numpy(pop0.u.copy()), torch.from_numpy(pop0.d.copy()),
                                torch.from_numpy(pop0.W.copy()), torch.from_numpy(pop0.s.copy()),
                                torch.from_numpy(pop0.anc.copy()))
@@ -115,37 +123,42 @@ def _worker(rank, ws, port, weight_mode, out):
         eps1, res = 0.0, []
         for t in range(1, 4):
             pop, st = shard.generation(be, comm, t, eps1, pop, c.N, c.M, c.alpha, c.weight_mode,
-                                       c.max_batches)
+                                       c.max_batches, mcmc=mcmc)
             assert st.status == 0
             eps1 = st.eps1
             res.append((st.eps, st.eps1, st.batches, st.accepted, st.exhausted, st.ess,
                         pop.u.numpy().copy(), pop.d.numpy().copy(), pop.W.numpy().copy(),
-                        pop.s.numpy().copy(), pop.anc.numpy().copy()))
+                        pop.s.numpy().copy(), pop.anc.numpy().copy(),
+                        (mcmc.s, mcmc.k, mcmc.batches) if mcmc else None))
         out[rank] = res
         dist.barrier()
     finally:
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("ws,weight_mode", [(2, 0), (3, 1), (2, 1)])
-def test_sharded_generations_equal_the_unsharded_oracle(ws, weight_mode):
+@pytest.mark.parametrize("ws,weight_mode,method", [(2, 0, "bdss"), (3, 1, "bdss"), (2, 1, "bdss"),
+                                                    (2, 0, "mcmc"), (3, 1, "mcmc")])
+def test_sharded_generations_equal_the_unsharded_oracle(ws, weight_mode, method):
     sys.path.insert(0, ROOT)
     import oracle as O
     port = _free_port()
     ctx = mp.get_context("spawn")
     with ctx.Manager() as mgr:
         out = mgr.dict()
-        mp.start_processes(_worker, args=(ws, port, weight_mode, out), nprocs=ws, join=True,
-                           start_method="spawn")
+        mp.start_processes(_worker, args=(ws, port, weight_mode, method, out), nprocs=ws,
+                           join=True, start_method="spawn")
         res = dict(out)
-    m, c = _setup_run(weight_mode)
+    m, c = _setup_run(weight_mode, method)
     pop = O.generation0(m, c)
+    ms = O.mcmc_start(c) if method == "mcmc" else None
     eps1 = 0.0
     for t in range(1, 4):
-        new, st = O.generation(m, c, t, eps1, pop)
+        new, st = O.generation(m, c, t, eps1, pop, ms)
         assert st.status == 0
         for rank in range(ws):
-            eps, e1, batches, acc, exh, ess, u, d, W, s, anc = res[rank][t - 1]
+            eps, e1, batches, acc, exh, ess, u, d, W, s, anc, step = res[rank][t - 1]
+            if ms is not None:
+                assert step == (ms.s, ms.k, ms.batches), (rank, t)
             assert (eps, e1, batches, acc, exh) == (st.eps, st.eps1, st.batches,
                                                     st.accepted_total, st.exhausted), (rank, t)
             assert ess == st.ess or (math.isnan(ess) and math.isnan(st.ess))
