@@ -279,14 +279,16 @@ def _sur_config(N, **kw):
     return saird_config(N, 60, 100_000, seed=4, **base)
 
 
-def test_screened_generation_keeps_oracle_proposals():
+@pytest.mark.parametrize("NN", [4096, 20000])
+def test_screened_generation_keeps_oracle_proposals(NN):
     """Paper weights (mode A) keep the run bit-exact before the screen: from
     the oracle's generation-1 population, generation 2 (not screened: nothing
     is trained yet) equals the oracle and trains the surrogate, and
     generation 3 screens.  Every particle of generation 3 is the
     oracle's proposal at some (batch, slot) with d <= eps, bit for bit, in
-    (batch, slot) order; the stats add up."""
-    cfg = _sur_config(4096)
+    (batch, slot) order; the stats add up.  At 20000 slots per batch the
+    compacted slots are simulated in the order of the regime key."""
+    cfg = _sur_config(NN)
     obs, _, _ = oracle_obs(cfg)
     m, c = oracle_model(cfg, obs), oracle_smc(cfg)
     pop = O.generation0(m, c)
@@ -300,7 +302,7 @@ def test_screened_generation_keeps_oracle_proposals():
         assert G.abc_generation(ctx) == 0
         p2, ost = O.generation(m, c, 2, eps1, pop)
         assert ost.status == 0
-        g2 = get_population(ctx, 4096)
+        g2 = get_population(ctx, NN)
         assert np.array_equal(g2["u"].view(np.uint32), p2.u.view(np.uint32))
         assert np.array_equal(g2["d"], p2.d)
         s2 = G.abc_get_stats(ctx, 2)
@@ -308,10 +310,10 @@ def test_screened_generation_keeps_oracle_proposals():
         # generation 3 screens
         assert G.abc_generation(ctx) == 0
         s3 = G.abc_get_stats(ctx, 3)
-        g3 = get_population(ctx, 4096)
+        g3 = get_population(ctx, NN)
     finally:
         G.abc_free(ctx)
-    N = M = 4096
+    N = M = NN
     eps = O.kth(p2.d, O.rank(0.5, N))
     assert s3.eps == eps
     q, pre, tot = O.resample_prefix(p2.d, p2.W, eps, 0)
@@ -339,7 +341,7 @@ def test_screened_generation_keeps_oracle_proposals():
     assert s3.screened + passed + s3.exhausted == s3.batches * M
     assert 0 <= s3.audit_accepted <= s3.audited <= s3.screened
     frr = s3.audit_accepted / max(s3.audited, 1)
-    REPORT["screened_generation"] = dict(
+    REPORT["screened_generation_%d" % NN] = dict(
         batches=int(s3.batches), oracle_acceptable=int(ou.shape[1]), screened=int(s3.screened),
         audited=int(s3.audited), audit_accepted=int(s3.audit_accepted),
         false_rejection_rate=frr, train_loss=float(s3.train_loss),
