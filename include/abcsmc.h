@@ -133,7 +133,8 @@ typedef struct {
    * with probability rho = clamp(sigmoid((log1p eps_t - y0) / tau), rho_min,
    * 1) and its importance weight divided by rho; screened-out proposals are
    * simulated anyway with probability audit_frac to estimate the
-   * false-rejection rate (never accepted).  Single-run contexts only. */
+   * false-rejection rate (never accepted).  Single-run contexts and
+   * batched runs (abc_batch_init) alike.  Not with ABC_STEP_MCMC. */
   int32_t surrogate;        /* 0 off, 1 on                                              */
   int32_t surrogate_start;  /* first generation that screens (>= 1)                      */
   int32_t surrogate_steps;  /* Adam steps after each generation                          */
@@ -532,9 +533,11 @@ ABC_API int abc_mlp_grad(abc_mlp* m, const float* X, const float* T, int32_t B, 
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step >= 1) on the fp32
  * parameters; refreshes the bf16 copy. */
 ABC_API int abc_mlp_adam(abc_mlp* m, const float* grad, int64_t step, float lr, void* stream);
-/* Inference on tensor cores: Y device [n][4] for u device [8][n] (layer 1 on
- * CUDA cores, hidden layer rounded to bf16, layer 2 on tcgen05 with GELU and
- * layer 3 fused).  Synchronises the stream. */
+/* Inference on tensor cores: Y device [n][4] for u device [8][n] (the input
+ * layer and layer 2 on tcgen05 with fp32 accumulation, the input split into
+ * three bf16 parts so that the input layer is fp32-accurate, the hidden layer
+ * rounded to bf16, GELU and layer 3 fused into the epilogue).  Synchronises
+ * the stream. */
 ABC_API int abc_mlp_forward(abc_mlp* m, const float* u, int64_t n, float* Y, void* scratch,
                             size_t scratch_bytes, void* stream);
 ABC_API void abc_mlp_free(abc_mlp* m);

@@ -12,10 +12,11 @@
 // Training: the three 256-wide products of a step on tcgen05 (bf16 operands,
 // fp32 accumulation) with fused epilogues, layers 1 and 3 and the gradient
 // reductions on CUDA cores, Adam in fp32.
-// Inference: layer 1 on CUDA cores writes the hidden layer as bf16 tiles in
-// the tensor-core operand layout; layer 2 runs on tcgen05 (M = 128, N = 256,
-// K = 256) with bias + GELU + layer 3 fused into the epilogue (one thread per
-// sample reads its 256 accumulators from tensor memory).
+// Inference: one persistent kernel per call; per tile of 128 samples the
+// input layer runs on tcgen05 from the standardised inputs split into three
+// bf16 parts (K = 32), its bias + GELU form the bf16 hidden layer in shared
+// memory, layer 2 runs on tcgen05 (M = 128, N = 256, K = 256) and bias +
+// GELU + layer 3 are fused into the epilogue.
 #include <cuda_bf16.h>
 
 #include <algorithm>
