@@ -817,11 +817,58 @@ __global__ void k_nz_max(const double* __restrict__ lw, int64_t n, double* part)
   }
 }
 
-// mode 0: w = exp(lw - M) written to W and summed (the only exponentials:
-// fp64 is slow on this GPU); mode 1: W scaled by 1/S in place, W^2 summed
+// exp(x) for -700 <= x <= 0 to fp64 precision with five fp64 operations
+// (this GPU's fp64 rate is far below its fp32 rate).  Tang's table-driven
+// method (ACM TOMS 15(2), 1989): x = (64 e + j) ln2 / 64 + r, |r| <= about
+// ln2 / 128, reduced in fp64 by two fma with ln2 / 64 split into a double
+// and its tail; r as a float pair (rh + rl); exp(r) - 1 = r + r^2 / 2 + r^3
+// (1/6 + r/24 + r^2/120), the first two terms as float pairs through
+// error-free fma remainders and sums, the rest in fp32 (below 3e-8); times
+// 2^(j/64) from a table of float pairs (tab, made from the fp64 exp2); the
+// pair recombined exactly in fp64 and scaled by 2^e in the exponent field.
+// Relative error below 1e-14 (tests compare with the host's exp).
+__device__ __forceinline__ double exp_tang(double x, const float2* tab) {
+  const double kLn2By64 = 0x1.62e42fefa39efp-7;     // ln 2 / 64, nearest double
+  const double kLn2By64T = 0x1.abc9e3b39803fp-62;   // ln 2 / 64 - kLn2By64
+  const float kf = rintf(__double2float_rn(x) * 92.33248261689366f);  // 64 / ln 2
+  const int k = static_cast<int>(kf);
+  const double kd = static_cast<double>(k);
+  double r = fma(-kd, kLn2By64, x);
+  r = fma(-kd, kLn2By64T, r);
+  const float rh = __double2float_rn(r);
+  const float rl = __double2float_rn(r - static_cast<double>(rh));
+  const float t = rh * rh;
+  const float te = fmaf(rh, rh, -t);                 // rh^2 = t + te exactly
+  const float hh = 0.5f * t;
+  const float hl = 0.5f * fmaf(2.0f * rh, rl, te);   // r^2 / 2 = hh + hl
+  const float q = t * rh * fmaf(rh, fmaf(rh, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f);
+  const float sh = rh + hh;                          // two-sum of rh and hh
+  const float bb = sh - rh;
+  const float se = (rh - (sh - bb)) + (hh - bb);
+  const float sl = se + (rl + (hl + q));             // exp(r) - 1 = sh + sl
+  const float2 T = tab[k & 63];                      // 2^(j/64) = T.x + T.y
+  const float P = T.x * sh;
+  const float Pe = fmaf(T.x, sh, -P);
+  const float Rh = T.x + P;                          // T.x >= 1 > |P|
+  const float Re = P - (Rh - T.x);
+  const float Rl = Re + (Pe + (T.y + fmaf(T.x, sl, T.y * sh)));
+  const double w = static_cast<double>(Rh) + static_cast<double>(Rl);
+  const long long e = static_cast<long long>(k >> 6);  // floor(k / 64)
+  return __longlong_as_double(__double_as_longlong(w) + (e << 52));
+}
+
+// mode 0: w = exp(lw - M) written to W and summed (the only exponentials);
+// mode 1: W scaled by 1/S in place, W^2 summed
 __global__ void k_nz_sum(const double* __restrict__ lw, int64_t n, const double* stat, int mode,
                          double* __restrict__ W, double* part) {
   __shared__ double sm[32];
+  __shared__ float2 tab[64];
+  if (mode == 0 && threadIdx.x < 64) {
+    const double v = exp2(static_cast<double>(threadIdx.x) / 64.0);
+    const float h = __double2float_rn(v);
+    tab[threadIdx.x] = make_float2(h, __double2float_rn(v - static_cast<double>(h)));
+  }
+  __syncthreads();
   const double M = stat[0];
   const bool uniform = !(M > -__longlong_as_double(0x7ff0000000000000ll));
   const double inv = mode == 1 ? (uniform ? 1.0 / static_cast<double>(n) : 1.0 / stat[1]) : 0.0;
@@ -831,7 +878,9 @@ __global__ void k_nz_sum(const double* __restrict__ lw, int64_t n, const double*
     double w;
     if (mode == 0) {
       const double li = lw[i];
-      w = uniform ? 1.0 : (li == li ? exp(li - M) : 0.0);
+      const double x = li - M;
+      // NaN weights count as 0; below -700 (weights under 1e-304) the library exp
+      w = uniform ? 1.0 : (x >= -700.0 ? exp_tang(x, tab) : (x == x ? exp(x) : 0.0));
       W[i] = w;
     } else {
       w = uniform ? inv : W[i] * inv;

@@ -408,6 +408,33 @@ def test_normalize_matches_oracle():
     assert np.allclose(host(W), oW, rtol=1e-12, atol=0) and oW[1] == 0.0
 
 
+def test_normalize_exponentials_across_the_range():
+    """The normalisation's table-driven exponential over log-weight gaps
+    from 0 to -720 (-700 and below take the library exp), against the
+    oracle's libm exp: the weights relative to the largest one (exp of the
+    gap, free of the sum's rounding; gaps down to -690, whose weights stay
+    clear of fp64's subnormal range) within 5e-14, the weights themselves
+    within 1e-12 (the sums are added in different orders)."""
+    n = (1 << 16) + 3
+    r = IN.rng(77)
+    lw = -720.0 * r.random(n)
+    lw[0] = 0.0
+    lw[1:50] = -r.random(49) * 1e-6      # tiny reductions
+    lw[50:60] = -700.0 + r.random(10) * 1e-9  # at the switch
+    W = empty(n, torch.float64)
+    ess = empty(1, torch.float64)
+    sc = scratch(G.abc_normalize_scratch_bytes(n))
+    G.abc_normalize(dev(lw), n, W, ess, sc, sc.numel())
+    oW, oess = O.normalize(lw)
+    got = host(W)
+    ok = lw >= -690.0  # weights / S far from fp64's subnormal range
+    rel = np.abs(got[ok] / got[0] - np.exp(lw[ok])) / np.exp(lw[ok])
+    REPORT["normalize_exp_max_rel"] = float(rel.max())
+    assert rel.max() <= 5e-14, rel.max()
+    assert np.allclose(got, oW, rtol=1e-12, atol=0)
+    assert abs(host(ess)[0] - oess) <= 1e-12 * oess
+
+
 # ---------------------------------------------------------- context --------
 def _stats_match(g, o):
     assert g.eps == o.eps and g.eps1 == o.eps1
