@@ -189,23 +189,41 @@ k_scan_tiles(const T* __restrict__ in, int64_t ntiles, T* __restrict__ out, T* t
 
 __global__ void k_prefix_tiles(const uint32_t* __restrict__ q, int64_t n,
                                const unsigned long long* __restrict__ tile_off,
-                               uint64_t* __restrict__ prefix) {
+                               uint64_t* __restrict__ prefix, bool vec) {
   __shared__ unsigned long long sm[32];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * kTile + 4 * threadIdx.x;
+  // four consecutive weights per thread: one 16-byte load and two 16-byte
+  // stores where all four exist and the arrays are 16-byte aligned (vec)
+  const bool whole = vec && base + 3 < n;
   unsigned long long v[4];
-  unsigned long long s = 0;
+  if (whole) {
+    const uint4 w4 = *reinterpret_cast<const uint4*>(q + base);
+    v[0] = w4.x;
+    v[1] = w4.y;
+    v[2] = w4.z;
+    v[3] = w4.w;
+  } else {
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    v[e] = base + e < n ? q[base + e] : 0ull;
-    s += v[e];
+    for (int e = 0; e < 4; ++e) v[e] = base + e < n ? q[base + e] : 0ull;
   }
+  const unsigned long long s = v[0] + v[1] + v[2] + v[3];
   const unsigned long long inc = block_incl_scan<unsigned long long>(s, sm);
-  unsigned long long run = tile_off[blockIdx.x] + inc - s;
+  const unsigned long long r0 = tile_off[blockIdx.x] + inc - s + v[0];
+  const unsigned long long r1 = r0 + v[1], r2 = r1 + v[2], r3 = r2 + v[3];
+  if (whole) {
+    *reinterpret_cast<ulonglong2*>(prefix + base) = make_ulonglong2(r0, r1);
+    *reinterpret_cast<ulonglong2*>(prefix + base + 2) = make_ulonglong2(r2, r3);
+  } else {
+    const unsigned long long r[4] = {r0, r1, r2, r3};
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    run += v[e];
-    if (base + e < n) prefix[base + e] = run;
+    for (int e = 0; e < 4; ++e)
+      if (base + e < n) prefix[base + e] = r[e];
   }
+}
+
+// the tile kernel's 16-byte accesses need both arrays 16-byte aligned
+static bool prefix_vec_ok(const uint32_t* q, const uint64_t* prefix) {
+  return (reinterpret_cast<uintptr_t>(q) & 15u) == 0 && (reinterpret_cast<uintptr_t>(prefix) & 15u) == 0;
 }
 
 size_t prefix_scratch_bytes(int64_t n) {
@@ -233,7 +251,8 @@ int launch_resample_prefix(const double* d, const double* W, int64_t n, const do
   ABC_LAUNCH_CHECK();
   k_scan_tiles<unsigned long long><<<1, 1024, 0, st>>>(tsum, nt, toff, nullptr);
   ABC_LAUNCH_CHECK();
-  k_prefix_tiles<<<static_cast<unsigned>(nt), kTileThr, 0, st>>>(q, n, toff, prefix);
+  k_prefix_tiles<<<static_cast<unsigned>(nt), kTileThr, 0, st>>>(q, n, toff, prefix,
+                                                               prefix_vec_ok(q, prefix));
   ABC_LAUNCH_CHECK();
   return ABC_OK;
 }

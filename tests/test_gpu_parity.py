@@ -202,6 +202,24 @@ def test_resample_prefix_bitexact(n, mode):
     assert np.array_equal(host(pre, np.uint64), opre)
 
 
+@pytest.mark.parametrize("n", [4099, 100_003])
+def test_resample_prefix_unaligned_outputs(n):
+    """q and prefix at 4- and 8-byte offsets (not 16-byte aligned): the scan
+    takes its element-wise path and the result is the same."""
+    d = IN.distances(n, 3, ties=True)
+    W = IN.weights(n, 4)
+    eps = O.kth(d, O.rank(0.5, n))
+    qb = empty(n + 1, torch.int32)
+    pb = empty(n + 1, torch.int64)
+    q, pre = qb[1:], pb[1:]
+    sc = scratch(G.abc_prefix_scratch_bytes(n))
+    G.abc_resample_prefix(dev(d), dev(W), n, dev(np.array([eps])), G.ABC_W_IMPORTANCE, q, pre,
+                          sc, sc.numel())
+    oq, opre, _ = O.resample_prefix(d, W, eps, 1)
+    assert np.array_equal(host(q, np.uint32), oq)
+    assert np.array_equal(host(pre, np.uint64), opre)
+
+
 def test_resample_prefix_degenerate():
     n = 3000
     d = np.full(n, 7.0)
