@@ -821,18 +821,36 @@ int launch_survivors(const float* u, const uint32_t* q, int64_t n, float* cu, fl
 // ------------------------------------------------------ A10 normalise ----
 constexpr int kNormBlocks = 512;
 
+// An unsigned key that orders doubles like their values (on the integer
+// pipes: fp64 is slow here); NaN maps to 0, below -inf, so that the maximum
+// ignores it as fmax does.
+__device__ __forceinline__ unsigned long long ord_key(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  if ((b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull) return 0ull;
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord_value(unsigned long long k) {
+  return __longlong_as_double(static_cast<long long>(
+      (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k));
+}
+
 __global__ void k_nz_max(const double* __restrict__ lw, int64_t n, double* part) {
-  __shared__ double sm[32];
-  double m = -__longlong_as_double(0x7ff0000000000000ll);
+  __shared__ unsigned long long sm[32];
+  unsigned long long m = ord_key(-__longlong_as_double(0x7ff0000000000000ll));
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    m = fmax(m, lw[i]);
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const unsigned long long k = ord_key(lw[i]);
+    m = k > m ? k : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long k = __shfl_xor_sync(0xffffffffu, m, o);
+    m = k > m ? k : m;
+  }
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < (blockDim.x >> 5); ++w) m = fmax(m, sm[w]);
-    part[blockIdx.x] = m;
+    for (int w = 1; w < (blockDim.x >> 5); ++w) m = sm[w] > m ? sm[w] : m;
+    part[blockIdx.x] = ord_value(m);
   }
 }
 
