@@ -43,6 +43,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "batch.cuh"
 #include "common.cuh"
@@ -778,89 +779,110 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     }
     int* lst = cand + (slot * rows + (refine ? row : 0)) * kCandCap;
     int nlist = 0;
-    TileIter it = tiles();
-    for (int t = 0; t < ntiles; ++t) {
-      const int tile = it.next();
-      const int b = t & 1;
-      const uint32_t tph = static_cast<uint32_t>(t >> 1) & 1u;
-      // warp-uniform: tcgen05.ld below is warp-collective
-      if (!__all_sync(0xffffffffu, mbar_wait(&sm.tfull[b], tph, err, 7u, wait_ns))) break;
-      tc_fence_after();
-      float ts = 0.0f;
-      // this thread's two 32-column chunks of the tile (c = g, g + 4), both
-      // loads in flight before one wait
-      static_assert(kTcN / 32 == 2 * kTcGroups, "two chunks per epilogue thread");
-      if (w_exp || w_cand) {
-        float vv[2][32];
-        tmem_ld32x2(lane_base + static_cast<uint32_t>(b * kTcN + g * 32),
-                    lane_base + static_cast<uint32_t>(b * kTcN + (g + kTcGroups) * 32), vv[0],
-                    vv[1]);
+    // The tile loop is compiled once per warp kind (exponential sums,
+    // candidate lists, both, neither) and entered on the warp-uniform votes
+    // above, so that a warp of class-0 rows carries no candidate code (a
+    // thread-varying class test inside one loop body was if-converted into
+    // per-column predicated work).
+    auto tile_loop = [&](auto exp_kind, auto cand_kind) {
+      constexpr bool kExp = decltype(exp_kind)::value;
+      constexpr bool kCand = decltype(cand_kind)::value;
+      TileIter it = tiles();
+      for (int t = 0; t < ntiles; ++t) {
+        const int tile = it.next();
+        const int b = t & 1;
+        const uint32_t tph = static_cast<uint32_t>(t >> 1) & 1u;
+        // warp-uniform: tcgen05.ld below is warp-collective
+        if (!__all_sync(0xffffffffu, mbar_wait(&sm.tfull[b], tph, err, 7u, wait_ns))) break;
+        tc_fence_after();
+        float ts = 0.0f;
+        // this thread's two 32-column chunks of the tile (c = g, g + 4), both
+        // loads in flight before one wait
+        static_assert(kTcN / 32 == 2 * kTcGroups, "two chunks per epilogue thread");
+        if constexpr (kExp || kCand) {
+          float vv[2][32];
+          tmem_ld32x2(lane_base + static_cast<uint32_t>(b * kTcN + g * 32),
+                      lane_base + static_cast<uint32_t>(b * kTcN + (g + kTcGroups) * 32), vv[0],
+                      vv[1]);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int c = g + h * kTcGroups;
-          const float (&v)[32] = vv[h];
-          // maxima of the four 8-column groups and of the chunk (three-input
-          // max instructions)
-          float gm[4];
+          for (int h = 0; h < 2; ++h) {
+            const int c = g + h * kTcGroups;
+            const float (&v)[32] = vv[h];
+            // maxima of the four 8-column groups and of the chunk (three-input
+            // max instructions)
+            float gm[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            gm[k] = max3(max3(v[8 * k], v[8 * k + 1], v[8 * k + 2]),
-                         max3(v[8 * k + 3], v[8 * k + 4], v[8 * k + 5]),
-                         fmaxf(v[8 * k + 6], v[8 * k + 7]));
-          const float cm = fmaxf(max3(gm[0], gm[1], gm[2]), gm[3]);
-          if (refine) {
-            lb = fmaxf(lb, cm - dl);
-            const float thr = lb - dl - kCandMargin;
-            if (cm > thr) {
-              // only the groups above the threshold are scanned (candidates
-              // are rare: a few per row among all columns)
-              // accumulator column c * 32 + i holds sorted column tile * kTcN + i * 8 + c
-              const int col0 = tile * kTcN + c;
+            for (int k = 0; k < 4; ++k)
+              gm[k] = max3(max3(v[8 * k], v[8 * k + 1], v[8 * k + 2]),
+                           max3(v[8 * k + 3], v[8 * k + 4], v[8 * k + 5]),
+                           fmaxf(v[8 * k + 6], v[8 * k + 7]));
+            const float cm = fmaxf(max3(gm[0], gm[1], gm[2]), gm[3]);
+            if constexpr (kCand) {
+              if (refine) {
+                lb = fmaxf(lb, cm - dl);
+                const float thr = lb - dl - kCandMargin;
+                if (cm > thr) {
+                  // only the groups above the threshold are scanned (candidates
+                  // are rare: a few per row among all columns)
+                  // accumulator column c * 32 + i holds sorted column
+                  // tile * kTcN + i * 8 + c
+                  const int col0 = tile * kTcN + c;
 #pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                if (!(gm[k] > thr)) continue;
+                  for (int k = 0; k < 4; ++k) {
+                    if (!(gm[k] > thr)) continue;
 #pragma unroll
-                for (int i = 8 * k; i < 8 * k + 8; ++i)
-                  if (v[i] > thr && col0 + 8 * i < nc) {
-                    if (nlist < kCandCap) lst[nlist] = col0 + 8 * i;
-                    ++nlist;
+                    for (int i = 8 * k; i < 8 * k + 8; ++i)
+                      if (v[i] > thr && col0 + 8 * i < nc) {
+                        if (nlist < kCandCap) lst[nlist] = col0 + 8 * i;
+                        ++nlist;
+                      }
                   }
+                }
               }
             }
-          }
-          if (!w_exp) continue;
-          if (cm > m) {
-            const float f = ex2(m - cm);
-            S *= f;
-            cS *= f;
-            ts *= f;
-            m = cm;
-          }
-          // v - m and the running sum in packed fp32x2 (two columns per
-          // instruction); the exponentials one by one on the MUFU
-          // (four independent accumulators keep the add chain short)
-          const unsigned long long m2 = f2_pack(m, m);
-          unsigned long long acc[4];
+            if constexpr (kExp) {
+              if (cm > m) {
+                const float f = ex2(m - cm);
+                S *= f;
+                cS *= f;
+                ts *= f;
+                m = cm;
+              }
+              // v - m and the running sum in packed fp32x2 (two columns per
+              // instruction); the exponentials one by one on the MUFU
+              // (four independent accumulators keep the add chain short)
+              const unsigned long long m2 = f2_pack(m, m);
+              unsigned long long acc[4];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) acc[a] = f2_pack(0.0f, 0.0f);
+              for (int a = 0; a < 4; ++a) acc[a] = f2_pack(0.0f, 0.0f);
 #pragma unroll
-          for (int i = 0; i < 32; i += 2) {
-            float d0, d1;
-            f2_unpack(f2_sub(f2_pack(v[i], v[i + 1]), m2), d0, d1);
-            acc[(i >> 1) & 3] = f2_add(acc[(i >> 1) & 3], f2_pack(ex2(d0), ex2(d1)));
+              for (int i = 0; i < 32; i += 2) {
+                float d0, d1;
+                f2_unpack(f2_sub(f2_pack(v[i], v[i + 1]), m2), d0, d1);
+                acc[(i >> 1) & 3] = f2_add(acc[(i >> 1) & 3], f2_pack(ex2(d0), ex2(d1)));
+              }
+              float a0, a1;
+              f2_unpack(f2_add(f2_add(acc[0], acc[1]), f2_add(acc[2], acc[3])), a0, a1);
+              ts += a0 + a1;
+            }
           }
-          float a0, a1;
-          f2_unpack(f2_add(f2_add(acc[0], acc[1]), f2_add(acc[2], acc[3])), a0, a1);
-          ts += a0 + a1;
+        }
+        tc_fence_before();
+        mbar_arrive(&sm.tempty[b]);
+        if constexpr (kExp) {
+          const float y = ts - cS;
+          const float tt = S + y;
+          cS = (tt - S) - y;
+          S = tt;
         }
       }
-      tc_fence_before();
-      mbar_arrive(&sm.tempty[b]);
-      const float y = ts - cS;
-      const float tt = S + y;
-      cS = (tt - S) - y;
-      S = tt;
-    }
+    };
+    using Yes = std::true_type;
+    using No = std::false_type;
+    if (w_exp && w_cand) tile_loop(Yes{}, Yes{});
+    else if (w_exp) tile_loop(Yes{}, No{});
+    else if (w_cand) tile_loop(No{}, Yes{});
+    else tile_loop(No{}, No{});
     if (row >= 0) {
       if (cls == 0) part[slot * rows + row] = make_float2(m, S);
       ccnt[slot * rows + row] = refine ? nlist : 0;
