@@ -804,32 +804,38 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
           tmem_ld32x2(lane_base + static_cast<uint32_t>(b * kTcN + g * 32),
                       lane_base + static_cast<uint32_t>(b * kTcN + (g + kTcGroups) * 32), vv[0],
                       vv[1]);
+          // chunk maxima (a tree of three-input maxima); class-1 lanes also
+          // list their candidates
+          float cmx[2];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const int c = g + h * kTcGroups;
             const float (&v)[32] = vv[h];
-            // maxima of the four 8-column groups and of the chunk (three-input
-            // max instructions)
-            float gm[4];
+            float t1[12];
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-              gm[k] = max3(max3(v[8 * k], v[8 * k + 1], v[8 * k + 2]),
-                           max3(v[8 * k + 3], v[8 * k + 4], v[8 * k + 5]),
-                           fmaxf(v[8 * k + 6], v[8 * k + 7]));
-            const float cm = fmaxf(max3(gm[0], gm[1], gm[2]), gm[3]);
+            for (int k = 0; k < 10; ++k) t1[k] = max3(v[3 * k], v[3 * k + 1], v[3 * k + 2]);
+            t1[10] = v[30];
+            t1[11] = v[31];
+            float t2[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) t2[k] = max3(t1[3 * k], t1[3 * k + 1], t1[3 * k + 2]);
+            const float cm = fmaxf(max3(t2[0], t2[1], t2[2]), t2[3]);
+            cmx[h] = cm;
             if constexpr (kCand) {
               if (refine) {
                 lb = fmaxf(lb, cm - dl);
                 const float thr = lb - dl - kCandMargin;
                 if (cm > thr) {
-                  // only the groups above the threshold are scanned (candidates
-                  // are rare: a few per row among all columns)
-                  // accumulator column c * 32 + i holds sorted column
-                  // tile * kTcN + i * 8 + c
-                  const int col0 = tile * kTcN + c;
+                  // only the 8-column groups whose maximum is above the
+                  // threshold are scanned (candidates are rare: a few per row
+                  // among all columns); accumulator column c * 32 + i holds
+                  // sorted column tile * kTcN + i * 8 + c
+                  const int col0 = tile * kTcN + g + h * kTcGroups;
 #pragma unroll
                   for (int k = 0; k < 4; ++k) {
-                    if (!(gm[k] > thr)) continue;
+                    const float gm = max3(max3(v[8 * k], v[8 * k + 1], v[8 * k + 2]),
+                                          max3(v[8 * k + 3], v[8 * k + 4], v[8 * k + 5]),
+                                          fmaxf(v[8 * k + 6], v[8 * k + 7]));
+                    if (!(gm > thr)) continue;
 #pragma unroll
                     for (int i = 8 * k; i < 8 * k + 8; ++i)
                       if (v[i] > thr && col0 + 8 * i < nc) {
@@ -840,31 +846,35 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
                 }
               }
             }
-            if constexpr (kExp) {
-              if (cm > m) {
-                const float f = ex2(m - cm);
-                S *= f;
-                cS *= f;
-                ts *= f;
-                m = cm;
-              }
-              // v - m and the running sum in packed fp32x2 (two columns per
-              // instruction); the exponentials one by one on the MUFU
-              // (four independent accumulators keep the add chain short)
-              const unsigned long long m2 = f2_pack(m, m);
-              unsigned long long acc[4];
+          }
+          if constexpr (kExp) {
+            // one rescale per tile, without a branch: the running maximum
+            // takes the tile's, and the sums scale by 2^(m_old - m_new)
+            // (1 when it did not move; 0 on the first tile, from -inf)
+            const float mn = max3(m, cmx[0], cmx[1]);
+            const float f = ex2(m - mn);
+            S *= f;
+            cS *= f;
+            m = mn;
+            // v - m and the running sum in packed fp32x2 (two columns per
+            // instruction); the exponentials one by one on the MUFU
+            // (four independent accumulators keep the add chains short)
+            const unsigned long long m2 = f2_pack(m, m);
+            unsigned long long acc[4];
 #pragma unroll
-              for (int a = 0; a < 4; ++a) acc[a] = f2_pack(0.0f, 0.0f);
+            for (int a = 0; a < 4; ++a) acc[a] = f2_pack(0.0f, 0.0f);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
 #pragma unroll
               for (int i = 0; i < 32; i += 2) {
                 float d0, d1;
-                f2_unpack(f2_sub(f2_pack(v[i], v[i + 1]), m2), d0, d1);
+                f2_unpack(f2_sub(f2_pack(vv[h][i], vv[h][i + 1]), m2), d0, d1);
                 acc[(i >> 1) & 3] = f2_add(acc[(i >> 1) & 3], f2_pack(ex2(d0), ex2(d1)));
               }
-              float a0, a1;
-              f2_unpack(f2_add(f2_add(acc[0], acc[1]), f2_add(acc[2], acc[3])), a0, a1);
-              ts += a0 + a1;
             }
+            float a0, a1;
+            f2_unpack(f2_add(f2_add(acc[0], acc[1]), f2_add(acc[2], acc[3])), a0, a1);
+            ts = a0 + a1;
           }
         }
         tc_fence_before();
