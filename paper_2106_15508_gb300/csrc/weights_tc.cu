@@ -787,6 +787,84 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     auto tile_loop = [&](auto exp_kind, auto cand_kind) {
       constexpr bool kExp = decltype(exp_kind)::value;
       constexpr bool kCand = decltype(cand_kind)::value;
+      if constexpr (kExp && !kCand) {
+        // Exponential sums only: software-pipelined TMEM reads.  The load of
+        // a tile's second chunk runs while its first chunk is summed, and the
+        // load of the next tile's first chunk while the second is summed.
+        if (ntiles <= 0) return;
+        const uint32_t off0 = static_cast<uint32_t>(g * 32);
+        const uint32_t off1 = static_cast<uint32_t>((g + kTcGroups) * 32);
+        // adds a chunk to the tile sum ts: one branch-free rescale (the
+        // running maximum takes the chunk's; the sums scale by
+        // 2^(m_old - m_new), 0 on the first chunk from -inf), then 2^(v - m)
+        // in packed fp32x2 with four independent accumulators
+        auto sum_chunk = [&](const uint32_t (&r)[32], float& ts) {
+          float t1[12];
+#pragma unroll
+          for (int k = 0; k < 10; ++k)
+            t1[k] = max3(__uint_as_float(r[3 * k]), __uint_as_float(r[3 * k + 1]),
+                         __uint_as_float(r[3 * k + 2]));
+          t1[10] = __uint_as_float(r[30]);
+          t1[11] = __uint_as_float(r[31]);
+          float t2[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) t2[k] = max3(t1[3 * k], t1[3 * k + 1], t1[3 * k + 2]);
+          const float mn = max3(m, max3(t2[0], t2[1], t2[2]), t2[3]);
+          const float f = ex2(m - mn);
+          S *= f;
+          cS *= f;
+          ts *= f;
+          m = mn;
+          const unsigned long long m2 = f2_pack(m, m);
+          unsigned long long acc[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) acc[a] = f2_pack(0.0f, 0.0f);
+#pragma unroll
+          for (int i = 0; i < 32; i += 2) {
+            float d0, d1;
+            f2_unpack(f2_sub(f2_pack(__uint_as_float(r[i]), __uint_as_float(r[i + 1])), m2), d0,
+                      d1);
+            acc[(i >> 1) & 3] = f2_add(acc[(i >> 1) & 3], f2_pack(ex2(d0), ex2(d1)));
+          }
+          float a0, a1;
+          f2_unpack(f2_add(f2_add(acc[0], acc[1]), f2_add(acc[2], acc[3])), a0, a1);
+          ts += a0 + a1;
+        };
+        uint32_t ra[32], rb[32];
+        if (!__all_sync(0xffffffffu, mbar_wait(&sm.tfull[0], 0u, err, 7u, wait_ns))) return;
+        tc_fence_after();
+        tmem_ld32_start(lane_base + off0, ra);
+        tmem_ld_wait(ra);
+        for (int t = 0; t < ntiles; ++t) {
+          const int b = t & 1;
+          tmem_ld32_start(lane_base + static_cast<uint32_t>(b * kTcN) + off1, rb);
+          float ts = 0.0f;
+          sum_chunk(ra, ts);
+          tmem_ld_wait(rb);
+          // both chunks of tile t are in registers: its accumulator is free
+          tc_fence_before();
+          mbar_arrive(&sm.tempty[b]);
+          bool next = t + 1 < ntiles;
+          if (next) {
+            const int b1 = (t + 1) & 1;
+            const uint32_t tph1 = static_cast<uint32_t>((t + 1) >> 1) & 1u;
+            // warp-uniform: tcgen05.ld is warp-collective
+            next = __all_sync(0xffffffffu, mbar_wait(&sm.tfull[b1], tph1, err, 7u, wait_ns));
+            if (next) {
+              tc_fence_after();
+              tmem_ld32_start(lane_base + static_cast<uint32_t>(b1 * kTcN) + off0, ra);
+            }
+          }
+          sum_chunk(rb, ts);
+          if (next) tmem_ld_wait(ra);
+          const float y = ts - cS;
+          const float tt = S + y;
+          cS = (tt - S) - y;
+          S = tt;
+          if (!next) break;  // last tile, or a wait that gave up
+        }
+        return;
+      }
       TileIter it = tiles();
       for (int t = 0; t < ntiles; ++t) {
         const int tile = it.next();
