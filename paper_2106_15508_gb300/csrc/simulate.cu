@@ -305,7 +305,7 @@ __global__ void k_philox(const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t
 // order changes no result.
 //
 // Key of a slot: its expected-value path (each day's draws replaced by
-// their means n p; Euler steps of two days, fast-math arithmetic) over the T
+// their means n p; Euler steps of three days, fast-math arithmetic) over the T
 // days; c counts the draws of that path whose n min(p, 1 - p) is below 10
 // (the sampler's inversion regime, trivial draws included) and dpk is the
 // day of its largest I; key = min(c, 511) << 7 | min(dpk, 127).  Skipped
@@ -337,19 +337,20 @@ __global__ void k_sim_order_key(SimParams p, const float* __restrict__ u, int64_
   const float qI = fminf(fI, 1.0f - fI), qA = fminf(fA, 1.0f - fA);
   int c = 0, dpk = 0;
   float peak = 0.0f;
-  for (int day = 0; day < p.T; day += 2) {
+  const float invP = 1.0f / Pf;
+  for (int day = 0; day < p.T; day += 3) {
     const float x = fmaxf(A + R + D, 1.0f);
     const float g = a0 + __fdividef(al, 1.0f + __expf(nn * __logf(x)));
-    const float pSI = 1.0f - __expf(-g * __fdividef(I, Pf));
+    const float pSI = 1.0f - __expf(-g * (I * invP));
     const float LI = I * pI, LA = A * pA;
-    c += 2 * ((S * fminf(pSI, 1.0f - pSI) < 10.0f) + (I * qpI < 10.0f) + (A * qpA < 10.0f) +
+    c += 3 * ((S * fminf(pSI, 1.0f - pSI) < 10.0f) + (I * qpI < 10.0f) + (A * qpA < 10.0f) +
               (LI * qI < 10.0f) + (LA * qA < 10.0f));
     const float k1 = S * pSI;
-    S = fmaxf(S - 2.0f * k1, 0.0f);
-    I = fmaxf(I + 2.0f * (k1 - LI), 0.0f);
-    A = fmaxf(A + 2.0f * (LI * fI - LA), 0.0f);
-    R += 2.0f * LA * fA;
-    D += 2.0f * LA * (1.0f - fA);
+    S = fmaxf(S - 3.0f * k1, 0.0f);
+    I = fmaxf(I + 3.0f * (k1 - LI), 0.0f);
+    A = fmaxf(A + 3.0f * (LI * fI - LA), 0.0f);
+    R += 3.0f * LA * fA;
+    D += 3.0f * LA * (1.0f - fA);
     if (I > peak) {
       peak = I;
       dpk = day;
