@@ -362,10 +362,12 @@ ABC_API int abc_ex2_probe(double* ex2_per_second, void* stream);
  * [sqrt(2)/2, sqrt(2)], 8.4e6 pairs); which = 1 BINV's (a / k, every float a
  * in [2^-100, 2^100], k = 2..111, 1.8e11 pairs); which = 2 the square root
  * that replaces __fsqrt_rn in the binomial and Box-Muller draws the same way
- * (every float in [2^-24, 2^32), 4.7e8 values).  *mismatches receives the
- * count of operands whose result differs in any bit from CUDA's correctly
- * rounded one (0 expected).  ABC_E_INVAL for another which.  Synchronises
- * the stream. */
+ * (every float in [2^-24, 2^32), 4.7e8 values); which = 3 the uniform built
+ * from a Philox word's bits (1.m - (1 - 2^-24)) against its direct form
+ * ((x >> 9) + 1/2) 2^-23 by conversion (all 2^23 significands).
+ * *mismatches receives the count of operands whose result differs in any bit
+ * from the exact form's (0 expected).  ABC_E_INVAL for another which.
+ * Synchronises the stream. */
 ABC_API int abc_numerics_check(int32_t which, uint64_t* mismatches, void* stream);
 
 /* Stable LSD radix sort (no counterpart in the paper; the weight pass uses it

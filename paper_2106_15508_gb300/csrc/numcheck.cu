@@ -1,8 +1,9 @@
 // numcheck.cu -- device-side exhaustive checks of the short arithmetic
-// sequences that stand in for CUDA's correctly rounded division and square
-// root on bounded domains (div_nr, sqrt_nr in numerics.cuh): each check runs
-// both on every operand of the domain on this GPU and counts the results
-// that differ in any bit.
+// sequences that stand in for longer exact forms: CUDA's correctly rounded
+// division and square root on bounded domains (div_nr, sqrt_nr in
+// numerics.cuh) and the uniform's construction from bits (unif): each check
+// runs both on every operand of the domain on this GPU and counts the
+// results that differ in any bit.
 #include <cstring>
 
 #include "common.cuh"
@@ -56,6 +57,18 @@ __global__ void k_check_sqrt(uint32_t lo, uint32_t hi, unsigned long long* bad) 
   if (c) atomicAdd(bad, c);
 }
 
+// domain 3: every 23-bit significand m (the uniform of any word x with
+// x >> 9 = m): unif against (m + 1/2) 2^-23 by conversion, addition and scaling
+__global__ void k_check_unif(uint32_t lo, uint32_t hi, unsigned long long* bad) {
+  unsigned long long c = 0;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t m = lo + blockIdx.x * blockDim.x + threadIdx.x; m <= hi && m >= lo; m += stride) {
+    const float direct = __fmul_rn(__fadd_rn(__uint2float_rn(m), 0.5f), 0x1p-23f);
+    c += __float_as_uint(unif((m << 9) | (m & 0x1FFu))) != __float_as_uint(direct);
+  }
+  if (c) atomicAdd(bad, c);
+}
+
 int numerics_check(int which, unsigned long long* bad_host, cudaStream_t st) {
   uint32_t lo, hi;
   if (which == 0) {
@@ -67,6 +80,9 @@ int numerics_check(int which, unsigned long long* bad_host, cudaStream_t st) {
   } else if (which == 2) {
     lo = bits_of(0x1p-24f);
     hi = bits_of(0x1p32f) - 1u;
+  } else if (which == 3) {
+    lo = 0u;
+    hi = (1u << 23) - 1u;
   } else {
     return ABC_E_INVAL;
   }
@@ -77,7 +93,8 @@ int numerics_check(int which, unsigned long long* bad_host, cudaStream_t st) {
   if (rc == ABC_OK) {
     if (which == 0) k_check_div_log<<<152 * 8, 256, 0, st>>>(lo, hi, bad);
     else if (which == 1) k_check_div_binv<<<152 * 8, 256, 0, st>>>(lo, hi, bad);
-    else k_check_sqrt<<<152 * 8, 256, 0, st>>>(lo, hi, bad);
+    else if (which == 2) k_check_sqrt<<<152 * 8, 256, 0, st>>>(lo, hi, bad);
+    else k_check_unif<<<152 * 8, 256, 0, st>>>(lo, hi, bad);
     if (cudaGetLastError() != cudaSuccess) rc = ABC_E_CUDA;
   }
   if (rc == ABC_OK &&

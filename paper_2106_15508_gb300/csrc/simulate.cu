@@ -24,6 +24,20 @@ __device__ __forceinline__ void acc_sq(U128& a, int32_t x, int32_t o) {
   a.lo = lo;
 }
 
+// one day's three squared errors at once, for counts and observations in
+// [0, 2^31): each difference fits int32, each square is below 2^62 and their
+// sum below 2^64, so one 64-bit add with carry takes the day
+__device__ __forceinline__ void acc_day(U128& a, int32_t x0, int32_t o0, int32_t x1, int32_t o1,
+                                        int32_t x2, int32_t o2) {
+  const int32_t d0 = x0 - o0, d1 = x1 - o1, d2 = x2 - o2;
+  uint64_t s = static_cast<uint64_t>(static_cast<int64_t>(d0) * d0);
+  s += static_cast<uint64_t>(static_cast<int64_t>(d1) * d1);
+  s += static_cast<uint64_t>(static_cast<int64_t>(d2) * d2);
+  const uint64_t lo = a.lo + s;
+  a.hi += lo < s ? 1ull : 0ull;
+  a.lo = lo;
+}
+
 // theta_d = lo_d + u_d (hi_d - lo_d)  (Sec. 3.1 reparameterisation)
 __device__ __forceinline__ float theta_of(const SimParams& p, int d, float u) {
   return __fadd_rn(p.lo[d], __fmul_rn(u, __fsub_rn(p.hi[d], p.lo[d])));
@@ -39,7 +53,7 @@ constexpr int kBinvQueue = 96;  // three draws per lane per batch
 __device__ U128 saird_path(const SimParams& p, const float th[8], uint32_t c0, uint32_t c1,
                            uint32_t tag, const int32_t* obs, int32_t* traj, int64_t stride,
                            int64_t col, int32_t* ard, unsigned mask, BinvJob* bq,
-                           int32_t* last = nullptr) {
+                           int32_t* last = nullptr, bool obs_nonneg = false) {
   const float alpha0 = th[0], alpha = th[1], n = th[2], beta = th[3], gamma = th[4],
               delta = th[5], eta = th[6], kappa = th[7];
   // initial state (Sec. 2.2): Ru = 0, I0 = kappa A0, S = P - (A0 + R0 + D0 + I0)
@@ -149,9 +163,14 @@ __device__ U128 saird_path(const SimParams& p, const float th[8], uint32_t c0, u
       ard[2 * (T + 1) + day + 1] = D;
     }
     if (obs) {
-      acc_sq(acc, A, obs[0 * (T + 1) + day + 1]);
-      acc_sq(acc, R, obs[1 * (T + 1) + day + 1]);
-      acc_sq(acc, D, obs[2 * (T + 1) + day + 1]);
+      if (obs_nonneg) {
+        acc_day(acc, A, obs[0 * (T + 1) + day + 1], R, obs[1 * (T + 1) + day + 1], D,
+                obs[2 * (T + 1) + day + 1]);
+      } else {
+        acc_sq(acc, A, obs[0 * (T + 1) + day + 1]);
+        acc_sq(acc, R, obs[1 * (T + 1) + day + 1]);
+        acc_sq(acc, D, obs[2 * (T + 1) + day + 1]);
+      }
     }
   }
   if (last) {
@@ -195,11 +214,17 @@ k_simulate(SimParams p, const int32_t* __restrict__ obs,
   if (off_dev && *off_dev) return;  // run finished: nothing to simulate
   if (c1_dev) c1 = *c1_dev;         // counter word set on the device (graph launches)
   const int nobs = (p.model == ABC_MODEL_SAIRD && obs) ? 3 * (p.T + 1) : 0;
-  for (int i = threadIdx.x; i < nobs; i += blockDim.x) s_obs[i] = obs[i];
+  int obs_ok = 1;
+  for (int i = threadIdx.x; i < nobs; i += blockDim.x) {
+    s_obs[i] = obs[i];
+    obs_ok &= s_obs[i] >= 0;
+  }
   // the warps' inversion queues follow the observations (16-byte aligned)
   BinvJob* bq = reinterpret_cast<BinvJob*>(s_obs + ((nobs + 3) & ~3)) +
                 (threadIdx.x >> 5) * kBinvQueue;
-  __syncthreads();
+  // every observation non-negative (block-uniform): the days' squared errors
+  // go in with one carry each
+  const bool obs_nonneg = __syncthreads_and(obs_ok) != 0;
   // perm (nullable): thread t runs slot perm[t] (an order that groups similar
   // trajectories into warps); every slot keeps its own counters and outputs
   // (with n_dev, over the slots in use only; the others keep their place)
@@ -237,7 +262,7 @@ k_simulate(SimParams p, const int32_t* __restrict__ obs,
   } else {
     int32_t last[3];
     const U128 a = saird_path(p, th, c0, c1, tag, nobs ? s_obs : nullptr, traj, n, i, nullptr,
-                              mask, bq, last);
+                              mask, bq, last, obs_nonneg);
     dist[i] = __dsqrt_rn(u128_to_double(a.hi, a.lo));
     if (ard_last) {
       ard_last[0 * n + i] = last[0];

@@ -3,8 +3,9 @@ corrected once by its exact remainder, after Markstein) that the logarithm and t
 on bounded operand domains equals CUDA's correctly rounded __fdiv_rn on
 every operand pair of those domains, and the square root of the binomial and
 Box-Muller draws (reciprocal-square-root approximation, one remainder
-correction) equals __fsqrt_rn on [2^-24, 2^32); all enumerated on the
-device."""
+correction) equals __fsqrt_rn on [2^-24, 2^32); and the uniform built from
+a Philox word's bits equals its direct form by integer-to-float conversion
+for every 23-bit significand; all enumerated on the device."""
 import pytest
 
 import paper_2106_15508_gb300 as G
@@ -22,7 +23,7 @@ def _setup():
     G.lib()
 
 
-@pytest.mark.parametrize("which", [0, 1, 2])
+@pytest.mark.parametrize("which", [0, 1, 2, 3])
 def test_short_sequences_are_exact_on_their_domains(which):
     assert G.abc_numerics_check(which) == 0
 

@@ -141,6 +141,32 @@ def test_simulate_ragged_skip_and_counter_index(n):
     assert np.all(np.isinf(d[skip == 1]))
 
 
+@pytest.mark.parametrize("kind", ["negative", "extreme"])
+def test_simulate_distance_with_unusual_observations(kind):
+    """The day's three squared errors go into the 128-bit distance with one
+    carry when every observation is a count (non-negative); a series with
+    negative entries takes the three-carry path.  Both must equal the
+    oracle's exact integer sum: negative entries down to INT32_MIN (squares
+    up to 2^64 - 2^33 + 1), and counts up to INT32_MAX (the one-carry path
+    at its bound: three squares near 2^62 per day)."""
+    cfg = saird_config(4097, 40, 100_000, seed=12)
+    obs, _, _ = oracle_obs(cfg)
+    obs = obs.copy()
+    r = IN.rng(13)
+    if kind == "negative":
+        obs[:, 1::3] = -obs[:, 1::3]
+        obs[0, 5] = np.iinfo(np.int32).min
+        obs[2, 7] = -1
+    else:
+        obs[:, 2::4] = np.iinfo(np.int32).max
+        obs[1, 3::5] = r.integers(2**30, 2**31 - 1, obs[1, 3::5].shape)
+    m = oracle_model(cfg, obs)
+    u = IN.unit_particles(4097, 14)
+    d = _sim_gpu(cfg, obs, u, c1=5)
+    od = O.simulate(m, u, c1=5, nthreads=8)
+    assert np.array_equal(d.view(np.uint64), od.view(np.uint64))
+
+
 def test_simulate_gaussian_toy_bitexact():
     lo, hi = [-10.0] * 8, [10.0] * 8
     cfg = G.config(model=G.ABC_MODEL_GAUSS_TOY, n_days=1, population=1, init_ard=[0, 0, 0],
