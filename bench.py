@@ -37,10 +37,10 @@ MUFU_EX2_PER_CLK_PER_SM = 16  # 32-bit exp2 issue rate of one SM (4 SMSPs x 4 la
 TC_K_USED = 60  # split-bf16 products per pair in the tensor-core weight GEMM (10 features x 6)
 K_EFF = 10  # features of the weight pass's inner product (its algorithmic K)
 # k_simulate per particle-day, from one ncu capture of every simulator launch of a whole
-# 20-generation run of the 262,144-particle case of the workload (54 launches, 1.698e9
+# 20-generation run of the 262,144-particle case of the workload (58 launches, 1.824e9
 # particle-days): smsp__thread_inst_executed.sum / particle-days, and DRAM read + write bytes
-SIM_THREAD_INST_PER_DAY = 967.9
-SIM_DRAM_BYTES_PER_DAY = 0.3117
+SIM_THREAD_INST_PER_DAY = 941.7
+SIM_DRAM_BYTES_PER_DAY = 0.3115
 
 
 def _peaks():
