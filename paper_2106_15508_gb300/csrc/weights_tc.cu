@@ -79,6 +79,8 @@ void set_tc_wait_limit(uint64_t ns) { g_tc_wait_ns.store(ns ? ns : kWaitNs); }
 constexpr float kPadLogit = -1.0e30f;
 constexpr int kCandCap = 32;          // listed columns per (row, partial slot)
 constexpr float kCandMargin = 45.0f;  // log2 units: listed = within 45 bits of the maximum
+constexpr float kFixSpan = 60.0f;     // log2 units: class-0 rows whose maximum is known within
+                                      // 60 bits of an upper bound sum against that bound
 // error bound of the tensor-core exponent up to which its row value is kept:
 // the value of B at s = 1e-3 with |x|, |y| <= sqrt 2 (0.0166, natural log)
 constexpr float kTcBoundMax = 0x1p-24f * (64.0f * (6.0f * 721.34752f + 32.0f) + 160.0f);
@@ -164,7 +166,7 @@ __device__ __forceinline__ void store_packed_row(__nv_bfloat16* tile, int r, con
 __global__ void k_tc_pack_rows(const float* __restrict__ up, const float* __restrict__ s,
                                int64_t rows, const float* __restrict__ centre,
                                const unsigned* __restrict__ y2max, AncInfo ai,
-                               double* __restrict__ rowc, float2* __restrict__ rinfo,
+                               double* __restrict__ rowc, float4* __restrict__ rinfo,
                                uint8_t* __restrict__ rcls, float* __restrict__ rrad2,
                                const unsigned* __restrict__ cbox, uint32_t* __restrict__ rkey) {
   const int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -209,8 +211,22 @@ __global__ void k_tc_pack_rows(const float* __restrict__ up, const float* __rest
   const float mag = L * (2.0f * X * Y + Y * Y) + 32.0f;
   const float delta = 0x1p-24f * 64.0f * mag;
   const float B = 0x1p-24f * (64.0f * mag + 160.0f);
-  rinfo[j] = make_float2(lb, delta);
   const uint8_t cls = B <= kTcBoundMax ? 0 : (isfinite(delta) && delta < 1e30f ? 1 : 2);
+  // Fixed reference of a class-0 row: an upper bound of its accumulator
+  // values.  Every exact exponent is at most 0 (c_k < 0, squared distances
+  // >= 0), so a value is at most L |x|^2 (the frame's shift) plus its error
+  // delta; 2^-19 of L |x|^2 and one bit cover the fp32 rounding of this
+  // estimate.  When the ancestor's lower bound of the maximum lies within
+  // kFixSpan bits of it, the epilogue sums 2^(v - ofs) with this reference
+  // instead of a running maximum: every term is at most 1 and the largest at
+  // least 2^-(kFixSpan + delta), so the terms that flush to zero (under
+  // 2^-126 each) are a negligible part of the sum.  NaN: not eligible.
+  float ofs = __int_as_float(0x7fc00000);
+  if (cls == 0 && lb > -__int_as_float(0x7f800000)) {
+    const float ub = L * xxf * (1.0f + 0x1p-19f) + delta + 1.0f;
+    if (ub - lb <= kFixSpan) ofs = ub;
+  }
+  rinfo[j] = make_float4(lb, delta, ofs, 0.0f);
   rcls[j] = cls;
   // Candidate radius.  The epilogue lists column k only if its accumulator
   // value exceeds lb - delta - kCandMargin (lb only rises), and that value is
@@ -589,7 +605,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
              const int* __restrict__ nc_p, int64_t rows,
              float2* __restrict__ part, unsigned* err, const int* __restrict__ off_dev,
-             const float2* __restrict__ rinfo, const uint8_t* __restrict__ rcls,
+             const float4* __restrict__ rinfo, const uint8_t* __restrict__ rcls,
              int* __restrict__ cand, int* __restrict__ ccnt, const int* __restrict__ perm,
              const float* __restrict__ rbox, const float* __restrict__ cbox,
              unsigned long long* __restrict__ tile_count, uint64_t wait_ns) {
@@ -771,12 +787,16 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     // warp single-class.
     const bool w_exp = __any_sync(0xffffffffu, cls == 0);
     const bool w_cand = __any_sync(0xffffffffu, refine);
-    float lb = -INFINITY, dl = 0.0f;
+    float lb = -INFINITY, dl = 0.0f, ofs = 0.0f;
     if (refine) {
-      const float2 ri = rinfo[row];
+      const float4 ri = rinfo[row];
       lb = ri.x;
       dl = ri.y;
+    } else if (cls == 0) {
+      ofs = rinfo[row].z;
     }
+    // warp-uniform: every class-0 row of the warp has a fixed reference
+    const bool w_fix = __all_sync(0xffffffffu, cls != 0 || ofs == ofs);
     int* lst = cand + (slot * rows + (refine ? row : 0)) * kCandCap;
     int nlist = 0;
     // The tile loop is compiled once per warp kind (exponential sums,
@@ -784,9 +804,10 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     // above, so that a warp of class-0 rows carries no candidate code (a
     // thread-varying class test inside one loop body was if-converted into
     // per-column predicated work).
-    auto tile_loop = [&](auto exp_kind, auto cand_kind) {
+    auto tile_loop = [&](auto exp_kind, auto cand_kind, auto fix_kind) {
       constexpr bool kExp = decltype(exp_kind)::value;
       constexpr bool kCand = decltype(cand_kind)::value;
+      constexpr bool kFix = decltype(fix_kind)::value;
       if constexpr (kExp && !kCand) {
         // Exponential sums only: software-pipelined TMEM reads.  The load of
         // a tile's second chunk runs while its first chunk is summed, and the
@@ -798,7 +819,26 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
         // running maximum takes the chunk's; the sums scale by
         // 2^(m_old - m_new), 0 on the first chunk from -inf), then 2^(v - m)
         // in packed fp32x2 with four independent accumulators
+        // (with a fixed reference, kFix: 2^(v - ofs) directly, no maximum)
+        if constexpr (kFix) m = ofs;
         auto sum_chunk = [&](const uint32_t (&r)[32], float& ts) {
+          if constexpr (kFix) {
+            const unsigned long long o2 = f2_pack(ofs, ofs);
+            unsigned long long acc[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a] = f2_pack(0.0f, 0.0f);
+#pragma unroll
+            for (int i = 0; i < 32; i += 2) {
+              float d0, d1;
+              f2_unpack(f2_sub(f2_pack(__uint_as_float(r[i]), __uint_as_float(r[i + 1])), o2), d0,
+                        d1);
+              acc[(i >> 1) & 3] = f2_add(acc[(i >> 1) & 3], f2_pack(ex2(d0), ex2(d1)));
+            }
+            float a0, a1;
+            f2_unpack(f2_add(f2_add(acc[0], acc[1]), f2_add(acc[2], acc[3])), a0, a1);
+            ts += a0 + a1;
+            return;
+          }
           float t1[12];
 #pragma unroll
           for (int k = 0; k < 10; ++k)
@@ -967,10 +1007,11 @@ k_weights_tc(const uint8_t* __restrict__ Apk, const uint8_t* __restrict__ Bpk,
     };
     using Yes = std::true_type;
     using No = std::false_type;
-    if (w_exp && w_cand) tile_loop(Yes{}, Yes{});
-    else if (w_exp) tile_loop(Yes{}, No{});
-    else if (w_cand) tile_loop(No{}, Yes{});
-    else tile_loop(No{}, No{});
+    if (w_exp && w_cand) tile_loop(Yes{}, Yes{}, No{});
+    else if (w_exp && w_fix) tile_loop(Yes{}, No{}, Yes{});
+    else if (w_exp) tile_loop(Yes{}, No{}, No{});
+    else if (w_cand) tile_loop(No{}, Yes{}, No{});
+    else tile_loop(No{}, No{}, No{});
     if (row >= 0) {
       if (cls == 0) part[slot * rows + row] = make_float2(m, S);
       ccnt[slot * rows + row] = refine ? nlist : 0;
@@ -1295,7 +1336,7 @@ static TcLayout tc_layout(int64_t rows, int64_t ncap, int mult) {
   take(l.rowc, sizeof(double) * R);
   take(l.part, sizeof(float2) * slots * R);
   take(l.err, sizeof(unsigned));
-  take(l.rinfo, sizeof(float2) * R);
+  take(l.rinfo, sizeof(float4) * R);
   take(l.rcls, R);
   take(l.cand, sizeof(int) * slots * R * kCandCap);
   take(l.ccnt, sizeof(int) * slots * R);
@@ -1367,7 +1408,7 @@ int launch_weights_tc(const float* up, const float* s, int64_t rows, const float
   auto* rowc = reinterpret_cast<double*>(b + l.rowc);
   auto* part = reinterpret_cast<float2*>(b + l.part);
   auto* err = reinterpret_cast<unsigned*>(b + l.err);
-  auto* rinfo = reinterpret_cast<float2*>(b + l.rinfo);
+  auto* rinfo = reinterpret_cast<float4*>(b + l.rinfo);
   auto* rcls = reinterpret_cast<uint8_t*>(b + l.rcls);
   auto* cand = reinterpret_cast<int*>(b + l.cand);
   auto* ccnt = reinterpret_cast<int*>(b + l.ccnt);
