@@ -31,8 +31,9 @@
 //   warps 0-15: epilogue, one thread per row (TMEM lane) and column group:
 //             warps w, w + 4, w + 8, w + 12 share TMEM lanes 32 (w % 4) ..
 //             and take every fourth 32-column chunk (tcgen05.ld); class-0
-//             warps keep an online max and sum of 2^(e - m), class-1 warps
-//             the chunk maxima and their candidate lists
+//             warps keep a sum of 2^(e - m) against a fixed per-row upper
+//             bound m (k_tc_pack_rows) or, without one, an online maximum;
+//             class-1 warps the chunk maxima and their candidate lists
 // Operands are packed by prep kernels in the canonical K-major layout
 // without swizzle: 8 x 8 bf16 core matrices (128 contiguous bytes), the 8
 // core matrices of a row group consecutive along K (LBO = 128 B), row groups
