@@ -588,8 +588,18 @@ def run_eps_final(args):
     def stats_of(get, n):
         return [get(t) for t in range(n)]
 
+    def ctx_stats(ctx):
+        # recorded generations of a context: the completed ones, and a last
+        # one that stopped on its batch budget (recorded, not counted)
+        n = G.abc_generations(ctx)
+        try:
+            G.abc_get_stats(ctx, n)
+            return n + 1
+        except G.AbcError:
+            return n
+
     # (1) plain
-    eps_final, t_plain, sims_plain = [], [], []
+    eps_final, t_plain, sims_plain, gens_plain = [], [], [], []
     for c, o in zip(cfgs, obs):
         ctx = G.abc_init(c, o, stream=sp)
         try:
@@ -598,11 +608,23 @@ def run_eps_final(args):
             G.abc_run(ctx, gens + 1)
             torch.cuda.synchronize()
             t_plain.append(time.perf_counter() - t0)
-            st = stats_of(lambda t: G.abc_get_stats(ctx, t), G.abc_generations(ctx))
+            st = stats_of(lambda t: G.abc_get_stats(ctx, t), ctx_stats(ctx))
             eps_final.append(st[-1].eps)
             sims_plain.append(sum(x.sims for x in st))
+            gens_plain.append(len(st) - 1)
         finally:
             G.abc_free(ctx)
+    def batch_gens(b, r):
+        # generations run r of batch b completed (a run can stop before the
+        # others: its stage budget exhausted, or its stop rule met)
+        n = 0
+        while True:
+            try:
+                G.abc_batch_get_stats(b, r, n)
+                n += 1
+            except G.AbcError:
+                return n
+
     # (2) batched
     b = G.abc_batch_init(cfgs, obs, stream=sp)
     try:
@@ -611,8 +633,7 @@ def run_eps_final(args):
         G.abc_batch_run(b, gens + 1)
         torch.cuda.synchronize()
         t_batch = time.perf_counter() - t0
-        last = G.abc_batch_generations(b) - 1
-        eps_b = [G.abc_batch_get_stats(b, r, last).eps for r in range(R)]
+        eps_b = [G.abc_batch_get_stats(b, r, batch_gens(b, r) - 1).eps for r in range(R)]
     finally:
         G.abc_batch_free(b)
 
@@ -650,14 +671,7 @@ def run_eps_final(args):
         torch.cuda.synchronize()
         t_sur_batch = time.perf_counter() - t0
         for r in range(R):
-            n = 0
-            while True:
-                try:
-                    G.abc_batch_get_stats(b, r, n)
-                    n += 1
-                except G.AbcError:
-                    break
-            sb.append(sur_summary(lambda t, r=r: G.abc_batch_get_stats(b, r, t), n))
+            sb.append(sur_summary(lambda t, r=r: G.abc_batch_get_stats(b, r, t), batch_gens(b, r)))
     finally:
         G.abc_batch_free(b)
     # (4) surrogate alone
@@ -670,7 +684,7 @@ def run_eps_final(args):
             G.abc_run(ctx, 3 * gens + 1)
             torch.cuda.synchronize()
             t_sur.append(time.perf_counter() - t0)
-            ss.append(sur_summary(lambda t: G.abc_get_stats(ctx, t), G.abc_generations(ctx)))
+            ss.append(sur_summary(lambda t: G.abc_get_stats(ctx, t), ctx_stats(ctx)))
         finally:
             G.abc_free(ctx)
     per = lambda xs: float(np.mean(xs)) if len(xs) else None
@@ -687,6 +701,7 @@ def run_eps_final(args):
             "plain_s_per_run": per(t_plain),
             "batched_s_per_run": t_batch / R,
             "batched_same_eps": bool(np.all(np.array(eps_b) == np.array(eps_final))),
+            "plain_generations": gens_plain,
             "surrogate_batched_s_per_run": t_sur_batch / R,
             "surrogate_batched_reached": reached(sb),
             "surrogate_batched_generations": per([x["gens"] for x in sb]),

@@ -491,7 +491,10 @@ ABC_API int abc_reset(abc_ctx* ctx, uint32_t run_id);
  * memory (device-to-device copy on the context stream), else host. */
 ABC_API int abc_get_population(abc_ctx* ctx, float* u, double* dist, double* W, float* s, int32_t* anc,
                        int32_t on_device);
-/* Stats of generation t (0 <= t < abc_generations(ctx)). */
+/* Stats of generation t: 0 <= t < abc_generations(ctx) (the completed
+ * generations), and t = abc_generations(ctx) when the last generation stopped
+ * on its batch budget (recorded with status ABC_STOP_BUDGET, not counted;
+ * batched runs record it the same way). */
 ABC_API int abc_get_stats(abc_ctx* ctx, int32_t t, abc_gen_stats* out);
 ABC_API int32_t abc_generations(const abc_ctx* ctx);
 /* abc_predict on the context's current population (its weights, its

@@ -108,6 +108,7 @@ def test_batch_budget_stop_is_per_run():
     cfgs[1].max_batches = 1
     obs = [oracle_obs(c)[0] for c in cfgs]
     b = G.abc_batch_init(cfgs, obs)
+    ctx = G.abc_init(cfgs[1], obs[1])
     try:
         G.abc_batch_run(b, 4)
         assert G.abc_batch_get_stats(b, 1, 1).status == G.ABC_STOP_BUDGET
@@ -115,8 +116,17 @@ def test_batch_budget_stop_is_per_run():
             G.abc_batch_get_stats(b, 1, 2)    # the stopped run records nothing more
         for r in (0, 2, 3):
             assert G.abc_batch_get_stats(b, r, 3).status == 0
+        # the run alone in a context: the same stopped generation, recorded
+        # after the completed ones (and not counted by abc_generations)
+        assert G.abc_run(ctx, 4) == G.ABC_STOP_BUDGET
+        assert G.abc_generations(ctx) == 1
+        x, y = G.abc_get_stats(ctx, 1), G.abc_batch_get_stats(b, 1, 1)
+        assert (x.status, x.eps, x.batches, x.sims) == (y.status, y.eps, y.batches, y.sims)
+        with pytest.raises(G.AbcError):
+            G.abc_get_stats(ctx, 2)
     finally:
         G.abc_batch_free(b)
+        G.abc_free(ctx)
 
 
 def test_autotune_keeps_results_and_writes_cache(tmp_path):
