@@ -39,3 +39,18 @@ def test_device_constants_are_correctly_rounded():
         assert np.float32(float(consts[name])) == _rn32(v), name
     # the 15-bit head makes e * LN2_HI exact for |e| < 2^9
     assert (int(np.float32(0.693145751953125).view(np.uint32)) & 0x1FF) == 0
+
+
+def test_uniform_from_bits_equals_direct_form():
+    """unif() builds ((x >> 9) + 1/2) 2^-23 as 1.m - (1 - 2^-24) from the bits of
+    x: the float 1.m is exact and so is the difference, so one rounded
+    subtraction gives the direct form exactly, for all 2^23 significands
+    (the device check abc_numerics_check(3) repeats this on the GPU)."""
+    src = open(SRC).read()
+    assert "__uint_as_float((x >> 9) | 0x3F800000u), 0x1.fffffep-1f" in src
+    m = np.arange(1 << 23, dtype=np.uint32)
+    direct = (m.astype(np.float32) + np.float32(0.5)) * np.float32(2.0**-23)
+    one_m = (m | np.uint32(0x3F800000)).view(np.float32)
+    bits = one_m - np.float32(1.0 - 2.0**-24)
+    assert np.float32(1.0 - 2.0**-24).view(np.uint32) == 0x3F7FFFFF
+    assert np.array_equal(direct.view(np.uint32), bits.view(np.uint32))
